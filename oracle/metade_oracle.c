@@ -1,0 +1,525 @@
+/*
+ * metade_oracle.c -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, FP64 CPU restatement of the MetaDE hot path: the
+ * parameterised DE (PDE) generation step of Alg. 2, its mutation (Eq. of
+ * Sec. III-A-2, "DE/bl-to-br/dn"), the three crossover schemes of Sec. II-A
+ * (binomial, exponential, arithmetic), greedy selection (Alg. 1/2), the
+ * best-fitness reduction that becomes the meta-fitness (Sec. III-B), the
+ * evolver's rand/1/bin step with floor decoding (Alg. 3), and the synthetic
+ * shifted-rotated objectives used as the CEC2022 stand-in.
+ *
+ * Only the tests, the smoke check and the benchmark's CPU-baseline leg may
+ * load this file.  It shares no code, header or table with the CUDA path;
+ * the random numbers it draws come from its own Philox4x32-10, written from
+ * the published definition (Salmon, Moraes, Dror, Shaw, "Parallel random
+ * numbers: as easy as 1, 2, 3", SC'11).
+ *
+ * Readings of points the paper leaves open (each one also has a test):
+ *  - generational ("tensorised", Alg. 2): every trial of a generation is
+ *    built from the population as it was at the start of that generation;
+ *  - "rand <= CR" is taken as the strict integer compare (w >> 8) < ceil(CR 2^24)
+ *    with CR held as a float32 value, so CR = 0 never and CR = 1 always passes;
+ *  - j_rand, the exponential start n and the pbest pick are 0-based;
+ *  - exponential length L: L = 1, then L grows while L < D and the L-th
+ *    uniform (0-based L-1) is below CR;
+ *  - K_i is one uniform per individual; it is drawn but unused unless the
+ *    crossover scheme is arithmetic;
+ *  - all rand indices of one individual are mutually distinct and differ from
+ *    i; best, pbest and current are not constrained (JADE convention);
+ *  - pbest: top k_p = max(1, ceil(NP * pct / 100)) by stored fitness, ties by
+ *    lower index; best is the first of that order;
+ *  - trial vectors are clipped to the box [lo, hi];
+ *  - NaN fitness counts as +inf; a tie accepts the trial (f(u) <= f(x)).
+ *
+ * Draw layout (both implementations follow it independently):
+ *   key     = (seed_lo32, seed_hi32 ^ TAG)          TAG_INNER / TAG_OUTER
+ *   counter = (stream, generation, individual, (epoch << 16) | slot)
+ *   inner slot 0      : [j_rand, exp start n, K_i, pbest pick]
+ *   inner slots 1..3  : rand index draws t = 0..8 (word t % 4 of slot 1 + t/4)
+ *   inner slot 4+j/4  : crossover uniform of coordinate j (word j % 4)
+ *   initialisation    : generation 0xFFFFFFFF, slot j/4 word j%4 -> coordinate j
+ *   outer slot 0      : [j_rand]; slot 1: three rand draws; slots 2,3: genes 0..5
+ *   uniform           : (w >> 8) * 2^-24;   integer in [0, m): floor(w m / 2^32)
+ *   t-th distinct draw: s = floor(w_t (NP-1-t) / 2^32); the s-th smallest
+ *                       member of {0..NP-1} \ ({i} U {r_0..r_{t-1}})
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_TAG_INNER 0x4D455441u
+#define OR_TAG_OUTER 0x4F555445u
+#define OR_INIT_GEN 0xFFFFFFFFu
+#define OR_REC 18 /* int32 record fields per individual, see or_pde_step */
+
+static const double OR_PI = 3.14159265358979323846;
+static const double OR_E = 2.71828182845904523536;
+
+/* ---------------------------------------------------------------- Philox */
+
+/* Philox4x32 with 10 rounds (SC'11, Sec. 3.2/Table 2): each round multiplies
+ * counter words 0 and 2 by the two round constants, swaps the halves and
+ * mixes in the key; the key is bumped by the Weyl constants between rounds. */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; round++) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static void or_slot(uint64_t seed, uint32_t tag, uint32_t stream, uint32_t gen,
+                    uint32_t indiv, uint32_t epoch, uint32_t slot, uint32_t w[4])
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32) ^ tag};
+    uint32_t ctr[4] = {stream, gen, indiv, (epoch << 16) | slot};
+    or_philox4x32_10(ctr, key, w);
+}
+
+/* word t of the stream that starts at slot `first` */
+static uint32_t or_word(uint64_t seed, uint32_t tag, uint32_t stream, uint32_t gen,
+                        uint32_t indiv, uint32_t epoch, uint32_t first, uint32_t t)
+{
+    uint32_t w[4];
+    or_slot(seed, tag, stream, gen, indiv, epoch, first + t / 4, w);
+    return w[t % 4];
+}
+
+static double or_uniform(uint32_t w) { return (double)(w >> 8) * (1.0 / 16777216.0); }
+
+static uint32_t or_below(uint32_t w, uint32_t m) { return (uint32_t)(((uint64_t)w * m) >> 32); }
+
+/* probability threshold: U < p  <=>  (w >> 8) < ceil(p * 2^24), p taken as float32 */
+static uint32_t or_threshold(double p)
+{
+    float pf = (float)p;
+    if (!(pf > 0.0f)) return 0u;
+    if (pf >= 1.0f) return 16777216u;
+    return (uint32_t)ceil((double)pf * 16777216.0);
+}
+
+/* The t-th distinct draw, written as the plain definition: list the
+ * admissible indices in increasing order and take the s-th one. */
+int or_distinct_draws(int np, int i, int m, const uint32_t *w, int32_t *r)
+{
+    if (m > np - 1) return -1;
+    int *cand = (int *)malloc(sizeof(int) * (size_t)np);
+    for (int t = 0; t < m; t++) {
+        int n = 0;
+        for (int c = 0; c < np; c++) {
+            int taken = (c == i);
+            for (int q = 0; q < t; q++) taken |= (c == r[q]);
+            if (!taken) cand[n++] = c;
+        }
+        uint32_t s = or_below(w[t], (uint32_t)(np - 1 - t));
+        r[t] = cand[s];
+    }
+    free(cand);
+    return 0;
+}
+
+/* ------------------------------------------------------------ objectives */
+
+/* z = R (x - o), R row-major */
+static void or_rotate(int dim, const double *x, const double *o, const double *R, double *z)
+{
+    for (int r = 0; r < dim; r++) {
+        double acc = 0.0;
+        for (int c = 0; c < dim; c++) acc += R[(size_t)r * dim + c] * (x[c] - o[c]);
+        z[r] = acc;
+    }
+}
+
+/* Textbook objective definitions on the rotated vector z. */
+double or_objective(int obj, int dim, const double *z)
+{
+    double f = 0.0;
+    switch (obj) {
+    case 0: /* sphere */
+        for (int j = 0; j < dim; j++) f += z[j] * z[j];
+        return f;
+    case 1: /* Rosenbrock evaluated on y = z + 1, so that the optimum sits at z = 0 */
+        for (int j = 0; j + 1 < dim; j++) {
+            double y0 = z[j] + 1.0, y1 = z[j + 1] + 1.0;
+            f += 100.0 * (y1 - y0 * y0) * (y1 - y0 * y0) + (y0 - 1.0) * (y0 - 1.0);
+        }
+        return f;
+    case 2: /* Rastrigin */
+        for (int j = 0; j < dim; j++) f += z[j] * z[j] - 10.0 * cos(2.0 * OR_PI * z[j]) + 10.0;
+        return f;
+    case 3: { /* Griewank */
+        double s = 0.0, p = 1.0;
+        for (int j = 0; j < dim; j++) {
+            s += z[j] * z[j] / 4000.0;
+            p *= cos(z[j] / sqrt((double)(j + 1)));
+        }
+        return s - p + 1.0;
+    }
+    case 4: { /* Ackley */
+        double s = 0.0, c = 0.0;
+        for (int j = 0; j < dim; j++) {
+            s += z[j] * z[j];
+            c += cos(2.0 * OR_PI * z[j]);
+        }
+        return -20.0 * exp(-0.2 * sqrt(s / dim)) - exp(c / dim) + 20.0 + OR_E;
+    }
+    case 5: { /* Schwefel 1.2 */
+        double pre = 0.0;
+        for (int j = 0; j < dim; j++) {
+            pre += z[j];
+            f += pre * pre;
+        }
+        return f;
+    }
+    default:
+        return NAN;
+    }
+}
+
+double or_eval(int obj, int dim, const double *x, const double *o, const double *R)
+{
+    double *z = (double *)malloc(sizeof(double) * (size_t)(dim > 0 ? dim : 1));
+    or_rotate(dim, x, o, R, z);
+    double f = or_objective(obj, dim, z);
+    free(z);
+    return f;
+}
+
+static double or_fitness(int obj, int dim, const double *x, const double *o, const double *R)
+{
+    double f = or_eval(obj, dim, x, o, R);
+    return isnan(f) ? INFINITY : f;
+}
+
+/* ------------------------------------------------------- initialisation */
+
+/* Alg. 2 line 1 (Alg. 1 line 1): uniform in the box. */
+void or_init_pop(int np, int dim, uint64_t seed, uint32_t stream, uint32_t epoch,
+                 double lo, double hi, double *pop)
+{
+    for (int i = 0; i < np; i++)
+        for (int j = 0; j < dim; j++) {
+            uint32_t w = or_word(seed, OR_TAG_INNER, stream, OR_INIT_GEN, (uint32_t)i, epoch, 0, (uint32_t)j);
+            pop[(size_t)i * dim + j] = lo + (hi - lo) * or_uniform(w);
+        }
+}
+
+/* Alg. 2 line 2 */
+void or_eval_pop(int np, int dim, int obj, const double *o, const double *R,
+                 const double *pop, double *fit)
+{
+    for (int i = 0; i < np; i++) fit[i] = or_fitness(obj, dim, pop + (size_t)i * dim, o, R);
+}
+
+/* ------------------------------------------------------------ PDE step */
+
+static int or_kp(int np, int pct)
+{
+    int k = (np * pct + 99) / 100;
+    return k < 1 ? 1 : k;
+}
+
+/* indices sorted by (fitness, index) ascending: insertion sort, plain */
+static void or_order(int np, const double *fit, int *order)
+{
+    for (int i = 0; i < np; i++) {
+        int j = i;
+        while (j > 0) {
+            int a = order[j - 1];
+            if (fit[a] > fit[i] || (fit[a] == fit[i] && a > i)) {
+                order[j] = order[j - 1];
+                j--;
+            } else break;
+        }
+        order[j] = i;
+    }
+}
+
+int or_required_np(int bl, int br, int dn)
+{
+    int a = (bl == 1 || br == 1) ? 1 : 0;
+    return a + 2 * dn + 1;
+}
+
+/*
+ * One generation of PDE (Alg. 2 lines 7-10) on one instance, in place.
+ *
+ * pop [np*dim], fit [np]: the generation-start state (in), the next state (out).
+ * theta = (F, CR, bl, br, dn, cs), categorical entries integral.
+ * Optional outputs (NULL to skip):
+ *   trial [np*dim], ftrial [np], accept [np],
+ *   mask [np*dim] (1 where the trial coordinate came from the mutant; all 1
+ *        for arithmetic recombination),
+ *   rec [np*OR_REC]: base-left index, base-right index, j_rand, exp start n,
+ *        exp length L (0 unless exponential), K_i raw 24-bit value, pbest
+ *        index, best index, m, r_0..r_8 (-1 when unused).
+ * Returns 0, or -1 when np is too small for the strategy, -2 on bad theta.
+ */
+int or_pde_step(int np, int dim, int obj, const double *o, const double *R,
+                double lo, double hi, uint64_t seed, uint32_t stream, uint32_t epoch, uint32_t gen,
+                int p_best_pct, const double *theta, double *pop, double *fit,
+                double *trial, double *ftrial, int32_t *accept, uint8_t *mask, int32_t *rec)
+{
+    double F = theta[0], CR = theta[1];
+    int bl = (int)theta[2], br = (int)theta[3], dn = (int)theta[4], cs = (int)theta[5];
+    if (bl < 1 || bl > 4 || br < 1 || br > 4 || dn < 1 || dn > 4 || cs < 1 || cs > 3) return -2;
+    if (np < or_required_np(bl, br, dn) || dim < 1) return -1;
+
+    int a = (bl == 1 || br == 1) ? 1 : 0;
+    int m = a + 2 * dn;
+    int kp = or_kp(np, p_best_pct);
+    uint32_t cri = or_threshold(CR);
+
+    int *order = (int *)malloc(sizeof(int) * (size_t)np);
+    or_order(np, fit, order);
+    int best = order[0];
+
+    double *U = (double *)malloc(sizeof(double) * (size_t)np * dim);
+    double *fU = (double *)malloc(sizeof(double) * (size_t)np);
+    uint8_t *M = (uint8_t *)malloc((size_t)np * dim);
+    double *v = (double *)malloc(sizeof(double) * (size_t)dim);
+
+    for (int i = 0; i < np; i++) {
+        uint32_t w0[4];
+        or_slot(seed, OR_TAG_INNER, stream, gen, (uint32_t)i, epoch, 0, w0);
+        int jrand = (int)or_below(w0[0], (uint32_t)dim);
+        int nstart = (int)or_below(w0[1], (uint32_t)dim);
+        uint32_t kraw = w0[2] >> 8;
+        double K = or_uniform(w0[2]);
+        int pbest = order[or_below(w0[3], (uint32_t)kp)];
+
+        uint32_t wr[9];
+        int32_t r[9];
+        for (int t = 0; t < 9; t++) r[t] = -1;
+        for (int t = 0; t < m; t++) wr[t] = or_word(seed, OR_TAG_INNER, stream, gen, (uint32_t)i, epoch, 1, (uint32_t)t);
+        or_distinct_draws(np, i, m, wr, r);
+
+        int ib[5];
+        ib[1] = r[0]; /* meaningful only when a rand base is used */
+        ib[2] = best;
+        ib[3] = pbest;
+        ib[4] = i;
+        const double *xl = pop + (size_t)ib[bl] * dim;
+        const double *xr = pop + (size_t)ib[br] * dim;
+        const double *xi = pop + (size_t)i * dim;
+
+        /* Eq. (PDE mutation): v = x_bl + F (x_br - x_bl) + F (D_1 + ... + D_dn) */
+        for (int j = 0; j < dim; j++) {
+            double sum = 0.0;
+            for (int q = 0; q < dn; q++)
+                sum += pop[(size_t)r[a + 2 * q] * dim + j] - pop[(size_t)r[a + 2 * q + 1] * dim + j];
+            double dir = (bl != br) ? F * (xr[j] - xl[j]) : 0.0;
+            v[j] = xl[j] + dir + F * sum;
+        }
+
+        /* crossover, Sec. II-A */
+        double *u = U + (size_t)i * dim;
+        uint8_t *mk = M + (size_t)i * dim;
+        int L = 0;
+        if (cs == 1) { /* binomial */
+            for (int j = 0; j < dim; j++) {
+                uint32_t w = or_word(seed, OR_TAG_INNER, stream, gen, (uint32_t)i, epoch, 4, (uint32_t)j);
+                int take = ((w >> 8) < cri) || (j == jrand);
+                mk[j] = (uint8_t)take;
+                u[j] = take ? v[j] : xi[j];
+            }
+        } else if (cs == 2) { /* exponential: a cyclic run of L coordinates from n */
+            L = 1;
+            while (L < dim) {
+                uint32_t w = or_word(seed, OR_TAG_INNER, stream, gen, (uint32_t)i, epoch, 4, (uint32_t)(L - 1));
+                if ((w >> 8) < cri) L++;
+                else break;
+            }
+            for (int j = 0; j < dim; j++) mk[j] = 0;
+            for (int l = 0; l < L; l++) mk[(nstart + l) % dim] = 1;
+            for (int j = 0; j < dim; j++) u[j] = mk[j] ? v[j] : xi[j];
+        } else { /* arithmetic recombination */
+            for (int j = 0; j < dim; j++) {
+                mk[j] = 1;
+                u[j] = xi[j] + K * (v[j] - xi[j]);
+            }
+        }
+        for (int j = 0; j < dim; j++) {
+            if (u[j] < lo) u[j] = lo;
+            if (u[j] > hi) u[j] = hi;
+        }
+        fU[i] = or_fitness(obj, dim, u, o, R);
+
+        if (rec) {
+            int32_t *q = rec + (size_t)i * OR_REC;
+            q[0] = ib[bl];
+            q[1] = ib[br];
+            q[2] = jrand;
+            q[3] = nstart;
+            q[4] = L;
+            q[5] = (int32_t)kraw;
+            q[6] = pbest;
+            q[7] = best;
+            q[8] = m;
+            for (int t = 0; t < 9; t++) q[9 + t] = r[t];
+        }
+    }
+
+    /* Alg. 2 line 10: greedy selection, all trials against the start population */
+    for (int i = 0; i < np; i++) {
+        int acc = fU[i] <= fit[i];
+        if (accept) accept[i] = acc;
+        if (trial) memcpy(trial + (size_t)i * dim, U + (size_t)i * dim, sizeof(double) * (size_t)dim);
+        if (ftrial) ftrial[i] = fU[i];
+        if (mask) memcpy(mask + (size_t)i * dim, M + (size_t)i * dim, (size_t)dim);
+        if (acc) {
+            memcpy(pop + (size_t)i * dim, U + (size_t)i * dim, sizeof(double) * (size_t)dim);
+            fit[i] = fU[i];
+        }
+    }
+    free(order); free(U); free(fU); free(M); free(v);
+    return 0;
+}
+
+/* Best fitness and its index (lowest index on ties): the executor's y*. */
+double or_best(int np, const double *fit, int32_t *best_index)
+{
+    int b = 0;
+    for (int i = 1; i < np; i++)
+        if (fit[i] < fit[b]) b = i;
+    if (best_index) *best_index = b;
+    return fit[b];
+}
+
+/* A whole PDE run (Alg. 2): initialise, evaluate, `gens` generations; returns y*. */
+double or_pde_run(int np, int dim, int obj, const double *o, const double *R,
+                  double lo, double hi, uint64_t seed, uint32_t stream, uint32_t epoch,
+                  int p_best_pct, const double *theta, int gens, double *pop, double *fit)
+{
+    or_init_pop(np, dim, seed, stream, epoch, lo, hi, pop);
+    or_eval_pop(np, dim, obj, o, R, pop, fit);
+    for (int g = 0; g < gens; g++)
+        if (or_pde_step(np, dim, obj, o, R, lo, hi, seed, stream, epoch, (uint32_t)g,
+                        p_best_pct, theta, pop, fit, NULL, NULL, NULL, NULL, NULL) != 0)
+            return NAN;
+    return or_best(np, fit, NULL);
+}
+
+/* ------------------------------------------------------------- evolver */
+
+static const double OR_LB[6] = {0.0, 0.0, 1.0, 1.0, 1.0, 1.0};
+static const double OR_UB[6] = {1.0, 1.0, 5.0, 5.0, 5.0, 4.0};
+
+/* Alg. 3 lines 1-2: evolver population uniform in [lb, ub], fitness +inf. */
+void or_outer_init(int n_out, uint64_t seed, uint32_t group, double *pop, double *fit)
+{
+    for (int i = 0; i < n_out; i++) {
+        for (int j = 0; j < 6; j++) {
+            uint32_t w = or_word(seed, OR_TAG_OUTER, group, OR_INIT_GEN, (uint32_t)i, 0, 0, (uint32_t)j);
+            pop[i * 6 + j] = OR_LB[j] + (OR_UB[j] - OR_LB[j]) * or_uniform(w);
+        }
+        fit[i] = INFINITY;
+    }
+}
+
+/* Alg. 3 line 5: rand/1/bin trials with F = 0.5, CR = 0.9 (Sec. IV-A),
+ * clipped to [lb, ub].  Returns -1 when n_out < 4. */
+int or_outer_trial(int n_out, uint64_t seed, uint32_t group, uint32_t gen,
+                   const double *pop, double *trial)
+{
+    if (n_out < 4) return -1;
+    const double F = 0.5;
+    uint32_t cri = or_threshold(0.9);
+    for (int i = 0; i < n_out; i++) {
+        uint32_t w0[4], w1[4];
+        or_slot(seed, OR_TAG_OUTER, group, gen, (uint32_t)i, 0, 0, w0);
+        or_slot(seed, OR_TAG_OUTER, group, gen, (uint32_t)i, 0, 1, w1);
+        int jrand = (int)or_below(w0[0], 6u);
+        int32_t r[3];
+        or_distinct_draws(n_out, i, 3, w1, r);
+        for (int j = 0; j < 6; j++) {
+            double v = pop[r[0] * 6 + j] + F * (pop[r[1] * 6 + j] - pop[r[2] * 6 + j]);
+            uint32_t w = or_word(seed, OR_TAG_OUTER, group, gen, (uint32_t)i, 0, 2, (uint32_t)j);
+            int take = ((w >> 8) < cri) || (j == jrand);
+            double u = take ? v : pop[i * 6 + j];
+            if (u < OR_LB[j]) u = OR_LB[j];
+            if (u > OR_UB[j]) u = OR_UB[j];
+            trial[i * 6 + j] = u;
+        }
+    }
+    return 0;
+}
+
+/* Alg. 3 line 6: F = u1, CR = u2, bl/br/dn/cs = floor of u3..u6, clamped to
+ * their domains so that the upper bound decodes to the top category. */
+void or_decode(const double *u, double *theta)
+{
+    static const int top[6] = {0, 0, 4, 4, 4, 3};
+    theta[0] = u[0];
+    theta[1] = u[1];
+    for (int j = 2; j < 6; j++) {
+        double c = floor(u[j]);
+        if (c < 1.0) c = 1.0;
+        if (c > top[j]) c = top[j];
+        theta[j] = c;
+    }
+}
+
+/* Alg. 3 line 12: a trial replaces its parent when its meta-fitness is <=. */
+void or_outer_select(int n_out, double *pop, double *fit, const double *trial,
+                     const double *meta_fit, int32_t *accept)
+{
+    for (int i = 0; i < n_out; i++) {
+        double y = isnan(meta_fit[i]) ? INFINITY : meta_fit[i];
+        int acc = y <= fit[i];
+        if (accept) accept[i] = acc;
+        if (acc) {
+            for (int j = 0; j < 6; j++) pop[i * 6 + j] = trial[i * 6 + j];
+            fit[i] = y;
+        }
+    }
+}
+
+/*
+ * A whole MetaDE run (Alg. 3) for one problem, one-shot evaluation: every
+ * executor starts from the same seed (stream = group, epoch 0).  `power_up`
+ * gives the last evolver generation 5x the inner generations (Sec. III-D).
+ * Writes the final evolver population/fitness; returns the best meta-fitness.
+ */
+double or_metade_run(int n_out, int np, int dim, int obj, const double *o, const double *R,
+                     double lo, double hi, uint64_t seed, uint32_t group, int p_best_pct,
+                     int inner_gens, int outer_gens, int power_up,
+                     double *opop, double *ofit)
+{
+    double *trial = (double *)malloc(sizeof(double) * (size_t)n_out * 6);
+    double *yf = (double *)malloc(sizeof(double) * (size_t)n_out);
+    double *pop = (double *)malloc(sizeof(double) * (size_t)np * dim);
+    double *fit = (double *)malloc(sizeof(double) * (size_t)np);
+    or_outer_init(n_out, seed, group, opop, ofit);
+    for (int g = 0; g < outer_gens; g++) {
+        or_outer_trial(n_out, seed, group, (uint32_t)g, opop, trial);
+        int gens = (power_up && g == outer_gens - 1) ? 5 * inner_gens : inner_gens;
+        for (int k = 0; k < n_out; k++) {
+            double th[6];
+            or_decode(trial + k * 6, th);
+            yf[k] = or_pde_run(np, dim, obj, o, R, lo, hi, seed, group, 0, p_best_pct, th, gens, pop, fit);
+        }
+        or_outer_select(n_out, opop, ofit, trial, yf, NULL);
+    }
+    double b = ofit[0];
+    for (int k = 1; k < n_out; k++)
+        if (ofit[k] < b) b = ofit[k];
+    free(trial); free(yf); free(pop); free(fit);
+    return b;
+}
