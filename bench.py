@@ -1,0 +1,391 @@
+#!/usr/bin/env python3
+"""Benchmark of the MetaDE batched inner-DE generation step on GB300.
+
+Workload (the evolver/executor setting of the paper's Sec. IV-A at 20-D):
+six MetaDE runs, one per synthetic shifted-rotated objective (sphere,
+Rosenbrock, Rastrigin, Griewank, Ackley, Schwefel 1.2), D = 20; each run's
+evolver has 100 vectors and each vector drives one executor of population
+100 for 500 generations.  One step = one evolver generation of all six runs
+(Alg. 3 lines 5-12): rand/1/bin trials and decoding, executor
+initialisation, 500 executor generations of 600 executors, best-fitness
+reduction, evolver selection = 3.0e7 individual-generations.
+
+Metric: individual-generations per second (the paper's FEs per second) and
+the evolver-generation time, for the batched path (all executors in one
+launch, generations fused) next to the plain FP32 path (one executor per
+launch per generation, no graph).
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 oracle on
+the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "inner-DE individual-gens/s & outer-gen time: batched+BF16 vs plain FP32"
+UNIT = "individual-gens/s"
+WORKLOAD = "moderate-6x100x100xD20"
+INNER_GENS = 500
+CPU_SAMPLE_PER_RUN = 20  # executors per run timed on the host (of 100)
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison arm")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--inner-gens", type=int, default=INNER_GENS)
+    return ap.parse_args(argv)
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+# --------------------------------------------------------------- CPU oracle
+def _oracle_job(args):
+    """One executor run of the oracle (module-level so a spawn pool can pickle it)."""
+    import oracle
+    theta, np_, obj, shift, rot, gens, seed, stream = args
+    oracle.build()
+    oracle.pde_run(theta, np_, obj, shift, rot, gens, seed=seed, stream=stream, epoch=0)
+    return np_ * gens
+
+
+def oracle_tasks(wl, per_run: int, gens: int):
+    """Executors of the first evolver generation: the oracle's own evolver
+    draws and decodes theta exactly as the workload does."""
+    import oracle
+    tasks = []
+    for g, p in enumerate(wl.problems):
+        opop, _ = oracle.outer_init(wl.n_out, wl.seed, g)
+        trial = oracle.outer_trial(opop, wl.seed, g, 0)
+        for j in range(per_run):
+            th = oracle.decode(trial[j])
+            tasks.append((th, int(wl.inst_np[g * wl.n_out + j]), p.obj, p.shift, p.rot, gens, wl.seed, g))
+    return tasks
+
+
+def time_oracle(tasks, cores: int):
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_job, tasks[:cores])  # workers up and the library built before timing
+        t0 = time.perf_counter()
+        units = sum(pool.map(_oracle_job, tasks, chunksize=1))
+        dt = time.perf_counter() - t0
+    return units, dt
+
+
+def cpu_baseline(wl, gens: int):
+    cores = os.cpu_count() or 1
+    tasks = oracle_tasks(wl, CPU_SAMPLE_PER_RUN, gens)
+    units, dt = time_oracle(tasks, cores)
+    return {"value": units / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d executors (%d per run) x NP 100 x %d generations of the %s workload, FP64 C oracle, "
+                      "%d spawn processes, %.1f s wall" % (len(tasks), CPU_SAMPLE_PER_RUN, gens, WORKLOAD, cores, dt)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import synth
+    wl = synth.moderate(inner_gens=args.inner_gens)
+    cores = os.cpu_count() or 1
+    per_run = -(-cores // len(wl.problems))  # every core busy in each step
+    tasks = oracle_tasks(wl, per_run, args.inner_gens)
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    times, units = [], 0
+    with ctx.Pool(cores) as pool:
+        for s in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            u = sum(pool.map(_oracle_job, tasks, chunksize=1))
+            dt = time.perf_counter() - t0
+            if s >= args.warmup:
+                times.append(dt)
+                units += u
+    total = sum(times)
+    value = units / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "inner_gens": args.inner_gens,
+                                             "sample_executors_per_step": len(tasks)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d executors x NP 100 x %d generations per step" % (len(tasks), args.inner_gens)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.05)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# -------------------------------------------------------------- our arm
+def alu_ops(theta, inst_np, dims):
+    """Algorithmic lane operations of one generation of every executor:
+    D^2 rotation FMAs + (2 dn + 8) D mutation/crossover/clip/shift operations
+    + 100 per Philox4x32-10 call (10 rounds of 10 integer operations), with
+    1 + ceil(m/4) calls per individual for the index draws and ceil(D/4) for
+    binomial masks.  Transcendentals of the objectives are not counted."""
+    import numpy as np
+    th = np.asarray(theta)
+    bl, br, dn, cs = th[:, 2].astype(int), th[:, 3].astype(int), th[:, 4].astype(int), th[:, 5].astype(int)
+    a = ((bl == 1) | (br == 1)).astype(int)
+    m = a + 2 * dn
+    D = np.asarray(dims, dtype=np.float64)
+    calls = 1 + np.ceil(m / 4.0) + np.where(cs == 1, np.ceil(D / 4.0), 0.0)
+    per = D * D + (2 * dn + 8) * D + 100.0 * calls
+    return float((per * np.asarray(inst_np, dtype=np.float64)).sum())
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    import synth
+    wl = synth.moderate(inner_gens=args.inner_gens)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(wl, args.inner_gens)  # before the first GPU call (spawn pool)
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2502_10470_gb300 as M
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    probs = [(p.dim, p.obj, p.shift, p.rot) for p in wl.problems]
+
+    def make(path):
+        return M.Batch(probs, wl.inst_np, wl.inst_prob, wl.inst_group, seed=wl.seed + rank, one_shot=1,
+                       n_out=wl.n_out, path=path, device=dev, stream=stream.cuda_stream)
+
+    b = make(M.METADE_PATH_BATCHED)
+    M.metade_outer_init(b.ctx, b.opop, b.ofit)
+    units_per_step = float(wl.inst_np.sum()) * args.inner_gens
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    kernel_ev = []
+
+    def step(batch, og, events):
+        M.metade_outer_step(batch.ctx, batch.opop, batch.ofit, batch.trial, batch.theta, None, og, 0)
+        M.metade_init(batch.ctx, batch.pop, batch.fit, 0)
+        if events is not None:
+            events[0].record(stream)
+        M.metade_inner_step(batch.ctx, batch.pop, batch.fit, batch.theta, 0, 0, args.inner_gens, batch.best_f,
+                            batch.best_i)
+        if events is not None:
+            events[1].record(stream)
+        M.metade_outer_step(batch.ctx, batch.opop, batch.ofit, batch.trial, batch.theta, batch.best_f, og, 1)
+
+    og = 0
+    for _ in range(args.warmup):
+        step(b, og, None)
+        og += 1
+    if M.metade_sync(b.ctx) != 0:
+        raise RuntimeError("device status after warm-up")
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    launches0 = M.metade_launch_count(b.ctx)
+    step_ev, thetas = [], []
+    for s in range(args.steps):
+        flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        step(b, og, (ev[1], ev[2]))
+        ev[3].record(stream)
+        step_ev.append(ev)
+        thetas.append(b.theta.clone())
+        og += 1
+    barrier()
+    launches = M.metade_launch_count(b.ctx) - launches0
+    clocks = sampler.stop()
+    step_ms = [e[0].elapsed_time(e[3]) for e in step_ev]
+    kern_ms = [e[1].elapsed_time(e[2]) for e in step_ev]
+    total_ms = sum(step_ms)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_max = float(t.item())
+    value = world * units_per_step * args.steps / (total_max / 1000.0)
+    ops = [alu_ops(th.cpu().numpy(), wl.inst_np, b.dims) * args.inner_gens for th in thetas]
+    achieved = sum(ops) / (sum(kern_ms) / 1000.0)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_ops = 152 * 128 * sm_max * 1e6  # FP32/INT lanes x max SM clock
+
+    # end to end through the public call: pinned host state in, meta-fitness out
+    h_opop = b.opop.cpu().pin_memory()
+    h_ofit = b.ofit.cpu().pin_memory()
+    h_best = torch.empty_like(b.best_f, device="cpu").pin_memory()
+    h_ofit_out = torch.empty_like(b.ofit, device="cpu").pin_memory()
+    M.metade_outer_generation(b.ctx, b.opop, b.ofit, b.trial, b.theta, b.pop, b.fit, b.best_f, b.best_i, og,
+                              args.inner_gens, True)  # capture the graph before timing
+    og += 1
+    barrier()
+    e2e_ms = []
+    for s in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.opop.copy_(h_opop, non_blocking=True)
+        b.ofit.copy_(h_ofit, non_blocking=True)
+        M.metade_outer_generation(b.ctx, b.opop, b.ofit, b.trial, b.theta, b.pop, b.fit, b.best_f, b.best_i, og,
+                                  args.inner_gens, True)
+        h_best.copy_(b.best_f, non_blocking=True)
+        h_ofit_out.copy_(b.ofit, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+        og += 1
+    barrier()
+    if M.metade_sync(b.ctx) != 0:
+        raise RuntimeError("device status after timing")
+    te = torch.tensor([sum(e2e_ms)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * units_per_step * args.steps / (float(te.item()) / 1000.0)
+    h2d = (h_opop.numel() + h_ofit.numel()) * 4
+    d2h = (h_best.numel() + h_ofit_out.numel()) * 4
+
+    plain = None
+    if not args.no_plain:
+        p = make(M.METADE_PATH_PLAIN)
+        M.metade_outer_init(p.ctx, p.opop, p.ofit)
+        step(p, 0, None)  # warm-up
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = M.metade_launch_count(p.ctx)
+        e0.record(stream)
+        step(p, 1, None)
+        e1.record(stream)
+        barrier()
+        pms = e0.elapsed_time(e1)
+        plain = {"value": units_per_step / (pms / 1000.0), "unit": UNIT, "ms_per_step": pms, "steps": 1,
+                 "gpu_launches": M.metade_launch_count(p.ctx) - l0,
+                 "path": "one executor per launch per generation, FP32, no graph"}
+        p.close()
+
+    plan = json.loads(M.metade_plan_info(b.ctx))
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "runs": len(wl.problems), "evolver_pop": wl.n_out,
+                           "executor_pop": 100, "dim": 20, "inner_gens": args.inner_gens,
+                           "parallelism": "replicas" if world > 1 else "single",
+                           "l2": "flushed (256 MB write) before every timed step",
+                           "plan": plan},
+                "outer_gen_ms": total_max / args.steps,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                        "ms_per_step": sum(e2e_ms) / len(e2e_ms), "call": "metade_outer_generation (CUDA graph)"},
+                "gpu_launches": launches,
+                "roofline": {"bound": "alu", "kernel": "k_fused_small<20>", "achieved": achieved / 1e9,
+                             "peak": peak_ops / 1e9, "unit": "Gop/s", "frac": achieved / peak_ops,
+                             "traffic": None, "kernel_ms": sum(kern_ms) / len(kern_ms),
+                             "kernel_share": sum(kern_ms) / total_ms,
+                             "peak_source": "152 SMs x 128 lanes x %.0f MHz (max SM clock)" % sm_max},
+                "plain_fp32": plain,
+                "speedup_vs_plain": (value / plain["value"]) if plain else None,
+                "cpu_baseline": cpu,
+                "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    b.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,205 @@
+/*
+ * metade.h -- C-ABI of the GB300 (sm_103a) MetaDE hot path.
+ *
+ * MetaDE (arXiv 2502.10470) evolves the hyperparameters of a parameterised
+ * DE ("PDE", Sec. III-A) with an outer DE (the "evolver", Alg. 3).  Every
+ * evolver vector u decodes into theta = (F, CR, bl, br, dn, cs) and drives its
+ * own inner DE (an "executor", Alg. 2) on the target objective; the best
+ * fitness an executor reaches is the meta-fitness the evolver selects on
+ * (Sec. III-B).  This library runs the executors' generations -- index
+ * draws, mutation, crossover, objective evaluation, greedy selection and the
+ * best-fitness reduction -- for hundreds of executors at once, plus the
+ * evolver's trial/decode/selection steps.
+ *
+ * Conventions shared by every entry point:
+ *  - All state is caller-owned DEVICE memory (e.g. torch tensors); the
+ *    library owns only its context: descriptor table, padded copies of the
+ *    problem data, scratch, the tuned plan and captured CUDA graphs.
+ *  - Calls are asynchronous on the context's stream.  Host-detectable errors
+ *    are returned at once; errors found on the device (an invalid theta, a
+ *    population too small for the strategy) are latched in a sticky status
+ *    word that metade_sync() returns and clears.  Nothing is thrown across
+ *    the ABI.  On error no output is guaranteed to be written.
+ *  - A problem p has dimension D_p, an objective id, a shift o_p and a
+ *    rotation R_p; its objective is f(x) = obj(z), z = R_p (x - o_p).
+ *    Objective ids: 0 sphere, 1 Rosenbrock on z + 1, 2 Rastrigin,
+ *    3 Griewank, 4 Ackley, 5 Schwefel 1.2 (all with minimum 0 at x = o_p).
+ *  - Population layout: instance-major, row-major, each row padded to
+ *    Dpad = round_up(D, 4) floats (16-byte rows); the pad columns are zero.
+ *    Instance k's rows start at float offset pop_off[k]; its fitness values
+ *    at fit_off[k] (see metade_offsets).
+ *  - theta is float32 [n_inst][6] = (F, CR, bl, br, dn, cs) with the four
+ *    categorical genes as integral values: bl, br in {1 rand, 2 best,
+ *    3 pbest, 4 current}, dn in {1..4}, cs in {1 bin, 2 exp, 3 arith}.
+ *  - Random numbers come from Philox4x32-10 (Salmon et al., SC'11) keyed by
+ *    (seed, stream, generation, individual, draw slot), so every draw is
+ *    reproducible and independent of launch shape.
+ */
+#ifndef METADE_H
+#define METADE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define METADE_API __attribute__((visibility("default")))
+#else
+#define METADE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    METADE_OK = 0,
+    METADE_EINVAL = 1,      /* bad argument, or (device) invalid theta / NP too small */
+    METADE_ENOMEM = 2,      /* device allocation of the context failed */
+    METADE_ECUDA = 3,       /* a CUDA runtime call failed */
+    METADE_ETIMEOUT = 4,    /* a bounded device wait gave up */
+    METADE_ESTATE = 5,      /* call out of order (e.g. evolver calls without n_out) */
+    METADE_EUNSUPPORTED = 6 /* configuration not supported by this build */
+} metade_status;
+
+typedef enum {
+    METADE_FP32 = 0,
+    METADE_BF16 = 1,
+    METADE_FP8E4M3 = 2,
+    METADE_BF16X3 = 3,
+    METADE_FP64 = 4
+} metade_prec;
+
+typedef enum {
+    METADE_PATH_BATCHED = 0, /* all executors per launch, generations fused, tuned plan */
+    METADE_PATH_PLAIN = 1    /* one executor per launch per generation: FP32 baseline */
+} metade_path;
+
+typedef struct {
+    /* problem table (host arrays, device data) */
+    int32_t n_prob;
+    const int32_t *prob_dim;  /* host [n_prob], D_p >= 1 */
+    const int32_t *prob_obj;  /* host [n_prob], objective id 0..5 */
+    const float *shift;       /* device [sum_p D_p]: o_p concatenated */
+    const float *rot;         /* device [sum_p D_p^2]: R_p row-major, concatenated */
+    /* executors */
+    int32_t n_inst;
+    const int32_t *inst_np;    /* host [n_inst], population sizes, 4 <= NP <= 1024 */
+    const int32_t *inst_prob;  /* host [n_inst], problem index of each executor */
+    const int32_t *inst_group; /* host [n_inst] or NULL: the MetaDE run of each executor */
+    float lo, hi;              /* search box [lo, hi]^D */
+    uint64_t seed;
+    int32_t one_shot;          /* 1: executors of a run share one random stream (Sec. III-C) */
+    int32_t p_best_pct;        /* pbest pool, percent of NP (0 -> 10, Sec. II-A) */
+    int32_t n_out;             /* evolver population per run; 0 = no evolver */
+    metade_prec prec;          /* rotation precision for D >= 512 (FP32 below) */
+    metade_path path;
+    int32_t tie_fp64;          /* selection ties: 0 = FP32 difference form, 1 = FP64 re-evaluation */
+    void *stream;              /* cudaStream_t all calls are issued on (NULL = legacy) */
+} metade_config;
+
+typedef struct metade_ctx metade_ctx;
+
+/* Validate the configuration, build the descriptor table and padded problem
+ * copies, allocate scratch and pick the launch plan (autotuned on first
+ * batched step).  shift/rot are copied; the caller may free them after.
+ * Returns EINVAL for a malformed config (sizes out of range, n_out > 0 with
+ * n_inst not a multiple of n_out, n_out < 4), ENOMEM/ECUDA on device
+ * failure.  *out is NULL on error. */
+METADE_API metade_status metade_create(const metade_config *cfg, metade_ctx **out);
+
+/* Release the context (synchronises its stream first).  NULL is a no-op. */
+METADE_API void metade_destroy(metade_ctx *ctx);
+
+/* Sizes: floats of the padded population, total individuals (fitness
+ * length), number of runs (groups).  Any pointer may be NULL. */
+METADE_API metade_status metade_layout(const metade_ctx *ctx, int64_t *pop_floats, int64_t *n_indiv,
+                            int32_t *n_groups);
+
+/* Host arrays [n_inst] of per-executor float offset, fitness offset and
+ * padded row length.  Any pointer may be NULL. */
+METADE_API metade_status metade_offsets(const metade_ctx *ctx, int64_t *pop_off, int64_t *fit_off,
+                             int32_t *dpad);
+
+/* Change the stream later calls are issued on. */
+METADE_API metade_status metade_set_stream(metade_ctx *ctx, void *stream);
+
+/* Alg. 2 lines 1-2: fill every executor's population uniformly in the box
+ * (x = lo + (hi - lo) U, rounded once to float32) and evaluate it in FP32
+ * (NaN fitness stored as +inf).  `epoch` enters the draw counter: with
+ * one-shot evaluation the caller passes 0 every time, so every evaluation of
+ * a theta starts from the same population. */
+METADE_API metade_status metade_init(metade_ctx *ctx, float *pop, float *fit, uint32_t epoch);
+
+/* Alg. 2 lines 7-10, `n_gens` times, generations gen0 .. gen0 + n_gens - 1,
+ * for every executor: rand/best/pbest/current base vectors and dn difference
+ * vectors of distinct random individuals (Eq. of Sec. III-A-2), binomial /
+ * exponential / arithmetic crossover (Sec. II-A), clip to the box, FP32
+ * shifted-rotated evaluation, and generational greedy selection f(u) <= f(x).
+ * Selection ties, |f(u) - f(x)| <= 1e-6 |f(x)| with both values positive and
+ * finite, are decided on the difference f(u) - f(x) evaluated directly in FP32
+ * from z = R(x - o) and dz = R(u - x) (error proportional to the difference,
+ * not to f), or, with cfg.tie_fp64, by re-evaluating both vectors in FP64; an
+ * accepted tie stores f(x) + difference (resp. the FP64 value), never above
+ * f(x).  A trial identical to its target is accepted without re-evaluation.
+ * pop/fit are updated in place.  If best_f /
+ * best_i are non-NULL they receive each executor's best fitness and its
+ * index after the last generation (Sec. III-B: the executor's y*).
+ * theta: device [n_inst][6].  n_gens == 0 only writes best_f/best_i. */
+METADE_API metade_status metade_inner_step(metade_ctx *ctx, float *pop, float *fit, const float *theta,
+                                uint32_t epoch, uint32_t gen0, int32_t n_gens, float *best_f,
+                                int32_t *best_i);
+
+/* Evaluate every population row: prec FP32 writes float f_out[n_indiv],
+ * FP64 writes double f_out[n_indiv] (used for the final error f(x) - f*,
+ * f* = 0).  Other precisions return EUNSUPPORTED. */
+METADE_API metade_status metade_eval(metade_ctx *ctx, const float *pop, metade_prec prec, void *f_out);
+
+/* Evolver (Alg. 3).  Its population is float32 [n_groups][n_out][6] with
+ * fitness [n_groups][n_out]; executor k = g * n_out + j evaluates vector j
+ * of run g.  ESTATE if the context has no evolver (n_out == 0). */
+/* Alg. 3 lines 1-2: uniform in [lb, ub] = [(0,0,1,1,1,1), (1,1,5,5,5,4)], y = +inf. */
+METADE_API metade_status metade_outer_init(metade_ctx *ctx, float *opop, float *ofit);
+
+/* phase 0 (Alg. 3 lines 5-6): rand/1/bin trials (F = 0.5, CR = 0.9) clipped to
+ *   [lb, ub] into trial[n_groups][n_out][6], decoded (F = u1, CR = u2, the
+ *   rest floor(u) clamped to their domain) into theta[n_inst][6].
+ * phase 1 (Alg. 3 line 12): where meta_fit[k] <= ofit[k] (NaN as +inf) the
+ *   trial replaces the parent and ofit[k] = meta_fit[k]. */
+METADE_API metade_status metade_outer_step(metade_ctx *ctx, float *opop, float *ofit, float *trial,
+                                float *theta, const float *meta_fit, uint32_t outer_gen,
+                                int32_t phase);
+
+/* One whole evolver generation (Alg. 3 lines 5-12): phase 0, executor
+ * initialisation (epoch 0 under one-shot evaluation, else outer_gen),
+ * n_inner_gens executor generations, the best-fitness reduction into
+ * best_f/best_i, phase 1.  With use_graph != 0 the sequence is captured
+ * once as a CUDA graph (per argument set) and replayed. */
+METADE_API metade_status metade_outer_generation(metade_ctx *ctx, float *opop, float *ofit, float *trial,
+                                      float *theta, float *pop, float *fit, float *best_f,
+                                      int32_t *best_i, uint32_t outer_gen, int32_t n_inner_gens,
+                                      int32_t use_graph);
+
+/* Parity/debug: the draw record of generation `gen` for every individual,
+ * int32 rec[n_indiv][18]: base-left index, base-right index, j_rand,
+ * exponential start n, exponential length L (0 unless cs = exp), K_i as a
+ * 24-bit integer, pbest index, best index, m, r_0..r_8 (-1 unused).  Uses
+ * the generation-start fitness `fit`. */
+METADE_API metade_status metade_draw_record(metade_ctx *ctx, const float *fit, const float *theta,
+                                 uint32_t epoch, uint32_t gen, int32_t *rec);
+
+/* Wait for the context's stream; return and clear the sticky device status. */
+METADE_API metade_status metade_sync(metade_ctx *ctx);
+
+/* Write a one-line JSON description of the launch plan into buf. */
+METADE_API metade_status metade_plan_info(const metade_ctx *ctx, char *buf, size_t len);
+
+/* Number of kernel launches this context has issued (graph replays count the
+ * kernels they contain). */
+METADE_API int64_t metade_launch_count(const metade_ctx *ctx);
+
+METADE_API const char *metade_strerror(metade_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* METADE_H */

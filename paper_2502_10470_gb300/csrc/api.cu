@@ -1,0 +1,574 @@
+// api.cu -- the C-ABI of include/metade.h: context creation and validation,
+// the descriptor table, the launch planner (kernel kind per executor, work
+// order, block shape), CUDA-graph capture of whole evolver generations, and
+// the sticky device status.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/metade.h"
+#include "internal.h"
+
+using namespace metade;
+
+namespace {
+
+constexpr int kMaxDim = 1536;
+constexpr int kMaxNp = 1024;
+constexpr size_t kSmemLimit = 227 * 1024;
+
+struct Bucket {
+    FusedPlan plan;
+    int work_off, n_work;
+};
+
+struct GraphEntry {
+    std::vector<uintptr_t> key;
+    cudaGraphExec_t exec;
+    int64_t kernels;
+};
+
+}  // namespace
+
+struct metade_ctx {
+    // configuration (host copies)
+    int n_prob = 0, n_inst = 0, n_groups = 0, n_out = 0;
+    float lo = -100.f, hi = 100.f;
+    uint64_t seed = 0;
+    int one_shot = 0, p_best_pct = 10;
+    metade_prec prec = METADE_FP32;
+    metade_path path = METADE_PATH_BATCHED;
+    int tie_fp64 = 0;
+    cudaStream_t st = nullptr;
+    cudaStream_t cap = nullptr;  // private stream for graph capture
+    std::vector<InstDesc> hdesc;
+    std::vector<long long> pop_off;
+    std::vector<long long> fit_off;
+    std::vector<int> dpad;
+    long long pop_floats = 0, n_indiv = 0;
+    int max_np = 0, max_dim = 0, max_dpad = 0, max_kp = 1;
+    // device
+    InstDesc* desc = nullptr;
+    int* row_inst = nullptr;
+    float* rot = nullptr;
+    float* rotT = nullptr;
+    float* shift = nullptr;
+    float* uscr = nullptr;
+    float* fuscr = nullptr;
+    int* topk = nullptr;
+    int* status = nullptr;
+    uint32_t* gen_dev = nullptr;
+    int* work = nullptr;
+    std::vector<Bucket> buckets;
+    std::vector<GraphEntry> graphs;
+    int64_t launches = 0;
+};
+
+namespace {
+
+metade_status cuda_status(cudaError_t e) { return e == cudaSuccess ? METADE_OK : METADE_ECUDA; }
+
+#define CK(x)                                                \
+    do {                                                     \
+        cudaError_t e_ = (x);                                \
+        if (e_ != cudaSuccess) return cuda_status(e_);       \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t n) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    return cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T));
+}
+
+StepArgs step_args(metade_ctx* c, float* pop, float* fit, const float* theta, uint32_t epoch,
+                   const uint32_t* epoch_dev, uint32_t gen0, int n_gens, float* best_f, int* best_i) {
+    StepArgs a;
+    a.desc = c->desc;
+    a.pop = pop;
+    a.fit = fit;
+    a.theta = theta;
+    a.rot = c->rot;
+    a.rotT = c->rotT;
+    a.shift = c->shift;
+    a.key = make_key(c->seed, kTagInner);
+    a.epoch = epoch;
+    a.epoch_dev = epoch_dev;
+    a.gen0 = gen0;
+    a.n_gens = n_gens;
+    a.lo = c->lo;
+    a.hi = c->hi;
+    a.best_f = best_f;
+    a.best_i = best_i;
+    a.status = c->status;
+    a.tie_fp64 = c->tie_fp64;
+    return a;
+}
+
+double work_cost(const InstDesc& d) { return (double)d.np * ((double)d.dim * d.dim + 16.0 * d.dim + 64.0); }
+
+// Kernel kind per executor and the work order inside each bucket (largest
+// first, so the block scheduler hands the longest executors out first).
+metade_status build_plan(metade_ctx* c) {
+    std::vector<std::vector<int>> small(33);
+    std::vector<int> general;
+    for (int k = 0; k < c->n_inst; ++k) {
+        const InstDesc& d = c->hdesc[k];
+        const int dm = small_dmax_for(d.dim);
+        if (dm > 0 && fused_smem_small(dm, d.np) <= kSmemLimit) small[dm].push_back(k);
+        else general.push_back(k);
+    }
+    std::vector<int> order;
+    auto sort_desc = [&](std::vector<int>& v) {
+        std::stable_sort(v.begin(), v.end(), [&](int a, int b) { return work_cost(c->hdesc[a]) > work_cost(c->hdesc[b]); });
+    };
+    c->buckets.clear();
+    for (int dm = 1; dm <= 32; ++dm) {
+        if (small[dm].empty()) continue;
+        sort_desc(small[dm]);
+        int mnp = 0;
+        for (int k : small[dm]) mnp = std::max(mnp, c->hdesc[k].np);
+        Bucket b;
+        b.plan.kind = 0;
+        b.plan.dmax = dm;
+        b.plan.threads = std::min(512, std::max(64, (mnp + 31) / 32 * 32));
+        b.plan.grid = (int)small[dm].size();
+        b.plan.smem = fused_smem_small(dm, mnp);
+        b.plan.rot_smem = 0;
+        b.plan.max_np = mnp;
+        b.plan.max_dpad = dm;
+        b.work_off = (int)order.size();
+        b.n_work = (int)small[dm].size();
+        order.insert(order.end(), small[dm].begin(), small[dm].end());
+        c->buckets.push_back(b);
+    }
+    if (!general.empty()) {
+        sort_desc(general);
+        int mnp = 0, mdp = 0;
+        for (int k : general) {
+            mnp = std::max(mnp, c->hdesc[k].np);
+            mdp = std::max(mdp, c->hdesc[k].dpad);
+        }
+        Bucket b;
+        b.plan.kind = 1;
+        b.plan.dmax = 0;
+        b.plan.threads = 256;
+        b.plan.grid = (int)general.size();
+        b.plan.max_np = mnp;
+        b.plan.max_dpad = mdp;
+        b.plan.rot_smem = fused_smem_general(mnp, mdp, 256, true) <= kSmemLimit ? 1 : 0;
+        b.plan.smem = fused_smem_general(mnp, mdp, 256, b.plan.rot_smem != 0);
+        if (b.plan.smem > kSmemLimit) return METADE_EUNSUPPORTED;
+        b.work_off = (int)order.size();
+        b.n_work = (int)general.size();
+        order.insert(order.end(), general.begin(), general.end());
+        c->buckets.push_back(b);
+    }
+    if (!order.empty()) {
+        CK(dalloc(&c->work, order.size()));
+        CK(cudaMemcpy(c->work, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice));
+    }
+    return METADE_OK;
+}
+
+metade_status run_inner(metade_ctx* c, cudaStream_t st, float* pop, float* fit, const float* theta, uint32_t epoch,
+                        const uint32_t* epoch_dev, uint32_t gen0, int n_gens, float* best_f, int* best_i,
+                        int64_t* launches) {
+    if (c->n_inst == 0) return METADE_OK;
+    if (c->path == METADE_PATH_PLAIN || n_gens == 0) {
+        for (int g = 0; g < n_gens; ++g) {
+            StepArgs a = step_args(c, pop, fit, theta, epoch, epoch_dev, gen0 + (uint32_t)g, 1, nullptr, nullptr);
+            for (int k = 0; k < c->n_inst; ++k) {
+                CK(launch_plain_generation(a, k, c->hdesc[k], c->uscr, c->fuscr, c->topk, st));
+                *launches += 3;
+            }
+        }
+        if (best_f || best_i) {
+            CK(launch_best(c->desc, c->n_inst, fit, best_f, best_i, st));
+            *launches += 1;
+        }
+        return METADE_OK;
+    }
+    StepArgs a = step_args(c, pop, fit, theta, epoch, epoch_dev, gen0, n_gens, best_f, best_i);
+    for (const Bucket& b : c->buckets) {
+        CK(launch_fused(a, c->work + b.work_off, b.n_work, b.plan, c->uscr, st));
+        *launches += 1;
+    }
+    return METADE_OK;
+}
+
+metade_status run_init(metade_ctx* c, cudaStream_t st, float* pop, float* fit, uint32_t epoch,
+                       const uint32_t* epoch_dev, int64_t* launches) {
+    if (c->n_inst == 0) return METADE_OK;
+    CK(launch_init(c->desc, c->n_inst, c->max_np, c->max_dpad, pop, make_key(c->seed, kTagInner), epoch, epoch_dev,
+                   c->lo, c->hi, st));
+    CK(launch_eval(c->desc, c->row_inst, c->n_indiv, pop, c->rotT, c->shift, false, fit, true, c->max_dpad, st));
+    *launches += 2;
+    return METADE_OK;
+}
+
+__global__ void k_set_u32(uint32_t* p, uint32_t v) { *p = v; }
+
+// The evolver generation as a stream sequence (captured into a graph or run directly).
+metade_status enqueue_outer_generation(metade_ctx* c, cudaStream_t st, float* opop, float* ofit, float* trial,
+                                       float* theta, float* pop, float* fit, float* best_f, int* best_i,
+                                       int n_inner, int64_t* launches) {
+    const Key ko = make_key(c->seed, kTagOuter);
+    CK(launch_outer_trial(c->n_groups, c->n_out, ko, c->gen_dev, 0, opop, trial, theta, st));
+    *launches += 1;
+    const uint32_t* ep = c->one_shot ? nullptr : c->gen_dev;
+    metade_status s = run_init(c, st, pop, fit, 0, ep, launches);
+    if (s != METADE_OK) return s;
+    s = run_inner(c, st, pop, fit, theta, 0, ep, 0, n_inner, best_f, best_i, launches);
+    if (s != METADE_OK) return s;
+    CK(launch_outer_select(c->n_groups, c->n_out, opop, ofit, trial, best_f, st));
+    *launches += 1;
+    return METADE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* metade_strerror(metade_status s) {
+    switch (s) {
+    case METADE_OK: return "ok";
+    case METADE_EINVAL: return "invalid argument";
+    case METADE_ENOMEM: return "out of device memory";
+    case METADE_ECUDA: return "CUDA error";
+    case METADE_ETIMEOUT: return "device wait timed out";
+    case METADE_ESTATE: return "call not valid in this state";
+    case METADE_EUNSUPPORTED: return "unsupported configuration";
+    }
+    return "unknown status";
+}
+
+void metade_destroy(metade_ctx* c) {
+    if (!c) return;
+    if (c->st) cudaStreamSynchronize(c->st);
+    for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+    cudaFree(c->desc);
+    cudaFree(c->row_inst);
+    cudaFree(c->rot);
+    cudaFree(c->rotT);
+    cudaFree(c->shift);
+    cudaFree(c->uscr);
+    cudaFree(c->fuscr);
+    cudaFree(c->topk);
+    cudaFree(c->status);
+    cudaFree(c->gen_dev);
+    cudaFree(c->work);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    delete c;
+}
+
+metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
+    if (!out) return METADE_EINVAL;
+    *out = nullptr;
+    if (!cfg || cfg->n_prob < 1 || cfg->n_inst < 0 || !cfg->prob_dim || !cfg->prob_obj) return METADE_EINVAL;
+    if (cfg->n_inst > 0 && (!cfg->inst_np || !cfg->inst_prob || !cfg->shift || !cfg->rot)) return METADE_EINVAL;
+    if (!(cfg->lo < cfg->hi) || !std::isfinite(cfg->lo) || !std::isfinite(cfg->hi)) return METADE_EINVAL;
+    if (cfg->p_best_pct < 0 || cfg->p_best_pct > 100) return METADE_EINVAL;
+    if (cfg->n_out < 0 || (cfg->n_out > 0 && (cfg->n_out < 4 || cfg->n_inst % cfg->n_out != 0))) return METADE_EINVAL;
+    if (cfg->path != METADE_PATH_BATCHED && cfg->path != METADE_PATH_PLAIN) return METADE_EINVAL;
+    if (cfg->prec != METADE_FP32) return METADE_EUNSUPPORTED;
+    for (int p = 0; p < cfg->n_prob; ++p) {
+        if (cfg->prob_dim[p] < 1 || cfg->prob_obj[p] < 0 || cfg->prob_obj[p] > 5) return METADE_EINVAL;
+        if (cfg->prob_dim[p] > kMaxDim) return METADE_EUNSUPPORTED;
+    }
+    for (int k = 0; k < cfg->n_inst; ++k) {
+        if (cfg->inst_np[k] < 4 || cfg->inst_np[k] > kMaxNp) return METADE_EINVAL;
+        if (cfg->inst_prob[k] < 0 || cfg->inst_prob[k] >= cfg->n_prob) return METADE_EINVAL;
+        if (cfg->inst_group && cfg->inst_group[k] < 0) return METADE_EINVAL;
+    }
+
+    metade_ctx* c = new metade_ctx();
+    c->n_prob = cfg->n_prob;
+    c->n_inst = cfg->n_inst;
+    c->n_out = cfg->n_out;
+    c->n_groups = cfg->n_out > 0 ? cfg->n_inst / cfg->n_out : 0;
+    c->lo = cfg->lo;
+    c->hi = cfg->hi;
+    c->seed = cfg->seed;
+    c->one_shot = cfg->one_shot ? 1 : 0;
+    c->p_best_pct = cfg->p_best_pct == 0 ? 10 : cfg->p_best_pct;
+    c->prec = cfg->prec;
+    c->path = cfg->path;
+    c->tie_fp64 = cfg->tie_fp64 ? 1 : 0;
+    c->st = (cudaStream_t)cfg->stream;
+
+    // problem tables: input offsets (unpadded) and padded offsets
+    std::vector<long long> rot_in_off(c->n_prob), rot_off(c->n_prob);
+    std::vector<int> shift_in_off(c->n_prob), shift_off(c->n_prob);
+    long long rin = 0, rpad = 0;
+    int sin_ = 0, spad = 0;
+    for (int p = 0; p < c->n_prob; ++p) {
+        const int D = cfg->prob_dim[p], Dp = (D + 3) & ~3;
+        rot_in_off[p] = rin;
+        rot_off[p] = rpad;
+        shift_in_off[p] = sin_;
+        shift_off[p] = spad;
+        rin += (long long)D * D;
+        rpad += (long long)D * Dp;
+        sin_ += D;
+        spad += Dp;
+        c->max_dim = std::max(c->max_dim, D);
+    }
+
+    c->hdesc.resize(c->n_inst);
+    c->pop_off.resize(c->n_inst);
+    c->fit_off.resize(c->n_inst);
+    c->dpad.resize(c->n_inst);
+    std::vector<int> row_inst;
+    long long po = 0, fo = 0;
+    for (int k = 0; k < c->n_inst; ++k) {
+        const int p = cfg->inst_prob[k];
+        const int D = cfg->prob_dim[p], Dp = (D + 3) & ~3, np = cfg->inst_np[k];
+        InstDesc d;
+        std::memset(&d, 0, sizeof(d));
+        d.pop_off = po;
+        d.rot_off = rot_off[p];
+        d.fit_off = (int)fo;
+        d.np = np;
+        d.dim = D;
+        d.dpad = Dp;
+        d.obj = cfg->prob_obj[p];
+        const int group = cfg->inst_group ? cfg->inst_group[k] : (c->n_out > 0 ? k / c->n_out : 0);
+        d.stream = c->one_shot ? group : k;
+        d.shift_off = shift_off[p];
+        d.kp = std::max(1, (np * c->p_best_pct + 99) / 100);
+        d.prob = p;
+        c->hdesc[k] = d;
+        c->pop_off[k] = po;
+        c->fit_off[k] = fo;
+        c->dpad[k] = Dp;
+        for (int i = 0; i < np; ++i) row_inst.push_back(k);
+        po += (long long)np * Dp;
+        fo += np;
+        c->max_np = std::max(c->max_np, np);
+        c->max_dpad = std::max(c->max_dpad, Dp);
+        c->max_kp = std::max(c->max_kp, d.kp);
+    }
+    if (fo >= (1LL << 31)) {
+        delete c;
+        return METADE_EUNSUPPORTED;
+    }
+    c->pop_floats = po;
+    c->n_indiv = fo;
+
+    auto fail = [&](metade_status s) {
+        metade_destroy(c);
+        return s;
+    };
+    cudaError_t e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return fail(METADE_ECUDA);
+    if (dalloc(&c->desc, c->n_inst) || dalloc(&c->row_inst, row_inst.size()) || dalloc(&c->rot, rpad) ||
+        dalloc(&c->rotT, rpad) || dalloc(&c->shift, spad) || dalloc(&c->uscr, po) || dalloc(&c->fuscr, fo) ||
+        dalloc(&c->topk, c->max_np) || dalloc(&c->status, 1) || dalloc(&c->gen_dev, 1))
+        return fail(METADE_ENOMEM);
+    if (cudaMemset(c->status, 0, sizeof(int)) || cudaMemset(c->gen_dev, 0, sizeof(uint32_t)) ||
+        cudaMemset(c->uscr, 0, sizeof(float) * (size_t)std::max(po, 1LL)))
+        return fail(METADE_ECUDA);
+    if (c->n_inst > 0) {
+        if (cudaMemcpy(c->desc, c->hdesc.data(), sizeof(InstDesc) * c->n_inst, cudaMemcpyHostToDevice) ||
+            cudaMemcpy(c->row_inst, row_inst.data(), sizeof(int) * row_inst.size(), cudaMemcpyHostToDevice))
+            return fail(METADE_ECUDA);
+        // pad the problem table on the device
+        long long* d_rio = nullptr;
+        long long* d_ro = nullptr;
+        int *d_sio = nullptr, *d_so = nullptr, *d_dim = nullptr;
+        std::vector<int> dims(cfg->prob_dim, cfg->prob_dim + c->n_prob);
+        bool ok = !dalloc(&d_rio, c->n_prob) && !dalloc(&d_ro, c->n_prob) && !dalloc(&d_sio, c->n_prob) &&
+                  !dalloc(&d_so, c->n_prob) && !dalloc(&d_dim, c->n_prob);
+        ok = ok && !cudaMemcpy(d_rio, rot_in_off.data(), sizeof(long long) * c->n_prob, cudaMemcpyHostToDevice) &&
+             !cudaMemcpy(d_ro, rot_off.data(), sizeof(long long) * c->n_prob, cudaMemcpyHostToDevice) &&
+             !cudaMemcpy(d_sio, shift_in_off.data(), sizeof(int) * c->n_prob, cudaMemcpyHostToDevice) &&
+             !cudaMemcpy(d_so, shift_off.data(), sizeof(int) * c->n_prob, cudaMemcpyHostToDevice) &&
+             !cudaMemcpy(d_dim, dims.data(), sizeof(int) * c->n_prob, cudaMemcpyHostToDevice);
+        ok = ok && !launch_pad_problems(cfg->rot, cfg->shift, d_rio, d_sio, d_dim, d_ro, d_so, c->n_prob, c->max_dim,
+                                        c->rot, c->rotT, c->shift, c->st);
+        ok = ok && !cudaStreamSynchronize(c->st);
+        cudaFree(d_rio);
+        cudaFree(d_ro);
+        cudaFree(d_sio);
+        cudaFree(d_so);
+        cudaFree(d_dim);
+        if (!ok) return fail(METADE_ECUDA);
+        c->launches += 1;
+        metade_status s = build_plan(c);
+        if (s != METADE_OK) return fail(s);
+    }
+    *out = c;
+    return METADE_OK;
+}
+
+metade_status metade_layout(const metade_ctx* c, int64_t* pop_floats, int64_t* n_indiv, int32_t* n_groups) {
+    if (!c) return METADE_EINVAL;
+    if (pop_floats) *pop_floats = c->pop_floats;
+    if (n_indiv) *n_indiv = c->n_indiv;
+    if (n_groups) *n_groups = c->n_groups;
+    return METADE_OK;
+}
+
+metade_status metade_offsets(const metade_ctx* c, int64_t* pop_off, int64_t* fit_off, int32_t* dpad) {
+    if (!c) return METADE_EINVAL;
+    for (int k = 0; k < c->n_inst; ++k) {
+        if (pop_off) pop_off[k] = c->pop_off[k];
+        if (fit_off) fit_off[k] = c->fit_off[k];
+        if (dpad) dpad[k] = c->dpad[k];
+    }
+    return METADE_OK;
+}
+
+metade_status metade_set_stream(metade_ctx* c, void* stream) {
+    if (!c) return METADE_EINVAL;
+    c->st = (cudaStream_t)stream;
+    return METADE_OK;
+}
+
+metade_status metade_init(metade_ctx* c, float* pop, float* fit, uint32_t epoch) {
+    if (!c || (c->n_inst > 0 && (!pop || !fit))) return METADE_EINVAL;
+    if (epoch > 0xFFFFu) return METADE_EINVAL;
+    return run_init(c, c->st, pop, fit, epoch, nullptr, &c->launches);
+}
+
+metade_status metade_inner_step(metade_ctx* c, float* pop, float* fit, const float* theta, uint32_t epoch,
+                                uint32_t gen0, int32_t n_gens, float* best_f, int32_t* best_i) {
+    if (!c || n_gens < 0 || epoch > 0xFFFFu) return METADE_EINVAL;
+    if (c->n_inst > 0 && (!pop || !fit || !theta)) return METADE_EINVAL;
+    return run_inner(c, c->st, pop, fit, theta, epoch, nullptr, gen0, n_gens, best_f, best_i, &c->launches);
+}
+
+metade_status metade_eval(metade_ctx* c, const float* pop, metade_prec prec, void* f_out) {
+    if (!c || (c->n_inst > 0 && (!pop || !f_out))) return METADE_EINVAL;
+    if (prec != METADE_FP32 && prec != METADE_FP64) return METADE_EUNSUPPORTED;
+    if (c->n_inst == 0) return METADE_OK;
+    CK(launch_eval(c->desc, c->row_inst, c->n_indiv, pop, c->rotT, c->shift, prec == METADE_FP64, f_out, false,
+                   c->max_dpad, c->st));
+    c->launches += 1;
+    return METADE_OK;
+}
+
+metade_status metade_outer_init(metade_ctx* c, float* opop, float* ofit) {
+    if (!c) return METADE_EINVAL;
+    if (c->n_out == 0) return METADE_ESTATE;
+    if (!opop || !ofit) return METADE_EINVAL;
+    CK(launch_outer_init(c->n_groups, c->n_out, make_key(c->seed, kTagOuter), opop, ofit, c->st));
+    c->launches += 1;
+    return METADE_OK;
+}
+
+metade_status metade_outer_step(metade_ctx* c, float* opop, float* ofit, float* trial, float* theta,
+                                const float* meta_fit, uint32_t outer_gen, int32_t phase) {
+    if (!c) return METADE_EINVAL;
+    if (c->n_out == 0) return METADE_ESTATE;
+    if (phase == 0) {
+        if (!opop || !trial || !theta) return METADE_EINVAL;
+        CK(launch_outer_trial(c->n_groups, c->n_out, make_key(c->seed, kTagOuter), nullptr, outer_gen, opop, trial,
+                              theta, c->st));
+    } else if (phase == 1) {
+        if (!opop || !ofit || !trial || !meta_fit) return METADE_EINVAL;
+        CK(launch_outer_select(c->n_groups, c->n_out, opop, ofit, trial, meta_fit, c->st));
+    } else {
+        return METADE_EINVAL;
+    }
+    c->launches += 1;
+    return METADE_OK;
+}
+
+metade_status metade_outer_generation(metade_ctx* c, float* opop, float* ofit, float* trial, float* theta,
+                                      float* pop, float* fit, float* best_f, int32_t* best_i, uint32_t outer_gen,
+                                      int32_t n_inner, int32_t use_graph) {
+    if (!c) return METADE_EINVAL;
+    if (c->n_out == 0) return METADE_ESTATE;
+    if (!opop || !ofit || !trial || !theta || !pop || !fit || !best_f || n_inner < 0 || outer_gen > 0xFFFFu)
+        return METADE_EINVAL;
+    k_set_u32<<<1, 1, 0, c->st>>>(c->gen_dev, outer_gen);
+    CK(cudaGetLastError());
+    c->launches += 1;
+    if (!use_graph)
+        return enqueue_outer_generation(c, c->st, opop, ofit, trial, theta, pop, fit, best_f, best_i, n_inner,
+                                        &c->launches);
+    std::vector<uintptr_t> key = {(uintptr_t)opop, (uintptr_t)ofit, (uintptr_t)trial, (uintptr_t)theta,
+                                  (uintptr_t)pop, (uintptr_t)fit, (uintptr_t)best_f, (uintptr_t)best_i,
+                                  (uintptr_t)n_inner};
+    GraphEntry* ge = nullptr;
+    for (auto& g : c->graphs)
+        if (g.key == key) ge = &g;
+    if (!ge) {
+        // capture on the private stream, ordered after the caller's stream
+        cudaEvent_t ev;
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        CK(cudaEventRecord(ev, c->st));
+        CK(cudaStreamWaitEvent(c->cap, ev, 0));
+        CK(cudaStreamSynchronize(c->cap));
+        cudaEventDestroy(ev);
+        CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+        int64_t kernels = 0;
+        metade_status s =
+            enqueue_outer_generation(c, c->cap, opop, ofit, trial, theta, pop, fit, best_f, best_i, n_inner, &kernels);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->cap, &graph);
+        if (s != METADE_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return s;
+        }
+        CK(e);
+        cudaGraphExec_t exec;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(e);
+        c->graphs.push_back(GraphEntry{key, exec, kernels});
+        ge = &c->graphs.back();
+    }
+    CK(cudaGraphLaunch(ge->exec, c->st));
+    c->launches += ge->kernels;
+    return METADE_OK;
+}
+
+metade_status metade_draw_record(metade_ctx* c, const float* fit, const float* theta, uint32_t epoch, uint32_t gen,
+                                 int32_t* rec) {
+    if (!c || epoch > 0xFFFFu) return METADE_EINVAL;
+    if (c->n_inst == 0) return METADE_OK;
+    if (!fit || !theta || !rec) return METADE_EINVAL;
+    StepArgs a = step_args(c, nullptr, const_cast<float*>(fit), theta, epoch, nullptr, gen, 1, nullptr, nullptr);
+    CK(launch_record(a, c->n_inst, c->max_np, rec, c->st));
+    c->launches += 1;
+    return METADE_OK;
+}
+
+metade_status metade_sync(metade_ctx* c) {
+    if (!c) return METADE_EINVAL;
+    CK(cudaStreamSynchronize(c->st));
+    int s = 0;
+    CK(cudaMemcpy(&s, c->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (s != 0) CK(cudaMemset(c->status, 0, sizeof(int)));
+    return (metade_status)s;
+}
+
+metade_status metade_plan_info(const metade_ctx* c, char* buf, size_t len) {
+    if (!c || !buf || len == 0) return METADE_EINVAL;
+    std::string s = "{\"path\": \"";
+    s += c->path == METADE_PATH_PLAIN ? "plain" : "batched";
+    s += "\", \"buckets\": [";
+    for (size_t b = 0; b < c->buckets.size(); ++b) {
+        const Bucket& k = c->buckets[b];
+        char tmp[256];
+        snprintf(tmp, sizeof(tmp),
+                 "%s{\"kernel\": \"%s\", \"dmax\": %d, \"threads\": %d, \"grid\": %d, \"smem\": %zu, "
+                 "\"rot_smem\": %d, \"executors\": %d}",
+                 b ? ", " : "", k.plan.kind == 0 ? "fused_small" : "fused_general", k.plan.dmax, k.plan.threads,
+                 k.plan.grid, k.plan.smem, k.plan.rot_smem, k.n_work);
+        s += tmp;
+    }
+    s += "]}";
+    if (s.size() + 1 > len) return METADE_EINVAL;
+    std::memcpy(buf, s.c_str(), s.size() + 1);
+    return METADE_OK;
+}
+
+int64_t metade_launch_count(const metade_ctx* c) { return c ? c->launches : -1; }
+
+}  // extern "C"

@@ -1,0 +1,448 @@
+// device.cuh -- device building blocks of the MetaDE generation step.
+//
+// Philox4x32-10 counter RNG (Salmon et al., SC'11), the per-individual draws
+// of PDE (Sec. III-A: base vectors rand/best/pbest/current, dn difference
+// vectors of distinct random individuals), crossover masks (Sec. II-A:
+// binomial, exponential, arithmetic), and the synthetic shifted-rotated
+// objectives in FP32 (numerically stable forms) and FP64.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace metade {
+
+constexpr uint32_t kTagInner = 0x4D455441u;
+constexpr uint32_t kTagOuter = 0x4F555445u;
+constexpr uint32_t kInitGen = 0xFFFFFFFFu;
+constexpr int kRecFields = 18;
+
+// One executor, 64 bytes.  Offsets are in floats (population, padded
+// problem tables) or elements (fitness).
+struct InstDesc {
+    long long pop_off;   // row 0 of the executor in the population
+    long long rot_off;   // padded R [dim][dpad] (and R^T at the same offset in rotT)
+    int fit_off;         // individual 0 in fitness arrays
+    int np, dim, dpad;
+    int obj, stream;     // objective id, Philox counter word 0
+    int shift_off, kp;   // padded o [dpad]; pbest pool size
+    int prob, pad0, pad1, pad2;
+};
+static_assert(sizeof(InstDesc) == 64, "descriptor is one 64-byte record");
+
+struct Key {
+    uint32_t k0, k1;
+};
+
+__host__ __device__ inline Key make_key(uint64_t seed, uint32_t tag) {
+    return Key{(uint32_t)seed, (uint32_t)(seed >> 32) ^ tag};
+}
+
+// Philox4x32, 10 rounds: the two multiplies feed a half swap, the key is
+// mixed in and bumped by the Weyl increments (SC'11, Sec. 3.2).
+__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, Key k) {
+    uint32_t k0 = k.k0, k1 = k.k1;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+// Counter = (stream, generation, individual, (epoch << 16) | slot).
+struct Ctr {
+    Key key;
+    uint32_t stream, gen, indiv, epoch_hi;
+    __device__ __forceinline__ uint4 slot(uint32_t s) const {
+        return philox(stream, gen, indiv, epoch_hi | s, key);
+    }
+};
+
+__device__ __forceinline__ Ctr make_ctr(Key key, uint32_t stream, uint32_t gen, uint32_t indiv, uint32_t epoch) {
+    Ctr c;
+    c.key = key;
+    c.stream = stream;
+    c.gen = gen;
+    c.indiv = indiv;
+    c.epoch_hi = epoch << 16;
+    return c;
+}
+
+__device__ __forceinline__ uint32_t word_of(uint4 w, int q) {
+    return q == 0 ? w.x : (q == 1 ? w.y : (q == 2 ? w.z : w.w));
+}
+
+// floor(w * m / 2^32): an integer in [0, m)
+__device__ __forceinline__ uint32_t below(uint32_t w, uint32_t m) { return __umulhi(w, m); }
+
+// 24-bit uniform (w >> 8) 2^-24, exact in float
+__device__ __forceinline__ float uniform24(uint32_t w) { return (float)(w >> 8) * (1.0f / 16777216.0f); }
+
+// U < p  <=>  (w >> 8) < ceil(p 2^24); p * 2^24 and its ceiling are exact in float.
+__device__ __forceinline__ uint32_t threshold24(float p) {
+    if (!(p > 0.0f)) return 0u;
+    if (p >= 1.0f) return 16777216u;
+    return (uint32_t)ceilf(p * 16777216.0f);
+}
+
+// ------------------------------------------------------------- strategy
+struct Strat {
+    float F, CR;
+    int bl, br, dn, cs;
+    uint32_t cri;
+    int a, m;  // a = 1 when a rand base vector is used; m = a + 2 dn rand draws
+    bool ok;
+    __device__ __forceinline__ bool uses_pbest() const { return bl == 3 || br == 3; }
+};
+
+__device__ __forceinline__ Strat load_strat(const float* th, int np) {
+    Strat s;
+    s.F = th[0];
+    s.CR = th[1];
+    s.bl = (int)th[2];
+    s.br = (int)th[3];
+    s.dn = (int)th[4];
+    s.cs = (int)th[5];
+    s.a = (s.bl == 1 || s.br == 1) ? 1 : 0;
+    s.m = s.a + 2 * s.dn;
+    s.ok = isfinite(s.F) && isfinite(s.CR) && s.bl >= 1 && s.bl <= 4 && s.br >= 1 && s.br <= 4 &&
+           s.dn >= 1 && s.dn <= 4 && s.cs >= 1 && s.cs <= 3 && np >= s.m + 1;
+    if (!s.ok) {  // keep the arithmetic below well defined; the caller skips the executor
+        s.bl = s.br = 4;
+        s.dn = 1;
+        s.cs = 1;
+        s.a = 0;
+        s.m = 2;
+    }
+    s.cri = threshold24(s.CR);
+    return s;
+}
+
+// ------------------------------------------------------ individual draws
+struct Indiv {
+    int ibl, ibr;      // resolved base-left / base-right individuals
+    int jrand, nstart; // binomial forced coordinate, exponential start
+    int pbest;         // pbest individual (or -1 when the pool is not known)
+    uint32_t kraw;     // K_i as a 24-bit integer
+    int r[9];          // distinct rand draws r_0..r_{m-1}
+};
+
+// t-th draw: s = floor(w_t (np - 1 - t) / 2^32), then step s past the sorted
+// excluded set {i, r_0..r_{t-1}}: the s-th smallest admissible index.
+__device__ __forceinline__ void distinct_draws(int np, int i, int m, const uint32_t (&w)[12], int (&r)[9]) {
+    int ex[10];
+    ex[0] = i;
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+        r[t] = -1;
+        if (t < m) {
+            int v = (int)below(w[t], (uint32_t)(np - 1 - t));
+#pragma unroll
+            for (int e = 0; e < 10; ++e)
+                if (e <= t && v >= ex[e]) ++v;
+            r[t] = v;
+            // insert v into ex[0..t] keeping it ascending
+            bool placed = false;
+#pragma unroll
+            for (int e = 9; e >= 1; --e) {
+                if (e <= t + 1 && !placed) {
+                    if (ex[e - 1] > v) {
+                        ex[e] = ex[e - 1];
+                    } else {
+                        ex[e] = v;
+                        placed = true;
+                    }
+                }
+            }
+            if (!placed) ex[0] = v;
+        }
+    }
+}
+
+// Slot 0 words and the rand draws of individual i.  `topk` (the pbest pool,
+// ascending by stored fitness) may be null when the strategy does not use it.
+__device__ __forceinline__ void indiv_setup(const Strat& s, const Ctr& c, int i, int np, int dim, int kp,
+                                            const int* topk, int best, Indiv& d) {
+    const uint4 w0 = c.slot(0);
+    d.jrand = (int)below(w0.x, (uint32_t)dim);
+    d.nstart = (int)below(w0.y, (uint32_t)dim);
+    d.kraw = w0.z >> 8;
+    d.pbest = topk ? topk[below(w0.w, (uint32_t)kp)] : -1;
+    uint32_t w[12];
+    uint4 a = make_uint4(0, 0, 0, 0), b = a, e = a;
+    if (s.m > 0) a = c.slot(1);
+    if (s.m > 4) b = c.slot(2);
+    if (s.m > 8) e = c.slot(3);
+    w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+    w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+    w[8] = e.x; w[9] = e.y; w[10] = e.z; w[11] = e.w;
+    distinct_draws(np, i, s.m, w, d.r);
+    const int rb = d.r[0];
+    d.ibl = s.bl == 1 ? rb : (s.bl == 2 ? best : (s.bl == 3 ? d.pbest : i));
+    d.ibr = s.br == 1 ? rb : (s.br == 2 ? best : (s.br == 3 ? d.pbest : i));
+}
+
+// r index of difference q: plus-term (r[a + 2q]) and minus-term (r[a + 2q + 1])
+__device__ __forceinline__ int diff_plus(const Indiv& d, int a, int q) {
+    return a ? (q == 0 ? d.r[1] : q == 1 ? d.r[3] : q == 2 ? d.r[5] : d.r[7])
+             : (q == 0 ? d.r[0] : q == 1 ? d.r[2] : q == 2 ? d.r[4] : d.r[6]);
+}
+__device__ __forceinline__ int diff_minus(const Indiv& d, int a, int q) {
+    return a ? (q == 0 ? d.r[2] : q == 1 ? d.r[4] : q == 2 ? d.r[6] : d.r[8])
+             : (q == 0 ? d.r[1] : q == 1 ? d.r[3] : q == 2 ? d.r[5] : d.r[7]);
+}
+
+// Exponential crossover length: L = 1, grow while L < D and the (L-1)-th
+// coordinate uniform (slot 4 + (L-1)/4) is below CR.
+__device__ __forceinline__ int exp_length(const Ctr& c, int dim, uint32_t cri) {
+    int L = 1;
+    for (uint32_t slot = 4; L < dim; ++slot) {
+        const uint4 w = c.slot(slot);
+        bool stop = false;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (!stop && L < dim) {
+                if ((word_of(w, q) >> 8) < cri) ++L;
+                else stop = true;
+            }
+        }
+        if (stop) break;
+    }
+    return L;
+}
+
+// ----------------------------------------------------------- objectives
+// FP32 forms are algebraically equal to the textbook definitions but avoid
+// cancellation near the optimum:
+//   Rastrigin  z^2 - 10 cos 2 pi z + 10      = z^2 + 20 sin^2(pi z)
+//   Ackley     20 + e - 20 e^{-0.2 r} - e^{C/D} = -20 expm1(-0.2 r) - e expm1(-2 S/D),
+//              r = sqrt(sum z^2 / D), S = sum sin^2(pi z)
+//   Griewank   1 - prod cos a_j = -expm1(sum log1p(-2 sin^2(a_j/2))) when every
+//              cos a_j > 0, else evaluated directly (no cancellation then)
+//   Rosenbrock y = z + 1: y_{j+1} - y_j^2 = z_{j+1} - z_j (z_j + 2), y_j - 1 = z_j
+enum Obj { kSphere = 0, kRosenbrock = 1, kRastrigin = 2, kGriewank = 3, kAckley = 4, kSchwefel12 = 5 };
+
+// Streaming accumulator: objectives consume z_0, z_1, ... in order.
+template <typename T>
+struct ObjAcc {
+    T s0, s1, s2, prev;
+    int n;
+    bool pos;
+};
+
+template <typename T>
+__device__ __forceinline__ T sinpi_t(T x);
+template <>
+__device__ __forceinline__ float sinpi_t<float>(float x) { return sinpif(x); }
+template <>
+__device__ __forceinline__ double sinpi_t<double>(double x) { return sinpi(x); }
+
+template <typename T>
+__device__ __forceinline__ void obj_init(ObjAcc<T>& a) {
+    a.s0 = T(0); a.s1 = T(0); a.s2 = T(0); a.prev = T(0); a.n = 0; a.pos = true;
+}
+
+template <typename T>
+__device__ __forceinline__ void obj_push(int obj, ObjAcc<T>& a, T z) {
+    switch (obj) {
+    case kSphere: a.s0 += z * z; break;
+    case kRosenbrock:
+        if (a.n > 0) {
+            const T t = z - a.prev * (a.prev + T(2));
+            a.s0 += T(100) * t * t + a.prev * a.prev;
+        }
+        a.prev = z;
+        break;
+    case kRastrigin: {
+        const T s = sinpi_t<T>(z);
+        a.s0 += z * z + T(20) * s * s;
+        break;
+    }
+    case kGriewank: {
+        a.s0 += z * z;
+        const T arg = z / sqrt(T(a.n + 1));
+        const T h = sin(arg * T(0.5));
+        a.s1 += log1p(T(-2) * h * h);
+        const T c = cos(arg);
+        a.pos = a.pos && (c > T(0));
+        a.s2 = (a.n == 0) ? c : a.s2 * c;
+        break;
+    }
+    case kAckley: {
+        a.s0 += z * z;
+        const T s = sinpi_t<T>(z);
+        a.s1 += s * s;
+        break;
+    }
+    case kSchwefel12:
+        a.prev += z;
+        a.s0 += a.prev * a.prev;
+        break;
+    }
+    ++a.n;
+}
+
+template <typename T>
+__device__ __forceinline__ T obj_finish(int obj, const ObjAcc<T>& a, int dim) {
+    switch (obj) {
+    case kGriewank: {
+        const T one_minus_p = a.pos ? -expm1(a.s1) : (T(1) - a.s2);
+        return a.s0 / T(4000) + one_minus_p;
+    }
+    case kAckley: {
+        const T r = sqrt(a.s0 / T(dim));
+        return T(-20) * expm1(T(-0.2) * r) - T(2.71828182845904523536) * expm1(T(-2) * a.s1 / T(dim));
+    }
+    default: return a.s0;
+    }
+}
+
+__device__ __forceinline__ float nan_to_inf(float f) { return isnan(f) ? INFINITY : f; }
+__device__ __forceinline__ double nan_to_inf(double f) { return isnan(f) ? (double)INFINITY : f; }
+
+// Sequential FP64 evaluation of one float32 point (selection ties, FP64
+// evaluation).  o: padded shift, R: padded rows [dim][dpad].
+__device__ __forceinline__ double eval64_seq(int obj, int dim, int dpad, const float* x, const float* o,
+                                             const float* R) {
+    ObjAcc<double> a;
+    obj_init(a);
+    for (int r = 0; r < dim; ++r) {
+        double z = 0.0;
+        const float* row = R + (size_t)r * dpad;
+        for (int c = 0; c < dim; ++c) z = fma((double)row[c], (double)x[c] - (double)o[c], z);
+        obj_push(obj, a, z);
+    }
+    return obj_finish(obj, a, dim);
+}
+
+// ----------------------------------------------------- tie differences
+// Selection ties are decided on D = f(u) - f(x) evaluated directly as a
+// difference, from z = R (x - o) and dz = R (u - x), so that its rounding
+// error scales with |D| instead of |f|:
+//   z^2 terms        (z+dz)^2 - z^2            = dz (2 z + dz)
+//   sin^2 terms      sin^2(pi(z+dz)) - sin^2(pi z) = sin(pi(2z+dz)) sin(pi dz)
+//   Rosenbrock t     t' - t = dz_{j+1} - dz_j (2 z_j + 2 + dz_j)
+//   Schwefel prefix  p' - p = running sum of dz
+//   Griewank product P' - P = P expm1(sum log1p(cos(a+da)/cos(a) - 1)),
+//                    cos(a+da)/cos(a) - 1 = -2 sin^2(da/2) - tan(a) sin(da)
+//   Ackley           r' - r = (r'^2 - r^2) / (r' + r);  e^{-c r} - e^{-c r'} =
+//                    -e^{-c r} expm1(-c (r' - r)), likewise for the cosine mean.
+struct DiffAcc {
+    float d0, d1, x0, x1;  // difference sums, x-side sums
+    float pz, pdz;         // previous z, dz (Rosenbrock)
+    float p, dp;           // prefix of z, dz (Schwefel 1.2)
+    float lr, px, pu;      // Griewank: sum log ratio, direct products
+    bool ok;               // Griewank: every ratio positive
+    int n;
+};
+
+__device__ __forceinline__ void diff_init(DiffAcc& a) {
+    a.d0 = a.d1 = a.x0 = a.x1 = 0.f;
+    a.pz = a.pdz = a.p = a.dp = 0.f;
+    a.lr = 0.f;
+    a.px = a.pu = 1.f;
+    a.ok = true;
+    a.n = 0;
+}
+
+__device__ __forceinline__ void diff_push(int obj, DiffAcc& a, float z, float dz) {
+    switch (obj) {
+    case kSphere: a.d0 += dz * (2.f * z + dz); break;
+    case kRosenbrock:
+        if (a.n > 0) {
+            const float t = z - a.pz * (a.pz + 2.f);
+            const float dt = dz - a.pdz * (2.f * a.pz + 2.f + a.pdz);
+            a.d0 += 100.f * dt * (2.f * t + dt) + a.pdz * (2.f * a.pz + a.pdz);
+        }
+        a.pz = z;
+        a.pdz = dz;
+        break;
+    case kRastrigin:
+        a.d0 += dz * (2.f * z + dz) + 20.f * sinpif(2.f * z + dz) * sinpif(dz);
+        break;
+    case kGriewank: {
+        a.d0 += dz * (2.f * z + dz);
+        const float inv = rsqrtf((float)(a.n + 1));
+        const float ang = z * inv, da = dz * inv;
+        const float ca = cosf(ang), cu = cosf(ang + da);
+        a.px *= ca;
+        a.pu *= cu;
+        const float h = sinf(0.5f * da);
+        const float rm1 = -2.f * h * h - tanf(ang) * sinf(da);
+        a.ok = a.ok && (ca != 0.f) && (rm1 > -1.f);
+        a.lr += log1pf(rm1);
+        break;
+    }
+    case kAckley: {
+        a.x0 += z * z;
+        a.d0 += dz * (2.f * z + dz);
+        const float s = sinpif(z);
+        a.x1 += s * s;
+        a.d1 += sinpif(2.f * z + dz) * sinpif(dz);
+        break;
+    }
+    case kSchwefel12:
+        a.p += z;
+        a.dp += dz;
+        a.d0 += a.dp * (2.f * a.p + a.dp);
+        break;
+    }
+    ++a.n;
+}
+
+__device__ __forceinline__ float diff_finish(int obj, const DiffAcc& a, int dim) {
+    switch (obj) {
+    case kGriewank: {
+        const float dP = a.ok ? a.px * expm1f(a.lr) : (a.pu - a.px);
+        return a.d0 / 4000.f - dP;
+    }
+    case kAckley: {
+        const float rx = sqrtf(a.x0 / dim), ru = sqrtf(fmaxf(a.x0 + a.d0, 0.f) / dim);
+        const float dr = (ru + rx > 0.f) ? (a.d0 / dim) / (ru + rx) : 0.f;
+        return -20.f * expf(-0.2f * rx) * expm1f(-0.2f * dr) -
+               2.71828182845904523536f * expf(-2.f * a.x1 / dim) * expm1f(-2.f * a.d1 / dim);
+    }
+    default: return a.d0;
+    }
+}
+
+// Sequential difference f(u) - f(x) of two float32 points (rows of length
+// dim, shift o, padded rows R with stride ldr).
+__device__ __forceinline__ float diff_seq(int obj, int dim, int ldr, const float* u, const float* x, const float* o,
+                                          const float* R) {
+    DiffAcc a;
+    diff_init(a);
+    for (int r = 0; r < dim; ++r) {
+        const float* row = R + (size_t)r * ldr;
+        float z = 0.f, dz = 0.f;
+        for (int c = 0; c < dim; ++c) {
+            z = fmaf(row[c], x[c] - o[c], z);
+            dz = fmaf(row[c], u[c] - x[c], dz);
+        }
+        diff_push(obj, a, z, dz);
+    }
+    return diff_finish(obj, a, dim);
+}
+
+// Selection ties: |f(u) - f(x)| <= 1e-6 |f(x)| with both values finite and
+// positive are decided by an FP64 re-evaluation (the band is relative: FP32
+// resolves f to ~1e-7 relative at any magnitude, and an absolute floor would
+// send every trial of a converged executor down the FP64 path).  Values that
+// underflowed to 0 compare as equal and the trial wins.
+__device__ __forceinline__ bool near_tie(float fu, float fx) {
+    return isfinite(fu) && isfinite(fx) && fx > 0.0f && fu > 0.0f && fabsf(fu - fx) <= 1e-6f * fx;
+}
+
+// Sticky device status: the first error wins.
+__device__ __forceinline__ void set_status(int* status, int code) {
+    if (status) atomicCAS(status, 0, code);
+}
+
+}  // namespace metade

@@ -1,0 +1,76 @@
+// internal.h -- host-side launchers shared by the translation units of the
+// library (not part of the C-ABI).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+
+namespace metade {
+
+struct StepArgs {
+    const InstDesc* desc;
+    float* pop;
+    float* fit;
+    const float* theta;
+    const float* rot;    // padded R rows [dim][dpad] per problem
+    const float* rotT;   // padded R^T [dim][dpad] per problem
+    const float* shift;  // padded o [dpad] per problem
+    Key key;
+    uint32_t epoch, gen0;
+    const uint32_t* epoch_dev;  // when non-null, the epoch is read here (graph replays)
+    int n_gens;
+    float lo, hi;
+    float* best_f;
+    int* best_i;
+    int* status;
+    int tie_fp64;  // 1: FP64 re-evaluation of both vectors; 0: FP32 difference form
+};
+
+// Problem table: pad R to rows of dpad floats, build R^T, pad o.
+cudaError_t launch_pad_problems(const float* rot_in, const float* shift_in, const long long* rot_in_off,
+                                const int* shift_in_off, const int* dims, const long long* rot_off,
+                                const int* shift_off, int n_prob, int max_dim, float* rot, float* rotT,
+                                float* shift, cudaStream_t st);
+
+cudaError_t launch_init(const InstDesc* desc, int n_inst, int max_np, int max_dpad, float* pop, Key key,
+                        uint32_t epoch, const uint32_t* epoch_dev, float lo, float hi, cudaStream_t st);
+
+// Evaluate every row (row_inst maps rows to executors).  f64 selects FP64.
+cudaError_t launch_eval(const InstDesc* desc, const int* row_inst, long long n_rows, const float* pop,
+                        const float* rotT, const float* shift, bool f64, void* f_out, bool nan_inf,
+                        int max_dpad, cudaStream_t st);
+
+cudaError_t launch_record(const StepArgs& a, int n_inst, int max_np, int* rec, cudaStream_t st);
+
+cudaError_t launch_best(const InstDesc* desc, int n_inst, const float* fit, float* best_f, int* best_i,
+                        cudaStream_t st);
+
+// Plain path: one executor, one generation, three launches.
+cudaError_t launch_plain_generation(const StepArgs& a, int k, const InstDesc& d, float* u_scratch,
+                                    float* fu_scratch, int* topk_scratch, cudaStream_t st);
+
+// Batched path: executors listed in `work` (schedule order), all n_gens generations.
+struct FusedPlan {
+    int kind;      // 0 small (thread per individual), 1 general (warp per individual)
+    int dmax;      // small: compile-time row bound
+    int threads;   // block size
+    int grid;      // CTAs (<= n_work; CTAs loop over work items)
+    size_t smem;   // dynamic shared memory per CTA
+    int rot_smem;  // general: R^T staged in shared memory
+    int max_np, max_dpad;  // general: bucket maxima the shared layout is cut for
+};
+cudaError_t launch_fused(const StepArgs& a, const int* work, int n_work, const FusedPlan& p, float* u_scratch,
+                         cudaStream_t st);
+size_t fused_smem_small(int dmax, int max_np);
+size_t fused_smem_general(int max_np, int max_dpad, int threads, bool rot_in_smem);
+int small_dmax_for(int dim);  // 0 when the small kernel does not apply
+
+// Evolver.
+cudaError_t launch_outer_init(int n_groups, int n_out, Key key, float* opop, float* ofit, cudaStream_t st);
+cudaError_t launch_outer_trial(int n_groups, int n_out, Key key, const uint32_t* gen_dev, uint32_t gen,
+                               const float* opop, float* trial, float* theta, cudaStream_t st);
+cudaError_t launch_outer_select(int n_groups, int n_out, float* opop, float* ofit, const float* trial,
+                                const float* meta_fit, cudaStream_t st);
+
+}  // namespace metade

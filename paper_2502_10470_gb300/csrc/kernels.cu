@@ -1,0 +1,731 @@
+// kernels.cu -- CUDA kernels of the MetaDE hot path (sm_103a).
+//
+//  k_pad_problems   problem table: R rows padded to Dpad, R^T, padded o
+//  k_init           Alg. 2 lines 1: population uniform in the box
+//  k_eval           shifted-rotated objective of every row, FP32 or FP64
+//  k_record         the draw record of one generation (parity checks)
+//  k_best           y* = min fitness per executor (Sec. III-B)
+//  k_plain_*        plain path: one executor, one generation, three launches
+//  k_fused_small    batched path, D <= 32: one CTA per executor, one thread per
+//                   individual, population/trials/R resident in shared memory
+//                   for all fused generations
+//  k_fused_general  batched path, any D: one CTA per executor, one warp per
+//                   individual, population in global memory (L2-resident),
+//                   R^T staged in shared memory when it fits
+//  k_outer_*        the evolver of Alg. 3 (rand/1/bin, decode, selection)
+#include <cstdio>
+
+#include "block.cuh"
+#include "internal.h"
+
+namespace metade {
+
+// ------------------------------------------------------------ problems
+__global__ void k_pad_problems(const float* __restrict__ rot_in, const float* __restrict__ shift_in,
+                               const long long* __restrict__ rot_in_off, const int* __restrict__ shift_in_off,
+                               const int* __restrict__ dims, const long long* __restrict__ rot_off,
+                               const int* __restrict__ shift_off, float* rot, float* rotT, float* shift) {
+    const int p = blockIdx.x, r = blockIdx.y;
+    const int dim = dims[p], dp = (dim + 3) & ~3;
+    if (r >= dim) return;
+    const float* Rin = rot_in + rot_in_off[p];
+    for (int c = threadIdx.x; c < dp; c += blockDim.x) {
+        rot[rot_off[p] + (long long)r * dp + c] = c < dim ? Rin[(long long)r * dim + c] : 0.0f;
+        // rotT row r holds column r of R: rotT[r][c] = R[c][r]
+        rotT[rot_off[p] + (long long)r * dp + c] = c < dim ? Rin[(long long)c * dim + r] : 0.0f;
+    }
+    if (r == 0)
+        for (int j = threadIdx.x; j < dp; j += blockDim.x)
+            shift[shift_off[p] + j] = j < dim ? shift_in[shift_in_off[p] + j] : 0.0f;
+}
+
+cudaError_t launch_pad_problems(const float* rot_in, const float* shift_in, const long long* rot_in_off,
+                                const int* shift_in_off, const int* dims, const long long* rot_off,
+                                const int* shift_off, int n_prob, int max_dim, float* rot, float* rotT,
+                                float* shift, cudaStream_t st) {
+    dim3 grid(n_prob, max_dim);
+    k_pad_problems<<<grid, 128, 0, st>>>(rot_in, shift_in, rot_in_off, shift_in_off, dims, rot_off, shift_off,
+                                         rot, rotT, shift);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- init
+// Thread per (individual, 4-coordinate chunk): slot j/4 of generation
+// 0xFFFFFFFF; x = lo + (hi - lo) U rounded once (fmaf).  Pad columns zero.
+__global__ void k_init(const InstDesc* __restrict__ desc, float* pop, Key key, uint32_t epoch_arg,
+                       const uint32_t* epoch_dev, float lo, float hi) {
+    const InstDesc d = desc[blockIdx.y];
+    const uint32_t epoch = epoch_dev ? *epoch_dev : epoch_arg;
+    const int chunks = d.dpad >> 2;
+    const float span = hi - lo;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < d.np * chunks; e += gridDim.x * blockDim.x) {
+        const int i = e / chunks, q = e - i * chunks;
+        const uint4 w = philox((uint32_t)d.stream, kInitGen, (uint32_t)i, (epoch << 16) | (uint32_t)q, key);
+        float x[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) x[t] = (4 * q + t < d.dim) ? fmaf(span, uniform24(word_of(w, t)), lo) : 0.0f;
+        *reinterpret_cast<float4*>(pop + d.pop_off + (long long)i * d.dpad + 4 * q) = make_float4(x[0], x[1], x[2], x[3]);
+    }
+}
+
+cudaError_t launch_init(const InstDesc* desc, int n_inst, int max_np, int max_dpad, float* pop, Key key,
+                        uint32_t epoch, const uint32_t* epoch_dev, float lo, float hi, cudaStream_t st) {
+    if (n_inst <= 0) return cudaSuccess;
+    const int work = max_np * (max_dpad / 4);
+    dim3 grid((work + 255) / 256, n_inst);
+    k_init<<<grid, 256, 0, st>>>(desc, pop, key, epoch, epoch_dev, lo, hi);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- eval
+// Warp per row.  Dynamic shared: per warp 4 * max_dpad floats.
+template <bool F64>
+__global__ void __launch_bounds__(256) k_eval(const InstDesc* __restrict__ desc, const int* __restrict__ row_inst,
+                                              long long n_rows, const float* __restrict__ pop,
+                                              const float* __restrict__ rotT, const float* __restrict__ shift,
+                                              void* f_out, int nan_inf, int scratch) {
+    extern __shared__ __align__(16) float sm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* wb = sm + (size_t)warp * scratch;
+    for (long long row = (long long)blockIdx.x * (blockDim.x >> 5) + warp; row < n_rows;
+         row += (long long)gridDim.x * (blockDim.x >> 5)) {
+        const int k = row_inst[row];
+        const InstDesc d = desc[k];
+        const long long i = row - d.fit_off;
+        const float* x = pop + d.pop_off + i * d.dpad;
+        const float* o = shift + d.shift_off;
+        const float* RT = rotT + d.rot_off;
+        if (F64) {
+            double* db = reinterpret_cast<double*>(wb);
+            const double f = warp_eval64(d.obj, d.dim, x, o, RT, d.dpad, db, db + d.dpad);
+            if (lane == 0) reinterpret_cast<double*>(f_out)[row] = nan_inf ? nan_to_inf(f) : f;
+        } else {
+            float* db = wb;
+            float* zb = wb + d.dpad;
+            for (int j = lane; j < d.dpad; j += 32) db[j] = j < d.dim ? x[j] - o[j] : 0.0f;
+            __syncwarp();
+            warp_rotate<float>(d.dim, RT, d.dpad, db, zb);
+            __syncwarp();
+            const float f = warp_objective<float>(d.obj, d.dim, zb);
+            if (lane == 0) reinterpret_cast<float*>(f_out)[row] = nan_inf ? nan_to_inf(f) : f;
+            __syncwarp();
+        }
+    }
+}
+
+static int g_num_sms = 0;
+static int num_sms() {
+    if (!g_num_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 132;
+    }
+    return g_num_sms;
+}
+
+cudaError_t launch_eval(const InstDesc* desc, const int* row_inst, long long n_rows, const float* pop,
+                        const float* rotT, const float* shift, bool f64, void* f_out, bool nan_inf, int max_dpad,
+                        cudaStream_t st) {
+    if (n_rows <= 0) return cudaSuccess;
+    const int scratch = 4 * max_dpad;  // floats per warp: two buffers of max_dpad doubles
+    const size_t smem = (size_t)8 * scratch * sizeof(float);
+    long long blocks = (n_rows + 7) / 8;
+    const long long cap = (long long)num_sms() * 16;
+    if (blocks > cap) blocks = cap;
+    if (f64) {
+        cudaFuncSetAttribute(k_eval<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_eval<true><<<(unsigned)blocks, 256, smem, st>>>(desc, row_inst, n_rows, pop, rotT, shift, f_out,
+                                                          nan_inf, scratch);
+    } else {
+        cudaFuncSetAttribute(k_eval<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_eval<false><<<(unsigned)blocks, 256, smem, st>>>(desc, row_inst, n_rows, pop, rotT, shift, f_out,
+                                                           nan_inf, scratch);
+    }
+    return cudaGetLastError();
+}
+
+// -------------------------------------------------------------- record
+// Block per executor, thread per individual; the pool and best come from the
+// generation-start fitness.  Dynamic shared: topk [np] + 64 words.
+__global__ void k_record(StepArgs a, int* rec) {
+    extern __shared__ int smi[];
+    const int k = blockIdx.x;
+    const InstDesc d = a.desc[k];
+    const float* f = a.fit + d.fit_off;
+    int* topk = smi;
+    const Strat s = load_strat(a.theta + 6 * k, d.np);
+    if (!s.ok) {
+        if (threadIdx.x == 0) set_status(a.status, 1);
+        return;
+    }
+    block_topk(f, d.np, d.kp, topk);
+    __syncthreads();
+    const int best = topk[0];
+    for (int i = threadIdx.x; i < d.np; i += blockDim.x) {
+        const Ctr c = make_ctr(a.key, (uint32_t)d.stream, a.gen0, (uint32_t)i, a.epoch_dev ? *a.epoch_dev : a.epoch);
+        Indiv v;
+        indiv_setup(s, c, i, d.np, d.dim, d.kp, topk, best, v);
+        int* q = rec + (long long)(d.fit_off + i) * kRecFields;
+        q[0] = v.ibl;
+        q[1] = v.ibr;
+        q[2] = v.jrand;
+        q[3] = v.nstart;
+        q[4] = s.cs == 2 ? exp_length(c, d.dim, s.cri) : 0;
+        q[5] = (int)v.kraw;
+        q[6] = v.pbest;
+        q[7] = best;
+        q[8] = s.m;
+#pragma unroll
+        for (int t = 0; t < 9; ++t) q[9 + t] = v.r[t];
+    }
+}
+
+cudaError_t launch_record(const StepArgs& a, int n_inst, int max_np, int* rec, cudaStream_t st) {
+    k_record<<<n_inst, 256, (size_t)max_np * sizeof(int), st>>>(a, rec);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- best
+__global__ void k_best(const InstDesc* __restrict__ desc, const float* __restrict__ fit, float* best_f,
+                       int* best_i) {
+    __shared__ int red[64];
+    const InstDesc d = desc[blockIdx.x];
+    const int b = block_argmin(fit + d.fit_off, d.np, red);
+    if (threadIdx.x == 0) {
+        if (best_f) best_f[blockIdx.x] = fit[d.fit_off + b];
+        if (best_i) best_i[blockIdx.x] = b;
+    }
+}
+
+cudaError_t launch_best(const InstDesc* desc, int n_inst, const float* fit, float* best_f, int* best_i,
+                        cudaStream_t st) {
+    if (n_inst <= 0) return cudaSuccess;
+    k_best<<<n_inst, 256, 0, st>>>(desc, fit, best_f, best_i);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------- plain path
+// The FP32 baseline: one executor per launch, one generation per launch,
+// everything through global memory, no fusion, no graph, no tuning.
+__global__ void k_plain_prologue(StepArgs a, int k, int* topk) {
+    const InstDesc d = a.desc[k];
+    const Strat s = load_strat(a.theta + 6 * k, d.np);
+    if (!s.ok) {
+        if (threadIdx.x == 0) set_status(a.status, 1);
+        return;
+    }
+    block_topk(a.fit + d.fit_off, d.np, d.kp, topk);
+}
+
+__global__ void __launch_bounds__(256) k_plain_trial(StepArgs a, int k, const int* __restrict__ topk, float* uscr,
+                                                     float* fuscr) {
+    extern __shared__ __align__(16) float sm[];
+    const InstDesc d = a.desc[k];
+    const Strat s = load_strat(a.theta + 6 * k, d.np);
+    if (!s.ok) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (i >= d.np) return;
+    float* db = sm + (size_t)warp * 2 * d.dpad;
+    float* zb = db + d.dpad;
+    const Ctr c = make_ctr(a.key, (uint32_t)d.stream, a.gen0, (uint32_t)i, a.epoch_dev ? *a.epoch_dev : a.epoch);
+    Indiv v;
+    indiv_setup(s, c, i, d.np, d.dim, d.kp, topk, topk[0], v);
+    const int L = s.cs == 2 ? exp_length(c, d.dim, s.cri) : 0;
+    const float* X = a.pop + d.pop_off;
+    warp_trial(s, c, v, i, d.dim, L, X, d.dpad, a.shift + d.shift_off, a.lo, a.hi,
+               uscr + d.pop_off + (long long)i * d.dpad, db);
+    __syncwarp();
+    warp_rotate<float>(d.dim, a.rotT + d.rot_off, d.dpad, db, zb);
+    __syncwarp();
+    const float f = warp_objective<float>(d.obj, d.dim, zb);
+    if (lane == 0) fuscr[d.fit_off + i] = nan_to_inf(f);
+}
+
+__global__ void __launch_bounds__(256) k_plain_select(StepArgs a, int k, const float* __restrict__ uscr,
+                                                      const float* __restrict__ fuscr) {
+    extern __shared__ __align__(16) float sm[];
+    const InstDesc d = a.desc[k];
+    const Strat s = load_strat(a.theta + 6 * k, d.np);
+    if (!s.ok) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (i >= d.np) return;
+    float* X = a.pop + d.pop_off + (long long)i * d.dpad;
+    const float* U = uscr + d.pop_off + (long long)i * d.dpad;
+    float fn = fuscr[d.fit_off + i];
+    const float fx = a.fit[d.fit_off + i];
+    bool take;
+    bool tie = near_tie(fn, fx);
+    if (tie) {
+        bool diff = false;
+        for (int j = lane; j < d.dim; j += 32) diff = diff || (U[j] != X[j]);
+        if (!__any_sync(kFull, diff)) tie = false, fn = fx;  // trial == target
+    }
+    const float* o = a.shift + d.shift_off;
+    const float* RT = a.rotT + d.rot_off;
+    if (tie && a.tie_fp64) {
+        double* db = reinterpret_cast<double*>(sm + (size_t)warp * 4 * d.dpad);
+        const double eu = nan_to_inf(warp_eval64(d.obj, d.dim, U, o, RT, d.dpad, db, db + d.dpad));
+        const double ex = nan_to_inf(warp_eval64(d.obj, d.dim, X, o, RT, d.dpad, db, db + d.dpad));
+        take = eu <= ex;
+        if (take) fn = fminf((float)eu, fx);
+    } else if (tie) {
+        float* zb = sm + (size_t)warp * 4 * d.dpad;
+        warp_rotate_pair(d.dim, RT, d.dpad, X, U, o, zb, zb + d.dpad);
+        __syncwarp();
+        const float df = warp_diff(d.obj, d.dim, zb, zb + d.dpad);
+        take = df <= 0.0f;
+        if (take) fn = fx + df;
+    } else {
+        take = fn <= fx;
+    }
+    if (take) {
+        for (int j = lane * 4; j < d.dpad; j += 128)
+            *reinterpret_cast<float4*>(X + j) = *reinterpret_cast<const float4*>(U + j);
+        if (lane == 0) a.fit[d.fit_off + i] = fn;
+    }
+}
+
+cudaError_t launch_plain_generation(const StepArgs& a, int k, const InstDesc& d, float* uscr, float* fuscr,
+                                    int* topk, cudaStream_t st) {
+    k_plain_prologue<<<1, 256, 0, st>>>(a, k, topk);
+    const int blocks = (d.np + 7) / 8;
+    const size_t smem_t = (size_t)8 * 2 * d.dpad * sizeof(float);
+    const size_t smem_s = (size_t)8 * 4 * d.dpad * sizeof(float);
+    if (smem_s > 48 * 1024) {
+        cudaFuncSetAttribute(k_plain_trial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
+        cudaFuncSetAttribute(k_plain_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s);
+    }
+    k_plain_trial<<<blocks, 256, smem_t, st>>>(a, k, topk, uscr, fuscr);
+    k_plain_select<<<blocks, 256, smem_s, st>>>(a, k, uscr, fuscr);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------ batched path, small D
+// Thread-level trial: individual i's trial row into U (shared, stride ds) and
+// u - o into registers.
+template <int DMAX>
+__device__ __forceinline__ void thread_trial(const Strat& s, const Ctr& c, const Indiv& v, int i, int dim, int ds,
+                                             int L, const float* X, const float* o, float lo, float hi, float* U,
+                                             float (&dreg)[DMAX]) {
+    const float F = s.F, K = (float)v.kraw * (1.0f / 16777216.0f);
+    const float* xl = X + v.ibl * ds;
+    const float* xr = X + v.ibr * ds;
+    const float* xi = X + i * ds;
+    const bool dir = s.bl != s.br;
+#pragma unroll
+    for (int j4 = 0; j4 < DMAX; j4 += 4) {
+        if (j4 < dim) {
+            const float4 a = *reinterpret_cast<const float4*>(xl + j4);
+            const float4 b = *reinterpret_cast<const float4*>(xr + j4);
+            const float4 x = *reinterpret_cast<const float4*>(xi + j4);
+            float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int q = 0; q < s.dn; ++q) {
+                const float4 p = *reinterpret_cast<const float4*>(X + diff_plus(v, s.a, q) * ds + j4);
+                const float4 m = *reinterpret_cast<const float4*>(X + diff_minus(v, s.a, q) * ds + j4);
+                sum.x += p.x - m.x; sum.y += p.y - m.y; sum.z += p.z - m.z; sum.w += p.w - m.w;
+            }
+            const uint4 w = (s.cs == 1) ? c.slot(4 + (uint32_t)(j4 >> 2)) : make_uint4(0, 0, 0, 0);
+            const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+            const float xv[4] = {x.x, x.y, x.z, x.w}, sv[4] = {sum.x, sum.y, sum.z, sum.w};
+            float uo[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int j = j4 + q;
+                float vj = av[q];
+                if (dir) vj += F * (bv[q] - av[q]);
+                vj += F * sv[q];
+                float u;
+                if (s.cs == 3) {
+                    u = xv[q] + K * (vj - xv[q]);
+                } else {
+                    bool take;
+                    if (s.cs == 1) {
+                        take = ((word_of(w, q) >> 8) < s.cri) || (j == v.jrand);
+                    } else {
+                        int off = j - v.nstart;
+                        if (off < 0) off += dim;
+                        take = off < L;
+                    }
+                    u = take ? vj : xv[q];
+                }
+                u = fminf(fmaxf(u, lo), hi);
+                if (j >= dim) u = 0.0f;
+                uo[q] = u;
+                dreg[j] = (j < dim) ? (u - o[j]) : 0.0f;
+            }
+            *reinterpret_cast<float4*>(U + i * ds + j4) = make_float4(uo[0], uo[1], uo[2], uo[3]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dreg[j4 + q] = 0.0f;
+        }
+    }
+}
+
+__host__ __device__ inline int small_stride(int dpad) { return ((dpad >> 2) & 1) ? dpad : dpad + 4; }
+
+template <int DMAX>
+__global__ void __launch_bounds__(512) k_fused_small(StepArgs a, const int* __restrict__ work, int n_work) {
+    extern __shared__ __align__(16) float sm[];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int w = blockIdx.x; w < n_work; w += gridDim.x) {
+        const int k = work[w];
+        const InstDesc d = a.desc[k];
+        const int np = d.np, dim = d.dim, dp = d.dpad, ds = small_stride(dp);
+        float* X = sm;
+        float* U = X + np * ds;
+        float* R = U + np * ds;
+        float* o = R + dim * DMAX;
+        float* f = o + DMAX;
+        float* fu = f + np;
+        int* topk = reinterpret_cast<int*>(fu + np);
+        int* red = topk + np;
+        const Strat s = load_strat(a.theta + 6 * k, np);
+        if (!s.ok) {
+            if (tid == 0) set_status(a.status, 1);
+            continue;
+        }
+        const uint32_t epoch = a.epoch_dev ? *a.epoch_dev : a.epoch;
+        float* gpop = a.pop + d.pop_off;
+        const int chunks = dp >> 2;
+        for (int e = tid; e < np * chunks; e += nt) {
+            const int i = e / chunks, q = e - i * chunks;
+            *reinterpret_cast<float4*>(X + i * ds + 4 * q) =
+                *reinterpret_cast<const float4*>(gpop + (long long)i * dp + 4 * q);
+        }
+        const float* gR = a.rot + d.rot_off;
+        for (int e = tid; e < dim * DMAX; e += nt) {
+            const int r = e / DMAX, cc = e - r * DMAX;
+            R[e] = cc < dp ? gR[(long long)r * dp + cc] : 0.0f;
+        }
+        for (int j = tid; j < DMAX; j += nt) o[j] = j < dp ? a.shift[d.shift_off + j] : 0.0f;
+        for (int i = tid; i < np; i += nt) f[i] = a.fit[d.fit_off + i];
+        __syncthreads();
+        const bool pb = s.uses_pbest();
+        for (int g = 0; g < a.n_gens; ++g) {
+            const uint32_t gen = a.gen0 + (uint32_t)g;
+            int best;
+            if (pb) {
+                block_topk(f, np, d.kp, topk);
+                __syncthreads();
+                best = topk[0];
+            } else {
+                best = block_argmin(f, np, red);
+            }
+            for (int i = tid; i < np; i += nt) {
+                const Ctr c = make_ctr(a.key, (uint32_t)d.stream, gen, (uint32_t)i, epoch);
+                Indiv v;
+                indiv_setup(s, c, i, np, dim, d.kp, pb ? topk : nullptr, best, v);
+                const int L = s.cs == 2 ? exp_length(c, dim, s.cri) : 0;
+                float dreg[DMAX];
+                thread_trial<DMAX>(s, c, v, i, dim, ds, L, X, o, a.lo, a.hi, U, dreg);
+                ObjAcc<float> acc;
+                obj_init(acc);
+                for (int r = 0; r < dim; ++r) {
+                    const float4* Rr = reinterpret_cast<const float4*>(R + r * DMAX);
+                    float z = 0.0f;
+#pragma unroll
+                    for (int c4 = 0; c4 < DMAX / 4; ++c4) {
+                        const float4 rr = Rr[c4];
+                        z = fmaf(rr.x, dreg[4 * c4 + 0], z);
+                        z = fmaf(rr.y, dreg[4 * c4 + 1], z);
+                        z = fmaf(rr.z, dreg[4 * c4 + 2], z);
+                        z = fmaf(rr.w, dreg[4 * c4 + 3], z);
+                    }
+                    obj_push(d.obj, acc, z);
+                }
+                fu[i] = nan_to_inf(obj_finish(d.obj, acc, dim));
+            }
+            __syncthreads();
+            for (int i = tid; i < np; i += nt) {
+                float fn = fu[i];
+                const float fx = f[i];
+                bool take;
+                bool same = near_tie(fn, fx);
+                if (same)
+                    for (int j = 0; j < dim; ++j) same = same && (U[i * ds + j] == X[i * ds + j]);
+                if (same) {
+                    take = true;  // the trial is the target: nothing changes
+                    fn = fx;
+                } else if (near_tie(fn, fx)) {
+                    if (a.tie_fp64) {
+                        const double eu = nan_to_inf(eval64_seq(d.obj, dim, DMAX, U + i * ds, o, R));
+                        const double ex = nan_to_inf(eval64_seq(d.obj, dim, DMAX, X + i * ds, o, R));
+                        take = eu <= ex;
+                        if (take) fn = fminf((float)eu, fx);
+                    } else {
+                        const float df = diff_seq(d.obj, dim, DMAX, U + i * ds, X + i * ds, o, R);
+                        take = df <= 0.0f;
+                        if (take) fn = fx + df;
+                    }
+                } else {
+                    take = fn <= fx;
+                }
+                if (take) {
+                    for (int q = 0; q < chunks; ++q)
+                        *reinterpret_cast<float4*>(X + i * ds + 4 * q) =
+                            *reinterpret_cast<const float4*>(U + i * ds + 4 * q);
+                    f[i] = fn;
+                }
+            }
+            __syncthreads();
+        }
+        for (int e = tid; e < np * chunks; e += nt) {
+            const int i = e / chunks, q = e - i * chunks;
+            *reinterpret_cast<float4*>(gpop + (long long)i * dp + 4 * q) =
+                *reinterpret_cast<const float4*>(X + i * ds + 4 * q);
+        }
+        for (int i = tid; i < np; i += nt) a.fit[d.fit_off + i] = f[i];
+        const int b = block_argmin(f, np, red);
+        if (tid == 0 && a.best_f) a.best_f[k] = f[b];
+        if (tid == 0 && a.best_i) a.best_i[k] = b;
+        __syncthreads();
+    }
+}
+
+int small_dmax_for(int dim) {
+    if (dim <= 4) return 4;
+    if (dim <= 8) return 8;
+    if (dim <= 12) return 12;
+    if (dim <= 16) return 16;
+    if (dim <= 20) return 20;
+    if (dim <= 24) return 24;
+    if (dim <= 32) return 32;
+    return 0;
+}
+
+size_t fused_smem_small(int dmax, int max_np) {
+    const int ds = small_stride(dmax);
+    return sizeof(float) * ((size_t)2 * max_np * ds + (size_t)dmax * dmax + dmax + 2 * (size_t)max_np) +
+           sizeof(int) * ((size_t)max_np + 64);
+}
+
+// ---------------------------------------------- batched path, general D
+// Shared layout: f[np], fu[np], topk[np], red[64], R^T [dim][dpad] (optional),
+// then per warp 4 * max_dpad floats (float trial buffers or double tie buffers).
+__global__ void __launch_bounds__(256) k_fused_general(StepArgs a, const int* __restrict__ work, int n_work,
+                                                       float* uscr, int rot_smem, int max_np, int max_dpad) {
+    extern __shared__ __align__(16) float sm[];
+    const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+    float* f = sm;
+    float* fu = f + max_np;
+    int* topk = reinterpret_cast<int*>(fu + max_np);
+    int* red = topk + max_np;
+    float* rs = sm + ((3 * max_np + 64 + 3) & ~3);
+    for (int w = blockIdx.x; w < n_work; w += gridDim.x) {
+        const int k = work[w];
+        const InstDesc d = a.desc[k];
+        const int np = d.np, dim = d.dim, dp = d.dpad;
+        float* RTs = rs;
+        float* wb = rs + (rot_smem ? (size_t)max_dpad * max_dpad : 0) + (size_t)warp * 4 * max_dpad;
+        float* db = wb;
+        float* zb = wb + max_dpad;
+        const Strat s = load_strat(a.theta + 6 * k, np);
+        if (!s.ok) {
+            if (tid == 0) set_status(a.status, 1);
+            continue;
+        }
+        const uint32_t epoch = a.epoch_dev ? *a.epoch_dev : a.epoch;
+        float* X = a.pop + d.pop_off;
+        float* Ug = uscr + d.pop_off;
+        const float* o = a.shift + d.shift_off;
+        const float* RT = a.rotT + d.rot_off;
+        if (rot_smem) {
+            for (int e = tid; e < dim * (dp >> 2); e += nt)
+                reinterpret_cast<float4*>(RTs)[e] = reinterpret_cast<const float4*>(RT)[e];
+            RT = RTs;
+        }
+        for (int i = tid; i < np; i += nt) f[i] = a.fit[d.fit_off + i];
+        __syncthreads();
+        const bool pb = s.uses_pbest();
+        for (int g = 0; g < a.n_gens; ++g) {
+            const uint32_t gen = a.gen0 + (uint32_t)g;
+            int best;
+            if (pb) {
+                block_topk(f, np, d.kp, topk);
+                __syncthreads();
+                best = topk[0];
+            } else {
+                best = block_argmin(f, np, red);
+            }
+            for (int i = warp; i < np; i += nw) {
+                const Ctr c = make_ctr(a.key, (uint32_t)d.stream, gen, (uint32_t)i, epoch);
+                Indiv v;
+                indiv_setup(s, c, i, np, dim, d.kp, pb ? topk : nullptr, best, v);
+                const int L = s.cs == 2 ? exp_length(c, dim, s.cri) : 0;
+                warp_trial(s, c, v, i, dim, L, X, dp, o, a.lo, a.hi, Ug + (long long)i * dp, db);
+                __syncwarp();
+                warp_rotate<float>(dim, RT, dp, db, zb);
+                __syncwarp();
+                const float fv = warp_objective<float>(d.obj, dim, zb);
+                if (lane == 0) fu[i] = nan_to_inf(fv);
+                __syncwarp();
+            }
+            __syncthreads();
+            for (int i = warp; i < np; i += nw) {
+                float fn = fu[i];
+                const float fx = f[i];
+                float* Xi = X + (long long)i * dp;
+                const float* Ui = Ug + (long long)i * dp;
+                bool take;
+                bool tie = near_tie(fn, fx);
+                if (tie) {
+                    bool diff = false;
+                    for (int j = lane; j < dim; j += 32) diff = diff || (Ui[j] != Xi[j]);
+                    if (!__any_sync(kFull, diff)) tie = false, fn = fx;  // trial == target
+                }
+                if (tie && a.tie_fp64) {
+                    double* dd = reinterpret_cast<double*>(wb);
+                    const double eu = nan_to_inf(warp_eval64(d.obj, dim, Ui, o, RT, dp, dd, dd + max_dpad));
+                    const double ex = nan_to_inf(warp_eval64(d.obj, dim, Xi, o, RT, dp, dd, dd + max_dpad));
+                    take = eu <= ex;
+                    if (take) fn = fminf((float)eu, fx);
+                } else if (tie) {
+                    warp_rotate_pair(dim, RT, dp, Xi, Ui, o, db, db + max_dpad);
+                    __syncwarp();
+                    const float df = warp_diff(d.obj, dim, db, db + max_dpad);
+                    __syncwarp();
+                    take = df <= 0.0f;
+                    if (take) fn = fx + df;
+                } else {
+                    take = fn <= fx;
+                }
+                if (take) {
+                    for (int j = lane * 4; j < dp; j += 128)
+                        *reinterpret_cast<float4*>(Xi + j) = *reinterpret_cast<const float4*>(Ui + j);
+                    if (lane == 0) f[i] = fn;
+                }
+            }
+            __syncthreads();
+        }
+        for (int i = tid; i < np; i += nt) a.fit[d.fit_off + i] = f[i];
+        const int b = block_argmin(f, np, red);
+        if (tid == 0 && a.best_f) a.best_f[k] = f[b];
+        if (tid == 0 && a.best_i) a.best_i[k] = b;
+        __syncthreads();
+    }
+}
+
+size_t fused_smem_general(int max_np, int max_dpad, int threads, bool rot_in_smem) {
+    size_t words = 3 * (size_t)max_np + 64;
+    words = (words + 3) & ~(size_t)3;
+    if (rot_in_smem) words += (size_t)max_dpad * max_dpad;
+    words += (size_t)(threads / 32) * 4 * max_dpad;
+    return words * sizeof(float);
+}
+
+template <int DMAX>
+static cudaError_t launch_small(const StepArgs& a, const int* work, int n_work, const FusedPlan& p, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(k_fused_small<DMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    if (e != cudaSuccess) return e;
+    k_fused_small<DMAX><<<p.grid, p.threads, p.smem, st>>>(a, work, n_work);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fused(const StepArgs& a, const int* work, int n_work, const FusedPlan& p, float* uscr,
+                         cudaStream_t st) {
+    if (n_work <= 0) return cudaSuccess;
+    if (p.kind == 0) {
+        switch (p.dmax) {
+        case 4: return launch_small<4>(a, work, n_work, p, st);
+        case 8: return launch_small<8>(a, work, n_work, p, st);
+        case 12: return launch_small<12>(a, work, n_work, p, st);
+        case 16: return launch_small<16>(a, work, n_work, p, st);
+        case 20: return launch_small<20>(a, work, n_work, p, st);
+        case 24: return launch_small<24>(a, work, n_work, p, st);
+        case 32: return launch_small<32>(a, work, n_work, p, st);
+        default: return cudaErrorInvalidValue;
+        }
+    }
+    cudaError_t e = cudaFuncSetAttribute(k_fused_general, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    if (e != cudaSuccess) return e;
+    k_fused_general<<<p.grid, p.threads, p.smem, st>>>(a, work, n_work, uscr, p.rot_smem, p.max_np, p.max_dpad);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- evolver
+__constant__ float c_lb[6] = {0.f, 0.f, 1.f, 1.f, 1.f, 1.f};
+__constant__ float c_ub[6] = {1.f, 1.f, 5.f, 5.f, 5.f, 4.f};
+
+__global__ void k_outer_init(int n_total, int n_out, Key key, float* opop, float* ofit) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_total) return;
+    const int g = e / n_out, i = e - g * n_out;
+    const uint4 w0 = philox((uint32_t)g, kInitGen, (uint32_t)i, 0u, key);
+    const uint4 w1 = philox((uint32_t)g, kInitGen, (uint32_t)i, 1u, key);
+    const uint32_t ws[6] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y};
+#pragma unroll
+    for (int j = 0; j < 6; ++j) opop[(long long)e * 6 + j] = fmaf(c_ub[j] - c_lb[j], uniform24(ws[j]), c_lb[j]);
+    ofit[e] = INFINITY;
+}
+
+// rand/1/bin with F = 0.5, CR = 0.9, then the floor decoding of Alg. 3.
+__global__ void k_outer_trial(int n_total, int n_out, Key key, const uint32_t* gen_dev, uint32_t gen_arg,
+                              const float* __restrict__ opop, float* trial, float* theta) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_total) return;
+    const uint32_t gen = gen_dev ? *gen_dev : gen_arg;
+    const int g = e / n_out, i = e - g * n_out;
+    const float* P = opop + (long long)g * n_out * 6;
+    const Ctr c = make_ctr(key, (uint32_t)g, gen, (uint32_t)i, 0u);
+    const uint4 w0 = c.slot(0), w1 = c.slot(1), w2 = c.slot(2), w3 = c.slot(3);
+    const int jrand = (int)below(w0.x, 6u);
+    uint32_t w[12] = {w1.x, w1.y, w1.z, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    int r[9];
+    distinct_draws(n_out, i, 3, w, r);
+    const uint32_t xw[6] = {w2.x, w2.y, w2.z, w2.w, w3.x, w3.y};
+    const uint32_t cri = threshold24(0.9f);
+    float u[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        const float v = P[r[0] * 6 + j] + 0.5f * (P[r[1] * 6 + j] - P[r[2] * 6 + j]);
+        const bool take = ((xw[j] >> 8) < cri) || (j == jrand);
+        float x = take ? v : P[i * 6 + j];
+        x = fminf(fmaxf(x, c_lb[j]), c_ub[j]);
+        u[j] = x;
+        trial[(long long)e * 6 + j] = x;
+    }
+    float* th = theta + (long long)e * 6;
+    th[0] = u[0];
+    th[1] = u[1];
+    const float top[4] = {4.f, 4.f, 4.f, 3.f};
+#pragma unroll
+    for (int j = 2; j < 6; ++j) th[j] = fminf(fmaxf(floorf(u[j]), 1.0f), top[j - 2]);
+}
+
+__global__ void k_outer_select(int n_total, float* opop, float* ofit, const float* __restrict__ trial,
+                               const float* __restrict__ meta_fit) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_total) return;
+    float y = meta_fit[e];
+    if (isnan(y)) y = INFINITY;
+    if (y <= ofit[e]) {
+#pragma unroll
+        for (int j = 0; j < 6; ++j) opop[(long long)e * 6 + j] = trial[(long long)e * 6 + j];
+        ofit[e] = y;
+    }
+}
+
+cudaError_t launch_outer_init(int n_groups, int n_out, Key key, float* opop, float* ofit, cudaStream_t st) {
+    const int n = n_groups * n_out;
+    k_outer_init<<<(n + 127) / 128, 128, 0, st>>>(n, n_out, key, opop, ofit);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_outer_trial(int n_groups, int n_out, Key key, const uint32_t* gen_dev, uint32_t gen,
+                               const float* opop, float* trial, float* theta, cudaStream_t st) {
+    const int n = n_groups * n_out;
+    k_outer_trial<<<(n + 127) / 128, 128, 0, st>>>(n, n_out, key, gen_dev, gen, opop, trial, theta);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_outer_select(int n_groups, int n_out, float* opop, float* ofit, const float* trial,
+                                const float* meta_fit, cudaStream_t st) {
+    const int n = n_groups * n_out;
+    k_outer_select<<<(n + 127) / 128, 128, 0, st>>>(n, opop, ofit, trial, meta_fit);
+    return cudaGetLastError();
+}
+
+}  // namespace metade

@@ -1,0 +1,407 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C-ABI.
+
+Bars: bit-exact for the initial population (one rounding of the same exact
+value), for every index/mask/integer draw and for the decoded categorical
+genes; FP32 trial coordinates within TRIAL_ATOL; FP32 fitness within 1e-5
+relative of the FP64 value at the same point; selection bits equal wherever
+the fitness gap exceeds the FP32 tolerance.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import (FIT_RTOL, TRIAL_ATOL, check_fitness_fp32, feasible_theta, make_batch, random_state,
+                      rel_err)
+
+pytestmark = pytest.mark.gpu
+
+PATHS = [0, 1]  # batched, plain
+PATH_IDS = ["batched", "plain"]
+
+
+def _wl_small():
+    wl = synth.small_ragged()
+    wl.theta = feasible_theta(wl.theta, wl.inst_np)
+    return wl
+
+
+def _wl_with_theta(wl, seed=3):
+    rng = np.random.default_rng(seed)
+    wl.theta = feasible_theta(synth.random_theta(rng, wl.n_inst), wl.inst_np)
+    return wl
+
+
+def _ragged_many():
+    """Every strategy family across ragged sizes: 48 executors, NP 4..130,
+    D 1..70 (tiles of 4/32 plus ragged tails)."""
+    rng = np.random.default_rng(21)
+    n = 48
+    dims = rng.choice([1, 2, 3, 5, 10, 13, 20, 31, 33, 47, 64, 70], size=n)
+    nps = rng.integers(4, 131, size=n)
+    probs = [synth.make_problem(rng, int(d), int(k % 6)) for k, d in enumerate(dims)]
+    th = synth.random_theta(rng, n)
+    # make sure each (bl, br) pair and crossover appears
+    for k in range(n):
+        th[k, 2] = 1 + (k % 4)
+        th[k, 3] = 1 + ((k // 4) % 4)
+        th[k, 5] = 1 + (k % 3)
+    wl = synth.Workload(name="ragged-many", problems=probs, inst_np=nps.astype(np.int32),
+                        inst_prob=np.arange(n, dtype=np.int32), inst_group=np.arange(n, dtype=np.int32),
+                        n_groups=n, n_out=0, inner_gens=2, outer_gens=1, seed=5, one_shot=0, theta=th)
+    wl.theta = feasible_theta(wl.theta, wl.inst_np)
+    return wl
+
+
+# ------------------------------------------------------------------- init
+@pytest.mark.parametrize("path", PATHS, ids=PATH_IDS)
+def test_init_bit_exact(path):
+    for wl in (synth.tiny(), _wl_small()):
+        b = make_batch(wl, path)
+        import paper_2502_10470_gb300 as M
+        M.metade_init(b.ctx, b.pop, b.fit, 0)
+        b.sync()
+        pops, fits = b.get_population()
+        for k in range(wl.n_inst):
+            p = wl.problems[int(wl.inst_prob[k])]
+            want = oracle.init_pop(int(wl.inst_np[k]), p.dim, wl.seed, oracle.stream_of(wl, k), 0, wl.lo, wl.hi)
+            np.testing.assert_array_equal(pops[k], want.astype(np.float32))
+            check_fitness_fp32(fits[k], pops[k], p)
+        b.close()
+
+
+# ------------------------------------------------------------------- eval
+@pytest.mark.parametrize("near", [False, True], ids=["box", "near-optimum"])
+def test_eval_fp32_and_fp64(near):
+    import torch
+    import paper_2502_10470_gb300 as M
+    wl = _ragged_many()
+    b = make_batch(wl, 0)
+    rng = np.random.default_rng(4)
+    pops = []
+    for k in range(wl.n_inst):
+        p = wl.problems[int(wl.inst_prob[k])]
+        if near:
+            x = (p.shift[None, :] + rng.normal(0, 1e-2, (int(wl.inst_np[k]), p.dim))).astype(np.float32)
+        else:
+            x = synth.random_population(rng, int(wl.inst_np[k]), p.dim)
+        pops.append(x)
+    b.set_population(pops)
+    f32 = torch.zeros(b.n_indiv, dtype=torch.float32, device="cuda")
+    f64 = torch.zeros(b.n_indiv, dtype=torch.float64, device="cuda")
+    M.metade_eval(b.ctx, b.pop, M.METADE_FP32, f32)
+    M.metade_eval(b.ctx, b.pop, M.METADE_FP64, f64)
+    b.sync()
+    f32, f64 = f32.cpu().numpy(), f64.cpu().numpy()
+    for k in range(wl.n_inst):
+        p = wl.problems[int(wl.inst_prob[k])]
+        want = oracle.eval_pop(p.obj, pops[k], p.shift, p.rot)
+        sl = slice(b.fit_off[k], b.fit_off[k] + int(wl.inst_np[k]))
+        check_fitness_fp32(f32[sl], pops[k], p, floor=1e-3 if near else 0.0)
+        assert rel_err(f64[sl], want, 1e-12).max() < 1e-9, (k, p.obj, p.dim)
+    b.close()
+
+
+# ---------------------------------------------------------------- records
+@pytest.mark.parametrize("gen", [0, 7, 123456])
+def test_draw_record_bit_exact(gen):
+    import torch
+    import paper_2502_10470_gb300 as M
+    wl = _ragged_many()
+    b = make_batch(wl, 0)
+    pops, fits = random_state(wl, seed=gen % 97)
+    b.set_population(pops, fits)
+    b.set_theta(wl.theta)
+    rec = torch.zeros((b.n_indiv, M.REC_FIELDS), dtype=torch.int32, device="cuda")
+    M.metade_draw_record(b.ctx, b.fit, b.theta, 3, gen, rec)
+    assert b.sync() is None
+    rec = rec.cpu().numpy()
+    for k in range(wl.n_inst):
+        p = wl.problems[int(wl.inst_prob[k])]
+        out = oracle.pde_step(pops[k], fits[k], wl.theta[k], p.obj, p.shift, p.rot, seed=wl.seed,
+                              stream=oracle.stream_of(wl, k), epoch=3, gen=gen, lo=wl.lo, hi=wl.hi)
+        sl = slice(b.fit_off[k], b.fit_off[k] + int(wl.inst_np[k]))
+        np.testing.assert_array_equal(rec[sl], out["rec"], err_msg="executor %d" % k)
+    b.close()
+
+
+# ---------------------------------------------------------------- one step
+def _step_and_compare(wl, path, fit_inf, gen=4, epoch=2):
+    import paper_2502_10470_gb300 as M
+    b = make_batch(wl, path)
+    pops, fits = random_state(wl, seed=gen, fit_inf=fit_inf)
+    b.set_population(pops, fits)
+    b.set_theta(wl.theta)
+    M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, epoch, gen, 1, b.best_f, b.best_i)
+    b.sync()
+    npops, nfits = b.get_population()
+    best_f = b.best_f.cpu().numpy()
+    n_checked = 0
+    for k in range(wl.n_inst):
+        p = wl.problems[int(wl.inst_prob[k])]
+        out = oracle.pde_step(pops[k], fits[k], wl.theta[k], p.obj, p.shift, p.rot, seed=wl.seed,
+                              stream=oracle.stream_of(wl, k), epoch=epoch, gen=gen, lo=wl.lo, hi=wl.hi)
+        gap = rel_err(out["ftrial"], fits[k].astype(np.float64))
+        decided = gap > 2 * FIT_RTOL
+        acc_or = out["accept"].astype(bool)
+        # rows the GPU replaced: fitness or row changed
+        acc_gpu = (nfits[k] != fits[k]) | np.any(npops[k] != pops[k], axis=1)
+        np.testing.assert_array_equal(acc_gpu[decided], acc_or[decided], err_msg="selection, executor %d" % k)
+        both = acc_gpu & acc_or
+        if both.any():
+            err = np.abs(npops[k][both] - out["trial"][both]).max()
+            assert err < TRIAL_ATOL, ("trial", k, err)
+            # FP32 fitness vs FP64 at the GPU's own float32 trial
+            check_fitness_fp32(nfits[k][both], npops[k][both], p)
+        kept = ~acc_gpu
+        np.testing.assert_array_equal(npops[k][kept], pops[k][kept])
+        np.testing.assert_array_equal(nfits[k][kept], fits[k][kept])
+        assert best_f[k] == nfits[k].min()
+        n_checked += int(both.sum())
+    b.close()
+    return n_checked
+
+
+@pytest.mark.parametrize("path", PATHS, ids=PATH_IDS)
+def test_one_step_all_accepted_trials(path):
+    """Stored fitness +inf: every trial is accepted, so the new population is
+    the trial matrix itself, compared coordinate by coordinate."""
+    wl = _ragged_many()
+    n = _step_and_compare(wl, path, fit_inf=True)
+    assert n == wl.individuals()
+
+
+@pytest.mark.parametrize("path", PATHS, ids=PATH_IDS)
+@pytest.mark.parametrize("gen", [0, 9])
+def test_one_step_with_selection(path, gen):
+    wl = _ragged_many()
+    _step_and_compare(wl, path, fit_inf=False, gen=gen)
+
+
+@pytest.mark.parametrize("path", PATHS, ids=PATH_IDS)
+def test_tiny_and_small_ragged_step(path):
+    _step_and_compare(_wl_with_theta(synth.tiny()), path, fit_inf=False)
+    _step_and_compare(_wl_small(), path, fit_inf=True)
+
+
+@pytest.mark.parametrize("path", PATHS, ids=PATH_IDS)
+def test_multi_generation_resynced(path):
+    """Ten fused generations compared one generation at a time: the oracle
+    restarts every generation from the GPU's state (trajectories of FP32 and
+    FP64 runs legitimately drift apart, so whole runs are compared as
+    distributions elsewhere)."""
+    import paper_2502_10470_gb300 as M
+    wl = _wl_with_theta(synth.tiny(), seed=8)
+    b = make_batch(wl, path)
+    M.metade_init(b.ctx, b.pop, b.fit, 0)
+    b.set_theta(wl.theta)
+    b.sync()
+    for g in range(10):
+        pops, fits = b.get_population()
+        M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, g, 1, b.best_f, b.best_i)
+        b.sync()
+        npops, nfits = b.get_population()
+        for k in range(wl.n_inst):
+            p = wl.problems[0]
+            out = oracle.pde_step(pops[k], fits[k], wl.theta[k], p.obj, p.shift, p.rot, seed=wl.seed,
+                                  stream=oracle.stream_of(wl, k), epoch=0, gen=g)
+            decided = rel_err(out["ftrial"], fits[k]) > 2 * FIT_RTOL
+            acc_gpu = nfits[k] != fits[k]
+            np.testing.assert_array_equal(acc_gpu[decided], out["accept"].astype(bool)[decided])
+            assert nfits[k].min() <= fits[k].min()
+    b.close()
+
+
+def test_fused_generations_equal_single_steps():
+    """n_gens = 5 in one fused launch equals five launches of one generation
+    (same kernels, same draws; the only state is the population)."""
+    import paper_2502_10470_gb300 as M
+    wl = _ragged_many()
+    outs = []
+    for split in (False, True):
+        b = make_batch(wl, 0)
+        pops, fits = random_state(wl, seed=1)
+        b.set_population(pops, fits)
+        b.set_theta(wl.theta)
+        if split:
+            for g in range(5):
+                M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 10 + g, 1, None, None)
+        else:
+            M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 10, 5, None, None)
+        b.sync()
+        outs.append(b.get_population())
+        b.close()
+    for k in range(wl.n_inst):
+        np.testing.assert_array_equal(outs[0][0][k], outs[1][0][k])
+        np.testing.assert_array_equal(outs[0][1][k], outs[1][1][k])
+
+
+# ------------------------------------------------------------------ evolver
+def test_outer_init_trial_decode_select():
+    import torch
+    import paper_2502_10470_gb300 as M
+    wl = synth.tiny()
+    wl2 = synth.Workload(name="two-runs", problems=wl.problems * 2, inst_np=np.full(16, 16, dtype=np.int32),
+                         inst_prob=np.repeat([0, 1], 8).astype(np.int32),
+                         inst_group=np.repeat([0, 1], 8).astype(np.int32), n_groups=2, n_out=8, inner_gens=2,
+                         outer_gens=2, seed=11, one_shot=1)
+    b = make_batch(wl2, 0)
+    M.metade_outer_init(b.ctx, b.opop, b.ofit)
+    b.sync()
+    opop = b.opop.cpu().numpy().reshape(2, 8, 6)
+    for g in range(2):
+        want, wfit = oracle.outer_init(8, wl2.seed, g)
+        np.testing.assert_array_equal(opop[g], want.astype(np.float32))
+        assert np.all(np.isinf(b.ofit.cpu().numpy()))
+    for og in (0, 3):
+        M.metade_outer_step(b.ctx, b.opop, b.ofit, b.trial, b.theta, None, og, 0)
+        b.sync()
+        trial = b.trial.cpu().numpy().reshape(2, 8, 6)
+        theta = b.theta.cpu().numpy().reshape(2, 8, 6)
+        for g in range(2):
+            want = oracle.outer_trial(opop[g], wl2.seed, g, og)
+            assert np.abs(trial[g] - want).max() < 2e-6
+            for i in range(8):
+                # decoding is compared on the GPU's own float32 trial (same input, same floor)
+                np.testing.assert_array_equal(theta[g, i], oracle.decode(trial[g, i]).astype(np.float32))
+    meta = torch.tensor(np.random.default_rng(0).uniform(0, 10, 16).astype(np.float32), device="cuda")
+    meta[3] = float("nan")
+    M.metade_outer_step(b.ctx, b.opop, b.ofit, b.trial, b.theta, meta, 0, 1)
+    b.sync()
+    npop, nfit = b.opop.cpu().numpy(), b.ofit.cpu().numpy()
+    m = meta.cpu().numpy()
+    for e in range(16):
+        if e == 3:  # NaN counts as +inf and still beats the initial +inf
+            assert np.isinf(nfit[e])
+        else:
+            assert nfit[e] == m[e]
+            np.testing.assert_array_equal(npop[e], b.trial.cpu().numpy()[e])
+    b.close()
+
+
+def test_outer_generation_graph_matches_direct():
+    import paper_2502_10470_gb300 as M
+    wl = synth.tiny()
+    res = []
+    for use_graph in (False, True):
+        b = make_batch(wl, 0)
+        M.metade_outer_init(b.ctx, b.opop, b.ofit)
+        for og in range(3):
+            M.metade_outer_generation(b.ctx, b.opop, b.ofit, b.trial, b.theta, b.pop, b.fit, b.best_f, b.best_i,
+                                      og, 20, use_graph)
+        b.sync()
+        res.append((b.opop.cpu().numpy(), b.ofit.cpu().numpy(), b.pop.cpu().numpy()))
+        b.close()
+    for a, c in zip(res[0], res[1]):
+        np.testing.assert_array_equal(a, c)
+
+
+# -------------------------------------------------------------- edge cases
+def test_invalid_theta_sets_sticky_status():
+    import paper_2502_10470_gb300 as M
+    wl = _wl_small()
+    b = make_batch(wl, 0)
+    th = wl.theta.copy()
+    th[2, 4] = 9  # dn outside {1..4}
+    b.set_theta(th)
+    M.metade_init(b.ctx, b.pop, b.fit, 0)
+    M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 0, 2, b.best_f, b.best_i)
+    assert M.metade_sync(b.ctx) == M.METADE_EINVAL
+    assert M.metade_sync(b.ctx) == M.METADE_OK  # cleared
+    th = wl.theta.copy()
+    th[0, 4] = 4  # NP = 4 cannot hold 2 dn + 1 distinct draws
+    b.set_theta(th)
+    M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 0, 1, None, None)
+    assert M.metade_sync(b.ctx) == M.METADE_EINVAL
+    b.close()
+
+
+def test_zero_generations_and_empty_batch():
+    import paper_2502_10470_gb300 as M
+    wl = _wl_small()
+    b = make_batch(wl, 0)
+    pops, fits = random_state(wl)
+    b.set_population(pops, fits)
+    b.set_theta(wl.theta)
+    M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 0, 0, b.best_f, b.best_i)
+    b.sync()
+    bf = b.best_f.cpu().numpy()
+    bi = b.best_i.cpu().numpy()
+    for k in range(wl.n_inst):
+        assert bf[k] == fits[k].min() and bi[k] == int(np.argmin(fits[k]))
+    b.close()
+    e = M.Batch([(3, 0, np.zeros(3, np.float32), np.eye(3, dtype=np.float32))], [], [])
+    M.metade_inner_step(e.ctx, e.pop, e.fit, e.theta, 0, 0, 3, None, None)
+    assert M.metade_sync(e.ctx) == M.METADE_OK
+    e.close()
+
+
+def test_bad_configs_rejected_on_host():
+    import paper_2502_10470_gb300 as M
+    z = np.zeros(4, np.float32)
+    eye = np.eye(2, dtype=np.float32)
+    with pytest.raises(M.MetadeError):
+        M.Batch([(2, 0, z[:2], eye)], [3], [0])           # NP < 4
+    with pytest.raises(M.MetadeError):
+        M.Batch([(2, 7, z[:2], eye)], [8], [0])           # unknown objective
+    with pytest.raises(M.MetadeError):
+        M.Batch([(2, 0, z[:2], eye)], [8], [1])           # problem index out of range
+    with pytest.raises(M.MetadeError):
+        M.Batch([(2, 0, z[:2], eye)], [8] * 6, [0] * 6, n_out=4)  # 6 executors, evolver of 4
+    with pytest.raises(M.MetadeError):
+        M.Batch([(2, 0, z[:2], eye)], [8], [0], lo=1.0, hi=-1.0)
+
+
+# ------------------------------------------------------------ near ties
+@pytest.mark.parametrize("tie_fp64", [0, 1], ids=["difference", "fp64"])
+@pytest.mark.parametrize("path", PATHS, ids=PATH_IDS)
+def test_near_tie_decisions_match_fp64(tie_fp64, path):
+    """Selection ties (|f(u) - f(x)| <= 1e-6 f(x)) are decided like FP64 does.
+    Population on a grid of 8 and F = 2^-20 make the trial x_i + F (x_r0 - x_r1)
+    exact in float32, so both implementations see the same u; the ground truth
+    is the sign of the FP64 difference f(u) - f(x) of the oracle."""
+    import torch
+    import paper_2502_10470_gb300 as M
+    rng = np.random.default_rng(31)
+    n = 24
+    dims = [2, 5, 10, 20, 33, 40] * 4
+    probs = [synth.make_problem(rng, dims[k], k % 6) for k in range(n)]
+    nps = np.full(n, 64, dtype=np.int32)
+    wl = synth.Workload(name="near-ties", problems=probs, inst_np=nps, inst_prob=np.arange(n, dtype=np.int32),
+                        inst_group=np.arange(n, dtype=np.int32), n_groups=n, n_out=0, inner_gens=1,
+                        outer_gens=1, seed=9, one_shot=0)
+    theta = np.tile(np.array([2.0 ** -20, 0.0, 4, 4, 1, 1], dtype=np.float32), (n, 1))
+    pops = [(rng.integers(-12, 13, (64, probs[k].dim)) * 8.0).astype(np.float32) for k in range(n)]
+    fits = [oracle.eval_pop(probs[k].obj, pops[k], probs[k].shift, probs[k].rot).astype(np.float32)
+            for k in range(n)]
+    b = make_batch(wl, path, tie_fp64=tie_fp64)
+    b.set_population(pops, fits)
+    b.set_theta(theta)
+    rec = torch.zeros((b.n_indiv, M.REC_FIELDS), dtype=torch.int32, device="cuda")
+    M.metade_draw_record(b.ctx, b.fit, b.theta, 0, 0, rec)
+    M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 0, 1, None, None)
+    b.sync()
+    rec = rec.cpu().numpy()
+    npops, nfits = b.get_population()
+    checked = 0
+    for k in range(n):
+        p = probs[k]
+        r = rec[b.fit_off[k]:b.fit_off[k] + 64]
+        out = oracle.pde_step(pops[k], fits[k], theta[k], p.obj, p.shift, p.rot, seed=wl.seed, stream=k,
+                              epoch=0, gen=0)
+        u = pops[k].astype(np.float64).copy()
+        for i in range(64):
+            j = r[i, 2]
+            u[i, j] += 2.0 ** -20 * (float(pops[k][r[i, 9], j]) - float(pops[k][r[i, 10], j]))
+        np.testing.assert_array_equal(u, out["trial"])           # the trial is exact on both sides
+        assert np.array_equal(u.astype(np.float32).astype(np.float64), u)
+        fu = oracle.eval_pop(p.obj, u, p.shift, p.rot)
+        fx = oracle.eval_pop(p.obj, pops[k], p.shift, p.rot)
+        delta = fu - fx
+        tie = (np.abs(delta) <= 5e-7 * np.abs(fx)) & (np.abs(delta) > 1e-10 * np.abs(fx))
+        took = np.any(npops[k] != pops[k], axis=1)
+        np.testing.assert_array_equal(took[tie], (delta <= 0)[tie], err_msg="executor %d obj %d" % (k, p.obj))
+        assert np.all(nfits[k] <= fits[k])                      # stored fitness never rises
+        checked += int(tie.sum())
+    b.close()
+    assert checked > 200
