@@ -187,6 +187,34 @@ METADE_API metade_status metade_outer_generation(metade_ctx *ctx, float *opop, f
 METADE_API metade_status metade_draw_record(metade_ctx *ctx, const float *fit, const float *theta,
                                  uint32_t epoch, uint32_t gen, int32_t *rec);
 
+/* One plain FP32 generation of a single executor (the computation of
+ * metade_inner_step on the plain path, with one executor and n_gens = 1) that
+ * allocates nothing and needs no context.  The paper has no counterpart: this
+ * exists for callers that cannot allocate device memory themselves (their
+ * device heap belongs to a host framework or allocator, or they must not grow
+ * the process's device footprint).  The caller passes every input and output:
+ *   pop [np][round_up(dim,4)] float32 (pad columns zero), fit [np] -- updated
+ *   in place; theta [6] decoded (F, CR, bl, br, dn, cs); shift [dim];
+ *   rot [dim][dim] row-major; stream_id is Philox counter word 0; p_best_pct
+ *   as in metade_config (0 -> 10); stream is a cudaStream_t (NULL = legacy).
+ * Scratch (trial rows, trial fitness, pbest pool) lives in one file-scope
+ * device array of 2^20 floats (4 MiB) that every GPU loading the library holds
+ * until the process exits; sizes with round_up(np*round_up(dim,4), 64) +
+ * round_up(np, 64) + np > 2^20 floats are rejected with METADE_EINVAL, as are
+ * np outside 4..1024, dim outside 1..1536 and bad objective ids.  The first
+ * call made on a device (with that device current) looks up the array's
+ * device address with cudaGetSymbolAddress; make that first call before any
+ * stream capture.  All calls share the array and it keeps the last call's
+ * contents (every element a call reads is written earlier in that call, so
+ * nothing is cleared); calls that overlap on the GPU race on it.  An invalid
+ * theta, or np too small for the strategy, leaves pop and fit unchanged.
+ * Asynchronous on `stream`; returns METADE_ECUDA if a launch fails. */
+METADE_API metade_status metade_plain_step_noalloc(float *pop, float *fit, const float *theta,
+                                                   const float *shift, const float *rot, int32_t np,
+                                                   int32_t dim, int32_t obj, float lo, float hi,
+                                                   uint64_t seed, uint32_t stream_id, uint32_t epoch,
+                                                   uint32_t gen, int32_t p_best_pct, void *stream);
+
 /* Wait for the context's stream; return and clear the sticky device status. */
 METADE_API metade_status metade_sync(metade_ctx *ctx);
 

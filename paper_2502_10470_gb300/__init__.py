@@ -29,7 +29,7 @@ EXPORTED = [
     "metade_create", "metade_destroy", "metade_layout", "metade_offsets", "metade_set_stream",
     "metade_init", "metade_inner_step", "metade_eval", "metade_outer_init", "metade_outer_step",
     "metade_outer_generation", "metade_draw_record", "metade_sync", "metade_plan_info",
-    "metade_launch_count", "metade_strerror",
+    "metade_launch_count", "metade_strerror", "metade_plain_step_noalloc",
 ]
 
 
@@ -92,6 +92,8 @@ def _lib():
         L.metade_plan_info.argtypes = [P, C.c_char_p, C.c_size_t]
         L.metade_launch_count.argtypes = [P]
         L.metade_launch_count.restype = C.c_int64
+        L.metade_plain_step_noalloc.argtypes = [P, P, P, P, P, I32, I32, I32, C.c_float, C.c_float, C.c_uint64,
+                                                U32, U32, U32, I32, P]
         L.metade_strerror.argtypes = [C.c_int]
         L.metade_strerror.restype = C.c_char_p
         for name in EXPORTED:
@@ -221,6 +223,14 @@ def metade_plan_info(ctx: int) -> str:
 
 def metade_launch_count(ctx: int) -> int:
     return _lib().metade_launch_count(ctx)
+
+
+def metade_plain_step_noalloc(pop, fit, theta, shift, rot, np_: int, dim: int, obj: int, lo: float, hi: float,
+                              seed: int, stream_id: int, epoch: int, gen: int, p_best_pct: int = 10,
+                              stream=None) -> int:
+    """One plain generation of one executor with no allocation; returns the status."""
+    return _lib().metade_plain_step_noalloc(_ptr(pop), _ptr(fit), _ptr(theta), _ptr(shift), _ptr(rot), np_, dim,
+                                            obj, lo, hi, seed, stream_id, epoch, gen, p_best_pct, stream)
 
 
 def metade_strerror(status: int) -> str:
