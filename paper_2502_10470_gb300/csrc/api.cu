@@ -133,7 +133,7 @@ metade_status build_plan(metade_ctx* c) {
         Bucket b;
         b.plan.kind = 0;
         b.plan.dmax = dm;
-        b.plan.threads = std::min(512, std::max(64, (mnp + 31) / 32 * 32));
+        b.plan.threads = std::min(256, std::max(32, (mnp + 31) / 32 * 32));
         b.plan.grid = (int)small[dm].size();
         b.plan.smem = fused_smem_small(dm, mnp);
         b.plan.rot_smem = 0;

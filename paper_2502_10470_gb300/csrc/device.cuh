@@ -171,13 +171,13 @@ __device__ __forceinline__ void distinct_draws(int np, int i, int m, const uint3
 __device__ __forceinline__ void indiv_setup(const Strat& s, const Ctr& c, int i, int np, int dim, int kp,
                                             const int* topk, int best, Indiv& d) {
     const uint4 w0 = c.slot(0);
+    const uint4 a = c.slot(1);  // m >= 2 always; independent of slot 0, so the two chains interleave
     d.jrand = (int)below(w0.x, (uint32_t)dim);
     d.nstart = (int)below(w0.y, (uint32_t)dim);
     d.kraw = w0.z >> 8;
     d.pbest = topk ? topk[below(w0.w, (uint32_t)kp)] : -1;
     uint32_t w[12];
-    uint4 a = make_uint4(0, 0, 0, 0), b = a, e = a;
-    if (s.m > 0) a = c.slot(1);
+    uint4 b = make_uint4(0, 0, 0, 0), e = b;
     if (s.m > 4) b = c.slot(2);
     if (s.m > 8) e = c.slot(3);
     w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
@@ -303,6 +303,102 @@ __device__ __forceinline__ T obj_finish(int obj, const ObjAcc<T>& a, int dim) {
     default: return a.s0;
     }
 }
+
+// Compile-time objective, FP32, streaming over z_0, z_1, ...  Griewank uses
+// the telescoping form 1 - prod c_j = sum_j (1 - c_j) prod_{k<j} c_k with
+// 1 - c_j = 2 sin^2(a_j / 2): one transcendental per coordinate and no
+// cancellation near the optimum.
+template <int OBJ>
+struct ObjF {
+    float s0 = 0.f, s1 = 0.f, prev = 0.f, pre = 1.f;
+    bool first = true;
+    __device__ __forceinline__ void push(float z, float inv_sqrt_j) {
+        if constexpr (OBJ == kSphere) {
+            s0 = fmaf(z, z, s0);
+        } else if constexpr (OBJ == kRosenbrock) {
+            if (!first) {
+                const float t = z - prev * (prev + 2.f);
+                s0 += 100.f * t * t + prev * prev;
+            }
+            prev = z;
+            first = false;
+        } else if constexpr (OBJ == kRastrigin) {
+            const float sp = sinpif(z);
+            s0 += z * z + 20.f * sp * sp;
+        } else if constexpr (OBJ == kGriewank) {
+            s0 = fmaf(z, z, s0);
+            const float h = sinf(0.5f * z * inv_sqrt_j);
+            const float w = 2.f * h * h;
+            s1 = fmaf(pre, w, s1);
+            pre *= 1.f - w;
+        } else if constexpr (OBJ == kAckley) {
+            s0 = fmaf(z, z, s0);
+            const float sp = sinpif(z);
+            s1 = fmaf(sp, sp, s1);
+        } else {
+            prev += z;
+            s0 = fmaf(prev, prev, s0);
+        }
+    }
+    __device__ __forceinline__ float finish(int dim) const {
+        if constexpr (OBJ == kGriewank) {
+            return s0 * (1.f / 4000.f) + s1;
+        } else if constexpr (OBJ == kAckley) {
+            return -20.f * expm1f(-0.2f * sqrtf(s0 / dim)) - 2.71828182845904523536f * expm1f(-2.f * s1 / dim);
+        } else {
+            return s0;
+        }
+    }
+};
+
+// The same FP32 objective with the objective chosen at run time (one code
+// path for all objectives keeps the fused kernel's instruction footprint small).
+struct ObjR {
+    float s0 = 0.f, s1 = 0.f, prev = 0.f, pre = 1.f;
+    bool first = true;
+    __device__ __forceinline__ void push(int obj, float z, float inv_sqrt_j) {
+        switch (obj) {
+        case kSphere: s0 = fmaf(z, z, s0); break;
+        case kRosenbrock:
+            if (!first) {
+                const float t = z - prev * (prev + 2.f);
+                s0 += 100.f * t * t + prev * prev;
+            }
+            prev = z;
+            first = false;
+            break;
+        case kRastrigin: {
+            const float sp = sinpif(z);
+            s0 += z * z + 20.f * sp * sp;
+            break;
+        }
+        case kGriewank: {
+            s0 = fmaf(z, z, s0);
+            const float h = sinf(0.5f * z * inv_sqrt_j);
+            const float w = 2.f * h * h;
+            s1 = fmaf(pre, w, s1);
+            pre *= 1.f - w;
+            break;
+        }
+        case kAckley: {
+            s0 = fmaf(z, z, s0);
+            const float sp = sinpif(z);
+            s1 = fmaf(sp, sp, s1);
+            break;
+        }
+        default:
+            prev += z;
+            s0 = fmaf(prev, prev, s0);
+            break;
+        }
+    }
+    __device__ __forceinline__ float finish(int obj, int dim) const {
+        if (obj == kGriewank) return s0 * (1.f / 4000.f) + s1;
+        if (obj == kAckley)
+            return -20.f * expm1f(-0.2f * sqrtf(s0 / dim)) - 2.71828182845904523536f * expm1f(-2.f * s1 / dim);
+        return s0;
+    }
+};
 
 __device__ __forceinline__ float nan_to_inf(float f) { return isnan(f) ? INFINITY : f; }
 __device__ __forceinline__ double nan_to_inf(double f) { return isnan(f) ? (double)INFINITY : f; }

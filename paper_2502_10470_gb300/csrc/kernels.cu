@@ -366,122 +366,155 @@ __device__ __forceinline__ void thread_trial(const Strat& s, const Ctr& c, const
 
 __host__ __device__ inline int small_stride(int dpad) { return ((dpad >> 2) & 1) ? dpad : dpad + 4; }
 
+// One executor, all fused generations, everything resident in shared memory;
+// the objective is a template parameter so the hot loop has no objective branch.
 template <int DMAX>
-__global__ void __launch_bounds__(512) k_fused_small(StepArgs a, const int* __restrict__ work, int n_work) {
-    extern __shared__ __align__(16) float sm[];
+__device__ __forceinline__ void small_executor(const StepArgs& a, int k, const InstDesc& d, const Strat& s,
+                                               float* sm) {
     const int tid = threadIdx.x, nt = blockDim.x;
+    const int np = d.np, dim = d.dim, dp = d.dpad, ds = small_stride(dp);
+    float* X = sm;
+    float* U = X + np * ds;
+    float* R = U + np * ds;
+    float* o = R + dim * DMAX;
+    float* isq = o + DMAX;
+    float* f = isq + DMAX;
+    float* fu = f + np;
+    int* topk = reinterpret_cast<int*>(fu + np);
+    int* red = topk + np;
+    const uint32_t epoch = a.epoch_dev ? *a.epoch_dev : a.epoch;
+    float* gpop = a.pop + d.pop_off;
+    const int chunks = dp >> 2;
+    for (int e = tid; e < np * chunks; e += nt) {
+        const int i = e / chunks, q = e - i * chunks;
+        *reinterpret_cast<float4*>(X + i * ds + 4 * q) =
+            *reinterpret_cast<const float4*>(gpop + (long long)i * dp + 4 * q);
+    }
+    const float* gR = a.rot + d.rot_off;
+    for (int e = tid; e < dim * DMAX; e += nt) {
+        const int r = e / DMAX, cc = e - r * DMAX;
+        R[e] = cc < dp ? gR[(long long)r * dp + cc] : 0.0f;
+    }
+    for (int j = tid; j < DMAX; j += nt) {
+        o[j] = j < dp ? a.shift[d.shift_off + j] : 0.0f;
+        isq[j] = 1.0f / sqrtf((float)(j + 1));
+    }
+    for (int i = tid; i < np; i += nt) f[i] = a.fit[d.fit_off + i];
+    __syncthreads();
+    const bool pb = s.uses_pbest();
+    for (int g = 0; g < a.n_gens; ++g) {
+        const uint32_t gen = a.gen0 + (uint32_t)g;
+        int best;
+        if (pb) {
+            block_topk(f, np, d.kp, topk);
+            __syncthreads();
+            best = topk[0];
+        } else {
+            best = block_argmin(f, np, red);
+        }
+        for (int i = tid; i < np; i += nt) {
+            const Ctr c = make_ctr(a.key, (uint32_t)d.stream, gen, (uint32_t)i, epoch);
+            Indiv v;
+            indiv_setup(s, c, i, np, dim, d.kp, pb ? topk : nullptr, best, v);
+            const int L = s.cs == 2 ? exp_length(c, dim, s.cri) : 0;
+            float dreg[DMAX];
+            thread_trial<DMAX>(s, c, v, i, dim, ds, L, X, o, a.lo, a.hi, U, dreg);
+            const int obj = d.obj;
+            ObjR acc;
+            int r = 0;
+            for (; r + 4 <= dim; r += 4) {
+                const float4* R0 = reinterpret_cast<const float4*>(R + (r + 0) * DMAX);
+                const float4* R1 = reinterpret_cast<const float4*>(R + (r + 1) * DMAX);
+                const float4* R2 = reinterpret_cast<const float4*>(R + (r + 2) * DMAX);
+                const float4* R3 = reinterpret_cast<const float4*>(R + (r + 3) * DMAX);
+                float z0 = 0.f, z1 = 0.f, z2 = 0.f, z3 = 0.f;
+#pragma unroll
+                for (int c4 = 0; c4 < DMAX / 4; ++c4) {
+                    const float d0 = dreg[4 * c4], d1 = dreg[4 * c4 + 1], d2 = dreg[4 * c4 + 2], d3 = dreg[4 * c4 + 3];
+                    const float4 q0 = R0[c4], q1 = R1[c4], q2 = R2[c4], q3 = R3[c4];
+                    z0 = fmaf(q0.x, d0, z0); z0 = fmaf(q0.y, d1, z0); z0 = fmaf(q0.z, d2, z0); z0 = fmaf(q0.w, d3, z0);
+                    z1 = fmaf(q1.x, d0, z1); z1 = fmaf(q1.y, d1, z1); z1 = fmaf(q1.z, d2, z1); z1 = fmaf(q1.w, d3, z1);
+                    z2 = fmaf(q2.x, d0, z2); z2 = fmaf(q2.y, d1, z2); z2 = fmaf(q2.z, d2, z2); z2 = fmaf(q2.w, d3, z2);
+                    z3 = fmaf(q3.x, d0, z3); z3 = fmaf(q3.y, d1, z3); z3 = fmaf(q3.z, d2, z3); z3 = fmaf(q3.w, d3, z3);
+                }
+                acc.push(obj, z0, isq[r]);
+                acc.push(obj, z1, isq[r + 1]);
+                acc.push(obj, z2, isq[r + 2]);
+                acc.push(obj, z3, isq[r + 3]);
+            }
+            for (; r < dim; ++r) {
+                const float4* Rr = reinterpret_cast<const float4*>(R + r * DMAX);
+                float z = 0.0f;
+#pragma unroll
+                for (int c4 = 0; c4 < DMAX / 4; ++c4) {
+                    const float4 rr = Rr[c4];
+                    z = fmaf(rr.x, dreg[4 * c4 + 0], z);
+                    z = fmaf(rr.y, dreg[4 * c4 + 1], z);
+                    z = fmaf(rr.z, dreg[4 * c4 + 2], z);
+                    z = fmaf(rr.w, dreg[4 * c4 + 3], z);
+                }
+                acc.push(obj, z, isq[r]);
+            }
+            fu[i] = nan_to_inf(acc.finish(obj, dim));
+        }
+        __syncthreads();
+        for (int i = tid; i < np; i += nt) {
+            float fn = fu[i];
+            const float fx = f[i];
+            bool take;
+            bool same = near_tie(fn, fx);
+            if (same)
+                for (int j = 0; j < dim; ++j) same = same && (U[i * ds + j] == X[i * ds + j]);
+            if (same) {
+                take = true;  // the trial is the target: nothing changes
+                fn = fx;
+            } else if (near_tie(fn, fx)) {
+                if (a.tie_fp64) {
+                    const double eu = nan_to_inf(eval64_seq(d.obj, dim, DMAX, U + i * ds, o, R));
+                    const double ex = nan_to_inf(eval64_seq(d.obj, dim, DMAX, X + i * ds, o, R));
+                    take = eu <= ex;
+                    if (take) fn = fminf((float)eu, fx);
+                } else {
+                    const float df = diff_seq(d.obj, dim, DMAX, U + i * ds, X + i * ds, o, R);
+                    take = df <= 0.0f;
+                    if (take) fn = fx + df;
+                }
+            } else {
+                take = fn <= fx;
+            }
+            if (take) {
+                for (int q = 0; q < chunks; ++q)
+                    *reinterpret_cast<float4*>(X + i * ds + 4 * q) =
+                        *reinterpret_cast<const float4*>(U + i * ds + 4 * q);
+                f[i] = fn;
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < np * chunks; e += nt) {
+        const int i = e / chunks, q = e - i * chunks;
+        *reinterpret_cast<float4*>(gpop + (long long)i * dp + 4 * q) =
+            *reinterpret_cast<const float4*>(X + i * ds + 4 * q);
+    }
+    for (int i = tid; i < np; i += nt) a.fit[d.fit_off + i] = f[i];
+    const int b = block_argmin(f, np, red);
+    if (tid == 0 && a.best_f) a.best_f[k] = f[b];
+    if (tid == 0 && a.best_i) a.best_i[k] = b;
+    __syncthreads();
+}
+
+template <int DMAX>
+__global__ void __launch_bounds__(256, 2) k_fused_small(StepArgs a, const int* __restrict__ work, int n_work) {
+    extern __shared__ __align__(16) float sm[];
     for (int w = blockIdx.x; w < n_work; w += gridDim.x) {
         const int k = work[w];
         const InstDesc d = a.desc[k];
-        const int np = d.np, dim = d.dim, dp = d.dpad, ds = small_stride(dp);
-        float* X = sm;
-        float* U = X + np * ds;
-        float* R = U + np * ds;
-        float* o = R + dim * DMAX;
-        float* f = o + DMAX;
-        float* fu = f + np;
-        int* topk = reinterpret_cast<int*>(fu + np);
-        int* red = topk + np;
-        const Strat s = load_strat(a.theta + 6 * k, np);
+        const Strat s = load_strat(a.theta + 6 * k, d.np);
         if (!s.ok) {
-            if (tid == 0) set_status(a.status, 1);
+            if (threadIdx.x == 0) set_status(a.status, 1);
             continue;
         }
-        const uint32_t epoch = a.epoch_dev ? *a.epoch_dev : a.epoch;
-        float* gpop = a.pop + d.pop_off;
-        const int chunks = dp >> 2;
-        for (int e = tid; e < np * chunks; e += nt) {
-            const int i = e / chunks, q = e - i * chunks;
-            *reinterpret_cast<float4*>(X + i * ds + 4 * q) =
-                *reinterpret_cast<const float4*>(gpop + (long long)i * dp + 4 * q);
-        }
-        const float* gR = a.rot + d.rot_off;
-        for (int e = tid; e < dim * DMAX; e += nt) {
-            const int r = e / DMAX, cc = e - r * DMAX;
-            R[e] = cc < dp ? gR[(long long)r * dp + cc] : 0.0f;
-        }
-        for (int j = tid; j < DMAX; j += nt) o[j] = j < dp ? a.shift[d.shift_off + j] : 0.0f;
-        for (int i = tid; i < np; i += nt) f[i] = a.fit[d.fit_off + i];
-        __syncthreads();
-        const bool pb = s.uses_pbest();
-        for (int g = 0; g < a.n_gens; ++g) {
-            const uint32_t gen = a.gen0 + (uint32_t)g;
-            int best;
-            if (pb) {
-                block_topk(f, np, d.kp, topk);
-                __syncthreads();
-                best = topk[0];
-            } else {
-                best = block_argmin(f, np, red);
-            }
-            for (int i = tid; i < np; i += nt) {
-                const Ctr c = make_ctr(a.key, (uint32_t)d.stream, gen, (uint32_t)i, epoch);
-                Indiv v;
-                indiv_setup(s, c, i, np, dim, d.kp, pb ? topk : nullptr, best, v);
-                const int L = s.cs == 2 ? exp_length(c, dim, s.cri) : 0;
-                float dreg[DMAX];
-                thread_trial<DMAX>(s, c, v, i, dim, ds, L, X, o, a.lo, a.hi, U, dreg);
-                ObjAcc<float> acc;
-                obj_init(acc);
-                for (int r = 0; r < dim; ++r) {
-                    const float4* Rr = reinterpret_cast<const float4*>(R + r * DMAX);
-                    float z = 0.0f;
-#pragma unroll
-                    for (int c4 = 0; c4 < DMAX / 4; ++c4) {
-                        const float4 rr = Rr[c4];
-                        z = fmaf(rr.x, dreg[4 * c4 + 0], z);
-                        z = fmaf(rr.y, dreg[4 * c4 + 1], z);
-                        z = fmaf(rr.z, dreg[4 * c4 + 2], z);
-                        z = fmaf(rr.w, dreg[4 * c4 + 3], z);
-                    }
-                    obj_push(d.obj, acc, z);
-                }
-                fu[i] = nan_to_inf(obj_finish(d.obj, acc, dim));
-            }
-            __syncthreads();
-            for (int i = tid; i < np; i += nt) {
-                float fn = fu[i];
-                const float fx = f[i];
-                bool take;
-                bool same = near_tie(fn, fx);
-                if (same)
-                    for (int j = 0; j < dim; ++j) same = same && (U[i * ds + j] == X[i * ds + j]);
-                if (same) {
-                    take = true;  // the trial is the target: nothing changes
-                    fn = fx;
-                } else if (near_tie(fn, fx)) {
-                    if (a.tie_fp64) {
-                        const double eu = nan_to_inf(eval64_seq(d.obj, dim, DMAX, U + i * ds, o, R));
-                        const double ex = nan_to_inf(eval64_seq(d.obj, dim, DMAX, X + i * ds, o, R));
-                        take = eu <= ex;
-                        if (take) fn = fminf((float)eu, fx);
-                    } else {
-                        const float df = diff_seq(d.obj, dim, DMAX, U + i * ds, X + i * ds, o, R);
-                        take = df <= 0.0f;
-                        if (take) fn = fx + df;
-                    }
-                } else {
-                    take = fn <= fx;
-                }
-                if (take) {
-                    for (int q = 0; q < chunks; ++q)
-                        *reinterpret_cast<float4*>(X + i * ds + 4 * q) =
-                            *reinterpret_cast<const float4*>(U + i * ds + 4 * q);
-                    f[i] = fn;
-                }
-            }
-            __syncthreads();
-        }
-        for (int e = tid; e < np * chunks; e += nt) {
-            const int i = e / chunks, q = e - i * chunks;
-            *reinterpret_cast<float4*>(gpop + (long long)i * dp + 4 * q) =
-                *reinterpret_cast<const float4*>(X + i * ds + 4 * q);
-        }
-        for (int i = tid; i < np; i += nt) a.fit[d.fit_off + i] = f[i];
-        const int b = block_argmin(f, np, red);
-        if (tid == 0 && a.best_f) a.best_f[k] = f[b];
-        if (tid == 0 && a.best_i) a.best_i[k] = b;
-        __syncthreads();
+        small_executor<DMAX>(a, k, d, s, sm);
     }
 }
 
@@ -498,7 +531,7 @@ int small_dmax_for(int dim) {
 
 size_t fused_smem_small(int dmax, int max_np) {
     const int ds = small_stride(dmax);
-    return sizeof(float) * ((size_t)2 * max_np * ds + (size_t)dmax * dmax + dmax + 2 * (size_t)max_np) +
+    return sizeof(float) * ((size_t)2 * max_np * ds + (size_t)dmax * dmax + 2 * dmax + 2 * (size_t)max_np) +
            sizeof(int) * ((size_t)max_np + 64);
 }
 
