@@ -251,8 +251,7 @@ __device__ __forceinline__ float warp_diff(int obj, int dim, const float* z, con
         }
         return warp_sum(s);
     }
-    float d0 = 0.f, d1 = 0.f, x0 = 0.f, x1 = 0.f, lr = 0.f, px = 1.f, pu = 1.f;
-    bool ok = true;
+    float d0 = 0.f, d1 = 0.f, x0 = 0.f, x1 = 0.f, lr = 0.f, px = 1.f;
     for (int j = lane; j < dim; j += 32) {
         const float zj = z[j], dj = dz[j];
         switch (obj) {
@@ -266,16 +265,15 @@ __device__ __forceinline__ float warp_diff(int obj, int dim, const float* z, con
             break;
         case kRastrigin: d0 += dj * (2.f * zj + dj) + 20.f * sinpif(2.f * zj + dj) * sinpif(dj); break;
         case kGriewank: {
+            // per lane: (A, B) with A = prod c, B = prod c' - prod c over its
+            // coordinates; combined across lanes in index order below
             d0 += dj * (2.f * zj + dj);
             const float inv = rsqrtf((float)(j + 1));
             const float ang = zj * inv, da = dj * inv;
-            const float ca = cosf(ang), cu = cosf(ang + da);
-            px *= ca;
-            pu *= cu;
-            const float h = sinf(0.5f * da);
-            const float rm1 = -2.f * h * h - tanf(ang) * sinf(da);
-            ok = ok && (ca != 0.f) && (rm1 > -1.f);
-            lr += log1pf(rm1);
+            float c;
+            const float dc = cos_step(ang, 0.5f * da, c);
+            lr = (c + dc) * lr + dc * px;
+            px *= c;
             break;
         }
         case kAckley: {
@@ -290,11 +288,20 @@ __device__ __forceinline__ float warp_diff(int obj, int dim, const float* z, con
     }
     d0 = warp_sum(d0);
     if (obj == kGriewank) {
-        lr = warp_sum(lr);
-        px = warp_prod(px);
-        pu = warp_prod(pu);
-        ok = __all_sync(kFull, ok);
-        return d0 / 4000.f - (ok ? px * expm1f(lr) : (pu - px));
+        // Each lane holds, for its coordinates j = lane, lane+32, ... (in
+        // increasing order), the product A = prod c and B = prod c' - prod c.
+        // Segments compose as (A1, B1) then (A2, B2): A = A1 A2,
+        // B = (A1 + B1) B2 + B1 A2.  The lanes' coordinate sets interleave,
+        // but a product does not depend on the order of its factors, so the
+        // lane values compose in any order.
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float A2 = __shfl_xor_sync(kFull, px, o), B2 = __shfl_xor_sync(kFull, lr, o);
+            const float A1 = px, B1 = lr;
+            px = A1 * A2;
+            lr = (A1 + B1) * B2 + B1 * A2;
+        }
+        return d0 / 4000.f - lr;
     }
     if (obj == kAckley) {
         d1 = warp_sum(d1);

@@ -418,6 +418,24 @@ __device__ __forceinline__ double eval64_seq(int obj, int dim, int dpad, const f
     return obj_finish(obj, a, dim);
 }
 
+// cos(a + 2h) - cos(a) = -2 sin(a + h) sin(h), with sin(a + h) expanded as
+// sin a cos h + cos a sin h so that one sincosf(a) serves both terms; sin h
+// and cos h come from their Taylor series when |h| <= 1/16 (relative error
+// below 1e-9) and from sincosf otherwise.  Writes cos(a) to c.
+__device__ __forceinline__ float cos_step(float a, float h, float& c) {
+    float sa, ca, sh, ch;
+    sincosf(a, &sa, &ca);
+    if (fabsf(h) <= 0.0625f) {
+        const float h2 = h * h;
+        sh = h * (1.f - h2 * (1.f / 6.f) * (1.f - h2 * (1.f / 20.f)));
+        ch = 1.f - 0.5f * h2 * (1.f - h2 * (1.f / 12.f));
+    } else {
+        sincosf(h, &sh, &ch);
+    }
+    c = ca;
+    return -2.f * (sa * ch + ca * sh) * sh;
+}
+
 // ----------------------------------------------------- tie differences
 // Selection ties are decided on D = f(u) - f(x) evaluated directly as a
 // difference, from z = R (x - o) and dz = R (u - x), so that its rounding
@@ -426,16 +444,15 @@ __device__ __forceinline__ double eval64_seq(int obj, int dim, int dpad, const f
 //   sin^2 terms      sin^2(pi(z+dz)) - sin^2(pi z) = sin(pi(2z+dz)) sin(pi dz)
 //   Rosenbrock t     t' - t = dz_{j+1} - dz_j (2 z_j + 2 + dz_j)
 //   Schwefel prefix  p' - p = running sum of dz
-//   Griewank product P' - P = P expm1(sum log1p(cos(a+da)/cos(a) - 1)),
-//                    cos(a+da)/cos(a) - 1 = -2 sin^2(da/2) - tan(a) sin(da)
+//   Griewank product P' - P by D_n = c'_n D_{n-1} + (c'_n - c_n) P_{n-1},
+//                    c' - c = -2 sin(a + da/2) sin(da/2)
 //   Ackley           r' - r = (r'^2 - r^2) / (r' + r);  e^{-c r} - e^{-c r'} =
 //                    -e^{-c r} expm1(-c (r' - r)), likewise for the cosine mean.
 struct DiffAcc {
     float d0, d1, x0, x1;  // difference sums, x-side sums
     float pz, pdz;         // previous z, dz (Rosenbrock)
     float p, dp;           // prefix of z, dz (Schwefel 1.2)
-    float lr, px, pu;      // Griewank: sum log ratio, direct products
-    bool ok;               // Griewank: every ratio positive
+    float lr, px;          // Griewank: product difference D_n, product P_n
     int n;
 };
 
@@ -443,8 +460,7 @@ __device__ __forceinline__ void diff_init(DiffAcc& a) {
     a.d0 = a.d1 = a.x0 = a.x1 = 0.f;
     a.pz = a.pdz = a.p = a.dp = 0.f;
     a.lr = 0.f;
-    a.px = a.pu = 1.f;
-    a.ok = true;
+    a.px = 1.f;
     a.n = 0;
 }
 
@@ -464,16 +480,15 @@ __device__ __forceinline__ void diff_push(int obj, DiffAcc& a, float z, float dz
         a.d0 += dz * (2.f * z + dz) + 20.f * sinpif(2.f * z + dz) * sinpif(dz);
         break;
     case kGriewank: {
+        // product difference by the telescoping recurrence
+        //   D_n = c'_n D_{n-1} + (c'_n - c_n) P_{n-1},  P_n = P_{n-1} c_n,
+        //   c' - c = cos(a + da) - cos(a) = -2 sin(a + da/2) sin(da/2)
         a.d0 += dz * (2.f * z + dz);
         const float inv = rsqrtf((float)(a.n + 1));
         const float ang = z * inv, da = dz * inv;
-        const float ca = cosf(ang), cu = cosf(ang + da);
-        a.px *= ca;
-        a.pu *= cu;
-        const float h = sinf(0.5f * da);
-        const float rm1 = -2.f * h * h - tanf(ang) * sinf(da);
-        a.ok = a.ok && (ca != 0.f) && (rm1 > -1.f);
-        a.lr += log1pf(rm1);
+        const float dc = cos_step(ang, 0.5f * da, a.pz);  // pz receives cos(ang)
+        a.lr = (a.pz + dc) * a.lr + dc * a.px;            // lr holds D_n, px holds P_n
+        a.px *= a.pz;
         break;
     }
     case kAckley: {
@@ -495,10 +510,7 @@ __device__ __forceinline__ void diff_push(int obj, DiffAcc& a, float z, float dz
 
 __device__ __forceinline__ float diff_finish(int obj, const DiffAcc& a, int dim) {
     switch (obj) {
-    case kGriewank: {
-        const float dP = a.ok ? a.px * expm1f(a.lr) : (a.pu - a.px);
-        return a.d0 / 4000.f - dP;
-    }
+    case kGriewank: return a.d0 / 4000.f - a.lr;
     case kAckley: {
         const float rx = sqrtf(a.x0 / dim), ru = sqrtf(fmaxf(a.x0 + a.d0, 0.f) / dim);
         const float dr = (ru + rx > 0.f) ? (a.d0 / dim) / (ru + rx) : 0.f;

@@ -364,6 +364,40 @@ __device__ __forceinline__ void thread_trial(const Strat& s, const Ctr& c, const
     }
 }
 
+// f(u) - f(x) for one individual by its own thread (selection ties): x - o
+// and u - x are formed once in registers, then both rotations share R loads.
+template <int DMAX>
+__device__ __forceinline__ float diff_small(int obj, int dim, const float* u, const float* x, const float* o,
+                                            const float* R) {
+    float dx[DMAX], dl[DMAX];
+#pragma unroll
+    for (int c = 0; c < DMAX; ++c) {
+        const bool in = c < dim;
+        dx[c] = in ? x[c] - o[c] : 0.f;
+        dl[c] = in ? u[c] - x[c] : 0.f;
+    }
+    DiffAcc acc;
+    diff_init(acc);
+    for (int r = 0; r < dim; ++r) {
+        const float4* Rr = reinterpret_cast<const float4*>(R + r * DMAX);
+        float z = 0.f, dz = 0.f;
+#pragma unroll
+        for (int c4 = 0; c4 < DMAX / 4; ++c4) {
+            const float4 q = Rr[c4];
+            z = fmaf(q.x, dx[4 * c4], z);
+            z = fmaf(q.y, dx[4 * c4 + 1], z);
+            z = fmaf(q.z, dx[4 * c4 + 2], z);
+            z = fmaf(q.w, dx[4 * c4 + 3], z);
+            dz = fmaf(q.x, dl[4 * c4], dz);
+            dz = fmaf(q.y, dl[4 * c4 + 1], dz);
+            dz = fmaf(q.z, dl[4 * c4 + 2], dz);
+            dz = fmaf(q.w, dl[4 * c4 + 3], dz);
+        }
+        diff_push(obj, acc, z, dz);
+    }
+    return diff_finish(obj, acc, dim);
+}
+
 __host__ __device__ inline int small_stride(int dpad) { return ((dpad >> 2) & 1) ? dpad : dpad + 4; }
 
 // One executor, all fused generations, everything resident in shared memory;
@@ -475,7 +509,7 @@ __device__ __forceinline__ void small_executor(const StepArgs& a, int k, const I
                     take = eu <= ex;
                     if (take) fn = fminf((float)eu, fx);
                 } else {
-                    const float df = diff_seq(d.obj, dim, DMAX, U + i * ds, X + i * ds, o, R);
+                    const float df = diff_small<DMAX>(d.obj, dim, U + i * ds, X + i * ds, o, R);
                     take = df <= 0.0f;
                     if (take) fn = fx + df;
                 }
