@@ -16,6 +16,7 @@ using namespace metade;
 namespace {
 
 constexpr int kMaxDim = 1536;
+constexpr int kTcMinDim = 256;  // reduced-precision executors at least this wide use the tensor cores
 constexpr int kMaxNp = 1024;
 constexpr size_t kSmemLimit = 227 * 1024;
 
@@ -64,6 +65,16 @@ struct metade_ctx {
     std::vector<Bucket> buckets;
     std::vector<GraphEntry> graphs;
     int64_t launches = 0;
+    // large-D executors on the tensor cores (prec BF16 / BF16X3)
+    bool tc = false;
+    TcPlan tcp;
+    std::vector<char> is_tc;
+    int* tc_execs = nullptr;
+    int* tc_row_exec = nullptr;
+    int* tc_tiles = nullptr;
+    long long* tc_brow = nullptr;
+    int* tc_topk = nullptr;
+    __nv_bfloat16 *aq = nullptr, *aq_lo = nullptr, *bq = nullptr, *bq_lo = nullptr;
 };
 
 namespace {
@@ -115,6 +126,7 @@ metade_status build_plan(metade_ctx* c) {
     std::vector<std::vector<int>> small(33);
     std::vector<int> general;
     for (int k = 0; k < c->n_inst; ++k) {
+        if (c->tc && c->is_tc[k]) continue;
         const InstDesc& d = c->hdesc[k];
         const int dm = small_dmax_for(d.dim);
         if (dm > 0 && fused_smem_small(dm, d.np) <= kSmemLimit) small[dm].push_back(k);
@@ -196,6 +208,17 @@ metade_status run_inner(metade_ctx* c, cudaStream_t st, float* pop, float* fit, 
         CK(launch_fused(a, c->work + b.work_off, b.n_work, b.plan, c->uscr, st));
         *launches += 1;
     }
+    if (c->tc) {
+        for (int g = 0; g < n_gens; ++g) {
+            StepArgs t = step_args(c, pop, fit, theta, epoch, epoch_dev, gen0 + (uint32_t)g, 1, nullptr, nullptr);
+            CK(launch_tc_generation(t, c->tcp, st));
+            *launches += 4;
+        }
+        if (best_f || best_i) {
+            CK(launch_best(c->desc, c->n_inst, fit, best_f, best_i, st));
+            *launches += 1;
+        }
+    }
     return METADE_OK;
 }
 
@@ -260,6 +283,15 @@ void metade_destroy(metade_ctx* c) {
     cudaFree(c->status);
     cudaFree(c->gen_dev);
     cudaFree(c->work);
+    cudaFree(c->tc_execs);
+    cudaFree(c->tc_row_exec);
+    cudaFree(c->tc_tiles);
+    cudaFree(c->tc_brow);
+    cudaFree(c->tc_topk);
+    cudaFree(c->aq);
+    cudaFree(c->aq_lo);
+    cudaFree(c->bq);
+    cudaFree(c->bq_lo);
     if (c->cap) cudaStreamDestroy(c->cap);
     delete c;
 }
@@ -273,7 +305,7 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
     if (cfg->p_best_pct < 0 || cfg->p_best_pct > 100) return METADE_EINVAL;
     if (cfg->n_out < 0 || (cfg->n_out > 0 && (cfg->n_out < 4 || cfg->n_inst % cfg->n_out != 0))) return METADE_EINVAL;
     if (cfg->path != METADE_PATH_BATCHED && cfg->path != METADE_PATH_PLAIN) return METADE_EINVAL;
-    if (cfg->prec != METADE_FP32) return METADE_EUNSUPPORTED;
+    if (cfg->prec != METADE_FP32 && cfg->prec != METADE_BF16 && cfg->prec != METADE_BF16X3) return METADE_EUNSUPPORTED;
     for (int p = 0; p < cfg->n_prob; ++p) {
         if (cfg->prob_dim[p] < 1 || cfg->prob_obj[p] < 0 || cfg->prob_obj[p] > 5) return METADE_EINVAL;
         if (cfg->prob_dim[p] > kMaxDim) return METADE_EUNSUPPORTED;
@@ -355,6 +387,33 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
         delete c;
         return METADE_EUNSUPPORTED;
     }
+    // executors on the tensor cores: operand row offsets (InstDesc.pad0), tiles
+    c->is_tc.assign(c->n_inst, 0);
+    std::vector<int> tc_execs, tc_row_exec, tc_tiles;
+    std::vector<long long> tc_brow(c->n_prob, -1);
+    long long tc_brows = 0;
+    int tc_kp = 0, tc_max_dpad = 0;
+    if (c->prec == METADE_BF16 || c->prec == METADE_BF16X3) {
+        for (int k = 0; k < c->n_inst; ++k) {
+            InstDesc& d = c->hdesc[k];
+            if (d.dim < kTcMinDim) continue;
+            c->is_tc[k] = 1;
+            d.pad0 = (int)tc_row_exec.size();
+            tc_execs.push_back(k);
+            for (int i = 0; i < d.np; ++i) tc_row_exec.push_back(k);
+            for (int m0 = 0; m0 < d.np; m0 += 128) {
+                tc_tiles.push_back(k);
+                tc_tiles.push_back(m0);
+            }
+            tc_kp = std::max(tc_kp, (d.dim + 63) / 64 * 64);
+            tc_max_dpad = std::max(tc_max_dpad, d.dpad);
+            if (tc_brow[d.prob] < 0) {
+                tc_brow[d.prob] = tc_brows;
+                tc_brows += (d.dim + 255) / 256 * 256;
+            }
+        }
+        c->tc = !tc_execs.empty();
+    }
     c->pop_floats = po;
     c->n_indiv = fo;
 
@@ -399,6 +458,57 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
         c->launches += 1;
         metade_status s = build_plan(c);
         if (s != METADE_OK) return fail(s);
+    }
+    if (c->tc) {
+        const bool split = c->prec == METADE_BF16X3;
+        const size_t nrows = tc_row_exec.size();
+        if (dalloc(&c->tc_execs, tc_execs.size()) || dalloc(&c->tc_row_exec, nrows) ||
+            dalloc(&c->tc_tiles, tc_tiles.size()) || dalloc(&c->tc_brow, (size_t)c->n_prob) ||
+            dalloc(&c->tc_topk, (size_t)c->n_indiv) || dalloc(&c->aq, nrows * tc_kp) ||
+            dalloc(&c->bq, (size_t)tc_brows * tc_kp) ||
+            (split && (dalloc(&c->aq_lo, nrows * tc_kp) || dalloc(&c->bq_lo, (size_t)tc_brows * tc_kp))))
+            return fail(METADE_ENOMEM);
+        if (cudaMemcpy(c->tc_execs, tc_execs.data(), sizeof(int) * tc_execs.size(), cudaMemcpyHostToDevice) ||
+            cudaMemcpy(c->tc_row_exec, tc_row_exec.data(), sizeof(int) * nrows, cudaMemcpyHostToDevice) ||
+            cudaMemcpy(c->tc_tiles, tc_tiles.data(), sizeof(int) * tc_tiles.size(), cudaMemcpyHostToDevice) ||
+            cudaMemcpy(c->tc_brow, tc_brow.data(), sizeof(long long) * c->n_prob, cudaMemcpyHostToDevice))
+            return fail(METADE_ECUDA);
+        for (int p = 0; p < c->n_prob; ++p) {
+            if (tc_brow[p] < 0) continue;
+            const int D = cfg->prob_dim[p], Dp = (D + 3) & ~3;
+            if (launch_tc_pack_rot(c->rot, rot_off[p], D, Dp, tc_kp, (D + 255) / 256 * 256, c->bq, split ? c->bq_lo : nullptr,
+                                   tc_brow[p], c->st))
+                return fail(METADE_ECUDA);
+        }
+        if (cudaStreamSynchronize(c->st)) return fail(METADE_ECUDA);
+        TcPlan& t = c->tcp;
+        t.execs = c->tc_execs;
+        t.n_exec = (int)tc_execs.size();
+        t.row_exec = c->tc_row_exec;
+        t.n_rows = (int)nrows;
+        t.tiles = c->tc_tiles;
+        t.n_tiles = (int)tc_tiles.size() / 2;
+        t.brow = c->tc_brow;
+        t.topk_all = c->tc_topk;
+        t.uscr = c->uscr;
+        t.fu = c->fuscr;
+        t.aq = c->aq;
+        t.aq_lo = c->aq_lo;
+        t.bq = c->bq;
+        t.bq_lo = c->bq_lo;
+        t.kp = tc_kp;
+        t.split = split ? 1 : 0;
+        t.max_dpad = tc_max_dpad;
+        if (!tc_make_map(&t.mapA, c->aq, (long long)nrows, tc_kp, 128) ||
+            !tc_make_map(&t.mapB, c->bq, tc_brows, tc_kp, 256) ||
+            (split && (!tc_make_map(&t.mapAlo, c->aq_lo, (long long)nrows, tc_kp, 128) ||
+                       !tc_make_map(&t.mapBlo, c->bq_lo, tc_brows, tc_kp, 256))))
+            return fail(METADE_ECUDA);
+        if (!split) {
+            t.mapAlo = t.mapA;
+            t.mapBlo = t.mapB;
+        }
+        c->launches += 1;
     }
     *out = c;
     return METADE_OK;
@@ -563,7 +673,16 @@ metade_status metade_plan_info(const metade_ctx* c, char* buf, size_t len) {
                  k.plan.grid, k.plan.smem, k.plan.rot_smem, k.n_work);
         s += tmp;
     }
-    s += "]}";
+    s += "]";
+    if (c->tc) {
+        char tmp[256];
+        snprintf(tmp, sizeof(tmp),
+                 ", \"tensor_core\": {\"kernel\": \"k_rot_tc\", \"precision\": \"%s\", \"executors\": %d, "
+                 "\"tiles\": %d, \"kp\": %d, \"tile\": [128, 256, 64]}",
+                 c->tcp.split ? "bf16x3" : "bf16", c->tcp.n_exec, c->tcp.n_tiles, c->tcp.kp);
+        s += tmp;
+    }
+    s += "}";
     if (s.size() + 1 > len) return METADE_EINVAL;
     std::memcpy(buf, s.c_str(), s.size() + 1);
     return METADE_OK;

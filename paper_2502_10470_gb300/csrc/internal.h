@@ -2,6 +2,8 @@
 // library (not part of the C-ABI).
 #pragma once
 #include <cstdint>
+#include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "device.cuh"
@@ -65,6 +67,28 @@ cudaError_t launch_fused(const StepArgs& a, const int* work, int n_work, const F
 size_t fused_smem_small(int dmax, int max_np);
 size_t fused_smem_general(int max_np, int max_dpad, int threads, bool rot_in_smem);
 int small_dmax_for(int dim);  // 0 when the small kernel does not apply
+
+// Large-D executors on the tensor cores (tc_rotate.cu).
+struct TcPlan {
+    const int* execs;        // device [n_exec] executors of the bucket
+    int n_exec;
+    const int* row_exec;     // device [n_rows] operand row -> executor (InstDesc.pad0 = first row)
+    int n_rows;
+    const int* tiles;        // device [n_tiles][2] (executor, first individual)
+    int n_tiles;
+    const long long* brow;   // device [n_prob] first B row of each problem
+    int* topk_all;           // device [n_indiv] pbest pools
+    float* uscr;             // trial rows (population layout)
+    float* fu;               // trial fitness [n_indiv]
+    __nv_bfloat16 *aq, *aq_lo, *bq, *bq_lo;
+    int kp, split, max_dpad;
+    CUtensorMap mapA, mapB, mapAlo, mapBlo;
+};
+bool tc_make_map(CUtensorMap* map, const void* base, long long rows, int kp, int box_rows);
+size_t tc_gemm_smem(bool split);
+cudaError_t launch_tc_pack_rot(const float* rot, long long rot_off, int dim, int dpad, int kp, int np_rows,
+                               __nv_bfloat16* bq, __nv_bfloat16* bq_lo, long long brow, cudaStream_t st);
+cudaError_t launch_tc_generation(const StepArgs& a, const TcPlan& p, cudaStream_t st);
 
 // Evolver.
 cudaError_t launch_outer_init(int n_groups, int n_out, Key key, float* opop, float* ofit, cudaStream_t st);

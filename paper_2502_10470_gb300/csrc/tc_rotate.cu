@@ -1,0 +1,436 @@
+// tc_rotate.cu -- large-D executors on the 5th-generation tensor cores.
+//
+// For D >= 256 the rotation z = R (u - o) of a whole population is a dense
+// GEMM, Z[NP x D] = Dq[NP x K] * Rq[D x K]^T, with both operands K-major.  One
+// generation of the large-D executors is four launches:
+//   k_tc_prologue  best and pbest pool per executor (block per executor)
+//   k_tc_trial     draws, mutation, crossover, clip (warp per individual);
+//                  writes the FP32 trial row and the BF16 GEMM operand(s)
+//   k_rot_tc       tcgen05 GEMM: TMA (128-byte swizzle) -> shared memory ->
+//                  tcgen05.mma (M 128, N 256, K 16, FP32 accumulate in TMEM);
+//                  the epilogue reads TMEM with tcgen05.ld, one thread per
+//                  individual (TMEM lane), and accumulates the objective
+//                  column chunk by column chunk, so Z never reaches memory
+//   k_tc_select    greedy selection and row copy (warp per individual)
+// Precision: BF16 operands, or bf16x3 (split precision, Henry, Tang &
+// Heinecke, ARITH 2019): d = d_hi + d_lo, R = R_hi + R_lo, and
+// Z = d_hi R_hi + d_hi R_lo + d_lo R_hi accumulated in FP32.
+//
+// Every mbarrier wait is bounded: on timeout the kernel latches
+// METADE_ETIMEOUT, drains its own outstanding copies (bounded), frees TMEM
+// and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "block.cuh"
+#include "internal.h"
+
+namespace metade {
+
+namespace {
+
+constexpr int kBM = 128, kBN = 256, kBK = 64;           // BF16: a 64-element K tile is one 128-byte row
+constexpr int kStages = 4;
+constexpr int kAT = kBM * kBK * 2;                        // 16 KB
+constexpr int kBT = kBN * kBK * 2;                        // 32 KB
+constexpr uint32_t kWaitLimit = 1u << 22;                 // try_wait rounds before giving up (seconds)
+constexpr int kStatusTimeout = 4;                         // METADE_ETIMEOUT
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t addr = smem_u32(bar);
+    for (uint32_t it = 0; it < kWaitLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, rows of 128
+// bytes grouped by 8 (stride 1024 bytes), descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;             // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset: 8 rows x 128 bytes
+    d |= (uint64_t)1 << 46;             // version
+    d |= (uint64_t)2 << 61;             // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::f16: BF16 A and B, FP32 D, K-major, M 128, N 256.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) |
+                            ((uint32_t)(kBM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct TcGemmArgs {
+    const InstDesc* desc;
+    const int* tiles;         // [n_tiles][2]: executor, first individual of the 128-row tile
+    const long long* brow;    // per problem: first row of its padded R in the B operand
+    float* fu;                // out: f(u) per individual (fitness index)
+    int kt;                   // K tiles of 64
+    int split;                // 1: bf16x3 (three products)
+    int* status;
+};
+
+// 128 threads: thread 0 issues TMA and MMA; all four warps run the epilogue
+// (warp w owns TMEM lanes 32w..32w+31, i.e. tile rows 32w..32w+31).
+__global__ void __launch_bounds__(128, 1)
+    k_rot_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+             const __grid_constant__ CUtensorMap tmAlo, const __grid_constant__ CUtensorMap tmBlo, TcGemmArgs a) {
+    extern __shared__ uint8_t smraw[];
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
+    __shared__ uint32_t tmem_base;
+    uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
+    const int nops = a.split ? 2 : 1;  // operand sets per stage (hi, and lo when split)
+    const int stage_bytes = nops * (kAT + kBT);
+    const int nst = a.split ? 2 : kStages;  // pipeline depth that fits shared memory
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    const int k = a.tiles[2 * blockIdx.x], m0 = a.tiles[2 * blockIdx.x + 1];
+    const InstDesc d = a.desc[k];
+    const int arow = d.pad0 + m0;  // first operand row of the tile
+    const int brow0 = (int)a.brow[d.prob];
+    const int nchunks = (d.dim + kBN - 1) / kBN;
+    const int total = nchunks * a.kt;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(kBN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = tmem_base;
+
+    auto load = [&](int it) {
+        const int s = it % nst, c = it / a.kt, kk = it - c * a.kt;
+        uint8_t* st = sm + s * stage_bytes;
+        mbar_expect_tx(&full[s], (uint32_t)stage_bytes);
+        tma_load_2d(st, &tmA, &full[s], kk * kBK, arow);
+        tma_load_2d(st + kAT, &tmB, &full[s], kk * kBK, brow0 + c * kBN);
+        if (a.split) {
+            tma_load_2d(st + kAT + kBT, &tmAlo, &full[s], kk * kBK, arow);
+            tma_load_2d(st + 2 * kAT + kBT, &tmBlo, &full[s], kk * kBK, brow0 + c * kBN);
+        }
+    };
+
+    bool ok = true;
+    int issued = 0, consumed = 0;  // loads issued / waited on by thread 0
+    if (tid == 0) {
+        const int pre = total < nst ? total : nst;
+        for (int it = 0; it < pre; ++it) load(it);
+        issued = pre;
+    }
+    ObjR acc;
+    const int row = 32 * warp + lane;  // tile row of this thread
+    for (int c = 0; c < nchunks; ++c) {
+        if (tid == 0 && ok) {
+            for (int kk = 0; kk < a.kt && ok; ++kk) {
+                const int it = c * a.kt + kk, s = it % nst;
+                const uint32_t ph = (uint32_t)(it / nst) & 1u;
+                if (!mbar_wait(&full[s], ph)) {
+                    ok = false;
+                    break;
+                }
+                ++consumed;
+                tc_fence_after();
+                uint8_t* st = sm + s * stage_bytes;
+                const uint64_t ad = sdesc_sw128(smem_u32(st)), bd = sdesc_sw128(smem_u32(st + kAT));
+#pragma unroll
+                for (int j = 0; j < kBK / 16; ++j)  // K 16 per instruction, 32 bytes along the swizzled row
+                    mma_bf16(taddr, ad + 2 * j, bd + 2 * j, (kk > 0 || j > 0) ? 1u : 0u);
+                if (a.split) {
+                    const uint64_t al = sdesc_sw128(smem_u32(st + kAT + kBT));
+                    const uint64_t bl = sdesc_sw128(smem_u32(st + 2 * kAT + kBT));
+#pragma unroll
+                    for (int j = 0; j < kBK / 16; ++j) {
+                        mma_bf16(taddr, ad + 2 * j, bl + 2 * j, 1u);
+                        mma_bf16(taddr, al + 2 * j, bd + 2 * j, 1u);
+                    }
+                }
+                mma_commit(&empty[s]);
+                // refill the stage used by the previous iteration once its MMAs are done
+                if (it >= 1 && issued < total) {
+                    const int pit = it - 1, ps = pit % nst;
+                    if (!mbar_wait(&empty[ps], (uint32_t)(pit / nst) & 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    load(issued);
+                    ++issued;
+                }
+            }
+            mma_commit(&done);
+        }
+        __syncwarp();
+        // epilogue for this column chunk
+        const bool got = __all_sync(kFull, mbar_wait(&done, (uint32_t)c & 1u) ? 1 : 0) != 0;  // warp-uniform
+        if (!got) ok = false;
+        tc_fence_after();
+        if (got) {
+            for (int p = 0; p < kBN / 32; ++p) {
+                const int col0 = c * kBN + 32 * p;
+                if (col0 >= d.dim) break;  // uniform across the CTA
+                float v[32];
+                tmem_ld32(taddr + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * p), v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (col0 + j < d.dim)
+                        acc.push(d.obj, v[j], d.obj == kGriewank ? rsqrtf((float)(col0 + j + 1)) : 0.f);
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+        ok = __syncthreads_and(ok ? 1 : 0) != 0;
+        if (!ok) break;
+    }
+    if (!ok) {
+        if (tid == 0) {
+            set_status(a.status, kStatusTimeout);
+            // drain copies still in flight into this CTA's shared memory (bounded)
+            for (int it = consumed; it < issued; ++it) mbar_wait(&full[it % nst], (uint32_t)(it / nst) & 1u);
+        }
+    } else if (m0 + row < d.np) {
+        a.fu[d.fit_off + m0 + row] = nan_to_inf(acc.finish(d.obj, d.dim));
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kBN) : "memory");
+}
+
+// ----------------------------------------------------------- other stages
+// Best and pbest pool from the generation-start fitness (block per executor).
+__global__ void k_tc_prologue(StepArgs a, const int* __restrict__ execs, int* topk_all) {
+    const int k = execs[blockIdx.x];
+    const InstDesc d = a.desc[k];
+    const Strat s = load_strat(a.theta + 6 * k, d.np);
+    if (!s.ok) {
+        if (threadIdx.x == 0) set_status(a.status, 1);
+        return;
+    }
+    block_topk(a.fit + d.fit_off, d.np, d.kp, topk_all + d.fit_off);
+}
+
+// Trial rows (FP32, into the scratch U) and the GEMM operand d = u - o, BF16
+// (hi, and lo = bf16(d - hi) when split), K zero-padded to kp floats.
+// Warps of one block may belong to different executors: per-warp shared
+// scratch is strided by the bucket's widest row (ws floats).
+__global__ void __launch_bounds__(256) k_tc_trial(StepArgs a, const int* __restrict__ row_exec, int n_rows,
+                                                  const int* __restrict__ topk_all, float* uscr, __nv_bfloat16* aq,
+                                                  __nv_bfloat16* aq_lo, int kp, int ws) {
+    extern __shared__ __align__(16) float smt[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (r >= n_rows) return;
+    const int k = row_exec[r];
+    const InstDesc d = a.desc[k];
+    const int i = r - d.pad0;
+    const Strat s = load_strat(a.theta + 6 * k, d.np);
+    if (!s.ok) return;
+    float* db = smt + (size_t)warp * ws;
+    const uint32_t epoch = a.epoch_dev ? *a.epoch_dev : a.epoch;
+    const Ctr c = make_ctr(a.key, (uint32_t)d.stream, a.gen0, (uint32_t)i, epoch);
+    const int* topk = topk_all + d.fit_off;
+    Indiv v;
+    indiv_setup(s, c, i, d.np, d.dim, d.kp, topk, topk[0], v);
+    const int L = s.cs == 2 ? exp_length(c, d.dim, s.cri) : 0;
+    warp_trial(s, c, v, i, d.dim, L, a.pop + d.pop_off, d.dpad, a.shift + d.shift_off, a.lo, a.hi,
+               uscr + d.pop_off + (long long)i * d.dpad, db);
+    __syncwarp();
+    __nv_bfloat16* row = aq + (long long)r * kp;
+    for (int j = lane; j < kp; j += 32) {
+        const float x = j < d.dim ? db[j] : 0.0f;
+        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+        row[j] = hi;
+        if (aq_lo) aq_lo[(long long)r * kp + j] = __float2bfloat16_rn(x - __bfloat162float(hi));
+    }
+}
+
+// Greedy selection (ties by the FP32 difference form on CUDA cores) and row copy.
+__global__ void __launch_bounds__(256) k_tc_select(StepArgs a, const int* __restrict__ row_exec, int n_rows,
+                                                   const float* __restrict__ uscr, const float* __restrict__ fu, int ws) {
+    extern __shared__ __align__(16) float sms[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (r >= n_rows) return;
+    const int k = row_exec[r];
+    const InstDesc d = a.desc[k];
+    const Strat s = load_strat(a.theta + 6 * k, d.np);
+    if (!s.ok) return;
+    const int i = r - d.pad0;
+    float* X = a.pop + d.pop_off + (long long)i * d.dpad;
+    const float* U = uscr + d.pop_off + (long long)i * d.dpad;
+    float fn = fu[d.fit_off + i];
+    const float fx = a.fit[d.fit_off + i];
+    bool tie = near_tie(fn, fx);
+    if (tie) {
+        bool diff = false;
+        for (int j = lane; j < d.dim; j += 32) diff = diff || (U[j] != X[j]);
+        if (!__any_sync(kFull, diff)) tie = false, fn = fx;  // trial == target
+    }
+    bool take;
+    if (tie) {
+        float* zb = sms + (size_t)warp * 2 * ws;
+        warp_rotate_pair(d.dim, a.rotT + d.rot_off, d.dpad, X, U, a.shift + d.shift_off, zb, zb + ws);
+        __syncwarp();
+        const float df = warp_diff(d.obj, d.dim, zb, zb + ws);
+        take = df <= 0.0f;
+        if (take) fn = fx + df;
+    } else {
+        take = fn <= fx;
+    }
+    if (take) {
+        for (int j = lane * 4; j < d.dpad; j += 128)
+            *reinterpret_cast<float4*>(X + j) = *reinterpret_cast<const float4*>(U + j);
+        if (lane == 0) a.fit[d.fit_off + i] = fn;
+    }
+}
+
+// B operand: padded R rows in BF16 (hi, and the lo residual when split).
+__global__ void k_tc_pack_rot(const float* __restrict__ rot, long long rot_off, int dim, int dpad, int kp,
+                              __nv_bfloat16* bq, __nv_bfloat16* bq_lo, long long brow) {
+    const int r = blockIdx.x;  // padded rows >= dim are zero
+    for (int c = threadIdx.x; c < kp; c += blockDim.x) {
+        const float x = (r < dim && c < dim) ? rot[rot_off + (long long)r * dpad + c] : 0.0f;
+        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+        bq[(brow + r) * kp + c] = hi;
+        if (bq_lo) bq_lo[(brow + r) * kp + c] = __float2bfloat16_rn(x - __bfloat162float(hi));
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+}  // namespace
+
+// 2-D BF16 tensor map over a row-major [rows][kp] matrix, box [64 x box_rows],
+// 128-byte swizzle, out-of-range rows read as zero.
+bool tc_make_map(CUtensorMap* map, const void* base, long long rows, int kp, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+size_t tc_gemm_smem(bool split) { return (size_t)(split ? 2 : kStages) * (split ? 2 : 1) * (kAT + kBT) + 1024; }
+
+cudaError_t launch_tc_pack_rot(const float* rot, long long rot_off, int dim, int dpad, int kp, int np_rows,
+                               __nv_bfloat16* bq, __nv_bfloat16* bq_lo, long long brow, cudaStream_t st) {
+    k_tc_pack_rot<<<np_rows, 256, 0, st>>>(rot, rot_off, dim, dpad, kp, bq, bq_lo, brow);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_generation(const StepArgs& a, const TcPlan& p, cudaStream_t st) {
+    k_tc_prologue<<<p.n_exec, 256, 0, st>>>(a, p.execs, p.topk_all);
+    const int blocks = (p.n_rows + 7) / 8;
+    size_t smem_t = (size_t)8 * p.max_dpad * sizeof(float);
+    size_t smem_s = (size_t)8 * 2 * p.max_dpad * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_tc_trial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_tc_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s);
+    if (e != cudaSuccess) return e;
+    k_tc_trial<<<blocks, 256, smem_t, st>>>(a, p.row_exec, p.n_rows, p.topk_all, p.uscr, p.aq, p.split ? p.aq_lo : nullptr,
+                                            p.kp, p.max_dpad);
+    const size_t smem_g = tc_gemm_smem(p.split);
+    e = cudaFuncSetAttribute(k_rot_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_g);
+    if (e != cudaSuccess) return e;
+    TcGemmArgs g;
+    g.desc = a.desc;
+    g.tiles = p.tiles;
+    g.brow = p.brow;
+    g.fu = p.fu;
+    g.kt = p.kp / kBK;
+    g.split = p.split;
+    g.status = a.status;
+    k_rot_tc<<<p.n_tiles, 128, smem_g, st>>>(p.mapA, p.mapB, p.split ? p.mapAlo : p.mapA, p.split ? p.mapBlo : p.mapB,
+                                             g);
+    k_tc_select<<<blocks, 256, smem_s, st>>>(a, p.row_exec, p.n_rows, p.uscr, p.fu, p.max_dpad);
+    return cudaGetLastError();
+}
+
+}  // namespace metade

@@ -56,18 +56,20 @@ def rel_err(a, b, floor=1.0):
         return np.abs(a - b) / np.maximum(np.abs(b), floor)
 
 
-def z_rounding_sensitivity(obj: int, x, shift, rot) -> np.ndarray:
-    """First-order change of f when every z_j moves by its FP32 error budget
-    h_j = 2^-24 (|z_j| + sqrt(D) sum_c |R_jc d_c|) (one rounding of z_j plus
-    the accumulation of a D-term float32 dot product), measured with the
-    oracle's FP64 objective by central differences.  No float32 evaluation of
-    f can be more accurate than this at that point."""
+def z_rounding_sensitivity(obj: int, x, shift, rot, unit: float = 2.0 ** -24, acc_unit: float = 2.0 ** -24) -> np.ndarray:
+    """First-order change of f when every z_j moves by its error budget
+    h_j = unit * sum_c |R_jc d_c| + acc_unit * (|z_j| + sqrt(D) sum_c |R_jc d_c|):
+    `unit` bounds the rounding of the products' operands (0 for float32
+    operands, 2^-8 for BF16 operands, 2^-16 for split bf16x3), `acc_unit` one
+    rounding of z_j plus a D-term float32 accumulation.  Measured with the
+    oracle's FP64 objective by central differences."""
     x = np.atleast_2d(np.asarray(x, dtype=np.float64))
     R = np.asarray(rot, dtype=np.float64)
     d = x - np.asarray(shift, dtype=np.float64)[None, :]
     z = d @ R.T
     D = z.shape[1]
-    h = 2.0 ** -24 * (np.abs(z) + np.sqrt(D) * (np.abs(d) @ np.abs(R).T))
+    s1 = np.abs(d) @ np.abs(R).T
+    h = unit * s1 + acc_unit * (np.abs(z) + np.sqrt(D) * s1)
     out = np.zeros(z.shape[0])
     for n in range(z.shape[0]):
         for j in range(D):
@@ -78,19 +80,24 @@ def z_rounding_sensitivity(obj: int, x, shift, rot) -> np.ndarray:
     return out
 
 
-def check_fitness_fp32(f32, x, prob, rtol: float = FIT_RTOL, floor: float = 0.0):
-    """FP32 fitness vs the FP64 oracle at the same float32 point: within rtol
-    relative, or -- where the objective itself is ill-conditioned -- within
-    rtol relative plus 4x the FP32 rounding sensitivity of z.  Returns the
-    fraction of points that needed the conditioning term."""
-    f32 = np.asarray(f32, dtype=np.float64)
+def check_fitness(fv, x, prob, rtol: float, unit: float, floor: float = 0.0):
+    """Fitness vs the FP64 oracle at the same float32 point: within rtol
+    relative, or -- where the objective is ill-conditioned at the point --
+    within rtol relative plus 4x the first-order effect of the evaluation's
+    rounding budget on z (see z_rounding_sensitivity).  Returns the fraction
+    of points that needed the conditioning term."""
+    fv = np.asarray(fv, dtype=np.float64)
     f64 = oracle.eval_pop(prob.obj, x, prob.shift, prob.rot)
-    err = np.abs(f32 - f64)
+    err = np.abs(fv - f64)
     base = rtol * np.maximum(np.abs(f64), floor)
     bad = np.nonzero(err > base)[0]
     if bad.size:
-        sens = z_rounding_sensitivity(prob.obj, np.asarray(x)[bad], prob.shift, prob.rot)
+        sens = z_rounding_sensitivity(prob.obj, np.asarray(x)[bad], prob.shift, prob.rot, unit=unit)
         over = err[bad] > base[bad] + 4.0 * sens
-        assert not over.any(), ("fp32 fitness", prob.obj, prob.dim, err[bad][over], f64[bad][over],
-                                sens[over])
-    return bad.size / max(1, f32.size)
+        assert not over.any(), ("fitness", prob.obj, prob.dim, err[bad][over], f64[bad][over], sens[over])
+    return bad.size / max(1, fv.size)
+
+
+def check_fitness_fp32(f32, x, prob, rtol: float = FIT_RTOL, floor: float = 0.0):
+    """FP32 evaluation: 1e-5 relative, or the FP32 conditioning bound."""
+    return check_fitness(f32, x, prob, rtol, 0.0, floor)
