@@ -49,6 +49,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison arm")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--inner-gens", type=int, default=INNER_GENS)
+    ap.add_argument("--workload", default="moderate", choices=["moderate", "precision"],
+                    help="moderate: the headline workload; precision: the D=1000 precision study")
+    ap.add_argument("--n-inst", type=int, default=64, help="executors of the precision study")
     return ap.parse_args(argv)
 
 
@@ -267,6 +270,8 @@ def run_ours(args):
     sampler = ClockSampler(local)
     sampler.start()
     launches0 = M.metade_launch_count(b.ctx)
+    M.metade_profile(b.ctx, True)
+    M.metade_profile_read(b.ctx)
     step_ev, thetas = [], []
     for s in range(args.steps):
         flush.zero_()
@@ -280,8 +285,10 @@ def run_ours(args):
     barrier()
     launches = M.metade_launch_count(b.ctx) - launches0
     clocks = sampler.stop()
+    prof = M.metade_profile_read(b.ctx)
+    M.metade_profile(b.ctx, False)
     step_ms = [e[0].elapsed_time(e[3]) for e in step_ev]
-    kern_ms = [e[1].elapsed_time(e[2]) for e in step_ev]
+    kern_ms = [prof["fused_small"][0] / max(1, prof["fused_small"][1])] * args.steps
     total_ms = sum(step_ms)
     t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
     if world > 1:
@@ -379,8 +386,118 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------- precision study
+def run_precision(args):
+    """64 executors, NP 512, D 1000 (Rastrigin / Rosenbrock): one generation
+    in FP32 (CUDA cores), BF16 and bf16x3 (tcgen05), from a shared state.
+    Per precision: generation time and individual-gens/s, the tensor-core
+    GEMM's own time and TFLOP/s (2 NP D^2 algorithmic flops per executor),
+    the relative fitness error against FP64 at the same trials, and the
+    selection-bit mismatch rate against FP64 decisions (f64(u) <= f64(x))
+    when both sides of each comparison are evaluated in the precision."""
+    import numpy as np
+    import torch
+    import paper_2502_10470_gb300 as M
+    import synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    wl = synth.precision(n_inst=args.n_inst)
+    probs = [(p.dim, p.obj, p.shift, p.rot) for p in wl.problems]
+
+    def make(prec):
+        return M.Batch(probs, wl.inst_np, wl.inst_prob, wl.inst_group, seed=wl.seed, one_shot=0, prec=prec,
+                       device=dev, stream=stream.cuda_stream)
+
+    ref = make(M.METADE_FP32)
+    ref.set_theta(wl.theta)
+    M.metade_init(ref.ctx, ref.pop, ref.fit, 0)
+    pop0, fit0 = ref.pop.clone(), ref.fit.clone()
+    n = ref.n_indiv
+    f64x = torch.empty(n, dtype=torch.float64, device=dev)
+    M.metade_eval(ref.ctx, pop0, M.METADE_FP64, f64x)
+    ident = np.tile(np.array([0.0, 1.0, 4, 4, 1, 1], dtype=np.float32), (wl.n_inst, 1))  # trial = target
+    inf = torch.full_like(fit0, float("inf"))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    gemm_flops = 2.0 * float((wl.inst_np.astype(np.float64) * wl.dims().astype(np.float64) ** 2).sum())
+    out = {}
+    for name, prec in (("fp32", M.METADE_FP32), ("bf16", M.METADE_BF16), ("bf16x3", M.METADE_BF16X3)):
+        b = make(prec)
+        b.set_theta(wl.theta)
+        b.pop.copy_(pop0)
+        b.fit.copy_(inf)
+        M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 0, 1, None, None)
+        trial, ft = b.pop.clone(), b.fit.clone()
+        b.set_theta(ident)
+        b.pop.copy_(pop0)
+        b.fit.copy_(inf)
+        M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 0, 1, None, None)
+        fxp = b.fit.clone()
+        f64u = torch.empty(n, dtype=torch.float64, device=dev)
+        M.metade_eval(ref.ctx, trial, M.METADE_FP64, f64u)
+        if M.metade_sync(b.ctx) != 0 or M.metade_sync(ref.ctx) != 0:
+            raise RuntimeError("device status")
+        rel = ((ft.double() - f64u).abs() / f64u.abs()).cpu().numpy()
+        relx = ((fxp.double() - f64x).abs() / f64x.abs()).cpu().numpy()
+        mism = float(((ft.double() <= fxp.double()) != (f64u <= f64x)).float().mean().item())
+        b.set_theta(wl.theta)
+        b.pop.copy_(pop0)
+        b.fit.copy_(fit0)
+        for w in range(args.warmup):
+            M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, w, 1, None, None)
+        torch.cuda.synchronize()
+        M.metade_profile(b.ctx, True)
+        M.metade_profile_read(b.ctx)
+        ms = []
+        for st in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, args.warmup + st, 1, None, None)
+            e1.record(stream)
+            ms.append((e0, e1))
+        torch.cuda.synchronize()
+        prof = M.metade_profile_read(b.ctx)
+        gen_ms = float(np.mean([a.elapsed_time(c) for a, c in ms]))
+        r = {"ms_per_generation": gen_ms, "indiv_gens_per_s": n / (gen_ms / 1e3),
+             "fitness_rel_err_vs_fp64": {"median": float(np.median(rel)), "p99": float(np.quantile(rel, 0.99)),
+                                         "max": float(rel.max())},
+             "target_fitness_rel_err_max": float(relx.max()),
+             "selection_mismatch_rate_vs_fp64": mism,
+             "plan": json.loads(M.metade_plan_info(b.ctx))}
+        if prof["tc_gemm"][1]:
+            gms = prof["tc_gemm"][0] / prof["tc_gemm"][1]
+            r["tc_gemm_ms"] = gms
+            r["tc_gemm_tflops_algorithmic"] = gemm_flops / (gms / 1e3) / 1e12
+            r["tc_gemm_tflops_issued"] = (3 if name == "bf16x3" else 1) * gemm_flops / (gms / 1e3) / 1e12
+        if prof["fused_general"][1]:
+            r["fused_general_ms"] = prof["fused_general"][0] / prof["fused_general"][1]
+        out[name] = r
+        b.close()
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    bf = out["bf16"]
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    line = {"metric": "precision study: individual-gens/s, GEMM TFLOP/s, fitness error and selection mismatch vs FP64",
+            "workload": "precision-%dx512xD1000" % wl.n_inst, "steps": args.steps, "warmup": args.warmup,
+            "gemm_gflop_per_generation": gemm_flops / 1e9, "results": out,
+            "roofline": {"bound": "tensor", "kernel": "k_rot_tc (bf16)", "achieved": bf.get("tc_gemm_tflops_algorithmic"),
+                         "peak": peak, "unit": "TFLOP/s",
+                         "frac": (bf.get("tc_gemm_tflops_algorithmic") or 0) / peak, "traffic": None,
+                         "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured"},
+            "l2": "flushed before every timed generation"}
+    print(json.dumps(line), flush=True)
+    ref.close()
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.workload == "precision":
+        run_precision(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -221,6 +221,16 @@ METADE_API metade_status metade_sync(metade_ctx *ctx);
 /* Write a one-line JSON description of the launch plan into buf. */
 METADE_API metade_status metade_plan_info(const metade_ctx *ctx, char *buf, size_t len);
 
+/* Timing of the context's own kernels: with profiling enabled, calls made
+ * outside stream capture record CUDA events on the context's stream around
+ * each launch of the fused kernels and the tensor-core stage.  Reading waits
+ * for the stream and returns, per kind, the summed milliseconds and the number
+ * of launches since the last read -- kinds: 0 fused small-D kernel, 1 fused
+ * general kernel, 2 tensor-core rotation GEMM, 3 whole tensor-core generation
+ * -- then clears them.  ms and count are host arrays of 4 (may be NULL). */
+METADE_API metade_status metade_profile(metade_ctx *ctx, int32_t enable);
+METADE_API metade_status metade_profile_read(metade_ctx *ctx, double *ms, int64_t *count);
+
 /* Number of kernel launches this context has issued (graph replays count the
  * kernels they contain). */
 METADE_API int64_t metade_launch_count(const metade_ctx *ctx);

@@ -29,7 +29,8 @@ EXPORTED = [
     "metade_create", "metade_destroy", "metade_layout", "metade_offsets", "metade_set_stream",
     "metade_init", "metade_inner_step", "metade_eval", "metade_outer_init", "metade_outer_step",
     "metade_outer_generation", "metade_draw_record", "metade_sync", "metade_plan_info",
-    "metade_launch_count", "metade_strerror", "metade_plain_step_noalloc",
+    "metade_launch_count", "metade_strerror", "metade_plain_step_noalloc", "metade_profile",
+    "metade_profile_read",
 ]
 
 
@@ -94,6 +95,8 @@ def _lib():
         L.metade_launch_count.restype = C.c_int64
         L.metade_plain_step_noalloc.argtypes = [P, P, P, P, P, I32, I32, I32, C.c_float, C.c_float, C.c_uint64,
                                                 U32, U32, U32, I32, P]
+        L.metade_profile.argtypes = [P, I32]
+        L.metade_profile_read.argtypes = [P, P, P]
         L.metade_strerror.argtypes = [C.c_int]
         L.metade_strerror.restype = C.c_char_p
         for name in EXPORTED:
@@ -231,6 +234,21 @@ def metade_plain_step_noalloc(pop, fit, theta, shift, rot, np_: int, dim: int, o
     """One plain generation of one executor with no allocation; returns the status."""
     return _lib().metade_plain_step_noalloc(_ptr(pop), _ptr(fit), _ptr(theta), _ptr(shift), _ptr(rot), np_, dim,
                                             obj, lo, hi, seed, stream_id, epoch, gen, p_best_pct, stream)
+
+
+PROFILE_KINDS = ["fused_small", "fused_general", "tc_gemm", "tc_generation"]
+
+
+def metade_profile(ctx: int, enable: bool) -> None:
+    _check(_lib().metade_profile(ctx, int(enable)), "metade_profile")
+
+
+def metade_profile_read(ctx: int):
+    """{kind: (milliseconds, launches)} since the last read."""
+    ms = np.zeros(4, dtype=np.float64)
+    n = np.zeros(4, dtype=np.int64)
+    _check(_lib().metade_profile_read(ctx, ms.ctypes.data, n.ctypes.data), "metade_profile_read")
+    return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(PROFILE_KINDS)}
 
 
 def metade_strerror(status: int) -> str:

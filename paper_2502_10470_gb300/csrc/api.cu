@@ -25,6 +25,13 @@ struct Bucket {
     int work_off, n_work;
 };
 
+enum ProfKind { kProfFusedSmall = 0, kProfFusedGeneral = 1, kProfTcGemm = 2, kProfTcGeneration = 3, kProfKinds = 4 };
+
+struct ProfRec {
+    int kind;
+    cudaEvent_t a, b;
+};
+
 struct GraphEntry {
     std::vector<uintptr_t> key;
     cudaGraphExec_t exec;
@@ -65,6 +72,8 @@ struct metade_ctx {
     std::vector<Bucket> buckets;
     std::vector<GraphEntry> graphs;
     int64_t launches = 0;
+    bool prof_on = false;
+    std::vector<ProfRec> prof;
     // large-D executors on the tensor cores (prec BF16 / BF16X3)
     bool tc = false;
     TcPlan tcp;
@@ -185,6 +194,21 @@ metade_status build_plan(metade_ctx* c) {
     return METADE_OK;
 }
 
+// Event pair around a launch when profiling is on (never inside a capture).
+bool prof_pair(metade_ctx* c, cudaStream_t st, int kind, cudaEvent_t* a, cudaEvent_t* b) {
+    *a = *b = nullptr;
+    if (!c->prof_on) return false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return false;
+    if (cudaEventCreate(a) != cudaSuccess) return false;
+    if (cudaEventCreate(b) != cudaSuccess) {
+        cudaEventDestroy(*a);
+        return false;
+    }
+    c->prof.push_back(ProfRec{kind, *a, *b});
+    return true;
+}
+
 metade_status run_inner(metade_ctx* c, cudaStream_t st, float* pop, float* fit, const float* theta, uint32_t epoch,
                         const uint32_t* epoch_dev, uint32_t gen0, int n_gens, float* best_f, int* best_i,
                         int64_t* launches) {
@@ -205,13 +229,22 @@ metade_status run_inner(metade_ctx* c, cudaStream_t st, float* pop, float* fit, 
     }
     StepArgs a = step_args(c, pop, fit, theta, epoch, epoch_dev, gen0, n_gens, best_f, best_i);
     for (const Bucket& b : c->buckets) {
+        cudaEvent_t e0, e1;
+        const bool pr = prof_pair(c, st, b.plan.kind == 0 ? kProfFusedSmall : kProfFusedGeneral, &e0, &e1);
+        if (pr) cudaEventRecord(e0, st);
         CK(launch_fused(a, c->work + b.work_off, b.n_work, b.plan, c->uscr, st));
+        if (pr) cudaEventRecord(e1, st);
         *launches += 1;
     }
     if (c->tc) {
         for (int g = 0; g < n_gens; ++g) {
             StepArgs t = step_args(c, pop, fit, theta, epoch, epoch_dev, gen0 + (uint32_t)g, 1, nullptr, nullptr);
-            CK(launch_tc_generation(t, c->tcp, st));
+            cudaEvent_t g0, g1, e0, e1;
+            const bool pg = prof_pair(c, st, kProfTcGemm, &g0, &g1);
+            const bool pe = prof_pair(c, st, kProfTcGeneration, &e0, &e1);
+            if (pe) cudaEventRecord(e0, st);
+            CK(launch_tc_generation(t, c->tcp, st, pg ? g0 : nullptr, pg ? g1 : nullptr));
+            if (pe) cudaEventRecord(e1, st);
             *launches += 4;
         }
         if (best_f || best_i) {
@@ -272,6 +305,10 @@ void metade_destroy(metade_ctx* c) {
     if (!c) return;
     if (c->st) cudaStreamSynchronize(c->st);
     for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+    for (auto& r : c->prof) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
     cudaFree(c->desc);
     cudaFree(c->row_inst);
     cudaFree(c->rot);
@@ -689,5 +726,33 @@ metade_status metade_plan_info(const metade_ctx* c, char* buf, size_t len) {
 }
 
 int64_t metade_launch_count(const metade_ctx* c) { return c ? c->launches : -1; }
+
+metade_status metade_profile(metade_ctx* c, int32_t enable) {
+    if (!c) return METADE_EINVAL;
+    c->prof_on = enable != 0;
+    return METADE_OK;
+}
+
+metade_status metade_profile_read(metade_ctx* c, double* ms, int64_t* count) {
+    if (!c) return METADE_EINVAL;
+    CK(cudaStreamSynchronize(c->st));
+    double tot[kProfKinds] = {0, 0, 0, 0};
+    int64_t n[kProfKinds] = {0, 0, 0, 0};
+    for (auto& r : c->prof) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+            tot[r.kind] += t;
+            n[r.kind] += 1;
+        }
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    c->prof.clear();
+    for (int k = 0; k < kProfKinds; ++k) {
+        if (ms) ms[k] = tot[k];
+        if (count) count[k] = n[k];
+    }
+    return METADE_OK;
+}
 
 }  // extern "C"

@@ -88,7 +88,8 @@ bool tc_make_map(CUtensorMap* map, const void* base, long long rows, int kp, int
 size_t tc_gemm_smem(bool split);
 cudaError_t launch_tc_pack_rot(const float* rot, long long rot_off, int dim, int dpad, int kp, int np_rows,
                                __nv_bfloat16* bq, __nv_bfloat16* bq_lo, long long brow, cudaStream_t st);
-cudaError_t launch_tc_generation(const StepArgs& a, const TcPlan& p, cudaStream_t st);
+cudaError_t launch_tc_generation(const StepArgs& a, const TcPlan& p, cudaStream_t st, cudaEvent_t gemm0 = nullptr,
+                                 cudaEvent_t gemm1 = nullptr);
 
 // Evolver.
 cudaError_t launch_outer_init(int n_groups, int n_out, Key key, float* opop, float* ofit, cudaStream_t st);

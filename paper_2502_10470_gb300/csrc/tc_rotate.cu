@@ -405,7 +405,8 @@ cudaError_t launch_tc_pack_rot(const float* rot, long long rot_off, int dim, int
     return cudaGetLastError();
 }
 
-cudaError_t launch_tc_generation(const StepArgs& a, const TcPlan& p, cudaStream_t st) {
+cudaError_t launch_tc_generation(const StepArgs& a, const TcPlan& p, cudaStream_t st, cudaEvent_t gemm0,
+                                 cudaEvent_t gemm1) {
     k_tc_prologue<<<p.n_exec, 256, 0, st>>>(a, p.execs, p.topk_all);
     const int blocks = (p.n_rows + 7) / 8;
     size_t smem_t = (size_t)8 * p.max_dpad * sizeof(float);
@@ -427,8 +428,10 @@ cudaError_t launch_tc_generation(const StepArgs& a, const TcPlan& p, cudaStream_
     g.kt = p.kp / kBK;
     g.split = p.split;
     g.status = a.status;
+    if (gemm0) cudaEventRecord(gemm0, st);
     k_rot_tc<<<p.n_tiles, 128, smem_g, st>>>(p.mapA, p.mapB, p.split ? p.mapAlo : p.mapA, p.split ? p.mapBlo : p.mapB,
                                              g);
+    if (gemm1) cudaEventRecord(gemm1, st);
     k_tc_select<<<blocks, 256, smem_s, st>>>(a, p.row_exec, p.n_rows, p.uscr, p.fu, p.max_dpad);
     return cudaGetLastError();
 }
