@@ -83,6 +83,7 @@ struct metade_ctx {
     int* tc_tiles = nullptr;
     long long* tc_brow = nullptr;
     int* tc_topk = nullptr;
+    int* tc_ties = nullptr;
     __nv_bfloat16 *aq = nullptr, *aq_lo = nullptr, *bq = nullptr, *bq_lo = nullptr;
 };
 
@@ -245,7 +246,7 @@ metade_status run_inner(metade_ctx* c, cudaStream_t st, float* pop, float* fit, 
             if (pe) cudaEventRecord(e0, st);
             CK(launch_tc_generation(t, c->tcp, st, pg ? g0 : nullptr, pg ? g1 : nullptr));
             if (pe) cudaEventRecord(e1, st);
-            *launches += 4;
+            *launches += 5;
         }
         if (best_f || best_i) {
             CK(launch_best(c->desc, c->n_inst, fit, best_f, best_i, st));
@@ -325,6 +326,7 @@ void metade_destroy(metade_ctx* c) {
     cudaFree(c->tc_tiles);
     cudaFree(c->tc_brow);
     cudaFree(c->tc_topk);
+    cudaFree(c->tc_ties);
     cudaFree(c->aq);
     cudaFree(c->aq_lo);
     cudaFree(c->bq);
@@ -501,7 +503,7 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
         const size_t nrows = tc_row_exec.size();
         if (dalloc(&c->tc_execs, tc_execs.size()) || dalloc(&c->tc_row_exec, nrows) ||
             dalloc(&c->tc_tiles, tc_tiles.size()) || dalloc(&c->tc_brow, (size_t)c->n_prob) ||
-            dalloc(&c->tc_topk, (size_t)c->n_indiv) || dalloc(&c->aq, nrows * tc_kp) ||
+            dalloc(&c->tc_topk, (size_t)c->n_indiv) || dalloc(&c->tc_ties, nrows + 1) || dalloc(&c->aq, nrows * tc_kp) ||
             dalloc(&c->bq, (size_t)tc_brows * tc_kp) ||
             (split && (dalloc(&c->aq_lo, nrows * tc_kp) || dalloc(&c->bq_lo, (size_t)tc_brows * tc_kp))))
             return fail(METADE_ENOMEM);
@@ -533,6 +535,14 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
         t.aq_lo = c->aq_lo;
         t.bq = c->bq;
         t.bq_lo = c->bq_lo;
+        t.tie_list = c->tc_ties + 1;
+        t.tie_count = c->tc_ties;
+        {
+            int dev = 0, sms = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            t.tie_ctas = std::max(1, sms) * 2;
+        }
         t.kp = tc_kp;
         t.split = split ? 1 : 0;
         t.max_dpad = tc_max_dpad;

@@ -81,6 +81,9 @@ struct TcPlan {
     float* uscr;             // trial rows (population layout)
     float* fu;               // trial fitness [n_indiv]
     __nv_bfloat16 *aq, *aq_lo, *bq, *bq_lo;
+    int* tie_list;           // device [n_rows] rows whose selection is a near tie
+    int* tie_count;          // device counter
+    int tie_ctas;            // CTAs of the tie kernel
     int kp, split, max_dpad;
     CUtensorMap mapA, mapB, mapAlo, mapBlo;
 };

@@ -11,7 +11,8 @@
 //                  the epilogue reads TMEM with tcgen05.ld, one thread per
 //                  individual (TMEM lane), and accumulates the objective
 //                  column chunk by column chunk, so Z never reaches memory
-//   k_tc_select    greedy selection and row copy (warp per individual)
+//   k_tc_select    greedy selection and row copy (warp per individual);
+//                  near ties are listed for k_tc_ties (a CTA per tie)
 // Precision: BF16 operands, or bf16x3 (split precision, Henry, Tang &
 // Heinecke, ARITH 2019): d = d_hi + d_lo, R = R_hi + R_lo, and
 // Z = d_hi R_hi + d_hi R_lo + d_lo R_hi accumulated in FP32.
@@ -312,10 +313,12 @@ __global__ void __launch_bounds__(256) k_tc_trial(StepArgs a, const int* __restr
     }
 }
 
-// Greedy selection (ties by the FP32 difference form on CUDA cores) and row copy.
+// Greedy selection and row copy.  Near ties are only listed here; k_tc_ties
+// decides them with a whole CTA each (a warp alone would stream two D x D
+// rotations from L2 one row group at a time).
 __global__ void __launch_bounds__(256) k_tc_select(StepArgs a, const int* __restrict__ row_exec, int n_rows,
-                                                   const float* __restrict__ uscr, const float* __restrict__ fu, int ws) {
-    extern __shared__ __align__(16) float sms[];
+                                                   const float* __restrict__ uscr, const float* __restrict__ fu,
+                                                   int* tie_list, int* tie_count) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int r = blockIdx.x * (blockDim.x >> 5) + warp;
     if (r >= n_rows) return;
@@ -334,21 +337,65 @@ __global__ void __launch_bounds__(256) k_tc_select(StepArgs a, const int* __rest
         for (int j = lane; j < d.dim; j += 32) diff = diff || (U[j] != X[j]);
         if (!__any_sync(kFull, diff)) tie = false, fn = fx;  // trial == target
     }
-    bool take;
     if (tie) {
-        float* zb = sms + (size_t)warp * 2 * ws;
-        warp_rotate_pair(d.dim, a.rotT + d.rot_off, d.dpad, X, U, a.shift + d.shift_off, zb, zb + ws);
-        __syncwarp();
-        const float df = warp_diff(d.obj, d.dim, zb, zb + ws);
-        take = df <= 0.0f;
-        if (take) fn = fx + df;
-    } else {
-        take = fn <= fx;
+        if (lane == 0) tie_list[atomicAdd(tie_count, 1)] = r;
+        return;
     }
-    if (take) {
+    if (fn <= fx) {
         for (int j = lane * 4; j < d.dpad; j += 128)
             *reinterpret_cast<float4*>(X + j) = *reinterpret_cast<const float4*>(U + j);
         if (lane == 0) a.fit[d.fit_off + i] = fn;
+    }
+}
+
+// Listed ties, one per CTA: threads own rows of z = R (x - o) and dz = R (u - x)
+// (coalesced reads of R^T rows), then one warp forms the difference
+// f(u) - f(x) (same difference forms as every other path).
+__global__ void __launch_bounds__(256) k_tc_ties(StepArgs a, const int* __restrict__ row_exec,
+                                                 const float* __restrict__ uscr, const int* __restrict__ tie_list,
+                                                 const int* __restrict__ tie_count, int ws) {
+    extern __shared__ __align__(16) float smz[];
+    __shared__ int take_s;
+    __shared__ float fn_s;
+    const int n = *tie_count;
+    for (int t = blockIdx.x; t < n; t += gridDim.x) {
+        const int r = tie_list[t];
+        const int k = row_exec[r];
+        const InstDesc d = a.desc[k];
+        const int i = r - d.pad0;
+        float* X = a.pop + d.pop_off + (long long)i * d.dpad;
+        const float* U = uscr + d.pop_off + (long long)i * d.dpad;
+        const float* o = a.shift + d.shift_off;
+        const float* RT = a.rotT + d.rot_off;
+        float* zx = smz;
+        float* dz = smz + ws;
+        for (int rr = threadIdx.x; rr < d.dim; rr += blockDim.x) {
+            float az = 0.f, ad = 0.f;
+            for (int c = 0; c < d.dim; ++c) {
+                const float rt = RT[(size_t)c * d.dpad + rr];
+                const float xc = X[c];
+                az = fmaf(rt, xc - o[c], az);
+                ad = fmaf(rt, U[c] - xc, ad);
+            }
+            zx[rr] = az;
+            dz[rr] = ad;
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const float df = warp_diff(d.obj, d.dim, zx, dz);
+            if (threadIdx.x == 0) {
+                const float fx = a.fit[d.fit_off + i];
+                take_s = df <= 0.0f ? 1 : 0;
+                fn_s = fx + df;
+            }
+        }
+        __syncthreads();
+        if (take_s) {
+            for (int j = threadIdx.x * 4; j < d.dpad; j += blockDim.x * 4)
+                *reinterpret_cast<float4*>(X + j) = *reinterpret_cast<const float4*>(U + j);
+            if (threadIdx.x == 0) a.fit[d.fit_off + i] = fn_s;
+        }
+        __syncthreads();
     }
 }
 
@@ -410,10 +457,8 @@ cudaError_t launch_tc_generation(const StepArgs& a, const TcPlan& p, cudaStream_
     k_tc_prologue<<<p.n_exec, 256, 0, st>>>(a, p.execs, p.topk_all);
     const int blocks = (p.n_rows + 7) / 8;
     size_t smem_t = (size_t)8 * p.max_dpad * sizeof(float);
-    size_t smem_s = (size_t)8 * 2 * p.max_dpad * sizeof(float);
+    size_t smem_s = (size_t)2 * p.max_dpad * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k_tc_trial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_tc_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s);
     if (e != cudaSuccess) return e;
     k_tc_trial<<<blocks, 256, smem_t, st>>>(a, p.row_exec, p.n_rows, p.topk_all, p.uscr, p.aq, p.split ? p.aq_lo : nullptr,
                                             p.kp, p.max_dpad);
@@ -432,7 +477,13 @@ cudaError_t launch_tc_generation(const StepArgs& a, const TcPlan& p, cudaStream_
     k_rot_tc<<<p.n_tiles, 128, smem_g, st>>>(p.mapA, p.mapB, p.split ? p.mapAlo : p.mapA, p.split ? p.mapBlo : p.mapB,
                                              g);
     if (gemm1) cudaEventRecord(gemm1, st);
-    k_tc_select<<<blocks, 256, smem_s, st>>>(a, p.row_exec, p.n_rows, p.uscr, p.fu, p.max_dpad);
+    e = cudaMemsetAsync(p.tie_count, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    k_tc_select<<<blocks, 256, 0, st>>>(a, p.row_exec, p.n_rows, p.uscr, p.fu, p.tie_list, p.tie_count);
+    e = cudaFuncSetAttribute(k_tc_ties, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s);
+    if (e != cudaSuccess) return e;
+    k_tc_ties<<<p.tie_ctas, 256, (size_t)2 * p.max_dpad * sizeof(float), st>>>(a, p.row_exec, p.uscr, p.tie_list,
+                                                                                p.tie_count, p.max_dpad);
     return cudaGetLastError();
 }
 
