@@ -49,7 +49,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison arm")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--inner-gens", type=int, default=INNER_GENS)
-    ap.add_argument("--workload", default="moderate", choices=["moderate", "precision"],
+    ap.add_argument("--workload", default="moderate", choices=["moderate", "precision", "batching"],
                     help="moderate: the headline workload; precision: the D=1000 precision study")
     ap.add_argument("--n-inst", type=int, default=64, help="executors of the precision study")
     return ap.parse_args(argv)
@@ -260,6 +260,10 @@ def run_ours(args):
             events[1].record(stream)
         M.metade_outer_step(batch.ctx, batch.opop, batch.ofit, batch.trial, batch.theta, batch.best_f, og, 1)
 
+    # autotune the block shapes on a real state: the first evolver generation's executors
+    M.metade_outer_step(b.ctx, b.opop, b.ofit, b.trial, b.theta, None, 0, 0)
+    M.metade_init(b.ctx, b.pop, b.fit, 0)
+    M.metade_autotune(b.ctx, b.pop, b.fit, b.theta, 20)
     og = 0
     for _ in range(args.warmup):
         step(b, og, None)
@@ -493,10 +497,70 @@ def run_precision(args):
     ref.close()
 
 
+# ------------------------------------------------------- batching study
+def run_batching(args):
+    """512 executors of uneven size (NP ~ U{20..400}, D ~ U{10,20,50,100},
+    objective ~ U{0..5}, theta sampled per executor): one step = 100
+    generations of every executor, batched path (one launch per size bucket)
+    vs plain path (one executor per launch per generation)."""
+    import numpy as np
+    import torch
+    import paper_2502_10470_gb300 as M
+    import synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    wl = synth.batching()
+    gens = wl.inner_gens
+    probs = [(p.dim, p.obj, p.shift, p.rot) for p in wl.problems]
+    units = float(wl.inst_np.sum()) * gens
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    out = {}
+    for name, path, steps in (("batched", M.METADE_PATH_BATCHED, args.steps), ("plain", M.METADE_PATH_PLAIN, 1)):
+        if name == "plain" and args.no_plain:
+            continue
+        b = M.Batch(probs, wl.inst_np, wl.inst_prob, wl.inst_group, seed=wl.seed, one_shot=0, path=path, device=dev,
+                    stream=stream.cuda_stream)
+        b.set_theta(wl.theta)
+        M.metade_init(b.ctx, b.pop, b.fit, 0)
+        if path == M.METADE_PATH_BATCHED:
+            M.metade_autotune(b.ctx, b.pop, b.fit, b.theta, 5)
+        for w in range(1 if name == "plain" else args.warmup):
+            M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, w * gens, gens, b.best_f, b.best_i)
+        torch.cuda.synchronize()
+        M.metade_profile(b.ctx, True)
+        M.metade_profile_read(b.ctx)
+        ms = []
+        for st in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, (10 + st) * gens, gens, b.best_f, b.best_i)
+            e1.record(stream)
+            ms.append((e0, e1))
+        torch.cuda.synchronize()
+        if M.metade_sync(b.ctx) != 0:
+            raise RuntimeError("device status")
+        prof = M.metade_profile_read(b.ctx)
+        t = float(np.mean([a.elapsed_time(c) for a, c in ms]))
+        out[name] = {"ms_per_step": t, "indiv_gens_per_s": units / (t / 1e3), "steps": steps,
+                     "kernels_ms_per_step": {k: v[0] / steps for k, v in prof.items() if v[1]},
+                     "plan": json.loads(M.metade_plan_info(b.ctx))}
+        b.close()
+    line = {"metric": "batching study: individual-gens/s, batched vs plain FP32", "workload": wl.name,
+            "executors": wl.n_inst, "individuals": wl.individuals(), "generations_per_step": gens,
+            "results": out, "speedup_vs_plain": (out["batched"]["indiv_gens_per_s"] / out["plain"]["indiv_gens_per_s"])
+            if "plain" in out else None, "l2": "flushed before every timed step"}
+    print(json.dumps(line), flush=True)
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.workload == "precision":
         run_precision(args)
+        return
+    if args.workload == "batching":
+        run_batching(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -218,6 +218,16 @@ METADE_API metade_status metade_plain_step_noalloc(float *pop, float *fit, const
 /* Wait for the context's stream; return and clear the sticky device status. */
 METADE_API metade_status metade_sync(metade_ctx *ctx);
 
+/* Autotuner: for every bucket of the batched path, time each candidate block
+ * shape (small-D kernel: 32, 64, 128, 256 threads; general kernel: 128, 256,
+ * 512 threads) on device copies of (pop, fit) for n_gens generations with the
+ * given theta, and keep the fastest.  The caller's pop/fit are not modified;
+ * the copies are allocated and freed inside the call, which synchronises the
+ * stream.  The measured times are reported by metade_plan_info.  No-op on
+ * the plain path. */
+METADE_API metade_status metade_autotune(metade_ctx *ctx, const float *pop, const float *fit, const float *theta,
+                                         int32_t n_gens);
+
 /* Write a one-line JSON description of the launch plan into buf. */
 METADE_API metade_status metade_plan_info(const metade_ctx *ctx, char *buf, size_t len);
 

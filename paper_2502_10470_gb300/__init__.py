@@ -30,7 +30,7 @@ EXPORTED = [
     "metade_init", "metade_inner_step", "metade_eval", "metade_outer_init", "metade_outer_step",
     "metade_outer_generation", "metade_draw_record", "metade_sync", "metade_plan_info",
     "metade_launch_count", "metade_strerror", "metade_plain_step_noalloc", "metade_profile",
-    "metade_profile_read",
+    "metade_profile_read", "metade_autotune",
 ]
 
 
@@ -96,6 +96,7 @@ def _lib():
         L.metade_plain_step_noalloc.argtypes = [P, P, P, P, P, I32, I32, I32, C.c_float, C.c_float, C.c_uint64,
                                                 U32, U32, U32, I32, P]
         L.metade_profile.argtypes = [P, I32]
+        L.metade_autotune.argtypes = [P, P, P, P, I32]
         L.metade_profile_read.argtypes = [P, P, P]
         L.metade_strerror.argtypes = [C.c_int]
         L.metade_strerror.restype = C.c_char_p
@@ -236,6 +237,10 @@ def metade_plain_step_noalloc(pop, fit, theta, shift, rot, np_: int, dim: int, o
                                             obj, lo, hi, seed, stream_id, epoch, gen, p_best_pct, stream)
 
 
+def metade_autotune(ctx: int, pop, fit, theta, n_gens: int = 3) -> None:
+    _check(_lib().metade_autotune(ctx, _ptr(pop), _ptr(fit), _ptr(theta), n_gens), "metade_autotune")
+
+
 PROFILE_KINDS = ["fused_small", "fused_general", "tc_gemm", "tc_generation"]
 
 
@@ -339,3 +344,20 @@ class Batch:
         s = metade_sync(self.ctx)
         if s != METADE_OK:
             raise MetadeError(s, "device status")
+
+    def run_metade(self, outer_gens: int, inner_gens: int, power_up: bool = False, use_graph: bool = True):
+        """Alg. 3: evolver initialisation, then `outer_gens` evolver generations
+        (trials and decoding, executor runs, selection), each one call of
+        metade_outer_generation.  With power_up the last generation gives the
+        executors 5x the inner generations (Sec. III-D).  Returns the evolver
+        population [n_groups, n_out, 6] and fitness [n_groups, n_out]."""
+        if not self.n_out:
+            raise MetadeError(METADE_ESTATE, "run_metade needs an evolver (n_out > 0)")
+        metade_outer_init(self.ctx, self.opop, self.ofit)
+        for g in range(outer_gens):
+            n = 5 * inner_gens if (power_up and g == outer_gens - 1) else inner_gens
+            metade_outer_generation(self.ctx, self.opop, self.ofit, self.trial, self.theta, self.pop, self.fit,
+                                    self.best_f, self.best_i, g, n, use_graph)
+        self.sync()
+        return (self.opop.cpu().numpy().reshape(self.n_groups, self.n_out, 6),
+                self.ofit.cpu().numpy().reshape(self.n_groups, self.n_out))

@@ -23,6 +23,7 @@ constexpr size_t kSmemLimit = 227 * 1024;
 struct Bucket {
     FusedPlan plan;
     int work_off, n_work;
+    std::string tuned;  // autotuner record: candidate threads -> ms
 };
 
 enum ProfKind { kProfFusedSmall = 0, kProfFusedGeneral = 1, kProfTcGemm = 2, kProfTcGeneration = 3, kProfKinds = 4 };
@@ -705,6 +706,63 @@ metade_status metade_sync(metade_ctx* c) {
     return (metade_status)s;
 }
 
+metade_status metade_autotune(metade_ctx* c, const float* pop, const float* fit, const float* theta, int32_t n_gens) {
+    if (!c || n_gens < 1 || (c->n_inst > 0 && (!pop || !fit || !theta))) return METADE_EINVAL;
+    if (c->path != METADE_PATH_BATCHED || c->buckets.empty()) return METADE_OK;
+    float* tpop = nullptr;
+    float* tfit = nullptr;
+    if (dalloc(&tpop, (size_t)c->pop_floats) || dalloc(&tfit, (size_t)c->n_indiv)) {
+        cudaFree(tpop);
+        return METADE_ENOMEM;
+    }
+    cudaEvent_t e0, e1;
+    metade_status st = METADE_OK;
+    if (cudaEventCreate(&e0) || cudaEventCreate(&e1)) st = METADE_ECUDA;
+    for (Bucket& b : c->buckets) {
+        if (st != METADE_OK) break;
+        std::vector<int> cands = b.plan.kind == 0 ? std::vector<int>{32, 64, 128, 256}
+                                                  : std::vector<int>{128, 256, 512};
+        FusedPlan best = b.plan;
+        float best_ms = -1.f;
+        b.tuned.clear();
+        for (int th : cands) {
+            FusedPlan p = b.plan;
+            p.threads = th;
+            if (p.kind == 1) {
+                p.rot_smem = fused_smem_general(p.max_np, p.max_dpad, th, true) <= kSmemLimit ? 1 : 0;
+                p.smem = fused_smem_general(p.max_np, p.max_dpad, th, p.rot_smem != 0);
+                if (p.smem > kSmemLimit) continue;
+            } else if (th < 32) {
+                continue;
+            }
+            StepArgs a = step_args(c, tpop, tfit, theta, 0, nullptr, 0, n_gens, nullptr, nullptr);
+            if (cudaMemcpyAsync(tpop, pop, sizeof(float) * (size_t)c->pop_floats, cudaMemcpyDeviceToDevice, c->st) ||
+                cudaMemcpyAsync(tfit, fit, sizeof(float) * (size_t)c->n_indiv, cudaMemcpyDeviceToDevice, c->st) ||
+                cudaEventRecord(e0, c->st) || launch_fused(a, c->work + b.work_off, b.n_work, p, c->uscr, c->st) ||
+                cudaEventRecord(e1, c->st) || cudaEventSynchronize(e1)) {
+                st = METADE_ECUDA;
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            char tmp[64];
+            snprintf(tmp, sizeof(tmp), "%s\"%d\": %.4f", b.tuned.empty() ? "" : ", ", th, ms);
+            b.tuned += tmp;
+            if (best_ms < 0.f || ms < best_ms) {
+                best_ms = ms;
+                best = p;
+            }
+        }
+        b.plan = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(tpop);
+    cudaFree(tfit);
+    if (st == METADE_OK && cudaMemset(c->status, 0, sizeof(int))) st = METADE_ECUDA;
+    return st;
+}
+
 metade_status metade_plan_info(const metade_ctx* c, char* buf, size_t len) {
     if (!c || !buf || len == 0) return METADE_EINVAL;
     std::string s = "{\"path\": \"";
@@ -715,10 +773,12 @@ metade_status metade_plan_info(const metade_ctx* c, char* buf, size_t len) {
         char tmp[256];
         snprintf(tmp, sizeof(tmp),
                  "%s{\"kernel\": \"%s\", \"dmax\": %d, \"threads\": %d, \"grid\": %d, \"smem\": %zu, "
-                 "\"rot_smem\": %d, \"executors\": %d}",
+                 "\"rot_smem\": %d, \"executors\": %d",
                  b ? ", " : "", k.plan.kind == 0 ? "fused_small" : "fused_general", k.plan.dmax, k.plan.threads,
                  k.plan.grid, k.plan.smem, k.plan.rot_smem, k.n_work);
         s += tmp;
+        if (!k.tuned.empty()) s += ", \"autotune_ms\": {" + k.tuned + "}";
+        s += "}";
     }
     s += "]";
     if (c->tc) {

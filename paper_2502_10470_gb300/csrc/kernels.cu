@@ -572,7 +572,7 @@ size_t fused_smem_small(int dmax, int max_np) {
 // ---------------------------------------------- batched path, general D
 // Shared layout: f[np], fu[np], topk[np], red[64], R^T [dim][dpad] (optional),
 // then per warp 4 * max_dpad floats (float trial buffers or double tie buffers).
-__global__ void __launch_bounds__(256) k_fused_general(StepArgs a, const int* __restrict__ work, int n_work,
+__global__ void __launch_bounds__(512) k_fused_general(StepArgs a, const int* __restrict__ work, int n_work,
                                                        float* uscr, int rot_smem, int max_np, int max_dpad) {
     extern __shared__ __align__(16) float sm[];
     const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nt >> 5;

@@ -6,6 +6,8 @@ genes; FP32 trial coordinates within TRIAL_ATOL; FP32 fitness within 1e-5
 relative of the FP64 value at the same point; selection bits equal wherever
 the fitness gap exceeds the FP32 tolerance.
 """
+import json
+
 import numpy as np
 import pytest
 
@@ -405,3 +407,32 @@ def test_near_tie_decisions_match_fp64(tie_fp64, path):
         checked += int(tie.sum())
     b.close()
     assert checked > 200
+
+
+def test_autotune_changes_speed_not_results():
+    """The autotuner only picks block shapes; every individual's arithmetic
+    and every reduction's tie-breaking are independent of them, so results
+    are bit-identical before and after tuning."""
+    import paper_2502_10470_gb300 as M
+    wl = _ragged_many()
+    outs = []
+    for tune in (False, True):
+        b = make_batch(wl, 0)
+        pops, fits = random_state(wl, seed=2)
+        b.set_population(pops, fits)
+        b.set_theta(wl.theta)
+        if tune:
+            M.metade_autotune(b.ctx, b.pop, b.fit, b.theta, 2)
+            info = json.loads(M.metade_plan_info(b.ctx))
+            assert all("autotune_ms" in bk for bk in info["buckets"])
+            # tuning used copies: the caller's state is untouched
+            p2, f2 = b.get_population()
+            for k in range(wl.n_inst):
+                np.testing.assert_array_equal(p2[k], pops[k])
+        M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 3, 4, b.best_f, b.best_i)
+        b.sync()
+        outs.append(b.get_population())
+        b.close()
+    for k in range(wl.n_inst):
+        np.testing.assert_array_equal(outs[0][0][k], outs[1][0][k])
+        np.testing.assert_array_equal(outs[0][1][k], outs[1][1][k])
