@@ -236,8 +236,9 @@ METADE_API metade_status metade_plan_info(const metade_ctx *ctx, char *buf, size
  * each launch of the fused kernels and the tensor-core stage.  Reading waits
  * for the stream and returns, per kind, the summed milliseconds and the number
  * of launches since the last read -- kinds: 0 fused small-D kernel, 1 fused
- * general kernel, 2 tensor-core rotation GEMM, 3 whole tensor-core generation
- * -- then clears them.  ms and count are host arrays of 4 (may be NULL). */
+ * general kernel, 2 tensor-core rotation GEMM, 3 whole tensor-core generation,
+ * 4 fused group kernel
+ * -- then clears them.  ms and count are host arrays of 5 (may be NULL). */
 METADE_API metade_status metade_profile(metade_ctx *ctx, int32_t enable);
 METADE_API metade_status metade_profile_read(metade_ctx *ctx, double *ms, int64_t *count);
 

@@ -241,7 +241,7 @@ def metade_autotune(ctx: int, pop, fit, theta, n_gens: int = 3) -> None:
     _check(_lib().metade_autotune(ctx, _ptr(pop), _ptr(fit), _ptr(theta), n_gens), "metade_autotune")
 
 
-PROFILE_KINDS = ["fused_small", "fused_general", "tc_gemm", "tc_generation"]
+PROFILE_KINDS = ["fused_small", "fused_general", "tc_gemm", "tc_generation", "fused_group"]
 
 
 def metade_profile(ctx: int, enable: bool) -> None:
@@ -250,8 +250,8 @@ def metade_profile(ctx: int, enable: bool) -> None:
 
 def metade_profile_read(ctx: int):
     """{kind: (milliseconds, launches)} since the last read."""
-    ms = np.zeros(4, dtype=np.float64)
-    n = np.zeros(4, dtype=np.int64)
+    ms = np.zeros(len(PROFILE_KINDS), dtype=np.float64)
+    n = np.zeros(len(PROFILE_KINDS), dtype=np.int64)
     _check(_lib().metade_profile_read(ctx, ms.ctypes.data, n.ctypes.data), "metade_profile_read")
     return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(PROFILE_KINDS)}
 

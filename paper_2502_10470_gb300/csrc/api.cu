@@ -26,7 +26,14 @@ struct Bucket {
     std::string tuned;  // autotuner record: candidate threads -> ms
 };
 
-enum ProfKind { kProfFusedSmall = 0, kProfFusedGeneral = 1, kProfTcGemm = 2, kProfTcGeneration = 3, kProfKinds = 4 };
+enum ProfKind {
+    kProfFusedSmall = 0,
+    kProfFusedGeneral = 1,
+    kProfTcGemm = 2,
+    kProfTcGeneration = 3,
+    kProfFusedGroup = 4,
+    kProfKinds = 5
+};
 
 struct ProfRec {
     int kind;
@@ -134,13 +141,15 @@ double work_cost(const InstDesc& d) { return (double)d.np * ((double)d.dim * d.d
 // Kernel kind per executor and the work order inside each bucket (largest
 // first, so the block scheduler hands the longest executors out first).
 metade_status build_plan(metade_ctx* c) {
-    std::vector<std::vector<int>> small(33);
+    std::vector<std::vector<int>> small(33), group(9);
     std::vector<int> general;
     for (int k = 0; k < c->n_inst; ++k) {
         if (c->tc && c->is_tc[k]) continue;
         const InstDesc& d = c->hdesc[k];
         const int dm = small_dmax_for(d.dim);
+        const int S = group_lanes_for(d.dpad);
         if (dm > 0 && fused_smem_small(dm, d.np) <= kSmemLimit) small[dm].push_back(k);
+        else if (S > 0 && fused_smem_group(d.np, d.dpad, 128, false) <= kSmemLimit) group[S].push_back(k);
         else general.push_back(k);
     }
     std::vector<int> order;
@@ -160,11 +169,36 @@ metade_status build_plan(metade_ctx* c) {
         b.plan.grid = (int)small[dm].size();
         b.plan.smem = fused_smem_small(dm, mnp);
         b.plan.rot_smem = 0;
+        b.plan.pop_smem = 1;
         b.plan.max_np = mnp;
         b.plan.max_dpad = dm;
         b.work_off = (int)order.size();
         b.n_work = (int)small[dm].size();
         order.insert(order.end(), small[dm].begin(), small[dm].end());
+        c->buckets.push_back(b);
+    }
+    for (int S = 2; S <= 8; S <<= 1) {
+        if (group[S].empty()) continue;
+        sort_desc(group[S]);
+        int mnp = 0, mdp = 0;
+        for (int k : group[S]) {
+            mnp = std::max(mnp, c->hdesc[k].np);
+            mdp = std::max(mdp, c->hdesc[k].dpad);
+        }
+        Bucket b;
+        b.plan.kind = 2;
+        b.plan.dmax = S;
+        b.plan.threads = std::min(512, std::max(128, (mnp * S + 31) / 32 * 32));
+        b.plan.grid = (int)group[S].size();
+        b.plan.max_np = mnp;
+        b.plan.max_dpad = mdp;
+        b.plan.pop_smem = fused_smem_group(mnp, mdp, b.plan.threads, false, true) <= kSmemLimit ? 1 : 0;
+        b.plan.rot_smem = fused_smem_group(mnp, mdp, b.plan.threads, true, b.plan.pop_smem != 0) <= kSmemLimit ? 1 : 0;
+        b.plan.smem = fused_smem_group(mnp, mdp, b.plan.threads, b.plan.rot_smem != 0, b.plan.pop_smem != 0);
+        if (b.plan.smem > kSmemLimit) return METADE_EUNSUPPORTED;
+        b.work_off = (int)order.size();
+        b.n_work = (int)group[S].size();
+        order.insert(order.end(), group[S].begin(), group[S].end());
         c->buckets.push_back(b);
     }
     if (!general.empty()) {
@@ -182,6 +216,7 @@ metade_status build_plan(metade_ctx* c) {
         b.plan.max_np = mnp;
         b.plan.max_dpad = mdp;
         b.plan.rot_smem = fused_smem_general(mnp, mdp, 256, true) <= kSmemLimit ? 1 : 0;
+        b.plan.pop_smem = 0;
         b.plan.smem = fused_smem_general(mnp, mdp, 256, b.plan.rot_smem != 0);
         if (b.plan.smem > kSmemLimit) return METADE_EUNSUPPORTED;
         b.work_off = (int)order.size();
@@ -232,7 +267,10 @@ metade_status run_inner(metade_ctx* c, cudaStream_t st, float* pop, float* fit, 
     StepArgs a = step_args(c, pop, fit, theta, epoch, epoch_dev, gen0, n_gens, best_f, best_i);
     for (const Bucket& b : c->buckets) {
         cudaEvent_t e0, e1;
-        const bool pr = prof_pair(c, st, b.plan.kind == 0 ? kProfFusedSmall : kProfFusedGeneral, &e0, &e1);
+        const bool pr = prof_pair(c, st,
+                                  b.plan.kind == 0 ? kProfFusedSmall
+                                                   : (b.plan.kind == 2 ? kProfFusedGroup : kProfFusedGeneral),
+                                  &e0, &e1);
         if (pr) cudaEventRecord(e0, st);
         CK(launch_fused(a, c->work + b.work_off, b.n_work, b.plan, c->uscr, st));
         if (pr) cudaEventRecord(e1, st);
@@ -722,6 +760,7 @@ metade_status metade_autotune(metade_ctx* c, const float* pop, const float* fit,
         if (st != METADE_OK) break;
         std::vector<int> cands = b.plan.kind == 0 ? std::vector<int>{32, 64, 128, 256}
                                                   : std::vector<int>{128, 256, 512};
+        if (b.plan.kind == 2 && b.plan.max_np * b.plan.dmax <= 256) cands = {64, 128, 256};
         FusedPlan best = b.plan;
         float best_ms = -1.f;
         b.tuned.clear();
@@ -731,6 +770,9 @@ metade_status metade_autotune(metade_ctx* c, const float* pop, const float* fit,
             if (p.kind == 1) {
                 p.rot_smem = fused_smem_general(p.max_np, p.max_dpad, th, true) <= kSmemLimit ? 1 : 0;
                 p.smem = fused_smem_general(p.max_np, p.max_dpad, th, p.rot_smem != 0);
+                if (p.smem > kSmemLimit) continue;
+            } else if (p.kind == 2) {
+                p.smem = fused_smem_group(p.max_np, p.max_dpad, th, p.rot_smem != 0, p.pop_smem != 0);
                 if (p.smem > kSmemLimit) continue;
             } else if (th < 32) {
                 continue;
@@ -773,9 +815,11 @@ metade_status metade_plan_info(const metade_ctx* c, char* buf, size_t len) {
         char tmp[256];
         snprintf(tmp, sizeof(tmp),
                  "%s{\"kernel\": \"%s\", \"dmax\": %d, \"threads\": %d, \"grid\": %d, \"smem\": %zu, "
-                 "\"rot_smem\": %d, \"executors\": %d",
-                 b ? ", " : "", k.plan.kind == 0 ? "fused_small" : "fused_general", k.plan.dmax, k.plan.threads,
-                 k.plan.grid, k.plan.smem, k.plan.rot_smem, k.n_work);
+                 "\"rot_smem\": %d, \"pop_smem\": %d, \"executors\": %d",
+                 b ? ", " : "",
+                 k.plan.kind == 0 ? "fused_small" : (k.plan.kind == 2 ? "fused_group" : "fused_general"), k.plan.dmax,
+                 k.plan.threads,
+                 k.plan.grid, k.plan.smem, k.plan.rot_smem, k.plan.pop_smem, k.n_work);
         s += tmp;
         if (!k.tuned.empty()) s += ", \"autotune_ms\": {" + k.tuned + "}";
         s += "}";
@@ -806,8 +850,8 @@ metade_status metade_profile(metade_ctx* c, int32_t enable) {
 metade_status metade_profile_read(metade_ctx* c, double* ms, int64_t* count) {
     if (!c) return METADE_EINVAL;
     CK(cudaStreamSynchronize(c->st));
-    double tot[kProfKinds] = {0, 0, 0, 0};
-    int64_t n[kProfKinds] = {0, 0, 0, 0};
+    double tot[kProfKinds] = {0, 0, 0, 0, 0};
+    int64_t n[kProfKinds] = {0, 0, 0, 0, 0};
     for (auto& r : c->prof) {
         float t = 0.f;
         if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {

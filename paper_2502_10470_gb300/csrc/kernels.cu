@@ -706,6 +706,7 @@ cudaError_t launch_fused(const StepArgs& a, const int* work, int n_work, const F
         default: return cudaErrorInvalidValue;
         }
     }
+    if (p.kind == 2) return launch_fused_group(a, work, n_work, p, uscr, st);
     cudaError_t e = cudaFuncSetAttribute(k_fused_general, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
     if (e != cudaSuccess) return e;
     k_fused_general<<<p.grid, p.threads, p.smem, st>>>(a, work, n_work, uscr, p.rot_smem, p.max_np, p.max_dpad);
