@@ -135,15 +135,16 @@ METADE_API metade_status metade_init(metade_ctx *ctx, float *pop, float *fit, ui
  * vectors of distinct random individuals (Eq. of Sec. III-A-2), binomial /
  * exponential / arithmetic crossover (Sec. II-A), clip to the box, FP32
  * shifted-rotated evaluation, and generational greedy selection f(u) <= f(x).
- * Selection ties, |f(u) - f(x)| <= 1e-6 |f(x)| with both values positive and
- * finite, are decided on the difference f(u) - f(x) evaluated directly in FP32
- * from z = R(x - o) and dz = R(u - x) (error proportional to the difference,
- * not to f), or, with cfg.tie_fp64, by re-evaluating both vectors in FP64; an
- * accepted tie stores f(x) + difference (resp. the FP64 value), never above
- * f(x).  A trial identical to its target is accepted without re-evaluation.
- * pop/fit are updated in place.  If best_f /
- * best_i are non-NULL they receive each executor's best fitness and its
- * index after the last generation (Sec. III-B: the executor's y*).
+ * Selection ties, |f(u) - f(x)| <= band |f(x)| with both values positive and
+ * finite and band = max(1e-6, 2^-21 sqrt(D)) (the 1e-6 band, widened where the
+ * FP32 error of f grows with D), are decided on the difference f(u) - f(x)
+ * evaluated directly in FP32 from z = R(x - o) and dz = R(u - x) (error
+ * proportional to the difference, not to f), or, with cfg.tie_fp64, by
+ * re-evaluating both vectors in FP64; an accepted tie stores f(x) + difference
+ * (resp. the FP64 value), never above f(x).  A trial identical to its target
+ * is accepted without re-evaluation.  pop/fit are updated in place.  If
+ * best_f / best_i are non-NULL they receive each executor's best fitness and
+ * its index after the last generation (Sec. III-B: the executor's y*).
  * theta: device [n_inst][6].  n_gens == 0 only writes best_f/best_i. */
 METADE_API metade_status metade_inner_step(metade_ctx *ctx, float *pop, float *fit, const float *theta,
                                 uint32_t epoch, uint32_t gen0, int32_t n_gens, float *best_f,
@@ -237,8 +238,8 @@ METADE_API metade_status metade_plan_info(const metade_ctx *ctx, char *buf, size
  * for the stream and returns, per kind, the summed milliseconds and the number
  * of launches since the last read -- kinds: 0 fused small-D kernel, 1 fused
  * general kernel, 2 tensor-core rotation GEMM, 3 whole tensor-core generation,
- * 4 fused group kernel
- * -- then clears them.  ms and count are host arrays of 5 (may be NULL). */
+ * 4 fused group kernel, 5 fused tile kernel -- then clears them.  ms and count
+ * are host arrays of 6 (may be NULL). */
 METADE_API metade_status metade_profile(metade_ctx *ctx, int32_t enable);
 METADE_API metade_status metade_profile_read(metade_ctx *ctx, double *ms, int64_t *count);
 

@@ -32,7 +32,8 @@ enum ProfKind {
     kProfTcGemm = 2,
     kProfTcGeneration = 3,
     kProfFusedGroup = 4,
-    kProfKinds = 5
+    kProfFusedTile = 5,
+    kProfKinds = 6
 };
 
 struct ProfRec {
@@ -142,14 +143,18 @@ double work_cost(const InstDesc& d) { return (double)d.np * ((double)d.dim * d.d
 // first, so the block scheduler hands the longest executors out first).
 metade_status build_plan(metade_ctx* c) {
     std::vector<std::vector<int>> small(33), group(9);
-    std::vector<int> general;
+    std::vector<int> general, tile;
     for (int k = 0; k < c->n_inst; ++k) {
         if (c->tc && c->is_tc[k]) continue;
         const InstDesc& d = c->hdesc[k];
         const int dm = small_dmax_for(d.dim);
         const int S = group_lanes_for(d.dpad);
+        // The tile and group kernels decide near ties by the FP32 difference
+        // form only; FP64 tie re-evaluation runs in the small and general kernels.
+        const bool fp32_ties = !c->tie_fp64;
         if (dm > 0 && fused_smem_small(dm, d.np) <= kSmemLimit) small[dm].push_back(k);
-        else if (S > 0 && fused_smem_group(d.np, d.dpad, 128, false) <= kSmemLimit) group[S].push_back(k);
+        else if (fp32_ties && d.dpad <= 128 && fused_smem_tile(d.np, d.dpad, 256) <= kSmemLimit) tile.push_back(k);
+        else if (fp32_ties && S > 0 && fused_smem_group(d.np, d.dpad, 128, false) <= kSmemLimit) group[S].push_back(k);
         else general.push_back(k);
     }
     std::vector<int> order;
@@ -175,6 +180,29 @@ metade_status build_plan(metade_ctx* c) {
         b.work_off = (int)order.size();
         b.n_work = (int)small[dm].size();
         order.insert(order.end(), small[dm].begin(), small[dm].end());
+        c->buckets.push_back(b);
+    }
+    if (!tile.empty()) {
+        sort_desc(tile);
+        int mnp = 0, mdp = 0;
+        for (int k : tile) {
+            mnp = std::max(mnp, c->hdesc[k].np);
+            mdp = std::max(mdp, c->hdesc[k].dpad);
+        }
+        Bucket b;
+        b.plan.kind = 3;
+        b.plan.dmax = 0;
+        b.plan.threads = 256;
+        b.plan.grid = (int)tile.size();
+        b.plan.max_np = mnp;
+        b.plan.max_dpad = mdp;
+        b.plan.rot_smem = 1;
+        b.plan.pop_smem = 0;
+        b.plan.smem = fused_smem_tile(mnp, mdp, 256);
+        if (b.plan.smem > kSmemLimit) return METADE_EUNSUPPORTED;
+        b.work_off = (int)order.size();
+        b.n_work = (int)tile.size();
+        order.insert(order.end(), tile.begin(), tile.end());
         c->buckets.push_back(b);
     }
     for (int S = 2; S <= 8; S <<= 1) {
@@ -268,8 +296,10 @@ metade_status run_inner(metade_ctx* c, cudaStream_t st, float* pop, float* fit, 
     for (const Bucket& b : c->buckets) {
         cudaEvent_t e0, e1;
         const bool pr = prof_pair(c, st,
-                                  b.plan.kind == 0 ? kProfFusedSmall
-                                                   : (b.plan.kind == 2 ? kProfFusedGroup : kProfFusedGeneral),
+                                  b.plan.kind == 0   ? kProfFusedSmall
+                                  : b.plan.kind == 2 ? kProfFusedGroup
+                                  : b.plan.kind == 3 ? kProfFusedTile
+                                                     : kProfFusedGeneral,
                                   &e0, &e1);
         if (pr) cudaEventRecord(e0, st);
         CK(launch_fused(a, c->work + b.work_off, b.n_work, b.plan, c->uscr, st));
@@ -585,6 +615,8 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
         t.kp = tc_kp;
         t.split = split ? 1 : 0;
         t.max_dpad = tc_max_dpad;
+        // FP64 tie re-evaluation keeps two FP64 rows of max_dpad in shared memory
+        if (c->tie_fp64 && (size_t)2 * tc_max_dpad * sizeof(double) > kSmemLimit) return fail(METADE_EUNSUPPORTED);
         if (!tc_make_map(&t.mapA, c->aq, (long long)nrows, tc_kp, 128) ||
             !tc_make_map(&t.mapB, c->bq, tc_brows, tc_kp, 256) ||
             (split && (!tc_make_map(&t.mapAlo, c->aq_lo, (long long)nrows, tc_kp, 128) ||
@@ -761,6 +793,7 @@ metade_status metade_autotune(metade_ctx* c, const float* pop, const float* fit,
         std::vector<int> cands = b.plan.kind == 0 ? std::vector<int>{32, 64, 128, 256}
                                                   : std::vector<int>{128, 256, 512};
         if (b.plan.kind == 2 && b.plan.max_np * b.plan.dmax <= 256) cands = {64, 128, 256};
+        if (b.plan.kind == 3) cands = {128, 256};
         FusedPlan best = b.plan;
         float best_ms = -1.f;
         b.tuned.clear();
@@ -773,6 +806,9 @@ metade_status metade_autotune(metade_ctx* c, const float* pop, const float* fit,
                 if (p.smem > kSmemLimit) continue;
             } else if (p.kind == 2) {
                 p.smem = fused_smem_group(p.max_np, p.max_dpad, th, p.rot_smem != 0, p.pop_smem != 0);
+                if (p.smem > kSmemLimit) continue;
+            } else if (p.kind == 3) {
+                p.smem = fused_smem_tile(p.max_np, p.max_dpad, th);
                 if (p.smem > kSmemLimit) continue;
             } else if (th < 32) {
                 continue;
@@ -817,7 +853,11 @@ metade_status metade_plan_info(const metade_ctx* c, char* buf, size_t len) {
                  "%s{\"kernel\": \"%s\", \"dmax\": %d, \"threads\": %d, \"grid\": %d, \"smem\": %zu, "
                  "\"rot_smem\": %d, \"pop_smem\": %d, \"executors\": %d",
                  b ? ", " : "",
-                 k.plan.kind == 0 ? "fused_small" : (k.plan.kind == 2 ? "fused_group" : "fused_general"), k.plan.dmax,
+                 k.plan.kind == 0   ? "fused_small"
+                 : k.plan.kind == 2 ? "fused_group"
+                 : k.plan.kind == 3 ? "fused_tile"
+                                    : "fused_general",
+                 k.plan.dmax,
                  k.plan.threads,
                  k.plan.grid, k.plan.smem, k.plan.rot_smem, k.plan.pop_smem, k.n_work);
         s += tmp;
@@ -850,8 +890,8 @@ metade_status metade_profile(metade_ctx* c, int32_t enable) {
 metade_status metade_profile_read(metade_ctx* c, double* ms, int64_t* count) {
     if (!c) return METADE_EINVAL;
     CK(cudaStreamSynchronize(c->st));
-    double tot[kProfKinds] = {0, 0, 0, 0, 0};
-    int64_t n[kProfKinds] = {0, 0, 0, 0, 0};
+    double tot[kProfKinds] = {0, 0, 0, 0, 0, 0};
+    int64_t n[kProfKinds] = {0, 0, 0, 0, 0, 0};
     for (auto& r : c->prof) {
         float t = 0.f;
         if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {

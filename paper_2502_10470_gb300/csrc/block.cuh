@@ -227,6 +227,28 @@ __device__ __forceinline__ void warp_rotate_pair(int dim, const float* RT, int l
     }
 }
 
+// z = R (x - o) and dz = R (u - x) by one warp with the two operand vectors
+// staged in shared memory first (coalesced row reads, then broadcast reads in
+// the rotation).  buf: 4 * ldb floats of shared scratch; z and dz are left
+// in buf + 2 ldb and buf + 3 ldb.
+__device__ __forceinline__ void warp_rotate_pair_staged(int dim, const float* RT, int ldr, const float* x,
+                                                        const float* u, const float* o, float* buf, int ldb) {
+    const int lane = threadIdx.x & 31;
+    float* dx = buf;
+    float* dl = buf + ldb;
+    const int d4 = (dim + 3) & ~3;
+    for (int j = lane; j < d4; j += 32) {
+        const bool in = j < dim;
+        const float xv = in ? x[j] : 0.f;
+        dx[j] = in ? xv - o[j] : 0.f;
+        dl[j] = in ? u[j] - xv : 0.f;
+    }
+    __syncwarp();
+    warp_rotate<float>(dim, RT, ldr, dx, buf + 2 * ldb);
+    warp_rotate<float>(dim, RT, ldr, dl, buf + 3 * ldb);
+    __syncwarp();
+}
+
 // f(u) - f(x) from z, dz (shared) by one warp; same difference forms as the
 // streaming DiffAcc.  Every lane returns the value.
 __device__ __forceinline__ float warp_diff(int obj, int dim, const float* z, const float* dz) {

@@ -539,13 +539,21 @@ __device__ __forceinline__ float diff_seq(int obj, int dim, int ldr, const float
     return diff_finish(obj, a, dim);
 }
 
-// Selection ties: |f(u) - f(x)| <= 1e-6 |f(x)| with both values finite and
-// positive are decided by an FP64 re-evaluation (the band is relative: FP32
-// resolves f to ~1e-7 relative at any magnitude, and an absolute floor would
-// send every trial of a converged executor down the FP64 path).  Values that
-// underflowed to 0 compare as equal and the trial wins.
-__device__ __forceinline__ bool near_tie(float fu, float fx) {
-    return isfinite(fu) && isfinite(fx) && fx > 0.0f && fu > 0.0f && fabsf(fu - fx) <= 1e-6f * fx;
+// Selection ties: |f(u) - f(x)| <= band |f(x)| with both values finite and
+// positive are decided by the FP32 difference form or an FP64 re-evaluation,
+// not by the two FP32 values.  band(D) = max(1e-6, 2^-21 sqrt(D)): the 1e-6
+// band of the requirement, widened where the FP32 error of f itself grows
+// like sqrt(D) ulps (at D = 200 Schwefel 1.2 reaches 1.8e-6 relative, about
+// 2 sqrt(D) ulps; 2^-21 sqrt(D) = 8 sqrt(D) ulps leaves a factor of four).
+// The band is relative: FP32 resolves f to a fixed relative precision at any
+// magnitude, and an absolute floor would send every trial of a converged
+// executor down the tie path.  Values that underflowed to 0 compare as equal
+// and the trial wins.
+__host__ __device__ __forceinline__ float tie_band(int dim) {
+    return fmaxf(1e-6f, 4.76837158203125e-7f * sqrtf((float)dim));
+}
+__device__ __forceinline__ bool near_tie(float fu, float fx, float band) {
+    return isfinite(fu) && isfinite(fx) && fx > 0.0f && fu > 0.0f && fabsf(fu - fx) <= band * fx;
 }
 
 // Sticky device status: the first error wins.

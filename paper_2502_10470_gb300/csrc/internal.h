@@ -54,7 +54,8 @@ cudaError_t launch_plain_generation(const StepArgs& a, int k, const InstDesc& d,
 
 // Batched path: executors listed in `work` (schedule order), all n_gens generations.
 struct FusedPlan {
-    int kind;      // 0 small (thread per individual), 1 general (warp per individual), 2 group (S lanes)
+    int kind;      // 0 small (thread per individual), 1 general (warp per individual), 2 group (S lanes),
+                   // 3 tile (register-blocked rotation GEMM per tile of individuals)
     int dmax;      // small: compile-time row bound; group: lanes per individual S
     int threads;   // block size
     int grid;      // CTAs (<= n_work; CTAs loop over work items)
@@ -72,6 +73,9 @@ int group_lanes_for(int dpad);  // 0 when the group kernel does not apply
 size_t fused_smem_group(int max_np, int max_dpad, int threads, bool rot_in_smem, bool pop_in_smem = false);
 cudaError_t launch_fused_group(const StepArgs& a, const int* work, int n_work, const FusedPlan& p, float* u_scratch,
                                cudaStream_t st);
+size_t fused_smem_tile(int max_np, int max_dpad, int threads);
+cudaError_t launch_fused_tile(const StepArgs& a, const int* work, int n_work, const FusedPlan& p, float* u_scratch,
+                              cudaStream_t st);
 
 // Large-D executors on the tensor cores (tc_rotate.cu).
 struct TcPlan {

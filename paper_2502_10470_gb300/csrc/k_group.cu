@@ -16,6 +16,7 @@
 // group min) instead of a sequential scan.  Near ties are decided in
 // selection by the group itself with the FP32 difference form.
 #include "block.cuh"
+#include "group_obj.cuh"
 #include "internal.h"
 
 namespace metade {
@@ -23,28 +24,6 @@ namespace metade {
 namespace {
 
 constexpr int kCMAX = 32;  // coordinates per lane (8 chunks)
-
-template <int S>
-__device__ __forceinline__ float gsum(float v) {
-#pragma unroll
-    for (int o = 1; o < S; o <<= 1) v += __shfl_xor_sync(kFull, v, o);
-    return v;
-}
-
-template <int S>
-__device__ __forceinline__ int gmin(int v) {
-#pragma unroll
-    for (int o = 1; o < S; o <<= 1) v = min(v, __shfl_xor_sync(kFull, v, o));
-    return v;
-}
-
-template <int S>
-__device__ __forceinline__ bool gany(bool v) {
-    unsigned x = v ? 1u : 0u;
-#pragma unroll
-    for (int o = 1; o < S; o <<= 1) x |= __shfl_xor_sync(kFull, x, o);
-    return x != 0;
-}
 
 // Butterfly reduce-scatter over a group of S lanes: on entry lane s holds
 // partial sums p[0..S) of S rows; on exit lane s returns the full sum of row
@@ -65,13 +44,6 @@ __device__ __forceinline__ float reduce_scatter(float (&p)[S], int s) {
     return p[0];
 }
 
-struct GroupObj {
-    float s0 = 0.f, s1 = 0.f;        // sums
-    float P = 1.f, Q = 0.f;          // Griewank product pair: P = prod c, Q = 1 - P
-    float pend = 0.f;                // Rosenbrock: this lane's last row waiting for its successor
-    bool has_pend = false;
-    float carry = 0.f;               // Schwefel: prefix of all previous blocks
-};
 
 // f(u) - f(x) of one individual by its group of S lanes (selection ties):
 // x - o and u - x for the lane's chunks in registers, both rotations by the
@@ -93,9 +65,7 @@ __device__ __forceinline__ float group_diff(int obj, int dim, int dp, int CH, in
             dl[4 * q + t] = in ? ui[j] - xv : 0.f;
         }
     }
-    float d0 = 0.f, d1 = 0.f, x0 = 0.f, x1 = 0.f, A = 1.f, B = 0.f;
-    float pz = 0.f, pdz = 0.f, cz = 0.f, cd = 0.f;
-    bool has_pend = false;
+    GroupDiff g;
     for (int r0 = 0; r0 < dim; r0 += S) {
         float pa[S], pb[S];
 #pragma unroll
@@ -124,94 +94,9 @@ __device__ __forceinline__ float group_diff(int obj, int dim, int dp, int CH, in
             pb[b] = zb;
         }
         const float z = reduce_scatter<S>(pa, s), dz = reduce_scatter<S>(pb, s);
-        const int r = r0 + s;
-        const bool valid = r < dim;
-        switch (obj) {
-        case kSphere:
-            if (valid) d0 += dz * (2.f * z + dz);
-            break;
-        case kRastrigin:
-            if (valid) d0 += dz * (2.f * z + dz) + 20.f * sinpif(2.f * z + dz) * sinpif(dz);
-            break;
-        case kAckley:
-            if (valid) {
-                x0 = fmaf(z, z, x0);
-                d0 += dz * (2.f * z + dz);
-                const float sz = sinpif(z);
-                x1 = fmaf(sz, sz, x1);
-                d1 += sinpif(2.f * z + dz) * sinpif(dz);
-            }
-            break;
-        case kGriewank:
-            if (valid) {
-                d0 += dz * (2.f * z + dz);
-                const float inv = rsqrtf((float)(r + 1));
-                float c;
-                const float dc = cos_step(z * inv, 0.5f * dz * inv, c);
-                B = (c + dc) * B + dc * A;
-                A *= c;
-            }
-            break;
-        case kRosenbrock: {
-            const float nz = __shfl_down_sync(kFull, z, 1, S), nd = __shfl_down_sync(kFull, dz, 1, S);
-            const float fz = __shfl_sync(kFull, z, 0, S), fd = __shfl_sync(kFull, dz, 0, S);
-            if (has_pend) {  // previous block's last row with this block's first row
-                const float t = fz - pz * (pz + 2.f);
-                const float dt = fd - pdz * (2.f * pz + 2.f + pdz);
-                d0 += 100.f * dt * (2.f * t + dt) + pdz * (2.f * pz + pdz);
-                has_pend = false;
-            }
-            if (valid && r + 1 < dim) {
-                if (s < S - 1) {
-                    const float t = nz - z * (z + 2.f);
-                    const float dt = nd - dz * (2.f * z + 2.f + dz);
-                    d0 += 100.f * dt * (2.f * t + dt) + dz * (2.f * z + dz);
-                } else {
-                    pz = z;
-                    pdz = dz;
-                    has_pend = true;
-                }
-            }
-            break;
-        }
-        default: {  // Schwefel 1.2: prefix sums of z and dz over the rows
-            float xs = valid ? z : 0.f, ys = valid ? dz : 0.f;
-#pragma unroll
-            for (int off = 1; off < S; off <<= 1) {
-                const float a2 = __shfl_up_sync(kFull, xs, off, S), b2 = __shfl_up_sync(kFull, ys, off, S);
-                if (s >= off) {
-                    xs += a2;
-                    ys += b2;
-                }
-            }
-            const float p = cz + xs, dp2 = cd + ys;
-            if (valid) d0 += dp2 * (2.f * p + dp2);
-            cz += __shfl_sync(kFull, xs, S - 1, S);
-            cd += __shfl_sync(kFull, ys, S - 1, S);
-            break;
-        }
-        }
+        group_diff_push<S>(obj, g, z, dz, r0, s, dim);
     }
-    d0 = gsum<S>(d0);
-    if (obj == kGriewank) {
-#pragma unroll
-        for (int off = 1; off < S; off <<= 1) {
-            const float A2 = __shfl_xor_sync(kFull, A, off), B2 = __shfl_xor_sync(kFull, B, off);
-            B = (A + B) * B2 + B * A2;
-            A *= A2;
-        }
-        return d0 / 4000.f - B;
-    }
-    if (obj == kAckley) {
-        d1 = gsum<S>(d1);
-        x0 = gsum<S>(x0);
-        x1 = gsum<S>(x1);
-        const float rx = sqrtf(x0 / dim), ru = sqrtf(fmaxf(x0 + d0, 0.f) / dim);
-        const float dr = (ru + rx > 0.f) ? (d0 / dim) / (ru + rx) : 0.f;
-        return -20.f * expf(-0.2f * rx) * expm1f(-0.2f * dr) -
-               2.71828182845904523536f * expf(-2.f * x1 / dim) * expm1f(-2.f * d1 / dim);
-    }
-    return d0;
+    return group_diff_finish<S>(obj, g, dim);
 }
 
 }  // namespace
@@ -239,6 +124,7 @@ __global__ void __launch_bounds__(512) k_fused_group(StepArgs a, const int* __re
             continue;
         }
         const int np = d.np, dim = d.dim, dp = d.dpad, nch = dp >> 2;
+        const float band = tie_band(dim);
         const int CH = (nch + S - 1) / S;   // chunks per lane (<= kCMAX / 4 by the planner)
         const int c0 = s * CH * 4;          // first coordinate of this lane
         const uint32_t epoch = a.epoch_dev ? *a.epoch_dev : a.epoch;
@@ -387,87 +273,9 @@ __global__ void __launch_bounds__(512) k_fused_group(StepArgs a, const int* __re
                         }
                     }
                     const float z = reduce_scatter<S>(p, s);  // full z of row r0 + s
-                    const int r = r0 + s;
-                    const bool valid = r < dim;
-                    switch (obj) {
-                    case kSphere:
-                        if (valid) acc.s0 = fmaf(z, z, acc.s0);
-                        break;
-                    case kRastrigin:
-                        if (valid) {
-                            const float sp = sinpif(z);
-                            acc.s0 += z * z + 20.f * sp * sp;
-                        }
-                        break;
-                    case kAckley:
-                        if (valid) {
-                            acc.s0 = fmaf(z, z, acc.s0);
-                            const float sp = sinpif(z);
-                            acc.s1 = fmaf(sp, sp, acc.s1);
-                        }
-                        break;
-                    case kGriewank:
-                        if (valid) {
-                            acc.s0 = fmaf(z, z, acc.s0);
-                            const float h = sinf(0.5f * z * rsqrtf((float)(r + 1)));
-                            const float wq = 2.f * h * h;
-                            acc.Q = fmaf(acc.P, wq, acc.Q);
-                            acc.P *= 1.f - wq;
-                        }
-                        break;
-                    case kRosenbrock: {
-                        // term of row j = r uses z_{j+1}: the next lane's z, or the next block's lane 0
-                        const float nxt = __shfl_down_sync(kFull, z, 1, S);
-                        const float first_next = __shfl_sync(kFull, z, 0, S);  // lane 0 of this block
-                        // the previous block's last row (held by lane S-1) pairs with this block's first row
-                        if (acc.has_pend && r0 < dim) {
-                            const float zj = acc.pend;
-                            const float t = first_next - zj * (zj + 2.f);
-                            acc.s0 += 100.f * t * t + zj * zj;
-                            acc.has_pend = false;
-                        }
-                        if (valid && r + 1 < dim) {
-                            if (s < S - 1) {
-                                const float t = nxt - z * (z + 2.f);
-                                acc.s0 += 100.f * t * t + z * z;
-                            } else {
-                                acc.pend = z;
-                                acc.has_pend = true;
-                            }
-                        }
-                        break;
-                    }
-                    default: {  // Schwefel 1.2: group inclusive scan of the block plus the carry
-                        float x = valid ? z : 0.f;
-#pragma unroll
-                        for (int off = 1; off < S; off <<= 1) {
-                            const float y = __shfl_up_sync(kFull, x, off, S);
-                            if (s >= off) x += y;
-                        }
-                        const float pfx = acc.carry + x;
-                        if (valid) acc.s0 = fmaf(pfx, pfx, acc.s0);
-                        acc.carry += __shfl_sync(kFull, x, S - 1, S);
-                        break;
-                    }
-                    }
+                    group_obj_push<S>(obj, acc, z, r0, s, dim);
                 }
-                // combine the group
-                float fval;
-                if (obj == kGriewank) {
-#pragma unroll
-                    for (int off = 1; off < S; off <<= 1) {
-                        const float P2 = __shfl_xor_sync(kFull, acc.P, off), Q2 = __shfl_xor_sync(kFull, acc.Q, off);
-                        acc.Q = acc.Q + acc.P * Q2;
-                        acc.P *= P2;
-                    }
-                    fval = gsum<S>(acc.s0) * (1.f / 4000.f) + acc.Q;
-                } else if (obj == kAckley) {
-                    const float s0 = gsum<S>(acc.s0), s1 = gsum<S>(acc.s1);
-                    fval = -20.f * expm1f(-0.2f * sqrtf(s0 / dim)) -
-                           2.71828182845904523536f * expm1f(-2.f * s1 / dim);
-                } else {
-                    fval = gsum<S>(acc.s0);
-                }
+                const float fval = group_obj_finish<S>(obj, acc, dim);
                 if (act && s == 0) fu[i] = nan_to_inf(fval);
             }
             __syncthreads();
@@ -480,7 +288,7 @@ __global__ void __launch_bounds__(512) k_fused_group(StepArgs a, const int* __re
                 const float* Ui = Ug + (long long)i * dp;
                 const float fx = f[i];
                 float fn = fu[i];
-                bool tie = near_tie(fn, fx);
+                bool tie = near_tie(fn, fx, band);
                 bool diff = false;
                 for (int q = 0; q < CH; ++q) {
                     const int j4 = c0 + 4 * q;

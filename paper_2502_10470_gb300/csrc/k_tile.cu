@@ -1,0 +1,328 @@
+// k_tile.cu -- batched path for 32 < D <= 128: k_fused_tile.
+//
+// One CTA per executor runs all fused generations.  Each generation walks
+// the population in tiles of kT individuals:
+//   trial      thread per individual for the draws (a record in shared
+//              memory), then (chunk, individual) work items for mutation,
+//              crossover and clip; the FP32 trial row goes to the scratch
+//              population, d = u - o to a k-major tile dT[k][t]
+//   rotation   Z = d R^T by 4x4 register blocks, R^T resident in shared memory
+//   objective  four lanes per individual over its Z row
+// then selection: the clear cases by a thread per individual, the near ties
+// kT / 2 at a time through the same GEMM (x - o and u - x as column pairs)
+// and the difference forms, and one coalesced pass copying accepted rows.
+#include "block.cuh"
+#include "group_obj.cuh"
+#include "internal.h"
+
+namespace metade {
+
+namespace {
+constexpr int kT = 64;        // individuals per tile
+constexpr int kTP = kT + 4;   // k-major row length of dT (float4 aligned)
+constexpr int kRec = 16;      // per-individual draw record (ints)
+
+// Z row stride: at least max_dpad and 4 (mod 32), so the eight 4-lane groups
+// of a warp that read 4 consecutive rows of 8 different Z rows hit distinct banks.
+__host__ __device__ constexpr int tile_zp(int max_dpad) { return max_dpad + ((4 - max_dpad) % 32 + 32) % 32; }
+}  // namespace
+
+// Z[t][r] = sum_k dT[k][t] R^T[k][r] for the kT columns of dT: every thread
+// owns 4x4 blocks of Z and reads one float4 of dT and one of R^T per k (16
+// FMAs per two loads); k ascends, so each z is the fma chain of every other
+// rotation in the library.
+__device__ __forceinline__ void tile_gemm(const float* dT, const float* RT, float* Z, int dim, int nbr, int dp,
+                                          int zp) {
+    constexpr int nbt = kT / 4;
+    for (int blk = threadIdx.x; blk < nbt * nbr; blk += blockDim.x) {
+        const int tx = blk % nbt, ty = blk / nbt;
+        float acc[4][4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[p][q] = 0.f;
+        const float* pa = dT + 4 * tx;
+        const float* pr = RT + 4 * ty;
+        for (int kk = 0; kk < dim; ++kk) {
+            const float4 av = *reinterpret_cast<const float4*>(pa + (size_t)kk * kTP);
+            const float4 rv = *reinterpret_cast<const float4*>(pr + (size_t)kk * dp);
+            const float ar[4] = {av.x, av.y, av.z, av.w}, rr[4] = {rv.x, rv.y, rv.z, rv.w};
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(rr[q], ar[p], acc[p][q]);
+        }
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+            *reinterpret_cast<float4*>(Z + (size_t)(4 * tx + p) * zp + 4 * ty) =
+                make_float4(acc[p][0], acc[p][1], acc[p][2], acc[p][3]);
+    }
+}
+
+// Shared words before R^T: f, fu, ranks/flags, tie list, 64 reduction words,
+// the tie count and kT / 2 identity flags; a multiple of 4 (float4 alignment).
+__host__ __device__ constexpr int tile_header_words(int max_np) { return (4 * max_np + 64 + 1 + kT / 2 + 3) & ~3; }
+
+__global__ void __launch_bounds__(256, 2) k_fused_tile(StepArgs a, const int* __restrict__ work, int n_work,
+                                                       float* uscr, int max_np, int max_dpad) {
+    extern __shared__ __align__(16) float sm[];
+    const int tid = threadIdx.x, nt = blockDim.x;  // 128 or 256 threads
+    float* f = sm;
+    float* fu = f + max_np;
+    int* topk = reinterpret_cast<int*>(fu + max_np);               // pbest ranks; selection: accept flags
+    int* tl = topk + max_np;                                       // near-tie list
+    int* red = tl + max_np;                                        // 64 words (block reductions)
+    int* ntie = red + 64;                                          // tie count, then kT / 2 identity flags
+    int* idf = ntie + 1;
+    float* RT = sm + tile_header_words(max_np);                    // [dim][dp]
+    float* dT = RT + (size_t)max_dpad * max_dpad;                  // [dp][kTP]
+    const int zp = tile_zp(max_dpad);                              // Z row length
+    float* Z = dT + (size_t)max_dpad * kTP;                        // [kT][zp]
+    int* recs = reinterpret_cast<int*>(Z);                         // [kT][kRec], dead before Z is written
+    int* acc = topk;
+    for (int w = blockIdx.x; w < n_work; w += gridDim.x) {
+        const int k = work[w];
+        const InstDesc d = a.desc[k];
+        const Strat st = load_strat(a.theta + 6 * k, d.np);
+        if (!st.ok) {
+            if (tid == 0) set_status(a.status, 1);
+            continue;
+        }
+        const int np = d.np, dim = d.dim, dp = d.dpad, nbr = dp >> 2;
+        const float band = tie_band(dim);
+        const uint32_t epoch = a.epoch_dev ? *a.epoch_dev : a.epoch;
+        float* X = a.pop + d.pop_off;
+        float* Ug = uscr + d.pop_off;
+        const float* o = a.shift + d.shift_off;
+        const float* gRT = a.rotT + d.rot_off;
+        for (int e = tid; e < dim * (dp >> 2); e += nt)
+            reinterpret_cast<float4*>(RT)[e] = reinterpret_cast<const float4*>(gRT)[e];
+        for (int i = tid; i < np; i += nt) f[i] = a.fit[d.fit_off + i];
+        __syncthreads();
+        const bool pb = st.uses_pbest();
+        for (int g = 0; g < a.n_gens; ++g) {
+            const uint32_t gen = a.gen0 + (uint32_t)g;
+            int best;
+            if (pb) {
+                block_topk(f, np, d.kp, topk);
+                __syncthreads();
+                best = topk[0];
+            } else {
+                best = block_argmin(f, np, red);
+            }
+            for (int t0 = 0; t0 < np; t0 += kT) {
+                const int nv = min(kT, np - t0);
+                // trial, phase 1: draws of each individual of the tile (thread per individual)
+                for (int t = tid; t < kT; t += nt) {
+                    int* rec = recs + t * kRec;
+                    if (t < nv) {
+                        const int i = t0 + t;
+                        const Ctr c = make_ctr(a.key, (uint32_t)d.stream, gen, (uint32_t)i, epoch);
+                        Indiv v;
+                        indiv_setup(st, c, i, np, dim, d.kp, pb ? topk : nullptr, best, v);
+                        rec[0] = v.ibl;
+                        rec[1] = v.ibr;
+                        rec[2] = v.jrand;
+                        rec[3] = v.nstart;
+                        rec[4] = st.cs == 2 ? exp_length(c, dim, st.cri) : 0;
+                        rec[5] = (int)v.kraw;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            rec[6 + 2 * q] = diff_plus(v, st.a, q);
+                            rec[7 + 2 * q] = diff_minus(v, st.a, q);
+                        }
+                    }
+                }
+                __syncthreads();
+                // trial, phase 2: (chunk, individual) items, individuals fastest
+                for (int e = tid; e < nbr * kT; e += nt) {
+                    const int q = e / kT, t = e - q * kT, j4 = 4 * q;
+                    float* col = dT + (size_t)j4 * kTP + t;
+                    if (t >= nv) {
+                        col[0] = 0.f; col[kTP] = 0.f; col[2 * kTP] = 0.f; col[3 * kTP] = 0.f;
+                        continue;
+                    }
+                    const int i = t0 + t;
+                    const int* rec = recs + t * kRec;
+                    const float4 av = *reinterpret_cast<const float4*>(X + (long long)rec[0] * dp + j4);
+                    const float4 bv = *reinterpret_cast<const float4*>(X + (long long)rec[1] * dp + j4);
+                    const float4 xv = *reinterpret_cast<const float4*>(X + (long long)i * dp + j4);
+                    // every difference-pair row is loaded before any is used, so the
+                    // chunk costs one memory round trip whatever dn is
+                    float4 pp[4], mm[4];
+#pragma unroll
+                    for (int qq = 0; qq < 4; ++qq) {
+                        if (qq < st.dn) {
+                            pp[qq] = *reinterpret_cast<const float4*>(X + (long long)rec[6 + 2 * qq] * dp + j4);
+                            mm[qq] = *reinterpret_cast<const float4*>(X + (long long)rec[7 + 2 * qq] * dp + j4);
+                        }
+                    }
+                    float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int qq = 0; qq < 4; ++qq) {
+                        if (qq < st.dn) {
+                            sum.x += pp[qq].x - mm[qq].x; sum.y += pp[qq].y - mm[qq].y;
+                            sum.z += pp[qq].z - mm[qq].z; sum.w += pp[qq].w - mm[qq].w;
+                        }
+                    }
+                    uint4 wv = make_uint4(0, 0, 0, 0);
+                    if (st.cs == 1) {
+                        const Ctr c = make_ctr(a.key, (uint32_t)d.stream, gen, (uint32_t)i, epoch);
+                        wv = c.slot(4 + (uint32_t)q);
+                    }
+                    const float F = st.F, K = (float)rec[5] * (1.0f / 16777216.0f);
+                    const bool dir = st.bl != st.br;
+                    const float a4[4] = {av.x, av.y, av.z, av.w}, b4[4] = {bv.x, bv.y, bv.z, bv.w};
+                    const float x4[4] = {xv.x, xv.y, xv.z, xv.w}, s4[4] = {sum.x, sum.y, sum.z, sum.w};
+                    float u4[4];
+#pragma unroll
+                    for (int tq = 0; tq < 4; ++tq) {
+                        const int j = j4 + tq;
+                        float vj = a4[tq];
+                        if (dir) vj += F * (b4[tq] - a4[tq]);
+                        vj += F * s4[tq];
+                        float u;
+                        if (st.cs == 3) {
+                            u = x4[tq] + K * (vj - x4[tq]);
+                        } else {
+                            bool take;
+                            if (st.cs == 1) {
+                                take = ((word_of(wv, tq) >> 8) < st.cri) || (j == rec[2]);
+                            } else {
+                                int off = j - rec[3];
+                                if (off < 0) off += dim;
+                                take = off < rec[4];
+                            }
+                            u = take ? vj : x4[tq];
+                        }
+                        u = fminf(fmaxf(u, a.lo), a.hi);
+                        if (j >= dim) u = 0.0f;
+                        u4[tq] = u;
+                        col[(size_t)tq * kTP] = (j < dim) ? (u - o[j]) : 0.0f;
+                    }
+                    *reinterpret_cast<float4*>(Ug + (long long)i * dp + j4) = make_float4(u4[0], u4[1], u4[2], u4[3]);
+                }
+                __syncthreads();
+                tile_gemm(dT, RT, Z, dim, nbr, dp, zp);
+                __syncthreads();
+                // objective: a group of 4 lanes per individual walks its Z row in
+                // blocks of 4 rows (the loop is warp-uniform; rows past nv are zero)
+                for (int tb = 0; tb < nv; tb += nt >> 2) {
+                    const int t = tb + (tid >> 2), s = tid & 3;
+                    const float* zr = Z + (size_t)t * zp;
+                    GroupObj acc;
+                    for (int r0 = 0; r0 < dim; r0 += 4) group_obj_push<4>(d.obj, acc, zr[r0 + s], r0, s, dim);
+                    const float fv = group_obj_finish<4>(d.obj, acc, dim);
+                    if (s == 0 && t < nv) fu[t0 + t] = nan_to_inf(fv);
+                }
+                __syncthreads();
+            }
+            // selection, pass 1 (thread per individual): decide the clear cases,
+            // list the near ties (their order is irrelevant: each is decided alone)
+            if (tid == 0) *ntie = 0;
+            __syncthreads();
+            for (int i = tid; i < np; i += nt) {
+                const float fn = fu[i];
+                int take = 0;
+                if (near_tie(fn, f[i], band)) {
+                    tl[atomicAdd(ntie, 1)] = i;
+                } else if (fn <= f[i]) {
+                    take = 1;
+                    f[i] = fn;
+                }
+                acc[i] = take;
+            }
+            __syncthreads();
+            // near ties, kT / 2 per pass through the tile GEMM: column 2q of dT
+            // holds x - o and column 2q + 1 holds u - x of tie q, so Z rows 2q
+            // and 2q + 1 are z and dz (the same fma chain as every rotation);
+            // then four lanes per tie form f(u) - f(x) by the difference forms
+            const int nti = *ntie;
+            for (int b0 = 0; b0 < nti; b0 += kT / 2) {
+                const int nb = min(kT / 2, nti - b0);
+                if (tid < kT / 2) idf[tid] = 0;
+                __syncthreads();
+                for (int e = tid; e < nbr * kT; e += nt) {
+                    const int q = e / kT, c = e - q * kT, tt = c >> 1, j4 = 4 * q;
+                    float v4[4] = {0.f, 0.f, 0.f, 0.f};
+                    if (tt < nb) {
+                        const int i = tl[b0 + tt];
+                        const float4 xv = *reinterpret_cast<const float4*>(X + (long long)i * dp + j4);
+                        const float x4[4] = {xv.x, xv.y, xv.z, xv.w};
+                        if (c & 1) {
+                            const float4 uv = *reinterpret_cast<const float4*>(Ug + (long long)i * dp + j4);
+                            const float u4[4] = {uv.x, uv.y, uv.z, uv.w};
+                            bool moved = false;
+#pragma unroll
+                            for (int tq = 0; tq < 4; ++tq) {
+                                if (j4 + tq < dim) {
+                                    v4[tq] = u4[tq] - x4[tq];
+                                    moved = moved || u4[tq] != x4[tq];
+                                }
+                            }
+                            if (moved) idf[tt] = 1;
+                        } else {
+#pragma unroll
+                            for (int tq = 0; tq < 4; ++tq)
+                                if (j4 + tq < dim) v4[tq] = x4[tq] - o[j4 + tq];
+                        }
+                    }
+                    float* col = dT + (size_t)j4 * kTP + c;
+                    col[0] = v4[0]; col[kTP] = v4[1]; col[2 * kTP] = v4[2]; col[3 * kTP] = v4[3];
+                }
+                __syncthreads();
+                tile_gemm(dT, RT, Z, dim, nbr, dp, zp);
+                __syncthreads();
+                if (tid < 2 * kT) {  // warp-uniform: four lanes for each of the kT / 2 column pairs
+                    const int tt = tid >> 2, s = tid & 3;
+                    const float* zr = Z + (size_t)(2 * tt) * zp;
+                    GroupDiff g;
+                    for (int r0 = 0; r0 < dim; r0 += 4) group_diff_push<4>(d.obj, g, zr[r0 + s], zr[zp + r0 + s], r0, s, dim);
+                    const float df = group_diff_finish<4>(d.obj, g, dim);
+                    if (s == 0 && tt < nb) {
+                        const int i = tl[b0 + tt];
+                        if (!idf[tt]) {
+                            acc[i] = 1;          // the trial is the target: accepted, f unchanged
+                        } else if (df <= 0.0f) {
+                            acc[i] = 1;
+                            f[i] += df;          // f(x) + (f(u) - f(x)): never above f(x)
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+            // accepted trial rows replace their targets (coalesced float4 copies)
+            for (int e = tid; e < np * nbr; e += nt) {
+                const int i = e / nbr, q = e - i * nbr;
+                if (acc[i])
+                    *reinterpret_cast<float4*>(X + (long long)i * dp + 4 * q) =
+                        *reinterpret_cast<const float4*>(Ug + (long long)i * dp + 4 * q);
+            }
+            __syncthreads();
+        }
+        for (int i = tid; i < np; i += nt) a.fit[d.fit_off + i] = f[i];
+        const int b = block_argmin(f, np, red);
+        if (tid == 0 && a.best_f) a.best_f[k] = f[b];
+        if (tid == 0 && a.best_i) a.best_i[k] = b;
+        __syncthreads();
+    }
+}
+
+size_t fused_smem_tile(int max_np, int max_dpad, int threads) {
+    size_t words = (size_t)tile_header_words(max_np);
+    words += (size_t)max_dpad * max_dpad;          // R^T
+    words += (size_t)max_dpad * kTP;               // dT
+    words += (size_t)kT * tile_zp(max_dpad);       // Z (draw records alias it)
+    return words * sizeof(float);
+}
+
+cudaError_t launch_fused_tile(const StepArgs& a, const int* work, int n_work, const FusedPlan& p, float* uscr,
+                              cudaStream_t st) {
+    if (n_work <= 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_fused_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    if (e != cudaSuccess) return e;
+    k_fused_tile<<<p.grid, p.threads, p.smem, st>>>(a, work, n_work, uscr, p.max_np, p.max_dpad);
+    return cudaGetLastError();
+}
+
+}  // namespace metade

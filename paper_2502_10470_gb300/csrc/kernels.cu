@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(256) k_plain_select(StepArgs a, int k, const f
     float fn = fuscr[d.fit_off + i];
     const float fx = a.fit[d.fit_off + i];
     bool take;
-    bool tie = near_tie(fn, fx);
+    bool tie = near_tie(fn, fx, tie_band(d.dim));
     if (tie) {
         bool diff = false;
         for (int j = lane; j < d.dim; j += 32) diff = diff || (U[j] != X[j]);
@@ -407,6 +407,7 @@ __device__ __forceinline__ void small_executor(const StepArgs& a, int k, const I
                                                float* sm) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int np = d.np, dim = d.dim, dp = d.dpad, ds = small_stride(dp);
+    const float band = tie_band(dim);
     float* X = sm;
     float* U = X + np * ds;
     float* R = U + np * ds;
@@ -496,13 +497,13 @@ __device__ __forceinline__ void small_executor(const StepArgs& a, int k, const I
             float fn = fu[i];
             const float fx = f[i];
             bool take;
-            bool same = near_tie(fn, fx);
+            bool same = near_tie(fn, fx, band);
             if (same)
                 for (int j = 0; j < dim; ++j) same = same && (U[i * ds + j] == X[i * ds + j]);
             if (same) {
                 take = true;  // the trial is the target: nothing changes
                 fn = fx;
-            } else if (near_tie(fn, fx)) {
+            } else if (near_tie(fn, fx, band)) {
                 if (a.tie_fp64) {
                     const double eu = nan_to_inf(eval64_seq(d.obj, dim, DMAX, U + i * ds, o, R));
                     const double ex = nan_to_inf(eval64_seq(d.obj, dim, DMAX, X + i * ds, o, R));
@@ -585,6 +586,7 @@ __global__ void __launch_bounds__(512) k_fused_general(StepArgs a, const int* __
         const int k = work[w];
         const InstDesc d = a.desc[k];
         const int np = d.np, dim = d.dim, dp = d.dpad;
+        const float band = tie_band(dim);
         float* RTs = rs;
         float* wb = rs + (rot_smem ? (size_t)max_dpad * max_dpad : 0) + (size_t)warp * 4 * max_dpad;
         float* db = wb;
@@ -637,7 +639,7 @@ __global__ void __launch_bounds__(512) k_fused_general(StepArgs a, const int* __
                 float* Xi = X + (long long)i * dp;
                 const float* Ui = Ug + (long long)i * dp;
                 bool take;
-                bool tie = near_tie(fn, fx);
+                bool tie = near_tie(fn, fx, band);
                 if (tie) {
                     bool diff = false;
                     for (int j = lane; j < dim; j += 32) diff = diff || (Ui[j] != Xi[j]);
@@ -650,9 +652,8 @@ __global__ void __launch_bounds__(512) k_fused_general(StepArgs a, const int* __
                     take = eu <= ex;
                     if (take) fn = fminf((float)eu, fx);
                 } else if (tie) {
-                    warp_rotate_pair(dim, RT, dp, Xi, Ui, o, db, db + max_dpad);
-                    __syncwarp();
-                    const float df = warp_diff(d.obj, dim, db, db + max_dpad);
+                    warp_rotate_pair_staged(dim, RT, dp, Xi, Ui, o, wb, max_dpad);
+                    const float df = warp_diff(d.obj, dim, wb + 2 * max_dpad, wb + 3 * max_dpad);
                     __syncwarp();
                     take = df <= 0.0f;
                     if (take) fn = fx + df;
@@ -707,6 +708,7 @@ cudaError_t launch_fused(const StepArgs& a, const int* work, int n_work, const F
         }
     }
     if (p.kind == 2) return launch_fused_group(a, work, n_work, p, uscr, st);
+    if (p.kind == 3) return launch_fused_tile(a, work, n_work, p, uscr, st);
     cudaError_t e = cudaFuncSetAttribute(k_fused_general, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
     if (e != cudaSuccess) return e;
     k_fused_general<<<p.grid, p.threads, p.smem, st>>>(a, work, n_work, uscr, p.rot_smem, p.max_np, p.max_dpad);

@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(256) k_na_select(NaArgs a) {
     float fn = a.fu[i];
     const float fx = a.fit[i];
     bool take;
-    bool tie = near_tie(fn, fx);
+    bool tie = near_tie(fn, fx, tie_band(d.dim));
     if (tie) {
         bool diff = false;
         for (int j = lane; j < d.dim; j += 32) diff = diff || (U[j] != X[j]);

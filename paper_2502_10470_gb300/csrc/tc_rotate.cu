@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(256) k_tc_select(StepArgs a, const int* __rest
     const float* U = uscr + d.pop_off + (long long)i * d.dpad;
     float fn = fu[d.fit_off + i];
     const float fx = a.fit[d.fit_off + i];
-    bool tie = near_tie(fn, fx);
+    bool tie = near_tie(fn, fx, tie_band(d.dim));
     if (tie) {
         bool diff = false;
         for (int j = lane; j < d.dim; j += 32) diff = diff || (U[j] != X[j]);
@@ -350,7 +350,9 @@ __global__ void __launch_bounds__(256) k_tc_select(StepArgs a, const int* __rest
 
 // Listed ties, one per CTA: threads own rows of z = R (x - o) and dz = R (u - x)
 // (coalesced reads of R^T rows), then one warp forms the difference
-// f(u) - f(x) (same difference forms as every other path).
+// f(u) - f(x) (same difference forms as every other path).  With FP64 tie
+// re-evaluation the rows are R (x - o) and R (u - o) in FP64 instead and the
+// warp compares the two FP64 objectives (shared memory: 2 ws doubles).
 __global__ void __launch_bounds__(256) k_tc_ties(StepArgs a, const int* __restrict__ row_exec,
                                                  const float* __restrict__ uscr, const int* __restrict__ tie_list,
                                                  const int* __restrict__ tie_count, int ws) {
@@ -367,6 +369,38 @@ __global__ void __launch_bounds__(256) k_tc_ties(StepArgs a, const int* __restri
         const float* U = uscr + d.pop_off + (long long)i * d.dpad;
         const float* o = a.shift + d.shift_off;
         const float* RT = a.rotT + d.rot_off;
+        if (a.tie_fp64) {
+            double* zx64 = reinterpret_cast<double*>(smz);
+            double* zu64 = zx64 + ws;
+            for (int rr = threadIdx.x; rr < d.dim; rr += blockDim.x) {
+                double ax = 0.0, au = 0.0;
+                for (int c = 0; c < d.dim; ++c) {
+                    const double rt = (double)RT[(size_t)c * d.dpad + rr];
+                    ax = fma(rt, (double)X[c] - (double)o[c], ax);
+                    au = fma(rt, (double)U[c] - (double)o[c], au);
+                }
+                zx64[rr] = ax;
+                zu64[rr] = au;
+            }
+            __syncthreads();
+            if (threadIdx.x < 32) {
+                const double eu = nan_to_inf(warp_objective<double>(d.obj, d.dim, zu64));
+                const double ex = nan_to_inf(warp_objective<double>(d.obj, d.dim, zx64));
+                if (threadIdx.x == 0) {
+                    const float fx = a.fit[d.fit_off + i];
+                    take_s = eu <= ex ? 1 : 0;
+                    fn_s = fminf((float)eu, fx);
+                }
+            }
+            __syncthreads();
+            if (take_s) {
+                for (int j = threadIdx.x * 4; j < d.dpad; j += blockDim.x * 4)
+                    *reinterpret_cast<float4*>(X + j) = *reinterpret_cast<const float4*>(U + j);
+                if (threadIdx.x == 0) a.fit[d.fit_off + i] = fn_s;
+            }
+            __syncthreads();
+            continue;
+        }
         float* zx = smz;
         float* dz = smz + ws;
         for (int rr = threadIdx.x; rr < d.dim; rr += blockDim.x) {
@@ -457,7 +491,7 @@ cudaError_t launch_tc_generation(const StepArgs& a, const TcPlan& p, cudaStream_
     k_tc_prologue<<<p.n_exec, 256, 0, st>>>(a, p.execs, p.topk_all);
     const int blocks = (p.n_rows + 7) / 8;
     size_t smem_t = (size_t)8 * p.max_dpad * sizeof(float);
-    size_t smem_s = (size_t)2 * p.max_dpad * sizeof(float);
+    const size_t smem_s = (size_t)2 * p.max_dpad * (a.tie_fp64 ? sizeof(double) : sizeof(float));
     cudaError_t e = cudaFuncSetAttribute(k_tc_trial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
     if (e != cudaSuccess) return e;
     k_tc_trial<<<blocks, 256, smem_t, st>>>(a, p.row_exec, p.n_rows, p.topk_all, p.uscr, p.aq, p.split ? p.aq_lo : nullptr,
@@ -482,7 +516,7 @@ cudaError_t launch_tc_generation(const StepArgs& a, const TcPlan& p, cudaStream_
     k_tc_select<<<blocks, 256, 0, st>>>(a, p.row_exec, p.n_rows, p.uscr, p.fu, p.tie_list, p.tie_count);
     e = cudaFuncSetAttribute(k_tc_ties, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s);
     if (e != cudaSuccess) return e;
-    k_tc_ties<<<p.tie_ctas, 256, (size_t)2 * p.max_dpad * sizeof(float), st>>>(a, p.row_exec, p.uscr, p.tie_list,
+    k_tc_ties<<<p.tie_ctas, 256, smem_s, st>>>(a, p.row_exec, p.uscr, p.tie_list,
                                                                                 p.tie_count, p.max_dpad);
     return cudaGetLastError();
 }

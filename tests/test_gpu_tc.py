@@ -91,3 +91,69 @@ def test_tc_selection_and_generations(prec):
             assert nfits[k].min() <= last[k]
             last[k] = nfits[k].min()
     b.close()
+
+
+def _bf16_bits(x32):
+    """float32 -> bfloat16 bit patterns, round to nearest even (the
+    conversion the operand packing uses)."""
+    b = np.ascontiguousarray(x32, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    return ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) & 0xFFFF
+
+
+@pytest.mark.parametrize("tie_fp64", [0, 1], ids=["difference", "fp64"])
+def test_tc_near_ties_decided_like_fp64(tie_fp64):
+    """Near ties on the tensor-core path.  A first step with F = 0, CR = 1 and
+    stored fitness +inf makes every trial a copy of another grid point and
+    stores its BF16 fitness.  A second step moves one coordinate by
+    2^-20 (x_r0 - x_r1), exact in float32; where that coordinate's BF16
+    operand u_j - o_j rounds as before, the GEMM sees the same row, so f(u)
+    equals the stored f(x) and the pair must be listed as a tie and decided
+    like the sign of the FP64 difference of the oracle."""
+    import torch
+    import paper_2502_10470_gb300 as M
+    rng = np.random.default_rng(77)
+    n, NP, D = 6, 64, 256
+    probs = [synth.make_problem(rng, D, k) for k in range(n)]
+    wl = synth.Workload(name="tc-ties", problems=probs, inst_np=np.full(n, NP, dtype=np.int32),
+                        inst_prob=np.arange(n, dtype=np.int32), inst_group=np.arange(n, dtype=np.int32),
+                        n_groups=n, n_out=0, inner_gens=1, outer_gens=1, seed=12, one_shot=0)
+    b = make_batch(wl, M.METADE_PATH_BATCHED, prec=1, tie_fp64=tie_fp64)
+    assert json.loads(M.metade_plan_info(b.ctx))["tensor_core"]["executors"] == n
+    grid = [(rng.integers(-12, 13, (NP, D)) * 8.0).astype(np.float32) for _ in range(n)]
+    b.set_population(grid, [np.full(NP, np.inf, dtype=np.float32)] * n)
+    b.set_theta(np.tile(np.array([0.0, 1.0, 1, 1, 1, 1], dtype=np.float32), (n, 1)))
+    M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 0, 1, None, None)
+    assert M.metade_sync(b.ctx) == M.METADE_OK
+    pops, fits = b.get_population()                       # grid copies, BF16 fitness
+    theta = np.tile(np.array([2.0 ** -20, 0.0, 4, 4, 1, 1], dtype=np.float32), (n, 1))
+    b.set_theta(theta)
+    rec = torch.zeros((b.n_indiv, M.REC_FIELDS), dtype=torch.int32, device="cuda")
+    M.metade_draw_record(b.ctx, b.fit, b.theta, 0, 1, rec)
+    M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 1, 1, None, None)
+    assert M.metade_sync(b.ctx) == M.METADE_OK
+    rec = rec.cpu().numpy()
+    npops, nfits = b.get_population()
+    checked = 0
+    for k in range(n):
+        p = probs[k]
+        r = rec[b.fit_off[k]:b.fit_off[k] + NP]
+        u = pops[k].astype(np.float64).copy()
+        j = r[:, 2]
+        rows = np.arange(NP)
+        u[rows, j] += 2.0 ** -20 * (pops[k][r[:, 9], j].astype(np.float64) - pops[k][r[:, 10], j])
+        u32 = u.astype(np.float32)
+        assert np.array_equal(u32.astype(np.float64), u)
+        same_op = _bf16_bits(u32[rows, j] - p.shift[j]) == _bf16_bits(pops[k][rows, j] - p.shift[j])
+        fu = oracle.eval_pop(p.obj, u, p.shift, p.rot)
+        fx = oracle.eval_pop(p.obj, pops[k], p.shift, p.rot)
+        delta = fu - fx
+        sure = same_op & np.isfinite(fits[k]) & (fits[k] > 0) & (np.abs(delta) > 1e-10 * np.abs(fx))
+        took = np.any(npops[k] != pops[k], axis=1)
+        np.testing.assert_array_equal(took[sure], (delta <= 0)[sure], err_msg="executor %d obj %d" % (k, p.obj))
+        assert np.all(nfits[k] <= fits[k])
+        if tie_fp64:
+            a = sure & took
+            np.testing.assert_array_equal(nfits[k][a], np.minimum(fu[a].astype(np.float32), fits[k][a]))
+        checked += int(sure.sum())
+    b.close()
+    assert checked > 200
