@@ -52,6 +52,8 @@ def parse_args(argv=None):
     ap.add_argument("--workload", default="moderate", choices=["moderate", "precision", "batching"],
                     help="moderate: the headline workload; precision: the D=1000 precision study")
     ap.add_argument("--n-inst", type=int, default=64, help="executors of the precision study")
+    ap.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES),
+                    help="run one small untimed case for an ncu capture and exit")
     return ap.parse_args(argv)
 
 
@@ -554,8 +556,50 @@ def run_batching(args):
     print(json.dumps(line), flush=True)
 
 
+def _case_tile_d100():
+    """The D = 100 executors of the batching study (133 executors, 27556
+    individuals), 20 fused generations: one k_fused_tile launch."""
+    import numpy as np
+    import paper_2502_10470_gb300 as M
+    import synth
+    wl = synth.batching()
+    keep = [k for k in range(wl.n_inst) if wl.problems[k].dim == 100]
+    probs = [(wl.problems[k].dim, wl.problems[k].obj, wl.problems[k].shift, wl.problems[k].rot) for k in keep]
+    b = M.Batch(probs, wl.inst_np[keep], np.arange(len(keep)), seed=0, one_shot=0)
+    b.set_theta(wl.theta[keep])
+    M.metade_init(b.ctx, b.pop, b.fit, 0)
+    M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 0, 20, None, None)
+    if M.metade_sync(b.ctx) != M.METADE_OK:
+        raise SystemExit("device status not OK")
+    b.close()
+
+
+def _case_tc_d1000():
+    """The precision study's 64 x 512 x D1000 state, one generation in BF16
+    and one in bf16x3: two k_rot_tc launches (and one of each tc kernel)."""
+    import paper_2502_10470_gb300 as M
+    import synth
+    wl = synth.precision()
+    probs = [(p.dim, p.obj, p.shift, p.rot) for p in wl.problems]
+    for prec in (M.METADE_BF16, M.METADE_BF16X3):
+        b = M.Batch(probs, wl.inst_np, wl.inst_prob, seed=0, one_shot=0, prec=prec)
+        b.set_theta(wl.theta)
+        M.metade_init(b.ctx, b.pop, b.fit, 0)
+        M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 0, 1, None, None)
+        if M.metade_sync(b.ctx) != M.METADE_OK:
+            raise SystemExit("device status not OK")
+        b.close()
+
+
+PROFILE_CASES = {"tile-d100": _case_tile_d100, "tc-d1000": _case_tc_d1000}
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.profile_case:
+        PROFILE_CASES[args.profile_case]()
+        print("profile case %s done" % args.profile_case)
+        return
     if args.workload == "precision":
         run_precision(args)
         return

@@ -615,8 +615,9 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
         t.kp = tc_kp;
         t.split = split ? 1 : 0;
         t.max_dpad = tc_max_dpad;
-        // FP64 tie re-evaluation keeps two FP64 rows of max_dpad in shared memory
-        if (c->tie_fp64 && (size_t)2 * tc_max_dpad * sizeof(double) > kSmemLimit) return fail(METADE_EUNSUPPORTED);
+        // a tie keeps four rows of max_dpad in shared memory (FP64 with tie_fp64)
+        if ((size_t)4 * tc_max_dpad * (c->tie_fp64 ? sizeof(double) : sizeof(float)) > kSmemLimit)
+            return fail(METADE_EUNSUPPORTED);
         if (!tc_make_map(&t.mapA, c->aq, (long long)nrows, tc_kp, 128) ||
             !tc_make_map(&t.mapB, c->bq, tc_brows, tc_kp, 256) ||
             (split && (!tc_make_map(&t.mapAlo, c->aq_lo, (long long)nrows, tc_kp, 128) ||

@@ -228,14 +228,17 @@ __device__ __forceinline__ void warp_rotate_pair(int dim, const float* RT, int l
 }
 
 // z = R (x - o) and dz = R (u - x) by one warp with the two operand vectors
-// staged in shared memory first (coalesced row reads, then broadcast reads in
-// the rotation).  buf: 4 * ldb floats of shared scratch; z and dz are left
-// in buf + 2 ldb and buf + 3 ldb.
+// staged in shared memory first (coalesced row reads), then one pass over R^T
+// for both (each coalesced R^T load feeds two fma chains; the operands are
+// broadcast reads).  buf: 4 * ldb floats of shared scratch; z and dz are left
+// in buf + 2 ldb and buf + 3 ldb.  Same fma chain per row as warp_rotate.
 __device__ __forceinline__ void warp_rotate_pair_staged(int dim, const float* RT, int ldr, const float* x,
                                                         const float* u, const float* o, float* buf, int ldb) {
     const int lane = threadIdx.x & 31;
     float* dx = buf;
     float* dl = buf + ldb;
+    float* z = buf + 2 * ldb;
+    float* dz = buf + 3 * ldb;
     const int d4 = (dim + 3) & ~3;
     for (int j = lane; j < d4; j += 32) {
         const bool in = j < dim;
@@ -244,8 +247,30 @@ __device__ __forceinline__ void warp_rotate_pair_staged(int dim, const float* RT
         dl[j] = in ? u[j] - xv : 0.f;
     }
     __syncwarp();
-    warp_rotate<float>(dim, RT, ldr, dx, buf + 2 * ldb);
-    warp_rotate<float>(dim, RT, ldr, dl, buf + 3 * ldb);
+    for (int r0 = 0; r0 < dim; r0 += 32) {
+        const int r = r0 + lane;
+        const bool act = r < dim;
+        float az = 0.f, ad = 0.f;
+        for (int c = 0; c < d4; c += 4) {
+            const float4 xv = *reinterpret_cast<const float4*>(dx + c);
+            const float4 lv = *reinterpret_cast<const float4*>(dl + c);
+            if (act) {
+                const float xs[4] = {xv.x, xv.y, xv.z, xv.w}, ls[4] = {lv.x, lv.y, lv.z, lv.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (c + q < dim) {
+                        const float rt = RT[(size_t)(c + q) * ldr + r];
+                        az = fmaf(rt, xs[q], az);
+                        ad = fmaf(rt, ls[q], ad);
+                    }
+                }
+            }
+        }
+        if (act) {
+            z[r] = az;
+            dz[r] = ad;
+        }
+    }
     __syncwarp();
 }
 

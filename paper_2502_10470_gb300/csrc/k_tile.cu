@@ -20,7 +20,8 @@ namespace metade {
 namespace {
 constexpr int kT = 64;        // individuals per tile
 constexpr int kTP = kT + 4;   // k-major row length of dT (float4 aligned)
-constexpr int kRec = 16;      // per-individual draw record (ints)
+constexpr int kRec = 14;      // draw record fields, stored field-major (recs[field * kT + t]: no bank conflicts)
+static_assert(kRec <= 36, "the draw records alias Z, whose rows are at least 36 floats long");
 
 // Z row stride: at least max_dpad and 4 (mod 32), so the eight 4-lane groups
 // of a warp that read 4 consecutive rows of 8 different Z rows hit distinct banks.
@@ -78,7 +79,7 @@ __global__ void __launch_bounds__(256, 2) k_fused_tile(StepArgs a, const int* __
     float* dT = RT + (size_t)max_dpad * max_dpad;                  // [dp][kTP]
     const int zp = tile_zp(max_dpad);                              // Z row length
     float* Z = dT + (size_t)max_dpad * kTP;                        // [kT][zp]
-    int* recs = reinterpret_cast<int*>(Z);                         // [kT][kRec], dead before Z is written
+    int* recs = reinterpret_cast<int*>(Z);                         // [kRec][kT], dead before Z is written
     int* acc = topk;
     for (int w = blockIdx.x; w < n_work; w += gridDim.x) {
         const int k = work[w];
@@ -114,22 +115,22 @@ __global__ void __launch_bounds__(256, 2) k_fused_tile(StepArgs a, const int* __
                 const int nv = min(kT, np - t0);
                 // trial, phase 1: draws of each individual of the tile (thread per individual)
                 for (int t = tid; t < kT; t += nt) {
-                    int* rec = recs + t * kRec;
+                    int* rec = recs + t;
                     if (t < nv) {
                         const int i = t0 + t;
                         const Ctr c = make_ctr(a.key, (uint32_t)d.stream, gen, (uint32_t)i, epoch);
                         Indiv v;
                         indiv_setup(st, c, i, np, dim, d.kp, pb ? topk : nullptr, best, v);
-                        rec[0] = v.ibl;
-                        rec[1] = v.ibr;
-                        rec[2] = v.jrand;
-                        rec[3] = v.nstart;
-                        rec[4] = st.cs == 2 ? exp_length(c, dim, st.cri) : 0;
-                        rec[5] = (int)v.kraw;
+                        rec[0 * kT] = v.ibl;
+                        rec[1 * kT] = v.ibr;
+                        rec[2 * kT] = v.jrand;
+                        rec[3 * kT] = v.nstart;
+                        rec[4 * kT] = st.cs == 2 ? exp_length(c, dim, st.cri) : 0;
+                        rec[5 * kT] = (int)v.kraw;
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
-                            rec[6 + 2 * q] = diff_plus(v, st.a, q);
-                            rec[7 + 2 * q] = diff_minus(v, st.a, q);
+                            rec[(6 + 2 * q) * kT] = diff_plus(v, st.a, q);
+                            rec[(7 + 2 * q) * kT] = diff_minus(v, st.a, q);
                         }
                     }
                 }
@@ -143,9 +144,9 @@ __global__ void __launch_bounds__(256, 2) k_fused_tile(StepArgs a, const int* __
                         continue;
                     }
                     const int i = t0 + t;
-                    const int* rec = recs + t * kRec;
-                    const float4 av = *reinterpret_cast<const float4*>(X + (long long)rec[0] * dp + j4);
-                    const float4 bv = *reinterpret_cast<const float4*>(X + (long long)rec[1] * dp + j4);
+                    const int* rec = recs + t;
+                    const float4 av = *reinterpret_cast<const float4*>(X + (long long)rec[0 * kT] * dp + j4);
+                    const float4 bv = *reinterpret_cast<const float4*>(X + (long long)rec[1 * kT] * dp + j4);
                     const float4 xv = *reinterpret_cast<const float4*>(X + (long long)i * dp + j4);
                     // every difference-pair row is loaded before any is used, so the
                     // chunk costs one memory round trip whatever dn is
@@ -153,8 +154,8 @@ __global__ void __launch_bounds__(256, 2) k_fused_tile(StepArgs a, const int* __
 #pragma unroll
                     for (int qq = 0; qq < 4; ++qq) {
                         if (qq < st.dn) {
-                            pp[qq] = *reinterpret_cast<const float4*>(X + (long long)rec[6 + 2 * qq] * dp + j4);
-                            mm[qq] = *reinterpret_cast<const float4*>(X + (long long)rec[7 + 2 * qq] * dp + j4);
+                            pp[qq] = *reinterpret_cast<const float4*>(X + (long long)rec[(6 + 2 * qq) * kT] * dp + j4);
+                            mm[qq] = *reinterpret_cast<const float4*>(X + (long long)rec[(7 + 2 * qq) * kT] * dp + j4);
                         }
                     }
                     float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -170,7 +171,7 @@ __global__ void __launch_bounds__(256, 2) k_fused_tile(StepArgs a, const int* __
                         const Ctr c = make_ctr(a.key, (uint32_t)d.stream, gen, (uint32_t)i, epoch);
                         wv = c.slot(4 + (uint32_t)q);
                     }
-                    const float F = st.F, K = (float)rec[5] * (1.0f / 16777216.0f);
+                    const float F = st.F, K = (float)rec[5 * kT] * (1.0f / 16777216.0f);
                     const bool dir = st.bl != st.br;
                     const float a4[4] = {av.x, av.y, av.z, av.w}, b4[4] = {bv.x, bv.y, bv.z, bv.w};
                     const float x4[4] = {xv.x, xv.y, xv.z, xv.w}, s4[4] = {sum.x, sum.y, sum.z, sum.w};
@@ -187,11 +188,11 @@ __global__ void __launch_bounds__(256, 2) k_fused_tile(StepArgs a, const int* __
                         } else {
                             bool take;
                             if (st.cs == 1) {
-                                take = ((word_of(wv, tq) >> 8) < st.cri) || (j == rec[2]);
+                                take = ((word_of(wv, tq) >> 8) < st.cri) || (j == rec[2 * kT]);
                             } else {
-                                int off = j - rec[3];
+                                int off = j - rec[3 * kT];
                                 if (off < 0) off += dim;
-                                take = off < rec[4];
+                                take = off < rec[4 * kT];
                             }
                             u = take ? vj : x4[tq];
                         }

@@ -348,11 +348,45 @@ __global__ void __launch_bounds__(256) k_tc_select(StepArgs a, const int* __rest
     }
 }
 
-// Listed ties, one per CTA: threads own rows of z = R (x - o) and dz = R (u - x)
-// (coalesced reads of R^T rows), then one warp forms the difference
-// f(u) - f(x) (same difference forms as every other path).  With FP64 tie
-// re-evaluation the rows are R (x - o) and R (u - o) in FP64 instead and the
-// warp compares the two FP64 objectives (shared memory: 2 ws doubles).
+// Listed ties, one per CTA.  x - o and u - x are staged in shared memory,
+// then every thread owns four rows of z = R (x - o) and dz = R (u - x) at
+// once (four independent coalesced loads of R^T per column feed eight fma
+// chains, so the L2 latency of streaming R^T is overlapped), and one warp
+// forms the difference f(u) - f(x) (same difference forms as every other
+// path).  With FP64 tie re-evaluation the rows are R (x - o) and R (u - o) in
+// FP64 and the warp compares the two FP64 objectives.  Shared memory: 4 ws
+// floats, or 4 ws doubles for FP64.
+template <typename T>
+__device__ __forceinline__ void tc_tie_rows(int dim, int dpad, const float* __restrict__ RT, const T* va,
+                                            const T* vb, T* za, T* zb) {
+    const int nt = blockDim.x;
+    for (int r0 = threadIdx.x; r0 < dim; r0 += 4 * nt) {
+        T aa[4] = {T(0), T(0), T(0), T(0)}, ab[4] = {T(0), T(0), T(0), T(0)};
+        bool in[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) in[q] = r0 + q * nt < dim;
+        for (int c = 0; c < dim; ++c) {
+            const float* col = RT + (size_t)c * dpad + r0;
+            const T xa = va[c], xb = vb[c];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (in[q]) {
+                    const T rt = T(col[q * nt]);
+                    aa[q] = fma(rt, xa, aa[q]);
+                    ab[q] = fma(rt, xb, ab[q]);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (in[q]) {
+                za[r0 + q * nt] = aa[q];
+                zb[r0 + q * nt] = ab[q];
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) k_tc_ties(StepArgs a, const int* __restrict__ row_exec,
                                                  const float* __restrict__ uscr, const int* __restrict__ tie_list,
                                                  const int* __restrict__ tie_count, int ws) {
@@ -370,57 +404,46 @@ __global__ void __launch_bounds__(256) k_tc_ties(StepArgs a, const int* __restri
         const float* o = a.shift + d.shift_off;
         const float* RT = a.rotT + d.rot_off;
         if (a.tie_fp64) {
-            double* zx64 = reinterpret_cast<double*>(smz);
-            double* zu64 = zx64 + ws;
-            for (int rr = threadIdx.x; rr < d.dim; rr += blockDim.x) {
-                double ax = 0.0, au = 0.0;
-                for (int c = 0; c < d.dim; ++c) {
-                    const double rt = (double)RT[(size_t)c * d.dpad + rr];
-                    ax = fma(rt, (double)X[c] - (double)o[c], ax);
-                    au = fma(rt, (double)U[c] - (double)o[c], au);
-                }
-                zx64[rr] = ax;
-                zu64[rr] = au;
+            double* vx = reinterpret_cast<double*>(smz);
+            double* vu = vx + ws;
+            double* zx = vu + ws;
+            double* zu = zx + ws;
+            for (int c = threadIdx.x; c < d.dim; c += blockDim.x) {
+                vx[c] = (double)X[c] - (double)o[c];
+                vu[c] = (double)U[c] - (double)o[c];
             }
             __syncthreads();
+            tc_tie_rows<double>(d.dim, d.dpad, RT, vx, vu, zx, zu);
+            __syncthreads();
             if (threadIdx.x < 32) {
-                const double eu = nan_to_inf(warp_objective<double>(d.obj, d.dim, zu64));
-                const double ex = nan_to_inf(warp_objective<double>(d.obj, d.dim, zx64));
+                const double eu = nan_to_inf(warp_objective<double>(d.obj, d.dim, zu));
+                const double ex = nan_to_inf(warp_objective<double>(d.obj, d.dim, zx));
                 if (threadIdx.x == 0) {
                     const float fx = a.fit[d.fit_off + i];
                     take_s = eu <= ex ? 1 : 0;
                     fn_s = fminf((float)eu, fx);
                 }
             }
-            __syncthreads();
-            if (take_s) {
-                for (int j = threadIdx.x * 4; j < d.dpad; j += blockDim.x * 4)
-                    *reinterpret_cast<float4*>(X + j) = *reinterpret_cast<const float4*>(U + j);
-                if (threadIdx.x == 0) a.fit[d.fit_off + i] = fn_s;
-            }
-            __syncthreads();
-            continue;
-        }
-        float* zx = smz;
-        float* dz = smz + ws;
-        for (int rr = threadIdx.x; rr < d.dim; rr += blockDim.x) {
-            float az = 0.f, ad = 0.f;
-            for (int c = 0; c < d.dim; ++c) {
-                const float rt = RT[(size_t)c * d.dpad + rr];
+        } else {
+            float* vx = smz;
+            float* vl = vx + ws;
+            float* zx = vl + ws;
+            float* dz = zx + ws;
+            for (int c = threadIdx.x; c < d.dim; c += blockDim.x) {
                 const float xc = X[c];
-                az = fmaf(rt, xc - o[c], az);
-                ad = fmaf(rt, U[c] - xc, ad);
+                vx[c] = xc - o[c];
+                vl[c] = U[c] - xc;
             }
-            zx[rr] = az;
-            dz[rr] = ad;
-        }
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            const float df = warp_diff(d.obj, d.dim, zx, dz);
-            if (threadIdx.x == 0) {
-                const float fx = a.fit[d.fit_off + i];
-                take_s = df <= 0.0f ? 1 : 0;
-                fn_s = fx + df;
+            __syncthreads();
+            tc_tie_rows<float>(d.dim, d.dpad, RT, vx, vl, zx, dz);
+            __syncthreads();
+            if (threadIdx.x < 32) {
+                const float df = warp_diff(d.obj, d.dim, zx, dz);
+                if (threadIdx.x == 0) {
+                    const float fx = a.fit[d.fit_off + i];
+                    take_s = df <= 0.0f ? 1 : 0;
+                    fn_s = fx + df;
+                }
             }
         }
         __syncthreads();
@@ -491,7 +514,7 @@ cudaError_t launch_tc_generation(const StepArgs& a, const TcPlan& p, cudaStream_
     k_tc_prologue<<<p.n_exec, 256, 0, st>>>(a, p.execs, p.topk_all);
     const int blocks = (p.n_rows + 7) / 8;
     size_t smem_t = (size_t)8 * p.max_dpad * sizeof(float);
-    const size_t smem_s = (size_t)2 * p.max_dpad * (a.tie_fp64 ? sizeof(double) : sizeof(float));
+    const size_t smem_s = (size_t)4 * p.max_dpad * (a.tie_fp64 ? sizeof(double) : sizeof(float));
     cudaError_t e = cudaFuncSetAttribute(k_tc_trial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
     if (e != cudaSuccess) return e;
     k_tc_trial<<<blocks, 256, smem_t, st>>>(a, p.row_exec, p.n_rows, p.topk_all, p.uscr, p.aq, p.split ? p.aq_lo : nullptr,
