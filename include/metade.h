@@ -124,8 +124,11 @@ METADE_API metade_status metade_offsets(const metade_ctx *ctx, int64_t *pop_off,
 METADE_API metade_status metade_set_stream(metade_ctx *ctx, void *stream);
 
 /* Alg. 2 lines 1-2: fill every executor's population uniformly in the box
- * (x = lo + (hi - lo) U, rounded once to float32) and evaluate it in FP32
- * (NaN fitness stored as +inf).  `epoch` enters the draw counter: with
+ * (x = lo + (hi - lo) U, rounded once to float32) and evaluate it (NaN
+ * fitness stored as +inf): in FP32, except executors on the tensor-core path
+ * (cfg.prec BF16 / BF16X3, D >= 256), which are evaluated by the rotation
+ * GEMM in that precision like all their later evaluations.  `epoch` enters
+ * the draw counter: with
  * one-shot evaluation the caller passes 0 every time, so every evaluation of
  * a theta starts from the same population. */
 METADE_API metade_status metade_init(metade_ctx *ctx, float *pop, float *fit, uint32_t epoch);

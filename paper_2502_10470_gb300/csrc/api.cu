@@ -330,8 +330,15 @@ metade_status run_init(metade_ctx* c, cudaStream_t st, float* pop, float* fit, u
     if (c->n_inst == 0) return METADE_OK;
     CK(launch_init(c->desc, c->n_inst, c->max_np, c->max_dpad, pop, make_key(c->seed, kTagInner), epoch, epoch_dev,
                    c->lo, c->hi, st));
-    CK(launch_eval(c->desc, c->row_inst, c->n_indiv, pop, c->rotT, c->shift, false, fit, true, c->max_dpad, st));
+    // executors on the tensor cores are evaluated by the rotation GEMM in the
+    // context's precision, like every later evaluation of theirs
+    CK(launch_eval(c->desc, c->row_inst, c->n_indiv, pop, c->rotT, c->shift, false, fit, true, c->max_dpad, st,
+                   c->tc));
     *launches += 2;
+    if (c->tc) {
+        CK(launch_tc_eval(c->desc, c->tcp, pop, c->shift, fit, c->status, st));
+        *launches += 2;
+    }
     return METADE_OK;
 }
 
@@ -495,7 +502,7 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
         delete c;
         return METADE_EUNSUPPORTED;
     }
-    // executors on the tensor cores: operand row offsets (InstDesc.pad0), tiles
+    // executors on the tensor cores: operand row offsets (InstDesc.tc_row), tiles
     c->is_tc.assign(c->n_inst, 0);
     std::vector<int> tc_execs, tc_row_exec, tc_tiles;
     std::vector<long long> tc_brow(c->n_prob, -1);
@@ -506,7 +513,8 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
             InstDesc& d = c->hdesc[k];
             if (d.dim < kTcMinDim) continue;
             c->is_tc[k] = 1;
-            d.pad0 = (int)tc_row_exec.size();
+            d.tc_row = (int)tc_row_exec.size();
+            d.on_tc = 1;
             tc_execs.push_back(k);
             for (int i = 0; i < d.np; ++i) tc_row_exec.push_back(k);
             for (int m0 = 0; m0 < d.np; m0 += 128) {
@@ -675,7 +683,7 @@ metade_status metade_eval(metade_ctx* c, const float* pop, metade_prec prec, voi
     if (prec != METADE_FP32 && prec != METADE_FP64) return METADE_EUNSUPPORTED;
     if (c->n_inst == 0) return METADE_OK;
     CK(launch_eval(c->desc, c->row_inst, c->n_indiv, pop, c->rotT, c->shift, prec == METADE_FP64, f_out, false,
-                   c->max_dpad, c->st));
+                   c->max_dpad, c->st, false));
     c->launches += 1;
     return METADE_OK;
 }

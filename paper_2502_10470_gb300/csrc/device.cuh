@@ -25,7 +25,10 @@ struct InstDesc {
     int np, dim, dpad;
     int obj, stream;     // objective id, Philox counter word 0
     int shift_off, kp;   // padded o [dpad]; pbest pool size
-    int prob, pad0, pad1, pad2;
+    int prob;            // problem index
+    int tc_row;          // tensor-core path: first row of the executor in the GEMM operands
+    int on_tc;           // 1: the executor is evaluated on the tensor-core path
+    int pad2;
 };
 static_assert(sizeof(InstDesc) == 64, "descriptor is one 64-byte record");
 

@@ -38,10 +38,11 @@ cudaError_t launch_pad_problems(const float* rot_in, const float* shift_in, cons
 cudaError_t launch_init(const InstDesc* desc, int n_inst, int max_np, int max_dpad, float* pop, Key key,
                         uint32_t epoch, const uint32_t* epoch_dev, float lo, float hi, cudaStream_t st);
 
-// Evaluate every row (row_inst maps rows to executors).  f64 selects FP64.
+// Evaluate every row (row_inst maps rows to executors).  f64 selects FP64;
+// skip_tc leaves the rows of executors on the tensor-core path untouched.
 cudaError_t launch_eval(const InstDesc* desc, const int* row_inst, long long n_rows, const float* pop,
                         const float* rotT, const float* shift, bool f64, void* f_out, bool nan_inf,
-                        int max_dpad, cudaStream_t st);
+                        int max_dpad, cudaStream_t st, bool skip_tc);
 
 cudaError_t launch_record(const StepArgs& a, int n_inst, int max_np, int* rec, cudaStream_t st);
 
@@ -81,7 +82,7 @@ cudaError_t launch_fused_tile(const StepArgs& a, const int* work, int n_work, co
 struct TcPlan {
     const int* execs;        // device [n_exec] executors of the bucket
     int n_exec;
-    const int* row_exec;     // device [n_rows] operand row -> executor (InstDesc.pad0 = first row)
+    const int* row_exec;     // device [n_rows] operand row -> executor (InstDesc.tc_row = first row)
     int n_rows;
     const int* tiles;        // device [n_tiles][2] (executor, first individual)
     int n_tiles;
@@ -100,6 +101,10 @@ bool tc_make_map(CUtensorMap* map, const void* base, long long rows, int kp, int
 size_t tc_gemm_smem(bool split);
 cudaError_t launch_tc_pack_rot(const float* rot, long long rot_off, int dim, int dpad, int kp, int np_rows,
                                __nv_bfloat16* bq, __nv_bfloat16* bq_lo, long long brow, cudaStream_t st);
+// Fitness of the population rows of every tensor-core executor, by the
+// rotation GEMM in the plan's precision (written into fit).
+cudaError_t launch_tc_eval(const InstDesc* desc, const TcPlan& p, const float* pop, const float* shift, float* fit,
+                           int* status, cudaStream_t st);
 cudaError_t launch_tc_generation(const StepArgs& a, const TcPlan& p, cudaStream_t st, cudaEvent_t gemm0 = nullptr,
                                  cudaEvent_t gemm1 = nullptr);
 

@@ -83,7 +83,7 @@ template <bool F64>
 __global__ void __launch_bounds__(256) k_eval(const InstDesc* __restrict__ desc, const int* __restrict__ row_inst,
                                               long long n_rows, const float* __restrict__ pop,
                                               const float* __restrict__ rotT, const float* __restrict__ shift,
-                                              void* f_out, int nan_inf, int scratch) {
+                                              void* f_out, int nan_inf, int scratch, int skip_tc) {
     extern __shared__ __align__(16) float sm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float* wb = sm + (size_t)warp * scratch;
@@ -91,6 +91,7 @@ __global__ void __launch_bounds__(256) k_eval(const InstDesc* __restrict__ desc,
          row += (long long)gridDim.x * (blockDim.x >> 5)) {
         const int k = row_inst[row];
         const InstDesc d = desc[k];
+        if (skip_tc && d.on_tc) continue;  // warp-uniform: one row per warp
         const long long i = row - d.fit_off;
         const float* x = pop + d.pop_off + i * d.dpad;
         const float* o = shift + d.shift_off;
@@ -126,7 +127,7 @@ static int num_sms() {
 
 cudaError_t launch_eval(const InstDesc* desc, const int* row_inst, long long n_rows, const float* pop,
                         const float* rotT, const float* shift, bool f64, void* f_out, bool nan_inf, int max_dpad,
-                        cudaStream_t st) {
+                        cudaStream_t st, bool skip_tc) {
     if (n_rows <= 0) return cudaSuccess;
     const int scratch = 4 * max_dpad;  // floats per warp: two buffers of max_dpad doubles
     const size_t smem = (size_t)8 * scratch * sizeof(float);
@@ -136,11 +137,11 @@ cudaError_t launch_eval(const InstDesc* desc, const int* row_inst, long long n_r
     if (f64) {
         cudaFuncSetAttribute(k_eval<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_eval<true><<<(unsigned)blocks, 256, smem, st>>>(desc, row_inst, n_rows, pop, rotT, shift, f_out,
-                                                          nan_inf, scratch);
+                                                          nan_inf, scratch, skip_tc ? 1 : 0);
     } else {
         cudaFuncSetAttribute(k_eval<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_eval<false><<<(unsigned)blocks, 256, smem, st>>>(desc, row_inst, n_rows, pop, rotT, shift, f_out,
-                                                           nan_inf, scratch);
+                                                           nan_inf, scratch, skip_tc ? 1 : 0);
     }
     return cudaGetLastError();
 }

@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(128, 1)
 
     const int k = a.tiles[2 * blockIdx.x], m0 = a.tiles[2 * blockIdx.x + 1];
     const InstDesc d = a.desc[k];
-    const int arow = d.pad0 + m0;  // first operand row of the tile
+    const int arow = d.tc_row + m0;  // first operand row of the tile
     const int brow0 = (int)a.brow[d.prob];
     const int nchunks = (d.dim + kBN - 1) / kBN;
     const int total = nchunks * a.kt;
@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(256) k_tc_trial(StepArgs a, const int* __restr
     if (r >= n_rows) return;
     const int k = row_exec[r];
     const InstDesc d = a.desc[k];
-    const int i = r - d.pad0;
+    const int i = r - d.tc_row;
     const Strat s = load_strat(a.theta + 6 * k, d.np);
     if (!s.ok) return;
     float* db = smt + (size_t)warp * ws;
@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(256) k_tc_select(StepArgs a, const int* __rest
     const InstDesc d = a.desc[k];
     const Strat s = load_strat(a.theta + 6 * k, d.np);
     if (!s.ok) return;
-    const int i = r - d.pad0;
+    const int i = r - d.tc_row;
     float* X = a.pop + d.pop_off + (long long)i * d.dpad;
     const float* U = uscr + d.pop_off + (long long)i * d.dpad;
     float fn = fu[d.fit_off + i];
@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(256) k_tc_ties(StepArgs a, const int* __restri
         const int r = tie_list[t];
         const int k = row_exec[r];
         const InstDesc d = a.desc[k];
-        const int i = r - d.pad0;
+        const int i = r - d.tc_row;
         float* X = a.pop + d.pop_off + (long long)i * d.dpad;
         const float* U = uscr + d.pop_off + (long long)i * d.dpad;
         const float* o = a.shift + d.shift_off;
@@ -456,6 +456,27 @@ __global__ void __launch_bounds__(256) k_tc_ties(StepArgs a, const int* __restri
     }
 }
 
+// A operand rows of the population itself, x - o, for evaluating it on the
+// tensor cores (initialisation).  Warp per row; the same FP32 subtraction and
+// BF16 rounding (hi, and the lo residual when split) as the trial kernel.
+__global__ void __launch_bounds__(256) k_tc_pack_pop(const InstDesc* __restrict__ desc,
+                                                     const int* __restrict__ row_exec, int n_rows,
+                                                     const float* __restrict__ pop, const float* __restrict__ shift,
+                                                     int kp, __nv_bfloat16* aq, __nv_bfloat16* aq_lo) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (r >= n_rows) return;
+    const InstDesc d = desc[row_exec[r]];
+    const float* x = pop + d.pop_off + (long long)(r - d.tc_row) * d.dpad;
+    const float* o = shift + d.shift_off;
+    for (int j = lane; j < kp; j += 32) {
+        const float v = j < d.dim ? x[j] - o[j] : 0.0f;
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        aq[(long long)r * kp + j] = hi;
+        if (aq_lo) aq_lo[(long long)r * kp + j] = __float2bfloat16_rn(v - __bfloat162float(hi));
+    }
+}
+
 // B operand: padded R rows in BF16 (hi, and the lo residual when split).
 __global__ void k_tc_pack_rot(const float* __restrict__ rot, long long rot_off, int dim, int dpad, int kp,
                               __nv_bfloat16* bq, __nv_bfloat16* bq_lo, long long brow) {
@@ -506,6 +527,27 @@ size_t tc_gemm_smem(bool split) { return (size_t)(split ? 2 : kStages) * (split 
 cudaError_t launch_tc_pack_rot(const float* rot, long long rot_off, int dim, int dpad, int kp, int np_rows,
                                __nv_bfloat16* bq, __nv_bfloat16* bq_lo, long long brow, cudaStream_t st) {
     k_tc_pack_rot<<<np_rows, 256, 0, st>>>(rot, rot_off, dim, dpad, kp, bq, bq_lo, brow);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_eval(const InstDesc* desc, const TcPlan& p, const float* pop, const float* shift, float* fit,
+                           int* status, cudaStream_t st) {
+    if (p.n_rows <= 0) return cudaSuccess;
+    k_tc_pack_pop<<<(p.n_rows + 7) / 8, 256, 0, st>>>(desc, p.row_exec, p.n_rows, pop, shift, p.kp, p.aq,
+                                                       p.split ? p.aq_lo : nullptr);
+    const size_t smem_g = tc_gemm_smem(p.split);
+    cudaError_t e = cudaFuncSetAttribute(k_rot_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_g);
+    if (e != cudaSuccess) return e;
+    TcGemmArgs g;
+    g.desc = desc;
+    g.tiles = p.tiles;
+    g.brow = p.brow;
+    g.fu = fit;  // the epilogue writes f of each row straight into the fitness array
+    g.kt = p.kp / kBK;
+    g.split = p.split;
+    g.status = status;
+    k_rot_tc<<<p.n_tiles, 128, smem_g, st>>>(p.mapA, p.mapB, p.split ? p.mapAlo : p.mapA, p.split ? p.mapBlo : p.mapB,
+                                             g);
     return cudaGetLastError();
 }
 

@@ -157,3 +157,33 @@ def test_tc_near_ties_decided_like_fp64(tie_fp64):
         checked += int(sure.sum())
     b.close()
     assert checked > 200
+
+
+@pytest.mark.parametrize("prec", [1, 3], ids=["bf16", "bf16x3"])
+def test_tc_init_evaluates_on_the_tensor_cores(prec):
+    """metade_init: executors on the tensor cores get their initial fitness
+    from the rotation GEMM in the context's precision (within its error
+    budget against FP64 at the same points); executors on the CUDA-core path
+    of the same context get exactly the FP32 values of an FP32 context."""
+    import paper_2502_10470_gb300 as M
+    rng = np.random.default_rng(47)
+    dims, nps, objs = [20, 300, 33, 256], [40, 130, 17, 64], [2, 1, 5, 3]
+    probs = [synth.make_problem(rng, d, o) for d, o in zip(dims, objs)]
+    n = len(probs)
+    wl = synth.Workload(name="tc-init", problems=probs, inst_np=np.array(nps, dtype=np.int32),
+                        inst_prob=np.arange(n, dtype=np.int32), inst_group=np.arange(n, dtype=np.int32),
+                        n_groups=n, n_out=0, inner_gens=1, outer_gens=1, seed=5, one_shot=0)
+    out = {}
+    for pr in (M.METADE_FP32, prec):
+        b = make_batch(wl, M.METADE_PATH_BATCHED, prec=pr)
+        M.metade_init(b.ctx, b.pop, b.fit, 3)
+        assert M.metade_sync(b.ctx) == M.METADE_OK
+        out[pr] = b.get_population()
+        b.close()
+    for k in range(n):
+        np.testing.assert_array_equal(out[prec][0][k], out[M.METADE_FP32][0][k])   # same initial points
+        if dims[k] < 256:
+            np.testing.assert_array_equal(out[prec][1][k], out[M.METADE_FP32][1][k])
+        else:
+            assert not np.array_equal(out[prec][1][k], out[M.METADE_FP32][1][k])  # not the FP32 values
+            check_fitness(out[prec][1][k], out[prec][0][k], probs[k], TOL[prec], UNIT[prec])
