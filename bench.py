@@ -395,7 +395,8 @@ def run_ours(args):
 # ------------------------------------------------------- precision study
 def run_precision(args):
     """64 executors, NP 512, D 1000 (Rastrigin / Rosenbrock): one generation
-    in FP32 (CUDA cores), BF16 and bf16x3 (tcgen05), from a shared state.
+    in FP32 (CUDA cores), BF16, bf16x3 and FP8-e4m3 (tcgen05), from a shared
+    state.
     Per precision: generation time and individual-gens/s, the tensor-core
     GEMM's own time and TFLOP/s (2 NP D^2 algorithmic flops per executor),
     the relative fitness error against FP64 at the same trials, and the
@@ -427,7 +428,8 @@ def run_precision(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     gemm_flops = 2.0 * float((wl.inst_np.astype(np.float64) * wl.dims().astype(np.float64) ** 2).sum())
     out = {}
-    for name, prec in (("fp32", M.METADE_FP32), ("bf16", M.METADE_BF16), ("bf16x3", M.METADE_BF16X3)):
+    for name, prec in (("fp32", M.METADE_FP32), ("bf16", M.METADE_BF16), ("bf16x3", M.METADE_BF16X3),
+                       ("fp8e4m3", M.METADE_FP8E4M3)):
         b = make(prec)
         b.set_theta(wl.theta)
         b.pop.copy_(pop0)
@@ -494,6 +496,11 @@ def run_precision(args):
                          "peak": peak, "unit": "TFLOP/s",
                          "frac": (bf.get("tc_gemm_tflops_algorithmic") or 0) / peak, "traffic": None,
                          "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured"},
+            "roofline_fp8": {"bound": "tensor", "kernel": "k_rot_tc (fp8e4m3)",
+                             "achieved": out["fp8e4m3"].get("tc_gemm_tflops_algorithmic"), "peak": 2.0 * peak,
+                             "unit": "TFLOP/s",
+                             "frac": (out["fp8e4m3"].get("tc_gemm_tflops_algorithmic") or 0) / (2.0 * peak),
+                             "peak_source": "2 x the measured bf16 burst peak (nominal fp8/bf16 dense ratio 4.5/2.25)"},
             "l2": "flushed before every timed generation"}
     print(json.dumps(line), flush=True)
     ref.close()

@@ -61,6 +61,12 @@ typedef enum {
     METADE_EUNSUPPORTED = 6 /* configuration not supported by this build */
 } metade_status;
 
+/* Precision of the rotation z = R (u - o).  FP32: CUDA cores.  BF16, BF16X3
+ * and FP8E4M3 apply to executors with D >= 256, which run on the tensor cores
+ * (tcgen05) with FP32 accumulation: BF16 operands; split BF16 (hi*hi + hi*lo +
+ * lo*hi, about FP32 accuracy); or e4m3 operands with a per-row scale of u - o
+ * and a per-problem scale of R (each maps the largest magnitude to 448),
+ * undone in the GEMM epilogue.  FP64 is only for metade_eval. */
 typedef enum {
     METADE_FP32 = 0,
     METADE_BF16 = 1,
@@ -91,7 +97,7 @@ typedef struct {
     int32_t one_shot;          /* 1: executors of a run share one random stream (Sec. III-C) */
     int32_t p_best_pct;        /* pbest pool, percent of NP (0 -> 10, Sec. II-A) */
     int32_t n_out;             /* evolver population per run; 0 = no evolver */
-    metade_prec prec;          /* rotation precision for D >= 512 (FP32 below) */
+    metade_prec prec;          /* rotation precision for D >= 256 (FP32 below): FP32, BF16, BF16X3, FP8E4M3 */
     metade_path path;
     int32_t tie_fp64;          /* selection ties: 0 = FP32 difference form, 1 = FP64 re-evaluation */
     void *stream;              /* cudaStream_t all calls are issued on (NULL = legacy) */

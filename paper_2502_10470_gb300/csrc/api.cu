@@ -93,7 +93,9 @@ struct metade_ctx {
     long long* tc_brow = nullptr;
     int* tc_topk = nullptr;
     int* tc_ties = nullptr;
-    __nv_bfloat16 *aq = nullptr, *aq_lo = nullptr, *bq = nullptr, *bq_lo = nullptr;
+    uint8_t *aq = nullptr, *aq_lo = nullptr, *bq = nullptr, *bq_lo = nullptr;  // BF16 pairs or e4m3 bytes
+    float *ascale = nullptr, *bscale = nullptr;                                // FP8 dequantisation factors
+    unsigned* amax = nullptr;                                                  // FP8: max|R| scratch
 };
 
 namespace {
@@ -407,6 +409,9 @@ void metade_destroy(metade_ctx* c) {
     cudaFree(c->aq_lo);
     cudaFree(c->bq);
     cudaFree(c->bq_lo);
+    cudaFree(c->ascale);
+    cudaFree(c->bscale);
+    cudaFree(c->amax);
     if (c->cap) cudaStreamDestroy(c->cap);
     delete c;
 }
@@ -420,7 +425,9 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
     if (cfg->p_best_pct < 0 || cfg->p_best_pct > 100) return METADE_EINVAL;
     if (cfg->n_out < 0 || (cfg->n_out > 0 && (cfg->n_out < 4 || cfg->n_inst % cfg->n_out != 0))) return METADE_EINVAL;
     if (cfg->path != METADE_PATH_BATCHED && cfg->path != METADE_PATH_PLAIN) return METADE_EINVAL;
-    if (cfg->prec != METADE_FP32 && cfg->prec != METADE_BF16 && cfg->prec != METADE_BF16X3) return METADE_EUNSUPPORTED;
+    if (cfg->prec != METADE_FP32 && cfg->prec != METADE_BF16 && cfg->prec != METADE_BF16X3 &&
+        cfg->prec != METADE_FP8E4M3)
+        return METADE_EUNSUPPORTED;
     for (int p = 0; p < cfg->n_prob; ++p) {
         if (cfg->prob_dim[p] < 1 || cfg->prob_obj[p] < 0 || cfg->prob_obj[p] > 5) return METADE_EINVAL;
         if (cfg->prob_dim[p] > kMaxDim) return METADE_EUNSUPPORTED;
@@ -508,7 +515,9 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
     std::vector<long long> tc_brow(c->n_prob, -1);
     long long tc_brows = 0;
     int tc_kp = 0, tc_max_dpad = 0;
-    if (c->prec == METADE_BF16 || c->prec == METADE_BF16X3) {
+    const bool fp8 = c->prec == METADE_FP8E4M3;
+    const int kalign = fp8 ? 128 : 64;  // K elements per 128-byte operand tile
+    if (c->prec == METADE_BF16 || c->prec == METADE_BF16X3 || fp8) {
         for (int k = 0; k < c->n_inst; ++k) {
             InstDesc& d = c->hdesc[k];
             if (d.dim < kTcMinDim) continue;
@@ -521,7 +530,7 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
                 tc_tiles.push_back(k);
                 tc_tiles.push_back(m0);
             }
-            tc_kp = std::max(tc_kp, (d.dim + 63) / 64 * 64);
+            tc_kp = std::max(tc_kp, (d.dim + kalign - 1) / kalign * kalign);
             tc_max_dpad = std::max(tc_max_dpad, d.dpad);
             if (tc_brow[d.prob] < 0) {
                 tc_brow[d.prob] = tc_brows;
@@ -578,11 +587,13 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
     if (c->tc) {
         const bool split = c->prec == METADE_BF16X3;
         const size_t nrows = tc_row_exec.size();
+        const size_t esz = fp8 ? 1 : 2;  // operand element bytes
         if (dalloc(&c->tc_execs, tc_execs.size()) || dalloc(&c->tc_row_exec, nrows) ||
             dalloc(&c->tc_tiles, tc_tiles.size()) || dalloc(&c->tc_brow, (size_t)c->n_prob) ||
-            dalloc(&c->tc_topk, (size_t)c->n_indiv) || dalloc(&c->tc_ties, nrows + 1) || dalloc(&c->aq, nrows * tc_kp) ||
-            dalloc(&c->bq, (size_t)tc_brows * tc_kp) ||
-            (split && (dalloc(&c->aq_lo, nrows * tc_kp) || dalloc(&c->bq_lo, (size_t)tc_brows * tc_kp))))
+            dalloc(&c->tc_topk, (size_t)c->n_indiv) || dalloc(&c->tc_ties, nrows + 1) ||
+            dalloc(&c->aq, nrows * tc_kp * esz) || dalloc(&c->bq, (size_t)tc_brows * tc_kp * esz) ||
+            (split && (dalloc(&c->aq_lo, nrows * tc_kp * esz) || dalloc(&c->bq_lo, (size_t)tc_brows * tc_kp * esz))) ||
+            (fp8 && (dalloc(&c->ascale, nrows) || dalloc(&c->bscale, (size_t)c->n_prob) || dalloc(&c->amax, 1))))
             return fail(METADE_ENOMEM);
         if (cudaMemcpy(c->tc_execs, tc_execs.data(), sizeof(int) * tc_execs.size(), cudaMemcpyHostToDevice) ||
             cudaMemcpy(c->tc_row_exec, tc_row_exec.data(), sizeof(int) * nrows, cudaMemcpyHostToDevice) ||
@@ -593,7 +604,7 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
             if (tc_brow[p] < 0) continue;
             const int D = cfg->prob_dim[p], Dp = (D + 3) & ~3;
             if (launch_tc_pack_rot(c->rot, rot_off[p], D, Dp, tc_kp, (D + 255) / 256 * 256, c->bq, split ? c->bq_lo : nullptr,
-                                   tc_brow[p], c->st))
+                                   tc_brow[p], fp8 ? 1 : 0, c->amax, fp8 ? c->bscale + p : nullptr, c->st))
                 return fail(METADE_ECUDA);
         }
         if (cudaStreamSynchronize(c->st)) return fail(METADE_ECUDA);
@@ -612,6 +623,9 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
         t.aq_lo = c->aq_lo;
         t.bq = c->bq;
         t.bq_lo = c->bq_lo;
+        t.ascale = c->ascale;
+        t.bscale = c->bscale;
+        t.fp8 = fp8 ? 1 : 0;
         t.tie_list = c->tc_ties + 1;
         t.tie_count = c->tc_ties;
         {
@@ -626,10 +640,10 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
         // a tie keeps four rows of max_dpad in shared memory (FP64 with tie_fp64)
         if ((size_t)4 * tc_max_dpad * (c->tie_fp64 ? sizeof(double) : sizeof(float)) > kSmemLimit)
             return fail(METADE_EUNSUPPORTED);
-        if (!tc_make_map(&t.mapA, c->aq, (long long)nrows, tc_kp, 128) ||
-            !tc_make_map(&t.mapB, c->bq, tc_brows, tc_kp, 256) ||
-            (split && (!tc_make_map(&t.mapAlo, c->aq_lo, (long long)nrows, tc_kp, 128) ||
-                       !tc_make_map(&t.mapBlo, c->bq_lo, tc_brows, tc_kp, 256))))
+        if (!tc_make_map(&t.mapA, c->aq, (long long)nrows, tc_kp, 128, (int)esz) ||
+            !tc_make_map(&t.mapB, c->bq, tc_brows, tc_kp, 256, (int)esz) ||
+            (split && (!tc_make_map(&t.mapAlo, c->aq_lo, (long long)nrows, tc_kp, 128, (int)esz) ||
+                       !tc_make_map(&t.mapBlo, c->bq_lo, tc_brows, tc_kp, 256, (int)esz))))
             return fail(METADE_ECUDA);
         if (!split) {
             t.mapAlo = t.mapA;
@@ -879,7 +893,7 @@ metade_status metade_plan_info(const metade_ctx* c, char* buf, size_t len) {
         snprintf(tmp, sizeof(tmp),
                  ", \"tensor_core\": {\"kernel\": \"k_rot_tc\", \"precision\": \"%s\", \"executors\": %d, "
                  "\"tiles\": %d, \"kp\": %d, \"tile\": [128, 256, 64]}",
-                 c->tcp.split ? "bf16x3" : "bf16", c->tcp.n_exec, c->tcp.n_tiles, c->tcp.kp);
+                 c->tcp.fp8 ? "fp8e4m3" : c->tcp.split ? "bf16x3" : "bf16", c->tcp.n_exec, c->tcp.n_tiles, c->tcp.kp);
         s += tmp;
     }
     s += "}";

@@ -90,17 +90,20 @@ struct TcPlan {
     int* topk_all;           // device [n_indiv] pbest pools
     float* uscr;             // trial rows (population layout)
     float* fu;               // trial fitness [n_indiv]
-    __nv_bfloat16 *aq, *aq_lo, *bq, *bq_lo;
+    void *aq, *aq_lo, *bq, *bq_lo;  // operands: BF16 (hi, lo) or e4m3 bytes
+    float* ascale;           // FP8: per operand row, max|d| / 448
+    float* bscale;           // FP8: per problem, max|R| / 448
+    int fp8;                 // 1: e4m3 operands (kind::f8f6f4)
     int* tie_list;           // device [n_rows] rows whose selection is a near tie
     int* tie_count;          // device counter
     int tie_ctas;            // CTAs of the tie kernel
     int kp, split, max_dpad;
     CUtensorMap mapA, mapB, mapAlo, mapBlo;
 };
-bool tc_make_map(CUtensorMap* map, const void* base, long long rows, int kp, int box_rows);
+bool tc_make_map(CUtensorMap* map, const void* base, long long rows, int kp, int box_rows, int esz);
 size_t tc_gemm_smem(bool split);
-cudaError_t launch_tc_pack_rot(const float* rot, long long rot_off, int dim, int dpad, int kp, int np_rows,
-                               __nv_bfloat16* bq, __nv_bfloat16* bq_lo, long long brow, cudaStream_t st);
+cudaError_t launch_tc_pack_rot(const float* rot, long long rot_off, int dim, int dpad, int kp, int np_rows, void* bq,
+                               void* bq_lo, long long brow, int fp8, unsigned* amax, float* bscale, cudaStream_t st);
 // Fitness of the population rows of every tensor-core executor, by the
 // rotation GEMM in the plan's precision (written into fit).
 cudaError_t launch_tc_eval(const InstDesc* desc, const TcPlan& p, const float* pop, const float* shift, float* fit,

@@ -22,6 +22,7 @@
 // and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "block.cuh"
 #include "internal.h"
@@ -31,6 +32,8 @@ namespace metade {
 namespace {
 
 constexpr int kBM = 128, kBN = 256, kBK = 64;           // BF16: a 64-element K tile is one 128-byte row
+constexpr int kBK8 = 128;                                 // FP8: a 128-element K tile is one 128-byte row
+constexpr float kE4M3Max = 448.0f;                        // largest finite e4m3 value
 constexpr int kStages = 4;
 constexpr int kAT = kBM * kBK * 2;                        // 16 KB
 constexpr int kBT = kBN * kBK * 2;                        // 32 KB
@@ -89,6 +92,18 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) |
                             ((uint32_t)(kBM >> 4) << 24);
 
+// Instruction descriptor, kind::f8f6f4: e4m3 A and B (format 0), FP32 D, K-major, M 128, N 256.
+constexpr uint32_t kIdesc8 = (1u << 4) | ((uint32_t)(kBN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+
+// K 32 e4m3 elements per instruction: 32 bytes along the swizzled row, like BF16.
+__device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::
+            "r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(kIdesc8), "r"(accumulate)
+        : "memory");
+}
+
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
@@ -122,8 +137,11 @@ struct TcGemmArgs {
     const int* tiles;         // [n_tiles][2]: executor, first individual of the 128-row tile
     const long long* brow;    // per problem: first row of its padded R in the B operand
     float* fu;                // out: f(u) per individual (fitness index)
-    int kt;                   // K tiles of 64
+    int kt;                   // K tiles (128 bytes: 64 BF16 or 128 e4m3 elements)
     int split;                // 1: bf16x3 (three products)
+    int fp8;                  // 1: e4m3 operands, z = acc * ascale[row] * bscale[problem]
+    const float* ascale;      // FP8: per operand row, max|d| / 448
+    const float* bscale;      // FP8: per problem, max|R| / 448
     int* status;
 };
 
@@ -167,15 +185,16 @@ __global__ void __launch_bounds__(128, 1)
     tc_fence_after();
     const uint32_t taddr = tmem_base;
 
+    const int kel = a.fp8 ? kBK8 : kBK;  // K elements per 128-byte tile (x is in elements, 128 bytes apart)
     auto load = [&](int it) {
         const int s = it % nst, c = it / a.kt, kk = it - c * a.kt;
         uint8_t* st = sm + s * stage_bytes;
         mbar_expect_tx(&full[s], (uint32_t)stage_bytes);
-        tma_load_2d(st, &tmA, &full[s], kk * kBK, arow);
-        tma_load_2d(st + kAT, &tmB, &full[s], kk * kBK, brow0 + c * kBN);
+        tma_load_2d(st, &tmA, &full[s], kk * kel, arow);
+        tma_load_2d(st + kAT, &tmB, &full[s], kk * kel, brow0 + c * kBN);
         if (a.split) {
-            tma_load_2d(st + kAT + kBT, &tmAlo, &full[s], kk * kBK, arow);
-            tma_load_2d(st + 2 * kAT + kBT, &tmBlo, &full[s], kk * kBK, brow0 + c * kBN);
+            tma_load_2d(st + kAT + kBT, &tmAlo, &full[s], kk * kel, arow);
+            tma_load_2d(st + 2 * kAT + kBT, &tmBlo, &full[s], kk * kel, brow0 + c * kBN);
         }
     };
 
@@ -188,6 +207,8 @@ __global__ void __launch_bounds__(128, 1)
     }
     ObjR acc;
     const int row = 32 * warp + lane;  // tile row of this thread
+    // FP8: dequantisation factor of this row (rows past the executor are not used)
+    const float zs = (a.fp8 && m0 + row < d.np) ? a.ascale[arow + row] * a.bscale[d.prob] : 1.0f;
     for (int c = 0; c < nchunks; ++c) {
         if (tid == 0 && ok) {
             for (int kk = 0; kk < a.kt && ok; ++kk) {
@@ -201,9 +222,15 @@ __global__ void __launch_bounds__(128, 1)
                 tc_fence_after();
                 uint8_t* st = sm + s * stage_bytes;
                 const uint64_t ad = sdesc_sw128(smem_u32(st)), bd = sdesc_sw128(smem_u32(st + kAT));
+                if (a.fp8) {
 #pragma unroll
-                for (int j = 0; j < kBK / 16; ++j)  // K 16 per instruction, 32 bytes along the swizzled row
-                    mma_bf16(taddr, ad + 2 * j, bd + 2 * j, (kk > 0 || j > 0) ? 1u : 0u);
+                    for (int j = 0; j < 4; ++j)  // K 32 per instruction, 32 bytes along the swizzled row
+                        mma_e4m3(taddr, ad + 2 * j, bd + 2 * j, (kk > 0 || j > 0) ? 1u : 0u);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < kBK / 16; ++j)  // K 16 per instruction, 32 bytes along the swizzled row
+                        mma_bf16(taddr, ad + 2 * j, bd + 2 * j, (kk > 0 || j > 0) ? 1u : 0u);
+                }
                 if (a.split) {
                     const uint64_t al = sdesc_sw128(smem_u32(st + kAT + kBT));
                     const uint64_t bl = sdesc_sw128(smem_u32(st + 2 * kAT + kBT));
@@ -238,6 +265,10 @@ __global__ void __launch_bounds__(128, 1)
                 if (col0 >= d.dim) break;  // uniform across the CTA
                 float v[32];
                 tmem_ld32(taddr + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * p), v);
+                if (a.fp8) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) v[j] *= zs;
+                }
 #pragma unroll
                 for (int j = 0; j < 32; ++j)
                     if (col0 + j < d.dim)
@@ -266,6 +297,35 @@ __global__ void __launch_bounds__(128, 1)
 }
 
 // ----------------------------------------------------------- other stages
+// One operand row of kp elements from v[0..dim) (zero past dim), by a warp.
+// BF16: hi = bf16(v), and lo = bf16(v - hi) when split.  FP8: a per-row scale
+// maps max|v| to 448, q = e4m3(v * scale) (round to nearest, saturating), and
+// max|v| / 448 goes to *inv_scale for the GEMM epilogue.
+__device__ __forceinline__ void pack_operand_row(const float* v, int dim, int kp, void* q, void* q_lo, long long r,
+                                                 int fp8, float* inv_scale) {
+    const int lane = threadIdx.x & 31;
+    if (fp8) {
+        float m = 0.0f;
+        for (int j = lane; j < dim; j += 32) m = fmaxf(m, fabsf(v[j]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
+        const float sc = m > 0.0f ? kE4M3Max / m : 1.0f;
+        if (lane == 0) *inv_scale = m > 0.0f ? m / kE4M3Max : 1.0f;
+        uint8_t* row = reinterpret_cast<uint8_t*>(q) + r * kp;
+        for (int j = lane; j < kp; j += 32)
+            row[j] = j < dim ? (uint8_t)__nv_cvt_float_to_fp8(v[j] * sc, __NV_SATFINITE, __NV_E4M3) : (uint8_t)0;
+        return;
+    }
+    __nv_bfloat16* row = reinterpret_cast<__nv_bfloat16*>(q) + r * kp;
+    __nv_bfloat16* row_lo = q_lo ? reinterpret_cast<__nv_bfloat16*>(q_lo) + r * kp : nullptr;
+    for (int j = lane; j < kp; j += 32) {
+        const float x = j < dim ? v[j] : 0.0f;
+        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+        row[j] = hi;
+        if (row_lo) row_lo[j] = __float2bfloat16_rn(x - __bfloat162float(hi));
+    }
+}
+
 // Best and pbest pool from the generation-start fitness (block per executor).
 __global__ void k_tc_prologue(StepArgs a, const int* __restrict__ execs, int* topk_all) {
     const int k = execs[blockIdx.x];
@@ -278,15 +338,16 @@ __global__ void k_tc_prologue(StepArgs a, const int* __restrict__ execs, int* to
     block_topk(a.fit + d.fit_off, d.np, d.kp, topk_all + d.fit_off);
 }
 
-// Trial rows (FP32, into the scratch U) and the GEMM operand d = u - o, BF16
-// (hi, and lo = bf16(d - hi) when split), K zero-padded to kp floats.
+// Trial rows (FP32, into the scratch U) and the GEMM operand d = u - o: BF16
+// (hi, and lo = bf16(d - hi) when split) or e4m3 with a per-row scale, K
+// zero-padded to kp elements.
 // Warps of one block may belong to different executors: per-warp shared
 // scratch is strided by the bucket's widest row (ws floats).
 __global__ void __launch_bounds__(256) k_tc_trial(StepArgs a, const int* __restrict__ row_exec, int n_rows,
-                                                  const int* __restrict__ topk_all, float* uscr, __nv_bfloat16* aq,
-                                                  __nv_bfloat16* aq_lo, int kp, int ws) {
+                                                  const int* __restrict__ topk_all, float* uscr, void* aq, void* aq_lo,
+                                                  int kp, int ws, int fp8, float* ascale) {
     extern __shared__ __align__(16) float smt[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
     const int r = blockIdx.x * (blockDim.x >> 5) + warp;
     if (r >= n_rows) return;
     const int k = row_exec[r];
@@ -304,13 +365,7 @@ __global__ void __launch_bounds__(256) k_tc_trial(StepArgs a, const int* __restr
     warp_trial(s, c, v, i, d.dim, L, a.pop + d.pop_off, d.dpad, a.shift + d.shift_off, a.lo, a.hi,
                uscr + d.pop_off + (long long)i * d.dpad, db);
     __syncwarp();
-    __nv_bfloat16* row = aq + (long long)r * kp;
-    for (int j = lane; j < kp; j += 32) {
-        const float x = j < d.dim ? db[j] : 0.0f;
-        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-        row[j] = hi;
-        if (aq_lo) aq_lo[(long long)r * kp + j] = __float2bfloat16_rn(x - __bfloat162float(hi));
-    }
+    pack_operand_row(db, d.dim, kp, aq, aq_lo, r, fp8, ascale + r);
 }
 
 // Greedy selection and row copy.  Near ties are only listed here; k_tc_ties
@@ -457,35 +512,63 @@ __global__ void __launch_bounds__(256) k_tc_ties(StepArgs a, const int* __restri
 }
 
 // A operand rows of the population itself, x - o, for evaluating it on the
-// tensor cores (initialisation).  Warp per row; the same FP32 subtraction and
-// BF16 rounding (hi, and the lo residual when split) as the trial kernel.
+// tensor cores (initialisation).  Warp per row: x - o is staged in the warp's
+// shared scratch (ws floats) and packed like a trial row.
 __global__ void __launch_bounds__(256) k_tc_pack_pop(const InstDesc* __restrict__ desc,
                                                      const int* __restrict__ row_exec, int n_rows,
                                                      const float* __restrict__ pop, const float* __restrict__ shift,
-                                                     int kp, __nv_bfloat16* aq, __nv_bfloat16* aq_lo) {
+                                                     int kp, void* aq, void* aq_lo, int ws, int fp8, float* ascale) {
+    extern __shared__ __align__(16) float smp[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int r = blockIdx.x * (blockDim.x >> 5) + warp;
     if (r >= n_rows) return;
     const InstDesc d = desc[row_exec[r]];
     const float* x = pop + d.pop_off + (long long)(r - d.tc_row) * d.dpad;
     const float* o = shift + d.shift_off;
-    for (int j = lane; j < kp; j += 32) {
-        const float v = j < d.dim ? x[j] - o[j] : 0.0f;
-        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-        aq[(long long)r * kp + j] = hi;
-        if (aq_lo) aq_lo[(long long)r * kp + j] = __float2bfloat16_rn(v - __bfloat162float(hi));
-    }
+    float* v = smp + (size_t)warp * ws;
+    for (int j = lane; j < d.dim; j += 32) v[j] = x[j] - o[j];
+    __syncwarp();
+    pack_operand_row(v, d.dim, kp, aq, aq_lo, r, fp8, ascale + r);
 }
 
-// B operand: padded R rows in BF16 (hi, and the lo residual when split).
-__global__ void k_tc_pack_rot(const float* __restrict__ rot, long long rot_off, int dim, int dpad, int kp,
-                              __nv_bfloat16* bq, __nv_bfloat16* bq_lo, long long brow) {
-    const int r = blockIdx.x;  // padded rows >= dim are zero
+// FP8: max |R| of one problem into *amax (as float bits; non-negative floats
+// order like their bit patterns).  *amax must start at 0.
+__global__ void k_tc_rot_amax(const float* __restrict__ rot, long long rot_off, int dim, int dpad, unsigned* amax) {
+    float m = 0.0f;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)dim * dim;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / dim), c = (int)(e - (long long)r * dim);
+        m = fmaxf(m, fabsf(rot[rot_off + (long long)r * dpad + c]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(amax, __float_as_uint(m));
+}
+
+// B operand: padded R rows (rows >= dim and columns >= dim are zero).  BF16:
+// hi, and the lo residual when split.  FP8: e4m3(R * 448 / max|R|), with the
+// problem's max|R| / 448 written to *bscale by block 0.
+__global__ void k_tc_pack_rot(const float* __restrict__ rot, long long rot_off, int dim, int dpad, int kp, void* bq,
+                              void* bq_lo, long long brow, int fp8, const unsigned* amax, float* bscale) {
+    const int r = blockIdx.x;
+    if (fp8) {
+        const float m = __uint_as_float(*amax);
+        const float sc = m > 0.0f ? kE4M3Max / m : 1.0f;
+        if (r == 0 && threadIdx.x == 0) *bscale = m > 0.0f ? m / kE4M3Max : 1.0f;
+        uint8_t* row = reinterpret_cast<uint8_t*>(bq) + (brow + r) * kp;
+        for (int c = threadIdx.x; c < kp; c += blockDim.x) {
+            const float x = (r < dim && c < dim) ? rot[rot_off + (long long)r * dpad + c] : 0.0f;
+            row[c] = (uint8_t)__nv_cvt_float_to_fp8(x * sc, __NV_SATFINITE, __NV_E4M3);
+        }
+        return;
+    }
+    __nv_bfloat16* row = reinterpret_cast<__nv_bfloat16*>(bq) + (brow + r) * kp;
+    __nv_bfloat16* row_lo = bq_lo ? reinterpret_cast<__nv_bfloat16*>(bq_lo) + (brow + r) * kp : nullptr;
     for (int c = threadIdx.x; c < kp; c += blockDim.x) {
         const float x = (r < dim && c < dim) ? rot[rot_off + (long long)r * dpad + c] : 0.0f;
         const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-        bq[(brow + r) * kp + c] = hi;
-        if (bq_lo) bq_lo[(brow + r) * kp + c] = __float2bfloat16_rn(x - __bfloat162float(hi));
+        row[c] = hi;
+        if (row_lo) row_lo[c] = __float2bfloat16_rn(x - __bfloat162float(hi));
     }
 }
 
@@ -508,43 +591,56 @@ EncodeTiledFn encode_fn() {
 
 }  // namespace
 
-// 2-D BF16 tensor map over a row-major [rows][kp] matrix, box [64 x box_rows],
-// 128-byte swizzle, out-of-range rows read as zero.
-bool tc_make_map(CUtensorMap* map, const void* base, long long rows, int kp, int box_rows) {
+// 2-D tensor map over a row-major [rows][kp] operand matrix of BF16 (esz 2)
+// or e4m3 bytes (esz 1), box [128 bytes x box_rows], 128-byte swizzle,
+// out-of-range rows read as zero.
+bool tc_make_map(CUtensorMap* map, const void* base, long long rows, int kp, int box_rows, int esz) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)kp * (cuuint64_t)esz};
+    const cuuint32_t box[2] = {(cuuint32_t)(esz == 1 ? kBK8 : kBK), (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+    return fn(map, esz == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+              const_cast<void*>(base), dims, strides, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 size_t tc_gemm_smem(bool split) { return (size_t)(split ? 2 : kStages) * (split ? 2 : 1) * (kAT + kBT) + 1024; }
 
-cudaError_t launch_tc_pack_rot(const float* rot, long long rot_off, int dim, int dpad, int kp, int np_rows,
-                               __nv_bfloat16* bq, __nv_bfloat16* bq_lo, long long brow, cudaStream_t st) {
-    k_tc_pack_rot<<<np_rows, 256, 0, st>>>(rot, rot_off, dim, dpad, kp, bq, bq_lo, brow);
+cudaError_t launch_tc_pack_rot(const float* rot, long long rot_off, int dim, int dpad, int kp, int np_rows, void* bq,
+                               void* bq_lo, long long brow, int fp8, unsigned* amax, float* bscale, cudaStream_t st) {
+    if (fp8) {
+        cudaError_t e = cudaMemsetAsync(amax, 0, sizeof(unsigned), st);
+        if (e != cudaSuccess) return e;
+        k_tc_rot_amax<<<64, 256, 0, st>>>(rot, rot_off, dim, dpad, amax);
+    }
+    k_tc_pack_rot<<<np_rows, 256, 0, st>>>(rot, rot_off, dim, dpad, kp, bq, bq_lo, brow, fp8, amax, bscale);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tc_eval(const InstDesc* desc, const TcPlan& p, const float* pop, const float* shift, float* fit,
                            int* status, cudaStream_t st) {
     if (p.n_rows <= 0) return cudaSuccess;
-    k_tc_pack_pop<<<(p.n_rows + 7) / 8, 256, 0, st>>>(desc, p.row_exec, p.n_rows, pop, shift, p.kp, p.aq,
-                                                       p.split ? p.aq_lo : nullptr);
+    const size_t smem_p = (size_t)8 * p.max_dpad * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_tc_pack_pop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p);
+    if (e != cudaSuccess) return e;
+    k_tc_pack_pop<<<(p.n_rows + 7) / 8, 256, smem_p, st>>>(desc, p.row_exec, p.n_rows, pop, shift, p.kp, p.aq,
+                                                            p.split ? p.aq_lo : nullptr, p.max_dpad, p.fp8, p.ascale);
     const size_t smem_g = tc_gemm_smem(p.split);
-    cudaError_t e = cudaFuncSetAttribute(k_rot_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_g);
+    e = cudaFuncSetAttribute(k_rot_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_g);
     if (e != cudaSuccess) return e;
     TcGemmArgs g;
     g.desc = desc;
     g.tiles = p.tiles;
     g.brow = p.brow;
     g.fu = fit;  // the epilogue writes f of each row straight into the fitness array
-    g.kt = p.kp / kBK;
+    g.kt = p.kp / (p.fp8 ? kBK8 : kBK);
     g.split = p.split;
+    g.fp8 = p.fp8;
+    g.ascale = p.ascale;
+    g.bscale = p.bscale;
     g.status = status;
     k_rot_tc<<<p.n_tiles, 128, smem_g, st>>>(p.mapA, p.mapB, p.split ? p.mapAlo : p.mapA, p.split ? p.mapBlo : p.mapB,
                                              g);
@@ -560,7 +656,7 @@ cudaError_t launch_tc_generation(const StepArgs& a, const TcPlan& p, cudaStream_
     cudaError_t e = cudaFuncSetAttribute(k_tc_trial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
     if (e != cudaSuccess) return e;
     k_tc_trial<<<blocks, 256, smem_t, st>>>(a, p.row_exec, p.n_rows, p.topk_all, p.uscr, p.aq, p.split ? p.aq_lo : nullptr,
-                                            p.kp, p.max_dpad);
+                                            p.kp, p.max_dpad, p.fp8, p.ascale);
     const size_t smem_g = tc_gemm_smem(p.split);
     e = cudaFuncSetAttribute(k_rot_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_g);
     if (e != cudaSuccess) return e;
@@ -569,8 +665,11 @@ cudaError_t launch_tc_generation(const StepArgs& a, const TcPlan& p, cudaStream_
     g.tiles = p.tiles;
     g.brow = p.brow;
     g.fu = p.fu;
-    g.kt = p.kp / kBK;
+    g.kt = p.kp / (p.fp8 ? kBK8 : kBK);
     g.split = p.split;
+    g.fp8 = p.fp8;
+    g.ascale = p.ascale;
+    g.bscale = p.bscale;
     g.status = a.status;
     if (gemm0) cudaEventRecord(gemm0, st);
     k_rot_tc<<<p.n_tiles, 128, smem_g, st>>>(p.mapA, p.mapB, p.split ? p.mapAlo : p.mapA, p.split ? p.mapBlo : p.mapB,
