@@ -359,40 +359,62 @@ struct ObjF {
 struct ObjR {
     float s0 = 0.f, s1 = 0.f, prev = 0.f, pre = 1.f;
     bool first = true;
-    __device__ __forceinline__ void push(int obj, float z, float inv_sqrt_j) {
-        switch (obj) {
-        case kSphere: s0 = fmaf(z, z, s0); break;
-        case kRosenbrock:
+    // One coordinate, objective fixed at compile time (no per-element switch,
+    // so independent elements of an unrolled block interleave).
+    template <int OBJ>
+    __device__ __forceinline__ void push_t(float z, float inv_sqrt_j) {
+        if constexpr (OBJ == kSphere) {
+            s0 = fmaf(z, z, s0);
+        } else if constexpr (OBJ == kRosenbrock) {
             if (!first) {
                 const float t = z - prev * (prev + 2.f);
                 s0 += 100.f * t * t + prev * prev;
             }
             prev = z;
             first = false;
-            break;
-        case kRastrigin: {
+        } else if constexpr (OBJ == kRastrigin) {
             const float sp = sinpif(z);
             s0 += z * z + 20.f * sp * sp;
-            break;
-        }
-        case kGriewank: {
+        } else if constexpr (OBJ == kGriewank) {
             s0 = fmaf(z, z, s0);
             const float h = sinf(0.5f * z * inv_sqrt_j);
             const float w = 2.f * h * h;
             s1 = fmaf(pre, w, s1);
             pre *= 1.f - w;
-            break;
-        }
-        case kAckley: {
+        } else if constexpr (OBJ == kAckley) {
             s0 = fmaf(z, z, s0);
             const float sp = sinpif(z);
             s1 = fmaf(sp, sp, s1);
-            break;
-        }
-        default:
+        } else {
             prev += z;
             s0 = fmaf(prev, prev, s0);
-            break;
+        }
+    }
+    __device__ __forceinline__ void push(int obj, float z, float inv_sqrt_j) {
+        switch (obj) {
+        case kSphere: push_t<kSphere>(z, inv_sqrt_j); break;
+        case kRosenbrock: push_t<kRosenbrock>(z, inv_sqrt_j); break;
+        case kRastrigin: push_t<kRastrigin>(z, inv_sqrt_j); break;
+        case kGriewank: push_t<kGriewank>(z, inv_sqrt_j); break;
+        case kAckley: push_t<kAckley>(z, inv_sqrt_j); break;
+        default: push_t<kSchwefel12>(z, inv_sqrt_j); break;
+        }
+    }
+    // 32 consecutive coordinates col0.. (those below dim), in order.
+    template <int OBJ>
+    __device__ __forceinline__ void push32_t(const float (&v)[32], int col0, int dim) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (col0 + j < dim) push_t<OBJ>(v[j], OBJ == kGriewank ? rsqrtf((float)(col0 + j + 1)) : 0.f);
+    }
+    __device__ __forceinline__ void push32(int obj, const float (&v)[32], int col0, int dim) {
+        switch (obj) {
+        case kSphere: push32_t<kSphere>(v, col0, dim); break;
+        case kRosenbrock: push32_t<kRosenbrock>(v, col0, dim); break;
+        case kRastrigin: push32_t<kRastrigin>(v, col0, dim); break;
+        case kGriewank: push32_t<kGriewank>(v, col0, dim); break;
+        case kAckley: push32_t<kAckley>(v, col0, dim); break;
+        default: push32_t<kSchwefel12>(v, col0, dim); break;
         }
     }
     __device__ __forceinline__ float finish(int obj, int dim) const {

@@ -34,7 +34,7 @@ namespace {
 constexpr int kBM = 128, kBN = 256, kBK = 64;           // BF16: a 64-element K tile is one 128-byte row
 constexpr int kBK8 = 128;                                 // FP8: a 128-element K tile is one 128-byte row
 constexpr float kE4M3Max = 448.0f;                        // largest finite e4m3 value
-constexpr int kStages = 4;
+constexpr int kStages = 2;                                 // 2 stages (97 KB): two CTAs share an SM
 constexpr int kAT = kBM * kBK * 2;                        // 16 KB
 constexpr int kBT = kBN * kBK * 2;                        // 32 KB
 constexpr uint32_t kWaitLimit = 1u << 22;                 // try_wait rounds before giving up (seconds)
@@ -147,7 +147,7 @@ struct TcGemmArgs {
 
 // 128 threads: thread 0 issues TMA and MMA; all four warps run the epilogue
 // (warp w owns TMEM lanes 32w..32w+31, i.e. tile rows 32w..32w+31).
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(128, 2)
     k_rot_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
              const __grid_constant__ CUtensorMap tmAlo, const __grid_constant__ CUtensorMap tmBlo, TcGemmArgs a) {
     extern __shared__ uint8_t smraw[];
@@ -269,10 +269,7 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
                     for (int j = 0; j < 32; ++j) v[j] *= zs;
                 }
-#pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    if (col0 + j < d.dim)
-                        acc.push(d.obj, v[j], d.obj == kGriewank ? rsqrtf((float)(col0 + j + 1)) : 0.f);
+                acc.push32(d.obj, v, col0, d.dim);
             }
         }
         tc_fence_before();
