@@ -400,6 +400,24 @@ struct ObjR {
         default: push_t<kSchwefel12>(z, inv_sqrt_j); break;
         }
     }
+    // Four consecutive coordinates, one dispatch.
+    template <int OBJ>
+    __device__ __forceinline__ void push4_t(float z0, float z1, float z2, float z3, const float* isq) {
+        push_t<OBJ>(z0, isq[0]);
+        push_t<OBJ>(z1, isq[1]);
+        push_t<OBJ>(z2, isq[2]);
+        push_t<OBJ>(z3, isq[3]);
+    }
+    __device__ __forceinline__ void push4(int obj, float z0, float z1, float z2, float z3, const float* isq) {
+        switch (obj) {
+        case kSphere: push4_t<kSphere>(z0, z1, z2, z3, isq); break;
+        case kRosenbrock: push4_t<kRosenbrock>(z0, z1, z2, z3, isq); break;
+        case kRastrigin: push4_t<kRastrigin>(z0, z1, z2, z3, isq); break;
+        case kGriewank: push4_t<kGriewank>(z0, z1, z2, z3, isq); break;
+        case kAckley: push4_t<kAckley>(z0, z1, z2, z3, isq); break;
+        default: push4_t<kSchwefel12>(z0, z1, z2, z3, isq); break;
+        }
+    }
     // 32 consecutive coordinates col0.. (those below dim), in order.
     template <int OBJ>
     __device__ __forceinline__ void push32_t(const float (&v)[32], int col0, int dim) {

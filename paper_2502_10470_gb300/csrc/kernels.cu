@@ -473,10 +473,7 @@ __device__ __forceinline__ void small_executor(const StepArgs& a, int k, const I
                     z2 = fmaf(q2.x, d0, z2); z2 = fmaf(q2.y, d1, z2); z2 = fmaf(q2.z, d2, z2); z2 = fmaf(q2.w, d3, z2);
                     z3 = fmaf(q3.x, d0, z3); z3 = fmaf(q3.y, d1, z3); z3 = fmaf(q3.z, d2, z3); z3 = fmaf(q3.w, d3, z3);
                 }
-                acc.push(obj, z0, isq[r]);
-                acc.push(obj, z1, isq[r + 1]);
-                acc.push(obj, z2, isq[r + 2]);
-                acc.push(obj, z3, isq[r + 3]);
+                acc.push4(obj, z0, z1, z2, z3, isq + r);
             }
             for (; r < dim; ++r) {
                 const float4* Rr = reinterpret_cast<const float4*>(R + r * DMAX);
