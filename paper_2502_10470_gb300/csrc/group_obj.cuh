@@ -42,10 +42,12 @@ struct GroupObj {
 };
 
 // Row block r0: this lane contributes z of row r0 + s (ignored past dim).
-template <int S>
+// OBJ < 0: the objective is the runtime value obj.
+template <int S, int OBJ = -1>
 __device__ __forceinline__ void group_obj_push(int obj, GroupObj& acc, float z, int r0, int s, int dim) {
     const int r = r0 + s;
     const bool valid = r < dim;
+    if (OBJ >= 0) obj = OBJ;
     switch (obj) {
     case kSphere:
         if (valid) acc.s0 = fmaf(z, z, acc.s0);
@@ -145,10 +147,11 @@ struct GroupDiff {
     bool has_pend = false;
 };
 
-template <int S>
+template <int S, int OBJ = -1>
 __device__ __forceinline__ void group_diff_push(int obj, GroupDiff& g, float z, float dz, int r0, int s, int dim) {
     const int r = r0 + s;
     const bool valid = r < dim;
+    if (OBJ >= 0) obj = OBJ;
     switch (obj) {
     case kSphere:
         if (valid) g.d0 += dz * (2.f * z + dz);
@@ -238,6 +241,46 @@ __device__ __forceinline__ float group_diff_finish(int obj, GroupDiff& g, int di
                2.71828182845904523536f * expf(-2.f * g.x1 / dim) * expm1f(-2.f * g.d1 / dim);
     }
     return g.d0;
+}
+
+// A whole row z[0..dim) held in shared memory, in blocks of S (lane s reads
+// z[r0 + s], which must exist up to the row's padded length): f, with one
+// dispatch on the objective per row instead of one per element.
+template <int S, int OBJ>
+__device__ __forceinline__ float group_obj_row_t(const float* z, int s, int dim) {
+    GroupObj acc;
+    for (int r0 = 0; r0 < dim; r0 += S) group_obj_push<S, OBJ>(OBJ, acc, z[r0 + s], r0, s, dim);
+    return group_obj_finish<S>(OBJ, acc, dim);
+}
+template <int S>
+__device__ __forceinline__ float group_obj_row(int obj, const float* z, int s, int dim) {
+    switch (obj) {
+    case kSphere: return group_obj_row_t<S, kSphere>(z, s, dim);
+    case kRosenbrock: return group_obj_row_t<S, kRosenbrock>(z, s, dim);
+    case kRastrigin: return group_obj_row_t<S, kRastrigin>(z, s, dim);
+    case kGriewank: return group_obj_row_t<S, kGriewank>(z, s, dim);
+    case kAckley: return group_obj_row_t<S, kAckley>(z, s, dim);
+    default: return group_obj_row_t<S, kSchwefel12>(z, s, dim);
+    }
+}
+
+// f(u) - f(x) from whole rows z and dz in shared memory, like group_obj_row.
+template <int S, int OBJ>
+__device__ __forceinline__ float group_diff_row_t(const float* z, const float* dz, int s, int dim) {
+    GroupDiff g;
+    for (int r0 = 0; r0 < dim; r0 += S) group_diff_push<S, OBJ>(OBJ, g, z[r0 + s], dz[r0 + s], r0, s, dim);
+    return group_diff_finish<S>(OBJ, g, dim);
+}
+template <int S>
+__device__ __forceinline__ float group_diff_row(int obj, const float* z, const float* dz, int s, int dim) {
+    switch (obj) {
+    case kSphere: return group_diff_row_t<S, kSphere>(z, dz, s, dim);
+    case kRosenbrock: return group_diff_row_t<S, kRosenbrock>(z, dz, s, dim);
+    case kRastrigin: return group_diff_row_t<S, kRastrigin>(z, dz, s, dim);
+    case kGriewank: return group_diff_row_t<S, kGriewank>(z, dz, s, dim);
+    case kAckley: return group_diff_row_t<S, kAckley>(z, dz, s, dim);
+    default: return group_diff_row_t<S, kSchwefel12>(z, dz, s, dim);
+    }
 }
 
 }  // namespace metade

@@ -210,10 +210,7 @@ __global__ void __launch_bounds__(256, 2) k_fused_tile(StepArgs a, const int* __
                 // blocks of 4 rows (the loop is warp-uniform; rows past nv are zero)
                 for (int tb = 0; tb < nv; tb += nt >> 2) {
                     const int t = tb + (tid >> 2), s = tid & 3;
-                    const float* zr = Z + (size_t)t * zp;
-                    GroupObj acc;
-                    for (int r0 = 0; r0 < dim; r0 += 4) group_obj_push<4>(d.obj, acc, zr[r0 + s], r0, s, dim);
-                    const float fv = group_obj_finish<4>(d.obj, acc, dim);
+                    const float fv = group_obj_row<4>(d.obj, Z + (size_t)t * zp, s, dim);
                     if (s == 0 && t < nv) fu[t0 + t] = nan_to_inf(fv);
                 }
                 __syncthreads();
@@ -277,9 +274,7 @@ __global__ void __launch_bounds__(256, 2) k_fused_tile(StepArgs a, const int* __
                 if (tid < 2 * kT) {  // warp-uniform: four lanes for each of the kT / 2 column pairs
                     const int tt = tid >> 2, s = tid & 3;
                     const float* zr = Z + (size_t)(2 * tt) * zp;
-                    GroupDiff g;
-                    for (int r0 = 0; r0 < dim; r0 += 4) group_diff_push<4>(d.obj, g, zr[r0 + s], zr[zp + r0 + s], r0, s, dim);
-                    const float df = group_diff_finish<4>(d.obj, g, dim);
+                    const float df = group_diff_row<4>(d.obj, zr, zr + zp, s, dim);
                     if (s == 0 && tt < nb) {
                         const int i = tl[b0 + tt];
                         if (!idf[tt]) {
