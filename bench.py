@@ -49,8 +49,10 @@ def parse_args(argv=None):
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison arm")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--inner-gens", type=int, default=INNER_GENS)
-    ap.add_argument("--workload", default="moderate", choices=["moderate", "precision", "batching"],
-                    help="moderate: the headline workload; precision: the D=1000 precision study")
+    ap.add_argument("--workload", default="moderate", choices=["moderate", "precision", "batching", "full"],
+                    help="moderate: the headline workload; precision: the D=1000 precision study; batching: "
+                         "512 ragged executors; full: 8 MetaDE runs x 128 executors")
+    ap.add_argument("--seeds", type=int, default=5, help="whole MetaDE runs of the full workload")
     ap.add_argument("--n-inst", type=int, default=64, help="executors of the precision study")
     ap.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES),
                     help="run one small untimed case for an ncu capture and exit")
@@ -563,6 +565,88 @@ def run_batching(args):
     print(json.dumps(line), flush=True)
 
 
+def run_full(args):
+    """The full workload: 8 MetaDE runs x 128 executors (1024 inner DEs), NP
+    ~ U{50..200}, D in {20, 50, 100, 200}, one-shot, 200 inner generations
+    per evolver generation (all D < 256, so every executor is on the FP32
+    CUDA-core kernels).  Per evolver generation: the batched path
+    (metade_outer_generation, CUDA graph, tuned plan) against the plain FP32
+    path (one executor per launch per generation, no graph, no tuning), both
+    timed with CUDA events after an L2 flush.  Then whole MetaDE runs (50
+    evolver generations) of the batched path over --seeds seeds: the final
+    error of each run, and the wall time of a whole run."""
+    import numpy as np
+    import torch
+    import paper_2502_10470_gb300 as M
+    import synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    wl = synth.full()
+    probs = [(p.dim, p.obj, p.shift, p.rot) for p in wl.problems]
+    gens = wl.inner_gens
+    units = float(wl.inst_np.sum()) * gens
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def make(path, seed):
+        return M.Batch(probs, wl.inst_np, wl.inst_prob, wl.inst_group, seed=seed, one_shot=1, n_out=wl.n_out,
+                       path=path, device=dev, stream=stream.cuda_stream)
+
+    out = {}
+    for name, path, steps, warm in (("batched", M.METADE_PATH_BATCHED, args.steps, args.warmup),
+                                    ("plain", M.METADE_PATH_PLAIN, 1, 0)):
+        b = make(path, 0)
+        M.metade_outer_init(b.ctx, b.opop, b.ofit)
+        og = 0
+        if path == M.METADE_PATH_BATCHED:
+            M.metade_outer_step(b.ctx, b.opop, b.ofit, b.trial, b.theta, None, 0, 0)
+            M.metade_init(b.ctx, b.pop, b.fit, 0)
+            M.metade_autotune(b.ctx, b.pop, b.fit, b.theta, 5)
+        use_graph = path == M.METADE_PATH_BATCHED
+        for _ in range(warm):
+            M.metade_outer_generation(b.ctx, b.opop, b.ofit, b.trial, b.theta, b.pop, b.fit, b.best_f, b.best_i,
+                                      og, gens, use_graph)
+            og += 1
+        torch.cuda.synchronize()
+        evs = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            M.metade_outer_generation(b.ctx, b.opop, b.ofit, b.trial, b.theta, b.pop, b.fit, b.best_f, b.best_i,
+                                      og, gens, use_graph)
+            e1.record(stream)
+            evs.append((e0, e1))
+            og += 1
+        torch.cuda.synchronize()
+        if M.metade_sync(b.ctx) != M.METADE_OK:
+            raise RuntimeError("device status")
+        ms = float(np.mean([a.elapsed_time(c) for a, c in evs]))
+        out[name] = {"ms_per_outer_generation": ms, "indiv_gens_per_s": units / (ms / 1e3), "steps": steps,
+                     "plan": json.loads(M.metade_plan_info(b.ctx))}
+        b.close()
+    finals, run_s = [], []
+    for seed in range(args.seeds):
+        b = make(M.METADE_PATH_BATCHED, seed)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, ofit = b.run_metade(wl.outer_gens, gens)
+        run_s.append(time.perf_counter() - t0)
+        finals.append(ofit.min(axis=1).astype(np.float64))
+        b.close()
+    finals = np.array(finals)  # [seeds][runs]
+    line = {"metric": "full workload: individual-gens/s per evolver generation, batched vs plain FP32",
+            "workload": wl.name, "executors": wl.n_inst, "individuals": wl.individuals(),
+            "inner_gens_per_outer_generation": gens, "results": out,
+            "speedup_vs_plain": out["batched"]["indiv_gens_per_s"] / out["plain"]["indiv_gens_per_s"],
+            "whole_runs": {"seeds": args.seeds, "outer_gens": wl.outer_gens,
+                           "wall_s_per_run_median": float(np.median(run_s)),
+                           "final_error_median_per_run": [float(v) for v in np.median(finals, axis=0)],
+                           "problems": [{"dim": p.dim, "obj": p.obj} for p in wl.problems]},
+            "l2": "flushed before every timed evolver generation"}
+    print(json.dumps(line), flush=True)
+
+
 def _case_tile_d100():
     """The D = 100 executors of the batching study (133 executors, 27556
     individuals), 20 fused generations: one k_fused_tile launch."""
@@ -612,6 +696,9 @@ def main(argv=None):
         return
     if args.workload == "batching":
         run_batching(args)
+        return
+    if args.workload == "full":
+        run_full(args)
         return
     if args.impl == "reference":
         run_reference(args)
