@@ -241,7 +241,7 @@ def metade_autotune(ctx: int, pop, fit, theta, n_gens: int = 3) -> None:
     _check(_lib().metade_autotune(ctx, _ptr(pop), _ptr(fit), _ptr(theta), n_gens), "metade_autotune")
 
 
-PROFILE_KINDS = ["fused_small", "fused_general", "tc_gemm", "tc_generation", "fused_group", "fused_tile"]
+PROFILE_KINDS = ["fused_small", "fused_general", "tc_gemm", "tc_generation", "fused_tile_stream", "fused_tile"]
 
 
 def metade_profile(ctx: int, enable: bool) -> None:

@@ -31,7 +31,7 @@ enum ProfKind {
     kProfFusedGeneral = 1,
     kProfTcGemm = 2,
     kProfTcGeneration = 3,
-    kProfFusedGroup = 4,
+    kProfFusedTileStream = 4,
     kProfFusedTile = 5,
     kProfKinds = 6
 };
@@ -144,19 +144,19 @@ double work_cost(const InstDesc& d) { return (double)d.np * ((double)d.dim * d.d
 // Kernel kind per executor and the work order inside each bucket (largest
 // first, so the block scheduler hands the longest executors out first).
 metade_status build_plan(metade_ctx* c) {
-    std::vector<std::vector<int>> small(33), group(9);
-    std::vector<int> general, tile;
+    std::vector<std::vector<int>> small(33);
+    std::vector<int> general, tile, tile_stream;
     for (int k = 0; k < c->n_inst; ++k) {
         if (c->tc && c->is_tc[k]) continue;
         const InstDesc& d = c->hdesc[k];
         const int dm = small_dmax_for(d.dim);
-        const int S = group_lanes_for(d.dpad);
-        // The tile and group kernels decide near ties by the FP32 difference
-        // form only; FP64 tie re-evaluation runs in the small and general kernels.
+        // The tile kernels decide near ties by the FP32 difference form only;
+        // FP64 tie re-evaluation runs in the small and general kernels.
         const bool fp32_ties = !c->tie_fp64;
         if (dm > 0 && fused_smem_small(dm, d.np) <= kSmemLimit) small[dm].push_back(k);
-        else if (fp32_ties && d.dpad <= 128 && fused_smem_tile(d.np, d.dpad, 256) <= kSmemLimit) tile.push_back(k);
-        else if (fp32_ties && S > 0 && fused_smem_group(d.np, d.dpad, 128, false) <= kSmemLimit) group[S].push_back(k);
+        else if (fp32_ties && d.dpad <= 128 && fused_smem_tile(d.np, d.dpad, 256, true) <= kSmemLimit) tile.push_back(k);
+        else if (fp32_ties && d.dpad <= 256 && fused_smem_tile(d.np, d.dpad, 256, false) <= kSmemLimit)
+            tile_stream.push_back(k);
         else general.push_back(k);
     }
     std::vector<int> order;
@@ -184,10 +184,13 @@ metade_status build_plan(metade_ctx* c) {
         order.insert(order.end(), small[dm].begin(), small[dm].end());
         c->buckets.push_back(b);
     }
-    if (!tile.empty()) {
-        sort_desc(tile);
+    // tile buckets: R^T resident (D_pad <= 128) and streamed (D_pad <= 256)
+    for (int mode = 1; mode >= 0; --mode) {
+        std::vector<int>& tv = mode ? tile : tile_stream;
+        if (tv.empty()) continue;
+        sort_desc(tv);
         int mnp = 0, mdp = 0;
-        for (int k : tile) {
+        for (int k : tv) {
             mnp = std::max(mnp, c->hdesc[k].np);
             mdp = std::max(mdp, c->hdesc[k].dpad);
         }
@@ -195,40 +198,16 @@ metade_status build_plan(metade_ctx* c) {
         b.plan.kind = 3;
         b.plan.dmax = 0;
         b.plan.threads = 256;
-        b.plan.grid = (int)tile.size();
+        b.plan.grid = (int)tv.size();
         b.plan.max_np = mnp;
         b.plan.max_dpad = mdp;
-        b.plan.rot_smem = 1;
+        b.plan.rot_smem = mode;
         b.plan.pop_smem = 0;
-        b.plan.smem = fused_smem_tile(mnp, mdp, 256);
+        b.plan.smem = fused_smem_tile(mnp, mdp, 256, mode != 0);
         if (b.plan.smem > kSmemLimit) return METADE_EUNSUPPORTED;
         b.work_off = (int)order.size();
-        b.n_work = (int)tile.size();
-        order.insert(order.end(), tile.begin(), tile.end());
-        c->buckets.push_back(b);
-    }
-    for (int S = 2; S <= 8; S <<= 1) {
-        if (group[S].empty()) continue;
-        sort_desc(group[S]);
-        int mnp = 0, mdp = 0;
-        for (int k : group[S]) {
-            mnp = std::max(mnp, c->hdesc[k].np);
-            mdp = std::max(mdp, c->hdesc[k].dpad);
-        }
-        Bucket b;
-        b.plan.kind = 2;
-        b.plan.dmax = S;
-        b.plan.threads = std::min(512, std::max(128, (mnp * S + 31) / 32 * 32));
-        b.plan.grid = (int)group[S].size();
-        b.plan.max_np = mnp;
-        b.plan.max_dpad = mdp;
-        b.plan.pop_smem = fused_smem_group(mnp, mdp, b.plan.threads, false, true) <= kSmemLimit ? 1 : 0;
-        b.plan.rot_smem = fused_smem_group(mnp, mdp, b.plan.threads, true, b.plan.pop_smem != 0) <= kSmemLimit ? 1 : 0;
-        b.plan.smem = fused_smem_group(mnp, mdp, b.plan.threads, b.plan.rot_smem != 0, b.plan.pop_smem != 0);
-        if (b.plan.smem > kSmemLimit) return METADE_EUNSUPPORTED;
-        b.work_off = (int)order.size();
-        b.n_work = (int)group[S].size();
-        order.insert(order.end(), group[S].begin(), group[S].end());
+        b.n_work = (int)tv.size();
+        order.insert(order.end(), tv.begin(), tv.end());
         c->buckets.push_back(b);
     }
     if (!general.empty()) {
@@ -299,8 +278,7 @@ metade_status run_inner(metade_ctx* c, cudaStream_t st, float* pop, float* fit, 
         cudaEvent_t e0, e1;
         const bool pr = prof_pair(c, st,
                                   b.plan.kind == 0   ? kProfFusedSmall
-                                  : b.plan.kind == 2 ? kProfFusedGroup
-                                  : b.plan.kind == 3 ? kProfFusedTile
+                                  : b.plan.kind == 3 ? (b.plan.rot_smem ? kProfFusedTile : kProfFusedTileStream)
                                                      : kProfFusedGeneral,
                                   &e0, &e1);
         if (pr) cudaEventRecord(e0, st);
@@ -815,8 +793,7 @@ metade_status metade_autotune(metade_ctx* c, const float* pop, const float* fit,
         if (st != METADE_OK) break;
         std::vector<int> cands = b.plan.kind == 0 ? std::vector<int>{32, 64, 128, 256}
                                                   : std::vector<int>{128, 256, 512};
-        if (b.plan.kind == 2 && b.plan.max_np * b.plan.dmax <= 256) cands = {64, 128, 256};
-        if (b.plan.kind == 3) cands = {128, 256};
+        if (b.plan.kind == 3) cands = b.plan.rot_smem ? std::vector<int>{128, 256} : std::vector<int>{256};
         FusedPlan best = b.plan;
         float best_ms = -1.f;
         b.tuned.clear();
@@ -827,11 +804,8 @@ metade_status metade_autotune(metade_ctx* c, const float* pop, const float* fit,
                 p.rot_smem = fused_smem_general(p.max_np, p.max_dpad, th, true) <= kSmemLimit ? 1 : 0;
                 p.smem = fused_smem_general(p.max_np, p.max_dpad, th, p.rot_smem != 0);
                 if (p.smem > kSmemLimit) continue;
-            } else if (p.kind == 2) {
-                p.smem = fused_smem_group(p.max_np, p.max_dpad, th, p.rot_smem != 0, p.pop_smem != 0);
-                if (p.smem > kSmemLimit) continue;
             } else if (p.kind == 3) {
-                p.smem = fused_smem_tile(p.max_np, p.max_dpad, th);
+                p.smem = fused_smem_tile(p.max_np, p.max_dpad, th, p.rot_smem != 0);
                 if (p.smem > kSmemLimit) continue;
             } else if (th < 32) {
                 continue;
@@ -877,8 +851,7 @@ metade_status metade_plan_info(const metade_ctx* c, char* buf, size_t len) {
                  "\"rot_smem\": %d, \"pop_smem\": %d, \"executors\": %d",
                  b ? ", " : "",
                  k.plan.kind == 0   ? "fused_small"
-                 : k.plan.kind == 2 ? "fused_group"
-                 : k.plan.kind == 3 ? "fused_tile"
+                 : k.plan.kind == 3 ? (k.plan.rot_smem ? "fused_tile" : "fused_tile_stream")
                                     : "fused_general",
                  k.plan.dmax,
                  k.plan.threads,

@@ -55,14 +55,14 @@ cudaError_t launch_plain_generation(const StepArgs& a, int k, const InstDesc& d,
 
 // Batched path: executors listed in `work` (schedule order), all n_gens generations.
 struct FusedPlan {
-    int kind;      // 0 small (thread per individual), 1 general (warp per individual), 2 group (S lanes),
+    int kind;      // 0 small (thread per individual), 1 general (warp per individual),
                    // 3 tile (register-blocked rotation GEMM per tile of individuals)
-    int dmax;      // small: compile-time row bound; group: lanes per individual S
+    int dmax;      // small: compile-time row bound
     int threads;   // block size
     int grid;      // CTAs (<= n_work; CTAs loop over work items)
     size_t smem;   // dynamic shared memory per CTA
-    int rot_smem;  // general: R^T staged in shared memory; group: R staged
-    int pop_smem;  // group: the population resident in shared memory for all fused generations
+    int rot_smem;  // general, tile: R^T staged in shared memory (tile: else streamed by chunks)
+    int pop_smem;  // small: the population resident in shared memory for all fused generations
     int max_np, max_dpad;  // general: bucket maxima the shared layout is cut for
 };
 cudaError_t launch_fused(const StepArgs& a, const int* work, int n_work, const FusedPlan& p, float* u_scratch,
@@ -70,11 +70,7 @@ cudaError_t launch_fused(const StepArgs& a, const int* work, int n_work, const F
 size_t fused_smem_small(int dmax, int max_np);
 size_t fused_smem_general(int max_np, int max_dpad, int threads, bool rot_in_smem);
 int small_dmax_for(int dim);  // 0 when the small kernel does not apply
-int group_lanes_for(int dpad);  // 0 when the group kernel does not apply
-size_t fused_smem_group(int max_np, int max_dpad, int threads, bool rot_in_smem, bool pop_in_smem = false);
-cudaError_t launch_fused_group(const StepArgs& a, const int* work, int n_work, const FusedPlan& p, float* u_scratch,
-                               cudaStream_t st);
-size_t fused_smem_tile(int max_np, int max_dpad, int threads);
+size_t fused_smem_tile(int max_np, int max_dpad, int threads, bool rot_smem);
 cudaError_t launch_fused_tile(const StepArgs& a, const int* work, int n_work, const FusedPlan& p, float* u_scratch,
                               cudaStream_t st);
 

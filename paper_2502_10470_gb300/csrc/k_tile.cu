@@ -60,10 +60,96 @@ __device__ __forceinline__ void tile_gemm(const float* dT, const float* RT, floa
     }
 }
 
+// R^T streamed from global memory (executors whose R^T does not stay in
+// shared memory, 128 < D_pad <= 256): kKC rows of R^T at a time go through a
+// double-buffered cp.async stage; every thread keeps the accumulators of up
+// to four 4x4 blocks of Z (the same tx, ty = ty0 + 16 j) in registers across
+// the chunks, so the fma chain of each z is the same as above.  256 threads.
+// Z may alias dT: it is written after the last chunk's barrier.
+constexpr int kKC = 16;
+
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ void stage_rt(float* dst, const float* __restrict__ gRT, int k0, int kn, int dp) {
+    const int n4 = kn * (dp >> 2);
+    const float* src = gRT + (size_t)k0 * dp;
+    for (int e = threadIdx.x; e < n4; e += blockDim.x) cp_async16(dst + 4 * e, src + 4 * e);
+}
+
+__device__ __forceinline__ void tile_gemm_stream(const float* dT, const float* __restrict__ gRT, float* rbuf, float* Z,
+                                                 int dim, int nbr, int dp, int zp) {
+    constexpr int nbt = kT / 4;                  // 16 column blocks of the tile
+    const int tid = threadIdx.x;
+    const int tx = tid % nbt, ty0 = tid / nbt;   // 256 threads: ty0 < 16, blocks ty0 + 16 j, j < 4
+    const int nj = ty0 < nbr ? (nbr - ty0 + 15) / 16 : 0;
+    float acc[4][4][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[j][p][q] = 0.f;
+    const int nch = (dim + kKC - 1) / kKC;
+    stage_rt(rbuf, gRT, 0, min(kKC, dim), dp);
+    cp_async_commit();
+    const float* pa = dT + 4 * tx;
+    for (int ch = 0; ch < nch; ++ch) {
+        if (ch + 1 < nch) {
+            stage_rt(rbuf + ((ch + 1) & 1) * kKC * dp, gRT, (ch + 1) * kKC, min(kKC, dim - (ch + 1) * kKC), dp);
+            cp_async_commit();
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const float* rb = rbuf + (ch & 1) * kKC * dp + 4 * ty0;
+        const int k0 = ch * kKC, kn = min(kKC, dim - k0);
+        for (int kk = 0; kk < kn; ++kk) {
+            const float4 av = *reinterpret_cast<const float4*>(pa + (size_t)(k0 + kk) * kTP);
+            const float ar[4] = {av.x, av.y, av.z, av.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (j < nj) {
+                    const float4 rv = *reinterpret_cast<const float4*>(rb + (size_t)kk * dp + 64 * j);
+                    const float rr[4] = {rv.x, rv.y, rv.z, rv.w};
+#pragma unroll
+                    for (int p = 0; p < 4; ++p)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) acc[j][p][q] = fmaf(rr[q], ar[p], acc[j][p][q]);
+                }
+            }
+        }
+        __syncthreads();  // every thread is done with this buffer (and, after the last chunk, with dT)
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (j < nj) {
+            const int ty = ty0 + 16 * j;
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+                *reinterpret_cast<float4*>(Z + (size_t)(4 * tx + p) * zp + 4 * ty) =
+                    make_float4(acc[j][p][0], acc[j][p][1], acc[j][p][2], acc[j][p][3]);
+        }
+    }
+}
+
 // Shared words before R^T: f, fu, ranks/flags, tie list, 64 reduction words,
 // the tie count and kT / 2 identity flags; a multiple of 4 (float4 alignment).
 __host__ __device__ constexpr int tile_header_words(int max_np) { return (4 * max_np + 64 + 1 + kT / 2 + 3) & ~3; }
 
+// Streamed layout: the dT / Z union (dT is dead when Z is written).
+__host__ __device__ constexpr int tile_dz_words(int max_dpad) {
+    return max_dpad * kTP > kT * tile_zp(max_dpad) ? max_dpad * kTP : kT * tile_zp(max_dpad);
+}
+
+// RS: R^T resident in shared memory (D_pad <= 128); otherwise streamed.
+template <bool RS>
 __global__ void __launch_bounds__(256, 2) k_fused_tile(StepArgs a, const int* __restrict__ work, int n_work,
                                                        float* uscr, int max_np, int max_dpad) {
     extern __shared__ __align__(16) float sm[];
@@ -75,11 +161,25 @@ __global__ void __launch_bounds__(256, 2) k_fused_tile(StepArgs a, const int* __
     int* red = tl + max_np;                                        // 64 words (block reductions)
     int* ntie = red + 64;                                          // tie count, then kT / 2 identity flags
     int* idf = ntie + 1;
-    float* RT = sm + tile_header_words(max_np);                    // [dim][dp]
-    float* dT = RT + (size_t)max_dpad * max_dpad;                  // [dp][kTP]
     const int zp = tile_zp(max_dpad);                              // Z row length
-    float* Z = dT + (size_t)max_dpad * kTP;                        // [kT][zp]
-    int* recs = reinterpret_cast<int*>(Z);                         // [kRec][kT], dead before Z is written
+    float* RT;    // resident: [dim][dp]
+    float* dT;    // [dp][kTP]
+    float* Z;     // [kT][zp]
+    float* rbuf;  // streamed: 2 x [kKC][dp]
+    int* recs;    // [kRec][kT]
+    if (RS) {
+        RT = sm + tile_header_words(max_np);
+        dT = RT + (size_t)max_dpad * max_dpad;
+        Z = dT + (size_t)max_dpad * kTP;
+        rbuf = nullptr;
+        recs = reinterpret_cast<int*>(Z);  // dead before Z is written
+    } else {
+        RT = nullptr;
+        dT = sm + tile_header_words(max_np);
+        Z = dT;                            // written after the GEMM's last read of dT
+        rbuf = dT + tile_dz_words(max_dpad);
+        recs = reinterpret_cast<int*>(rbuf + 2 * kKC * max_dpad);
+    }
     int* acc = topk;
     for (int w = blockIdx.x; w < n_work; w += gridDim.x) {
         const int k = work[w];
@@ -96,8 +196,9 @@ __global__ void __launch_bounds__(256, 2) k_fused_tile(StepArgs a, const int* __
         float* Ug = uscr + d.pop_off;
         const float* o = a.shift + d.shift_off;
         const float* gRT = a.rotT + d.rot_off;
-        for (int e = tid; e < dim * (dp >> 2); e += nt)
-            reinterpret_cast<float4*>(RT)[e] = reinterpret_cast<const float4*>(gRT)[e];
+        if (RS)
+            for (int e = tid; e < dim * (dp >> 2); e += nt)
+                reinterpret_cast<float4*>(RT)[e] = reinterpret_cast<const float4*>(gRT)[e];
         for (int i = tid; i < np; i += nt) f[i] = a.fit[d.fit_off + i];
         __syncthreads();
         const bool pb = st.uses_pbest();
@@ -204,7 +305,8 @@ __global__ void __launch_bounds__(256, 2) k_fused_tile(StepArgs a, const int* __
                     *reinterpret_cast<float4*>(Ug + (long long)i * dp + j4) = make_float4(u4[0], u4[1], u4[2], u4[3]);
                 }
                 __syncthreads();
-                tile_gemm(dT, RT, Z, dim, nbr, dp, zp);
+                if (RS) tile_gemm(dT, RT, Z, dim, nbr, dp, zp);
+                else tile_gemm_stream(dT, gRT, rbuf, Z, dim, nbr, dp, zp);
                 __syncthreads();
                 // objective: a group of 4 lanes per individual walks its Z row in
                 // blocks of 4 rows (the loop is warp-uniform; rows past nv are zero)
@@ -269,7 +371,8 @@ __global__ void __launch_bounds__(256, 2) k_fused_tile(StepArgs a, const int* __
                     col[0] = v4[0]; col[kTP] = v4[1]; col[2 * kTP] = v4[2]; col[3 * kTP] = v4[3];
                 }
                 __syncthreads();
-                tile_gemm(dT, RT, Z, dim, nbr, dp, zp);
+                if (RS) tile_gemm(dT, RT, Z, dim, nbr, dp, zp);
+                else tile_gemm_stream(dT, gRT, rbuf, Z, dim, nbr, dp, zp);
                 __syncthreads();
                 if (tid < 2 * kT) {  // warp-uniform: four lanes for each of the kT / 2 column pairs
                     const int tt = tid >> 2, s = tid & 3;
@@ -304,20 +407,30 @@ __global__ void __launch_bounds__(256, 2) k_fused_tile(StepArgs a, const int* __
     }
 }
 
-size_t fused_smem_tile(int max_np, int max_dpad, int threads) {
+size_t fused_smem_tile(int max_np, int max_dpad, int threads, bool rot_smem) {
+    (void)threads;
     size_t words = (size_t)tile_header_words(max_np);
-    words += (size_t)max_dpad * max_dpad;          // R^T
-    words += (size_t)max_dpad * kTP;               // dT
-    words += (size_t)kT * tile_zp(max_dpad);       // Z (draw records alias it)
+    if (rot_smem) {
+        words += (size_t)max_dpad * max_dpad;          // R^T
+        words += (size_t)max_dpad * kTP;               // dT
+        words += (size_t)kT * tile_zp(max_dpad);       // Z (draw records alias it)
+    } else {
+        words += (size_t)tile_dz_words(max_dpad);      // dT / Z
+        words += (size_t)2 * kKC * max_dpad;           // R^T stage
+        words += (size_t)kRec * kT;                    // draw records
+    }
     return words * sizeof(float);
 }
 
 cudaError_t launch_fused_tile(const StepArgs& a, const int* work, int n_work, const FusedPlan& p, float* uscr,
                               cudaStream_t st) {
     if (n_work <= 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_fused_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    if (p.threads != 128 && p.threads != 256) return cudaErrorInvalidValue;
+    if (!p.rot_smem && (p.threads != 256 || p.max_dpad > 256)) return cudaErrorInvalidValue;
+    auto kern = p.rot_smem ? k_fused_tile<true> : k_fused_tile<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
     if (e != cudaSuccess) return e;
-    k_fused_tile<<<p.grid, p.threads, p.smem, st>>>(a, work, n_work, uscr, p.max_np, p.max_dpad);
+    kern<<<p.grid, p.threads, p.smem, st>>>(a, work, n_work, uscr, p.max_np, p.max_dpad);
     return cudaGetLastError();
 }
 

@@ -705,7 +705,6 @@ cudaError_t launch_fused(const StepArgs& a, const int* work, int n_work, const F
         default: return cudaErrorInvalidValue;
         }
     }
-    if (p.kind == 2) return launch_fused_group(a, work, n_work, p, uscr, st);
     if (p.kind == 3) return launch_fused_tile(a, work, n_work, p, uscr, st);
     cudaError_t e = cudaFuncSetAttribute(k_fused_general, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
     if (e != cudaSuccess) return e;
