@@ -573,8 +573,11 @@ def run_full(args):
     (metade_outer_generation, CUDA graph, tuned plan) against the plain FP32
     path (one executor per launch per generation, no graph, no tuning), both
     timed with CUDA events after an L2 flush.  Then whole MetaDE runs (50
-    evolver generations) of the batched path over --seeds seeds: the final
-    error of each run, and the wall time of a whole run."""
+    evolver generations) of the batched path over --seeds seeds, with
+    one-shot evaluation (every executor of a run starts from the same
+    population and draw stream, Sec. III-C) and with a stream per executor:
+    the final error of each run per mode, the wall time of a whole run, and a
+    rank-sum p-value per run between the two modes."""
     import numpy as np
     import torch
     import paper_2502_10470_gb300 as M
@@ -588,9 +591,9 @@ def run_full(args):
     units = float(wl.inst_np.sum()) * gens
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
-    def make(path, seed):
-        return M.Batch(probs, wl.inst_np, wl.inst_prob, wl.inst_group, seed=seed, one_shot=1, n_out=wl.n_out,
-                       path=path, device=dev, stream=stream.cuda_stream)
+    def make(path, seed, one_shot=1):
+        return M.Batch(probs, wl.inst_np, wl.inst_prob, wl.inst_group, seed=seed, one_shot=one_shot,
+                       n_out=wl.n_out, path=path, device=dev, stream=stream.cuda_stream)
 
     out = {}
     for name, path, steps, warm in (("batched", M.METADE_PATH_BATCHED, args.steps, args.warmup),
@@ -625,23 +628,29 @@ def run_full(args):
         out[name] = {"ms_per_outer_generation": ms, "indiv_gens_per_s": units / (ms / 1e3), "steps": steps,
                      "plan": json.loads(M.metade_plan_info(b.ctx))}
         b.close()
-    finals, run_s = [], []
-    for seed in range(args.seeds):
-        b = make(M.METADE_PATH_BATCHED, seed)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        _, ofit = b.run_metade(wl.outer_gens, gens)
-        run_s.append(time.perf_counter() - t0)
-        finals.append(ofit.min(axis=1).astype(np.float64))
-        b.close()
-    finals = np.array(finals)  # [seeds][runs]
+    finals = {1: [], 0: []}
+    run_s = []
+    for one_shot in (1, 0):
+        for seed in range(args.seeds):
+            b = make(M.METADE_PATH_BATCHED, seed, one_shot)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, ofit = b.run_metade(wl.outer_gens, gens)
+            run_s.append(time.perf_counter() - t0)
+            finals[one_shot].append(ofit.min(axis=1).astype(np.float64))
+            b.close()
+    from scipy.stats import ranksums
+    f1, f0 = np.array(finals[1]), np.array(finals[0])  # [seeds][runs]
+    pvals = [float(ranksums(f1[:, r], f0[:, r])[1]) if args.seeds > 1 else None for r in range(f1.shape[1])]
     line = {"metric": "full workload: individual-gens/s per evolver generation, batched vs plain FP32",
             "workload": wl.name, "executors": wl.n_inst, "individuals": wl.individuals(),
             "inner_gens_per_outer_generation": gens, "results": out,
             "speedup_vs_plain": out["batched"]["indiv_gens_per_s"] / out["plain"]["indiv_gens_per_s"],
             "whole_runs": {"seeds": args.seeds, "outer_gens": wl.outer_gens,
                            "wall_s_per_run_median": float(np.median(run_s)),
-                           "final_error_median_per_run": [float(v) for v in np.median(finals, axis=0)],
+                           "final_error_median_per_run_one_shot": [float(v) for v in np.median(f1, axis=0)],
+                           "final_error_median_per_run_stream_per_executor": [float(v) for v in np.median(f0, axis=0)],
+                           "ranksum_p_per_run": pvals,
                            "problems": [{"dim": p.dim, "obj": p.obj} for p in wl.problems]},
             "l2": "flushed before every timed evolver generation"}
     print(json.dumps(line), flush=True)

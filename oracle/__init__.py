@@ -77,7 +77,9 @@ def lib():
         L.or_decode.argtypes = [P, P]
         L.or_outer_select.argtypes = [C.c_int, P, P, P, P, P]
         L.or_metade_run.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, P, P, C.c_double, C.c_double,
-                                    C.c_uint64, C.c_uint32, C.c_int, C.c_int, C.c_int, C.c_int, P, P]
+                                    C.c_uint64, C.c_uint32, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, P, P]
+        L.or_pso_move.argtypes = [C.c_int, C.c_uint64, C.c_uint32, C.c_uint32, C.c_double, C.c_double,
+                                  C.c_double, P, P, P, P]
         L.or_metade_run.restype = C.c_double
         _lib = L
     return _lib
@@ -208,14 +210,25 @@ def outer_select(pop, fit, trial, meta_fit):
     return pop, fit, acc
 
 
+def pso_move(pbest, pfit, x, v, seed: int, group: int, gen: int, w: float = 0.729, c1: float = 1.49,
+             c2: float = 1.49):
+    """PSO evolver move: returns the new positions and velocities (gen 0:
+    x = pbest, v = 0)."""
+    pbest, pfit = _f64(pbest), _f64(pfit)
+    x, v = _f64(x).copy(), _f64(v).copy()
+    lib().or_pso_move(pbest.shape[0], seed, group, gen, w, c1, c2, _p(pbest), _p(pfit), _p(x), _p(v))
+    return x, v
+
+
 def metade_run(n_out: int, np_: int, obj: int, o, R, inner_gens: int, outer_gens: int, *,
                seed: int, group: int = 0, power_up: bool = False,
-               lo: float = -100.0, hi: float = 100.0, p_best_pct: int = 10):
+               lo: float = -100.0, hi: float = 100.0, p_best_pct: int = 10, evolver: int = 0):
+    """evolver 0: DE/rand/1/bin (Alg. 3); 1: PSO (w = 0.729, c1 = c2 = 1.49)."""
     o, R = _f64(o), _f64(R)
     opop = np.zeros((n_out, 6))
     ofit = np.zeros(n_out)
     y = lib().or_metade_run(n_out, np_, o.shape[0], obj, _p(o), _p(R), lo, hi, seed, group,
-                            p_best_pct, inner_gens, outer_gens, int(power_up), _p(opop), _p(ofit))
+                            p_best_pct, inner_gens, outer_gens, int(power_up), int(evolver), _p(opop), _p(ofit))
     return y, opop, ofit
 
 

@@ -6,8 +6,9 @@
  * Sec. III-A-2, "DE/bl-to-br/dn"), the three crossover schemes of Sec. II-A
  * (binomial, exponential, arithmetic), greedy selection (Alg. 1/2), the
  * best-fitness reduction that becomes the meta-fitness (Sec. III-B), the
- * evolver's rand/1/bin step with floor decoding (Alg. 3), and the synthetic
- * shifted-rotated objectives used as the CEC2022 stand-in.
+ * evolver's rand/1/bin step with floor decoding (Alg. 3), the PSO evolver of
+ * the supplement's comparison of evolvers, and the synthetic shifted-rotated
+ * objectives used as the CEC2022 stand-in.
  *
  * Only the tests, the smoke check and the benchmark's CPU-baseline leg may
  * load this file.  It shares no code, header or table with the CUDA path;
@@ -492,6 +493,51 @@ void or_outer_select(int n_out, double *pop, double *fit, const double *trial,
 }
 
 /*
+ * PSO as the evolver (the supplement's comparison of evolvers: inertia
+ * weight w and acceleration coefficients c1, c2; the paper sets w = 0.729,
+ * c1 = c2 = 1.49).  Particle i has a position x (the vector evaluated this
+ * generation), a velocity v, and a personal best pbest with fitness pfit,
+ * which play the evolver population and fitness of Alg. 3.  Generation 0
+ * evaluates the initial swarm: x = pbest (from or_outer_init), v = 0.  From
+ * generation 1 every particle moves toward its own best and the run's best
+ * gbest (the personal best of lowest fitness, ties to the lower index):
+ *   v_j <- w v_j + c1 r1_j (pbest_j - x_j) + c2 r2_j (gbest_j - x_j)
+ *   x_j <- x_j + v_j, clipped to [lb_j, ub_j] (v is kept as computed)
+ * with r1_j, r2_j uniform in [0, 1): evolver draw slots 0-2, r1 = words
+ * 0..5 and r2 = words 6..11 (slot = word / 4).  Selection is that of Alg. 3
+ * (or_outer_select: x replaces pbest when its meta-fitness is <=).
+ */
+void or_pso_move(int n_out, uint64_t seed, uint32_t group, uint32_t gen, double w, double c1, double c2,
+                 const double *pbest, const double *pfit, double *x, double *v)
+{
+    if (gen == 0) {
+        for (int i = 0; i < n_out * 6; i++) {
+            x[i] = pbest[i];
+            v[i] = 0.0;
+        }
+        return;
+    }
+    int gb = 0;
+    for (int i = 1; i < n_out; i++)
+        if (pfit[i] < pfit[gb]) gb = i;
+    for (int i = 0; i < n_out; i++) {
+        for (int j = 0; j < 6; j++) {
+            uint32_t a = or_word(seed, OR_TAG_OUTER, group, gen, (uint32_t)i, 0, (uint32_t)(j / 4), (uint32_t)(j % 4));
+            uint32_t b = or_word(seed, OR_TAG_OUTER, group, gen, (uint32_t)i, 0, (uint32_t)((6 + j) / 4),
+                                 (uint32_t)((6 + j) % 4));
+            double r1 = (double)(a >> 8) / 16777216.0, r2 = (double)(b >> 8) / 16777216.0;
+            double xi = x[i * 6 + j];
+            double vi = w * v[i * 6 + j] + c1 * r1 * (pbest[i * 6 + j] - xi) + c2 * r2 * (pbest[gb * 6 + j] - xi);
+            double xn = xi + vi;
+            if (xn < OR_LB[j]) xn = OR_LB[j];
+            if (xn > OR_UB[j]) xn = OR_UB[j];
+            v[i * 6 + j] = vi;
+            x[i * 6 + j] = xn;
+        }
+    }
+}
+
+/*
  * A whole MetaDE run (Alg. 3) for one problem, one-shot evaluation: every
  * executor starts from the same seed (stream = group, epoch 0).  `power_up`
  * gives the last evolver generation 5x the inner generations (Sec. III-D).
@@ -499,16 +545,20 @@ void or_outer_select(int n_out, double *pop, double *fit, const double *trial,
  */
 double or_metade_run(int n_out, int np, int dim, int obj, const double *o, const double *R,
                      double lo, double hi, uint64_t seed, uint32_t group, int p_best_pct,
-                     int inner_gens, int outer_gens, int power_up,
+                     int inner_gens, int outer_gens, int power_up, int evolver,
                      double *opop, double *ofit)
 {
     double *trial = (double *)malloc(sizeof(double) * (size_t)n_out * 6);
+    double *vel = (double *)malloc(sizeof(double) * (size_t)n_out * 6);
     double *yf = (double *)malloc(sizeof(double) * (size_t)n_out);
     double *pop = (double *)malloc(sizeof(double) * (size_t)np * dim);
     double *fit = (double *)malloc(sizeof(double) * (size_t)np);
     or_outer_init(n_out, seed, group, opop, ofit);
     for (int g = 0; g < outer_gens; g++) {
-        or_outer_trial(n_out, seed, group, (uint32_t)g, opop, trial);
+        if (evolver == 1)
+            or_pso_move(n_out, seed, group, (uint32_t)g, 0.729, 1.49, 1.49, opop, ofit, trial, vel);
+        else
+            or_outer_trial(n_out, seed, group, (uint32_t)g, opop, trial);
         int gens = (power_up && g == outer_gens - 1) ? 5 * inner_gens : inner_gens;
         for (int k = 0; k < n_out; k++) {
             double th[6];
@@ -520,6 +570,6 @@ double or_metade_run(int n_out, int np, int dim, int obj, const double *o, const
     double b = ofit[0];
     for (int k = 1; k < n_out; k++)
         if (ofit[k] < b) b = ofit[k];
-    free(trial); free(yf); free(pop); free(fit);
+    free(trial); free(vel); free(yf); free(pop); free(fit);
     return b;
 }

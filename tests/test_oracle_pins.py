@@ -541,3 +541,101 @@ def test_metade_tiny_run_improves_meta_fitness():
         y, opop, ofit = oracle.metade_run(8, 16, p.obj, p.shift, p.rot, 5, og, seed=0)
         ys.append(y)
     assert ys[0] >= ys[1] >= ys[2]
+
+
+# ------------------------------------------------------------ PSO evolver
+# The supplement's PSO evolver (w = 0.729, c1 = c2 = 1.49).  Each pin
+# switches terms off through w, c1, c2 so that a dropped, swapped or
+# sign-flipped term, or the wrong global best, fails one of them.
+LB = synth.OUTER_LB.astype(np.float64)
+UB = synth.OUTER_UB.astype(np.float64)
+
+
+def _swarm(n=8, seed=11):
+    rng = np.random.default_rng(seed)
+    pbest = LB + (UB - LB) * rng.random((n, 6))
+    x = LB + (UB - LB) * rng.random((n, 6))
+    v = 0.3 * (UB - LB) * (rng.random((n, 6)) - 0.5)
+    pfit = rng.random(n) * 10
+    return pbest, pfit, x, v
+
+
+def test_pso_generation0_evaluates_the_initial_swarm():
+    pbest, pfit, x, v = _swarm()
+    xn, vn = oracle.pso_move(pbest, pfit, x, v, seed=3, group=1, gen=0)
+    np.testing.assert_array_equal(xn, pbest)
+    assert not vn.any()
+
+
+def test_pso_inertia_only():
+    """c1 = c2 = 0: the velocity only decays by w and the particle coasts."""
+    pbest, pfit, x, v = _swarm()
+    x = np.clip(x, LB + 0.2 * (UB - LB), UB - 0.2 * (UB - LB))
+    v = 0.1 * v
+    xn, vn = oracle.pso_move(pbest, pfit, x, v, seed=3, group=1, gen=4, w=0.5, c1=0.0, c2=0.0)
+    np.testing.assert_allclose(vn, 0.5 * v, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(xn, x + 0.5 * v, rtol=0, atol=1e-15)
+
+
+def test_pso_cognitive_term_pulls_toward_the_own_best():
+    """w = 0, c2 = 0: v = c1 r1 (pbest - x) with r1 in [0, 1), so every
+    coordinate moves toward the particle's own best and never past it."""
+    pbest, pfit, x, v = _swarm()
+    _, vn = oracle.pso_move(pbest, pfit, x, v, seed=5, group=2, gen=7, w=0.0, c1=1.0, c2=0.0)
+    r1 = vn / (pbest - x)
+    assert np.all((r1 >= 0.0) & (r1 < 1.0))
+    assert np.std(r1) > 0.1                                   # one uniform per coordinate
+
+
+def test_pso_social_term_pulls_toward_the_run_best():
+    """w = 0, c1 = 0: v = c2 r2 (gbest - x), gbest = personal best of lowest
+    fitness, ties to the lower index."""
+    pbest, pfit, x, v = _swarm()
+    pfit[5] = pfit[2] = pfit.min() - 1.0                      # tie: index 2 wins
+    _, vn = oracle.pso_move(pbest, pfit, x, v, seed=5, group=2, gen=7, w=0.0, c1=0.0, c2=1.0)
+    r2 = vn / (pbest[2] - x)
+    assert np.all((r2 >= 0.0) & (r2 < 1.0))
+    r1 = oracle.pso_move(pbest, pfit, x, v, seed=5, group=2, gen=7, w=0.0, c1=1.0, c2=0.0)[1] / (pbest - x)
+    assert np.abs(r1 - r2).max() > 0.1                        # r1 and r2 are separate draws
+
+
+def test_pso_full_update_is_the_sum_of_its_terms():
+    pbest, pfit, x, v = _swarm()
+    x = np.clip(x, LB + 0.3 * (UB - LB), UB - 0.3 * (UB - LB))
+    v = 0.05 * v
+    pbest = np.clip(pbest, LB + 0.3 * (UB - LB), UB - 0.3 * (UB - LB))
+    args = dict(seed=9, group=0, gen=3)
+    vw = oracle.pso_move(pbest, pfit, x, v, w=0.729, c1=0.0, c2=0.0, **args)[1]
+    vc = oracle.pso_move(pbest, pfit, x, v, w=0.0, c1=1.49, c2=0.0, **args)[1]
+    vs = oracle.pso_move(pbest, pfit, x, v, w=0.0, c1=0.0, c2=1.49, **args)[1]
+    xn, vn = oracle.pso_move(pbest, pfit, x, v, **args)
+    np.testing.assert_allclose(vn, vw + vc + vs, rtol=0, atol=1e-12)
+    inside = (x + vn > LB) & (x + vn < UB)
+    np.testing.assert_allclose(xn[inside], (x + vn)[inside], rtol=0, atol=1e-12)
+
+
+def test_pso_positions_stay_in_the_box():
+    pbest, pfit, x, v = _swarm()
+    xn, _ = oracle.pso_move(pbest, pfit, x, 50.0 * v, seed=1, group=0, gen=2)
+    assert np.all(xn >= LB) and np.all(xn <= UB)
+
+
+def test_pso_minimises_a_sphere_in_the_evolver_box():
+    """Move + Alg. 3 selection on f(x) = |x - c|^2 inside the gene box."""
+    c = LB + 0.37 * (UB - LB)
+    pbest, pfit = oracle.outer_init(16, seed=4, group=0)
+    x = np.zeros_like(pbest)
+    v = np.zeros_like(pbest)
+    for g in range(120):
+        x, v = oracle.pso_move(pbest, pfit, x, v, seed=4, group=0, gen=g)
+        y = ((x - c) ** 2).sum(axis=1)
+        pbest, pfit, _ = oracle.outer_select(pbest, pfit, x, y)
+    assert pfit.min() < 1e-6
+
+
+def test_pso_metade_run_meta_fitness_does_not_rise():
+    wl = synth.tiny()
+    p = wl.problems[0]
+    y3 = oracle.metade_run(wl.n_out, 16, p.obj, p.shift, p.rot, 10, 3, seed=2, evolver=1)[0]
+    y6 = oracle.metade_run(wl.n_out, 16, p.obj, p.shift, p.rot, 10, 6, seed=2, evolver=1)[0]
+    assert y6 <= y3
