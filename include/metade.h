@@ -101,6 +101,7 @@ typedef struct {
     metade_path path;
     int32_t tie_fp64;          /* selection ties: 0 = FP32 difference form, 1 = FP64 re-evaluation */
     void *stream;              /* cudaStream_t all calls are issued on (NULL = legacy) */
+    int32_t evolver;           /* 0 = DE/rand/1/bin (Alg. 3); 1 = PSO (w = 0.729, c1 = c2 = 1.49) */
 } metade_config;
 
 typedef struct metade_ctx metade_ctx;
@@ -166,7 +167,15 @@ METADE_API metade_status metade_eval(metade_ctx *ctx, const float *pop, metade_p
 
 /* Evolver (Alg. 3).  Its population is float32 [n_groups][n_out][6] with
  * fitness [n_groups][n_out]; executor k = g * n_out + j evaluates vector j
- * of run g.  ESTATE if the context has no evolver (n_out == 0). */
+ * of run g.  ESTATE if the context has no evolver (n_out == 0).
+ * With cfg.evolver = 1 (PSO, the supplement's comparison of evolvers) the
+ * population and fitness are the particles' personal bests, and `trial` is
+ * float32 [n_groups][n_out][12]: position (the vector evaluated) then
+ * velocity.  Phase 0 of generation 0 evaluates the initial swarm (position =
+ * personal best, velocity 0); later generations move every particle by
+ * v <- w v + c1 r1 (pbest - x) + c2 r2 (gbest - x), x <- clip(x + v), gbest the
+ * run's best personal best (ties to the lower index).  Phase 1 is Alg. 3's
+ * selection applied to the positions.  ofit is read by phase 0. */
 /* Alg. 3 lines 1-2: uniform in [lb, ub] = [(0,0,1,1,1,1), (1,1,5,5,5,4)], y = +inf. */
 METADE_API metade_status metade_outer_init(metade_ctx *ctx, float *opop, float *ofit);
 

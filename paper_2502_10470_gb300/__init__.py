@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libmetade.so")
 
 METADE_OK, METADE_EINVAL, METADE_ENOMEM, METADE_ECUDA, METADE_ETIMEOUT, METADE_ESTATE, METADE_EUNSUPPORTED = range(7)
 METADE_FP32, METADE_BF16, METADE_FP8E4M3, METADE_BF16X3, METADE_FP64 = range(5)
+EVOLVER_DE, EVOLVER_PSO = 0, 1
 METADE_PATH_BATCHED, METADE_PATH_PLAIN = 0, 1
 REC_FIELDS = 18
 
@@ -62,6 +63,7 @@ class metade_config(C.Structure):
         ("path", C.c_int),
         ("tie_fp64", C.c_int32),
         ("stream", C.c_void_p),
+        ("evolver", C.c_int32),
     ]
 
 
@@ -131,7 +133,7 @@ def _i32p(a: np.ndarray):
 # ---------------------------------------------------------------- C names
 def metade_create(prob_dim, prob_obj, shift, rot, inst_np, inst_prob, inst_group=None, *, lo=-100.0, hi=100.0,
                   seed=0, one_shot=0, p_best_pct=10, n_out=0, prec=METADE_FP32, path=METADE_PATH_BATCHED,
-                  tie_fp64=0, stream=None) -> int:
+                  tie_fp64=0, stream=None, evolver=EVOLVER_DE) -> int:
     """shift/rot: device float32 tensors (concatenated o_p and row-major R_p)."""
     pd, po, nps, ip = _i32(prob_dim), _i32(prob_obj), _i32(inst_np), _i32(inst_prob)
     ig = _i32(inst_group) if inst_group is not None else None
@@ -154,6 +156,7 @@ def metade_create(prob_dim, prob_obj, shift, rot, inst_np, inst_prob, inst_group
     cfg.path = path
     cfg.tie_fp64 = int(tie_fp64)
     cfg.stream = stream
+    cfg.evolver = int(evolver)
     out = C.c_void_p()
     _check(_lib().metade_create(C.byref(cfg), C.byref(out)), "metade_create")
     return out.value
@@ -269,7 +272,7 @@ class Batch:
 
     def __init__(self, problems: Sequence, inst_np, inst_prob, inst_group=None, *, seed=0, one_shot=0,
                  p_best_pct=10, n_out=0, path=METADE_PATH_BATCHED, prec=METADE_FP32, lo=-100.0, hi=100.0,
-                 tie_fp64=0, device="cuda", stream=None):
+                 tie_fp64=0, device="cuda", stream=None, evolver=EVOLVER_DE):
         import torch
         self.torch = torch
         self.device = torch.device(device)
@@ -288,7 +291,7 @@ class Batch:
         self.stream = stream
         self.ctx = metade_create(dims, objs, self.shift_d, self.rot_d, self.inst_np, self.inst_prob, inst_group,
                                  lo=lo, hi=hi, seed=seed, one_shot=one_shot, p_best_pct=p_best_pct, n_out=n_out,
-                                 prec=prec, path=path, tie_fp64=tie_fp64, stream=stream)
+                                 prec=prec, path=path, tie_fp64=tie_fp64, stream=stream, evolver=evolver)
         self.dims = np.array([dims[p] for p in self.inst_prob], dtype=np.int32)
         self.pop_floats, self.n_indiv, self.n_groups = metade_layout(self.ctx)
         self.pop_off, self.fit_off, self.dpad = metade_offsets(self.ctx, self.n_inst)
@@ -301,7 +304,8 @@ class Batch:
         if n_out:
             self.opop = torch.zeros((self.n_groups * n_out, 6), **f32)
             self.ofit = torch.zeros(self.n_groups * n_out, **f32)
-            self.trial = torch.zeros((self.n_groups * n_out, 6), **f32)
+            # DE: the trial vectors; PSO: position then velocity of every particle
+            self.trial = torch.zeros((self.n_groups * n_out, 12 if evolver == EVOLVER_PSO else 6), **f32)
 
     def close(self):
         if self.ctx:

@@ -58,6 +58,7 @@ struct metade_ctx {
     metade_prec prec = METADE_FP32;
     metade_path path = METADE_PATH_BATCHED;
     int tie_fp64 = 0;
+    int evolver = 0;  // 0 DE/rand/1/bin (Alg. 3), 1 PSO
     cudaStream_t st = nullptr;
     cudaStream_t cap = nullptr;  // private stream for graph capture
     std::vector<InstDesc> hdesc;
@@ -329,14 +330,15 @@ metade_status enqueue_outer_generation(metade_ctx* c, cudaStream_t st, float* op
                                        float* theta, float* pop, float* fit, float* best_f, int* best_i,
                                        int n_inner, int64_t* launches) {
     const Key ko = make_key(c->seed, kTagOuter);
-    CK(launch_outer_trial(c->n_groups, c->n_out, ko, c->gen_dev, 0, opop, trial, theta, st));
+    if (c->evolver == 1) CK(launch_pso_move(c->n_groups, c->n_out, ko, c->gen_dev, 0, opop, ofit, trial, theta, st));
+    else CK(launch_outer_trial(c->n_groups, c->n_out, ko, c->gen_dev, 0, opop, trial, theta, st));
     *launches += 1;
     const uint32_t* ep = c->one_shot ? nullptr : c->gen_dev;
     metade_status s = run_init(c, st, pop, fit, 0, ep, launches);
     if (s != METADE_OK) return s;
     s = run_inner(c, st, pop, fit, theta, 0, ep, 0, n_inner, best_f, best_i, launches);
     if (s != METADE_OK) return s;
-    CK(launch_outer_select(c->n_groups, c->n_out, opop, ofit, trial, best_f, st));
+    CK(launch_outer_select(c->n_groups, c->n_out, opop, ofit, trial, best_f, c->evolver == 1 ? 12 : 6, st));
     *launches += 1;
     return METADE_OK;
 }
@@ -416,6 +418,8 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
         if (cfg->inst_group && cfg->inst_group[k] < 0) return METADE_EINVAL;
     }
 
+    if (cfg->evolver != 0 && cfg->evolver != 1) return METADE_EINVAL;
+
     metade_ctx* c = new metade_ctx();
     c->n_prob = cfg->n_prob;
     c->n_inst = cfg->n_inst;
@@ -429,6 +433,7 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
     c->prec = cfg->prec;
     c->path = cfg->path;
     c->tie_fp64 = cfg->tie_fp64 ? 1 : 0;
+    c->evolver = cfg->evolver;
     c->st = (cudaStream_t)cfg->stream;
 
     // problem tables: input offsets (unpadded) and padded offsets
@@ -695,11 +700,17 @@ metade_status metade_outer_step(metade_ctx* c, float* opop, float* ofit, float* 
     if (c->n_out == 0) return METADE_ESTATE;
     if (phase == 0) {
         if (!opop || !trial || !theta) return METADE_EINVAL;
-        CK(launch_outer_trial(c->n_groups, c->n_out, make_key(c->seed, kTagOuter), nullptr, outer_gen, opop, trial,
-                              theta, c->st));
+        if (c->evolver == 1) {
+            if (!ofit) return METADE_EINVAL;
+            CK(launch_pso_move(c->n_groups, c->n_out, make_key(c->seed, kTagOuter), nullptr, outer_gen, opop, ofit,
+                               trial, theta, c->st));
+        } else {
+            CK(launch_outer_trial(c->n_groups, c->n_out, make_key(c->seed, kTagOuter), nullptr, outer_gen, opop,
+                                  trial, theta, c->st));
+        }
     } else if (phase == 1) {
         if (!opop || !ofit || !trial || !meta_fit) return METADE_EINVAL;
-        CK(launch_outer_select(c->n_groups, c->n_out, opop, ofit, trial, meta_fit, c->st));
+        CK(launch_outer_select(c->n_groups, c->n_out, opop, ofit, trial, meta_fit, c->evolver == 1 ? 12 : 6, c->st));
     } else {
         return METADE_EINVAL;
     }

@@ -112,6 +112,8 @@ cudaError_t launch_outer_init(int n_groups, int n_out, Key key, float* opop, flo
 cudaError_t launch_outer_trial(int n_groups, int n_out, Key key, const uint32_t* gen_dev, uint32_t gen,
                                const float* opop, float* trial, float* theta, cudaStream_t st);
 cudaError_t launch_outer_select(int n_groups, int n_out, float* opop, float* ofit, const float* trial,
-                                const float* meta_fit, cudaStream_t st);
+                                const float* meta_fit, int tstride, cudaStream_t st);
+cudaError_t launch_pso_move(int n_groups, int n_out, Key key, const uint32_t* gen_dev, uint32_t gen,
+                            const float* opop, const float* ofit, float* trial, float* theta, cudaStream_t st);
 
 }  // namespace metade

@@ -762,15 +762,71 @@ __global__ void k_outer_trial(int n_total, int n_out, Key key, const uint32_t* g
     for (int j = 2; j < 6; ++j) th[j] = fminf(fmaxf(floorf(u[j]), 1.0f), top[j - 2]);
 }
 
+// PSO evolver (the supplement's comparison of evolvers; w = 0.729, c1 = c2 =
+// 1.49).  opop / ofit hold the personal bests and their fitness; trial holds
+// [position 6 | velocity 6] per particle.  Generation 0 evaluates the initial
+// swarm (x = pbest, v = 0); later generations move every particle:
+//   v <- w v + c1 r1 (pbest - x) + c2 r2 (gbest - x),  x <- clip(x + v)
+// with gbest the run's personal best of lowest fitness (ties to the lower
+// index) and r1 / r2 the uniforms of draw words 0..5 / 6..11 (slot = word / 4).
+// The position is decoded into theta like a DE trial.
+__global__ void k_pso_move(int n_total, int n_out, Key key, const uint32_t* gen_dev, uint32_t gen_arg,
+                           const float* __restrict__ opop, const float* __restrict__ ofit, float* trial,
+                           float* theta) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_total) return;
+    const uint32_t gen = gen_dev ? *gen_dev : gen_arg;
+    const int g = e / n_out, i = e - g * n_out;
+    float* xv = trial + (long long)e * 12;
+    const float* pb = opop + (long long)e * 6;
+    float u[6];
+    if (gen == 0) {
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            u[j] = pb[j];
+            xv[j] = pb[j];
+            xv[6 + j] = 0.0f;
+        }
+    } else {
+        const float* F = ofit + (long long)g * n_out;
+        int gb = 0;
+        for (int q = 1; q < n_out; ++q)
+            if (F[q] < F[gb]) gb = q;
+        const float* gbest = opop + ((long long)g * n_out + gb) * 6;
+        const Ctr c = make_ctr(key, (uint32_t)g, gen, (uint32_t)i, 0u);
+        const uint4 w0 = c.slot(0), w1 = c.slot(1), w2 = c.slot(2);
+        const uint32_t r1w[6] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y};
+        const uint32_t r2w[6] = {w1.z, w1.w, w2.x, w2.y, w2.z, w2.w};
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            const float x = xv[j];
+            const float v = 0.729f * xv[6 + j] + 1.49f * uniform24(r1w[j]) * (pb[j] - x) +
+                            1.49f * uniform24(r2w[j]) * (gbest[j] - x);
+            const float xn = fminf(fmaxf(x + v, c_lb[j]), c_ub[j]);
+            xv[6 + j] = v;
+            xv[j] = xn;
+            u[j] = xn;
+        }
+    }
+    float* th = theta + (long long)e * 6;
+    th[0] = u[0];
+    th[1] = u[1];
+    const float top[4] = {4.f, 4.f, 4.f, 3.f};
+#pragma unroll
+    for (int j = 2; j < 6; ++j) th[j] = fminf(fmaxf(floorf(u[j]), 1.0f), top[j - 2]);
+}
+
+// Alg. 3 selection; tstride is the trial's floats per vector (6 for DE, 12
+// for PSO, whose first 6 are the position).
 __global__ void k_outer_select(int n_total, float* opop, float* ofit, const float* __restrict__ trial,
-                               const float* __restrict__ meta_fit) {
+                               const float* __restrict__ meta_fit, int tstride) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n_total) return;
     float y = meta_fit[e];
     if (isnan(y)) y = INFINITY;
     if (y <= ofit[e]) {
 #pragma unroll
-        for (int j = 0; j < 6; ++j) opop[(long long)e * 6 + j] = trial[(long long)e * 6 + j];
+        for (int j = 0; j < 6; ++j) opop[(long long)e * 6 + j] = trial[(long long)e * tstride + j];
         ofit[e] = y;
     }
 }
@@ -789,9 +845,16 @@ cudaError_t launch_outer_trial(int n_groups, int n_out, Key key, const uint32_t*
 }
 
 cudaError_t launch_outer_select(int n_groups, int n_out, float* opop, float* ofit, const float* trial,
-                                const float* meta_fit, cudaStream_t st) {
+                                const float* meta_fit, int tstride, cudaStream_t st) {
     const int n = n_groups * n_out;
-    k_outer_select<<<(n + 127) / 128, 128, 0, st>>>(n, opop, ofit, trial, meta_fit);
+    k_outer_select<<<(n + 127) / 128, 128, 0, st>>>(n, opop, ofit, trial, meta_fit, tstride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pso_move(int n_groups, int n_out, Key key, const uint32_t* gen_dev, uint32_t gen,
+                            const float* opop, const float* ofit, float* trial, float* theta, cudaStream_t st) {
+    const int n = n_groups * n_out;
+    k_pso_move<<<(n + 127) / 128, 128, 0, st>>>(n, n_out, key, gen_dev, gen, opop, ofit, trial, theta);
     return cudaGetLastError();
 }
 

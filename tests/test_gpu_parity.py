@@ -281,6 +281,63 @@ def test_outer_init_trial_decode_select():
     b.close()
 
 
+def test_pso_evolver_move_and_select():
+    """PSO evolver: generation 0 evaluates the initial swarm exactly; a later
+    move matches the FP64 oracle's update from the same float32 state (two
+    runs, so gbest is per run), decoding is the DE evolver's, and selection
+    copies positions into the personal bests."""
+    import torch
+    import paper_2502_10470_gb300 as M
+    wl = synth.tiny()
+    wl2 = synth.Workload(name="two-runs", problems=wl.problems * 2, inst_np=np.full(16, 16, dtype=np.int32),
+                         inst_prob=np.repeat([0, 1], 8).astype(np.int32),
+                         inst_group=np.repeat([0, 1], 8).astype(np.int32), n_groups=2, n_out=8, inner_gens=2,
+                         outer_gens=2, seed=13, one_shot=1)
+    b = make_batch(wl2, 0, evolver=M.EVOLVER_PSO)
+    assert tuple(b.trial.shape) == (16, 12)
+    M.metade_outer_init(b.ctx, b.opop, b.ofit)
+    M.metade_outer_step(b.ctx, b.opop, b.ofit, b.trial, b.theta, None, 0, 0)
+    b.sync()
+    tr = b.trial.cpu().numpy()
+    np.testing.assert_array_equal(tr[:, :6], b.opop.cpu().numpy())
+    assert not tr[:, 6:].any()
+    # a mid-run state: personal bests, fitness with a tie for the run best, positions, velocities
+    rng = np.random.default_rng(3)
+    lb, ub = synth.OUTER_LB, synth.OUTER_UB
+    pbest = (lb + (ub - lb) * rng.random((16, 6))).astype(np.float32)
+    x = (lb + (ub - lb) * rng.random((16, 6))).astype(np.float32)
+    v = (0.4 * (ub - lb) * (rng.random((16, 6)) - 0.5)).astype(np.float32)
+    pfit = rng.uniform(1, 10, 16).astype(np.float32)
+    pfit[[2, 5]] = 0.5           # run 0: tie, index 2 is gbest
+    pfit[12] = 0.25              # run 1: gbest 12
+    b.opop.copy_(torch.from_numpy(pbest))
+    b.ofit.copy_(torch.from_numpy(pfit))
+    b.trial.copy_(torch.from_numpy(np.concatenate([x, v], axis=1)))
+    M.metade_outer_step(b.ctx, b.opop, b.ofit, b.trial, b.theta, None, 4, 0)
+    b.sync()
+    tr = b.trial.cpu().numpy()
+    theta = b.theta.cpu().numpy()
+    for g in range(2):
+        sl = slice(8 * g, 8 * g + 8)
+        wx, wv = oracle.pso_move(pbest[sl], pfit[sl], x[sl], v[sl], seed=wl2.seed, group=g, gen=4)
+        assert np.abs(tr[sl, :6] - wx).max() < 1e-5
+        assert np.abs(tr[sl, 6:] - wv).max() < 1e-5
+        for i in range(8):
+            np.testing.assert_array_equal(theta[8 * g + i], oracle.decode(tr[8 * g + i, :6]).astype(np.float32))
+    meta = torch.tensor(np.where(np.arange(16) % 2 == 0, 0.1, 100.0).astype(np.float32), device="cuda")
+    M.metade_outer_step(b.ctx, b.opop, b.ofit, b.trial, b.theta, meta, 4, 1)
+    b.sync()
+    npb, nf = b.opop.cpu().numpy(), b.ofit.cpu().numpy()
+    for e in range(16):
+        if e % 2 == 0:
+            np.testing.assert_array_equal(npb[e], tr[e, :6])
+            assert nf[e] == np.float32(0.1)
+        else:
+            np.testing.assert_array_equal(npb[e], pbest[e])
+            assert nf[e] == pfit[e]
+    b.close()
+
+
 def test_outer_generation_graph_matches_direct():
     import paper_2502_10470_gb300 as M
     wl = synth.tiny()

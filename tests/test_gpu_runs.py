@@ -18,14 +18,14 @@ def _truncate(y):
     return np.where(y < 1e-8, 0.0, y)
 
 
-def _gpu_runs(power_up=False, seeds=SEEDS, path=0):
+def _gpu_runs(power_up=False, seeds=SEEDS, path=0, evolver=0):
     import paper_2502_10470_gb300 as M
     wl = synth.tiny()
     p = wl.problems[0]
     ys = []
     for s in seeds:
         b = M.Batch([(p.dim, p.obj, p.shift, p.rot)], wl.inst_np, wl.inst_prob, wl.inst_group, seed=s,
-                    one_shot=1, n_out=wl.n_out, path=path)
+                    one_shot=1, n_out=wl.n_out, path=path, evolver=evolver)
         _, ofit = b.run_metade(wl.outer_gens, wl.inner_gens, power_up=power_up,
                                use_graph=path == M.METADE_PATH_BATCHED)
         ys.append(float(ofit.min()))
@@ -33,11 +33,11 @@ def _gpu_runs(power_up=False, seeds=SEEDS, path=0):
     return np.array(ys)
 
 
-def _oracle_runs(power_up=False, seeds=SEEDS):
+def _oracle_runs(power_up=False, seeds=SEEDS, evolver=0):
     wl = synth.tiny()
     p = wl.problems[0]
     return np.array([oracle.metade_run(wl.n_out, 16, p.obj, p.shift, p.rot, wl.inner_gens, wl.outer_gens,
-                                       seed=s, power_up=power_up)[0] for s in seeds])
+                                       seed=s, power_up=power_up, evolver=evolver)[0] for s in seeds])
 
 
 def test_final_meta_fitness_distribution_matches_oracle():
@@ -78,4 +78,16 @@ def test_batched_and_plain_runs_agree_in_distribution():
     plain = _truncate(_gpu_runs(path=M.METADE_PATH_PLAIN))
     stat, pval = ranksums(batched, plain)
     print("median batched %.4g plain %.4g, rank-sum p = %.3f" % (np.median(batched), np.median(plain), pval))
+    assert pval > 0.05
+
+
+def test_pso_evolver_runs_match_oracle_in_distribution():
+    """Whole MetaDE runs with the PSO evolver: GPU against the FP64 oracle's
+    PSO, 31 seeds, rank-sum test at 0.05."""
+    import paper_2502_10470_gb300 as M
+    from scipy.stats import ranksums
+    g = _truncate(_gpu_runs(evolver=M.EVOLVER_PSO))
+    o = _truncate(_oracle_runs(evolver=1))
+    stat, pval = ranksums(g, o)
+    print("PSO evolver: median gpu %.4g oracle %.4g, rank-sum p = %.3f" % (np.median(g), np.median(o), pval))
     assert pval > 0.05
