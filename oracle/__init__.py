@@ -78,6 +78,11 @@ def lib():
         L.or_outer_select.argtypes = [C.c_int, P, P, P, P, P]
         L.or_metade_run.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, P, P, C.c_double, C.c_double,
                                     C.c_uint64, C.c_uint32, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, P, P]
+        L.or_mlp_inputs.argtypes = [P]
+        L.or_mlp_hidden.argtypes = [C.c_int]
+        L.or_mlp_hidden.restype = C.c_int
+        L.or_mlp.argtypes = [C.c_int, P, P]
+        L.or_mlp.restype = C.c_double
         L.or_pso_move.argtypes = [C.c_int, C.c_uint64, C.c_uint32, C.c_uint32, C.c_double, C.c_double,
                                   C.c_double, P, P, P, P]
         L.or_metade_run.restype = C.c_double
@@ -124,6 +129,28 @@ def objective(obj: int, z) -> float:
 def eval(obj: int, x, o, R) -> float:  # noqa: A001 - the paper's "evaluate"
     x, o, R = _f64(x), _f64(o), _f64(R)
     return lib().or_eval(obj, x.shape[0], _p(x), _p(o), _p(R))
+
+
+MLP_IN, MLP_OUT, MLP_N = 16, 2, 256
+
+
+def mlp_hidden(dim: int) -> int:
+    """Hidden width h of the MLP objective for D = 19 h + 2 (0 if D has no such h)."""
+    return lib().or_mlp_hidden(dim)
+
+
+def mlp_inputs() -> np.ndarray:
+    """The MLP objective's inputs, [256][16], uniform in [-1, 1]."""
+    X = np.zeros((MLP_N, MLP_IN))
+    lib().or_mlp_inputs(_p(X))
+    return X
+
+
+def mlp(theta, teacher) -> float:
+    """MLP objective: mean squared difference between the outputs of the
+    parameters theta and of the teacher over the inputs."""
+    theta, teacher = _f64(theta), _f64(teacher)
+    return lib().or_mlp(theta.shape[0], _p(theta), _p(teacher))
 
 
 def eval_pop(obj: int, pop, o, R) -> np.ndarray:

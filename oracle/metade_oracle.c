@@ -180,7 +180,7 @@ double or_objective(int obj, int dim, const double *z)
         }
         return -20.0 * exp(-0.2 * sqrt(s / dim)) - exp(c / dim) + 20.0 + OR_E;
     }
-    case 5: { /* Schwefel 1.2 */
+    case 5: { /* Schwefel 1.2 (6, the MLP objective, is evaluated by or_eval on the parameters) */
         double pre = 0.0;
         for (int j = 0; j < dim; j++) {
             pre += z[j];
@@ -193,8 +193,65 @@ double or_objective(int obj, int dim, const double *z)
     }
 }
 
+/* ------------------------------------------- MLP regression objective (6)
+ * A neuroevolution-like large-D objective: theta holds the parameters of a
+ * 16-h-2 perceptron with one tanh hidden layer, laid out as W1 [16][h]
+ * (index k h + j), b1 [h], W2 [h][2] (index j 2 + o), b2 [2], so D = 19 h + 2.
+ * The teacher is the problem's shift vector o, so f(o) = 0 like every other
+ * objective here.  f(theta) is the mean over N = 256 inputs and the two
+ * outputs of (y_theta - y_o)^2.  The inputs are uniform in [-1, 1]: input n,
+ * coordinate k is 2 U - 1 with U from Philox key (0, 0 ^ TAG_DATA), counter
+ * (0, 0, n, k / 4), word k % 4 (the same counter-based generator as every
+ * other draw). */
+#define OR_TAG_DATA 0x4D4C5044u
+#define OR_MLP_IN 16
+#define OR_MLP_OUT 2
+#define OR_MLP_N 256
+
+int or_mlp_hidden(int dim) { return (dim >= 21 && (dim - 2) % 19 == 0) ? (dim - 2) / 19 : 0; }
+
+void or_mlp_inputs(double *X)
+{
+    for (int n = 0; n < OR_MLP_N; n++)
+        for (int k = 0; k < OR_MLP_IN; k++)
+            X[n * OR_MLP_IN + k] = 2.0 * or_uniform(or_word(0, OR_TAG_DATA, 0, 0, (uint32_t)n, 0, 0, (uint32_t)k)) - 1.0;
+}
+
+static void or_mlp_forward(int h, const double *th, const double *x, double *y)
+{
+    const double *W1 = th, *b1 = th + OR_MLP_IN * h, *W2 = b1 + h, *b2 = W2 + h * OR_MLP_OUT;
+    for (int o = 0; o < OR_MLP_OUT; o++) y[o] = b2[o];
+    for (int j = 0; j < h; j++) {
+        double a = b1[j];
+        for (int k = 0; k < OR_MLP_IN; k++) a += x[k] * W1[k * h + j];
+        double t = tanh(a);
+        for (int o = 0; o < OR_MLP_OUT; o++) y[o] += t * W2[j * OR_MLP_OUT + o];
+    }
+}
+
+double or_mlp(int dim, const double *theta, const double *teacher)
+{
+    static double X[OR_MLP_N * OR_MLP_IN];
+    static int have_x = 0;
+    int h = or_mlp_hidden(dim);
+    if (!h) return NAN;
+    if (!have_x) {
+        or_mlp_inputs(X);
+        have_x = 1;
+    }
+    double s = 0.0;
+    for (int n = 0; n < OR_MLP_N; n++) {
+        double yt[OR_MLP_OUT], y[OR_MLP_OUT];
+        or_mlp_forward(h, teacher, X + n * OR_MLP_IN, yt);
+        or_mlp_forward(h, theta, X + n * OR_MLP_IN, y);
+        for (int o = 0; o < OR_MLP_OUT; o++) s += (y[o] - yt[o]) * (y[o] - yt[o]);
+    }
+    return s / (OR_MLP_N * OR_MLP_OUT);
+}
+
 double or_eval(int obj, int dim, const double *x, const double *o, const double *R)
 {
+    if (obj == 6) return or_mlp(dim, x, o);  /* no rotation: f of the parameters themselves */
     double *z = (double *)malloc(sizeof(double) * (size_t)(dim > 0 ? dim : 1));
     or_rotate(dim, x, o, R, z);
     double f = or_objective(obj, dim, z);

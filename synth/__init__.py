@@ -25,8 +25,9 @@ from typing import List, Optional
 
 import numpy as np
 
-OBJ_SPHERE, OBJ_ROSENBROCK, OBJ_RASTRIGIN, OBJ_GRIEWANK, OBJ_ACKLEY, OBJ_SCHWEFEL12 = range(6)
-OBJ_NAMES = ["sphere", "rosenbrock", "rastrigin", "griewank", "ackley", "schwefel12"]
+OBJ_SPHERE, OBJ_ROSENBROCK, OBJ_RASTRIGIN, OBJ_GRIEWANK, OBJ_ACKLEY, OBJ_SCHWEFEL12, OBJ_MLP = range(7)
+OBJ_NAMES = ["sphere", "rosenbrock", "rastrigin", "griewank", "ackley", "schwefel12", "mlp"]
+MLP_TEACHER = 0.75  # teacher parameters ~ U[-0.75, 0.75]: hidden pre-activations of unit variance
 
 BOX_LO, BOX_HI = -100.0, 100.0
 SHIFT_LO, SHIFT_HI = -80.0, 80.0
@@ -54,6 +55,15 @@ class Problem:
     obj: int
     shift: np.ndarray  # float32 [dim]
     rot: np.ndarray    # float32 [dim, dim], row-major, z = rot @ (x - shift)
+
+
+def make_mlp_problem(rng: np.random.Generator, hidden: int) -> Problem:
+    """MLP regression objective (id 6): D = 19 hidden + 2 parameters of a
+    16-hidden-2 tanh perceptron; the shift is the teacher's parameters, the
+    rotation is unused (identity)."""
+    dim = 19 * hidden + 2
+    shift = rng.uniform(-MLP_TEACHER, MLP_TEACHER, size=dim).astype(np.float32)
+    return Problem(dim=dim, obj=OBJ_MLP, shift=shift, rot=np.eye(dim, dtype=np.float32))
 
 
 def make_problem(rng: np.random.Generator, dim: int, obj: int) -> Problem:

@@ -639,3 +639,83 @@ def test_pso_metade_run_meta_fitness_does_not_rise():
     y3 = oracle.metade_run(wl.n_out, 16, p.obj, p.shift, p.rot, 10, 3, seed=2, evolver=1)[0]
     y6 = oracle.metade_run(wl.n_out, 16, p.obj, p.shift, p.rot, 10, 6, seed=2, evolver=1)[0]
     assert y6 <= y3
+
+
+# ------------------------------------------------------------ MLP objective
+# Objective 6: a 16-h-2 tanh perceptron's parameters against a teacher (the
+# shift).  The pins are symmetries and exact identities of the network, so
+# a transposed weight layout, a bias outside the tanh, a wrong output index
+# or a wrong normalisation fails one of them.
+def _mlp_parts(th, h):
+    W1 = th[:16 * h].reshape(16, h)
+    b1 = th[16 * h:17 * h]
+    W2 = th[17 * h:19 * h].reshape(h, 2)
+    b2 = th[19 * h:]
+    return W1, b1, W2, b2
+
+
+def _mlp_join(W1, b1, W2, b2):
+    return np.concatenate([W1.reshape(-1), b1, W2.reshape(-1), b2])
+
+
+def _mlp_case(h=6, seed=5):
+    rng = np.random.default_rng(seed)
+    p = synth.make_mlp_problem(rng, h)
+    th = rng.uniform(-1.0, 1.0, p.dim)
+    return p, th
+
+
+def test_mlp_dimension_rule_and_teacher_optimum():
+    p, th = _mlp_case()
+    assert oracle.mlp_hidden(p.dim) == 6 and oracle.mlp_hidden(p.dim + 1) == 0
+    assert np.isnan(oracle.mlp(th[:-1], p.shift[:-1]))
+    assert oracle.mlp(p.shift, p.shift) == 0.0
+    assert oracle.eval(synth.OBJ_MLP, th, p.shift, p.rot) == oracle.mlp(th, p.shift) > 0.0
+
+
+def test_mlp_inputs_are_uniform_in_the_unit_box():
+    X = oracle.mlp_inputs()
+    assert X.shape == (256, 16) and X.min() >= -1.0 and X.max() < 1.0
+    assert abs(X.mean()) < 0.05 and abs(X.var() - 1.0 / 3.0) < 0.03
+    np.testing.assert_array_equal(X, oracle.mlp_inputs())
+
+
+def test_mlp_hidden_unit_permutation_and_sign_symmetry():
+    p, th = _mlp_case()
+    W1, b1, W2, b2 = _mlp_parts(th, 6)
+    f = oracle.mlp(th, p.shift)
+    perm = np.array([3, 0, 5, 1, 4, 2])
+    assert np.isclose(oracle.mlp(_mlp_join(W1[:, perm], b1[perm], W2[perm], b2), p.shift), f, rtol=1e-13)
+    s = np.array([1, -1, 1, -1, -1, 1.0])          # tanh is odd: flip units 1, 3, 4
+    assert np.isclose(oracle.mlp(_mlp_join(W1 * s, b1 * s, W2 * s[:, None], b2), p.shift), f, rtol=1e-13)
+
+
+def test_mlp_hidden_bias_enters_through_the_tanh_and_its_output_row():
+    """A unit with zero input weights outputs tanh(b1_j) W2[j, :] for every
+    input: moving that constant into b2 leaves f unchanged, and a unit whose
+    output row is zero does not matter at all."""
+    p, th = _mlp_case()
+    W1, b1, W2, b2 = _mlp_parts(th, 6)
+    W1[:, 2] = 0.0
+    f = oracle.mlp(_mlp_join(W1, b1, W2, b2), p.shift)
+    moved_b1 = b1.copy()
+    moved_b1[2] = 0.0
+    assert np.isclose(oracle.mlp(_mlp_join(W1, moved_b1, W2, b2 + np.tanh(b1[2]) * W2[2]), p.shift), f, rtol=1e-12)
+    W2[4] = 0.0
+    f0 = oracle.mlp(_mlp_join(W1, b1, W2, b2), p.shift)
+    W1b, b1b = W1.copy(), b1.copy()
+    W1b[:, 4] += 3.0
+    b1b[4] -= 2.0
+    assert oracle.mlp(_mlp_join(W1b, b1b, W2, b2), p.shift) == f0
+
+
+def test_mlp_is_a_mean_of_squares_in_the_output_bias():
+    """f is quadratic in each output bias with second difference 2 delta^2 /
+    (number of outputs): the mean is over inputs and both outputs."""
+    p, th = _mlp_case()
+    d = 0.37
+    for o in range(2):
+        e = np.zeros(p.dim)
+        e[-2 + o] = d
+        second = oracle.mlp(th + e, p.shift) + oracle.mlp(th - e, p.shift) - 2.0 * oracle.mlp(th, p.shift)
+        assert abs(second - d * d) < 1e-12
