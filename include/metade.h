@@ -24,6 +24,17 @@
  *    rotation R_p; its objective is f(x) = obj(z), z = R_p (x - o_p).
  *    Objective ids: 0 sphere, 1 Rosenbrock on z + 1, 2 Rastrigin,
  *    3 Griewank, 4 Ackley, 5 Schwefel 1.2 (all with minimum 0 at x = o_p).
+ *    Id 6 is a neuroevolution-like regression problem (the paper's policy
+ *    search, made synthetic): x holds the parameters of a 16-h-2 perceptron
+ *    with one tanh hidden layer, laid out W1 [16][h] (k h + j), b1 [h],
+ *    W2 [h][2] (2 j + o), b2 [2], so D_p = 19 h + 2 (other D_p: EINVAL).  f is
+ *    the mean over 256 fixed inputs (uniform in [-1, 1], Philox key tag
+ *    0x4D4C5044, counter (0, 0, input, coordinate / 4)) and both outputs of
+ *    the squared difference to the outputs of the teacher network o_p, so the
+ *    minimum is again 0 at x = o_p.  R_p is not used (pass any D_p^2 array).
+ *    Id 6 runs on the batched path only (plain path: EUNSUPPORTED), in FP32
+ *    whatever cfg.prec is, and its selection compares the FP32 values: it has
+ *    no difference form for near ties.
  *  - Population layout: instance-major, row-major, each row padded to
  *    Dpad = round_up(D, 4) floats (16-byte rows); the pad columns are zero.
  *    Instance k's rows start at float offset pop_off[k]; its fitness values
@@ -84,7 +95,7 @@ typedef struct {
     /* problem table (host arrays, device data) */
     int32_t n_prob;
     const int32_t *prob_dim;  /* host [n_prob], D_p >= 1 */
-    const int32_t *prob_obj;  /* host [n_prob], objective id 0..5 */
+    const int32_t *prob_obj;  /* host [n_prob], objective id 0..6 (6: MLP regression, see below) */
     const float *shift;       /* device [sum_p D_p]: o_p concatenated */
     const float *rot;         /* device [sum_p D_p^2]: R_p row-major, concatenated */
     /* executors */
@@ -257,8 +268,8 @@ METADE_API metade_status metade_plan_info(const metade_ctx *ctx, char *buf, size
  * of launches since the last read -- kinds: 0 fused small-D kernel, 1 fused
  * general kernel, 2 tensor-core rotation GEMM, 3 whole tensor-core generation,
  * 4 fused tile kernel with R^T streamed (128 < D_pad <= 256), 5 fused tile
- * kernel with R^T resident (D_pad <= 128) -- then clears them.  ms and count
- * are host arrays of 6 (may be NULL). */
+ * kernel with R^T resident (D_pad <= 128), 6 fused MLP-objective kernel --
+ * then clears them.  ms and count are host arrays of 7 (may be NULL). */
 METADE_API metade_status metade_profile(metade_ctx *ctx, int32_t enable);
 METADE_API metade_status metade_profile_read(metade_ctx *ctx, double *ms, int64_t *count);
 

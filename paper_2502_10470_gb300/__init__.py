@@ -244,7 +244,8 @@ def metade_autotune(ctx: int, pop, fit, theta, n_gens: int = 3) -> None:
     _check(_lib().metade_autotune(ctx, _ptr(pop), _ptr(fit), _ptr(theta), n_gens), "metade_autotune")
 
 
-PROFILE_KINDS = ["fused_small", "fused_general", "tc_gemm", "tc_generation", "fused_tile_stream", "fused_tile"]
+PROFILE_KINDS = ["fused_small", "fused_general", "tc_gemm", "tc_generation", "fused_tile_stream", "fused_tile",
+                 "fused_mlp"]
 
 
 def metade_profile(ctx: int, enable: bool) -> None:

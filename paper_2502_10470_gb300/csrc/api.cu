@@ -33,7 +33,8 @@ enum ProfKind {
     kProfTcGeneration = 3,
     kProfFusedTileStream = 4,
     kProfFusedTile = 5,
-    kProfKinds = 6
+    kProfFusedMlp = 6,
+    kProfKinds = 7
 };
 
 struct ProfRec {
@@ -97,6 +98,7 @@ struct metade_ctx {
     uint8_t *aq = nullptr, *aq_lo = nullptr, *bq = nullptr, *bq_lo = nullptr;  // BF16 pairs or e4m3 bytes
     float *ascale = nullptr, *bscale = nullptr;                                // FP8 dequantisation factors
     unsigned* amax = nullptr;                                                  // FP8: max|R| scratch
+    float *mlp_x = nullptr, *mlp_y = nullptr;  // MLP objective: inputs [256][16], targets per problem [256][2]
 };
 
 namespace {
@@ -146,10 +148,14 @@ double work_cost(const InstDesc& d) { return (double)d.np * ((double)d.dim * d.d
 // first, so the block scheduler hands the longest executors out first).
 metade_status build_plan(metade_ctx* c) {
     std::vector<std::vector<int>> small(33);
-    std::vector<int> general, tile, tile_stream;
+    std::vector<int> general, tile, tile_stream, mlp;
     for (int k = 0; k < c->n_inst; ++k) {
         if (c->tc && c->is_tc[k]) continue;
         const InstDesc& d = c->hdesc[k];
+        if (d.obj == kMlp) {  // the MLP objective has its own kernel
+            mlp.push_back(k);
+            continue;
+        }
         const int dm = small_dmax_for(d.dim);
         // The tile kernels decide near ties by the FP32 difference form only;
         // FP64 tie re-evaluation runs in the small and general kernels.
@@ -209,6 +215,29 @@ metade_status build_plan(metade_ctx* c) {
         b.work_off = (int)order.size();
         b.n_work = (int)tv.size();
         order.insert(order.end(), tv.begin(), tv.end());
+        c->buckets.push_back(b);
+    }
+    if (!mlp.empty()) {
+        sort_desc(mlp);
+        int mnp = 0, mdp = 0;
+        for (int k : mlp) {
+            mnp = std::max(mnp, c->hdesc[k].np);
+            mdp = std::max(mdp, c->hdesc[k].dpad);
+        }
+        Bucket b;
+        b.plan.kind = 4;
+        b.plan.dmax = 0;
+        b.plan.threads = kMlpN;
+        b.plan.grid = (int)mlp.size();
+        b.plan.max_np = mnp;
+        b.plan.max_dpad = mdp;
+        b.plan.rot_smem = 0;
+        b.plan.pop_smem = 0;
+        b.plan.smem = fused_smem_mlp(mnp, mdp);
+        if (b.plan.smem > kSmemLimit) return METADE_EUNSUPPORTED;
+        b.work_off = (int)order.size();
+        b.n_work = (int)mlp.size();
+        order.insert(order.end(), mlp.begin(), mlp.end());
         c->buckets.push_back(b);
     }
     if (!general.empty()) {
@@ -280,10 +309,14 @@ metade_status run_inner(metade_ctx* c, cudaStream_t st, float* pop, float* fit, 
         const bool pr = prof_pair(c, st,
                                   b.plan.kind == 0   ? kProfFusedSmall
                                   : b.plan.kind == 3 ? (b.plan.rot_smem ? kProfFusedTile : kProfFusedTileStream)
+                                  : b.plan.kind == 4 ? kProfFusedMlp
                                                      : kProfFusedGeneral,
                                   &e0, &e1);
         if (pr) cudaEventRecord(e0, st);
-        CK(launch_fused(a, c->work + b.work_off, b.n_work, b.plan, c->uscr, st));
+        if (b.plan.kind == 4)
+            CK(launch_fused_mlp(a, c->work + b.work_off, b.n_work, b.plan, c->uscr, c->mlp_x, c->mlp_y, st));
+        else
+            CK(launch_fused(a, c->work + b.work_off, b.n_work, b.plan, c->uscr, st));
         if (pr) cudaEventRecord(e1, st);
         *launches += 1;
     }
@@ -314,7 +347,7 @@ metade_status run_init(metade_ctx* c, cudaStream_t st, float* pop, float* fit, u
     // executors on the tensor cores are evaluated by the rotation GEMM in the
     // context's precision, like every later evaluation of theirs
     CK(launch_eval(c->desc, c->row_inst, c->n_indiv, pop, c->rotT, c->shift, false, fit, true, c->max_dpad, st,
-                   c->tc));
+                   c->tc, c->mlp_x, c->mlp_y));
     *launches += 2;
     if (c->tc) {
         CK(launch_tc_eval(c->desc, c->tcp, pop, c->shift, fit, c->status, st));
@@ -392,6 +425,8 @@ void metade_destroy(metade_ctx* c) {
     cudaFree(c->ascale);
     cudaFree(c->bscale);
     cudaFree(c->amax);
+    cudaFree(c->mlp_x);
+    cudaFree(c->mlp_y);
     if (c->cap) cudaStreamDestroy(c->cap);
     delete c;
 }
@@ -409,7 +444,11 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
         cfg->prec != METADE_FP8E4M3)
         return METADE_EUNSUPPORTED;
     for (int p = 0; p < cfg->n_prob; ++p) {
-        if (cfg->prob_dim[p] < 1 || cfg->prob_obj[p] < 0 || cfg->prob_obj[p] > 5) return METADE_EINVAL;
+        if (cfg->prob_dim[p] < 1 || cfg->prob_obj[p] < 0 || cfg->prob_obj[p] > kMlp) return METADE_EINVAL;
+        if (cfg->prob_obj[p] == kMlp) {
+            if (!mlp_hidden(cfg->prob_dim[p])) return METADE_EINVAL;      // D = 19 h + 2
+            if (cfg->path == METADE_PATH_PLAIN) return METADE_EUNSUPPORTED;  // batched kernel only
+        }
         if (cfg->prob_dim[p] > kMaxDim) return METADE_EUNSUPPORTED;
     }
     for (int k = 0; k < cfg->n_inst; ++k) {
@@ -439,6 +478,8 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
     // problem tables: input offsets (unpadded) and padded offsets
     std::vector<long long> rot_in_off(c->n_prob), rot_off(c->n_prob);
     std::vector<int> shift_in_off(c->n_prob), shift_off(c->n_prob);
+    std::vector<int> mlp_yoff(c->n_prob, 0);  // MLP problems: offset of their targets
+    int n_mlp = 0;
     long long rin = 0, rpad = 0;
     int sin_ = 0, spad = 0;
     for (int p = 0; p < c->n_prob; ++p) {
@@ -452,6 +493,7 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
         sin_ += D;
         spad += Dp;
         c->max_dim = std::max(c->max_dim, D);
+        if (cfg->prob_obj[p] == kMlp) mlp_yoff[p] = kMlpN * kMlpOut * n_mlp++;
     }
 
     c->hdesc.resize(c->n_inst);
@@ -477,6 +519,7 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
         d.shift_off = shift_off[p];
         d.kp = std::max(1, (np * c->p_best_pct + 99) / 100);
         d.prob = p;
+        d.aux = mlp_yoff[p];
         c->hdesc[k] = d;
         c->pop_off[k] = po;
         c->fit_off[k] = fo;
@@ -503,7 +546,7 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
     if (c->prec == METADE_BF16 || c->prec == METADE_BF16X3 || fp8) {
         for (int k = 0; k < c->n_inst; ++k) {
             InstDesc& d = c->hdesc[k];
-            if (d.dim < kTcMinDim) continue;
+            if (d.dim < kTcMinDim || d.obj == kMlp) continue;
             c->is_tc[k] = 1;
             d.tc_row = (int)tc_row_exec.size();
             d.on_tc = 1;
@@ -564,6 +607,17 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
         cudaFree(d_dim);
         if (!ok) return fail(METADE_ECUDA);
         c->launches += 1;
+        if (n_mlp > 0) {  // MLP objective: the fixed inputs and every problem's teacher outputs
+            if (dalloc(&c->mlp_x, (size_t)kMlpN * kMlpIn) || dalloc(&c->mlp_y, (size_t)kMlpN * kMlpOut * n_mlp))
+                return fail(METADE_ENOMEM);
+            bool okm = !launch_mlp_inputs(c->mlp_x, c->st);
+            for (int p = 0; p < c->n_prob && okm; ++p)
+                if (cfg->prob_obj[p] == kMlp)
+                    okm = !launch_mlp_targets(c->mlp_x, c->shift + shift_off[p], mlp_hidden(cfg->prob_dim[p]),
+                                              c->mlp_y + mlp_yoff[p], c->st);
+            if (!okm || cudaStreamSynchronize(c->st)) return fail(METADE_ECUDA);
+            c->launches += 1 + n_mlp;
+        }
         metade_status s = build_plan(c);
         if (s != METADE_OK) return fail(s);
     }
@@ -680,7 +734,7 @@ metade_status metade_eval(metade_ctx* c, const float* pop, metade_prec prec, voi
     if (prec != METADE_FP32 && prec != METADE_FP64) return METADE_EUNSUPPORTED;
     if (c->n_inst == 0) return METADE_OK;
     CK(launch_eval(c->desc, c->row_inst, c->n_indiv, pop, c->rotT, c->shift, prec == METADE_FP64, f_out, false,
-                   c->max_dpad, c->st, false));
+                   c->max_dpad, c->st, false, c->mlp_x, c->mlp_y));
     c->launches += 1;
     return METADE_OK;
 }
@@ -802,6 +856,7 @@ metade_status metade_autotune(metade_ctx* c, const float* pop, const float* fit,
     if (cudaEventCreate(&e0) || cudaEventCreate(&e1)) st = METADE_ECUDA;
     for (Bucket& b : c->buckets) {
         if (st != METADE_OK) break;
+        if (b.plan.kind == 4) continue;  // MLP kernel: one thread per input, nothing to tune
         std::vector<int> cands = b.plan.kind == 0 ? std::vector<int>{32, 64, 128, 256}
                                                   : std::vector<int>{128, 256, 512};
         if (b.plan.kind == 3) cands = b.plan.rot_smem ? std::vector<int>{128, 256} : std::vector<int>{256};
@@ -863,6 +918,7 @@ metade_status metade_plan_info(const metade_ctx* c, char* buf, size_t len) {
                  b ? ", " : "",
                  k.plan.kind == 0   ? "fused_small"
                  : k.plan.kind == 3 ? (k.plan.rot_smem ? "fused_tile" : "fused_tile_stream")
+                 : k.plan.kind == 4 ? "fused_mlp"
                                     : "fused_general",
                  k.plan.dmax,
                  k.plan.threads,
@@ -897,8 +953,8 @@ metade_status metade_profile(metade_ctx* c, int32_t enable) {
 metade_status metade_profile_read(metade_ctx* c, double* ms, int64_t* count) {
     if (!c) return METADE_EINVAL;
     CK(cudaStreamSynchronize(c->st));
-    double tot[kProfKinds] = {0, 0, 0, 0, 0, 0};
-    int64_t n[kProfKinds] = {0, 0, 0, 0, 0, 0};
+    double tot[kProfKinds] = {};
+    int64_t n[kProfKinds] = {};
     for (auto& r : c->prof) {
         float t = 0.f;
         if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {

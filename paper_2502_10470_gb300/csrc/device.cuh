@@ -28,7 +28,7 @@ struct InstDesc {
     int prob;            // problem index
     int tc_row;          // tensor-core path: first row of the executor in the GEMM operands
     int on_tc;           // 1: the executor is evaluated on the tensor-core path
-    int pad2;
+    int aux;             // MLP objective: offset of the problem's targets [256][2]
 };
 static_assert(sizeof(InstDesc) == 64, "descriptor is one 64-byte record");
 
@@ -230,7 +230,38 @@ __device__ __forceinline__ int exp_length(const Ctr& c, int dim, uint32_t cri) {
 //   Griewank   1 - prod cos a_j = -expm1(sum log1p(-2 sin^2(a_j/2))) when every
 //              cos a_j > 0, else evaluated directly (no cancellation then)
 //   Rosenbrock y = z + 1: y_{j+1} - y_j^2 = z_{j+1} - z_j (z_j + 2), y_j - 1 = z_j
-enum Obj { kSphere = 0, kRosenbrock = 1, kRastrigin = 2, kGriewank = 3, kAckley = 4, kSchwefel12 = 5 };
+enum Obj { kSphere = 0, kRosenbrock = 1, kRastrigin = 2, kGriewank = 3, kAckley = 4, kSchwefel12 = 5, kMlp = 6 };
+
+// MLP regression objective (6): the parameters of a 16-h-2 perceptron with
+// one tanh hidden layer, W1 [16][h] (k h + j), b1 [h], W2 [h][2] (2 j + o),
+// b2 [2], so D = 19 h + 2, against a teacher network (the problem's shift).
+// f = mean over 256 fixed inputs and both outputs of the squared output
+// difference.  Input n, coordinate k: 2 U - 1, U from Philox key
+// (0, TAG_DATA), counter (0, 0, n, k / 4), word k % 4.
+constexpr int kMlpIn = 16, kMlpOut = 2, kMlpN = 256;
+constexpr uint32_t kTagData = 0x4D4C5044u;
+__host__ __device__ inline int mlp_hidden(int dim) { return (dim >= 21 && (dim - 2) % 19 == 0) ? (dim - 2) / 19 : 0; }
+
+// Network output for one input x: hidden units in order j = 0..h-1, each
+// pre-activation summed over k ascending (fma), output accumulated over j.
+// T = float (FP32 evaluation) or double (FP64 evaluation).
+template <typename T>
+__device__ __forceinline__ void mlp_forward(int h, const float* th, const T (&x)[kMlpIn], T (&y)[kMlpOut]) {
+    const float* W1 = th;
+    const float* b1 = th + kMlpIn * h;
+    const float* W2 = b1 + h;
+    const float* b2 = W2 + kMlpOut * h;
+    y[0] = T(b2[0]);
+    y[1] = T(b2[1]);
+    for (int j = 0; j < h; ++j) {
+        T a = T(b1[j]);
+#pragma unroll
+        for (int k = 0; k < kMlpIn; ++k) a = fma(x[k], T(W1[k * h + j]), a);
+        const T t = tanh(a);
+        y[0] = fma(t, T(W2[2 * j]), y[0]);
+        y[1] = fma(t, T(W2[2 * j + 1]), y[1]);
+    }
+}
 
 // Streaming accumulator: objectives consume z_0, z_1, ... in order.
 template <typename T>

@@ -42,7 +42,8 @@ cudaError_t launch_init(const InstDesc* desc, int n_inst, int max_np, int max_dp
 // skip_tc leaves the rows of executors on the tensor-core path untouched.
 cudaError_t launch_eval(const InstDesc* desc, const int* row_inst, long long n_rows, const float* pop,
                         const float* rotT, const float* shift, bool f64, void* f_out, bool nan_inf,
-                        int max_dpad, cudaStream_t st, bool skip_tc);
+                        int max_dpad, cudaStream_t st, bool skip_tc, const float* mlp_x = nullptr,
+                        const float* mlp_y = nullptr);
 
 cudaError_t launch_record(const StepArgs& a, int n_inst, int max_np, int* rec, cudaStream_t st);
 
@@ -56,7 +57,7 @@ cudaError_t launch_plain_generation(const StepArgs& a, int k, const InstDesc& d,
 // Batched path: executors listed in `work` (schedule order), all n_gens generations.
 struct FusedPlan {
     int kind;      // 0 small (thread per individual), 1 general (warp per individual),
-                   // 3 tile (register-blocked rotation GEMM per tile of individuals)
+                   // 3 tile (register-blocked rotation GEMM per tile of individuals), 4 MLP objective
     int dmax;      // small: compile-time row bound
     int threads;   // block size
     int grid;      // CTAs (<= n_work; CTAs loop over work items)
@@ -71,6 +72,12 @@ size_t fused_smem_small(int dmax, int max_np);
 size_t fused_smem_general(int max_np, int max_dpad, int threads, bool rot_in_smem);
 int small_dmax_for(int dim);  // 0 when the small kernel does not apply
 size_t fused_smem_tile(int max_np, int max_dpad, int threads, bool rot_smem);
+// MLP objective (k_mlp.cu): kind 4, 256 threads (thread n evaluates input n)
+size_t fused_smem_mlp(int max_np, int max_dpad);
+cudaError_t launch_fused_mlp(const StepArgs& a, const int* work, int n_work, const FusedPlan& p, float* uscr,
+                             const float* mlp_x, const float* mlp_y, cudaStream_t st);
+cudaError_t launch_mlp_inputs(float* X, cudaStream_t st);
+cudaError_t launch_mlp_targets(const float* X, const float* teacher, int h, float* Y, cudaStream_t st);
 cudaError_t launch_fused_tile(const StepArgs& a, const int* work, int n_work, const FusedPlan& p, float* u_scratch,
                               cudaStream_t st);
 

@@ -83,7 +83,8 @@ template <bool F64>
 __global__ void __launch_bounds__(256) k_eval(const InstDesc* __restrict__ desc, const int* __restrict__ row_inst,
                                               long long n_rows, const float* __restrict__ pop,
                                               const float* __restrict__ rotT, const float* __restrict__ shift,
-                                              void* f_out, int nan_inf, int scratch, int skip_tc) {
+                                              void* f_out, int nan_inf, int scratch, int skip_tc,
+                                              const float* __restrict__ mlp_x, const float* __restrict__ mlp_y) {
     extern __shared__ __align__(16) float sm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float* wb = sm + (size_t)warp * scratch;
@@ -96,6 +97,35 @@ __global__ void __launch_bounds__(256) k_eval(const InstDesc* __restrict__ desc,
         const float* x = pop + d.pop_off + i * d.dpad;
         const float* o = shift + d.shift_off;
         const float* RT = rotT + d.rot_off;
+        if (d.obj == kMlp) {  // warp-uniform; lanes take inputs n = lane, lane + 32, ...
+            const int h = mlp_hidden(d.dim);
+            if (F64) {  // teacher outputs recomputed in FP64 from the shift
+                double s = 0.0;
+                for (int n = lane; n < kMlpN; n += 32) {
+                    double xv[kMlpIn], yt[kMlpOut], y[kMlpOut];
+#pragma unroll
+                    for (int q = 0; q < kMlpIn; ++q) xv[q] = (double)mlp_x[n * kMlpIn + q];
+                    mlp_forward<double>(h, o, xv, yt);
+                    mlp_forward<double>(h, x, xv, y);
+                    s += (y[0] - yt[0]) * (y[0] - yt[0]) + (y[1] - yt[1]) * (y[1] - yt[1]);
+                }
+                const double f = warp_sum(s) / (kMlpN * kMlpOut);
+                if (lane == 0) reinterpret_cast<double*>(f_out)[row] = nan_inf ? nan_to_inf(f) : f;
+            } else {
+                float s = 0.0f;
+                for (int n = lane; n < kMlpN; n += 32) {
+                    float xv[kMlpIn], y[kMlpOut];
+#pragma unroll
+                    for (int q = 0; q < kMlpIn; ++q) xv[q] = mlp_x[n * kMlpIn + q];
+                    mlp_forward<float>(h, x, xv, y);
+                    const float e0 = y[0] - mlp_y[d.aux + 2 * n], e1 = y[1] - mlp_y[d.aux + 2 * n + 1];
+                    s += fmaf(e0, e0, e1 * e1);
+                }
+                const float f = warp_sum(s) * (1.0f / (kMlpN * kMlpOut));
+                if (lane == 0) reinterpret_cast<float*>(f_out)[row] = nan_inf ? nan_to_inf(f) : f;
+            }
+            continue;
+        }
         if (F64) {
             double* db = reinterpret_cast<double*>(wb);
             const double f = warp_eval64(d.obj, d.dim, x, o, RT, d.dpad, db, db + d.dpad);
@@ -127,7 +157,7 @@ static int num_sms() {
 
 cudaError_t launch_eval(const InstDesc* desc, const int* row_inst, long long n_rows, const float* pop,
                         const float* rotT, const float* shift, bool f64, void* f_out, bool nan_inf, int max_dpad,
-                        cudaStream_t st, bool skip_tc) {
+                        cudaStream_t st, bool skip_tc, const float* mlp_x, const float* mlp_y) {
     if (n_rows <= 0) return cudaSuccess;
     const int scratch = 4 * max_dpad;  // floats per warp: two buffers of max_dpad doubles
     const size_t smem = (size_t)8 * scratch * sizeof(float);
@@ -137,11 +167,11 @@ cudaError_t launch_eval(const InstDesc* desc, const int* row_inst, long long n_r
     if (f64) {
         cudaFuncSetAttribute(k_eval<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_eval<true><<<(unsigned)blocks, 256, smem, st>>>(desc, row_inst, n_rows, pop, rotT, shift, f_out,
-                                                          nan_inf, scratch, skip_tc ? 1 : 0);
+                                                          nan_inf, scratch, skip_tc ? 1 : 0, mlp_x, mlp_y);
     } else {
         cudaFuncSetAttribute(k_eval<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_eval<false><<<(unsigned)blocks, 256, smem, st>>>(desc, row_inst, n_rows, pop, rotT, shift, f_out,
-                                                           nan_inf, scratch, skip_tc ? 1 : 0);
+                                                           nan_inf, scratch, skip_tc ? 1 : 0, mlp_x, mlp_y);
     }
     return cudaGetLastError();
 }
