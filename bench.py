@@ -49,7 +49,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison arm")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--inner-gens", type=int, default=INNER_GENS)
-    ap.add_argument("--workload", default="moderate", choices=["moderate", "precision", "batching", "full"],
+    ap.add_argument("--workload", default="moderate", choices=["moderate", "precision", "batching", "full", "mlp"],
                     help="moderate: the headline workload; precision: the D=1000 precision study; batching: "
                          "512 ragged executors; full: 8 MetaDE runs x 128 executors")
     ap.add_argument("--seeds", type=int, default=5, help="whole MetaDE runs of the full workload")
@@ -88,13 +88,22 @@ def oracle_tasks(wl, per_run: int, gens: int):
     return tasks
 
 
-def time_oracle(tasks, cores: int):
+def _oracle_box_job(args):
+    """One executor run of the oracle in a given box (module-level for the spawn pool)."""
+    import oracle
+    theta, np_, obj, shift, rot, gens, seed, stream, lo, hi = args
+    oracle.build()
+    oracle.pde_run(theta, np_, obj, shift, rot, gens, seed=seed, stream=stream, epoch=0, lo=lo, hi=hi)
+    return np_ * gens
+
+
+def time_oracle(tasks, cores: int, job=_oracle_job):
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
     with ctx.Pool(cores) as pool:
-        pool.map(_oracle_job, tasks[:cores])  # workers up and the library built before timing
+        pool.map(job, [t[:5] + (1,) + t[6:] for t in tasks[:cores]])  # workers up, library built, before timing
         t0 = time.perf_counter()
-        units = sum(pool.map(_oracle_job, tasks, chunksize=1))
+        units = sum(pool.map(job, tasks, chunksize=1))
         dt = time.perf_counter() - t0
     return units, dt
 
@@ -656,6 +665,86 @@ def run_full(args):
     print(json.dumps(line), flush=True)
 
 
+def run_mlp(args):
+    """The MLP workload (64 executors x NP 100, D = 1522): batched
+    generations of the MLP-objective path, timed with CUDA events after an
+    L2 flush.  Roofline: FP32 FMA throughput, 256 inputs x (16 h + 2 h)
+    multiply-adds = 256 * 36 h flops per evaluation (tanh not counted)
+    against 152 SMs x 128 lanes x 2 flops x the sampled maximum SM clock.
+    Beside it, the FP64 oracle on the host cores on a bounded sample (one
+    generation of as many executors as there are cores)."""
+    import numpy as np
+    import torch
+    import synth
+    wl = synth.mlp()
+    gens = wl.inner_gens
+    cores = os.cpu_count() or 1
+    tiny_rot = np.zeros((1, 1), dtype=np.float32)  # the objective does not read R
+    tasks = [(wl.theta[k], int(wl.inst_np[k]), synth.OBJ_MLP, wl.problems[int(wl.inst_prob[k])].shift, tiny_rot, 1,
+              wl.seed, k, wl.lo, wl.hi) for k in range(min(cores, wl.n_inst))]
+    cpu_units, cpu_dt = time_oracle(tasks, cores, _oracle_box_job)  # before the first GPU call
+    import paper_2502_10470_gb300 as M
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    probs = [(p.dim, p.obj, p.shift, p.rot) for p in wl.problems]
+    b = M.Batch(probs, wl.inst_np, wl.inst_prob, wl.inst_group, seed=wl.seed, one_shot=0, lo=wl.lo, hi=wl.hi,
+                device=dev, stream=stream.cuda_stream)
+    b.set_theta(wl.theta)
+    M.metade_init(b.ctx, b.pop, b.fit, 0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    g0 = 0
+    for _ in range(args.warmup):
+        M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, g0, gens, b.best_f, b.best_i)
+        g0 += gens
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    M.metade_profile(b.ctx, True)
+    M.metade_profile_read(b.ctx)
+    evs = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, g0, gens, b.best_f, b.best_i)
+        e1.record(stream)
+        evs.append((e0, e1))
+        g0 += gens
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    prof = M.metade_profile_read(b.ctx)
+    if M.metade_sync(b.ctx) != M.METADE_OK:
+        raise RuntimeError("device status")
+    ms = float(np.mean([a.elapsed_time(c) for a, c in evs]))
+    units = float(wl.inst_np.sum()) * gens
+    h = (wl.problems[0].dim - 2) // 19
+    flops = units * 256 * 36 * h
+    kms = prof["mlp_generations"][0] / max(1, prof["mlp_generations"][1])
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    sm_max = float((clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0))
+    peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    best = b.best_f.cpu().numpy()
+    line = {"metric": "MLP workload: individual-gens/s (MLP-objective path)", "workload": wl.name,
+            "value": units / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
+            "generations_per_step": gens, "dtype": "f32", "data": "synthetic",
+            "roofline": {"bound": "fp32", "kernel": "MLP generations (k_mlp_eval dominant)",
+                         "achieved": flops / (kms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                         "frac": flops / (kms / 1e3) / 1e12 / peak, "traffic": None,
+                         "peak_source": "152 SMs x 128 lanes x 2 flops x %.0f MHz (max SM clock)" % sm_max},
+            "cpu_baseline": {"value": cpu_units / cpu_dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d executors x NP 100 x 1 generation of the MLP workload, FP64 C oracle, "
+                                       "%d spawn processes, %.1f s wall" % (len(tasks), cores, cpu_dt)},
+            "best_f_median": float(np.median(best)), "clocks": clocks,
+            "l2": "flushed before every timed step"}
+    print(json.dumps(line), flush=True)
+    b.close()
+
+
 def _case_tile_d100():
     """The D = 100 executors of the batching study (133 executors, 27556
     individuals), 20 fused generations: one k_fused_tile launch."""
@@ -708,6 +797,9 @@ def main(argv=None):
         return
     if args.workload == "full":
         run_full(args)
+        return
+    if args.workload == "mlp":
+        run_mlp(args)
         return
     if args.impl == "reference":
         run_reference(args)

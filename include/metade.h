@@ -268,7 +268,7 @@ METADE_API metade_status metade_plan_info(const metade_ctx *ctx, char *buf, size
  * of launches since the last read -- kinds: 0 fused small-D kernel, 1 fused
  * general kernel, 2 tensor-core rotation GEMM, 3 whole tensor-core generation,
  * 4 fused tile kernel with R^T streamed (128 < D_pad <= 256), 5 fused tile
- * kernel with R^T resident (D_pad <= 128), 6 fused MLP-objective kernel --
+ * kernel with R^T resident (D_pad <= 128), 6 MLP-objective generations --
  * then clears them.  ms and count are host arrays of 7 (may be NULL). */
 METADE_API metade_status metade_profile(metade_ctx *ctx, int32_t enable);
 METADE_API metade_status metade_profile_read(metade_ctx *ctx, double *ms, int64_t *count);

@@ -245,7 +245,7 @@ def metade_autotune(ctx: int, pop, fit, theta, n_gens: int = 3) -> None:
 
 
 PROFILE_KINDS = ["fused_small", "fused_general", "tc_gemm", "tc_generation", "fused_tile_stream", "fused_tile",
-                 "fused_mlp"]
+                 "mlp_generations"]
 
 
 def metade_profile(ctx: int, enable: bool) -> None:

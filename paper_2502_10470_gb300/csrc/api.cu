@@ -99,6 +99,8 @@ struct metade_ctx {
     float *ascale = nullptr, *bscale = nullptr;                                // FP8 dequantisation factors
     unsigned* amax = nullptr;                                                  // FP8: max|R| scratch
     float *mlp_x = nullptr, *mlp_y = nullptr;  // MLP objective: inputs [256][16], targets per problem [256][2]
+    MlpPlan mlpp{};                             // MLP executors' rows (n_rows 0: none)
+    int *mlp_execs = nullptr, *mlp_row_exec = nullptr, *mlp_topk = nullptr;
 };
 
 namespace {
@@ -148,14 +150,11 @@ double work_cost(const InstDesc& d) { return (double)d.np * ((double)d.dim * d.d
 // first, so the block scheduler hands the longest executors out first).
 metade_status build_plan(metade_ctx* c) {
     std::vector<std::vector<int>> small(33);
-    std::vector<int> general, tile, tile_stream, mlp;
+    std::vector<int> general, tile, tile_stream;
     for (int k = 0; k < c->n_inst; ++k) {
         if (c->tc && c->is_tc[k]) continue;
         const InstDesc& d = c->hdesc[k];
-        if (d.obj == kMlp) {  // the MLP objective has its own kernel
-            mlp.push_back(k);
-            continue;
-        }
+        if (d.obj == kMlp) continue;  // the MLP objective has its own per-generation path
         const int dm = small_dmax_for(d.dim);
         // The tile kernels decide near ties by the FP32 difference form only;
         // FP64 tie re-evaluation runs in the small and general kernels.
@@ -215,29 +214,6 @@ metade_status build_plan(metade_ctx* c) {
         b.work_off = (int)order.size();
         b.n_work = (int)tv.size();
         order.insert(order.end(), tv.begin(), tv.end());
-        c->buckets.push_back(b);
-    }
-    if (!mlp.empty()) {
-        sort_desc(mlp);
-        int mnp = 0, mdp = 0;
-        for (int k : mlp) {
-            mnp = std::max(mnp, c->hdesc[k].np);
-            mdp = std::max(mdp, c->hdesc[k].dpad);
-        }
-        Bucket b;
-        b.plan.kind = 4;
-        b.plan.dmax = 0;
-        b.plan.threads = kMlpN;
-        b.plan.grid = (int)mlp.size();
-        b.plan.max_np = mnp;
-        b.plan.max_dpad = mdp;
-        b.plan.rot_smem = 0;
-        b.plan.pop_smem = 0;
-        b.plan.smem = fused_smem_mlp(mnp, mdp);
-        if (b.plan.smem > kSmemLimit) return METADE_EUNSUPPORTED;
-        b.work_off = (int)order.size();
-        b.n_work = (int)mlp.size();
-        order.insert(order.end(), mlp.begin(), mlp.end());
         c->buckets.push_back(b);
     }
     if (!general.empty()) {
@@ -309,14 +285,10 @@ metade_status run_inner(metade_ctx* c, cudaStream_t st, float* pop, float* fit, 
         const bool pr = prof_pair(c, st,
                                   b.plan.kind == 0   ? kProfFusedSmall
                                   : b.plan.kind == 3 ? (b.plan.rot_smem ? kProfFusedTile : kProfFusedTileStream)
-                                  : b.plan.kind == 4 ? kProfFusedMlp
                                                      : kProfFusedGeneral,
                                   &e0, &e1);
         if (pr) cudaEventRecord(e0, st);
-        if (b.plan.kind == 4)
-            CK(launch_fused_mlp(a, c->work + b.work_off, b.n_work, b.plan, c->uscr, c->mlp_x, c->mlp_y, st));
-        else
-            CK(launch_fused(a, c->work + b.work_off, b.n_work, b.plan, c->uscr, st));
+        CK(launch_fused(a, c->work + b.work_off, b.n_work, b.plan, c->uscr, st));
         if (pr) cudaEventRecord(e1, st);
         *launches += 1;
     }
@@ -331,10 +303,23 @@ metade_status run_inner(metade_ctx* c, cudaStream_t st, float* pop, float* fit, 
             if (pe) cudaEventRecord(e1, st);
             *launches += 5;
         }
-        if (best_f || best_i) {
-            CK(launch_best(c->desc, c->n_inst, fit, best_f, best_i, st));
-            *launches += 1;
+    }
+    if (c->mlpp.n_rows > 0) {  // MLP executors: four launches per generation
+        cudaEvent_t e0, e1;
+        const bool pr = prof_pair(c, st, kProfFusedMlp, &e0, &e1);
+        if (pr) cudaEventRecord(e0, st);
+        for (int g = 0; g < n_gens; ++g) {
+            StepArgs t = step_args(c, pop, fit, theta, epoch, epoch_dev, gen0 + (uint32_t)g, 1, nullptr, nullptr);
+            CK(launch_mlp_generation(t, c->mlpp, st));
+            *launches += 4;
         }
+        if (pr) cudaEventRecord(e1, st);
+    }
+    // the per-generation paths leave best_f / best_i to one reduction over
+    // every executor (the fused kernels write their own too)
+    if ((c->tc || c->mlpp.n_rows > 0) && (best_f || best_i)) {
+        CK(launch_best(c->desc, c->n_inst, fit, best_f, best_i, st));
+        *launches += 1;
     }
     return METADE_OK;
 }
@@ -427,6 +412,9 @@ void metade_destroy(metade_ctx* c) {
     cudaFree(c->amax);
     cudaFree(c->mlp_x);
     cudaFree(c->mlp_y);
+    cudaFree(c->mlp_execs);
+    cudaFree(c->mlp_row_exec);
+    cudaFree(c->mlp_topk);
     if (c->cap) cudaStreamDestroy(c->cap);
     delete c;
 }
@@ -535,6 +523,15 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
         delete c;
         return METADE_EUNSUPPORTED;
     }
+    // executors of the MLP objective: their first row (InstDesc.tc_row) in the MLP row list
+    std::vector<int> mlp_execs, mlp_row_exec;
+    for (int k = 0; k < c->n_inst; ++k) {
+        InstDesc& d = c->hdesc[k];
+        if (d.obj != kMlp) continue;
+        d.tc_row = (int)mlp_row_exec.size();
+        mlp_execs.push_back(k);
+        for (int i = 0; i < d.np; ++i) mlp_row_exec.push_back(k);
+    }
     // executors on the tensor cores: operand row offsets (InstDesc.tc_row), tiles
     c->is_tc.assign(c->n_inst, 0);
     std::vector<int> tc_execs, tc_row_exec, tc_tiles;
@@ -617,6 +614,26 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
                                               c->mlp_y + mlp_yoff[p], c->st);
             if (!okm || cudaStreamSynchronize(c->st)) return fail(METADE_ECUDA);
             c->launches += 1 + n_mlp;
+            if (dalloc(&c->mlp_execs, mlp_execs.size()) || dalloc(&c->mlp_row_exec, mlp_row_exec.size()) ||
+                dalloc(&c->mlp_topk, (size_t)c->n_indiv))
+                return fail(METADE_ENOMEM);
+            if (cudaMemcpy(c->mlp_execs, mlp_execs.data(), sizeof(int) * mlp_execs.size(), cudaMemcpyHostToDevice) ||
+                cudaMemcpy(c->mlp_row_exec, mlp_row_exec.data(), sizeof(int) * mlp_row_exec.size(),
+                           cudaMemcpyHostToDevice))
+                return fail(METADE_ECUDA);
+            MlpPlan& m = c->mlpp;
+            m.execs = c->mlp_execs;
+            m.n_exec = (int)mlp_execs.size();
+            m.row_exec = c->mlp_row_exec;
+            m.n_rows = (int)mlp_row_exec.size();
+            m.topk_all = c->mlp_topk;
+            m.uscr = c->uscr;
+            m.fu = c->fuscr;
+            m.x = c->mlp_x;
+            m.y = c->mlp_y;
+            m.max_dpad = 0;
+            for (int k : mlp_execs) m.max_dpad = std::max(m.max_dpad, c->hdesc[k].dpad);
+            if ((size_t)8 * m.max_dpad * sizeof(float) > kSmemLimit) return fail(METADE_EUNSUPPORTED);
         }
         metade_status s = build_plan(c);
         if (s != METADE_OK) return fail(s);
@@ -856,7 +873,6 @@ metade_status metade_autotune(metade_ctx* c, const float* pop, const float* fit,
     if (cudaEventCreate(&e0) || cudaEventCreate(&e1)) st = METADE_ECUDA;
     for (Bucket& b : c->buckets) {
         if (st != METADE_OK) break;
-        if (b.plan.kind == 4) continue;  // MLP kernel: one thread per input, nothing to tune
         std::vector<int> cands = b.plan.kind == 0 ? std::vector<int>{32, 64, 128, 256}
                                                   : std::vector<int>{128, 256, 512};
         if (b.plan.kind == 3) cands = b.plan.rot_smem ? std::vector<int>{128, 256} : std::vector<int>{256};
@@ -918,7 +934,6 @@ metade_status metade_plan_info(const metade_ctx* c, char* buf, size_t len) {
                  b ? ", " : "",
                  k.plan.kind == 0   ? "fused_small"
                  : k.plan.kind == 3 ? (k.plan.rot_smem ? "fused_tile" : "fused_tile_stream")
-                 : k.plan.kind == 4 ? "fused_mlp"
                                     : "fused_general",
                  k.plan.dmax,
                  k.plan.threads,
@@ -934,6 +949,14 @@ metade_status metade_plan_info(const metade_ctx* c, char* buf, size_t len) {
                  ", \"tensor_core\": {\"kernel\": \"k_rot_tc\", \"precision\": \"%s\", \"executors\": %d, "
                  "\"tiles\": %d, \"kp\": %d, \"tile\": [128, 256, 64]}",
                  c->tcp.fp8 ? "fp8e4m3" : c->tcp.split ? "bf16x3" : "bf16", c->tcp.n_exec, c->tcp.n_tiles, c->tcp.kp);
+        s += tmp;
+    }
+    if (c->mlpp.n_rows > 0) {
+        char tmp[160];
+        snprintf(tmp, sizeof(tmp),
+                 ", \"mlp\": {\"kernels\": [\"k_mlp_prologue\", \"k_mlp_trial\", \"k_mlp_eval\", \"k_mlp_select\"], "
+                 "\"executors\": %d, \"rows\": %d}",
+                 c->mlpp.n_exec, c->mlpp.n_rows);
         s += tmp;
     }
     s += "}";

@@ -26,7 +26,7 @@ struct InstDesc {
     int obj, stream;     // objective id, Philox counter word 0
     int shift_off, kp;   // padded o [dpad]; pbest pool size
     int prob;            // problem index
-    int tc_row;          // tensor-core path: first row of the executor in the GEMM operands
+    int tc_row;          // tensor-core / MLP path: first row of the executor in that path's row list
     int on_tc;           // 1: the executor is evaluated on the tensor-core path
     int aux;             // MLP objective: offset of the problem's targets [256][2]
 };
@@ -244,6 +244,9 @@ __host__ __device__ inline int mlp_hidden(int dim) { return (dim >= 21 && (dim -
 
 // Network output for one input x: hidden units in order j = 0..h-1, each
 // pre-activation summed over k ascending (fma), output accumulated over j.
+// Four hidden units at a time when h % 4 == 0 (one float4 load of W1 feeds
+// four fma chains; th must then be 16-byte aligned); the arithmetic of every
+// unit and the order of the output sums are the same either way.
 // T = float (FP32 evaluation) or double (FP64 evaluation).
 template <typename T>
 __device__ __forceinline__ void mlp_forward(int h, const float* th, const T (&x)[kMlpIn], T (&y)[kMlpOut]) {
@@ -253,7 +256,31 @@ __device__ __forceinline__ void mlp_forward(int h, const float* th, const T (&x)
     const float* b2 = W2 + kMlpOut * h;
     y[0] = T(b2[0]);
     y[1] = T(b2[1]);
-    for (int j = 0; j < h; ++j) {
+    int j = 0;
+    if ((h & 3) == 0) {
+        for (; j < h; j += 4) {
+            const float4 bb = *reinterpret_cast<const float4*>(b1 + j);
+            T a[4] = {T(bb.x), T(bb.y), T(bb.z), T(bb.w)};
+#pragma unroll
+            for (int k = 0; k < kMlpIn; ++k) {
+                const float4 w = *reinterpret_cast<const float4*>(W1 + k * h + j);
+                a[0] = fma(x[k], T(w.x), a[0]);
+                a[1] = fma(x[k], T(w.y), a[1]);
+                a[2] = fma(x[k], T(w.z), a[2]);
+                a[3] = fma(x[k], T(w.w), a[3]);
+            }
+            const float4 w2a = *reinterpret_cast<const float4*>(W2 + 2 * j);
+            const float4 w2b = *reinterpret_cast<const float4*>(W2 + 2 * j + 4);
+            const float v2[8] = {w2a.x, w2a.y, w2a.z, w2a.w, w2b.x, w2b.y, w2b.z, w2b.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const T t = tanh(a[q]);
+                y[0] = fma(t, T(v2[2 * q]), y[0]);
+                y[1] = fma(t, T(v2[2 * q + 1]), y[1]);
+            }
+        }
+    }
+    for (; j < h; ++j) {
         T a = T(b1[j]);
 #pragma unroll
         for (int k = 0; k < kMlpIn; ++k) a = fma(x[k], T(W1[k * h + j]), a);

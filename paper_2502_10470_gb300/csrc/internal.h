@@ -57,7 +57,7 @@ cudaError_t launch_plain_generation(const StepArgs& a, int k, const InstDesc& d,
 // Batched path: executors listed in `work` (schedule order), all n_gens generations.
 struct FusedPlan {
     int kind;      // 0 small (thread per individual), 1 general (warp per individual),
-                   // 3 tile (register-blocked rotation GEMM per tile of individuals), 4 MLP objective
+                   // 3 tile (register-blocked rotation GEMM per tile of individuals)
     int dmax;      // small: compile-time row bound
     int threads;   // block size
     int grid;      // CTAs (<= n_work; CTAs loop over work items)
@@ -72,10 +72,20 @@ size_t fused_smem_small(int dmax, int max_np);
 size_t fused_smem_general(int max_np, int max_dpad, int threads, bool rot_in_smem);
 int small_dmax_for(int dim);  // 0 when the small kernel does not apply
 size_t fused_smem_tile(int max_np, int max_dpad, int threads, bool rot_smem);
-// MLP objective (k_mlp.cu): kind 4, 256 threads (thread n evaluates input n)
-size_t fused_smem_mlp(int max_np, int max_dpad);
-cudaError_t launch_fused_mlp(const StepArgs& a, const int* work, int n_work, const FusedPlan& p, float* uscr,
-                             const float* mlp_x, const float* mlp_y, cudaStream_t st);
+// MLP objective (k_mlp.cu): its executors' rows (InstDesc.tc_row = first row)
+struct MlpPlan {
+    const int* execs;      // device [n_exec]
+    int n_exec;
+    const int* row_exec;   // device [n_rows] row -> executor
+    int n_rows;
+    int* topk_all;         // device [n_indiv] pbest pools
+    float* uscr;           // trial rows (population layout)
+    float* fu;             // trial fitness [n_indiv]
+    const float* x;        // inputs [256][16]
+    const float* y;        // targets of every MLP problem ([256][2] at InstDesc.aux)
+    int max_dpad;
+};
+cudaError_t launch_mlp_generation(const StepArgs& a, const MlpPlan& p, cudaStream_t st);
 cudaError_t launch_mlp_inputs(float* X, cudaStream_t st);
 cudaError_t launch_mlp_targets(const float* X, const float* teacher, int h, float* Y, cudaStream_t st);
 cudaError_t launch_fused_tile(const StepArgs& a, const int* work, int n_work, const FusedPlan& p, float* u_scratch,

@@ -1,16 +1,20 @@
 // k_mlp.cu -- the MLP regression objective (6), a neuroevolution-like
 // large-D problem: its fixed inputs and teacher targets, and the batched path
-// for its executors.
+// for its executors, one generation of all of them per four launches:
 //
 // k_mlp_inputs    the 256 x 16 inputs, uniform in [-1, 1] (counter-based draws)
 // k_mlp_targets   teacher outputs of one problem, by the same FP32 forward pass
 //                 the evaluation uses (so f(teacher) = 0 exactly)
-// k_fused_mlp     one CTA (256 threads) per executor runs all fused
-//                 generations: trials by warps (the PDE step of every other
-//                 kernel), then each individual's f with thread n evaluating
-//                 input n (the parameters in shared memory, read as
-//                 broadcasts; the thread's input row in registers), a block
-//                 sum, then greedy selection on the FP32 values
+// k_mlp_prologue  best and pbest pool per executor (block per executor)
+// k_mlp_trial     trial rows, warp per individual (the PDE step of every
+//                 other kernel), into the scratch population
+// k_mlp_eval      f of every trial, CTA per individual: thread n runs input n
+//                 (the parameters in shared memory, read as broadcasts; the
+//                 input row in registers), then a block sum
+// k_mlp_select    greedy selection on the FP32 values, warp per individual
+//
+// Executor k's individuals are rows InstDesc.tc_row .. tc_row + NP - 1 of the
+// MLP row list.
 #include "block.cuh"
 #include "internal.h"
 
@@ -34,114 +38,99 @@ __global__ void k_mlp_targets(const float* __restrict__ X, const float* __restri
     Y[2 * n + 1] = y[1];
 }
 
-__global__ void __launch_bounds__(256) k_fused_mlp(StepArgs a, const int* __restrict__ work, int n_work,
-                                                   float* uscr, const float* __restrict__ mlp_x,
-                                                   const float* __restrict__ mlp_y, int max_np, int max_dpad) {
-    extern __shared__ __align__(16) float sm[];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;  // thread tid evaluates input tid
-    float* f = sm;
-    float* fu = f + max_np;
-    int* topk = reinterpret_cast<int*>(fu + max_np);  // pbest ranks; selection: accept flags
-    int* red = topk + max_np;                         // 64 words
-    float* th = sm + ((3 * max_np + 64 + 3) & ~3);    // parameters of the individual being evaluated
-    float* db = th + max_dpad;                        // per warp: u - o of the trial kernel
+__global__ void k_mlp_prologue(StepArgs a, const int* __restrict__ execs, int* topk_all) {
+    const int k = execs[blockIdx.x];
+    const InstDesc d = a.desc[k];
+    const Strat s = load_strat(a.theta + 6 * k, d.np);
+    if (!s.ok) {
+        if (threadIdx.x == 0) set_status(a.status, 1);
+        return;
+    }
+    block_topk(a.fit + d.fit_off, d.np, d.kp, topk_all + d.fit_off);  // topk[0] is the best
+}
+
+__global__ void __launch_bounds__(256) k_mlp_trial(StepArgs a, const int* __restrict__ row_exec, int n_rows,
+                                                   const int* __restrict__ topk_all, float* uscr, int ws) {
+    extern __shared__ __align__(16) float smt[];
+    const int warp = threadIdx.x >> 5;
+    const int r = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (r >= n_rows) return;
+    const int k = row_exec[r];
+    const InstDesc d = a.desc[k];
+    const int i = r - d.tc_row;
+    const Strat s = load_strat(a.theta + 6 * k, d.np);
+    if (!s.ok) return;
+    const uint32_t epoch = a.epoch_dev ? *a.epoch_dev : a.epoch;
+    const Ctr c = make_ctr(a.key, (uint32_t)d.stream, a.gen0, (uint32_t)i, epoch);
+    const int* topk = topk_all + d.fit_off;
+    Indiv v;
+    indiv_setup(s, c, i, d.np, d.dim, d.kp, topk, topk[0], v);
+    const int L = s.cs == 2 ? exp_length(c, d.dim, s.cri) : 0;
+    warp_trial(s, c, v, i, d.dim, L, a.pop + d.pop_off, d.dpad, a.shift + d.shift_off, a.lo, a.hi,
+               uscr + d.pop_off + (long long)i * d.dpad, smt + (size_t)warp * ws);
+}
+
+__global__ void __launch_bounds__(256) k_mlp_eval(const InstDesc* __restrict__ desc, const int* __restrict__ row_exec,
+                                                  const float* __restrict__ uscr, const float* __restrict__ mlp_x,
+                                                  const float* __restrict__ mlp_y, float* fu) {
+    extern __shared__ __align__(16) float th[];  // parameters of this row's trial
+    __shared__ float part[kMlpN / 32];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;  // thread tid runs input tid
+    const int r = blockIdx.x;
+    const InstDesc d = desc[row_exec[r]];
+    const int i = r - d.tc_row, h = mlp_hidden(d.dim);
+    const float* u = uscr + d.pop_off + (long long)i * d.dpad;
+    for (int e = tid; e < d.dim; e += blockDim.x) th[e] = u[e];
     float x[kMlpIn];
 #pragma unroll
-    for (int k = 0; k < kMlpIn; ++k) x[k] = mlp_x[tid * kMlpIn + k];
-    for (int w = blockIdx.x; w < n_work; w += gridDim.x) {
-        const int k = work[w];
-        const InstDesc d = a.desc[k];
-        const Strat st = load_strat(a.theta + 6 * k, d.np);
-        if (!st.ok) {
-            if (tid == 0) set_status(a.status, 1);
-            continue;
-        }
-        const int np = d.np, dim = d.dim, dp = d.dpad, nbr = dp >> 2, h = mlp_hidden(dim);
-        const float y0 = mlp_y[d.aux + 2 * tid], y1 = mlp_y[d.aux + 2 * tid + 1];
-        const uint32_t epoch = a.epoch_dev ? *a.epoch_dev : a.epoch;
-        float* X = a.pop + d.pop_off;
-        float* Ug = uscr + d.pop_off;
-        const float* o = a.shift + d.shift_off;
-        for (int i = tid; i < np; i += blockDim.x) f[i] = a.fit[d.fit_off + i];
-        __syncthreads();
-        const bool pb = st.uses_pbest();
-        for (int g = 0; g < a.n_gens; ++g) {
-            const uint32_t gen = a.gen0 + (uint32_t)g;
-            int best;
-            if (pb) {
-                block_topk(f, np, d.kp, topk);
-                __syncthreads();
-                best = topk[0];
-            } else {
-                best = block_argmin(f, np, red);
-            }
-            // trials, warp per individual, into the scratch population
-            for (int i = warp; i < np; i += blockDim.x >> 5) {
-                const Ctr c = make_ctr(a.key, (uint32_t)d.stream, gen, (uint32_t)i, epoch);
-                Indiv v;
-                indiv_setup(st, c, i, np, dim, d.kp, pb ? topk : nullptr, best, v);
-                const int L = st.cs == 2 ? exp_length(c, dim, st.cri) : 0;
-                warp_trial(st, c, v, i, dim, L, X, dp, o, a.lo, a.hi, Ug + (long long)i * dp,
-                           db + (size_t)warp * max_dpad);
-                __syncwarp();
-            }
-            __syncthreads();
-            // f of every trial: thread n runs input n, then a block sum
-            for (int i = 0; i < np; ++i) {
-                for (int e = tid; e < dim; e += blockDim.x) th[e] = Ug[(long long)i * dp + e];
-                __syncthreads();
-                float y[kMlpOut];
-                mlp_forward<float>(h, th, x, y);
-                const float e0 = y[0] - y0, e1 = y[1] - y1;
-                float s = warp_sum(fmaf(e0, e0, e1 * e1));
-                if (lane == 0) reinterpret_cast<float*>(red)[warp] = s;
-                __syncthreads();
-                if (tid == 0) {
-                    float t = 0.0f;
-                    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += reinterpret_cast<float*>(red)[q];
-                    fu[i] = nan_to_inf(t * (1.0f / (kMlpN * kMlpOut)));
-                }
-                __syncthreads();
-            }
-            // greedy selection on the FP32 values (no difference form exists for this objective)
-            int* acc = topk;
-            for (int i = tid; i < np; i += blockDim.x) {
-                const float fn = fu[i];
-                const int take = fn <= f[i] ? 1 : 0;
-                if (take) f[i] = fn;
-                acc[i] = take;
-            }
-            __syncthreads();
-            for (int e = tid; e < np * nbr; e += blockDim.x) {
-                const int i = e / nbr, q = e - i * nbr;
-                if (acc[i])
-                    *reinterpret_cast<float4*>(X + (long long)i * dp + 4 * q) =
-                        *reinterpret_cast<const float4*>(Ug + (long long)i * dp + 4 * q);
-            }
-            __syncthreads();
-        }
-        for (int i = tid; i < np; i += blockDim.x) a.fit[d.fit_off + i] = f[i];
-        const int b = block_argmin(f, np, red);
-        if (tid == 0 && a.best_f) a.best_f[k] = f[b];
-        if (tid == 0 && a.best_i) a.best_i[k] = b;
-        __syncthreads();
+    for (int q = 0; q < kMlpIn; ++q) x[q] = mlp_x[tid * kMlpIn + q];
+    const float y0 = mlp_y[d.aux + 2 * tid], y1 = mlp_y[d.aux + 2 * tid + 1];
+    __syncthreads();
+    float y[kMlpOut];
+    mlp_forward<float>(h, th, x, y);
+    const float e0 = y[0] - y0, e1 = y[1] - y1;
+    const float s = warp_sum(fmaf(e0, e0, e1 * e1));
+    if (lane == 0) part[warp] = s;
+    __syncthreads();
+    if (tid == 0) {
+        float t = 0.0f;
+        for (int q = 0; q < kMlpN / 32; ++q) t += part[q];
+        fu[d.fit_off + i] = nan_to_inf(t * (1.0f / (kMlpN * kMlpOut)));
     }
 }
 
-size_t fused_smem_mlp(int max_np, int max_dpad) {
-    size_t words = (3 * (size_t)max_np + 64 + 3) & ~(size_t)3;
-    words += (size_t)max_dpad;      // parameters being evaluated
-    words += (size_t)8 * max_dpad;  // per-warp trial scratch (8 warps)
-    return words * sizeof(float);
+__global__ void __launch_bounds__(256) k_mlp_select(StepArgs a, const int* __restrict__ row_exec, int n_rows,
+                                                    const float* __restrict__ uscr, const float* __restrict__ fu) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (r >= n_rows) return;
+    const int k = row_exec[r];
+    const InstDesc d = a.desc[k];
+    if (!load_strat(a.theta + 6 * k, d.np).ok) return;
+    const int i = r - d.tc_row;
+    const float fn = fu[d.fit_off + i];
+    if (fn <= a.fit[d.fit_off + i]) {  // FP32 values decide: the objective has no difference form
+        float* X = a.pop + d.pop_off + (long long)i * d.dpad;
+        const float* U = uscr + d.pop_off + (long long)i * d.dpad;
+        for (int j = lane * 4; j < d.dpad; j += 128)
+            *reinterpret_cast<float4*>(X + j) = *reinterpret_cast<const float4*>(U + j);
+        if (lane == 0) a.fit[d.fit_off + i] = fn;
+    }
 }
 
-cudaError_t launch_fused_mlp(const StepArgs& a, const int* work, int n_work, const FusedPlan& p, float* uscr,
-                             const float* mlp_x, const float* mlp_y, cudaStream_t st) {
-    if (n_work <= 0) return cudaSuccess;
-    if (p.threads != kMlpN) return cudaErrorInvalidValue;  // thread n evaluates input n
-    cudaError_t e = cudaFuncSetAttribute(k_fused_mlp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+cudaError_t launch_mlp_generation(const StepArgs& a, const MlpPlan& p, cudaStream_t st) {
+    if (p.n_rows <= 0) return cudaSuccess;
+    k_mlp_prologue<<<p.n_exec, 256, 0, st>>>(a, p.execs, p.topk_all);
+    const int blocks = (p.n_rows + 7) / 8;
+    const size_t smem_t = (size_t)8 * p.max_dpad * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_trial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
     if (e != cudaSuccess) return e;
-    k_fused_mlp<<<p.grid, p.threads, p.smem, st>>>(a, work, n_work, uscr, mlp_x, mlp_y, p.max_np, p.max_dpad);
+    k_mlp_trial<<<blocks, 256, smem_t, st>>>(a, p.row_exec, p.n_rows, p.topk_all, p.uscr, p.max_dpad);
+    const size_t smem_e = (size_t)p.max_dpad * sizeof(float);
+    e = cudaFuncSetAttribute(k_mlp_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_e);
+    if (e != cudaSuccess) return e;
+    k_mlp_eval<<<p.n_rows, kMlpN, smem_e, st>>>(a.desc, p.row_exec, p.uscr, p.x, p.y, p.fu);
+    k_mlp_select<<<blocks, 256, 0, st>>>(a, p.row_exec, p.n_rows, p.uscr, p.fu);
     return cudaGetLastError();
 }
 

@@ -183,6 +183,22 @@ def precision(problem_seed: int = 3, run_seed: int = 0, n_inst: int = 64, np_: i
                     inner_gens=100, outer_gens=1, seed=run_seed, one_shot=0, theta=theta)
 
 
+def mlp(problem_seed: int = 5, run_seed: int = 0, n_inst: int = 64, np_: int = 100, hidden: int = 80,
+        n_prob: int = 4, inner_gens: int = 50) -> Workload:
+    """The neuroevolution-like workload: 64 inner DEs of NP 100 on the MLP
+    regression objective with h = 80 (D = 1522, the size of the paper's
+    policy networks), four teacher networks shared by 16 executors each,
+    random theta, box [-2, 2] (the teachers lie in [-0.75, 0.75])."""
+    rng = np.random.default_rng(problem_seed)
+    probs = [make_mlp_problem(rng, hidden) for _ in range(n_prob)]
+    inst_prob = (np.arange(n_inst) * n_prob // n_inst).astype(np.int32)
+    theta = random_theta(rng, n_inst)
+    return Workload(name=f"mlp-{n_inst}x{np_}xD{19 * hidden + 2}", problems=probs,
+                    inst_np=np.full(n_inst, np_, dtype=np.int32), inst_prob=inst_prob,
+                    inst_group=np.arange(n_inst, dtype=np.int32), n_groups=n_inst, n_out=0,
+                    inner_gens=inner_gens, outer_gens=1, seed=run_seed, one_shot=0, theta=theta, lo=-2.0, hi=2.0)
+
+
 def full(problem_seed: int = 4, run_seed: int = 0, n_runs: int = 8, n_out: int = 128,
          inner_gens: int = 200, outer_gens: int = 50) -> Workload:
     """Eight MetaDE runs of 128 executors (1024 concurrent inner DEs); per run

@@ -1,7 +1,9 @@
 """The MLP regression objective (id 6), a neuroevolution-like large-D
-problem, on its own fused kernel: initial and FP64 evaluations, the teacher
-optimum, one PDE step against the FP64 oracle, the fused loop against single
-launches, and its place in the plan (never the rotation kernels)."""
+problem, on its own per-generation path: initial and FP64 evaluations, the
+teacher optimum, one PDE step against the FP64 oracle, several generations
+in one call against single calls, and its place in the plan (never the
+rotation kernels).  h = 4 runs the forward pass four hidden units at a time,
+h = 21 one at a time."""
 import json
 
 import numpy as np
@@ -14,7 +16,7 @@ from gpu_util import TRIAL_ATOL, feasible_theta, make_batch, rel_err
 pytestmark = pytest.mark.gpu
 
 
-def _wl(seed=61, prec_dims=(4, 20)):
+def _wl(seed=61, prec_dims=(4, 21)):
     rng = np.random.default_rng(seed)
     probs = [synth.make_mlp_problem(rng, h) for h in prec_dims] + [synth.make_problem(rng, 10, synth.OBJ_RASTRIGIN)]
     nps = np.array([40, 64, 24], dtype=np.int32)
@@ -33,8 +35,7 @@ def test_mlp_init_eval_and_teacher_optimum():
     wl = _wl()
     b = make_batch(wl, M.METADE_PATH_BATCHED)
     plan = json.loads(M.metade_plan_info(b.ctx))
-    kinds = {bk["kernel"]: bk["executors"] for bk in plan["buckets"]}
-    assert kinds.get("fused_mlp") == 2
+    assert plan["mlp"]["executors"] == 2 and plan["mlp"]["rows"] == 104
     M.metade_init(b.ctx, b.pop, b.fit, 0)
     f64 = torch.empty(b.n_indiv, dtype=torch.float64, device="cuda")
     M.metade_eval(b.ctx, b.pop, M.METADE_FP64, f64)
@@ -84,7 +85,7 @@ def test_mlp_one_step_against_oracle():
     b.close()
 
 
-def test_mlp_fused_generations_equal_single_launches():
+def test_mlp_generations_in_one_call_equal_single_calls():
     import paper_2502_10470_gb300 as M
     wl = _wl(seed=63)
     res = []
@@ -114,8 +115,8 @@ def test_mlp_stays_off_the_rotation_paths():
     wl = _wl(seed=64, prec_dims=(14, 20))      # D = 268 and 382
     b = make_batch(wl, M.METADE_PATH_BATCHED, prec=M.METADE_BF16)
     plan = json.loads(M.metade_plan_info(b.ctx))
-    assert {bk["kernel"]: bk["executors"] for bk in plan["buckets"]}.get("fused_mlp") == 2
-    assert "tensor_core" not in plan or plan["tensor_core"]["executors"] == 0
+    assert plan["mlp"]["executors"] == 2
+    assert "tensor_core" not in plan
     b.close()
     with pytest.raises(M.MetadeError):
         make_batch(wl, M.METADE_PATH_PLAIN)
