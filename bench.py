@@ -780,7 +780,23 @@ def _case_tc_d1000():
         b.close()
 
 
-PROFILE_CASES = {"tile-d100": _case_tile_d100, "tc-d1000": _case_tc_d1000}
+def _case_mlp_d1522():
+    """The MLP workload (64 executors x NP 100, D = 1522): initialisation and
+    two generations, so 8 launches of the MLP path (k_mlp_eval twice)."""
+    import paper_2502_10470_gb300 as M
+    import synth
+    wl = synth.mlp()
+    probs = [(p.dim, p.obj, p.shift, p.rot) for p in wl.problems]
+    b = M.Batch(probs, wl.inst_np, wl.inst_prob, wl.inst_group, seed=wl.seed, one_shot=0, lo=wl.lo, hi=wl.hi)
+    b.set_theta(wl.theta)
+    M.metade_init(b.ctx, b.pop, b.fit, 0)
+    M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 0, 2, None, None)
+    if M.metade_sync(b.ctx) != M.METADE_OK:
+        raise SystemExit("device status not OK")
+    b.close()
+
+
+PROFILE_CASES = {"tile-d100": _case_tile_d100, "tc-d1000": _case_tc_d1000, "mlp-d1522": _case_mlp_d1522}
 
 
 def main(argv=None):

@@ -144,8 +144,9 @@ METADE_API metade_status metade_set_stream(metade_ctx *ctx, void *stream);
 /* Alg. 2 lines 1-2: fill every executor's population uniformly in the box
  * (x = lo + (hi - lo) U, rounded once to float32) and evaluate it (NaN
  * fitness stored as +inf): in FP32, except executors on the tensor-core path
- * (cfg.prec BF16 / BF16X3, D >= 256), which are evaluated by the rotation
- * GEMM in that precision like all their later evaluations.  `epoch` enters
+ * (cfg.prec BF16 / BF16X3 / FP8E4M3, D >= 256), which are evaluated by the
+ * rotation GEMM in that precision like all their later evaluations, and
+ * executors of the MLP objective, evaluated by that objective's kernel.  `epoch` enters
  * the draw counter: with
  * one-shot evaluation the caller passes 0 every time, so every evaluation of
  * a theta starts from the same population. */

@@ -331,9 +331,14 @@ metade_status run_init(metade_ctx* c, cudaStream_t st, float* pop, float* fit, u
                    c->lo, c->hi, st));
     // executors on the tensor cores are evaluated by the rotation GEMM in the
     // context's precision, like every later evaluation of theirs
+    // and the MLP objective's by its own evaluation kernel
     CK(launch_eval(c->desc, c->row_inst, c->n_indiv, pop, c->rotT, c->shift, false, fit, true, c->max_dpad, st,
-                   c->tc, c->mlp_x, c->mlp_y));
+                   c->tc || c->mlpp.n_rows > 0, c->mlp_x, c->mlp_y));
     *launches += 2;
+    if (c->mlpp.n_rows > 0) {
+        CK(launch_mlp_eval(c->desc, c->mlpp, pop, fit, st));
+        *launches += 1;
+    }
     if (c->tc) {
         CK(launch_tc_eval(c->desc, c->tcp, pop, c->shift, fit, c->status, st));
         *launches += 2;

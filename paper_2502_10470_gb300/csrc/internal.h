@@ -39,7 +39,8 @@ cudaError_t launch_init(const InstDesc* desc, int n_inst, int max_np, int max_dp
                         uint32_t epoch, const uint32_t* epoch_dev, float lo, float hi, cudaStream_t st);
 
 // Evaluate every row (row_inst maps rows to executors).  f64 selects FP64;
-// skip_tc leaves the rows of executors on the tensor-core path untouched.
+// skip_tc leaves the rows of executors on the tensor-core and MLP paths
+// untouched (those paths evaluate them).
 cudaError_t launch_eval(const InstDesc* desc, const int* row_inst, long long n_rows, const float* pop,
                         const float* rotT, const float* shift, bool f64, void* f_out, bool nan_inf,
                         int max_dpad, cudaStream_t st, bool skip_tc, const float* mlp_x = nullptr,
@@ -86,6 +87,8 @@ struct MlpPlan {
     int max_dpad;
 };
 cudaError_t launch_mlp_generation(const StepArgs& a, const MlpPlan& p, cudaStream_t st);
+// f of the rows `rows` (population layout) of every MLP executor into f_out (fitness layout)
+cudaError_t launch_mlp_eval(const InstDesc* desc, const MlpPlan& p, const float* rows, float* f_out, cudaStream_t st);
 cudaError_t launch_mlp_inputs(float* X, cudaStream_t st);
 cudaError_t launch_mlp_targets(const float* X, const float* teacher, int h, float* Y, cudaStream_t st);
 cudaError_t launch_fused_tile(const StepArgs& a, const int* work, int n_work, const FusedPlan& p, float* u_scratch,

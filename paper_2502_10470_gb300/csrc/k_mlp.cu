@@ -8,7 +8,8 @@
 // k_mlp_prologue  best and pbest pool per executor (block per executor)
 // k_mlp_trial     trial rows, warp per individual (the PDE step of every
 //                 other kernel), into the scratch population
-// k_mlp_eval      f of every trial, CTA per individual: thread n runs input n
+// k_mlp_eval      f of every trial (and of the initial population), CTA per
+//                 individual: thread n runs input n
 //                 (the parameters in shared memory, read as broadcasts; the
 //                 input row in registers), then a block sum
 // k_mlp_select    greedy selection on the FP32 values, warp per individual
@@ -131,6 +132,15 @@ cudaError_t launch_mlp_generation(const StepArgs& a, const MlpPlan& p, cudaStrea
     if (e != cudaSuccess) return e;
     k_mlp_eval<<<p.n_rows, kMlpN, smem_e, st>>>(a.desc, p.row_exec, p.uscr, p.x, p.y, p.fu);
     k_mlp_select<<<blocks, 256, 0, st>>>(a, p.row_exec, p.n_rows, p.uscr, p.fu);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_eval(const InstDesc* desc, const MlpPlan& p, const float* rows, float* f_out, cudaStream_t st) {
+    if (p.n_rows <= 0) return cudaSuccess;
+    const size_t smem_e = (size_t)p.max_dpad * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_e);
+    if (e != cudaSuccess) return e;
+    k_mlp_eval<<<p.n_rows, kMlpN, smem_e, st>>>(desc, p.row_exec, rows, p.x, p.y, f_out);
     return cudaGetLastError();
 }
 

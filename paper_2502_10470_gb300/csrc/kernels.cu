@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(256) k_eval(const InstDesc* __restrict__ desc,
          row += (long long)gridDim.x * (blockDim.x >> 5)) {
         const int k = row_inst[row];
         const InstDesc d = desc[k];
-        if (skip_tc && d.on_tc) continue;  // warp-uniform: one row per warp
+        if (skip_tc && (d.on_tc || d.obj == kMlp)) continue;  // warp-uniform: one row per warp
         const long long i = row - d.fit_off;
         const float* x = pop + d.pop_off + i * d.dpad;
         const float* o = shift + d.shift_off;
