@@ -340,7 +340,7 @@ metade_status run_init(metade_ctx* c, cudaStream_t st, float* pop, float* fit, u
         *launches += 1;
     }
     if (c->tc) {
-        CK(launch_tc_eval(c->desc, c->tcp, pop, c->shift, fit, c->status, st));
+        CK(launch_tc_eval(c->desc, c->tcp, pop, c->shift, c->rotT, fit, c->status, st));
         *launches += 2;
     }
     return METADE_OK;
@@ -544,17 +544,20 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
     long long tc_brows = 0;
     int tc_kp = 0, tc_max_dpad = 0;
     const bool fp8 = c->prec == METADE_FP8E4M3;
-    const int kalign = fp8 ? 128 : 64;  // K elements per 128-byte operand tile
-    if (c->prec == METADE_BF16 || c->prec == METADE_BF16X3 || fp8) {
+    const int kalign = fp8 ? 128 : 64;  // K elements per 128-byte operand tile (unused by the FP32 GEMM)
+    // FP32 contexts send executors too wide for the tile kernels (D_pad > 256)
+    // through the same pipeline with the GEMM on the CUDA cores
+    const bool simt = c->prec == METADE_FP32 && c->path == METADE_PATH_BATCHED;
+    if (c->prec == METADE_BF16 || c->prec == METADE_BF16X3 || fp8 || simt) {
         for (int k = 0; k < c->n_inst; ++k) {
             InstDesc& d = c->hdesc[k];
-            if (d.dim < kTcMinDim || d.obj == kMlp) continue;
+            if (d.obj == kMlp || (simt ? d.dpad <= 256 : d.dim < kTcMinDim)) continue;
             c->is_tc[k] = 1;
             d.tc_row = (int)tc_row_exec.size();
             d.on_tc = 1;
             tc_execs.push_back(k);
             for (int i = 0; i < d.np; ++i) tc_row_exec.push_back(k);
-            for (int m0 = 0; m0 < d.np; m0 += 128) {
+            for (int m0 = 0; m0 < d.np; m0 += simt ? 64 : 128) {
                 tc_tiles.push_back(k);
                 tc_tiles.push_back(m0);
             }
@@ -650,7 +653,7 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
         if (dalloc(&c->tc_execs, tc_execs.size()) || dalloc(&c->tc_row_exec, nrows) ||
             dalloc(&c->tc_tiles, tc_tiles.size()) || dalloc(&c->tc_brow, (size_t)c->n_prob) ||
             dalloc(&c->tc_topk, (size_t)c->n_indiv) || dalloc(&c->tc_ties, nrows + 1) ||
-            dalloc(&c->aq, nrows * tc_kp * esz) || dalloc(&c->bq, (size_t)tc_brows * tc_kp * esz) ||
+            (!simt && (dalloc(&c->aq, nrows * tc_kp * esz) || dalloc(&c->bq, (size_t)tc_brows * tc_kp * esz))) ||
             (split && (dalloc(&c->aq_lo, nrows * tc_kp * esz) || dalloc(&c->bq_lo, (size_t)tc_brows * tc_kp * esz))) ||
             (fp8 && (dalloc(&c->ascale, nrows) || dalloc(&c->bscale, (size_t)c->n_prob) || dalloc(&c->amax, 1))))
             return fail(METADE_ENOMEM);
@@ -659,7 +662,7 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
             cudaMemcpy(c->tc_tiles, tc_tiles.data(), sizeof(int) * tc_tiles.size(), cudaMemcpyHostToDevice) ||
             cudaMemcpy(c->tc_brow, tc_brow.data(), sizeof(long long) * c->n_prob, cudaMemcpyHostToDevice))
             return fail(METADE_ECUDA);
-        for (int p = 0; p < c->n_prob; ++p) {
+        for (int p = 0; p < c->n_prob && !simt; ++p) {
             if (tc_brow[p] < 0) continue;
             const int D = cfg->prob_dim[p], Dp = (D + 3) & ~3;
             if (launch_tc_pack_rot(c->rot, rot_off[p], D, Dp, tc_kp, (D + 255) / 256 * 256, c->bq, split ? c->bq_lo : nullptr,
@@ -685,6 +688,7 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
         t.ascale = c->ascale;
         t.bscale = c->bscale;
         t.fp8 = fp8 ? 1 : 0;
+        t.simt = simt ? 1 : 0;
         t.tie_list = c->tc_ties + 1;
         t.tie_count = c->tc_ties;
         {
@@ -699,12 +703,14 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
         // a tie keeps four rows of max_dpad in shared memory (FP64 with tie_fp64)
         if ((size_t)4 * tc_max_dpad * (c->tie_fp64 ? sizeof(double) : sizeof(float)) > kSmemLimit)
             return fail(METADE_EUNSUPPORTED);
-        if (!tc_make_map(&t.mapA, c->aq, (long long)nrows, tc_kp, 128, (int)esz) ||
+        if (simt) {
+            // no operands, no tensor maps: k_rot_simt reads the trial rows and R^T itself
+        } else if (!tc_make_map(&t.mapA, c->aq, (long long)nrows, tc_kp, 128, (int)esz) ||
             !tc_make_map(&t.mapB, c->bq, tc_brows, tc_kp, 256, (int)esz) ||
             (split && (!tc_make_map(&t.mapAlo, c->aq_lo, (long long)nrows, tc_kp, 128, (int)esz) ||
                        !tc_make_map(&t.mapBlo, c->bq_lo, tc_brows, tc_kp, 256, (int)esz))))
             return fail(METADE_ECUDA);
-        if (!split) {
+        if (!split && !simt) {
             t.mapAlo = t.mapA;
             t.mapBlo = t.mapB;
         }
@@ -951,9 +957,11 @@ metade_status metade_plan_info(const metade_ctx* c, char* buf, size_t len) {
     if (c->tc) {
         char tmp[256];
         snprintf(tmp, sizeof(tmp),
-                 ", \"tensor_core\": {\"kernel\": \"k_rot_tc\", \"precision\": \"%s\", \"executors\": %d, "
-                 "\"tiles\": %d, \"kp\": %d, \"tile\": [128, 256, 64]}",
-                 c->tcp.fp8 ? "fp8e4m3" : c->tcp.split ? "bf16x3" : "bf16", c->tcp.n_exec, c->tcp.n_tiles, c->tcp.kp);
+                 ", \"tensor_core\": {\"kernel\": \"%s\", \"precision\": \"%s\", \"executors\": %d, "
+                 "\"tiles\": %d, \"kp\": %d, \"tile\": [%d, 256, %d]}",
+                 c->tcp.simt ? "k_rot_simt" : "k_rot_tc",
+                 c->tcp.simt ? "fp32" : c->tcp.fp8 ? "fp8e4m3" : c->tcp.split ? "bf16x3" : "bf16", c->tcp.n_exec,
+                 c->tcp.n_tiles, c->tcp.kp, c->tcp.simt ? 64 : 128, c->tcp.simt ? 16 : 64);
         s += tmp;
     }
     if (c->mlpp.n_rows > 0) {

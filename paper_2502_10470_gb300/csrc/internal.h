@@ -110,6 +110,7 @@ struct TcPlan {
     float* ascale;           // FP8: per operand row, max|d| / 448
     float* bscale;           // FP8: per problem, max|R| / 448
     int fp8;                 // 1: e4m3 operands (kind::f8f6f4)
+    int simt;                // 1: FP32 GEMM on the CUDA cores (k_rot_simt, 64-row tiles, no operands)
     int* tie_list;           // device [n_rows] rows whose selection is a near tie
     int* tie_count;          // device counter
     int tie_ctas;            // CTAs of the tie kernel
@@ -122,8 +123,13 @@ cudaError_t launch_tc_pack_rot(const float* rot, long long rot_off, int dim, int
                                void* bq_lo, long long brow, int fp8, unsigned* amax, float* bscale, cudaStream_t st);
 // Fitness of the population rows of every tensor-core executor, by the
 // rotation GEMM in the plan's precision (written into fit).
-cudaError_t launch_tc_eval(const InstDesc* desc, const TcPlan& p, const float* pop, const float* shift, float* fit,
-                           int* status, cudaStream_t st);
+cudaError_t launch_tc_eval(const InstDesc* desc, const TcPlan& p, const float* pop, const float* shift,
+                           const float* rotT, float* fit, int* status, cudaStream_t st);
+// FP32 rotation GEMM + objective on the CUDA cores (k_gemm32.cu): f of the
+// rows `rows` (population layout) of every 64-row tile into f_out
+size_t rot_simt_smem();
+cudaError_t launch_rot_simt(const InstDesc* desc, const int* tiles, int n_tiles, const float* rows, const float* shift,
+                            const float* rotT, float* f_out, cudaStream_t st);
 cudaError_t launch_tc_generation(const StepArgs& a, const TcPlan& p, cudaStream_t st, cudaEvent_t gemm0 = nullptr,
                                  cudaEvent_t gemm1 = nullptr);
 

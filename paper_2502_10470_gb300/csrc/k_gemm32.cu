@@ -1,0 +1,124 @@
+// k_gemm32.cu -- k_rot_simt: the rotation GEMM and objective on the CUDA
+// cores in FP32, for executors too wide for the tile kernels (D_pad > 256)
+// when the context computes in FP32.  It takes the place of k_rot_tc in the
+// tensor-core pipeline (prologue, trial, GEMM + objective, selection, ties).
+//
+// One CTA (256 threads) per 64-row tile of an executor.  The CTA walks the
+// columns of Z in chunks of 256; for each chunk it streams K in chunks of 16:
+// (u - o)^T [16][64] (formed from the trial rows) and R^T [16][256] go to
+// shared memory, and every thread accumulates four 4x4 blocks of Z (rows
+// 4 tx.., columns 4 (ty0 + 16 j)..) in registers.  k ascends in every fma
+// chain, so z is bit-identical to the other FP32 rotations.  The chunk of Z
+// then goes to shared memory and four lanes per row push it, in column order,
+// into the objective's running state (group_obj_push), which carries across
+// the chunks; the last chunk gives f.
+#include "block.cuh"
+#include "group_obj.cuh"
+#include "internal.h"
+
+namespace metade {
+
+namespace {
+constexpr int kSM = 64;         // rows per tile
+constexpr int kSN = 256;        // columns of Z per chunk
+constexpr int kSK = 16;         // K per stage
+constexpr int kSAP = kSM + 4;   // row length of the (u - o)^T stage
+constexpr int kSZP = kSN + 4;   // row length of the Z chunk
+
+template <int OBJ>
+__device__ __forceinline__ void push_chunk(GroupObj& g, const float* zr, int col0, int ncol, int s, int dim) {
+    for (int r0 = 0; r0 < ncol; r0 += 4) group_obj_push<4, OBJ>(OBJ, g, zr[r0 + s], col0 + r0, s, dim);
+}
+}  // namespace
+
+__global__ void __launch_bounds__(256, 2) k_rot_simt(const InstDesc* __restrict__ desc, const int* __restrict__ tiles,
+                                                     const float* __restrict__ rows, const float* __restrict__ shift,
+                                                     const float* __restrict__ rotT, float* f_out) {
+    extern __shared__ __align__(16) float sm[];
+    float* As = sm;                    // [kSK][kSAP]
+    float* Bs = As + kSK * kSAP;       // [kSK][kSN]
+    float* Zs = Bs + kSK * kSN;        // [kSM][kSZP]
+    const int tid = threadIdx.x;
+    const int k = tiles[2 * blockIdx.x], m0 = tiles[2 * blockIdx.x + 1];
+    const InstDesc d = desc[k];
+    const int dim = d.dim, dp = d.dpad, nv = min(kSM, d.np - m0);
+    const float* X = rows + d.pop_off + (long long)m0 * dp;
+    const float* o = shift + d.shift_off;
+    const float* RT = rotT + d.rot_off;
+    const int tx = tid & 15, ty0 = tid >> 4;    // GEMM blocks
+    const int orow = tid >> 2, os = tid & 3;    // objective: four lanes per row
+    GroupObj g;
+    for (int col0 = 0; col0 < dim; col0 += kSN) {
+        float acc[4][4][4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[j][p][q] = 0.f;
+        for (int k0 = 0; k0 < dim; k0 += kSK) {
+            const int kn = min(kSK, dim - k0);
+            for (int e = tid; e < kSK * kSM; e += blockDim.x) {  // consecutive threads read along a row
+                const int t = e / kSK, kk = e - t * kSK;
+                float v = 0.f;
+                if (t < nv && kk < kn) v = X[(long long)t * dp + k0 + kk] - o[k0 + kk];
+                As[kk * kSAP + t] = v;
+            }
+            for (int e = tid; e < kSK * kSN / 4; e += blockDim.x) {
+                const int kk = e / (kSN / 4), q = e - kk * (kSN / 4), col = col0 + 4 * q;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (kk < kn && col < dp) v = *reinterpret_cast<const float4*>(RT + (long long)(k0 + kk) * dp + col);
+                *reinterpret_cast<float4*>(Bs + kk * kSN + 4 * q) = v;
+            }
+            __syncthreads();
+            for (int kk = 0; kk < kn; ++kk) {
+                const float4 av = *reinterpret_cast<const float4*>(As + kk * kSAP + 4 * tx);
+                const float ar[4] = {av.x, av.y, av.z, av.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float4 rv = *reinterpret_cast<const float4*>(Bs + kk * kSN + 4 * (ty0 + 16 * j));
+                    const float rr[4] = {rv.x, rv.y, rv.z, rv.w};
+#pragma unroll
+                    for (int p = 0; p < 4; ++p)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) acc[j][p][q] = fmaf(rr[q], ar[p], acc[j][p][q]);
+                }
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+                *reinterpret_cast<float4*>(Zs + (4 * tx + p) * kSZP + 4 * (ty0 + 16 * j)) =
+                    make_float4(acc[j][p][0], acc[j][p][1], acc[j][p][2], acc[j][p][3]);
+        __syncthreads();
+        const int ncol = min(kSN, dim - col0);
+        const float* zr = Zs + orow * kSZP;
+        switch (d.obj) {  // one dispatch per chunk; every lane of the CTA takes part (shuffles)
+        case kSphere: push_chunk<kSphere>(g, zr, col0, ncol, os, dim); break;
+        case kRosenbrock: push_chunk<kRosenbrock>(g, zr, col0, ncol, os, dim); break;
+        case kRastrigin: push_chunk<kRastrigin>(g, zr, col0, ncol, os, dim); break;
+        case kGriewank: push_chunk<kGriewank>(g, zr, col0, ncol, os, dim); break;
+        case kAckley: push_chunk<kAckley>(g, zr, col0, ncol, os, dim); break;
+        default: push_chunk<kSchwefel12>(g, zr, col0, ncol, os, dim); break;
+        }
+        __syncthreads();
+    }
+    const float f = group_obj_finish<4>(d.obj, g, dim);
+    if (os == 0 && orow < nv) f_out[d.fit_off + m0 + orow] = nan_to_inf(f);
+}
+
+size_t rot_simt_smem() { return (size_t)(kSK * kSAP + kSK * kSN + kSM * kSZP) * sizeof(float); }
+
+cudaError_t launch_rot_simt(const InstDesc* desc, const int* tiles, int n_tiles, const float* rows, const float* shift,
+                            const float* rotT, float* f_out, cudaStream_t st) {
+    if (n_tiles <= 0) return cudaSuccess;
+    const size_t smem = rot_simt_smem();
+    cudaError_t e = cudaFuncSetAttribute(k_rot_simt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_rot_simt<<<n_tiles, 256, smem, st>>>(desc, tiles, rows, shift, rotT, f_out);
+    return cudaGetLastError();
+}
+
+}  // namespace metade

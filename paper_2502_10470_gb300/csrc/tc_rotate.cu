@@ -300,6 +300,7 @@ __global__ void __launch_bounds__(128, 2)
 // max|v| / 448 goes to *inv_scale for the GEMM epilogue.
 __device__ __forceinline__ void pack_operand_row(const float* v, int dim, int kp, void* q, void* q_lo, long long r,
                                                  int fp8, float* inv_scale) {
+    if (!q) return;  // FP32 GEMM on the CUDA cores: no operand rows
     const int lane = threadIdx.x & 31;
     if (fp8) {
         float m = 0.0f;
@@ -617,9 +618,10 @@ cudaError_t launch_tc_pack_rot(const float* rot, long long rot_off, int dim, int
     return cudaGetLastError();
 }
 
-cudaError_t launch_tc_eval(const InstDesc* desc, const TcPlan& p, const float* pop, const float* shift, float* fit,
-                           int* status, cudaStream_t st) {
+cudaError_t launch_tc_eval(const InstDesc* desc, const TcPlan& p, const float* pop, const float* shift,
+                           const float* rotT, float* fit, int* status, cudaStream_t st) {
     if (p.n_rows <= 0) return cudaSuccess;
+    if (p.simt) return launch_rot_simt(desc, p.tiles, p.n_tiles, pop, shift, rotT, fit, st);
     const size_t smem_p = (size_t)8 * p.max_dpad * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k_tc_pack_pop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p);
     if (e != cudaSuccess) return e;
@@ -654,23 +656,29 @@ cudaError_t launch_tc_generation(const StepArgs& a, const TcPlan& p, cudaStream_
     if (e != cudaSuccess) return e;
     k_tc_trial<<<blocks, 256, smem_t, st>>>(a, p.row_exec, p.n_rows, p.topk_all, p.uscr, p.aq, p.split ? p.aq_lo : nullptr,
                                             p.kp, p.max_dpad, p.fp8, p.ascale);
-    const size_t smem_g = tc_gemm_smem(p.split);
-    e = cudaFuncSetAttribute(k_rot_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_g);
-    if (e != cudaSuccess) return e;
-    TcGemmArgs g;
-    g.desc = a.desc;
-    g.tiles = p.tiles;
-    g.brow = p.brow;
-    g.fu = p.fu;
-    g.kt = p.kp / (p.fp8 ? kBK8 : kBK);
-    g.split = p.split;
-    g.fp8 = p.fp8;
-    g.ascale = p.ascale;
-    g.bscale = p.bscale;
-    g.status = a.status;
-    if (gemm0) cudaEventRecord(gemm0, st);
-    k_rot_tc<<<p.n_tiles, 128, smem_g, st>>>(p.mapA, p.mapB, p.split ? p.mapAlo : p.mapA, p.split ? p.mapBlo : p.mapB,
-                                             g);
+    if (p.simt) {
+        if (gemm0) cudaEventRecord(gemm0, st);
+        e = launch_rot_simt(a.desc, p.tiles, p.n_tiles, p.uscr, a.shift, a.rotT, p.fu, st);
+        if (e != cudaSuccess) return e;
+    } else {
+        const size_t smem_g = tc_gemm_smem(p.split);
+        e = cudaFuncSetAttribute(k_rot_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_g);
+        if (e != cudaSuccess) return e;
+        TcGemmArgs g;
+        g.desc = a.desc;
+        g.tiles = p.tiles;
+        g.brow = p.brow;
+        g.fu = p.fu;
+        g.kt = p.kp / (p.fp8 ? kBK8 : kBK);
+        g.split = p.split;
+        g.fp8 = p.fp8;
+        g.ascale = p.ascale;
+        g.bscale = p.bscale;
+        g.status = a.status;
+        if (gemm0) cudaEventRecord(gemm0, st);
+        k_rot_tc<<<p.n_tiles, 128, smem_g, st>>>(p.mapA, p.mapB, p.split ? p.mapAlo : p.mapA, p.split ? p.mapBlo : p.mapB,
+                                                 g);
+    }
     if (gemm1) cudaEventRecord(gemm1, st);
     e = cudaMemsetAsync(p.tie_count, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;

@@ -1,6 +1,7 @@
 """Large-D executors on the tensor cores (tcgen05 rotation GEMM with the
 objective fused into the epilogue), BF16, bf16x3 and FP8-e4m3, against the
-FP64 oracle.
+FP64 oracle; and the same pipeline in FP32 with the GEMM on the CUDA cores
+(k_rot_simt, for D_pad > 256), whose operands are exact (unit 0).
 
 The trial vectors are built by the same FP32 code as the other paths, so they
 must agree with the oracle to TRIAL_ATOL; the fitness carries the rotation's
@@ -21,10 +22,16 @@ from gpu_util import TRIAL_ATOL, check_fitness, feasible_theta, make_batch, rand
 
 pytestmark = pytest.mark.gpu
 
-TOL = {1: 4e-3, 2: 3e-2, 3: 1e-5}     # relative: 2^-8 (BF16), a few % (e4m3), 1e-5 (bf16x3, as FP32)
-UNIT = {1: 2.0 ** -8, 2: 2.0 ** -3, 3: 2.0 ** -16}
-GAP = {1: 0.1, 2: 0.3, 3: 1e-3}       # relative fitness gap beyond which selection must match FP64
+TOL = {0: 1e-5, 1: 4e-3, 2: 3e-2, 3: 1e-5}     # relative: FP32, 2^-8 (BF16), a few % (e4m3), 1e-5 (bf16x3)
+UNIT = {0: 0.0, 1: 2.0 ** -8, 2: 2.0 ** -3, 3: 2.0 ** -16}
+GAP = {0: 1e-4, 1: 0.1, 2: 0.3, 3: 1e-3}      # relative fitness gap beyond which selection must match FP64
 PRECS = pytest.mark.parametrize("prec", [1, 2, 3], ids=["bf16", "fp8e4m3", "bf16x3"])
+# FP32 runs the same pipeline with the GEMM on the CUDA cores (k_rot_simt) for D_pad > 256
+PIPE = pytest.mark.parametrize("prec", [0, 1, 2, 3], ids=["fp32-simt", "bf16", "fp8e4m3", "bf16x3"])
+
+
+def _on_pipeline(wl, prec):
+    return sum(1 for p in wl.problems if (((p.dim + 3) // 4) * 4 > 256 if prec == 0 else p.dim >= 256))
 
 
 def _wl(seed=41):
@@ -41,13 +48,14 @@ def _wl(seed=41):
     return wl
 
 
-@PRECS
+@PIPE
 def test_tc_one_step_against_oracle(prec):
     import paper_2502_10470_gb300 as M
     wl = _wl()
     b = make_batch(wl, M.METADE_PATH_BATCHED, prec=prec)
     plan = json.loads(M.metade_plan_info(b.ctx))
-    assert plan["tensor_core"]["executors"] == wl.n_inst
+    assert plan["tensor_core"]["executors"] == _on_pipeline(wl, prec)
+    assert plan["tensor_core"]["kernel"] == ("k_rot_simt" if prec == 0 else "k_rot_tc")
     pops, fits = random_state(wl, seed=5, fit_inf=True)
     b.set_population(pops, fits)
     b.set_theta(wl.theta)
@@ -68,7 +76,7 @@ def test_tc_one_step_against_oracle(prec):
     b.close()
 
 
-@PRECS
+@PIPE
 def test_tc_selection_and_generations(prec):
     """Several generations with real stored fitness: the best never rises,
     and a generation's selection matches FP64 wherever the fitness gap
