@@ -796,7 +796,24 @@ def _case_mlp_d1522():
     b.close()
 
 
-PROFILE_CASES = {"tile-d100": _case_tile_d100, "tc-d1000": _case_tc_d1000, "mlp-d1522": _case_mlp_d1522}
+def _case_simt_d1000():
+    """The precision study's 64 x 512 x D1000 state in FP32: initialisation
+    and one generation, two k_rot_simt launches."""
+    import paper_2502_10470_gb300 as M
+    import synth
+    wl = synth.precision()
+    probs = [(p.dim, p.obj, p.shift, p.rot) for p in wl.problems]
+    b = M.Batch(probs, wl.inst_np, wl.inst_prob, seed=0, one_shot=0, prec=M.METADE_FP32)
+    b.set_theta(wl.theta)
+    M.metade_init(b.ctx, b.pop, b.fit, 0)
+    M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 0, 1, None, None)
+    if M.metade_sync(b.ctx) != M.METADE_OK:
+        raise SystemExit("device status not OK")
+    b.close()
+
+
+PROFILE_CASES = {"tile-d100": _case_tile_d100, "tc-d1000": _case_tc_d1000, "mlp-d1522": _case_mlp_d1522,
+                 "simt-d1000": _case_simt_d1000}
 
 
 def main(argv=None):

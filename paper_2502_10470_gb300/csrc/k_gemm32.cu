@@ -4,10 +4,12 @@
 // tensor-core pipeline (prologue, trial, GEMM + objective, selection, ties).
 //
 // One CTA (256 threads) per 64-row tile of an executor.  The CTA walks the
-// columns of Z in chunks of 256; for each chunk it streams K in chunks of 16:
-// (u - o)^T [16][64] (formed from the trial rows) and R^T [16][256] go to
-// shared memory, and every thread accumulates four 4x4 blocks of Z (rows
-// 4 tx.., columns 4 (ty0 + 16 j)..) in registers.  k ascends in every fma
+// columns of Z in chunks of 256; for each chunk it streams K in chunks of 16
+// through two shared-memory buffers: while the current chunk is multiplied,
+// R^T [16][256] of the next one arrives by cp.async and its (u - o)^T
+// [16][64] values (formed from the trial rows) wait in registers.  Every
+// thread accumulates four 4x4 blocks of Z (rows 4 tx.., columns
+// 4 (ty0 + 16 j)..) in registers.  k ascends in every fma
 // chain, so z is bit-identical to the other FP32 rotations.  The chunk of Z
 // then goes to shared memory and four lanes per row push it, in column order,
 // into the objective's running state (group_obj_push), which carries across
@@ -25,6 +27,15 @@ constexpr int kSK = 16;         // K per stage
 constexpr int kSAP = kSM + 4;   // row length of the (u - o)^T stage
 constexpr int kSZP = kSN + 4;   // row length of the Z chunk
 
+// 16-byte cp.async; src_bytes 0 fills the destination with zeros
+__device__ __forceinline__ void cpa16(float* dst, const float* src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cpa_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 template <int OBJ>
 __device__ __forceinline__ void push_chunk(GroupObj& g, const float* zr, int col0, int ncol, int s, int dim) {
     for (int r0 = 0; r0 < ncol; r0 += 4) group_obj_push<4, OBJ>(OBJ, g, zr[r0 + s], col0 + r0, s, dim);
@@ -35,9 +46,9 @@ __global__ void __launch_bounds__(256, 2) k_rot_simt(const InstDesc* __restrict_
                                                      const float* __restrict__ rows, const float* __restrict__ shift,
                                                      const float* __restrict__ rotT, float* f_out) {
     extern __shared__ __align__(16) float sm[];
-    float* As = sm;                    // [kSK][kSAP]
-    float* Bs = As + kSK * kSAP;       // [kSK][kSN]
-    float* Zs = Bs + kSK * kSN;        // [kSM][kSZP]
+    float* As = sm;                        // 2 x [kSK][kSAP]
+    float* Bs = As + 2 * kSK * kSAP;       // 2 x [kSK][kSN]
+    float* Zs = Bs + 2 * kSK * kSN;        // [kSM][kSZP]
     const int tid = threadIdx.x;
     const int k = tiles[2 * blockIdx.x], m0 = tiles[2 * blockIdx.x + 1];
     const InstDesc d = desc[k];
@@ -47,6 +58,31 @@ __global__ void __launch_bounds__(256, 2) k_rot_simt(const InstDesc* __restrict_
     const float* RT = rotT + d.rot_off;
     const int tx = tid & 15, ty0 = tid >> 4;    // GEMM blocks
     const int orow = tid >> 2, os = tid & 3;    // objective: four lanes per row
+    const int nks = (dim + kSK - 1) / kSK;      // K chunks per column chunk
+    // this thread's four (u - o) elements of a K chunk: e = tid + 256 q, row t = e / 16, k = e % 16
+    auto load_a = [&](int k0, float (&v)[4]) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + 256 * q, t = e / kSK, kk = e - t * kSK;
+            v[q] = (t < nv && k0 + kk < dim) ? X[(long long)t * dp + k0 + kk] - o[k0 + kk] : 0.f;
+        }
+    };
+    auto store_a = [&](float* dst, const float (&v)[4]) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + 256 * q, t = e / kSK, kk = e - t * kSK;
+            dst[kk * kSAP + t] = v[q];
+        }
+    };
+    auto issue_b = [&](float* dst, int k0, int col0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + 256 * q, kk = e / (kSN / 4), c4 = e - kk * (kSN / 4), col = col0 + 4 * c4;
+            const bool in = k0 + kk < dim && col < dp;
+            cpa16(dst + kk * kSN + 4 * c4, in ? RT + (long long)(k0 + kk) * dp + col : RT, in ? 16 : 0);
+        }
+        cpa_commit();
+    };
     GroupObj g;
     for (int col0 = 0; col0 < dim; col0 += kSN) {
         float acc[4][4][4];
@@ -56,27 +92,30 @@ __global__ void __launch_bounds__(256, 2) k_rot_simt(const InstDesc* __restrict_
             for (int p = 0; p < 4; ++p)
 #pragma unroll
                 for (int q = 0; q < 4; ++q) acc[j][p][q] = 0.f;
-        for (int k0 = 0; k0 < dim; k0 += kSK) {
-            const int kn = min(kSK, dim - k0);
-            for (int e = tid; e < kSK * kSM; e += blockDim.x) {  // consecutive threads read along a row
-                const int t = e / kSK, kk = e - t * kSK;
-                float v = 0.f;
-                if (t < nv && kk < kn) v = X[(long long)t * dp + k0 + kk] - o[k0 + kk];
-                As[kk * kSAP + t] = v;
-            }
-            for (int e = tid; e < kSK * kSN / 4; e += blockDim.x) {
-                const int kk = e / (kSN / 4), q = e - kk * (kSN / 4), col = col0 + 4 * q;
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (kk < kn && col < dp) v = *reinterpret_cast<const float4*>(RT + (long long)(k0 + kk) * dp + col);
-                *reinterpret_cast<float4*>(Bs + kk * kSN + 4 * q) = v;
-            }
+        {
+            float v[4];
+            load_a(0, v);
+            store_a(As, v);
+            issue_b(Bs, 0, col0);
+            cpa_wait_all();
             __syncthreads();
+        }
+        for (int it = 0; it < nks; ++it) {
+            const int cur = it & 1, k0 = it * kSK, kn = min(kSK, dim - k0);
+            const bool more = it + 1 < nks;
+            float nxt[4];
+            if (more) {
+                issue_b(Bs + (cur ^ 1) * kSK * kSN, k0 + kSK, col0);
+                load_a(k0 + kSK, nxt);
+            }
+            const float* Ac = As + cur * kSK * kSAP;
+            const float* Bc = Bs + cur * kSK * kSN;
             for (int kk = 0; kk < kn; ++kk) {
-                const float4 av = *reinterpret_cast<const float4*>(As + kk * kSAP + 4 * tx);
+                const float4 av = *reinterpret_cast<const float4*>(Ac + kk * kSAP + 4 * tx);
                 const float ar[4] = {av.x, av.y, av.z, av.w};
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const float4 rv = *reinterpret_cast<const float4*>(Bs + kk * kSN + 4 * (ty0 + 16 * j));
+                    const float4 rv = *reinterpret_cast<const float4*>(Bc + kk * kSN + 4 * (ty0 + 16 * j));
                     const float rr[4] = {rv.x, rv.y, rv.z, rv.w};
 #pragma unroll
                     for (int p = 0; p < 4; ++p)
@@ -84,7 +123,11 @@ __global__ void __launch_bounds__(256, 2) k_rot_simt(const InstDesc* __restrict_
                         for (int q = 0; q < 4; ++q) acc[j][p][q] = fmaf(rr[q], ar[p], acc[j][p][q]);
                 }
             }
-            __syncthreads();
+            if (more) {
+                store_a(As + (cur ^ 1) * kSK * kSAP, nxt);
+                cpa_wait_all();
+            }
+            __syncthreads();  // the next chunk is in place; this one is free for the chunk after
         }
 #pragma unroll
         for (int j = 0; j < 4; ++j)
@@ -109,7 +152,7 @@ __global__ void __launch_bounds__(256, 2) k_rot_simt(const InstDesc* __restrict_
     if (os == 0 && orow < nv) f_out[d.fit_off + m0 + orow] = nan_to_inf(f);
 }
 
-size_t rot_simt_smem() { return (size_t)(kSK * kSAP + kSK * kSN + kSM * kSZP) * sizeof(float); }
+size_t rot_simt_smem() { return (size_t)(2 * kSK * kSAP + 2 * kSK * kSN + kSM * kSZP) * sizeof(float); }
 
 cudaError_t launch_rot_simt(const InstDesc* desc, const int* tiles, int n_tiles, const float* rows, const float* shift,
                             const float* rotT, float* f_out, cudaStream_t st) {
