@@ -290,6 +290,51 @@ __device__ __forceinline__ void mlp_forward(int h, const float* th, const T (&x)
     }
 }
 
+// The same forward pass for two inputs at once: every weight load feeds both
+// (each input's arithmetic is exactly that of mlp_forward).  FP32 only.
+__device__ __forceinline__ void mlp_forward2(int h, const float* th, const float (&xa)[kMlpIn],
+                                             const float (&xb)[kMlpIn], float (&ya)[kMlpOut],
+                                             float (&yb)[kMlpOut]) {
+    if ((h & 3) != 0) {
+        mlp_forward<float>(h, th, xa, ya);
+        mlp_forward<float>(h, th, xb, yb);
+        return;
+    }
+    const float* W1 = th;
+    const float* b1 = th + kMlpIn * h;
+    const float* W2 = b1 + h;
+    const float* b2 = W2 + kMlpOut * h;
+    ya[0] = yb[0] = b2[0];
+    ya[1] = yb[1] = b2[1];
+    for (int j = 0; j < h; j += 4) {
+        const float4 bb = *reinterpret_cast<const float4*>(b1 + j);
+        float a[4] = {bb.x, bb.y, bb.z, bb.w}, c[4] = {bb.x, bb.y, bb.z, bb.w};
+#pragma unroll
+        for (int k = 0; k < kMlpIn; ++k) {
+            const float4 w = *reinterpret_cast<const float4*>(W1 + k * h + j);
+            a[0] = fmaf(xa[k], w.x, a[0]);
+            a[1] = fmaf(xa[k], w.y, a[1]);
+            a[2] = fmaf(xa[k], w.z, a[2]);
+            a[3] = fmaf(xa[k], w.w, a[3]);
+            c[0] = fmaf(xb[k], w.x, c[0]);
+            c[1] = fmaf(xb[k], w.y, c[1]);
+            c[2] = fmaf(xb[k], w.z, c[2]);
+            c[3] = fmaf(xb[k], w.w, c[3]);
+        }
+        const float4 w2a = *reinterpret_cast<const float4*>(W2 + 2 * j);
+        const float4 w2b = *reinterpret_cast<const float4*>(W2 + 2 * j + 4);
+        const float v2[8] = {w2a.x, w2a.y, w2a.z, w2a.w, w2b.x, w2b.y, w2b.z, w2b.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float ta = tanhf(a[q]), tb = tanhf(c[q]);
+            ya[0] = fmaf(ta, v2[2 * q], ya[0]);
+            ya[1] = fmaf(ta, v2[2 * q + 1], ya[1]);
+            yb[0] = fmaf(tb, v2[2 * q], yb[0]);
+            yb[1] = fmaf(tb, v2[2 * q + 1], yb[1]);
+        }
+    }
+}
+
 // Streaming accumulator: objectives consume z_0, z_1, ... in order.
 template <typename T>
 struct ObjAcc {

@@ -8,10 +8,11 @@
 // k_mlp_prologue  best and pbest pool per executor (block per executor)
 // k_mlp_trial     trial rows, warp per individual (the PDE step of every
 //                 other kernel), into the scratch population
-// k_mlp_eval      f of every trial (and of the initial population), CTA per
-//                 individual: thread n runs input n
-//                 (the parameters in shared memory, read as broadcasts; the
-//                 input row in registers), then a block sum
+// k_mlp_eval      f of every trial (and of the initial population), CTA of
+//                 128 threads per individual: thread n runs inputs n and
+//                 n + 128 together, so every weight load (a shared-memory
+//                 broadcast) feeds both; the input rows are in registers;
+//                 then a block sum
 // k_mlp_select    greedy selection on the FP32 values, warp per individual
 //
 // Executor k's individuals are rows InstDesc.tc_row .. tc_row + NP - 1 of the
@@ -71,31 +72,36 @@ __global__ void __launch_bounds__(256) k_mlp_trial(StepArgs a, const int* __rest
                uscr + d.pop_off + (long long)i * d.dpad, smt + (size_t)warp * ws);
 }
 
-__global__ void __launch_bounds__(256) k_mlp_eval(const InstDesc* __restrict__ desc, const int* __restrict__ row_exec,
-                                                  const float* __restrict__ uscr, const float* __restrict__ mlp_x,
-                                                  const float* __restrict__ mlp_y, float* fu) {
+__global__ void __launch_bounds__(kMlpN / 2) k_mlp_eval(const InstDesc* __restrict__ desc,
+                                                       const int* __restrict__ row_exec,
+                                                       const float* __restrict__ uscr, const float* __restrict__ mlp_x,
+                                                       const float* __restrict__ mlp_y, float* fu) {
     extern __shared__ __align__(16) float th[];  // parameters of this row's trial
-    __shared__ float part[kMlpN / 32];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;  // thread tid runs input tid
+    __shared__ float part[kMlpN / 64];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;  // thread tid runs inputs tid, tid + 128
+    const int nb = tid + kMlpN / 2;
     const int r = blockIdx.x;
     const InstDesc d = desc[row_exec[r]];
     const int i = r - d.tc_row, h = mlp_hidden(d.dim);
     const float* u = uscr + d.pop_off + (long long)i * d.dpad;
     for (int e = tid; e < d.dim; e += blockDim.x) th[e] = u[e];
-    float x[kMlpIn];
+    float xa[kMlpIn], xb[kMlpIn];
 #pragma unroll
-    for (int q = 0; q < kMlpIn; ++q) x[q] = mlp_x[tid * kMlpIn + q];
-    const float y0 = mlp_y[d.aux + 2 * tid], y1 = mlp_y[d.aux + 2 * tid + 1];
+    for (int q = 0; q < kMlpIn; ++q) {
+        xa[q] = mlp_x[tid * kMlpIn + q];
+        xb[q] = mlp_x[nb * kMlpIn + q];
+    }
     __syncthreads();
-    float y[kMlpOut];
-    mlp_forward<float>(h, th, x, y);
-    const float e0 = y[0] - y0, e1 = y[1] - y1;
-    const float s = warp_sum(fmaf(e0, e0, e1 * e1));
+    float ya[kMlpOut], yb[kMlpOut];
+    mlp_forward2(h, th, xa, xb, ya, yb);
+    const float ea0 = ya[0] - mlp_y[d.aux + 2 * tid], ea1 = ya[1] - mlp_y[d.aux + 2 * tid + 1];
+    const float eb0 = yb[0] - mlp_y[d.aux + 2 * nb], eb1 = yb[1] - mlp_y[d.aux + 2 * nb + 1];
+    const float s = warp_sum(fmaf(ea0, ea0, ea1 * ea1) + fmaf(eb0, eb0, eb1 * eb1));
     if (lane == 0) part[warp] = s;
     __syncthreads();
     if (tid == 0) {
         float t = 0.0f;
-        for (int q = 0; q < kMlpN / 32; ++q) t += part[q];
+        for (int q = 0; q < kMlpN / 64; ++q) t += part[q];
         fu[d.fit_off + i] = nan_to_inf(t * (1.0f / (kMlpN * kMlpOut)));
     }
 }
@@ -130,7 +136,7 @@ cudaError_t launch_mlp_generation(const StepArgs& a, const MlpPlan& p, cudaStrea
     const size_t smem_e = (size_t)p.max_dpad * sizeof(float);
     e = cudaFuncSetAttribute(k_mlp_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_e);
     if (e != cudaSuccess) return e;
-    k_mlp_eval<<<p.n_rows, kMlpN, smem_e, st>>>(a.desc, p.row_exec, p.uscr, p.x, p.y, p.fu);
+    k_mlp_eval<<<p.n_rows, kMlpN / 2, smem_e, st>>>(a.desc, p.row_exec, p.uscr, p.x, p.y, p.fu);
     k_mlp_select<<<blocks, 256, 0, st>>>(a, p.row_exec, p.n_rows, p.uscr, p.fu);
     return cudaGetLastError();
 }
@@ -140,7 +146,7 @@ cudaError_t launch_mlp_eval(const InstDesc* desc, const MlpPlan& p, const float*
     const size_t smem_e = (size_t)p.max_dpad * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k_mlp_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_e);
     if (e != cudaSuccess) return e;
-    k_mlp_eval<<<p.n_rows, kMlpN, smem_e, st>>>(desc, p.row_exec, rows, p.x, p.y, f_out);
+    k_mlp_eval<<<p.n_rows, kMlpN / 2, smem_e, st>>>(desc, p.row_exec, rows, p.x, p.y, f_out);
     return cudaGetLastError();
 }
 
