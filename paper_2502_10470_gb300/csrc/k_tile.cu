@@ -236,9 +236,14 @@ __global__ void __launch_bounds__(256, 2) k_fused_tile(StepArgs a, const int* __
                     }
                 }
                 __syncthreads();
-                // trial, phase 2: (chunk, individual) items, individuals fastest
-                for (int e = tid; e < nbr * kT; e += nt) {
-                    const int q = e / kT, t = e - q * kT, j4 = 4 * q;
+                // trial, phase 2: (chunk, individual) items; a warp takes 8
+                // individuals x 4 consecutive chunks, so four lanes read 64
+                // contiguous bytes of each parent row (two full sectors)
+                const int nqb = (nbr + 3) >> 2;
+                for (int e = tid; e < nqb * 4 * kT; e += nt) {
+                    const int blk = e >> 5, ln = e & 31;
+                    const int t = (blk & 7) * 8 + (ln >> 2), q = (blk >> 3) * 4 + (ln & 3), j4 = 4 * q;
+                    if (q >= nbr) continue;
                     float* col = dT + (size_t)j4 * kTP + t;
                     if (t >= nv) {
                         col[0] = 0.f; col[kTP] = 0.f; col[2 * kTP] = 0.f; col[3 * kTP] = 0.f;
@@ -342,8 +347,11 @@ __global__ void __launch_bounds__(256, 2) k_fused_tile(StepArgs a, const int* __
                 const int nb = min(kT / 2, nti - b0);
                 if (tid < kT / 2) idf[tid] = 0;
                 __syncthreads();
-                for (int e = tid; e < nbr * kT; e += nt) {
-                    const int q = e / kT, c = e - q * kT, tt = c >> 1, j4 = 4 * q;
+                const int nqb = (nbr + 3) >> 2;  // a warp: 8 columns x 4 consecutive chunks (as in the trial)
+                for (int e = tid; e < nqb * 4 * kT; e += nt) {
+                    const int blk = e >> 5, ln = e & 31;
+                    const int c = (blk & 7) * 8 + (ln >> 2), q = (blk >> 3) * 4 + (ln & 3), tt = c >> 1, j4 = 4 * q;
+                    if (q >= nbr) continue;
                     float v4[4] = {0.f, 0.f, 0.f, 0.f};
                     if (tt < nb) {
                         const int i = tl[b0 + tt];
