@@ -6,7 +6,7 @@ six MetaDE runs, one per synthetic shifted-rotated objective (sphere,
 Rosenbrock, Rastrigin, Griewank, Ackley, Schwefel 1.2), D = 20; each run's
 evolver has 100 vectors and each vector drives one executor of population
 100 for 500 generations.  One step = one evolver generation of all six runs
-(Alg. 3 lines 5-12): rand/1/bin trials and decoding, executor
+(Alg. 3): rand/1/bin trials and decoding, executor
 initialisation, 500 executor generations of 600 executors, best-fitness
 reduction, evolver selection = 3.0e7 individual-generations.
 

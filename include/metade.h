@@ -141,7 +141,7 @@ METADE_API metade_status metade_offsets(const metade_ctx *ctx, int64_t *pop_off,
 /* Change the stream later calls are issued on. */
 METADE_API metade_status metade_set_stream(metade_ctx *ctx, void *stream);
 
-/* Alg. 2 lines 1-2: fill every executor's population uniformly in the box
+/* Alg. 2, initialisation: fill every executor's population uniformly in the box
  * (x = lo + (hi - lo) U, rounded once to float32) and evaluate it (NaN
  * fitness stored as +inf): in FP32, except executors on the tensor-core path
  * (cfg.prec BF16 / BF16X3 / FP8E4M3, D >= 256), which are evaluated by the
@@ -152,7 +152,7 @@ METADE_API metade_status metade_set_stream(metade_ctx *ctx, void *stream);
  * a theta starts from the same population. */
 METADE_API metade_status metade_init(metade_ctx *ctx, float *pop, float *fit, uint32_t epoch);
 
-/* Alg. 2 lines 7-10, `n_gens` times, generations gen0 .. gen0 + n_gens - 1,
+/* Alg. 2's generation loop, `n_gens` times, generations gen0 .. gen0 + n_gens - 1,
  * for every executor: rand/best/pbest/current base vectors and dn difference
  * vectors of distinct random individuals (Eq. of Sec. III-A-2), binomial /
  * exponential / arithmetic crossover (Sec. II-A), clip to the box, FP32
@@ -188,19 +188,19 @@ METADE_API metade_status metade_eval(metade_ctx *ctx, const float *pop, metade_p
  * v <- w v + c1 r1 (pbest - x) + c2 r2 (gbest - x), x <- clip(x + v), gbest the
  * run's best personal best (ties to the lower index).  Phase 1 is Alg. 3's
  * selection applied to the positions.  ofit is read by phase 0. */
-/* Alg. 3 lines 1-2: uniform in [lb, ub] = [(0,0,1,1,1,1), (1,1,5,5,5,4)], y = +inf. */
+/* Alg. 3, initialisation: uniform in [lb, ub] = [(0,0,1,1,1,1), (1,1,5,5,5,4)], y = +inf. */
 METADE_API metade_status metade_outer_init(metade_ctx *ctx, float *opop, float *ofit);
 
-/* phase 0 (Alg. 3 lines 5-6): rand/1/bin trials (F = 0.5, CR = 0.9) clipped to
+/* phase 0 (Alg. 3, trials and decoding): rand/1/bin trials (F = 0.5, CR = 0.9) clipped to
  *   [lb, ub] into trial[n_groups][n_out][6], decoded (F = u1, CR = u2, the
  *   rest floor(u) clamped to their domain) into theta[n_inst][6].
- * phase 1 (Alg. 3 line 12): where meta_fit[k] <= ofit[k] (NaN as +inf) the
+ * phase 1 (Alg. 3, selection): where meta_fit[k] <= ofit[k] (NaN as +inf) the
  *   trial replaces the parent and ofit[k] = meta_fit[k]. */
 METADE_API metade_status metade_outer_step(metade_ctx *ctx, float *opop, float *ofit, float *trial,
                                 float *theta, const float *meta_fit, uint32_t outer_gen,
                                 int32_t phase);
 
-/* One whole evolver generation (Alg. 3 lines 5-12): phase 0, executor
+/* One whole evolver generation (Alg. 3): phase 0, executor
  * initialisation (epoch 0 under one-shot evaluation, else outer_gen),
  * n_inner_gens executor generations, the best-fitness reduction into
  * best_f/best_i, phase 1.  With use_graph != 0 the sequence is captured

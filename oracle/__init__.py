@@ -7,10 +7,10 @@ arithmetic: the functions below marshal numpy arrays and loop over
 instances.  It imports nothing from the CUDA package.
 
 What each function follows in the paper:
-  pde_step      one generation of PDE, Alg. 2 lines 7-10 (mutation Eq. of
+  pde_step      one generation of PDE, Alg. 2 (mutation Eq. of
                 Sec. III-A-2, crossovers of Sec. II-A, greedy selection)
   pde_run       a whole PDE run, Alg. 2
-  init_pop      Alg. 2 lines 1-2 (uniform in the box, evaluate)
+  init_pop      Alg. 2, initialisation (uniform in the box, evaluate)
   eval          the synthetic shifted-rotated objectives, z = R (x - o)
   outer_*       the evolver of Alg. 3 (rand/1/bin, F = 0.5, CR = 0.9,
                 y initialised to +inf, floor decoding, selection)

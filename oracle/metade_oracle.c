@@ -267,7 +267,7 @@ static double or_fitness(int obj, int dim, const double *x, const double *o, con
 
 /* ------------------------------------------------------- initialisation */
 
-/* Alg. 2 line 1 (Alg. 1 line 1): uniform in the box. */
+/* Alg. 2 and Alg. 1, initialisation: uniform in the box. */
 void or_init_pop(int np, int dim, uint64_t seed, uint32_t stream, uint32_t epoch,
                  double lo, double hi, double *pop)
 {
@@ -278,7 +278,7 @@ void or_init_pop(int np, int dim, uint64_t seed, uint32_t stream, uint32_t epoch
         }
 }
 
-/* Alg. 2 line 2 */
+/* Alg. 2, evaluation of the initial population */
 void or_eval_pop(int np, int dim, int obj, const double *o, const double *R,
                  const double *pop, double *fit)
 {
@@ -316,7 +316,7 @@ int or_required_np(int bl, int br, int dn)
 }
 
 /*
- * One generation of PDE (Alg. 2 lines 7-10) on one instance, in place.
+ * One generation of PDE (Alg. 2) on one instance, in place.
  *
  * pop [np*dim], fit [np]: the generation-start state (in), the next state (out).
  * theta = (F, CR, bl, br, dn, cs), categorical entries integral.
@@ -434,7 +434,7 @@ int or_pde_step(int np, int dim, int obj, const double *o, const double *R,
         }
     }
 
-    /* Alg. 2 line 10: greedy selection, all trials against the start population */
+    /* Alg. 2, selection: greedy selection, all trials against the start population */
     for (int i = 0; i < np; i++) {
         int acc = fU[i] <= fit[i];
         if (accept) accept[i] = acc;
@@ -479,7 +479,7 @@ double or_pde_run(int np, int dim, int obj, const double *o, const double *R,
 static const double OR_LB[6] = {0.0, 0.0, 1.0, 1.0, 1.0, 1.0};
 static const double OR_UB[6] = {1.0, 1.0, 5.0, 5.0, 5.0, 4.0};
 
-/* Alg. 3 lines 1-2: evolver population uniform in [lb, ub], fitness +inf. */
+/* Alg. 3, initialisation: evolver population uniform in [lb, ub], fitness +inf. */
 void or_outer_init(int n_out, uint64_t seed, uint32_t group, double *pop, double *fit)
 {
     for (int i = 0; i < n_out; i++) {
@@ -491,7 +491,7 @@ void or_outer_init(int n_out, uint64_t seed, uint32_t group, double *pop, double
     }
 }
 
-/* Alg. 3 line 5: rand/1/bin trials with F = 0.5, CR = 0.9 (Sec. IV-A),
+/* Alg. 3, trial generation: rand/1/bin trials with F = 0.5, CR = 0.9 (Sec. IV-A),
  * clipped to [lb, ub].  Returns -1 when n_out < 4. */
 int or_outer_trial(int n_out, uint64_t seed, uint32_t group, uint32_t gen,
                    const double *pop, double *trial)
@@ -519,7 +519,7 @@ int or_outer_trial(int n_out, uint64_t seed, uint32_t group, uint32_t gen,
     return 0;
 }
 
-/* Alg. 3 line 6: F = u1, CR = u2, bl/br/dn/cs = floor of u3..u6, clamped to
+/* Alg. 3, decoding: F = u1, CR = u2, bl/br/dn/cs = floor of u3..u6, clamped to
  * their domains so that the upper bound decodes to the top category. */
 void or_decode(const double *u, double *theta)
 {
@@ -534,7 +534,7 @@ void or_decode(const double *u, double *theta)
     }
 }
 
-/* Alg. 3 line 12: a trial replaces its parent when its meta-fitness is <=. */
+/* Alg. 3, selection: a trial replaces its parent when its meta-fitness is <=. */
 void or_outer_select(int n_out, double *pop, double *fit, const double *trial,
                      const double *meta_fit, int32_t *accept)
 {

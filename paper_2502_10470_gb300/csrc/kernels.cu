@@ -1,7 +1,7 @@
 // kernels.cu -- CUDA kernels of the MetaDE hot path (sm_103a).
 //
 //  k_pad_problems   problem table: R rows padded to Dpad, R^T, padded o
-//  k_init           Alg. 2 lines 1: population uniform in the box
+//  k_init           Alg. 2 initialisation: population uniform in the box
 //  k_eval           shifted-rotated objective of every row, FP32 or FP64
 //  k_record         the draw record of one generation (parity checks)
 //  k_best           y* = min fitness per executor (Sec. III-B)

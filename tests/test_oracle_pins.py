@@ -105,7 +105,7 @@ def _word_for(s, P):
 
 @pytest.mark.parametrize("i", range(4))
 def test_distinct_draws_bruteforce_np4(i):
-    """Alg. 1 line 6 (r1 != r2 != r3 != i): at NP = 4 the 3*2*1 draw values map
+    """Alg. 1, mutation (r1 != r2 != r3 != i): at NP = 4 the 3*2*1 draw values map
     one-to-one onto the 6 ordered triples of {0..3} \\ {i}."""
     seen = set()
     for s0 in range(3):
@@ -435,7 +435,7 @@ def test_pbest_drawn_from_top_ten_percent():
 
 # --------------------------------------------------------------- selection
 def test_tie_accepts_trial():
-    """Alg. 1 line 10: f(u) <= f(x) accepts; with F = 0 and bl = br = current
+    """Alg. 1, selection: f(u) <= f(x) accepts; with F = 0 and bl = br = current
     the trial is the target itself, so every individual ties and accepts."""
     rng = np.random.default_rng(14)
     pop = rng.uniform(-100, 100, (10, 6))
@@ -483,7 +483,7 @@ def test_rand1bin_converges_on_sphere():
 
 # ----------------------------------------------------------------- evolver
 def test_decode_table1_and_bounds():
-    """Alg. 3 line 6: floor decoding; each Table I row decodes from any point of
+    """Alg. 3, decoding: floor decoding; each Table I row decodes from any point of
     its unit cell, and the upper bound decodes to the top category."""
     for name, bl, br, dn, cs in table1():
         for frac in (0.0, 0.5, 0.999):
