@@ -146,8 +146,34 @@ StepArgs step_args(metade_ctx* c, float* pop, float* fit, const float* theta, ui
 
 double work_cost(const InstDesc& d) { return (double)d.np * ((double)d.dim * d.dim + 16.0 * d.dim + 64.0); }
 
+static int device_sms() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+// Order of a small-D bucket: when the bucket has more executors than the GPU
+// has SMs, the executors that share an SM (one wave: blocks w, w + n_SM,
+// w + 2 n_SM, ... land on one SM, as measured on GB300 with %smid) are made
+// to share an objective, so the resident CTAs of an SM run the same branch of
+// the objective code and compete less for instruction cache.  Any order is
+// correct (each executor's result depends only on its own state and draws);
+// this one is faster (8.85 -> 8.67 ms per 500 generations of the 600-executor
+// D = 20 workload).
+static void cohere_by_objective(const metade_ctx* c, std::vector<int>& v) {
+    const int n = (int)v.size(), nsm = device_sms();
+    if (nsm <= 0 || n <= nsm) return;
+    std::vector<int> L = v;
+    std::stable_sort(L.begin(), L.end(), [&](int x, int y) { return c->hdesc[x].obj < c->hdesc[y].obj; });
+    int j = 0;
+    for (int sm = 0; sm < nsm; ++sm)
+        for (int w = sm; w < n; w += nsm) v[w] = L[j++];
+}
+
 // Kernel kind per executor and the work order inside each bucket (largest
-// first, so the block scheduler hands the longest executors out first).
+// first, so the block scheduler hands the longest executors out first; small-D
+// buckets then grouped by objective per SM).
 metade_status build_plan(metade_ctx* c) {
     std::vector<std::vector<int>> small(33);
     std::vector<int> general, tile, tile_stream;
@@ -173,6 +199,7 @@ metade_status build_plan(metade_ctx* c) {
     for (int dm = 1; dm <= 32; ++dm) {
         if (small[dm].empty()) continue;
         sort_desc(small[dm]);
+        cohere_by_objective(c, small[dm]);
         int mnp = 0;
         for (int k : small[dm]) mnp = std::max(mnp, c->hdesc[k].np);
         Bucket b;
@@ -691,12 +718,7 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
         t.simt = simt ? 1 : 0;
         t.tie_list = c->tc_ties + 1;
         t.tie_count = c->tc_ties;
-        {
-            int dev = 0, sms = 0;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            t.tie_ctas = std::max(1, sms) * 2;
-        }
+        t.tie_ctas = std::max(1, device_sms()) * 2;
         t.kp = tc_kp;
         t.split = split ? 1 : 0;
         t.max_dpad = tc_max_dpad;

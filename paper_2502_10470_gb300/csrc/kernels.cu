@@ -8,7 +8,8 @@
 //  k_plain_*        plain path: one executor, one generation, three launches
 //  k_fused_small    batched path, D <= 32: one CTA per executor, one thread per
 //                   individual, population/trials/R resident in shared memory
-//                   for all fused generations
+//                   for all fused generations; the pbest pool is re-ranked
+//                   each generation among the old pool and the improved
 //  k_fused_general  batched path, any D: one CTA per executor, one warp per
 //                   individual, population in global memory (L2-resident),
 //                   R^T staged in shared memory when it fits
@@ -448,6 +449,12 @@ __device__ __forceinline__ void small_executor(const StepArgs& a, int k, const I
     float* fu = f + np;
     int* topk = reinterpret_cast<int*>(fu + np);
     int* red = topk + np;
+    // pbest pool bookkeeping: the candidates for the next generation's pool
+    // (listed by the selection), their fitness, pool membership, the count
+    int* cand = red + 64;
+    float* candf = reinterpret_cast<float*>(cand + np);
+    int* inpool = reinterpret_cast<int*>(candf + np);
+    int* ncand = inpool + np;
     const uint32_t epoch = a.epoch_dev ? *a.epoch_dev : a.epoch;
     float* gpop = a.pop + d.pop_off;
     const int chunks = dp >> 2;
@@ -465,15 +472,40 @@ __device__ __forceinline__ void small_executor(const StepArgs& a, int k, const I
         o[j] = j < dp ? a.shift[d.shift_off + j] : 0.0f;
         isq[j] = 1.0f / sqrtf((float)(j + 1));
     }
-    for (int i = tid; i < np; i += nt) f[i] = a.fit[d.fit_off + i];
+    for (int i = tid; i < np; i += nt) {
+        f[i] = a.fit[d.fit_off + i];
+        inpool[i] = 0;
+    }
+    if (tid == 0) *ncand = 0;
     __syncthreads();
     const bool pb = s.uses_pbest();
     for (int g = 0; g < a.n_gens; ++g) {
         const uint32_t gen = a.gen0 + (uint32_t)g;
         int best;
         if (pb) {
-            block_topk(f, np, d.kp, topk);
-            __syncthreads();
+            if (g == 0) {
+                block_topk(f, np, d.kp, topk);
+                __syncthreads();
+                for (int t = tid; t < d.kp; t += nt) inpool[topk[t]] = 1;
+            } else {
+                // Stored fitness never rises (greedy selection), so an individual
+                // outside the old pool whose fitness did not fall still has k_p
+                // better ones: the new pool lies within the old pool and the
+                // individuals whose fitness fell.  Everyone better than a pool
+                // member is in the pool, so its rank among these candidates is
+                // its exact rank by (f, index); a non-member ranks >= k_p there.
+                const int m = *ncand;
+                for (int t = tid; t < m; t += nt) {
+                    const int ci = cand[t];
+                    const float fc = candf[t];
+                    int rank = 0;
+                    for (int j = 0; j < m; ++j) rank += better(candf[j], cand[j], fc, ci) ? 1 : 0;
+                    inpool[ci] = rank < d.kp;
+                    if (rank < d.kp) topk[rank] = ci;
+                }
+                __syncthreads();
+                if (tid == 0) *ncand = 0;
+            }
             best = topk[0];
         } else {
             best = block_argmin(f, np, red);
@@ -545,6 +577,11 @@ __device__ __forceinline__ void small_executor(const StepArgs& a, int k, const I
             } else {
                 take = fn <= fx;
             }
+            if (pb && (inpool[i] || (take && fn < fx))) {  // candidate for the next pool
+                const int slot = atomicAdd(ncand, 1);
+                cand[slot] = i;
+                candf[slot] = take ? fn : fx;
+            }
             if (take) {
                 for (int q = 0; q < chunks; ++q)
                     *reinterpret_cast<float4*>(X + i * ds + 4 * q) =
@@ -595,7 +632,7 @@ int small_dmax_for(int dim) {
 size_t fused_smem_small(int dmax, int max_np) {
     const int ds = small_stride(dmax);
     return sizeof(float) * ((size_t)2 * max_np * ds + (size_t)dmax * dmax + 2 * dmax + 2 * (size_t)max_np) +
-           sizeof(int) * ((size_t)max_np + 64);
+           sizeof(int) * ((size_t)4 * max_np + 64 + 1);
 }
 
 // ---------------------------------------------- batched path, general D

@@ -239,6 +239,52 @@ def test_fused_generations_equal_single_steps():
 
 
 # ------------------------------------------------------------------ evolver
+def test_fused_pbest_pool_with_equal_fitness():
+    """Inside one fused launch the small-D kernel re-ranks the pbest pool
+    among the previous pool and the individuals whose fitness fell; a launch
+    of one generation ranks every individual.  With pairs of identical rows
+    (equal fitness, so the index decides the order) and a 30% pool, eight
+    fused generations equal eight single-generation launches bit for bit."""
+    import paper_2502_10470_gb300 as M
+    rng = np.random.default_rng(33)
+    n = 24
+    dims = rng.choice([2, 5, 10, 20, 31], size=n)
+    nps = rng.choice([8, 17, 40, 100, 130], size=n)
+    probs = [synth.make_problem(rng, int(d), int(k % 6)) for k, d in enumerate(dims)]
+    th = synth.random_theta(rng, n)
+    for k in range(n):
+        th[k, 2] = 3 if k % 2 == 0 else 1 + (k // 2) % 4   # pbest base or pbest right vector
+        th[k, 3] = 3 if k % 2 == 1 else 1 + (k // 2) % 4
+        th[k, 5] = 1 + (k % 3)
+    wl = synth.Workload(name="pbest-equal", problems=probs, inst_np=nps.astype(np.int32),
+                        inst_prob=np.arange(n, dtype=np.int32), inst_group=np.arange(n, dtype=np.int32),
+                        n_groups=n, n_out=0, inner_gens=8, outer_gens=1, seed=7, one_shot=0, theta=th,
+                        p_best_pct=30)
+    wl.theta = feasible_theta(wl.theta, wl.inst_np)
+    pops, fits = random_state(wl, seed=4)
+    for k in range(n):
+        pops[k][1::2] = pops[k][0:pops[k].shape[0] - 1:2][: pops[k][1::2].shape[0]]
+        fits[k][1::2] = fits[k][0:fits[k].shape[0] - 1:2][: fits[k][1::2].shape[0]]
+    outs = []
+    for split in (False, True):
+        b = make_batch(wl, 0)
+        info = json.loads(M.metade_plan_info(b.ctx))
+        assert all(bk["kernel"] == "fused_small" for bk in info["buckets"])
+        b.set_population(pops, fits)
+        b.set_theta(wl.theta)
+        if split:
+            for g in range(8):
+                M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 20 + g, 1, None, None)
+        else:
+            M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 20, 8, None, None)
+        b.sync()
+        outs.append(b.get_population())
+        b.close()
+    for k in range(n):
+        np.testing.assert_array_equal(outs[0][0][k], outs[1][0][k])
+        np.testing.assert_array_equal(outs[0][1][k], outs[1][1][k])
+
+
 def test_outer_init_trial_decode_select():
     import torch
     import paper_2502_10470_gb300 as M
