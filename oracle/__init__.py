@@ -15,6 +15,10 @@ What each function follows in the paper:
   outer_*       the evolver of Alg. 3 (rand/1/bin, F = 0.5, CR = 0.9,
                 y initialised to +inf, floor decoding, selection)
   metade_run    Alg. 3 end to end with one-shot evaluation (Sec. III-C)
+  pso_move      PSO as the evolver (supplement, comparison of evolvers)
+  cso_*         CSO as the evolver (Cheng and Jin 2015; same supplement)
+  nes_*         xNES as the evolver (Wierstra et al. 2014; same supplement),
+                with expm_sym its matrix exponential (Jacobi eigenvectors)
 """
 from __future__ import annotations
 
@@ -85,6 +89,12 @@ def lib():
         L.or_mlp.restype = C.c_double
         L.or_pso_move.argtypes = [C.c_int, C.c_uint64, C.c_uint32, C.c_uint32, C.c_double, C.c_double,
                                   C.c_double, P, P, P, P]
+        L.or_cso_move.argtypes = [C.c_int, C.c_uint64, C.c_uint32, C.c_uint32, P, P, P, P, P]
+        L.or_cso_select.argtypes = [C.c_int, P, P, P, P, P]
+        L.or_nes_init.argtypes = [P]
+        L.or_nes_sample.argtypes = [C.c_int, C.c_uint64, C.c_uint32, C.c_uint32, P, P, P, P]
+        L.or_nes_update.argtypes = [C.c_int, P, P, P]
+        L.or_expm_sym.argtypes = [C.c_int, P, P]
         L.or_metade_run.restype = C.c_double
         _lib = L
     return _lib
@@ -247,10 +257,64 @@ def pso_move(pbest, pfit, x, v, seed: int, group: int, gen: int, w: float = 0.72
     return x, v
 
 
+def cso_move(pop, fit, v, seed: int, group: int, gen: int):
+    """CSO evolver move: returns (x', v', flag) -- x' the positions to
+    evaluate (losers moved, winners as they were), flag 1 for the particles
+    whose evaluation replaces their position and fitness (gen 0: all)."""
+    pop, fit = _f64(pop), _f64(fit)
+    v = _f64(v).copy()
+    xn = np.zeros_like(pop)
+    flag = np.zeros(pop.shape[0], dtype=np.int32)
+    lib().or_cso_move(pop.shape[0], seed, group, gen, _p(pop), _p(fit), _p(xn), _p(v), _p(flag))
+    return xn, v, flag
+
+
+def cso_select(pop, fit, xn, flag, meta_fit):
+    pop, fit = _f64(pop).copy(), _f64(fit).copy()
+    flag = np.ascontiguousarray(np.asarray(flag, dtype=np.int32))
+    lib().or_cso_select(pop.shape[0], _p(pop), _p(fit), _p(_f64(xn)), _p(flag), _p(_f64(meta_fit)))
+    return pop, fit
+
+
+NES_STATE = 43  # mu[6], sigma, B[6][6] row-major
+
+
+def nes_init() -> np.ndarray:
+    st = np.zeros(NES_STATE)
+    lib().or_nes_init(_p(st))
+    return st
+
+
+def nes_sample(st, n_out: int, seed: int, group: int, gen: int):
+    """xNES samples of one generation: (s, z, clip(z)), each [n_out][6]."""
+    st = _f64(st)
+    s = np.zeros((n_out, 6))
+    z = np.zeros((n_out, 6))
+    zc = np.zeros((n_out, 6))
+    lib().or_nes_sample(n_out, seed, group, gen, _p(st), _p(s), _p(z), _p(zc))
+    return s, z, zc
+
+
+def nes_update(st, s, meta_fit) -> np.ndarray:
+    st = _f64(st).copy()
+    s = _f64(s)
+    lib().or_nes_update(s.shape[0], _p(st), _p(s), _p(_f64(meta_fit)))
+    return st
+
+
+def expm_sym(S) -> np.ndarray:
+    """exp of a symmetric matrix (n <= 8) by Jacobi eigendecomposition."""
+    S = _f64(S)
+    E = np.zeros_like(S)
+    lib().or_expm_sym(S.shape[0], _p(S), _p(E))
+    return E
+
+
 def metade_run(n_out: int, np_: int, obj: int, o, R, inner_gens: int, outer_gens: int, *,
                seed: int, group: int = 0, power_up: bool = False,
                lo: float = -100.0, hi: float = 100.0, p_best_pct: int = 10, evolver: int = 0):
-    """evolver 0: DE/rand/1/bin (Alg. 3); 1: PSO (w = 0.729, c1 = c2 = 1.49)."""
+    """evolver 0: DE/rand/1/bin (Alg. 3); 1: PSO (w = 0.729, c1 = c2 = 1.49);
+    2: CSO; 3: NES (xNES)."""
     o, R = _f64(o), _f64(R)
     opop = np.zeros((n_out, 6))
     ofit = np.zeros(n_out)

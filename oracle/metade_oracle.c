@@ -6,8 +6,8 @@
  * Sec. III-A-2, "DE/bl-to-br/dn"), the three crossover schemes of Sec. II-A
  * (binomial, exponential, arithmetic), greedy selection (Alg. 1/2), the
  * best-fitness reduction that becomes the meta-fitness (Sec. III-B), the
- * evolver's rand/1/bin step with floor decoding (Alg. 3), the PSO evolver of
- * the supplement's comparison of evolvers, and the synthetic shifted-rotated
+ * evolver's rand/1/bin step with floor decoding (Alg. 3), the PSO, CSO and
+ * NES evolvers of the supplement's comparison of evolvers, and the synthetic shifted-rotated
  * objectives used as the CEC2022 stand-in.
  *
  * Only the tests, the smoke check and the benchmark's CPU-baseline leg may
@@ -595,9 +595,252 @@ void or_pso_move(int n_out, uint64_t seed, uint32_t group, uint32_t gen, double 
 }
 
 /*
+ * CSO as the evolver (Competitive Swarm Optimizer, Cheng and Jin, IEEE Trans.
+ * Cybernetics 45(2), 2015; the supplement's comparison of evolvers uses it
+ * without tuning).  Particle i has a position x_i (the evolver population
+ * `pop`, fitness `fit`) and a velocity v_i.  Generation 0 evaluates the
+ * initial swarm: x'_i = x_i, v_i = 0, every particle flagged.  From
+ * generation 1 the swarm is paired at random: pi = a permutation of 0..m-1
+ * by Fisher-Yates (pi = identity; for t = m-1 down to 1, j = int[0, t+1)
+ * from evolver draw slot 3 word 0 of individual t, swap pi[t] and pi[j]);
+ * pair p is (pi[2p], pi[2p+1]) and an odd last particle sits the generation
+ * out.  In a pair the particle of lower fitness (ties to the lower index)
+ * wins and is kept as it is; the loser l learns from the winner w:
+ *   v_l,j <- r1_j v_l,j + r2_j (x_w,j - x_l,j)
+ *   x'_l,j = x_l,j + v_l,j, clipped to [lb_j, ub_j]   (v is kept as computed)
+ * with r1 = words 0..5 and r2 = words 6..11 of individual l (slots 0-2), as
+ * in PSO.  The swarm-mean term of CSO is taken with its factor phi = 0 (the
+ * setting Cheng and Jin give for small swarms; the supplement tunes nothing).
+ * Selection (or_cso_select): a flagged particle (a loser, or any particle at
+ * generation 0) takes x' and its meta-fitness unconditionally; a winner keeps
+ * its position and stored fitness.
+ */
+void or_cso_move(int n_out, uint64_t seed, uint32_t group, uint32_t gen, const double *pop, const double *fit,
+                 double *xn, double *v, int32_t *flag)
+{
+    for (int i = 0; i < n_out * 6; i++) xn[i] = pop[i];
+    if (gen == 0) {
+        for (int i = 0; i < n_out; i++) {
+            flag[i] = 1;
+            for (int j = 0; j < 6; j++) v[i * 6 + j] = 0.0;
+        }
+        return;
+    }
+    int32_t *pi = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n_out > 0 ? n_out : 1));
+    for (int i = 0; i < n_out; i++) {
+        pi[i] = i;
+        flag[i] = 0;
+    }
+    for (int t = n_out - 1; t >= 1; t--) {
+        uint32_t w = or_word(seed, OR_TAG_OUTER, group, gen, (uint32_t)t, 0, 3, 0);
+        int j = (int)or_below(w, (uint32_t)(t + 1));
+        int32_t tmp = pi[t];
+        pi[t] = pi[j];
+        pi[j] = tmp;
+    }
+    for (int q = 0; q + 1 < n_out; q += 2) {
+        int a = pi[q], b = pi[q + 1];
+        int a_wins = fit[a] < fit[b] || (fit[a] == fit[b] && a < b);
+        int w = a_wins ? a : b, l = a_wins ? b : a;
+        flag[l] = 1;
+        for (int j = 0; j < 6; j++) {
+            uint32_t wa = or_word(seed, OR_TAG_OUTER, group, gen, (uint32_t)l, 0, (uint32_t)(j / 4), (uint32_t)(j % 4));
+            uint32_t wb = or_word(seed, OR_TAG_OUTER, group, gen, (uint32_t)l, 0, (uint32_t)((6 + j) / 4),
+                                  (uint32_t)((6 + j) % 4));
+            double r1 = or_uniform(wa), r2 = or_uniform(wb);
+            double vj = r1 * v[l * 6 + j] + r2 * (pop[w * 6 + j] - pop[l * 6 + j]);
+            double x = pop[l * 6 + j] + vj;
+            if (x < OR_LB[j]) x = OR_LB[j];
+            if (x > OR_UB[j]) x = OR_UB[j];
+            v[l * 6 + j] = vj;
+            xn[l * 6 + j] = x;
+        }
+    }
+    free(pi);
+}
+
+void or_cso_select(int n_out, double *pop, double *fit, const double *xn, const int32_t *flag, const double *meta_fit)
+{
+    for (int i = 0; i < n_out; i++) {
+        if (!flag[i]) continue;
+        for (int j = 0; j < 6; j++) pop[i * 6 + j] = xn[i * 6 + j];
+        fit[i] = isnan(meta_fit[i]) ? INFINITY : meta_fit[i];
+    }
+}
+
+/*
+ * NES as the evolver: exponential natural evolution strategies (xNES,
+ * Wierstra, Schaul, Glasmachers, Sun, Peters, Schmidhuber, "Natural
+ * Evolution Strategies", JMLR 15, 2014), whose learning rates have fixed
+ * defaults (the supplement tunes nothing).  The search distribution over
+ * the d = 6 genes is N(mu, sigma^2 B B^T) with det B = 1.  Generation t
+ * draws lambda = n_out samples
+ *   s_k ~ N(0, I): Box-Muller on evolver draw words 2q, 2q+1 (slot = word / 4)
+ *       of individual k: u1 = ((w >> 8) + 1) 2^-24, u2 = (w >> 8) 2^-24,
+ *       s_2q = sqrt(-2 ln u1) cos(2 pi u2), s_2q+1 = sqrt(-2 ln u1) sin(2 pi u2)
+ *   z_k = mu + sigma B s_k, evaluated at clip(z_k, lb, ub) (floor-decoded).
+ * With the samples ranked by meta-fitness (ascending, NaN as +inf, ties to
+ * the lower index) and the utilities of rank r = 0..lambda-1
+ *   u_r = max(0, ln(lambda/2 + 1) - ln(r + 1)) / sum_r' max(0, ...) - 1/lambda,
+ * the natural-gradient step is
+ *   G_delta = sum_k u_k s_k,  G_M = sum_k u_k (s_k s_k^T - I),
+ *   G_sigma = tr(G_M) / d,    G_B = G_M - G_sigma I,
+ *   mu <- mu + eta_mu sigma B G_delta,  sigma <- sigma exp(eta_sigma G_sigma / 2),
+ *   B <- B expm(eta_B G_B / 2),
+ * eta_mu = 1, eta_sigma = eta_B = 3 (3 + ln d) / (5 d sqrt d).  The initial
+ * distribution is centred in the box, mu = (lb + ub) / 2, with
+ * sigma B = diag((ub - lb) / 4): sigma = the geometric mean of (ub - lb) / 4
+ * and B = diag((ub - lb) / 4) / sigma.  The evolver population and fitness
+ * of Alg. 3 hold the latest samples clip(z_k) and their meta-fitness.
+ * expm of the symmetric G_B here goes through a cyclic Jacobi
+ * eigendecomposition, Q diag(exp(lambda_i)) Q^T.
+ * State layout: st[0..5] = mu, st[6] = sigma, st[7..42] = B row-major.
+ */
+static const double OR_NES_D = 6.0;
+
+void or_nes_init(double *st)
+{
+    double lg = 0.0;
+    for (int j = 0; j < 6; j++) lg += log((OR_UB[j] - OR_LB[j]) / 4.0);
+    double sigma = exp(lg / OR_NES_D);
+    for (int j = 0; j < 6; j++) st[j] = 0.5 * (OR_LB[j] + OR_UB[j]);
+    st[6] = sigma;
+    for (int r = 0; r < 6; r++)
+        for (int c = 0; c < 6; c++) st[7 + r * 6 + c] = (r == c) ? ((OR_UB[r] - OR_LB[r]) / 4.0) / sigma : 0.0;
+}
+
+/* Samples of generation `gen`: s [n_out][6], z [n_out][6] (unclipped), zc = clip(z). */
+void or_nes_sample(int n_out, uint64_t seed, uint32_t group, uint32_t gen, const double *st, double *s, double *z,
+                   double *zc)
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int k = 0; k < n_out; k++) {
+        for (int q = 0; q < 3; q++) {
+            uint32_t wa = or_word(seed, OR_TAG_OUTER, group, gen, (uint32_t)k, 0, (uint32_t)((2 * q) / 4),
+                                  (uint32_t)((2 * q) % 4));
+            uint32_t wb = or_word(seed, OR_TAG_OUTER, group, gen, (uint32_t)k, 0, (uint32_t)((2 * q + 1) / 4),
+                                  (uint32_t)((2 * q + 1) % 4));
+            double u1 = (double)((wa >> 8) + 1u) * (1.0 / 16777216.0);
+            double u2 = (double)(wb >> 8) * (1.0 / 16777216.0);
+            double rad = sqrt(-2.0 * log(u1));
+            s[k * 6 + 2 * q] = rad * cos(two_pi * u2);
+            s[k * 6 + 2 * q + 1] = rad * sin(two_pi * u2);
+        }
+        for (int r = 0; r < 6; r++) {
+            double a = 0.0;
+            for (int c = 0; c < 6; c++) a += st[7 + r * 6 + c] * s[k * 6 + c];
+            double x = st[r] + st[6] * a;
+            z[k * 6 + r] = x;
+            if (x < OR_LB[r]) x = OR_LB[r];
+            if (x > OR_UB[r]) x = OR_UB[r];
+            zc[k * 6 + r] = x;
+        }
+    }
+}
+
+/* exp of a symmetric n x n matrix S (row-major) by cyclic Jacobi rotations. */
+void or_expm_sym(int n, const double *S, double *E)
+{
+    double A[64], V[64];
+    for (int i = 0; i < n * n; i++) A[i] = S[i];
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) V[i * n + j] = (i == j) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 100; sweep++) {
+        double off = 0.0;
+        for (int p = 0; p < n; p++)
+            for (int q = p + 1; q < n; q++) off += A[p * n + q] * A[p * n + q];
+        if (off < 1e-300) break;
+        for (int p = 0; p < n; p++) {
+            for (int q = p + 1; q < n; q++) {
+                double apq = A[p * n + q];
+                if (apq == 0.0) continue;
+                /* rotation angle that zeroes A[p][q] (Golub and Van Loan, Sec. 8.5) */
+                double tau = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+                double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                double c = 1.0 / sqrt(1.0 + t * t), sn = t * c;
+                for (int k = 0; k < n; k++) { /* A <- A J */
+                    double akp = A[k * n + p], akq = A[k * n + q];
+                    A[k * n + p] = c * akp - sn * akq;
+                    A[k * n + q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < n; k++) { /* A <- J^T A */
+                    double apk = A[p * n + k], aqk = A[q * n + k];
+                    A[p * n + k] = c * apk - sn * aqk;
+                    A[q * n + k] = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < n; k++) { /* V <- V J */
+                    double vkp = V[k * n + p], vkq = V[k * n + q];
+                    V[k * n + p] = c * vkp - sn * vkq;
+                    V[k * n + q] = sn * vkp + c * vkq;
+                }
+            }
+        }
+    }
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) {
+            double a = 0.0;
+            for (int k = 0; k < n; k++) a += V[i * n + k] * exp(A[k * n + k]) * V[j * n + k];
+            E[i * n + j] = a;
+        }
+}
+
+/* The xNES update from one generation's samples s and meta-fitness y. */
+void or_nes_update(int n_out, double *st, const double *s, const double *meta_fit)
+{
+    const int d = 6, lam = n_out;
+    const double eta_mu = 1.0, eta = 3.0 * (3.0 + log(OR_NES_D)) / (5.0 * OR_NES_D * sqrt(OR_NES_D));
+    double *u = (double *)malloc(sizeof(double) * (size_t)(lam > 0 ? lam : 1));
+    double den = 0.0;
+    for (int r = 0; r < lam; r++) {
+        double a = log(lam / 2.0 + 1.0) - log(r + 1.0);
+        den += a > 0.0 ? a : 0.0;
+    }
+    for (int k = 0; k < lam; k++) {
+        double yk = isnan(meta_fit[k]) ? INFINITY : meta_fit[k];
+        int rank = 0;
+        for (int j = 0; j < lam; j++) {
+            double yj = isnan(meta_fit[j]) ? INFINITY : meta_fit[j];
+            if (yj < yk || (yj == yk && j < k)) rank++;
+        }
+        double a = log(lam / 2.0 + 1.0) - log(rank + 1.0);
+        u[k] = (a > 0.0 ? a : 0.0) / den - 1.0 / lam;
+    }
+    double gd[6] = {0}, gm[36] = {0};
+    for (int k = 0; k < lam; k++) {
+        for (int i = 0; i < d; i++) {
+            gd[i] += u[k] * s[k * 6 + i];
+            for (int j = 0; j < d; j++) gm[i * 6 + j] += u[k] * (s[k * 6 + i] * s[k * 6 + j] - (i == j ? 1.0 : 0.0));
+        }
+    }
+    double gs = 0.0;
+    for (int i = 0; i < d; i++) gs += gm[i * 6 + i];
+    gs /= d;
+    double half[36], E[36], Bn[36];
+    for (int i = 0; i < d; i++)
+        for (int j = 0; j < d; j++) half[i * 6 + j] = 0.5 * eta * (gm[i * 6 + j] - (i == j ? gs : 0.0));
+    or_expm_sym(d, half, E);
+    const double sigma = st[6];
+    for (int i = 0; i < d; i++) {
+        double a = 0.0;
+        for (int j = 0; j < d; j++) a += st[7 + i * 6 + j] * gd[j];
+        st[i] += eta_mu * sigma * a;
+    }
+    st[6] = sigma * exp(0.5 * eta * gs);
+    for (int i = 0; i < d; i++)
+        for (int j = 0; j < d; j++) {
+            double a = 0.0;
+            for (int k = 0; k < d; k++) a += st[7 + i * 6 + k] * E[k * 6 + j];
+            Bn[i * 6 + j] = a;
+        }
+    for (int i = 0; i < 36; i++) st[7 + i] = Bn[i];
+    free(u);
+}
+
+/*
  * A whole MetaDE run (Alg. 3) for one problem, one-shot evaluation: every
  * executor starts from the same seed (stream = group, epoch 0).  `power_up`
  * gives the last evolver generation 5x the inner generations (Sec. III-D).
+ * evolver: 0 DE/rand/1/bin (Alg. 3), 1 PSO, 2 CSO, 3 NES (xNES).
  * Writes the final evolver population/fitness; returns the best meta-fitness.
  */
 double or_metade_run(int n_out, int np, int dim, int obj, const double *o, const double *R,
@@ -607,13 +850,21 @@ double or_metade_run(int n_out, int np, int dim, int obj, const double *o, const
 {
     double *trial = (double *)malloc(sizeof(double) * (size_t)n_out * 6);
     double *vel = (double *)malloc(sizeof(double) * (size_t)n_out * 6);
+    double *ns = (double *)malloc(sizeof(double) * (size_t)n_out * 6);
+    int32_t *flag = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_out);
     double *yf = (double *)malloc(sizeof(double) * (size_t)n_out);
     double *pop = (double *)malloc(sizeof(double) * (size_t)np * dim);
     double *fit = (double *)malloc(sizeof(double) * (size_t)np);
+    double nes[43];
     or_outer_init(n_out, seed, group, opop, ofit);
+    if (evolver == 3) or_nes_init(nes);
     for (int g = 0; g < outer_gens; g++) {
         if (evolver == 1)
             or_pso_move(n_out, seed, group, (uint32_t)g, 0.729, 1.49, 1.49, opop, ofit, trial, vel);
+        else if (evolver == 2)
+            or_cso_move(n_out, seed, group, (uint32_t)g, opop, ofit, trial, vel, flag);
+        else if (evolver == 3)
+            or_nes_sample(n_out, seed, group, (uint32_t)g, nes, ns, vel, trial);
         else
             or_outer_trial(n_out, seed, group, (uint32_t)g, opop, trial);
         int gens = (power_up && g == outer_gens - 1) ? 5 * inner_gens : inner_gens;
@@ -622,11 +873,21 @@ double or_metade_run(int n_out, int np, int dim, int obj, const double *o, const
             or_decode(trial + k * 6, th);
             yf[k] = or_pde_run(np, dim, obj, o, R, lo, hi, seed, group, 0, p_best_pct, th, gens, pop, fit);
         }
-        or_outer_select(n_out, opop, ofit, trial, yf, NULL);
+        if (evolver == 2) {
+            or_cso_select(n_out, opop, ofit, trial, flag, yf);
+        } else if (evolver == 3) {
+            or_nes_update(n_out, nes, ns, yf);
+            for (int k = 0; k < n_out; k++) {
+                for (int j = 0; j < 6; j++) opop[k * 6 + j] = trial[k * 6 + j];
+                ofit[k] = isnan(yf[k]) ? INFINITY : yf[k];
+            }
+        } else {
+            or_outer_select(n_out, opop, ofit, trial, yf, NULL);
+        }
     }
     double b = ofit[0];
     for (int k = 1; k < n_out; k++)
         if (ofit[k] < b) b = ofit[k];
-    free(trial); free(vel); free(yf); free(pop); free(fit);
+    free(trial); free(vel); free(ns); free(flag); free(yf); free(pop); free(fit);
     return b;
 }

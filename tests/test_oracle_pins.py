@@ -641,6 +641,208 @@ def test_pso_metade_run_meta_fitness_does_not_rise():
     assert y6 <= y3
 
 
+# ------------------------------------------------------------- CSO evolver
+# Competitive Swarm Optimizer (Cheng and Jin 2015) as the evolver: random
+# pairs, the fitter particle of a pair is kept, the other learns from it
+# (v <- r1 v + r2 (x_w - x_l), x <- x + v; swarm-mean factor phi = 0).
+def _cso_partner(pop, fit, xn, flag, l):
+    """The winner whose segment from x_l contains x'_l (gen-1 move, v = 0)."""
+    d = xn[l] - pop[l]
+    cands = []
+    for w in np.flatnonzero(flag == 0):
+        span = pop[w] - pop[l]
+        r = np.divide(d, span, out=np.full(6, np.nan), where=span != 0)
+        if np.all((span != 0) & (r >= 0) & (r < 1)):
+            cands.append(int(w))
+    return cands
+
+
+def test_cso_generation0_evaluates_the_initial_swarm():
+    pop, fit, _, _ = _swarm(9)
+    xn, v, flag = oracle.cso_move(pop, fit, np.ones((9, 6)), seed=3, group=1, gen=0)
+    np.testing.assert_array_equal(xn, pop)
+    assert not v.any() and flag.all()
+
+
+@pytest.mark.parametrize("n", [8, 9, 30])
+def test_cso_losers_learn_from_their_winners(n):
+    """floor(n/2) losers; a winner (and an odd particle out) is unchanged;
+    with v = 0 each loser moves onto the segment toward exactly one winner,
+    which is no worse than the loser; the winners found this way are
+    distinct (one per pair)."""
+    pop, fit, _, _ = _swarm(n, seed=n)
+    xn, v, flag = oracle.cso_move(pop, fit, np.zeros((n, 6)), seed=7, group=2, gen=1)
+    assert flag.sum() == n // 2
+    np.testing.assert_array_equal(xn[flag == 0], pop[flag == 0])
+    np.testing.assert_array_equal(v[flag == 0], 0.0)
+    losers = [int(l) for l in np.flatnonzero(flag)]
+    cands = {}
+    for l in losers:
+        np.testing.assert_allclose(v[l], xn[l] - pop[l], rtol=0, atol=1e-12)
+        cands[l] = [w for w in _cso_partner(pop, fit, xn, flag, l)
+                    if fit[w] < fit[l] or (fit[w] == fit[l] and w < l)]
+        assert cands[l], l
+    # every loser has its own winner: a perfect matching (augmenting paths)
+    match = {}
+
+    def augment(l, seen):
+        for w in cands[l]:
+            if w in seen:
+                continue
+            seen.add(w)
+            if w not in match or augment(match[w], seen):
+                match[w] = l
+                return True
+        return False
+
+    assert all(augment(l, set()) for l in losers)
+
+
+def test_cso_velocity_memory():
+    """A loser's old velocity enters scaled by r1 in [0, 1): with x_w = x_l
+    (identical pair) the move is r1 v exactly."""
+    pop = np.tile(LB + 0.5 * (UB - LB), (2, 1))
+    fit = np.array([1.0, 2.0])
+    v0 = 0.1 * (UB - LB) * np.array([[1, -1, 1, -1, 1, -1], [1, 1, -1, -1, 1, 1]], dtype=float)
+    xn, v, flag = oracle.cso_move(pop, fit, v0, seed=5, group=0, gen=3)
+    assert flag.tolist() == [0, 1]
+    r1 = v[1] / v0[1]
+    assert np.all((r1 >= 0) & (r1 < 1)) and np.std(r1) > 0.05
+    np.testing.assert_allclose(xn[1], pop[1] + v[1], rtol=0, atol=1e-12)
+    np.testing.assert_array_equal(v[0], v0[0])
+
+
+def test_cso_pairings_are_uniform():
+    """m = 4 has three pairings, each with probability 1/3 under a uniform
+    random permutation (Fisher-Yates); chi-square over 3000 generations."""
+    # positions whose differences to the possible winners of each loser
+    # differ in sign in some coordinate, so the move names the partner
+    unit = np.array([[0.1] * 6, [0.7] * 6, [0.9, 0.2] * 3, [0.3, 0.8] * 3])
+    pop = LB + (UB - LB) * unit
+    fit = np.array([1.0, 2.0, 3.0, 4.0])
+    counts = {}
+    for g in range(1, 3001):
+        xn, v, flag = oracle.cso_move(pop, fit, np.zeros((4, 6)), seed=11, group=0, gen=g)
+        pairs = []
+        for l in np.flatnonzero(flag):
+            (w,) = _cso_partner(pop, fit, xn, flag, l)
+            pairs.append(tuple(sorted((int(w), int(l)))))
+        key = tuple(sorted(pairs))
+        counts[key] = counts.get(key, 0) + 1
+    assert len(counts) == 3
+    obs = np.array(list(counts.values()), dtype=float)
+    chi2 = ((obs - 1000.0) ** 2 / 1000.0).sum()
+    assert chi2 < 13.8                                        # p > 0.001 at 2 dof
+
+
+def test_cso_select_replaces_flagged_unconditionally():
+    pop, fit, _, _ = _swarm(6)
+    xn = pop + 0.01
+    flag = np.array([1, 0, 1, 0, 1, 0], dtype=np.int32)
+    y = fit + 100.0                                           # worse, still taken
+    y[4] = np.nan
+    p2, f2 = oracle.cso_select(pop, fit, xn, flag, y)
+    np.testing.assert_array_equal(p2[flag == 1], xn[flag == 1])
+    np.testing.assert_array_equal(p2[flag == 0], pop[flag == 0])
+    assert f2[0] == y[0] and f2[2] == y[2] and np.isinf(f2[4])
+    np.testing.assert_array_equal(f2[flag == 0], fit[flag == 0])
+
+
+def test_cso_minimises_a_sphere_in_the_evolver_box():
+    c = LB + 0.37 * (UB - LB)
+    pop, fit = oracle.outer_init(32, seed=4, group=0)
+    v = np.zeros_like(pop)
+    for g in range(300):
+        xn, v, flag = oracle.cso_move(pop, fit, v, seed=4, group=0, gen=g)
+        pop, fit = oracle.cso_select(pop, fit, xn, flag, ((xn - c) ** 2).sum(axis=1))
+    assert fit.min() < 1e-6
+
+
+# ------------------------------------------------------------- NES evolver
+# xNES (Wierstra et al. 2014): the pins are the matrix exponential against
+# scipy, the normal draws, the initial distribution, det B = 1 under every
+# update (tr G_B = 0), and the two-sample closed form of the update.
+NES_ETA = 3.0 * (3.0 + math.log(6.0)) / (5.0 * 6.0 * math.sqrt(6.0))
+
+
+def test_nes_expm_matches_scipy():
+    sl = pytest.importorskip("scipy.linalg")
+    rng = np.random.default_rng(0)
+    for n in (1, 2, 6):
+        for _ in range(5):
+            A = rng.normal(size=(n, n))
+            S = 0.5 * (A + A.T)
+            np.testing.assert_allclose(oracle.expm_sym(S), sl.expm(S), rtol=1e-12, atol=1e-12)
+
+
+def test_nes_samples_are_standard_normal():
+    stats = pytest.importorskip("scipy.stats")
+    st = oracle.nes_init()
+    s = np.concatenate([oracle.nes_sample(st, 500, seed=5, group=g, gen=1)[0] for g in range(4)])
+    for j in range(6):
+        assert stats.kstest(s[:, j], "norm").pvalue > 1e-3
+    c = np.corrcoef(s.T)
+    assert np.abs(c - np.eye(6)).max() < 0.06                  # independent coordinates
+
+
+def test_nes_initial_distribution_and_sample_map():
+    st = oracle.nes_init()
+    np.testing.assert_allclose(st[:6], 0.5 * (LB + UB))
+    B = st[7:].reshape(6, 6)
+    np.testing.assert_allclose(st[6] * B, np.diag((UB - LB) / 4.0), atol=1e-15)
+    assert abs(np.linalg.det(B) - 1.0) < 1e-12
+    s, z, zc = oracle.nes_sample(st, 64, seed=2, group=0, gen=0)
+    np.testing.assert_allclose(z, st[:6] + st[6] * s @ B.T, atol=1e-12)
+    np.testing.assert_array_equal(zc, np.clip(z, LB, UB))
+
+
+def test_nes_update_keeps_det_b_one():
+    rng = np.random.default_rng(1)
+    st = oracle.nes_init()
+    for g in range(20):
+        s, z, zc = oracle.nes_sample(st, 24, seed=3, group=0, gen=g)
+        st = oracle.nes_update(st, s, rng.random(24))
+        assert abs(np.linalg.det(st[7:].reshape(6, 6)) - 1.0) < 1e-9
+
+
+def test_nes_two_sample_closed_form():
+    """lambda = 2: utilities +1/2 (better) and -1/2 (worse), so
+    mu' = mu + sigma B (s_b - s_w)/2, sigma' = sigma exp(eta (|s_b|^2 - |s_w|^2) / (4 d)),
+    B' = B expm(eta/2 (G_M - G_sigma I)) with G_M = (s_b s_b^T - s_w s_w^T)/2."""
+    sl = pytest.importorskip("scipy.linalg")
+    st = oracle.nes_init()
+    st[7:] = (st[7:].reshape(6, 6) @ sl.expm(0.1 * np.triu(np.ones((6, 6))) - 0.1 * np.tril(np.ones((6, 6))))).ravel()
+    s, _, _ = oracle.nes_sample(st, 2, seed=8, group=1, gen=5)
+    for y in ([1.0, 2.0], [3.0, -1.0]):
+        b, w = (0, 1) if y[0] < y[1] else (1, 0)
+        st2 = oracle.nes_update(st, s, np.array(y))
+        B, sig = st[7:].reshape(6, 6), st[6]
+        np.testing.assert_allclose(st2[:6], st[:6] + sig * B @ (s[b] - s[w]) / 2, rtol=0, atol=1e-12)
+        gs = (s[b] @ s[b] - s[w] @ s[w]) / (2 * 6)
+        np.testing.assert_allclose(st2[6], sig * math.exp(0.5 * NES_ETA * gs), rtol=1e-13)
+        GM = 0.5 * (np.outer(s[b], s[b]) - np.outer(s[w], s[w]))
+        np.testing.assert_allclose(st2[7:].reshape(6, 6), B @ sl.expm(0.5 * NES_ETA * (GM - gs * np.eye(6))),
+                                   rtol=0, atol=1e-12)
+
+
+def test_nes_minimises_a_sphere_in_the_evolver_box():
+    c = LB + 0.37 * (UB - LB)
+    st = oracle.nes_init()
+    for g in range(150):
+        s, z, zc = oracle.nes_sample(st, 16, seed=4, group=0, gen=g)
+        st = oracle.nes_update(st, s, ((zc - c) ** 2).sum(axis=1))
+    assert ((st[:6] - c) ** 2).sum() < 1e-6
+
+
+def test_cso_and_nes_metade_runs():
+    wl = synth.tiny()
+    p = wl.problems[0]
+    for ev in (2, 3):
+        y, opop, ofit = oracle.metade_run(wl.n_out, 16, p.obj, p.shift, p.rot, 10, 3, seed=2, evolver=ev)
+        assert np.isfinite(y) and y == ofit.min()
+        assert np.all(opop >= LB) and np.all(opop <= UB)
+
+
 # ------------------------------------------------------------ MLP objective
 # Objective 6: a 16-h-2 tanh perceptron's parameters against a teacher (the
 # shift).  The pins are symmetries and exact identities of the network, so
