@@ -112,7 +112,8 @@ typedef struct {
     metade_path path;
     int32_t tie_fp64;          /* selection ties: 0 = FP32 difference form, 1 = FP64 re-evaluation */
     void *stream;              /* cudaStream_t all calls are issued on (NULL = legacy) */
-    int32_t evolver;           /* 0 = DE/rand/1/bin (Alg. 3); 1 = PSO (w = 0.729, c1 = c2 = 1.49) */
+    int32_t evolver;           /* 0 = DE/rand/1/bin (Alg. 3); 1 = PSO (w = 0.729, c1 = c2 = 1.49);
+                                  2 = CSO (n_out <= 4096); 3 = NES (xNES) */
 } metade_config;
 
 typedef struct metade_ctx metade_ctx;
@@ -187,7 +188,24 @@ METADE_API metade_status metade_eval(metade_ctx *ctx, const float *pop, metade_p
  * personal best, velocity 0); later generations move every particle by
  * v <- w v + c1 r1 (pbest - x) + c2 r2 (gbest - x), x <- clip(x + v), gbest the
  * run's best personal best (ties to the lower index).  Phase 1 is Alg. 3's
- * selection applied to the positions.  ofit is read by phase 0. */
+ * selection applied to the positions.  ofit is read by phase 0.
+ * With cfg.evolver = 2 (CSO, Cheng and Jin 2015) the population holds the
+ * particles' positions and `trial` is float32 [n_groups][n_out][13]: the
+ * position to evaluate, the velocity, a flag.  Phase 0 of generation 0
+ * evaluates the initial swarm (all flagged, velocity 0); later generations
+ * pair the swarm at random (Fisher-Yates on evolver draws), keep the fitter
+ * particle of each pair (ties to the lower index) and move the other:
+ * v <- r1 v + r2 (x_winner - x), x <- clip(x + v), flagged.  Phase 1 gives
+ * every flagged particle its new position and meta-fitness unconditionally.
+ * With cfg.evolver = 3 (NES: xNES, Wierstra et al. 2014) `trial` is float32
+ * [n_groups][12 n_out + 96]: per run, the n_out samples [clip(z) 6 | s 6],
+ * then the search distribution as doubles (mu[6], sigma, B[6][6] row-major),
+ * set by phase 0 of generation 0 to mu = (lb + ub)/2, sigma B =
+ * diag((ub - lb)/4).  Phase 0 draws z = mu + sigma B s, s ~ N(0, I)
+ * (Box-Muller), decoded from clip(z); phase 1 ranks the samples by
+ * meta-fitness and takes the xNES natural-gradient step (utilities, default
+ * learning rates), then writes the samples and their meta-fitness (NaN as
+ * +inf) to the population and fitness. */
 /* Alg. 3, initialisation: uniform in [lb, ub] = [(0,0,1,1,1,1), (1,1,5,5,5,4)], y = +inf. */
 METADE_API metade_status metade_outer_init(metade_ctx *ctx, float *opop, float *ofit);
 

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libmetade.so")
 
 METADE_OK, METADE_EINVAL, METADE_ENOMEM, METADE_ECUDA, METADE_ETIMEOUT, METADE_ESTATE, METADE_EUNSUPPORTED = range(7)
 METADE_FP32, METADE_BF16, METADE_FP8E4M3, METADE_BF16X3, METADE_FP64 = range(5)
-EVOLVER_DE, EVOLVER_PSO = 0, 1
+EVOLVER_DE, EVOLVER_PSO, EVOLVER_CSO, EVOLVER_NES = 0, 1, 2, 3
 METADE_PATH_BATCHED, METADE_PATH_PLAIN = 0, 1
 REC_FIELDS = 18
 
@@ -265,6 +265,16 @@ def metade_strerror(status: int) -> str:
 
 
 # ------------------------------------------------------------ convenience
+def trial_shape(evolver: int, n_groups: int, n_out: int):
+    """Shape of the evolver's `trial` buffer (float32): DE [n][6], PSO [n][12]
+    (position, velocity), CSO [n][13] (position, velocity, flag) with
+    n = n_groups * n_out; NES [n_groups][12 n_out + 96] (samples, then the
+    search distribution as doubles)."""
+    if evolver == EVOLVER_NES:
+        return (n_groups, 12 * n_out + 96)
+    return (n_groups * n_out, {EVOLVER_PSO: 12, EVOLVER_CSO: 13}.get(evolver, 6))
+
+
 class Batch:
     """Device tensors and a context for one batch of executors.
 
@@ -306,7 +316,7 @@ class Batch:
             self.opop = torch.zeros((self.n_groups * n_out, 6), **f32)
             self.ofit = torch.zeros(self.n_groups * n_out, **f32)
             # DE: the trial vectors; PSO: position then velocity of every particle
-            self.trial = torch.zeros((self.n_groups * n_out, 12 if evolver == EVOLVER_PSO else 6), **f32)
+            self.trial = torch.zeros(trial_shape(evolver, self.n_groups, n_out), **f32)
 
     def close(self):
         if self.ctx:

@@ -59,7 +59,7 @@ struct metade_ctx {
     metade_prec prec = METADE_FP32;
     metade_path path = METADE_PATH_BATCHED;
     int tie_fp64 = 0;
-    int evolver = 0;  // 0 DE/rand/1/bin (Alg. 3), 1 PSO
+    int evolver = 0;  // 0 DE/rand/1/bin (Alg. 3), 1 PSO, 2 CSO, 3 NES (xNES)
     cudaStream_t st = nullptr;
     cudaStream_t cap = nullptr;  // private stream for graph capture
     std::vector<InstDesc> hdesc;
@@ -375,20 +375,41 @@ metade_status run_init(metade_ctx* c, cudaStream_t st, float* pop, float* fit, u
 
 __global__ void k_set_u32(uint32_t* p, uint32_t v) { *p = v; }
 
+// Phase 0 of the context's evolver: the vectors to evaluate, decoded into theta.
+cudaError_t launch_evolver_phase0(const metade_ctx* c, Key ko, const uint32_t* gen_dev, uint32_t gen, float* opop,
+                                  float* ofit, float* trial, float* theta, cudaStream_t st) {
+    switch (c->evolver) {
+    case 1: return launch_pso_move(c->n_groups, c->n_out, ko, gen_dev, gen, opop, ofit, trial, theta, st);
+    case 2: return launch_cso_move(c->n_groups, c->n_out, ko, gen_dev, gen, opop, ofit, trial, theta, st);
+    case 3: return launch_nes_sample(c->n_groups, c->n_out, ko, gen_dev, gen, trial, theta, st);
+    default: return launch_outer_trial(c->n_groups, c->n_out, ko, gen_dev, gen, opop, trial, theta, st);
+    }
+}
+
+// Phase 1: the evolver's update from the meta-fitness of phase 0's vectors.
+cudaError_t launch_evolver_phase1(const metade_ctx* c, float* opop, float* ofit, float* trial, const float* meta_fit,
+                                  cudaStream_t st) {
+    switch (c->evolver) {
+    case 1: return launch_outer_select(c->n_groups, c->n_out, opop, ofit, trial, meta_fit, 12, st);
+    case 2: return launch_cso_select(c->n_groups, c->n_out, opop, ofit, trial, meta_fit, st);
+    case 3: return launch_nes_update(c->n_groups, c->n_out, opop, ofit, trial, meta_fit, st);
+    default: return launch_outer_select(c->n_groups, c->n_out, opop, ofit, trial, meta_fit, 6, st);
+    }
+}
+
 // The evolver generation as a stream sequence (captured into a graph or run directly).
 metade_status enqueue_outer_generation(metade_ctx* c, cudaStream_t st, float* opop, float* ofit, float* trial,
                                        float* theta, float* pop, float* fit, float* best_f, int* best_i,
                                        int n_inner, int64_t* launches) {
     const Key ko = make_key(c->seed, kTagOuter);
-    if (c->evolver == 1) CK(launch_pso_move(c->n_groups, c->n_out, ko, c->gen_dev, 0, opop, ofit, trial, theta, st));
-    else CK(launch_outer_trial(c->n_groups, c->n_out, ko, c->gen_dev, 0, opop, trial, theta, st));
+    CK(launch_evolver_phase0(c, ko, c->gen_dev, 0, opop, ofit, trial, theta, st));
     *launches += 1;
     const uint32_t* ep = c->one_shot ? nullptr : c->gen_dev;
     metade_status s = run_init(c, st, pop, fit, 0, ep, launches);
     if (s != METADE_OK) return s;
     s = run_inner(c, st, pop, fit, theta, 0, ep, 0, n_inner, best_f, best_i, launches);
     if (s != METADE_OK) return s;
-    CK(launch_outer_select(c->n_groups, c->n_out, opop, ofit, trial, best_f, c->evolver == 1 ? 12 : 6, st));
+    CK(launch_evolver_phase1(c, opop, ofit, trial, best_f, st));
     *launches += 1;
     return METADE_OK;
 }
@@ -477,7 +498,8 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
         if (cfg->inst_group && cfg->inst_group[k] < 0) return METADE_EINVAL;
     }
 
-    if (cfg->evolver != 0 && cfg->evolver != 1) return METADE_EINVAL;
+    if (cfg->evolver < 0 || cfg->evolver > 3) return METADE_EINVAL;
+    if (cfg->evolver == 2 && cfg->n_out > 4096) return METADE_EINVAL;  // the pairing lives in shared memory
 
     metade_ctx* c = new metade_ctx();
     c->n_prob = cfg->n_prob;
@@ -803,18 +825,11 @@ metade_status metade_outer_step(metade_ctx* c, float* opop, float* ofit, float* 
     if (!c) return METADE_EINVAL;
     if (c->n_out == 0) return METADE_ESTATE;
     if (phase == 0) {
-        if (!opop || !trial || !theta) return METADE_EINVAL;
-        if (c->evolver == 1) {
-            if (!ofit) return METADE_EINVAL;
-            CK(launch_pso_move(c->n_groups, c->n_out, make_key(c->seed, kTagOuter), nullptr, outer_gen, opop, ofit,
-                               trial, theta, c->st));
-        } else {
-            CK(launch_outer_trial(c->n_groups, c->n_out, make_key(c->seed, kTagOuter), nullptr, outer_gen, opop,
-                                  trial, theta, c->st));
-        }
+        if (!opop || !trial || !theta || ((c->evolver == 1 || c->evolver == 2) && !ofit)) return METADE_EINVAL;
+        CK(launch_evolver_phase0(c, make_key(c->seed, kTagOuter), nullptr, outer_gen, opop, ofit, trial, theta, c->st));
     } else if (phase == 1) {
         if (!opop || !ofit || !trial || !meta_fit) return METADE_EINVAL;
-        CK(launch_outer_select(c->n_groups, c->n_out, opop, ofit, trial, meta_fit, c->evolver == 1 ? 12 : 6, c->st));
+        CK(launch_evolver_phase1(c, opop, ofit, trial, meta_fit, c->st));
     } else {
         return METADE_EINVAL;
     }

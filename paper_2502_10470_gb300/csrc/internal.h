@@ -139,6 +139,14 @@ cudaError_t launch_outer_trial(int n_groups, int n_out, Key key, const uint32_t*
                                const float* opop, float* trial, float* theta, cudaStream_t st);
 cudaError_t launch_outer_select(int n_groups, int n_out, float* opop, float* ofit, const float* trial,
                                 const float* meta_fit, int tstride, cudaStream_t st);
+cudaError_t launch_cso_move(int n_groups, int n_out, Key key, const uint32_t* gen_dev, uint32_t gen,
+                            const float* opop, const float* ofit, float* trial, float* theta, cudaStream_t st);
+cudaError_t launch_cso_select(int n_groups, int n_out, float* opop, float* ofit, const float* trial,
+                              const float* meta_fit, cudaStream_t st);
+cudaError_t launch_nes_sample(int n_groups, int n_out, Key key, const uint32_t* gen_dev, uint32_t gen, float* trial,
+                              float* theta, cudaStream_t st);
+cudaError_t launch_nes_update(int n_groups, int n_out, float* opop, float* ofit, float* trial, const float* meta_fit,
+                              cudaStream_t st);
 cudaError_t launch_pso_move(int n_groups, int n_out, Key key, const uint32_t* gen_dev, uint32_t gen,
                             const float* opop, const float* ofit, float* trial, float* theta, cudaStream_t st);
 

@@ -883,6 +883,296 @@ __global__ void k_pso_move(int n_total, int n_out, Key key, const uint32_t* gen_
     for (int j = 2; j < 6; ++j) th[j] = fminf(fmaxf(floorf(u[j]), 1.0f), top[j - 2]);
 }
 
+// theta of one evolver vector: F = u1, CR = u2, the categorical genes
+// floor(u) clamped to their domains (Alg. 3, decoding).
+__device__ __forceinline__ void write_theta(const float (&u)[6], float* th) {
+    th[0] = u[0];
+    th[1] = u[1];
+    const float top[4] = {4.f, 4.f, 4.f, 3.f};
+#pragma unroll
+    for (int j = 2; j < 6; ++j) th[j] = fminf(fmaxf(floorf(u[j]), 1.0f), top[j - 2]);
+}
+
+// CSO evolver (Competitive Swarm Optimizer, Cheng and Jin 2015; the
+// supplement's comparison of evolvers).  opop / ofit hold the positions and
+// their fitness; trial holds [position to evaluate 6 | velocity 6 | flag] per
+// particle.  Generation 0 evaluates the initial swarm (all flagged, v = 0).
+// Later generations pair the swarm by a Fisher-Yates permutation (position t
+// swaps with int[0, t + 1) from draw slot 3 word 0 of individual t, for
+// t = m - 1 down to 1; pairs (pi[2p], pi[2p + 1]), an odd last particle sits
+// out).  The fitter particle of a pair (ties to the lower index) is kept; the
+// other is flagged and learns from it, with the swarm-mean factor phi = 0:
+//   v <- r1 v + r2 (x_w - x_l),  x' = clip(x_l + v),
+// r1 / r2 the uniforms of the loser's draw words 0..5 / 6..11 (slot = word / 4).
+// One CTA per run; shared memory holds the permutation and the swap targets.
+__global__ void k_cso_move(int n_out, Key key, const uint32_t* gen_dev, uint32_t gen_arg,
+                           const float* __restrict__ opop, const float* __restrict__ ofit, float* trial,
+                           float* theta) {
+    extern __shared__ int perm[];
+    int* jt = perm + n_out;
+    const int g = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+    const uint32_t gen = gen_dev ? *gen_dev : gen_arg;
+    const long long base = (long long)g * n_out;
+    auto keep = [&](int i) {  // evaluated as it is; its stored fitness stays
+        float* tr = trial + (base + i) * 13;
+        float u[6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            u[j] = opop[(base + i) * 6 + j];
+            tr[j] = u[j];
+        }
+        tr[12] = 0.f;
+        write_theta(u, theta + (base + i) * 6);
+    };
+    if (gen == 0) {
+        for (int i = tid; i < n_out; i += nt) {
+            keep(i);
+            float* tr = trial + (base + i) * 13;
+#pragma unroll
+            for (int j = 0; j < 6; ++j) tr[6 + j] = 0.f;
+            tr[12] = 1.f;
+        }
+        return;
+    }
+    for (int t = tid; t < n_out; t += nt) {
+        perm[t] = t;
+        jt[t] = t >= 1 ? (int)below(make_ctr(key, (uint32_t)g, gen, (uint32_t)t, 0u).slot(3).x, (uint32_t)(t + 1)) : 0;
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int t = n_out - 1; t >= 1; --t) {
+            const int a = perm[t];
+            perm[t] = perm[jt[t]];
+            perm[jt[t]] = a;
+        }
+    __syncthreads();
+    const int npair = n_out / 2;
+    for (int q = tid; q < npair + (n_out & 1); q += nt) {
+        if (q == npair) {
+            keep(perm[n_out - 1]);
+            continue;
+        }
+        const int a = perm[2 * q], b = perm[2 * q + 1];
+        const float fa = ofit[base + a], fb = ofit[base + b];
+        const bool a_wins = fa < fb || (fa == fb && a < b);
+        const int w = a_wins ? a : b, l = a_wins ? b : a;
+        keep(w);
+        const Ctr c = make_ctr(key, (uint32_t)g, gen, (uint32_t)l, 0u);
+        const uint4 w0 = c.slot(0), w1 = c.slot(1), w2 = c.slot(2);
+        const uint32_t r1w[6] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y};
+        const uint32_t r2w[6] = {w1.z, w1.w, w2.x, w2.y, w2.z, w2.w};
+        float* tr = trial + (base + l) * 13;
+        float u[6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            const float xl = opop[(base + l) * 6 + j], xw = opop[(base + w) * 6 + j];
+            const float v = uniform24(r1w[j]) * tr[6 + j] + uniform24(r2w[j]) * (xw - xl);
+            const float x = fminf(fmaxf(xl + v, c_lb[j]), c_ub[j]);
+            tr[6 + j] = v;
+            tr[j] = x;
+            u[j] = x;
+        }
+        tr[12] = 1.f;
+        write_theta(u, theta + (base + l) * 6);
+    }
+}
+
+// CSO selection: a flagged particle takes its evaluated position and
+// meta-fitness (NaN as +inf) unconditionally; the others keep theirs.
+__global__ void k_cso_select(int n_total, float* opop, float* ofit, const float* __restrict__ trial,
+                             const float* __restrict__ meta_fit) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_total) return;
+    const float* tr = trial + (long long)e * 13;
+    if (tr[12] == 0.f) return;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) opop[(long long)e * 6 + j] = tr[j];
+    const float y = meta_fit[e];
+    ofit[e] = isnan(y) ? INFINITY : y;
+}
+
+// NES evolver: xNES (Wierstra et al., JMLR 2014) over the 6 genes, search
+// distribution N(mu, sigma^2 B B^T), det B = 1.  trial holds per run
+// [n_out][z 6 | s 6] (the clipped sample evaluated and its standard-normal
+// draw) followed by 96 floats holding the state as doubles: mu[6], sigma,
+// B[6][6] row-major.  Generation 0 first sets mu = (lb + ub) / 2 and
+// sigma B = diag((ub - lb) / 4) (sigma the geometric mean of the diagonal).
+// Sample k: Box-Muller on draw words 2q, 2q + 1 of individual k
+// (u1 = ((w >> 8) + 1) 2^-24, u2 = (w >> 8) 2^-24), z = mu + sigma B s,
+// evaluated at clip(z).  The update ranks the samples by meta-fitness (NaN
+// as +inf, ties to the lower index), weights them by the utilities
+// u_r = max(0, ln(lambda/2 + 1) - ln(r + 1)) / sum - 1/lambda and takes the
+// natural-gradient step
+//   mu += sigma B G_delta,  sigma *= exp(eta G_sigma / 2),  B <- B expm(eta G_B / 2),
+// G_delta = sum u s, G_M = sum u (s s^T - I), G_sigma = tr G_M / 6,
+// G_B = G_M - G_sigma I, eta = 3 (3 + ln 6) / (5 6 sqrt 6) (the paper's
+// defaults, eta_mu = 1).  opop / ofit then hold the samples and their
+// meta-fitness.  All of it in FP64, one CTA (a warp) per run.
+__host__ __device__ inline long long nes_block(int n_out) { return 12LL * n_out + 96; }
+
+__device__ __forceinline__ double* nes_state(float* trial, int g, int n_out) {
+    return reinterpret_cast<double*>(trial + (long long)g * nes_block(n_out) + 12LL * n_out);
+}
+
+__global__ void k_nes_sample(int n_out, Key key, const uint32_t* gen_dev, uint32_t gen_arg, float* trial,
+                             float* theta) {
+    __shared__ double sst[43];
+    const int g = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+    const uint32_t gen = gen_dev ? *gen_dev : gen_arg;
+    double* st = nes_state(trial, g, n_out);
+    if (gen == 0 && tid == 0) {
+        double lg = 0.0;
+        for (int j = 0; j < 6; ++j) lg += log((double)(c_ub[j] - c_lb[j]) * 0.25);
+        const double sigma = exp(lg / 6.0);
+        for (int j = 0; j < 6; ++j) st[j] = 0.5 * ((double)c_lb[j] + (double)c_ub[j]);
+        st[6] = sigma;
+        for (int r = 0; r < 6; ++r)
+            for (int c = 0; c < 6; ++c) st[7 + 6 * r + c] = r == c ? (double)(c_ub[r] - c_lb[r]) * 0.25 / sigma : 0.0;
+    }
+    __syncthreads();
+    for (int q = tid; q < 43; q += nt) sst[q] = st[q];
+    __syncthreads();
+    for (int k = tid; k < n_out; k += nt) {
+        const Ctr c = make_ctr(key, (uint32_t)g, gen, (uint32_t)k, 0u);
+        const uint4 w0 = c.slot(0), w1 = c.slot(1);
+        const uint32_t w[6] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y};
+        double sv[6];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const double u1 = (double)((w[2 * q] >> 8) + 1u) * (1.0 / 16777216.0);
+            const double u2 = (double)(w[2 * q + 1] >> 8) * (1.0 / 16777216.0);
+            const double rad = sqrt(-2.0 * log(u1));
+            double sn, cs;
+            sincospi(2.0 * u2, &sn, &cs);
+            sv[2 * q] = rad * cs;
+            sv[2 * q + 1] = rad * sn;
+        }
+        float* tr = trial + (long long)g * nes_block(n_out) + 12LL * k;
+        float u[6];
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {
+            double a = 0.0;
+#pragma unroll
+            for (int cc = 0; cc < 6; ++cc) a += sst[7 + 6 * r + cc] * sv[cc];
+            const double z = fmin(fmax(sst[r] + sst[6] * a, (double)c_lb[r]), (double)c_ub[r]);
+            u[r] = (float)z;
+            tr[r] = u[r];
+            tr[6 + r] = (float)sv[r];
+        }
+        write_theta(u, theta + ((long long)g * n_out + k) * 6);
+    }
+}
+
+// exp of a 6 x 6 matrix by scaling and squaring of its Taylor series:
+// A / 2^s with infinity norm <= 1/2, 20 terms, then s squarings.
+__device__ void expm6(const double* A, double* E) {
+    double nrm = 0.0;
+    for (int i = 0; i < 6; ++i) {
+        double r = 0.0;
+        for (int j = 0; j < 6; ++j) r += fabs(A[6 * i + j]);
+        nrm = fmax(nrm, r);
+    }
+    int sq = 0;
+    while (nrm > 0.5 && sq < 60) {
+        nrm *= 0.5;
+        ++sq;
+    }
+    const double sc = ldexp(1.0, -sq);
+    double X[36], T[36], W[36];
+    for (int i = 0; i < 36; ++i) {
+        X[i] = A[i] * sc;
+        T[i] = (i % 7 == 0) ? 1.0 : 0.0;
+        E[i] = T[i];
+    }
+    for (int k = 1; k <= 20; ++k) {
+        for (int i = 0; i < 6; ++i)
+            for (int j = 0; j < 6; ++j) {
+                double a = 0.0;
+                for (int q = 0; q < 6; ++q) a += T[6 * i + q] * X[6 * q + j];
+                W[6 * i + j] = a / k;
+            }
+        for (int i = 0; i < 36; ++i) {
+            T[i] = W[i];
+            E[i] += W[i];
+        }
+    }
+    for (int r = 0; r < sq; ++r) {
+        for (int i = 0; i < 6; ++i)
+            for (int j = 0; j < 6; ++j) {
+                double a = 0.0;
+                for (int q = 0; q < 6; ++q) a += E[6 * i + q] * E[6 * q + j];
+                W[6 * i + j] = a;
+            }
+        for (int i = 0; i < 36; ++i) E[i] = W[i];
+    }
+}
+
+__global__ void __launch_bounds__(32) k_nes_update(int n_out, float* opop, float* ofit, float* trial,
+                                                   const float* __restrict__ meta_fit) {
+    const int g = blockIdx.x, lane = threadIdx.x;
+    const long long base = (long long)g * n_out;
+    const float* tg = trial + (long long)g * nes_block(n_out);
+    double* st = nes_state(trial, g, n_out);
+    const double lam = (double)n_out, top = log(lam * 0.5 + 1.0);
+    double den = 0.0;
+    for (int r = lane; r < n_out; r += 32) den += fmax(0.0, top - log(r + 1.0));
+    den = warp_sum(den);
+    double gd[6] = {0, 0, 0, 0, 0, 0}, gm[21] = {0};  // G_delta, upper triangle of G_M
+    for (int k = lane; k < n_out; k += 32) {
+        float yk = meta_fit[base + k];
+        if (isnan(yk)) yk = INFINITY;
+        int rank = 0;
+        for (int j = 0; j < n_out; ++j) {
+            float yj = meta_fit[base + j];
+            if (isnan(yj)) yj = INFINITY;
+            rank += (yj < yk || (yj == yk && j < k)) ? 1 : 0;
+        }
+        const double uk = fmax(0.0, top - log(rank + 1.0)) / den - 1.0 / lam;
+        double sv[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            sv[i] = (double)tg[12LL * k + 6 + i];
+            gd[i] += uk * sv[i];
+        }
+        int t = 0;
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+#pragma unroll
+            for (int j = i; j < 6; ++j, ++t) gm[t] += uk * (sv[i] * sv[j] - (i == j ? 1.0 : 0.0));
+#pragma unroll
+        for (int i = 0; i < 6; ++i) opop[(base + k) * 6 + i] = tg[12LL * k + i];
+        ofit[base + k] = yk;
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) gd[i] = warp_sum(gd[i]);
+#pragma unroll
+    for (int t = 0; t < 21; ++t) gm[t] = warp_sum(gm[t]);
+    if (lane != 0) return;
+    const double eta = 3.0 * (3.0 + log(6.0)) / (5.0 * 6.0 * sqrt(6.0));
+    double GM[36];
+    int t = 0;
+    for (int i = 0; i < 6; ++i)
+        for (int j = i; j < 6; ++j, ++t) GM[6 * i + j] = GM[6 * j + i] = gm[t];
+    const double gs = (GM[0] + GM[7] + GM[14] + GM[21] + GM[28] + GM[35]) / 6.0;
+    double H[36], Ex[36], Bn[36];
+    for (int i = 0; i < 36; ++i) H[i] = 0.5 * eta * (GM[i] - ((i % 7 == 0) ? gs : 0.0));
+    expm6(H, Ex);
+    const double sigma = st[6];
+    for (int i = 0; i < 6; ++i) {
+        double a = 0.0;
+        for (int j = 0; j < 6; ++j) a += st[7 + 6 * i + j] * gd[j];
+        st[i] += sigma * a;
+    }
+    st[6] = sigma * exp(0.5 * eta * gs);
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) {
+            double a = 0.0;
+            for (int q = 0; q < 6; ++q) a += st[7 + 6 * i + q] * Ex[6 * q + j];
+            Bn[6 * i + j] = a;
+        }
+    for (int i = 0; i < 36; ++i) st[7 + i] = Bn[i];
+}
+
 // Alg. 3 selection; tstride is the trial's floats per vector (6 for DE, 12
 // for PSO, whose first 6 are the position).
 __global__ void k_outer_select(int n_total, float* opop, float* ofit, const float* __restrict__ trial,
@@ -915,6 +1205,36 @@ cudaError_t launch_outer_select(int n_groups, int n_out, float* opop, float* ofi
                                 const float* meta_fit, int tstride, cudaStream_t st) {
     const int n = n_groups * n_out;
     k_outer_select<<<(n + 127) / 128, 128, 0, st>>>(n, opop, ofit, trial, meta_fit, tstride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cso_move(int n_groups, int n_out, Key key, const uint32_t* gen_dev, uint32_t gen,
+                            const float* opop, const float* ofit, float* trial, float* theta, cudaStream_t st) {
+    if (n_groups <= 0) return cudaSuccess;
+    k_cso_move<<<n_groups, 128, 2 * sizeof(int) * (size_t)n_out, st>>>(n_out, key, gen_dev, gen, opop, ofit, trial,
+                                                                      theta);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cso_select(int n_groups, int n_out, float* opop, float* ofit, const float* trial,
+                              const float* meta_fit, cudaStream_t st) {
+    const int n = n_groups * n_out;
+    if (n <= 0) return cudaSuccess;
+    k_cso_select<<<(n + 127) / 128, 128, 0, st>>>(n, opop, ofit, trial, meta_fit);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nes_sample(int n_groups, int n_out, Key key, const uint32_t* gen_dev, uint32_t gen, float* trial,
+                              float* theta, cudaStream_t st) {
+    if (n_groups <= 0) return cudaSuccess;
+    k_nes_sample<<<n_groups, 128, 0, st>>>(n_out, key, gen_dev, gen, trial, theta);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nes_update(int n_groups, int n_out, float* opop, float* ofit, float* trial, const float* meta_fit,
+                              cudaStream_t st) {
+    if (n_groups <= 0) return cudaSuccess;
+    k_nes_update<<<n_groups, 32, 0, st>>>(n_out, opop, ofit, trial, meta_fit);
     return cudaGetLastError();
 }
 

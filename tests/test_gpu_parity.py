@@ -384,6 +384,169 @@ def test_pso_evolver_move_and_select():
     b.close()
 
 
+def _two_runs(n_out=8, seed=13):
+    wl = synth.tiny()
+    n = 2 * n_out
+    return synth.Workload(name="two-runs", problems=wl.problems * 2, inst_np=np.full(n, 16, dtype=np.int32),
+                          inst_prob=np.repeat([0, 1], n_out).astype(np.int32),
+                          inst_group=np.repeat([0, 1], n_out).astype(np.int32), n_groups=2, n_out=n_out,
+                          inner_gens=2, outer_gens=2, seed=seed, one_shot=1)
+
+
+@pytest.mark.parametrize("n_out", [8, 9])
+def test_cso_evolver_move_and_select(n_out):
+    """CSO evolver: generation 0 evaluates the initial swarm, all flagged; a
+    later move pairs each run exactly as the oracle (flags bit-exact: the
+    permutation and the pair decisions are integer work on the same stored
+    fitness), moves the losers within FP32 rounding of the FP64 update, keeps
+    the winners; selection replaces the flagged particles unconditionally."""
+    import torch
+    import paper_2502_10470_gb300 as M
+    wl2 = _two_runs(n_out)
+    n = 2 * n_out
+    b = make_batch(wl2, 0, evolver=M.EVOLVER_CSO)
+    assert tuple(b.trial.shape) == (n, 13)
+    M.metade_outer_init(b.ctx, b.opop, b.ofit)
+    M.metade_outer_step(b.ctx, b.opop, b.ofit, b.trial, b.theta, None, 0, 0)
+    b.sync()
+    tr = b.trial.cpu().numpy()
+    np.testing.assert_array_equal(tr[:, :6], b.opop.cpu().numpy())
+    assert not tr[:, 6:12].any() and (tr[:, 12] == 1).all()
+    rng = np.random.default_rng(5)
+    lb, ub = synth.OUTER_LB, synth.OUTER_UB
+    x = (lb + (ub - lb) * rng.random((n, 6))).astype(np.float32)
+    v = (0.3 * (ub - lb) * (rng.random((n, 6)) - 0.5)).astype(np.float32)
+    fit = rng.uniform(1, 10, n).astype(np.float32)
+    fit[[1, 3]] = 0.5                                           # an equal-fitness pair decides by index
+    b.opop.copy_(torch.from_numpy(x))
+    b.ofit.copy_(torch.from_numpy(fit))
+    b.trial.copy_(torch.from_numpy(np.concatenate([x, v, np.zeros((n, 1), np.float32)], axis=1)))
+    for gen in (1, 6):
+        M.metade_outer_step(b.ctx, b.opop, b.ofit, b.trial, b.theta, None, gen, 0)
+        b.sync()
+        tr = b.trial.cpu().numpy()
+        theta = b.theta.cpu().numpy()
+        for g in range(2):
+            sl = slice(n_out * g, n_out * (g + 1))
+            wx, wv, wf = oracle.cso_move(x[sl], fit[sl], v[sl], seed=wl2.seed, group=g, gen=gen)
+            np.testing.assert_array_equal(tr[sl, 12].astype(np.int32), wf)
+            assert wf.sum() == n_out // 2
+            assert np.abs(tr[sl, :6] - wx).max() < 1e-5
+            assert np.abs(tr[sl, 6:12] - wv).max() < 1e-5
+            np.testing.assert_array_equal(tr[sl, :6][wf == 0], x[sl][wf == 0])
+            for i in range(n_out):
+                np.testing.assert_array_equal(theta[n_out * g + i], oracle.decode(tr[n_out * g + i, :6]).astype(np.float32))
+        b.trial.copy_(torch.from_numpy(np.concatenate([x, v, np.zeros((n, 1), np.float32)], axis=1)))
+    M.metade_outer_step(b.ctx, b.opop, b.ofit, b.trial, b.theta, None, 6, 0)
+    b.sync()
+    tr = b.trial.cpu().numpy()
+    meta = np.full(n, 50.0, dtype=np.float32)
+    meta[0] = np.nan
+    M.metade_outer_step(b.ctx, b.opop, b.ofit, b.trial, b.theta, torch.from_numpy(meta).cuda(), 6, 1)
+    b.sync()
+    npop, nf = b.opop.cpu().numpy(), b.ofit.cpu().numpy()
+    for g in range(2):
+        sl = slice(n_out * g, n_out * (g + 1))
+        wp, wf = oracle.cso_select(x[sl], fit[sl], tr[sl, :6], tr[sl, 12].astype(np.int32), meta[sl])
+        np.testing.assert_array_equal(npop[sl], wp.astype(np.float32))
+        np.testing.assert_array_equal(nf[sl], wf.astype(np.float32))
+    b.close()
+
+
+def test_nes_evolver_sample_and_update():
+    """NES (xNES) evolver: generation 0 sets the oracle's initial distribution;
+    the samples (standard normals and clip(z)) and their decoding match the
+    FP64 oracle from the same state; the update matches the oracle's
+    natural-gradient step (the oracle's expm by Jacobi eigenvectors, the
+    kernel's by Taylor scaling and squaring) and keeps det B = 1; population
+    and fitness then hold the samples and their meta-fitness."""
+    import torch
+    import paper_2502_10470_gb300 as M
+    n_out = 12
+    wl2 = _two_runs(n_out, seed=17)
+    b = make_batch(wl2, 0, evolver=M.EVOLVER_NES)
+    assert tuple(b.trial.shape) == (2, 12 * n_out + 96)
+
+    def state(g):
+        blk = b.trial.cpu().numpy()[g]
+        return blk[12 * n_out:12 * n_out + 86].copy().view(np.float64)
+
+    M.metade_outer_init(b.ctx, b.opop, b.ofit)
+    rng = np.random.default_rng(2)
+    st_prev = [oracle.nes_init(), oracle.nes_init()]
+    for gen in range(4):
+        M.metade_outer_step(b.ctx, b.opop, b.ofit, b.trial, b.theta, None, gen, 0)
+        b.sync()
+        blk = b.trial.cpu().numpy()
+        theta = b.theta.cpu().numpy()
+        for g in range(2):
+            st = state(g)
+            if gen == 0:
+                np.testing.assert_allclose(st, st_prev[g], rtol=1e-14, atol=1e-15)
+            ws, wz, wzc = oracle.nes_sample(st, n_out, seed=wl2.seed, group=g, gen=gen)
+            smp = blk[g, :12 * n_out].reshape(n_out, 12)
+            ds = np.abs(smp[:, 6:] - ws) / (1 + np.abs(ws))
+            dz = np.abs(smp[:, :6] - wzc) / (1 + np.abs(wzc))
+            assert ds.max() < 1e-6 and dz.max() < 1e-6, (gen, g, ds.max(), dz.max(), smp[:2], ws[:2], wzc[:2], st)
+            for k in range(n_out):
+                np.testing.assert_array_equal(theta[n_out * g + k], oracle.decode(smp[k, :6]).astype(np.float32))
+        meta = rng.uniform(0, 5, 2 * n_out).astype(np.float32)
+        meta[3] = meta[4]                                   # equal meta-fitness ranks by index
+        meta[7] = np.nan
+        before = [state(g) for g in range(2)]
+        smps = [b.trial.cpu().numpy()[g, :12 * n_out].reshape(n_out, 12).copy() for g in range(2)]
+        M.metade_outer_step(b.ctx, b.opop, b.ofit, b.trial, b.theta, torch.from_numpy(meta).cuda(), gen, 1)
+        b.sync()
+        opop, ofit = b.opop.cpu().numpy(), b.ofit.cpu().numpy()
+        for g in range(2):
+            sl = slice(n_out * g, n_out * (g + 1))
+            want = oracle.nes_update(before[g], smps[g][:, 6:].astype(np.float64), meta[sl].astype(np.float64))
+            got = state(g)
+            np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12)
+            assert abs(np.linalg.det(got[7:].reshape(6, 6)) - 1.0) < 1e-9
+            np.testing.assert_array_equal(opop[sl], smps[g][:, :6])
+            np.testing.assert_array_equal(ofit[sl], np.where(np.isnan(meta[sl]), np.inf, meta[sl]))
+    b.close()
+
+
+@pytest.mark.parametrize("evolver", [2, 3], ids=["cso", "nes"])
+def test_cso_nes_outer_generation_graph_matches_direct(evolver):
+    import paper_2502_10470_gb300 as M
+    wl = synth.tiny()
+    res = []
+    for use_graph in (False, True):
+        b = make_batch(wl, 0, evolver=evolver)
+        M.metade_outer_init(b.ctx, b.opop, b.ofit)
+        for og in range(3):
+            M.metade_outer_generation(b.ctx, b.opop, b.ofit, b.trial, b.theta, b.pop, b.fit, b.best_f, b.best_i,
+                                      og, 10, use_graph)
+        assert M.metade_sync(b.ctx) == 0
+        res.append((b.opop.cpu().numpy(), b.ofit.cpu().numpy(), b.trial.cpu().numpy()))
+        b.close()
+    for a, c in zip(res[0], res[1]):
+        np.testing.assert_array_equal(a, c)
+    assert np.isfinite(res[0][1]).all()
+
+
+def test_cso_run_best_never_rises():
+    """In CSO the swarm's best particle wins its pair and is kept, so each
+    run's best stored meta-fitness never rises from one evolver generation
+    to the next (generation 0 evaluates everyone)."""
+    import paper_2502_10470_gb300 as M
+    wl = synth.tiny()
+    b = make_batch(wl, 0, evolver=M.EVOLVER_CSO)
+    M.metade_outer_init(b.ctx, b.opop, b.ofit)
+    best = []
+    for og in range(6):
+        M.metade_outer_generation(b.ctx, b.opop, b.ofit, b.trial, b.theta, b.pop, b.fit, b.best_f, b.best_i,
+                                  og, 10, True)
+        b.sync()
+        best.append(float(b.ofit.min().item()))
+    assert M.metade_sync(b.ctx) == 0
+    assert all(y1 <= y0 for y0, y1 in zip(best, best[1:])), best
+    b.close()
+
+
 def test_outer_generation_graph_matches_direct():
     import paper_2502_10470_gb300 as M
     wl = synth.tiny()
