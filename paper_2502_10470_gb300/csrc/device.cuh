@@ -410,62 +410,26 @@ __device__ __forceinline__ T obj_finish(int obj, const ObjAcc<T>& a, int dim) {
     }
 }
 
-// Compile-time objective, FP32, streaming over z_0, z_1, ...  Griewank uses
-// the telescoping form 1 - prod c_j = sum_j (1 - c_j) prod_{k<j} c_k with
-// 1 - c_j = 2 sin^2(a_j / 2): one transcendental per coordinate and no
-// cancellation near the optimum.
-template <int OBJ>
-struct ObjF {
-    float s0 = 0.f, s1 = 0.f, prev = 0.f, pre = 1.f;
-    bool first = true;
-    __device__ __forceinline__ void push(float z, float inv_sqrt_j) {
-        if constexpr (OBJ == kSphere) {
-            s0 = fmaf(z, z, s0);
-        } else if constexpr (OBJ == kRosenbrock) {
-            if (!first) {
-                const float t = z - prev * (prev + 2.f);
-                s0 += 100.f * t * t + prev * prev;
-            }
-            prev = z;
-            first = false;
-        } else if constexpr (OBJ == kRastrigin) {
-            const float sp = sinpif(z);
-            s0 += z * z + 20.f * sp * sp;
-        } else if constexpr (OBJ == kGriewank) {
-            s0 = fmaf(z, z, s0);
-            const float h = sinf(0.5f * z * inv_sqrt_j);
-            const float w = 2.f * h * h;
-            s1 = fmaf(pre, w, s1);
-            pre *= 1.f - w;
-        } else if constexpr (OBJ == kAckley) {
-            s0 = fmaf(z, z, s0);
-            const float sp = sinpif(z);
-            s1 = fmaf(sp, sp, s1);
-        } else {
-            prev += z;
-            s0 = fmaf(prev, prev, s0);
-        }
-    }
-    __device__ __forceinline__ float finish(int dim) const {
-        if constexpr (OBJ == kGriewank) {
-            return s0 * (1.f / 4000.f) + s1;
-        } else if constexpr (OBJ == kAckley) {
-            return -20.f * expm1f(-0.2f * sqrtf(s0 / dim)) - 2.71828182845904523536f * expm1f(-2.f * s1 / dim);
-        } else {
-            return s0;
-        }
-    }
-};
+// 1/pi and 1/(2 pi) as floats: sine and cosine of a multiple of pi go through
+// sinpif / sincospif, whose range reduction is exact and cheap.
+constexpr float kInvPi = 0.318309886f;
+constexpr float kInv2Pi = 0.159154943f;
 
-// The same FP32 objective with the objective chosen at run time (one code
-// path for all objectives keeps the fused kernel's instruction footprint small).
+// FP32 objective streaming over z_0, z_1, ... with the objective chosen at run
+// time (one code path for all objectives keeps the fused kernel's instruction
+// footprint small).  Griewank uses the telescoping form
+// 1 - prod c_j = sum_j (1 - c_j) prod_{k<j} c_k with
+// 1 - c_j = 2 sin^2(a_j / 2), a_j = z_j / sqrt(j), and sin(a_j / 2) taken as
+// sinpi(z_j k_j), k_j = 1 / (2 pi sqrt(j)) (the caller's per-coordinate
+// argument): one transcendental per coordinate and no cancellation near the
+// optimum.
 struct ObjR {
     float s0 = 0.f, s1 = 0.f, prev = 0.f, pre = 1.f;
     bool first = true;
     // One coordinate, objective fixed at compile time (no per-element switch,
     // so independent elements of an unrolled block interleave).
     template <int OBJ>
-    __device__ __forceinline__ void push_t(float z, float inv_sqrt_j) {
+    __device__ __forceinline__ void push_t(float z, float kj) {
         if constexpr (OBJ == kSphere) {
             s0 = fmaf(z, z, s0);
         } else if constexpr (OBJ == kRosenbrock) {
@@ -480,7 +444,7 @@ struct ObjR {
             s0 += z * z + 20.f * sp * sp;
         } else if constexpr (OBJ == kGriewank) {
             s0 = fmaf(z, z, s0);
-            const float h = sinf(0.5f * z * inv_sqrt_j);
+            const float h = sinpif(z * kj);
             const float w = 2.f * h * h;
             s1 = fmaf(pre, w, s1);
             pre *= 1.f - w;
@@ -493,14 +457,14 @@ struct ObjR {
             s0 = fmaf(prev, prev, s0);
         }
     }
-    __device__ __forceinline__ void push(int obj, float z, float inv_sqrt_j) {
+    __device__ __forceinline__ void push(int obj, float z, float kj) {
         switch (obj) {
-        case kSphere: push_t<kSphere>(z, inv_sqrt_j); break;
-        case kRosenbrock: push_t<kRosenbrock>(z, inv_sqrt_j); break;
-        case kRastrigin: push_t<kRastrigin>(z, inv_sqrt_j); break;
-        case kGriewank: push_t<kGriewank>(z, inv_sqrt_j); break;
-        case kAckley: push_t<kAckley>(z, inv_sqrt_j); break;
-        default: push_t<kSchwefel12>(z, inv_sqrt_j); break;
+        case kSphere: push_t<kSphere>(z, kj); break;
+        case kRosenbrock: push_t<kRosenbrock>(z, kj); break;
+        case kRastrigin: push_t<kRastrigin>(z, kj); break;
+        case kGriewank: push_t<kGriewank>(z, kj); break;
+        case kAckley: push_t<kAckley>(z, kj); break;
+        default: push_t<kSchwefel12>(z, kj); break;
         }
     }
     // Four consecutive coordinates, one dispatch.
@@ -526,7 +490,7 @@ struct ObjR {
     __device__ __forceinline__ void push32_t(const float (&v)[32], int col0, int dim) {
 #pragma unroll
         for (int j = 0; j < 32; ++j)
-            if (col0 + j < dim) push_t<OBJ>(v[j], OBJ == kGriewank ? rsqrtf((float)(col0 + j + 1)) : 0.f);
+            if (col0 + j < dim) push_t<OBJ>(v[j], OBJ == kGriewank ? rsqrtf((float)(col0 + j + 1)) * kInv2Pi : 0.f);
     }
     __device__ __forceinline__ void push32(int obj, const float (&v)[32], int col0, int dim) {
         switch (obj) {
@@ -565,12 +529,12 @@ __device__ __forceinline__ double eval64_seq(int obj, int dim, int dpad, const f
 }
 
 // cos(a + 2h) - cos(a) = -2 sin(a + h) sin(h), with sin(a + h) expanded as
-// sin a cos h + cos a sin h so that one sincosf(a) serves both terms; sin h
-// and cos h come from their Taylor series when |h| <= 1/16 (relative error
-// below 1e-9) and from sincosf otherwise.  Writes cos(a) to c.
+// sin a cos h + cos a sin h so that one sincospif(a / pi) serves both terms;
+// sin h and cos h come from their Taylor series when |h| <= 1/16 (relative
+// error below 1e-9) and from sincosf otherwise.  Writes cos(a) to c.
 __device__ __forceinline__ float cos_step(float a, float h, float& c) {
     float sa, ca, sh, ch;
-    sincosf(a, &sa, &ca);
+    sincospif(a * kInvPi, &sa, &ca);
     if (fabsf(h) <= 0.0625f) {
         const float h2 = h * h;
         sh = h * (1.f - h2 * (1.f / 6.f) * (1.f - h2 * (1.f / 20.f)));

@@ -68,7 +68,7 @@ __device__ __forceinline__ void group_obj_push(int obj, GroupObj& acc, float z, 
     case kGriewank:
         if (valid) {
             acc.s0 = fmaf(z, z, acc.s0);
-            const float h = sinf(0.5f * z * rsqrtf((float)(r + 1)));
+            const float h = sinpif(z * (rsqrtf((float)(r + 1)) * kInv2Pi));  // sin(z / (2 sqrt j))
             const float wq = 2.f * h * h;
             acc.Q = fmaf(acc.P, wq, acc.Q);
             acc.P *= 1.f - wq;

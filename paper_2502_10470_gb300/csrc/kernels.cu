@@ -470,7 +470,7 @@ __device__ __forceinline__ void small_executor(const StepArgs& a, int k, const I
     }
     for (int j = tid; j < DMAX; j += nt) {
         o[j] = j < dp ? a.shift[d.shift_off + j] : 0.0f;
-        isq[j] = 1.0f / sqrtf((float)(j + 1));
+        isq[j] = (float)(0.15915494309189535 / sqrt((double)(j + 1)));  // Griewank's 1/(2 pi sqrt j)
     }
     for (int i = tid; i < np; i += nt) {
         f[i] = a.fit[d.fit_off + i];
