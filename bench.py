@@ -49,9 +49,11 @@ def parse_args(argv=None):
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison arm")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--inner-gens", type=int, default=INNER_GENS)
-    ap.add_argument("--workload", default="moderate", choices=["moderate", "precision", "batching", "full", "mlp"],
+    ap.add_argument("--workload", default="moderate",
+                    choices=["moderate", "precision", "batching", "full", "mlp", "evolvers"],
                     help="moderate: the headline workload; precision: the D=1000 precision study; batching: "
-                         "512 ragged executors; full: 8 MetaDE runs x 128 executors")
+                         "512 ragged executors; full: 8 MetaDE runs x 128 executors; evolvers: whole MetaDE "
+                         "runs of the full workload with each evolver (DE, PSO, CSO, NES)")
     ap.add_argument("--seeds", type=int, default=5, help="whole MetaDE runs of the full workload")
     ap.add_argument("--n-inst", type=int, default=64, help="executors of the precision study")
     ap.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES),
@@ -665,6 +667,72 @@ def run_full(args):
     print(json.dumps(line), flush=True)
 
 
+def run_evolvers(args):
+    """The supplement's comparison of evolvers on the full workload (8 MetaDE
+    runs x 128 executors, one-shot, 200 inner generations per evolver
+    generation, 50 evolver generations): for DE/rand/1/bin, PSO, CSO and NES
+    (xNES), --seeds whole runs each through metade_outer_generation (CUDA
+    graph).  Reports the time per evolver generation (CUDA events, graph
+    replays after the first), the time of the evolver's own two kernels per
+    generation, the final best meta-fitness per run (median over seeds) and a
+    rank-sum p-value per run against DE."""
+    import numpy as np
+    import torch
+    import paper_2502_10470_gb300 as M
+    import synth
+    from scipy.stats import ranksums
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    wl = synth.full()
+    probs = [(p.dim, p.obj, p.shift, p.rot) for p in wl.problems]
+    gens = wl.inner_gens
+    names = {M.EVOLVER_DE: "de", M.EVOLVER_PSO: "pso", M.EVOLVER_CSO: "cso", M.EVOLVER_NES: "nes"}
+    out, finals = {}, {}
+    for ev, name in names.items():
+        ms, evo_ms, fin = [], [], []
+        for seed in range(args.seeds):
+            b = M.Batch(probs, wl.inst_np, wl.inst_prob, wl.inst_group, seed=seed, one_shot=1, n_out=wl.n_out,
+                        device=dev, stream=stream.cuda_stream, evolver=ev)
+            M.metade_outer_init(b.ctx, b.opop, b.ofit)
+            evs = []
+            for og in range(wl.outer_gens):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                M.metade_outer_generation(b.ctx, b.opop, b.ofit, b.trial, b.theta, b.pop, b.fit, b.best_f,
+                                          b.best_i, og, gens, True)
+                e1.record(stream)
+                evs.append((e0, e1))
+            torch.cuda.synchronize()
+            if M.metade_sync(b.ctx) != M.METADE_OK:
+                raise RuntimeError("device status")
+            ms.append(float(np.median([a.elapsed_time(c) for a, c in evs[1:]])))
+            fin.append(b.ofit.cpu().numpy().reshape(wl.n_groups, wl.n_out).min(axis=1).astype(np.float64))
+            # the evolver's own kernels: phase 0 and phase 1 after the run, timed alone
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            e[0].record(stream)
+            for _ in range(20):
+                M.metade_outer_step(b.ctx, b.opop, b.ofit, b.trial, b.theta, None, wl.outer_gens, 0)
+                M.metade_outer_step(b.ctx, b.opop, b.ofit, b.trial, b.theta, b.best_f, wl.outer_gens, 1)
+            e[1].record(stream)
+            torch.cuda.synchronize()
+            evo_ms.append(e[0].elapsed_time(e[1]) / 20)
+            b.close()
+        finals[name] = np.array(fin)  # [seeds][runs]
+        out[name] = {"ms_per_outer_generation_median": float(np.median(ms)),
+                     "evolver_kernels_ms_per_generation": float(np.median(evo_ms)),
+                     "final_best_median_per_run": [float(v) for v in np.median(finals[name], axis=0)]}
+    for name in names.values():
+        out[name]["ranksum_p_vs_de_per_run"] = (
+            [float(ranksums(finals[name][:, r], finals["de"][:, r])[1]) for r in range(wl.n_groups)]
+            if args.seeds > 1 and name != "de" else None)
+    line = {"metric": "comparison of evolvers: time per evolver generation and final best meta-fitness",
+            "workload": wl.name, "executors": wl.n_inst, "inner_gens_per_outer_generation": gens,
+            "outer_gens": wl.outer_gens, "seeds": args.seeds, "results": out,
+            "problems": [{"dim": p.dim, "obj": p.obj} for p in wl.problems]}
+    print(json.dumps(line), flush=True)
+
+
 def run_mlp(args):
     """The MLP workload (64 executors x NP 100, D = 1522): batched
     generations of the MLP-objective path, timed with CUDA events after an
@@ -833,6 +901,9 @@ def main(argv=None):
         return
     if args.workload == "mlp":
         run_mlp(args)
+        return
+    if args.workload == "evolvers":
+        run_evolvers(args)
         return
     if args.impl == "reference":
         run_reference(args)
