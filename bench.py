@@ -61,6 +61,23 @@ def parse_args(argv=None):
     return ap.parse_args(argv)
 
 
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The slowest rank's time: all_reduce(MAX) over the process group (the
+    replicas' timed regions are bracketed by the same barriers)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_step: float, steps: int, world: int, max_ms: float) -> float:
+    """Units all ranks processed over the slowest rank's time (weak scaling:
+    every rank runs the whole workload)."""
+    return world * units_per_step * steps / (max_ms / 1000.0)
+
+
 def dist_env():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
@@ -309,11 +326,8 @@ def run_ours(args):
     step_ms = [e[0].elapsed_time(e[3]) for e in step_ev]
     kern_ms = [prof["fused_small"][0] / max(1, prof["fused_small"][1])] * args.steps
     total_ms = sum(step_ms)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_max = float(t.item())
-    value = world * units_per_step * args.steps / (total_max / 1000.0)
+    total_max = max_over_ranks(total_ms, world, dev)
+    value = whole_job_rate(units_per_step, args.steps, world, total_max)
     ops = [alu_ops(th.cpu().numpy(), wl.inst_np, b.dims) * args.inner_gens for th in thetas]
     achieved = sum(ops) / (sum(kern_ms) / 1000.0)
     peaks = {}
@@ -351,10 +365,7 @@ def run_ours(args):
     barrier()
     if M.metade_sync(b.ctx) != 0:
         raise RuntimeError("device status after timing")
-    te = torch.tensor([sum(e2e_ms)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * units_per_step * args.steps / (float(te.item()) / 1000.0)
+    e2e_value = whole_job_rate(units_per_step, args.steps, world, max_over_ranks(sum(e2e_ms), world, dev))
     h2d = (h_opop.numel() + h_ofit.numel()) * 4
     d2h = (h_best.numel() + h_ofit_out.numel()) * 4
 
