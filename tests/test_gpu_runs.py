@@ -91,3 +91,15 @@ def test_pso_evolver_runs_match_oracle_in_distribution():
     stat, pval = ranksums(g, o)
     print("PSO evolver: median gpu %.4g oracle %.4g, rank-sum p = %.3f" % (np.median(g), np.median(o), pval))
     assert pval > 0.05
+
+
+@pytest.mark.parametrize("evolver", [2, 3], ids=["cso", "nes"])
+def test_cso_nes_evolver_runs_match_oracle_in_distribution(evolver):
+    """Whole MetaDE runs with the CSO and NES (xNES) evolvers: GPU against the
+    FP64 oracle's, 31 seeds, rank-sum test at 0.05."""
+    from scipy.stats import ranksums
+    g = _truncate(_gpu_runs(evolver=evolver))
+    o = _truncate(_oracle_runs(evolver=evolver))
+    stat, pval = ranksums(g, o)
+    print("evolver %d: median gpu %.4g oracle %.4g, rank-sum p = %.3f" % (evolver, np.median(g), np.median(o), pval))
+    assert pval > 0.05
