@@ -6,11 +6,13 @@
 //   k_tc_prologue  best and pbest pool per executor (block per executor)
 //   k_tc_trial     draws, mutation, crossover, clip (warp per individual);
 //                  writes the FP32 trial row and the BF16 GEMM operand(s)
-//   k_rot_tc       tcgen05 GEMM: TMA (128-byte swizzle) -> shared memory ->
-//                  tcgen05.mma (M 128, N 256, K 16, FP32 accumulate in TMEM);
-//                  the epilogue reads TMEM with tcgen05.ld, one thread per
-//                  individual (TMEM lane), and accumulates the objective
-//                  column chunk by column chunk, so Z never reaches memory
+//   k_rot_tc       tcgen05 GEMM: TMA (128-byte swizzle, 4 stages) -> shared
+//                  memory -> tcgen05.mma (M 128, N 256, K 16, FP32 accumulate
+//                  into one of two TMEM accumulators) issued by a producer
+//                  warp; four epilogue warps read TMEM with tcgen05.ld, one
+//                  thread per individual (TMEM lane), and accumulate the
+//                  objective column chunk by column chunk while the MMAs of
+//                  the next chunk run, so Z never reaches memory
 //   k_tc_select    greedy selection and row copy (warp per individual);
 //                  near ties are listed for k_tc_ties (a CTA per tie)
 // Precision: BF16 operands, or bf16x3 (split precision, Henry, Tang &
@@ -34,7 +36,7 @@ namespace {
 constexpr int kBM = 128, kBN = 256, kBK = 64;           // BF16: a 64-element K tile is one 128-byte row
 constexpr int kBK8 = 128;                                 // FP8: a 128-element K tile is one 128-byte row
 constexpr float kE4M3Max = 448.0f;                        // largest finite e4m3 value
-constexpr int kStages = 2;                                 // 2 stages (97 KB): two CTAs share an SM
+constexpr int kStages = 4;                                 // 4 stages (193 KB): one CTA per SM
 constexpr int kAT = kBM * kBK * 2;                        // 16 KB
 constexpr int kBT = kBN * kBK * 2;                        // 32 KB
 constexpr uint32_t kWaitLimit = 1u << 22;                 // try_wait rounds before giving up (seconds)
@@ -132,6 +134,40 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// a <- a followed by b, where b is the objective state of the next columns
+// evaluated from a fresh state: zf is b's first z, q1 the sum of b's running
+// prefixes (Schwefel 1.2) and nb its number of columns.
+__device__ __forceinline__ void obj_compose(int obj, ObjR& a, const ObjR& b, float zf, float q1, int nb) {
+    if (nb == 0) return;
+    switch (obj) {
+    case kAckley:
+        a.s0 += b.s0;
+        a.s1 += b.s1;
+        break;
+    case kGriewank:  // 1 - prod c over both: s1 = s1_a + prod_a s1_b
+        a.s0 += b.s0;
+        a.s1 = fmaf(a.pre, b.s1, a.s1);
+        a.pre *= b.pre;
+        break;
+    case kRosenbrock:  // the pair across the boundary, then b's own pairs
+        if (!a.first) {
+            const float t = zf - a.prev * (a.prev + 2.f);
+            a.s0 += 100.f * t * t + a.prev * a.prev;
+        }
+        a.s0 += b.s0;
+        a.prev = b.prev;
+        a.first = false;
+        break;
+    case kSchwefel12: {  // sum over b of (P + q_i)^2, P = a's prefix
+        const float P = a.prev;
+        a.s0 += b.s0 + (float)nb * P * P + 2.f * P * q1;
+        a.prev = P + b.prev;
+        break;
+    }
+    default: a.s0 += b.s0; break;
+    }
+}
+
 struct TcGemmArgs {
     const InstDesc* desc;
     const int* tiles;         // [n_tiles][2]: executor, first individual of the 128-row tile
@@ -145,13 +181,19 @@ struct TcGemmArgs {
     int* status;
 };
 
-// 128 threads: thread 0 issues TMA and MMA; all four warps run the epilogue
-// (warp w owns TMEM lanes 32w..32w+31, i.e. tile rows 32w..32w+31).
-__global__ void __launch_bounds__(128, 2)
+// 288 threads.  Warps 0-7 run the epilogue: warp w reads TMEM lanes
+// 32 (w % 4).. (tile rows), warps 0-3 the first 128 columns of every chunk and
+// warps 4-7 the last 128, whose objective state is handed over through shared
+// memory (part_ready) and composed in column order.  Lane 0 of warp 8 issues
+// the TMA loads and the MMAs.  Two accumulators of kBN TMEM columns: the MMAs of
+// column chunk c + 1 run while the epilogue drains chunk c (acc_full: the
+// chunk's MMAs are done; acc_empty: the four epilogue warps have read it).
+__global__ void __launch_bounds__(288, 1)
     k_rot_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
              const __grid_constant__ CUtensorMap tmAlo, const __grid_constant__ CUtensorMap tmBlo, TcGemmArgs a) {
     extern __shared__ uint8_t smraw[];
-    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], acc_full[2], acc_empty[2], part_ready[4][2];
+    __shared__ __align__(16) float part[2][kBM][8];
     __shared__ uint32_t tmem_base;
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
     const int nops = a.split ? 2 : 1;  // operand sets per stage (hi, and lo when split)
@@ -168,7 +210,7 @@ __global__ void __launch_bounds__(128, 2)
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                     "r"(kBN)
+                     "r"(2 * kBN)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -177,7 +219,11 @@ __global__ void __launch_bounds__(128, 2)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(&done, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 8);  // one arrival per epilogue warp
+            for (int q = 0; q < 4; ++q) mbar_init(&part_ready[q][b], 1);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tc_fence_before();
@@ -198,99 +244,155 @@ __global__ void __launch_bounds__(128, 2)
         }
     };
 
-    bool ok = true;
-    int issued = 0, consumed = 0;  // loads issued / waited on by thread 0
-    if (tid == 0) {
-        const int pre = total < nst ? total : nst;
-        for (int it = 0; it < pre; ++it) load(it);
-        issued = pre;
-    }
-    ObjR acc;
-    const int row = 32 * warp + lane;  // tile row of this thread
-    // FP8: dequantisation factor of this row (rows past the executor are not used)
-    const float zs = (a.fp8 && m0 + row < d.np) ? a.ascale[arow + row] * a.bscale[d.prob] : 1.0f;
-    for (int c = 0; c < nchunks; ++c) {
-        if (tid == 0 && ok) {
-            for (int kk = 0; kk < a.kt && ok; ++kk) {
-                const int it = c * a.kt + kk, s = it % nst;
-                const uint32_t ph = (uint32_t)(it / nst) & 1u;
-                if (!mbar_wait(&full[s], ph)) {
+    if (warp == 8) {
+        if (lane == 0) {
+            bool ok = true;
+            int issued = 0, consumed = 0;  // loads issued / waited on
+            const int pre = total < nst ? total : nst;
+            for (int it = 0; it < pre; ++it) load(it);
+            issued = pre;
+            for (int c = 0; c < nchunks && ok; ++c) {
+                const int b = c & 1;
+                const uint32_t dacc = taddr + (uint32_t)(b * kBN);
+                // the epilogue has drained this accumulator (chunk c - 2)
+                if (c >= 2 && !mbar_wait(&acc_empty[b], (uint32_t)((c - 2) >> 1) & 1u)) {
                     ok = false;
                     break;
                 }
-                ++consumed;
                 tc_fence_after();
-                uint8_t* st = sm + s * stage_bytes;
-                const uint64_t ad = sdesc_sw128(smem_u32(st)), bd = sdesc_sw128(smem_u32(st + kAT));
-                if (a.fp8) {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)  // K 32 per instruction, 32 bytes along the swizzled row
-                        mma_e4m3(taddr, ad + 2 * j, bd + 2 * j, (kk > 0 || j > 0) ? 1u : 0u);
-                } else {
-#pragma unroll
-                    for (int j = 0; j < kBK / 16; ++j)  // K 16 per instruction, 32 bytes along the swizzled row
-                        mma_bf16(taddr, ad + 2 * j, bd + 2 * j, (kk > 0 || j > 0) ? 1u : 0u);
-                }
-                if (a.split) {
-                    const uint64_t al = sdesc_sw128(smem_u32(st + kAT + kBT));
-                    const uint64_t bl = sdesc_sw128(smem_u32(st + 2 * kAT + kBT));
-#pragma unroll
-                    for (int j = 0; j < kBK / 16; ++j) {
-                        mma_bf16(taddr, ad + 2 * j, bl + 2 * j, 1u);
-                        mma_bf16(taddr, al + 2 * j, bd + 2 * j, 1u);
-                    }
-                }
-                mma_commit(&empty[s]);
-                // refill the stage used by the previous iteration once its MMAs are done
-                if (it >= 1 && issued < total) {
-                    const int pit = it - 1, ps = pit % nst;
-                    if (!mbar_wait(&empty[ps], (uint32_t)(pit / nst) & 1u)) {
+                for (int kk = 0; kk < a.kt; ++kk) {
+                    const int it = c * a.kt + kk, s = it % nst;
+                    if (!mbar_wait(&full[s], (uint32_t)(it / nst) & 1u)) {
                         ok = false;
                         break;
                     }
-                    load(issued);
-                    ++issued;
+                    ++consumed;
+                    tc_fence_after();
+                    uint8_t* st = sm + s * stage_bytes;
+                    const uint64_t ad = sdesc_sw128(smem_u32(st)), bd = sdesc_sw128(smem_u32(st + kAT));
+                    if (a.fp8) {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)  // K 32 per instruction, 32 bytes along the swizzled row
+                            mma_e4m3(dacc, ad + 2 * j, bd + 2 * j, (kk > 0 || j > 0) ? 1u : 0u);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < kBK / 16; ++j)  // K 16 per instruction, 32 bytes along the swizzled row
+                            mma_bf16(dacc, ad + 2 * j, bd + 2 * j, (kk > 0 || j > 0) ? 1u : 0u);
+                    }
+                    if (a.split) {
+                        const uint64_t al = sdesc_sw128(smem_u32(st + kAT + kBT));
+                        const uint64_t bl = sdesc_sw128(smem_u32(st + 2 * kAT + kBT));
+#pragma unroll
+                        for (int j = 0; j < kBK / 16; ++j) {
+                            mma_bf16(dacc, ad + 2 * j, bl + 2 * j, 1u);
+                            mma_bf16(dacc, al + 2 * j, bd + 2 * j, 1u);
+                        }
+                    }
+                    mma_commit(&empty[s]);
+                    // refill the stage used by the previous iteration once its MMAs are done
+                    if (it >= 1 && issued < total) {
+                        const int pit = it - 1, ps = pit % nst;
+                        if (!mbar_wait(&empty[ps], (uint32_t)(pit / nst) & 1u)) {
+                            ok = false;
+                            break;
+                        }
+                        load(issued);
+                        ++issued;
+                    }
                 }
+                if (ok) mma_commit(&acc_full[b]);
             }
-            mma_commit(&done);
+            if (!ok) {
+                set_status(a.status, kStatusTimeout);
+                // drain copies still in flight into this CTA's shared memory (bounded)
+                for (int it = consumed; it < issued; ++it) mbar_wait(&full[it % nst], (uint32_t)(it / nst) & 1u);
+            }
         }
         __syncwarp();
-        // epilogue for this column chunk
-        const bool got = __all_sync(kFull, mbar_wait(&done, (uint32_t)c & 1u) ? 1 : 0) != 0;  // warp-uniform
-        if (!got) ok = false;
-        tc_fence_after();
-        if (got) {
-            for (int p = 0; p < kBN / 32; ++p) {
+    } else {
+        const int qd = warp & 3, half = warp >> 2;
+        ObjR acc;                           // half 0: the row's running state; half 1: the chunk's
+        const int row = 32 * qd + lane;     // tile row of this thread
+        // FP8: dequantisation factor of this row (rows past the executor are not used)
+        const float zs = (a.fp8 && m0 + row < d.np) ? a.ascale[arow + row] * a.bscale[d.prob] : 1.0f;
+        bool eok = true;
+        for (int c = 0; c < nchunks; ++c) {
+            const int b = c & 1;
+            const bool got = __all_sync(kFull, mbar_wait(&acc_full[b], (uint32_t)(c >> 1) & 1u) ? 1 : 0) != 0;
+            if (!got) {
+                eok = false;
+                break;
+            }
+            tc_fence_after();
+            if (half) acc = ObjR();          // half 1: this chunk's last 128 columns from a fresh state
+            float zf = 0.f, q1 = 0.f, qrun = 0.f;
+            int nb = 0;
+            for (int p = 4 * half; p < 4 * half + 4; ++p) {
                 const int col0 = c * kBN + 32 * p;
-                if (col0 >= d.dim) break;  // uniform across the CTA
+                if (col0 >= d.dim) break;  // uniform across the warp
                 float v[32];
-                tmem_ld32(taddr + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * p), v);
+                tmem_ld32(taddr + ((uint32_t)(32 * qd) << 16) + (uint32_t)(b * kBN + 32 * p), v);
                 if (a.fp8) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) v[j] *= zs;
                 }
+                if (half) {
+                    if (nb == 0) zf = v[0];
+                    const int m = min(32, d.dim - col0);
+                    if (d.obj == kSchwefel12) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (j < m) {
+                                qrun += v[j];
+                                q1 += qrun;
+                            }
+                    }
+                    nb += m;
+                }
                 acc.push32(d.obj, v, col0, d.dim);
             }
+            tc_fence_before();
+            __syncwarp();
+            if (half) {
+                float* sl = part[b][row];
+                *reinterpret_cast<float4*>(sl) = make_float4(acc.s0, acc.s1, acc.prev, acc.pre);
+                *reinterpret_cast<float4*>(sl + 4) = make_float4(zf, q1, __int_as_float(nb), 0.f);
+                __syncwarp();
+                if (lane == 0) {
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&part_ready[qd][b])) : "memory");
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[b])) : "memory");
+                }
+            } else {
+                const bool have = __all_sync(kFull, mbar_wait(&part_ready[qd][b], (uint32_t)(c >> 1) & 1u) ? 1 : 0) != 0;
+                if (!have) {
+                    eok = false;
+                    break;
+                }
+                const float* sl = part[b][row];
+                const float4 x0 = *reinterpret_cast<const float4*>(sl), x1 = *reinterpret_cast<const float4*>(sl + 4);
+                ObjR rb;
+                rb.s0 = x0.x;
+                rb.s1 = x0.y;
+                rb.prev = x0.z;
+                rb.pre = x0.w;
+                rb.first = __float_as_int(x1.z) == 0;
+                obj_compose(d.obj, acc, rb, x1.x, x1.y, __float_as_int(x1.z));
+                __syncwarp();
+                if (lane == 0)
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[b])) : "memory");
+            }
         }
-        tc_fence_before();
-        __syncthreads();
-        ok = __syncthreads_and(ok ? 1 : 0) != 0;
-        if (!ok) break;
-    }
-    if (!ok) {
-        if (tid == 0) {
-            set_status(a.status, kStatusTimeout);
-            // drain copies still in flight into this CTA's shared memory (bounded)
-            for (int it = consumed; it < issued; ++it) mbar_wait(&full[it % nst], (uint32_t)(it / nst) & 1u);
+        if (!eok) {
+            if (lane == 0) set_status(a.status, kStatusTimeout);
+        } else if (half == 0 && m0 + row < d.np) {
+            a.fu[d.fit_off + m0 + row] = nan_to_inf(acc.finish(d.obj, d.dim));
         }
-    } else if (m0 + row < d.np) {
-        a.fu[d.fit_off + m0 + row] = nan_to_inf(acc.finish(d.obj, d.dim));
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kBN) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(2 * kBN) : "memory");
 }
 
 // ----------------------------------------------------------- other stages
@@ -641,7 +743,7 @@ cudaError_t launch_tc_eval(const InstDesc* desc, const TcPlan& p, const float* p
     g.ascale = p.ascale;
     g.bscale = p.bscale;
     g.status = status;
-    k_rot_tc<<<p.n_tiles, 128, smem_g, st>>>(p.mapA, p.mapB, p.split ? p.mapAlo : p.mapA, p.split ? p.mapBlo : p.mapB,
+    k_rot_tc<<<p.n_tiles, 288, smem_g, st>>>(p.mapA, p.mapB, p.split ? p.mapAlo : p.mapA, p.split ? p.mapBlo : p.mapB,
                                              g);
     return cudaGetLastError();
 }
@@ -676,7 +778,7 @@ cudaError_t launch_tc_generation(const StepArgs& a, const TcPlan& p, cudaStream_
         g.bscale = p.bscale;
         g.status = a.status;
         if (gemm0) cudaEventRecord(gemm0, st);
-        k_rot_tc<<<p.n_tiles, 128, smem_g, st>>>(p.mapA, p.mapB, p.split ? p.mapAlo : p.mapA, p.split ? p.mapBlo : p.mapB,
+        k_rot_tc<<<p.n_tiles, 288, smem_g, st>>>(p.mapA, p.mapB, p.split ? p.mapAlo : p.mapA, p.split ? p.mapBlo : p.mapB,
                                                  g);
     }
     if (gemm1) cudaEventRecord(gemm1, st);

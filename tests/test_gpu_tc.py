@@ -199,3 +199,31 @@ def test_tc_init_evaluates_on_the_tensor_cores(prec):
         else:
             assert not np.array_equal(out[prec][1][k], out[M.METADE_FP32][1][k])  # not the FP32 values
             check_fitness(out[prec][1][k], out[prec][0][k], probs[k], TOL[prec], UNIT[prec])
+
+
+@pytest.mark.parametrize("prec", [1, 3], ids=["bf16", "bf16x3"])
+def test_tc_epilogue_all_objectives_multi_chunk(prec):
+    """The GEMM epilogue evaluates each 256-column chunk in two halves on
+    separate warps and composes the halves' objective states in column order
+    (sums; Griewank's product pair; Rosenbrock's pair across the boundary;
+    Schwefel 1.2's prefix carry).  Every objective at D = 300 (second chunk
+    ends in the first half), 511 and 777 (ragged last halves): the initial
+    fitness from the GEMM agrees with the FP64 oracle within the precision's
+    budget."""
+    import paper_2502_10470_gb300 as M
+    rng = np.random.default_rng(91)
+    dims = [300, 511, 777]
+    probs = [synth.make_problem(rng, d, o) for d in dims for o in range(6)]
+    n = len(probs)
+    wl = synth.Workload(name="tc-objectives", problems=probs, inst_np=np.full(n, 40, dtype=np.int32),
+                        inst_prob=np.arange(n, dtype=np.int32), inst_group=np.arange(n, dtype=np.int32),
+                        n_groups=n, n_out=0, inner_gens=1, outer_gens=1, seed=6, one_shot=0)
+    b = make_batch(wl, M.METADE_PATH_BATCHED, prec=prec)
+    assert json.loads(M.metade_plan_info(b.ctx))["tensor_core"]["executors"] == n
+    M.metade_init(b.ctx, b.pop, b.fit, 0)
+    assert M.metade_sync(b.ctx) == M.METADE_OK
+    pops, fits = b.get_population()
+    for k, p in enumerate(probs):
+        frac = check_fitness(fits[k], pops[k], p, TOL[prec], UNIT[prec])
+        print("D", p.dim, "obj", p.obj, "beyond rtol:", frac)
+    b.close()
