@@ -37,6 +37,9 @@ constexpr int kBM = 128, kBN = 256, kBK = 64;           // BF16: a 64-element K 
 constexpr int kBK8 = 128;                                 // FP8: a 128-element K tile is one 128-byte row
 constexpr float kE4M3Max = 448.0f;                        // largest finite e4m3 value
 constexpr int kStages = 4;                                 // 4 stages (193 KB): one CTA per SM
+constexpr int kParts = 4;                                  // epilogue warps per TMEM lane quadrant
+constexpr int kEpiWarps = 4 * kParts;                      // each takes kBN / kParts columns of a chunk
+constexpr int kTcThreads = 32 * (kEpiWarps + 1);           // + the producer/MMA warp
 constexpr int kAT = kBM * kBK * 2;                        // 16 KB
 constexpr int kBT = kBN * kBK * 2;                        // 32 KB
 constexpr uint32_t kWaitLimit = 1u << 22;                 // try_wait rounds before giving up (seconds)
@@ -181,19 +184,20 @@ struct TcGemmArgs {
     int* status;
 };
 
-// 288 threads.  Warps 0-7 run the epilogue: warp w reads TMEM lanes
-// 32 (w % 4).. (tile rows), warps 0-3 the first 128 columns of every chunk and
-// warps 4-7 the last 128, whose objective state is handed over through shared
-// memory (part_ready) and composed in column order.  Lane 0 of warp 8 issues
-// the TMA loads and the MMAs.  Two accumulators of kBN TMEM columns: the MMAs of
+// kTcThreads threads.  Warps 0 .. kEpiWarps-1 run the epilogue: warp w reads
+// TMEM lanes 32 (w % 4).. (tile rows) and column part w / 4 (kBN / kParts
+// columns) of every chunk; parts 1.. start from a fresh objective state and
+// hand it over through shared memory (part_ready) to part 0, which composes
+// them in column order.  Lane 0 of the last warp issues the TMA loads and the
+// MMAs.  Two accumulators of kBN TMEM columns: the MMAs of
 // column chunk c + 1 run while the epilogue drains chunk c (acc_full: the
 // chunk's MMAs are done; acc_empty: the four epilogue warps have read it).
-__global__ void __launch_bounds__(288, 1)
+__global__ void __launch_bounds__(kTcThreads, 1)
     k_rot_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
              const __grid_constant__ CUtensorMap tmAlo, const __grid_constant__ CUtensorMap tmBlo, TcGemmArgs a) {
     extern __shared__ uint8_t smraw[];
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages], acc_full[2], acc_empty[2], part_ready[4][2];
-    __shared__ __align__(16) float part[2][kBM][8];
+    __shared__ __align__(16) float part[2][kParts - 1][kBM][8];
     __shared__ uint32_t tmem_base;
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
     const int nops = a.split ? 2 : 1;  // operand sets per stage (hi, and lo when split)
@@ -221,8 +225,8 @@ __global__ void __launch_bounds__(288, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
-            mbar_init(&acc_empty[b], 8);  // one arrival per epilogue warp
-            for (int q = 0; q < 4; ++q) mbar_init(&part_ready[q][b], 1);
+            mbar_init(&acc_empty[b], kEpiWarps);  // one arrival per epilogue warp
+            for (int q = 0; q < 4; ++q) mbar_init(&part_ready[q][b], kParts - 1);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -244,7 +248,7 @@ __global__ void __launch_bounds__(288, 1)
         }
     };
 
-    if (warp == 8) {
+    if (warp == kEpiWarps) {
         if (lane == 0) {
             bool ok = true;
             int issued = 0, consumed = 0;  // loads issued / waited on
@@ -310,8 +314,9 @@ __global__ void __launch_bounds__(288, 1)
         }
         __syncwarp();
     } else {
-        const int qd = warp & 3, half = warp >> 2;
-        ObjR acc;                           // half 0: the row's running state; half 1: the chunk's
+        const int qd = warp & 3, half = warp >> 2;  // half: this warp's column part of every chunk
+        constexpr int kBpp = kBN / 32 / kParts;       // 32-column blocks per part
+        ObjR acc;                           // part 0: the row's running state; parts 1..: the chunk's
         const int row = 32 * qd + lane;     // tile row of this thread
         // FP8: dequantisation factor of this row (rows past the executor are not used)
         const float zs = (a.fp8 && m0 + row < d.np) ? a.ascale[arow + row] * a.bscale[d.prob] : 1.0f;
@@ -324,10 +329,10 @@ __global__ void __launch_bounds__(288, 1)
                 break;
             }
             tc_fence_after();
-            if (half) acc = ObjR();          // half 1: this chunk's last 128 columns from a fresh state
+            if (half) acc = ObjR();          // parts 1..: this chunk's columns from a fresh state
             float zf = 0.f, q1 = 0.f, qrun = 0.f;
             int nb = 0;
-            for (int p = 4 * half; p < 4 * half + 4; ++p) {
+            for (int p = kBpp * half; p < kBpp * (half + 1); ++p) {
                 const int col0 = c * kBN + 32 * p;
                 if (col0 >= d.dim) break;  // uniform across the warp
                 float v[32];
@@ -354,7 +359,7 @@ __global__ void __launch_bounds__(288, 1)
             tc_fence_before();
             __syncwarp();
             if (half) {
-                float* sl = part[b][row];
+                float* sl = part[b][half - 1][row];
                 *reinterpret_cast<float4*>(sl) = make_float4(acc.s0, acc.s1, acc.prev, acc.pre);
                 *reinterpret_cast<float4*>(sl + 4) = make_float4(zf, q1, __int_as_float(nb), 0.f);
                 __syncwarp();
@@ -368,15 +373,17 @@ __global__ void __launch_bounds__(288, 1)
                     eok = false;
                     break;
                 }
-                const float* sl = part[b][row];
-                const float4 x0 = *reinterpret_cast<const float4*>(sl), x1 = *reinterpret_cast<const float4*>(sl + 4);
-                ObjR rb;
-                rb.s0 = x0.x;
-                rb.s1 = x0.y;
-                rb.prev = x0.z;
-                rb.pre = x0.w;
-                rb.first = __float_as_int(x1.z) == 0;
-                obj_compose(d.obj, acc, rb, x1.x, x1.y, __float_as_int(x1.z));
+                for (int j = 0; j < kParts - 1; ++j) {
+                    const float* sl = part[b][j][row];
+                    const float4 x0 = *reinterpret_cast<const float4*>(sl), x1 = *reinterpret_cast<const float4*>(sl + 4);
+                    ObjR rb;
+                    rb.s0 = x0.x;
+                    rb.s1 = x0.y;
+                    rb.prev = x0.z;
+                    rb.pre = x0.w;
+                    rb.first = __float_as_int(x1.z) == 0;
+                    obj_compose(d.obj, acc, rb, x1.x, x1.y, __float_as_int(x1.z));
+                }
                 __syncwarp();
                 if (lane == 0)
                     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[b])) : "memory");
@@ -743,7 +750,7 @@ cudaError_t launch_tc_eval(const InstDesc* desc, const TcPlan& p, const float* p
     g.ascale = p.ascale;
     g.bscale = p.bscale;
     g.status = status;
-    k_rot_tc<<<p.n_tiles, 288, smem_g, st>>>(p.mapA, p.mapB, p.split ? p.mapAlo : p.mapA, p.split ? p.mapBlo : p.mapB,
+    k_rot_tc<<<p.n_tiles, kTcThreads, smem_g, st>>>(p.mapA, p.mapB, p.split ? p.mapAlo : p.mapA, p.split ? p.mapBlo : p.mapB,
                                              g);
     return cudaGetLastError();
 }
@@ -778,7 +785,7 @@ cudaError_t launch_tc_generation(const StepArgs& a, const TcPlan& p, cudaStream_
         g.bscale = p.bscale;
         g.status = a.status;
         if (gemm0) cudaEventRecord(gemm0, st);
-        k_rot_tc<<<p.n_tiles, 288, smem_g, st>>>(p.mapA, p.mapB, p.split ? p.mapAlo : p.mapA, p.split ? p.mapBlo : p.mapB,
+        k_rot_tc<<<p.n_tiles, kTcThreads, smem_g, st>>>(p.mapA, p.mapB, p.split ? p.mapAlo : p.mapA, p.split ? p.mapBlo : p.mapB,
                                                  g);
     }
     if (gemm1) cudaEventRecord(gemm1, st);
