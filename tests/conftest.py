@@ -15,7 +15,7 @@ def pytest_configure(config):
 
 def pytest_collection_modifyitems(config, items):
     # Make `gpu` tests skip cleanly on a machine without a GPU rather than fail
-    # at import time; the driver selects them explicitly with -m gpu.
+    # at import time; they are selected explicitly with -m gpu.
     try:
         import torch
         has_gpu = torch.cuda.is_available()
