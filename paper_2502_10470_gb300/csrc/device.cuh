@@ -415,6 +415,23 @@ __device__ __forceinline__ T obj_finish(int obj, const ObjAcc<T>& a, int dim) {
 constexpr float kInvPi = 0.318309886f;
 constexpr float kInv2Pi = 0.159154943f;
 
+// sin^2(pi x) in FP32: t = x - rint(x) (exact), u = t^2, and
+// sin^2(pi t) = u P(u) with P of degree 5 fitted to sin^2(pi sqrt(u)) / u on
+// [0, 1/4] in the relative sense (weighted least squares driven toward the
+// minimax error; fit error 1.4e-8).  Relative error of the FP32 evaluation
+// below 2.2e-7 over all x: that of a correctly rounded sin(pi x), squared.
+__device__ __forceinline__ float sin2pi(float x) {
+    const float t = x - rintf(x);
+    const float u = t * t;
+    float p = -3.336236715e+00f;
+    p = fmaf(p, u, 1.303712845e+01f);
+    p = fmaf(p, u, -3.009855652e+01f);
+    p = fmaf(p, u, 4.272692871e+01f);
+    p = fmaf(p, u, -3.246966171e+01f);
+    p = fmaf(p, u, 9.869604111e+00f);
+    return u * p;
+}
+
 // FP32 objective streaming over z_0, z_1, ... with the objective chosen at run
 // time (one code path for all objectives keeps the fused kernel's instruction
 // footprint small).  Griewank uses the telescoping form
@@ -440,18 +457,15 @@ struct ObjR {
             prev = z;
             first = false;
         } else if constexpr (OBJ == kRastrigin) {
-            const float sp = sinpif(z);
-            s0 += z * z + 20.f * sp * sp;
+            s0 += z * z + 20.f * sin2pi(z);
         } else if constexpr (OBJ == kGriewank) {
             s0 = fmaf(z, z, s0);
-            const float h = sinpif(z * kj);
-            const float w = 2.f * h * h;
+            const float w = 2.f * sin2pi(z * kj);
             s1 = fmaf(pre, w, s1);
             pre *= 1.f - w;
         } else if constexpr (OBJ == kAckley) {
             s0 = fmaf(z, z, s0);
-            const float sp = sinpif(z);
-            s1 = fmaf(sp, sp, s1);
+            s1 += sin2pi(z);
         } else {
             prev += z;
             s0 = fmaf(prev, prev, s0);

@@ -53,23 +53,18 @@ __device__ __forceinline__ void group_obj_push(int obj, GroupObj& acc, float z, 
         if (valid) acc.s0 = fmaf(z, z, acc.s0);
         break;
     case kRastrigin:
-        if (valid) {
-            const float sp = sinpif(z);
-            acc.s0 += z * z + 20.f * sp * sp;
-        }
+        if (valid) acc.s0 += z * z + 20.f * sin2pi(z);
         break;
     case kAckley:
         if (valid) {
             acc.s0 = fmaf(z, z, acc.s0);
-            const float sp = sinpif(z);
-            acc.s1 = fmaf(sp, sp, acc.s1);
+            acc.s1 += sin2pi(z);
         }
         break;
     case kGriewank:
         if (valid) {
             acc.s0 = fmaf(z, z, acc.s0);
-            const float h = sinpif(z * (rsqrtf((float)(r + 1)) * kInv2Pi));  // sin(z / (2 sqrt j))
-            const float wq = 2.f * h * h;
+            const float wq = 2.f * sin2pi(z * (rsqrtf((float)(r + 1)) * kInv2Pi));  // 2 sin^2(z / (2 sqrt j))
             acc.Q = fmaf(acc.P, wq, acc.Q);
             acc.P *= 1.f - wq;
         }
