@@ -310,7 +310,7 @@ __device__ __forceinline__ float warp_diff(int obj, int dim, const float* z, con
                 d0 += 100.f * dt * (2.f * t + dt) + dj * (2.f * zj + dj);
             }
             break;
-        case kRastrigin: d0 += dj * (2.f * zj + dj) + 20.f * sinpif(2.f * zj + dj) * sinpif(dj); break;
+        case kRastrigin: d0 += dj * (2.f * zj + dj) + 20.f * sin_pi(2.f * zj + dj) * sin_pi(dj); break;
         case kGriewank: {
             // per lane: (A, B) with A = prod c, B = prod c' - prod c over its
             // coordinates; combined across lanes in index order below
@@ -326,9 +326,8 @@ __device__ __forceinline__ float warp_diff(int obj, int dim, const float* z, con
         case kAckley: {
             x0 += zj * zj;
             d0 += dj * (2.f * zj + dj);
-            const float sz = sinpif(zj);
-            x1 += sz * sz;
-            d1 += sinpif(2.f * zj + dj) * sinpif(dj);
+            x1 += sin2pi(zj);
+            d1 += sin_pi(2.f * zj + dj) * sin_pi(dj);
             break;
         }
         }

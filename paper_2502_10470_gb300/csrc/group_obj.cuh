@@ -152,15 +152,14 @@ __device__ __forceinline__ void group_diff_push(int obj, GroupDiff& g, float z, 
         if (valid) g.d0 += dz * (2.f * z + dz);
         break;
     case kRastrigin:
-        if (valid) g.d0 += dz * (2.f * z + dz) + 20.f * sinpif(2.f * z + dz) * sinpif(dz);
+        if (valid) g.d0 += dz * (2.f * z + dz) + 20.f * sin_pi(2.f * z + dz) * sin_pi(dz);
         break;
     case kAckley:
         if (valid) {
             g.x0 = fmaf(z, z, g.x0);
             g.d0 += dz * (2.f * z + dz);
-            const float sz = sinpif(z);
-            g.x1 = fmaf(sz, sz, g.x1);
-            g.d1 += sinpif(2.f * z + dz) * sinpif(dz);
+            g.x1 += sin2pi(z);
+            g.d1 += sin_pi(2.f * z + dz) * sin_pi(dz);
         }
         break;
     case kGriewank:
