@@ -410,8 +410,8 @@ __device__ __forceinline__ T obj_finish(int obj, const ObjAcc<T>& a, int dim) {
     }
 }
 
-// 1/pi and 1/(2 pi) as floats: sine and cosine of a multiple of pi go through
-// sinpif / sincospif, whose range reduction is exact and cheap.
+// 1/pi and 1/(2 pi) as floats: angles are passed in units of pi to sin_pi,
+// sincos_pi and sin2pi, whose range reduction (x - rint(x)) is exact.
 constexpr float kInvPi = 0.318309886f;
 constexpr float kInv2Pi = 0.159154943f;
 
@@ -581,9 +581,9 @@ __device__ __forceinline__ double eval64_seq(int obj, int dim, int dpad, const f
 }
 
 // cos(a + 2h) - cos(a) = -2 sin(a + h) sin(h), with sin(a + h) expanded as
-// sin a cos h + cos a sin h so that one sincospif(a / pi) serves both terms;
+// sin a cos h + cos a sin h so that one sincos_pi(a / pi) serves both terms;
 // sin h and cos h come from their Taylor series when |h| <= 1/16 (relative
-// error below 1e-9) and from sincosf otherwise.  Writes cos(a) to c.
+// error below 1e-9) and from sincos_pi otherwise.  Writes cos(a) to c.
 __device__ __forceinline__ float cos_step(float a, float h, float& c) {
     float sa, ca, sh, ch;
     sincos_pi(a * kInvPi, &sa, &ca);
