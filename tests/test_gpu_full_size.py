@@ -148,3 +148,36 @@ def test_batching_full_size_generation_sampled():
     for k in picked:
         _compare_step(wl, k, pops, fits, theta, npops, nfits, 2 * FIT_RTOL, FIT_RTOL, 0.0)
     b.close()
+
+
+def test_largest_executors_each_kernel():
+    """Maximum sizes: the largest population the small-D kernel holds at
+    D = 32 (population, trials and R in shared memory: NP 700), the largest
+    accepted population (NP 1024) at D = 100 and 200 (tile kernels), and
+    D = 300 (the per-generation pipeline in FP32); one generation against the
+    oracle."""
+    import json
+    import paper_2502_10470_gb300 as M
+    rng = np.random.default_rng(99)
+    dims, nps = [32, 100, 200, 300], [700, 1024, 1024, 600]   # NP 1024 is the largest accepted
+    probs = [synth.make_problem(rng, d, k % 6) for k, d in enumerate(dims)]
+    n = len(probs)
+    th = synth.random_theta(rng, n)
+    wl = synth.Workload(name="largest", problems=probs, inst_np=np.array(nps, dtype=np.int32),
+                        inst_prob=np.arange(n, dtype=np.int32), inst_group=np.arange(n, dtype=np.int32),
+                        n_groups=n, n_out=0, inner_gens=1, outer_gens=1, seed=4, one_shot=0, theta=th)
+    b = M.Batch([(p.dim, p.obj, p.shift, p.rot) for p in probs], wl.inst_np, wl.inst_prob, wl.inst_group,
+                seed=wl.seed, one_shot=0)
+    kernels = {bk["kernel"] for bk in json.loads(M.metade_plan_info(b.ctx))["buckets"]}
+    assert "fused_small" in kernels
+    b.set_theta(wl.theta)
+    M.metade_init(b.ctx, b.pop, b.fit, 0)
+    b.sync()
+    pops, fits = b.get_population()
+    M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 0, 1, b.best_f, b.best_i)
+    assert M.metade_sync(b.ctx) == M.METADE_OK
+    npops, nfits = b.get_population()
+    theta = wl.theta.astype(np.float32)
+    for k in range(n):
+        _compare_step(wl, k, pops, fits, theta, npops, nfits, 2 * FIT_RTOL, FIT_RTOL, 0.0)
+    b.close()
