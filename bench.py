@@ -228,6 +228,13 @@ class ClockSampler:
 
 
 # -------------------------------------------------------------- our arm
+# DRAM bytes (read + written) of one k_fused_small<20> launch of the moderate
+# workload, from the ncu capture summarised in profiles/k_fused_small_moderate_d20.md:
+# the launch loads the executors' state once and stores it once, so the figure
+# does not depend on the number of fused generations.
+SMALL_KERNEL_DRAM_BYTES = 5.206016e6
+
+
 def alu_ops(theta, inst_np, dims):
     """Algorithmic lane operations of one generation of every executor:
     D^2 rotation FMAs + (2 dn + 8) D mutation/crossover/clip/shift operations
@@ -403,7 +410,8 @@ def run_ours(args):
                 "gpu_launches": launches,
                 "roofline": {"bound": "alu", "kernel": "k_fused_small<20>", "achieved": achieved / 1e9,
                              "peak": peak_ops / 1e9, "unit": "Gop/s", "frac": achieved / peak_ops,
-                             "traffic": None, "kernel_ms": sum(kern_ms) / len(kern_ms),
+                             "traffic": SMALL_KERNEL_DRAM_BYTES, "traffic_unit": "bytes per launch",
+                             "kernel_ms": sum(kern_ms) / len(kern_ms),
                              "kernel_share": sum(kern_ms) / total_ms,
                              "peak_source": "152 SMs x 128 lanes x %.0f MHz (max SM clock)" % sm_max},
                 "plain_fp32": plain,
