@@ -430,6 +430,17 @@ __device__ __forceinline__ float diff_small(int obj, int dim, const float* u, co
     return diff_finish(obj, acc, dim);
 }
 
+// FP64 re-evaluation of a near tie by one thread, kept out of line: it is
+// rare, and inlined it would spread the fused loop's code.  Returns the
+// decision and, when taken, the stored value min(f32(f64 f(u)), f(x)) in fn.
+__device__ __noinline__ bool tie_fp64_small(int obj, int dim, int dmax, const float* u, const float* x,
+                                            const float* o, const float* R, float fx, float& fn) {
+    const double eu = nan_to_inf(eval64_seq(obj, dim, dmax, u, o, R));
+    const double ex = nan_to_inf(eval64_seq(obj, dim, dmax, x, o, R));
+    if (eu <= ex) fn = fminf((float)eu, fx);
+    return eu <= ex;
+}
+
 __host__ __device__ inline int small_stride(int dpad) { return ((dpad >> 2) & 1) ? dpad : dpad + 4; }
 
 // One executor, all fused generations, everything resident in shared memory;
@@ -565,10 +576,7 @@ __device__ __forceinline__ void small_executor(const StepArgs& a, int k, const I
                 fn = fx;
             } else if (near_tie(fn, fx, band)) {
                 if (a.tie_fp64) {
-                    const double eu = nan_to_inf(eval64_seq(d.obj, dim, DMAX, U + i * ds, o, R));
-                    const double ex = nan_to_inf(eval64_seq(d.obj, dim, DMAX, X + i * ds, o, R));
-                    take = eu <= ex;
-                    if (take) fn = fminf((float)eu, fx);
+                    take = tie_fp64_small(d.obj, dim, DMAX, U + i * ds, X + i * ds, o, R, fx, fn);
                 } else {
                     const float df = diff_small<DMAX>(d.obj, dim, U + i * ds, X + i * ds, o, R);
                     take = df <= 0.0f;
