@@ -50,10 +50,12 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--inner-gens", type=int, default=INNER_GENS)
     ap.add_argument("--workload", default="moderate",
-                    choices=["moderate", "precision", "batching", "full", "mlp", "evolvers"],
+                    choices=["moderate", "precision", "batching", "full", "mlp", "evolvers", "oracle"],
                     help="moderate: the headline workload; precision: the D=1000 precision study; batching: "
                          "512 ragged executors; full: 8 MetaDE runs x 128 executors; evolvers: whole MetaDE "
-                         "runs of the full workload with each evolver (DE, PSO, CSO, NES)")
+                         "runs of the full workload with each evolver (DE, PSO, CSO, NES); oracle: the FP64 "
+                         "oracle alone on the host cores (one core and all cores) on the tiny, moderate, "
+                         "batching and precision workloads")
     ap.add_argument("--seeds", type=int, default=5, help="whole MetaDE runs of the full workload")
     ap.add_argument("--n-inst", type=int, default=64, help="executors of the precision study")
     ap.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES),
@@ -899,6 +901,97 @@ def _case_simt_d1000():
     b.close()
 
 
+def _oracle_run_job(args):
+    """One whole MetaDE run of the oracle (module-level for the spawn pool)."""
+    import oracle
+    n_out, np_, obj, shift, rot, inner, outer, seed = args
+    oracle.build()
+    oracle.metade_run(n_out, np_, obj, shift, rot, inner, outer, seed=seed)
+    return n_out * np_ * inner * outer
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def run_oracle_timing(args):
+    """The FP64 oracle alone on the host cores, one core and all cores (a
+    spawn pool, one executor or run per task), on four workloads: the tiny
+    workload as whole MetaDE runs (20 inner x 5 outer generations; all cores:
+    one run per core, run seeds 0..cores-1), the moderate workload for 5
+    inner generations, the batching workload for 1 and the precision workload
+    (D 1000) for 1.  Each executor's inner DE also initialises and evaluates
+    its population once, which the generations counted do not include.  No
+    GPU is used.  One JSON line, rank 0 only."""
+    import numpy as np
+    import synth
+    rank, _, _ = dist_env()
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+
+    def inner_tasks(wl, ks, gens):
+        return [(wl.theta[k], int(wl.inst_np[k]), wl.problems[int(wl.inst_prob[k])].obj,
+                 wl.problems[int(wl.inst_prob[k])].shift, wl.problems[int(wl.inst_prob[k])].rot, gens, wl.seed,
+                 int(k), wl.lo, wl.hi) for k in ks]
+
+    cases = []
+    t = synth.tiny()
+    p = t.problems[0]
+    run = lambda s: (t.n_out, int(t.inst_np[0]), p.obj, p.shift, p.rot, t.inner_gens, t.outer_gens, s)
+    cases.append(("tiny: whole MetaDE runs, evolver 8 x NP 16 x D 10, 20 x 5 generations", _oracle_run_job,
+                  [run(0)], [run(s) for s in range(cores)]))
+    m = synth.moderate(inner_gens=5)
+    tasks = oracle_tasks(m, m.n_out, 5)
+    one = [tasks[g * m.n_out] for g in range(len(m.problems))]  # one executor per run
+    cases.append(("moderate: 600 executors x NP 100 x D 20, 5 generations (one core: 6 executors)",
+                  _oracle_job, one, tasks))
+    bt = synth.batching()
+    rng = np.random.default_rng(0)
+    cases.append(("batching: 512 ragged executors, NP 20..400, D 10..100, 1 generation (one core: 32 executors)",
+                  _oracle_box_job, inner_tasks(bt, sorted(rng.choice(bt.n_inst, 32, replace=False)), 1),
+                  inner_tasks(bt, range(bt.n_inst), 1)))
+    pr = synth.precision()
+    cases.append(("precision: 64 executors x NP 512 x D 1000, 1 generation (one core: 1 executor)",
+                  _oracle_box_job, inner_tasks(pr, [0], 1), inner_tasks(pr, range(pr.n_inst), 1)))
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    out = {}
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_job, [tasks[0][:5] + (1,) + tasks[0][6:]] * cores)  # workers up, library built
+        for name, job, single, full in cases:
+            u1, n1, t0 = 0, 0, time.perf_counter()
+            while True:  # this process, one core; repeated to at least 0.5 s
+                u1 += sum(job(a) for a in single)
+                n1 += len(single)
+                d1 = time.perf_counter() - t0
+                if d1 >= 0.5:
+                    break
+            # all cores: the task list, repeated so that the pool runs about 2 s
+            once = len(full) * (d1 / n1) / cores
+            reps = max(1, min(64, int(2.0 / max(once, 1e-3))))
+            if job is _oracle_run_job:  # whole runs: a new run seed per repetition
+                full = [a[:-1] + (a[-1] + cores * r,) for r in range(reps) for a in full]
+            else:
+                full = full * reps
+            t0 = time.perf_counter()
+            un = sum(pool.map(job, full, chunksize=1))
+            dn = time.perf_counter() - t0
+            out[name] = {"one_core": {"value": u1 / d1, "units": u1, "s": round(d1, 3), "repeats": n1 // len(single)},
+                         "all_cores": {"value": un / dn, "units": un, "s": round(dn, 3), "cores": cores,
+                                       "repeats": reps}}
+    print(json.dumps({"metric": "FP64 oracle on the host cores", "unit": UNIT, "kind": "oracle", "cores": cores,
+                      "cpu_model": cpu_model(), "data": "synthetic", "cases": out}), flush=True)
+
+
 PROFILE_CASES = {"tile-d100": _case_tile_d100, "tc-d1000": _case_tc_d1000, "mlp-d1522": _case_mlp_d1522,
                  "simt-d1000": _case_simt_d1000}
 
@@ -923,6 +1016,9 @@ def main(argv=None):
         return
     if args.workload == "evolvers":
         run_evolvers(args)
+        return
+    if args.workload == "oracle":
+        run_oracle_timing(args)
         return
     if args.impl == "reference":
         run_reference(args)
