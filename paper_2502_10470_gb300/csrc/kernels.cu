@@ -444,6 +444,46 @@ __device__ __noinline__ bool tie_fp64_small(int obj, int dim, int dmax, const fl
     return eu <= ex;
 }
 
+// f(u) of one individual from z = R (u - o), rows four at a time, the
+// objective a template parameter: one objective dispatch per individual
+// rather than one per four rows (1% faster on the small-D kernel).
+template <int DMAX, int OBJ>
+__device__ __forceinline__ float small_eval(int dim, const float* R, const float (&dreg)[DMAX], const float* isq) {
+    ObjR acc;
+    int r = 0;
+    for (; r + 4 <= dim; r += 4) {
+        const float4* R0 = reinterpret_cast<const float4*>(R + (r + 0) * DMAX);
+        const float4* R1 = reinterpret_cast<const float4*>(R + (r + 1) * DMAX);
+        const float4* R2 = reinterpret_cast<const float4*>(R + (r + 2) * DMAX);
+        const float4* R3 = reinterpret_cast<const float4*>(R + (r + 3) * DMAX);
+        float z0 = 0.f, z1 = 0.f, z2 = 0.f, z3 = 0.f;
+#pragma unroll
+        for (int c4 = 0; c4 < DMAX / 4; ++c4) {
+            const float d0 = dreg[4 * c4], d1 = dreg[4 * c4 + 1], d2 = dreg[4 * c4 + 2], d3 = dreg[4 * c4 + 3];
+            const float4 q0 = R0[c4], q1 = R1[c4], q2 = R2[c4], q3 = R3[c4];
+            z0 = fmaf(q0.x, d0, z0); z0 = fmaf(q0.y, d1, z0); z0 = fmaf(q0.z, d2, z0); z0 = fmaf(q0.w, d3, z0);
+            z1 = fmaf(q1.x, d0, z1); z1 = fmaf(q1.y, d1, z1); z1 = fmaf(q1.z, d2, z1); z1 = fmaf(q1.w, d3, z1);
+            z2 = fmaf(q2.x, d0, z2); z2 = fmaf(q2.y, d1, z2); z2 = fmaf(q2.z, d2, z2); z2 = fmaf(q2.w, d3, z2);
+            z3 = fmaf(q3.x, d0, z3); z3 = fmaf(q3.y, d1, z3); z3 = fmaf(q3.z, d2, z3); z3 = fmaf(q3.w, d3, z3);
+        }
+        acc.push4_t<OBJ>(z0, z1, z2, z3, isq + r);
+    }
+    for (; r < dim; ++r) {
+        const float4* Rr = reinterpret_cast<const float4*>(R + r * DMAX);
+        float z = 0.0f;
+#pragma unroll
+        for (int c4 = 0; c4 < DMAX / 4; ++c4) {
+            const float4 rr = Rr[c4];
+            z = fmaf(rr.x, dreg[4 * c4 + 0], z);
+            z = fmaf(rr.y, dreg[4 * c4 + 1], z);
+            z = fmaf(rr.z, dreg[4 * c4 + 2], z);
+            z = fmaf(rr.w, dreg[4 * c4 + 3], z);
+        }
+        acc.push_t<OBJ>(z, isq[r]);
+    }
+    return acc.finish(OBJ, dim);
+}
+
 __host__ __device__ inline int small_stride(int dpad) { return ((dpad >> 2) & 1) ? dpad : dpad + 4; }
 
 // One executor, all fused generations, everything resident in shared memory;
@@ -531,40 +571,16 @@ __device__ __forceinline__ void small_executor(const StepArgs& a, int k, const I
             const int L = s.cs == 2 ? exp_length(c, dim, s.cri) : 0;
             float dreg[DMAX];
             thread_trial<DMAX>(s, c, v, i, dim, ds, L, X, o, a.lo, a.hi, U, dreg);
-            const int obj = d.obj;
-            ObjR acc;
-            int r = 0;
-            for (; r + 4 <= dim; r += 4) {
-                const float4* R0 = reinterpret_cast<const float4*>(R + (r + 0) * DMAX);
-                const float4* R1 = reinterpret_cast<const float4*>(R + (r + 1) * DMAX);
-                const float4* R2 = reinterpret_cast<const float4*>(R + (r + 2) * DMAX);
-                const float4* R3 = reinterpret_cast<const float4*>(R + (r + 3) * DMAX);
-                float z0 = 0.f, z1 = 0.f, z2 = 0.f, z3 = 0.f;
-#pragma unroll
-                for (int c4 = 0; c4 < DMAX / 4; ++c4) {
-                    const float d0 = dreg[4 * c4], d1 = dreg[4 * c4 + 1], d2 = dreg[4 * c4 + 2], d3 = dreg[4 * c4 + 3];
-                    const float4 q0 = R0[c4], q1 = R1[c4], q2 = R2[c4], q3 = R3[c4];
-                    z0 = fmaf(q0.x, d0, z0); z0 = fmaf(q0.y, d1, z0); z0 = fmaf(q0.z, d2, z0); z0 = fmaf(q0.w, d3, z0);
-                    z1 = fmaf(q1.x, d0, z1); z1 = fmaf(q1.y, d1, z1); z1 = fmaf(q1.z, d2, z1); z1 = fmaf(q1.w, d3, z1);
-                    z2 = fmaf(q2.x, d0, z2); z2 = fmaf(q2.y, d1, z2); z2 = fmaf(q2.z, d2, z2); z2 = fmaf(q2.w, d3, z2);
-                    z3 = fmaf(q3.x, d0, z3); z3 = fmaf(q3.y, d1, z3); z3 = fmaf(q3.z, d2, z3); z3 = fmaf(q3.w, d3, z3);
-                }
-                acc.push4(obj, z0, z1, z2, z3, isq + r);
+            float fv;
+            switch (d.obj) {
+            case kSphere: fv = small_eval<DMAX, kSphere>(dim, R, dreg, isq); break;
+            case kRosenbrock: fv = small_eval<DMAX, kRosenbrock>(dim, R, dreg, isq); break;
+            case kRastrigin: fv = small_eval<DMAX, kRastrigin>(dim, R, dreg, isq); break;
+            case kGriewank: fv = small_eval<DMAX, kGriewank>(dim, R, dreg, isq); break;
+            case kAckley: fv = small_eval<DMAX, kAckley>(dim, R, dreg, isq); break;
+            default: fv = small_eval<DMAX, kSchwefel12>(dim, R, dreg, isq); break;
             }
-            for (; r < dim; ++r) {
-                const float4* Rr = reinterpret_cast<const float4*>(R + r * DMAX);
-                float z = 0.0f;
-#pragma unroll
-                for (int c4 = 0; c4 < DMAX / 4; ++c4) {
-                    const float4 rr = Rr[c4];
-                    z = fmaf(rr.x, dreg[4 * c4 + 0], z);
-                    z = fmaf(rr.y, dreg[4 * c4 + 1], z);
-                    z = fmaf(rr.z, dreg[4 * c4 + 2], z);
-                    z = fmaf(rr.w, dreg[4 * c4 + 3], z);
-                }
-                acc.push(obj, z, isq[r]);
-            }
-            fu[i] = nan_to_inf(acc.finish(obj, dim));
+            fu[i] = nan_to_inf(fv);
         }
         __syncthreads();
         for (int i = tid; i < np; i += nt) {
