@@ -292,6 +292,20 @@ METADE_API metade_status metade_plan_info(const metade_ctx *ctx, char *buf, size
 METADE_API metade_status metade_profile(metade_ctx *ctx, int32_t enable);
 METADE_API metade_status metade_profile_read(metade_ctx *ctx, double *ms, int64_t *count);
 
+/* Check of the bounded device wait that every mbarrier wait of the
+ * tensor-core pipeline uses (no context needed; runs on the current device,
+ * legacy default stream, synchronously).  One thread initialises an mbarrier
+ * in shared memory for one arrival and waits on its first phase for at most
+ * `rounds` try_wait rounds (0: the pipeline's own limit).  arrive = 1: the
+ * thread arrives first, so the wait completes; arrive = 0: nothing arrives,
+ * so the wait gives up.  *completed (may be NULL) = 1 if the phase completed;
+ * *seconds (may be NULL) = the wait's length in SM clock cycles over the
+ * device's nominal clock rate.  Returns METADE_OK when the wait completed,
+ * METADE_ETIMEOUT when it gave up (the device context stays usable),
+ * METADE_EINVAL for arrive outside {0, 1}, METADE_ENOMEM / METADE_ECUDA on
+ * allocation or runtime failures. */
+METADE_API metade_status metade_wait_check(int32_t arrive, uint32_t rounds, int32_t *completed, double *seconds);
+
 /* Number of kernel launches this context has issued (graph replays count the
  * kernels they contain). */
 METADE_API int64_t metade_launch_count(const metade_ctx *ctx);

@@ -31,7 +31,7 @@ EXPORTED = [
     "metade_init", "metade_inner_step", "metade_eval", "metade_outer_init", "metade_outer_step",
     "metade_outer_generation", "metade_draw_record", "metade_sync", "metade_plan_info",
     "metade_launch_count", "metade_strerror", "metade_plain_step_noalloc", "metade_profile",
-    "metade_profile_read", "metade_autotune",
+    "metade_profile_read", "metade_autotune", "metade_wait_check",
 ]
 
 
@@ -100,6 +100,7 @@ def _lib():
         L.metade_profile.argtypes = [P, I32]
         L.metade_autotune.argtypes = [P, P, P, P, I32]
         L.metade_profile_read.argtypes = [P, P, P]
+        L.metade_wait_check.argtypes = [I32, U32, P, P]
         L.metade_strerror.argtypes = [C.c_int]
         L.metade_strerror.restype = C.c_char_p
         for name in EXPORTED:
@@ -258,6 +259,15 @@ def metade_profile_read(ctx: int):
     n = np.zeros(len(PROFILE_KINDS), dtype=np.int64)
     _check(_lib().metade_profile_read(ctx, ms.ctypes.data, n.ctypes.data), "metade_profile_read")
     return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(PROFILE_KINDS)}
+
+
+def metade_wait_check(arrive: bool, rounds: int = 0):
+    """The tensor-core pipeline's bounded mbarrier wait on its own: returns
+    (status, completed, seconds); status METADE_ETIMEOUT when the wait gave up."""
+    done = C.c_int32(0)
+    sec = C.c_double(0.0)
+    st = _lib().metade_wait_check(int(arrive), int(rounds), C.byref(done), C.byref(sec))
+    return int(st), int(done.value), float(sec.value)
 
 
 def metade_strerror(status: int) -> str:

@@ -1045,4 +1045,29 @@ metade_status metade_profile_read(metade_ctx* c, double* ms, int64_t* count) {
     return METADE_OK;
 }
 
+metade_status metade_wait_check(int32_t arrive, uint32_t rounds, int32_t* completed, double* seconds) {
+    if (arrive != 0 && arrive != 1) return METADE_EINVAL;
+    long long* d = nullptr;
+    int* st = nullptr;
+    if (cudaMalloc(&d, 2 * sizeof(long long)) != cudaSuccess) return METADE_ENOMEM;
+    if (cudaMalloc(&st, sizeof(int)) != cudaSuccess) {
+        cudaFree(d);
+        return METADE_ENOMEM;
+    }
+    long long h[2] = {0, 0};
+    int hs = 0, khz = 0, dev = 0;
+    metade_status r = METADE_OK;
+    if (cudaMemset(d, 0, 2 * sizeof(long long)) || cudaMemset(st, 0, sizeof(int)) ||
+        launch_wait_check(rounds, arrive, d, st, 0) || cudaDeviceSynchronize() ||
+        cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost) || cudaMemcpy(&hs, st, sizeof(int), cudaMemcpyDeviceToHost) ||
+        cudaGetDevice(&dev) || cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev))
+        r = METADE_ECUDA;
+    cudaFree(d);
+    cudaFree(st);
+    if (r != METADE_OK) return r;
+    if (completed) *completed = (int32_t)h[0];
+    if (seconds) *seconds = khz > 0 ? (double)h[1] / (1e3 * khz) : 0.0;
+    return hs ? (metade_status)hs : METADE_OK;
+}
+
 }  // extern "C"

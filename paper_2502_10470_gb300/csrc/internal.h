@@ -86,6 +86,10 @@ struct MlpPlan {
     const float* y;        // targets of every MLP problem ([256][2] at InstDesc.aux)
     int max_dpad;
 };
+// The GEMM pipeline's bounded mbarrier wait on its own (rounds 0: the
+// pipeline's limit); out[0] completed, out[1] SM cycles; timeout latched in *status.
+cudaError_t launch_wait_check(uint32_t rounds, int arrive, long long* out, int* status, cudaStream_t st);
+
 cudaError_t launch_mlp_generation(const StepArgs& a, const MlpPlan& p, cudaStream_t st);
 // f of the rows `rows` (population layout) of every MLP executor into f_out (fitness layout)
 cudaError_t launch_mlp_eval(const InstDesc* desc, const MlpPlan& p, const float* rows, float* f_out, cudaStream_t st);

@@ -42,7 +42,7 @@ constexpr int kEpiWarps = 4 * kParts;                      // each takes kBN / k
 constexpr int kTcThreads = 32 * (kEpiWarps + 1);           // + the producer/MMA warp
 constexpr int kAT = kBM * kBK * 2;                        // 16 KB
 constexpr int kBT = kBN * kBK * 2;                        // 32 KB
-constexpr uint32_t kWaitLimit = 1u << 22;                 // try_wait rounds before giving up (seconds)
+constexpr uint32_t kWaitLimit = 1u << 18;                 // try_wait rounds before giving up: ~1 s (a round waits <= 3.8 us)
 constexpr int kStatusTimeout = 4;                         // METADE_ETIMEOUT
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -56,9 +56,9 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                  : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t rounds = kWaitLimit) {
     const uint32_t addr = smem_u32(bar);
-    for (uint32_t it = 0; it < kWaitLimit; ++it) {
+    for (uint32_t it = 0; it < rounds; ++it) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -169,6 +169,24 @@ __device__ __forceinline__ void obj_compose(int obj, ObjR& a, const ObjR& b, flo
     }
     default: a.s0 += b.s0; break;
     }
+}
+
+// The bounded wait on its own: one thread initialises an mbarrier for one
+// arrival, arrives on it first when `arrive` is set, and waits on phase 0 for
+// at most `rounds` try_wait rounds (every wait of the GEMM pipeline is this
+// loop with kWaitLimit rounds).  out[0] = 1 when the phase completed, else the
+// timeout is latched in *status; out[1] = the SM clock cycles the wait took.
+__global__ void k_wait_check(uint32_t rounds, int arrive, long long* out, int* status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (arrive) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar)) : "memory");
+    const long long t0 = clock64();
+    const bool done = mbar_wait(&bar, 0u, rounds);
+    out[1] = clock64() - t0;
+    out[0] = done ? 1 : 0;
+    if (!done) set_status(status, kStatusTimeout);
 }
 
 struct TcGemmArgs {
@@ -752,6 +770,11 @@ cudaError_t launch_tc_eval(const InstDesc* desc, const TcPlan& p, const float* p
     g.status = status;
     k_rot_tc<<<p.n_tiles, kTcThreads, smem_g, st>>>(p.mapA, p.mapB, p.split ? p.mapAlo : p.mapA, p.split ? p.mapBlo : p.mapB,
                                              g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wait_check(uint32_t rounds, int arrive, long long* out, int* status, cudaStream_t st) {
+    k_wait_check<<<1, 32, 0, st>>>(rounds ? rounds : kWaitLimit, arrive, out, status);
     return cudaGetLastError();
 }
 

@@ -710,3 +710,18 @@ def test_autotune_changes_speed_not_results():
     for k in range(wl.n_inst):
         np.testing.assert_array_equal(outs[0][0][k], outs[1][0][k])
         np.testing.assert_array_equal(outs[0][1][k], outs[1][1][k])
+
+
+# ------------------------------------------------------------ bounded waits
+def test_bounded_wait_gives_up_and_the_context_stays_usable():
+    """The tensor-core pipeline's bounded mbarrier wait, on its own: on a
+    barrier that nothing arrives at it gives up after its rounds with
+    METADE_ETIMEOUT (no fault, no hang), on a completed phase it returns at
+    once, and the device then runs a generation that matches the oracle."""
+    import paper_2502_10470_gb300 as M
+    st, done, sec = M.metade_wait_check(False, 1 << 16)
+    assert st == M.METADE_ETIMEOUT and done == 0 and sec > 0.0
+    st, done, sec1 = M.metade_wait_check(True, 1 << 16)
+    assert st == M.METADE_OK and done == 1 and sec1 < sec
+    assert M.metade_wait_check(2, 1)[0] == M.METADE_EINVAL
+    _step_and_compare(_wl_with_theta(synth.tiny()), 0, fit_inf=False)
