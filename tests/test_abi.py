@@ -29,6 +29,9 @@ def test_library_loads_and_exports_every_declared_symbol():
         assert hasattr(lib, name), name
     assert sorted(M.EXPORTED) == declared_symbols()
     assert M.metade_strerror(M.METADE_EINVAL) == "invalid argument"
+    # host-side argument checks answer before any device call
+    assert M.metade_wait_check(2, 1)[0] == M.METADE_EINVAL
+    assert M.metade_strerror(M.METADE_ETIMEOUT) == "device wait timed out"
 
 
 def test_library_links_no_cpu_fallback():
