@@ -393,7 +393,7 @@ def _two_runs(n_out=8, seed=13):
                           inner_gens=2, outer_gens=2, seed=seed, one_shot=1)
 
 
-@pytest.mark.parametrize("n_out", [8, 9])
+@pytest.mark.parametrize("n_out", [8, 9, 4095, 4096])  # 4096: the largest swarm the pairing holds
 def test_cso_evolver_move_and_select(n_out):
     """CSO evolver: generation 0 evaluates the initial swarm, all flagged; a
     later move pairs each run exactly as the oracle (flags bit-exact: the
