@@ -588,8 +588,14 @@ __device__ __forceinline__ void small_executor(const StepArgs& a, int k, const I
             const float fx = f[i];
             bool take;
             bool same = near_tie(fn, fx, band);
-            if (same)
-                for (int j = 0; j < dim; ++j) same = same && (U[i * ds + j] == X[i * ds + j]);
+            if (same) {  // padding columns are zero in both rows
+                const float4* u4 = reinterpret_cast<const float4*>(U + i * ds);
+                const float4* x4 = reinterpret_cast<const float4*>(X + i * ds);
+                for (int q = 0; q < chunks && same; ++q) {
+                    const float4 p = u4[q], r = x4[q];
+                    same = p.x == r.x && p.y == r.y && p.z == r.z && p.w == r.w;
+                }
+            }
             if (same) {
                 take = true;  // the trial is the target: nothing changes
                 fn = fx;
