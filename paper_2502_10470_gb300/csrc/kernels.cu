@@ -406,10 +406,16 @@ __device__ __noinline__ float diff_small(int obj, int dim, const float* u, const
                                          const float* R) {
     float dx[DMAX], dl[DMAX];
 #pragma unroll
-    for (int c = 0; c < DMAX; ++c) {
-        const bool in = c < dim;
-        dx[c] = in ? x[c] - o[c] : 0.f;
-        dl[c] = in ? u[c] - x[c] : 0.f;
+    for (int c4 = 0; c4 < DMAX / 4; ++c4) {  // whole chunks below dim; padding columns are zero
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+        if (4 * c4 < dim) {
+            const float4 xv = reinterpret_cast<const float4*>(x)[c4], uv = reinterpret_cast<const float4*>(u)[c4];
+            const float4 ov = reinterpret_cast<const float4*>(o)[c4];
+            a = make_float4(xv.x - ov.x, xv.y - ov.y, xv.z - ov.z, xv.w - ov.w);
+            b = make_float4(uv.x - xv.x, uv.y - xv.y, uv.z - xv.z, uv.w - xv.w);
+        }
+        dx[4 * c4] = a.x; dx[4 * c4 + 1] = a.y; dx[4 * c4 + 2] = a.z; dx[4 * c4 + 3] = a.w;
+        dl[4 * c4] = b.x; dl[4 * c4 + 1] = b.y; dl[4 * c4 + 2] = b.z; dl[4 * c4 + 3] = b.w;
     }
     DiffAcc acc;
     diff_init(acc);
