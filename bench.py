@@ -16,7 +16,11 @@ launch, generations fused) next to the plain FP32 path (one executor per
 launch per generation, no graph).
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 oracle on
-the host cores on a bounded sample of the same workload.
+the host cores on a bounded sample of the same workload.  Other studies
+(`--workload`): precision (D 1000 on the tensor cores), batching (512 ragged
+executors), full (8 runs x 128 executors, whole MetaDE runs), mlp (the MLP
+objective), evolvers (DE, PSO, CSO, NES), oracle (the FP64 oracle alone on
+one core and on all host cores).
 """
 from __future__ import annotations
 
