@@ -268,7 +268,8 @@ METADE_API metade_status metade_plain_step_noalloc(float *pop, float *fit, const
 METADE_API metade_status metade_sync(metade_ctx *ctx);
 
 /* Autotuner: for every bucket of the batched path, time each candidate block
- * shape (small-D kernel: 32, 64, 128, 256 threads; general kernel: 128, 256,
+ * shape (small-D kernel: 32, 64, 128, 256 threads; tile kernel: 128 or 256
+ * threads with R^T resident, 256 with R^T streamed; general kernel: 128, 256,
  * 512 threads) on device copies of (pop, fit) for n_gens generations with the
  * given theta, and keep the fastest.  The caller's pop/fit are not modified;
  * the copies are allocated and freed inside the call, which synchronises the
