@@ -1,26 +1,31 @@
 #!/usr/bin/env python3
 """Benchmark of the MetaDE batched inner-DE generation step on GB300.
 
-Workload (the evolver/executor setting of the paper's Sec. IV-A at 20-D):
-six MetaDE runs, one per synthetic shifted-rotated objective (sphere,
-Rosenbrock, Rastrigin, Griewank, Ackley, Schwefel 1.2), D = 20; each run's
-evolver has 100 vectors and each vector drives one executor of population
-100 for 500 generations.  One step = one evolver generation of all six runs
-(Alg. 3): rand/1/bin trials and decoding, executor
-initialisation, 500 executor generations of 600 executors, best-fitness
-reduction, evolver selection = 3.0e7 individual-generations.
+Headline workload (the full MetaDE configuration): eight MetaDE runs of 128
+executors each (1024 concurrent inner DEs).  Per run the population size is
+drawn from U{50..200}, the dimension from {20, 50, 100, 200} and the
+objective from the six synthetic shifted-rotated functions (sphere,
+Rosenbrock, Rastrigin, Griewank, Ackley, Schwefel 1.2).  One step = one
+evolver generation of all eight runs (Alg. 3): rand/1/bin trials and
+decoding, executor initialisation, 200 executor generations, best-fitness
+reduction, evolver selection = 2.6e7 individual-generations.  The batched
+path runs the rotation of every executor with D >= 129 as a BF16 tcgen05 GEMM
+with FP32 accumulation (the width is autotuned) and the rest in FP32.
 
 Metric: individual-generations per second (the paper's FEs per second) and
-the evolver-generation time, for the batched path (all executors in one
-launch, generations fused) next to the plain FP32 path (one executor per
-launch per generation, no graph).
+the evolver-generation time, for the batched mixed-precision path next to
+the plain FP32 path (one executor per launch per generation, no graph, no
+tuning).  The line also carries the FP64 final error of every run's best
+individual, and the moderate workload (six runs x 100 executors x NP 100 x
+D 20, 500 generations) with both selection-tie modes as a secondary key.
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 oracle on
 the host cores on a bounded sample of the same workload.  Other studies
-(`--workload`): precision (D 1000 on the tensor cores), batching (512 ragged
-executors), full (8 runs x 128 executors, whole MetaDE runs), mlp (the MLP
-objective), evolvers (DE, PSO, CSO, NES), oracle (the FP64 oracle alone on
-one core and on all host cores).
+(`--workload`): moderate (the D 20 workload alone), precision (D 1000 on the
+tensor cores), batching (512 ragged executors), full (whole MetaDE runs),
+equal_error (batched mixed precision vs plain FP32 over 31 seeds), mlp (the
+MLP objective), evolvers (DE, PSO, CSO, NES), oracle (the FP64 oracle alone
+on one core and on all host cores).
 """
 from __future__ import annotations
 
@@ -39,9 +44,12 @@ if ROOT not in sys.path:
 
 METRIC = "inner-DE individual-gens/s & outer-gen time: batched+BF16 vs plain FP32"
 UNIT = "individual-gens/s"
-WORKLOAD = "moderate-6x100x100xD20"
-INNER_GENS = 500
-CPU_SAMPLE_PER_RUN = 20  # executors per run timed on the host (of 100)
+WORKLOAD = "full-8x128-ragged"
+INNER_GENS = 200
+MODERATE = "moderate-6x100x100xD20"
+MODERATE_GENS = 500
+CPU_SAMPLE_PER_RUN = 2  # executors per run of the full workload timed on the host (of 128)
+ERROR_FLOOR = 1e-8      # final errors below this are reported as 0 (Sec. IV-A)
 
 
 def parse_args(argv=None):
@@ -53,13 +61,19 @@ def parse_args(argv=None):
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison arm")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--inner-gens", type=int, default=INNER_GENS)
-    ap.add_argument("--workload", default="moderate",
-                    choices=["moderate", "precision", "batching", "full", "mlp", "evolvers", "oracle"],
-                    help="moderate: the headline workload; precision: the D=1000 precision study; batching: "
-                         "512 ragged executors; full: 8 MetaDE runs x 128 executors; evolvers: whole MetaDE "
-                         "runs of the full workload with each evolver (DE, PSO, CSO, NES); oracle: the FP64 "
-                         "oracle alone on the host cores (one core and all cores) on the tiny, moderate, "
-                         "batching and precision workloads")
+    ap.add_argument("--workload", default="headline",
+                    choices=["headline", "moderate", "precision", "batching", "full", "equal_error", "mlp",
+                             "evolvers", "oracle"],
+                    help="headline: the full workload, batched mixed precision vs plain FP32 (the JSON line "
+                         "of the benchmark contract); moderate: 6 runs x 100 executors, D 20; precision: the "
+                         "D=1000 precision study; batching: 512 ragged executors; full: whole MetaDE runs of "
+                         "the full workload; equal_error: batched mixed precision vs plain FP32 over 31 seeds "
+                         "at an equal FE budget; evolvers: whole MetaDE runs with each evolver (DE, PSO, CSO, "
+                         "NES); oracle: the FP64 oracle alone on the host cores (one core and all cores) on "
+                         "the tiny, moderate, batching and precision workloads")
+    ap.add_argument("--outer-gens", type=int, default=3, help="evolver generations per run of equal_error")
+    ap.add_argument("--eq-seeds", type=int, default=31, help="seeds of equal_error")
+    ap.add_argument("--no-moderate", action="store_true", help="skip the moderate secondary key")
     ap.add_argument("--seeds", type=int, default=5, help="whole MetaDE runs of the full workload")
     ap.add_argument("--n-inst", type=int, default=64, help="executors of the precision study")
     ap.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES),
@@ -133,13 +147,14 @@ def time_oracle(tasks, cores: int, job=_oracle_job):
     return units, dt
 
 
-def cpu_baseline(wl, gens: int):
+def cpu_baseline(wl, gens: int, per_run: int = CPU_SAMPLE_PER_RUN):
     cores = os.cpu_count() or 1
-    tasks = oracle_tasks(wl, CPU_SAMPLE_PER_RUN, gens)
+    tasks = oracle_tasks(wl, per_run, gens)
     units, dt = time_oracle(tasks, cores)
     return {"value": units / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%d executors (%d per run) x NP 100 x %d generations of the %s workload, FP64 C oracle, "
-                      "%d spawn processes, %.1f s wall" % (len(tasks), CPU_SAMPLE_PER_RUN, gens, WORKLOAD, cores, dt)}
+            "sample": "%d executors (%d per run, the first of the evolver's first generation) x %d generations "
+                      "of the %s workload (%d individual-generations), FP64 C oracle, %d spawn processes, %.1f s "
+                      "wall" % (len(tasks), per_run, gens, wl.name, units, cores, dt)}
 
 
 def run_reference(args):
@@ -147,7 +162,7 @@ def run_reference(args):
     if rank != 0:
         return
     import synth
-    wl = synth.moderate(inner_gens=args.inner_gens)
+    wl = synth.full(inner_gens=args.inner_gens)
     cores = os.cpu_count() or 1
     per_run = -(-cores // len(wl.problems))  # every core busy in each step
     tasks = oracle_tasks(wl, per_run, args.inner_gens)
@@ -170,7 +185,8 @@ def run_reference(args):
             "data": "synthetic", "config": {"workload": WORKLOAD, "inner_gens": args.inner_gens,
                                              "sample_executors_per_step": len(tasks)},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "%d executors x NP 100 x %d generations per step" % (len(tasks), args.inner_gens)},
+                             "sample": "%d executors (%d per run, NP of their run) x %d generations per step"
+                                       % (len(tasks), per_run, args.inner_gens)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -258,17 +274,207 @@ def alu_ops(theta, inst_np, dims):
     return float((per * np.asarray(inst_np, dtype=np.float64)).sum())
 
 
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def measure_moderate(args, dev, stream, rank, world, tie_fp64=0, steps=None, e2e=False, plain=False):
+    """The moderate workload (6 runs x 100 executors x NP 100 x D 20, 500
+    generations per evolver generation; the small-D kernel keeps every
+    executor in shared memory): batched steps timed with CUDA events after an
+    L2 flush, the roofline of k_fused_small<20> (ALU-bound: alu_ops lane
+    operations per launch over its event time, against 152 SMs x 128 lanes x
+    the maximum SM clock).  Optionally e2e through the graph call with host
+    copies, and the plain FP32 arm (one step)."""
+    import torch
+    import torch.distributed as dist
+    import paper_2502_10470_gb300 as M
+    import synth
+    gens = MODERATE_GENS
+    steps = steps or args.steps
+    wl = synth.moderate(inner_gens=gens)
+    probs = [(p.dim, p.obj, p.shift, p.rot) for p in wl.problems]
+
+    def make(path):
+        return M.Batch(probs, wl.inst_np, wl.inst_prob, wl.inst_group, seed=wl.seed + rank, one_shot=1,
+                       n_out=wl.n_out, path=path, device=dev, stream=stream.cuda_stream, tie_fp64=tie_fp64)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    def step(batch, og):
+        M.metade_outer_step(batch.ctx, batch.opop, batch.ofit, batch.trial, batch.theta, None, og, 0)
+        M.metade_init(batch.ctx, batch.pop, batch.fit, 0)
+        M.metade_inner_step(batch.ctx, batch.pop, batch.fit, batch.theta, 0, 0, gens, batch.best_f, batch.best_i)
+        M.metade_outer_step(batch.ctx, batch.opop, batch.ofit, batch.trial, batch.theta, batch.best_f, og, 1)
+
+    b = make(M.METADE_PATH_BATCHED)
+    M.metade_outer_init(b.ctx, b.opop, b.ofit)
+    M.metade_outer_step(b.ctx, b.opop, b.ofit, b.trial, b.theta, None, 0, 0)
+    M.metade_init(b.ctx, b.pop, b.fit, 0)
+    M.metade_autotune(b.ctx, b.pop, b.fit, b.theta, 20)
+    units = float(wl.inst_np.sum()) * gens
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    og = 0
+    for _ in range(args.warmup):
+        step(b, og)
+        og += 1
+    if M.metade_sync(b.ctx) != 0:
+        raise RuntimeError("device status after warm-up")
+    barrier()
+    M.metade_profile(b.ctx, True)
+    M.metade_profile_read(b.ctx)
+    evs, thetas = [], []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(b, og)
+        e1.record(stream)
+        evs.append((e0, e1))
+        thetas.append(b.theta.clone())
+        og += 1
+    barrier()
+    prof = M.metade_profile_read(b.ctx)
+    M.metade_profile(b.ctx, False)
+    total = sum(a.elapsed_time(c) for a, c in evs)
+    total_max = max_over_ranks(total, world, dev)
+    kern = prof["fused_small"][0] / max(1, prof["fused_small"][1])
+    ops = sum(alu_ops(th.cpu().numpy(), wl.inst_np, b.dims) * gens for th in thetas) / steps
+    sm_max = float(load_peaks().get("sm_max_mhz", 2070.0))
+    peak_ops = 152 * 128 * sm_max * 1e6
+    out = {"workload": wl.name, "tie_fp64": tie_fp64, "value": whole_job_rate(units, steps, world, total_max),
+           "unit": UNIT, "ms_per_step": total_max / steps, "steps": steps,
+           "roofline": {"bound": "alu", "kernel": "k_fused_small<20>", "achieved": ops / (kern / 1e3) / 1e9,
+                        "peak": peak_ops / 1e9, "unit": "Gop/s", "frac": ops / (kern / 1e3) / peak_ops,
+                        "kernel_ms": kern, "kernel_share": kern * steps / total,
+                        "peak_source": "152 SMs x 128 lanes x %.0f MHz (max SM clock), of derived peak" % sm_max}}
+    if e2e:
+        out["e2e"] = measure_e2e(b, wl, gens, og, steps, dev, stream, world, units)
+    if plain:
+        p = make(M.METADE_PATH_PLAIN)
+        M.metade_outer_init(p.ctx, p.opop, p.ofit)
+        M.metade_outer_step(p.ctx, p.opop, p.ofit, p.trial, p.theta, None, 0, 0)
+        M.metade_init(p.ctx, p.pop, p.fit, 0)
+        M.metade_inner_step(p.ctx, p.pop, p.fit, p.theta, 0, 0, 1, None, None)  # warm-up
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = M.metade_launch_count(p.ctx)
+        e0.record(stream)
+        step(p, 1)
+        e1.record(stream)
+        barrier()
+        pms = e0.elapsed_time(e1)
+        out["plain_fp32"] = {"value": units / (pms / 1000.0), "unit": UNIT, "ms_per_step": pms, "steps": 1,
+                             "gpu_launches": M.metade_launch_count(p.ctx) - l0,
+                             "path": "one cooperative launch per executor per generation, FP32, no graph"}
+        p.close()
+    out["plan"] = json.loads(M.metade_plan_info(b.ctx))
+    b.close()
+    return out
+
+
+def measure_e2e(b, wl, gens, og, steps, dev, stream, world, units):
+    """End to end through the public call a user makes, metade_outer_generation
+    (one CUDA graph per evolver generation): every step copies the evolver
+    state host -> device from pinned memory and reads the meta-fitness and the
+    evolver fitness back device -> host, inside the timed region."""
+    import torch
+    import paper_2502_10470_gb300 as M
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    h_opop = b.opop.cpu().pin_memory()
+    h_ofit = b.ofit.cpu().pin_memory()
+    h_best = torch.empty_like(b.best_f, device="cpu").pin_memory()
+    h_ofit_out = torch.empty_like(b.ofit, device="cpu").pin_memory()
+    M.metade_outer_generation(b.ctx, b.opop, b.ofit, b.trial, b.theta, b.pop, b.fit, b.best_f, b.best_i, og,
+                              gens, True)  # capture the graph before timing
+    og += 1
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.opop.copy_(h_opop, non_blocking=True)
+        b.ofit.copy_(h_ofit, non_blocking=True)
+        M.metade_outer_generation(b.ctx, b.opop, b.ofit, b.trial, b.theta, b.pop, b.fit, b.best_f, b.best_i, og,
+                                  gens, True)
+        h_best.copy_(b.best_f, non_blocking=True)
+        h_ofit_out.copy_(b.ofit, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        og += 1
+    if M.metade_sync(b.ctx) != 0:
+        raise RuntimeError("device status after the e2e steps")
+    tot = max_over_ranks(sum(ms), world, dev)
+    return {"value": whole_job_rate(units, steps, world, tot), "unit": UNIT,
+            "h2d_bytes_per_step": (h_opop.numel() + h_ofit.numel()) * 4,
+            "d2h_bytes_per_step": (h_best.numel() + h_ofit_out.numel()) * 4,
+            "ms_per_step": tot / steps, "call": "metade_outer_generation (CUDA graph)"}
+
+
+def final_errors(b, wl):
+    """FP64 final error f(x_best) - f* (f* = 0) of every run's best
+    individual after the last evolver generation (Sec. IV-A; values below
+    1e-8 reported as 0), through metade_eval on caller-given points, with the
+    stored fitness of the same individual next to it."""
+    import numpy as np
+    import torch
+    import paper_2502_10470_gb300 as M
+    bf = b.best_f.cpu().numpy()
+    bi = b.best_i.cpu().numpy()
+    ldx = int(np.max(b.dpad))
+    pts, inst, stored = [], [], []
+    pop = b.pop.cpu().numpy()
+    for g in range(wl.n_groups):
+        ks = np.arange(g * wl.n_out, (g + 1) * wl.n_out)
+        k = int(ks[np.argmin(bf[ks])])
+        dp = int(b.dpad[k])
+        row = pop[b.pop_off[k] + int(bi[k]) * dp:b.pop_off[k] + (int(bi[k]) + 1) * dp]
+        x = np.zeros(ldx, dtype=np.float32)
+        x[:dp] = row
+        pts.append(x)
+        inst.append(k)
+        stored.append(float(bf[k]))
+    xd = torch.from_numpy(np.stack(pts)).to(b.device)
+    idd = torch.tensor(inst, dtype=torch.int32, device=b.device)
+    f64 = torch.zeros(len(inst), dtype=torch.float64, device=b.device)
+    M.metade_eval(b.ctx, xd, len(inst), idd, ldx, M.METADE_FP64, f64)
+    if M.metade_sync(b.ctx) != 0:
+        raise RuntimeError("device status after metade_eval")
+    f64 = f64.cpu().numpy()
+    err = [0.0 if v < ERROR_FLOOR else float(v) for v in f64]
+    rel = [abs(s - v) / abs(v) if v != 0 else abs(s) for s, v in zip(stored, f64)]
+    return {"per_run": err, "median": float(np.median(err)), "stored_rel_err_vs_fp64_max": float(max(rel)),
+            "problems": [{"dim": p.dim, "obj": synth_name(p.obj)} for p in wl.problems],
+            "how": "metade_eval(FP64) at each run's best individual after the last timed evolver generation; "
+                   "< 1e-8 reported as 0"}
+
+
+def synth_name(obj):
+    import synth
+    return synth.OBJ_NAMES[obj]
+
+
 def run_ours(args):
+    """The headline line: the full workload, batched mixed precision."""
     import numpy as np
     import torch
     import torch.distributed as dist
 
     rank, world, local = dist_env()
     import synth
-    wl = synth.moderate(inner_gens=args.inner_gens)
+    wl = synth.full(inner_gens=args.inner_gens)
+    gens = args.inner_gens
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(wl, args.inner_gens)  # before the first GPU call (spawn pool)
+        cpu = cpu_baseline(wl, gens)  # before the first GPU call (spawn pool)
 
     torch.cuda.set_device(local)
     if world > 1:
@@ -278,40 +484,32 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     probs = [(p.dim, p.obj, p.shift, p.rot) for p in wl.problems]
 
-    def make(path):
+    def make(path, prec):
         return M.Batch(probs, wl.inst_np, wl.inst_prob, wl.inst_group, seed=wl.seed + rank, one_shot=1,
-                       n_out=wl.n_out, path=path, device=dev, stream=stream.cuda_stream)
-
-    b = make(M.METADE_PATH_BATCHED)
-    M.metade_outer_init(b.ctx, b.opop, b.ofit)
-    units_per_step = float(wl.inst_np.sum()) * args.inner_gens
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+                       n_out=wl.n_out, path=path, prec=prec, device=dev, stream=stream.cuda_stream)
 
     def barrier():
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
 
-    kernel_ev = []
-
-    def step(batch, og, events):
+    def step(batch, og):
         M.metade_outer_step(batch.ctx, batch.opop, batch.ofit, batch.trial, batch.theta, None, og, 0)
         M.metade_init(batch.ctx, batch.pop, batch.fit, 0)
-        if events is not None:
-            events[0].record(stream)
-        M.metade_inner_step(batch.ctx, batch.pop, batch.fit, batch.theta, 0, 0, args.inner_gens, batch.best_f,
-                            batch.best_i)
-        if events is not None:
-            events[1].record(stream)
+        M.metade_inner_step(batch.ctx, batch.pop, batch.fit, batch.theta, 0, 0, gens, batch.best_f, batch.best_i)
         M.metade_outer_step(batch.ctx, batch.opop, batch.ofit, batch.trial, batch.theta, batch.best_f, og, 1)
 
-    # autotune the block shapes on a real state: the first evolver generation's executors
+    b = make(M.METADE_PATH_BATCHED, M.METADE_BF16)
+    M.metade_outer_init(b.ctx, b.opop, b.ofit)
+    units = float(wl.inst_np.sum()) * gens
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    # autotune (tensor-core width, block shapes) on a real state: the first evolver generation's executors
     M.metade_outer_step(b.ctx, b.opop, b.ofit, b.trial, b.theta, None, 0, 0)
     M.metade_init(b.ctx, b.pop, b.fit, 0)
-    M.metade_autotune(b.ctx, b.pop, b.fit, b.theta, 20)
+    M.metade_autotune(b.ctx, b.pop, b.fit, b.theta, 5)
     og = 0
     for _ in range(args.warmup):
-        step(b, og, None)
+        step(b, og)
         og += 1
     if M.metade_sync(b.ctx) != 0:
         raise RuntimeError("device status after warm-up")
@@ -321,14 +519,14 @@ def run_ours(args):
     launches0 = M.metade_launch_count(b.ctx)
     M.metade_profile(b.ctx, True)
     M.metade_profile_read(b.ctx)
-    step_ev, thetas = [], []
-    for s in range(args.steps):
+    evs, thetas = [], []
+    for _ in range(args.steps):
         flush.zero_()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-        ev[0].record(stream)
-        step(b, og, (ev[1], ev[2]))
-        ev[3].record(stream)
-        step_ev.append(ev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(b, og)
+        e1.record(stream)
+        evs.append((e0, e1))
         thetas.append(b.theta.clone())
         og += 1
     barrier()
@@ -336,98 +534,225 @@ def run_ours(args):
     clocks = sampler.stop()
     prof = M.metade_profile_read(b.ctx)
     M.metade_profile(b.ctx, False)
-    step_ms = [e[0].elapsed_time(e[3]) for e in step_ev]
-    kern_ms = [prof["fused_small"][0] / max(1, prof["fused_small"][1])] * args.steps
-    total_ms = sum(step_ms)
-    total_max = max_over_ranks(total_ms, world, dev)
-    value = whole_job_rate(units_per_step, args.steps, world, total_max)
-    ops = [alu_ops(th.cpu().numpy(), wl.inst_np, b.dims) * args.inner_gens for th in thetas]
-    achieved = sum(ops) / (sum(kern_ms) / 1000.0)
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_ops = 152 * 128 * sm_max * 1e6  # FP32/INT lanes x max SM clock
-
-    # end to end through the public call: pinned host state in, meta-fitness out
-    h_opop = b.opop.cpu().pin_memory()
-    h_ofit = b.ofit.cpu().pin_memory()
-    h_best = torch.empty_like(b.best_f, device="cpu").pin_memory()
-    h_ofit_out = torch.empty_like(b.ofit, device="cpu").pin_memory()
-    M.metade_outer_generation(b.ctx, b.opop, b.ofit, b.trial, b.theta, b.pop, b.fit, b.best_f, b.best_i, og,
-                              args.inner_gens, True)  # capture the graph before timing
-    og += 1
-    barrier()
-    e2e_ms = []
-    for s in range(args.steps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        b.opop.copy_(h_opop, non_blocking=True)
-        b.ofit.copy_(h_ofit, non_blocking=True)
-        M.metade_outer_generation(b.ctx, b.opop, b.ofit, b.trial, b.theta, b.pop, b.fit, b.best_f, b.best_i, og,
-                                  args.inner_gens, True)
-        h_best.copy_(b.best_f, non_blocking=True)
-        h_ofit_out.copy_(b.ofit, non_blocking=True)
-        e1.record(stream)
-        e1.synchronize()
-        e2e_ms.append(e0.elapsed_time(e1))
-        og += 1
-    barrier()
     if M.metade_sync(b.ctx) != 0:
         raise RuntimeError("device status after timing")
-    e2e_value = whole_job_rate(units_per_step, args.steps, world, max_over_ranks(sum(e2e_ms), world, dev))
-    h2d = (h_opop.numel() + h_ofit.numel()) * 4
-    d2h = (h_best.numel() + h_ofit_out.numel()) * 4
+    total = sum(a.elapsed_time(c) for a, c in evs)
+    total_max = max_over_ranks(total, world, dev)
+    value = whole_job_rate(units, args.steps, world, total_max)
+    plan = json.loads(M.metade_plan_info(b.ctx))
+    kernels = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+               for k, v in prof.items() if v[1]}
+    roof = rooflines(wl, b, plan, prof, thetas, gens, args.steps, total, clocks)
+    fe = final_errors(b, wl)
+    e2e = measure_e2e(b, wl, gens, og + 1, args.steps, dev, stream, world, units)
+    b.close()
 
     plain = None
     if not args.no_plain:
-        p = make(M.METADE_PATH_PLAIN)
+        p = make(M.METADE_PATH_PLAIN, M.METADE_FP32)
         M.metade_outer_init(p.ctx, p.opop, p.ofit)
-        step(p, 0, None)  # warm-up
+        M.metade_outer_step(p.ctx, p.opop, p.ofit, p.trial, p.theta, None, 0, 0)
+        M.metade_init(p.ctx, p.pop, p.fit, 0)
+        M.metade_inner_step(p.ctx, p.pop, p.fit, p.theta, 0, 0, 1, None, None)  # warm-up: one generation
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         l0 = M.metade_launch_count(p.ctx)
         e0.record(stream)
-        step(p, 1, None)
+        step(p, 1)
         e1.record(stream)
         barrier()
         pms = e0.elapsed_time(e1)
-        plain = {"value": units_per_step / (pms / 1000.0), "unit": UNIT, "ms_per_step": pms, "steps": 1,
+        plain = {"value": units / (pms / 1000.0), "unit": UNIT, "ms_per_step": pms, "steps": 1,
                  "gpu_launches": M.metade_launch_count(p.ctx) - l0,
-                 "path": "one executor per launch per generation, FP32, no graph"}
+                 "path": "one cooperative launch per executor per generation, FP32, no graph, no tuning"}
         p.close()
 
-    plan = json.loads(M.metade_plan_info(b.ctx))
+    moderate = None
+    if not args.no_moderate:
+        ms = min(args.steps, 20)
+        moderate = measure_moderate(args, dev, stream, rank, world, tie_fp64=0, steps=ms)
+        lit = measure_moderate(args, dev, stream, rank, world, tie_fp64=1, steps=ms)
+        moderate["tie_fp64"] = {"value": lit["value"], "ms_per_step": lit["ms_per_step"],
+                                "kernel_ms": lit["roofline"]["kernel_ms"],
+                                "ties": "FP64 re-evaluation of both vectors"}
+        moderate.pop("plan", None)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "runs": len(wl.problems), "evolver_pop": wl.n_out,
-                           "executor_pop": 100, "dim": 20, "inner_gens": args.inner_gens,
+                "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "runs": wl.n_groups, "evolver_pop": wl.n_out,
+                           "executors": wl.n_inst, "individuals": wl.individuals(),
+                           "executor_pop": "U{50..200} per run", "dims": [p.dim for p in wl.problems],
+                           "objectives": [synth_name(p.obj) for p in wl.problems],
+                           "inner_gens": gens, "precision": "BF16 tcgen05 rotation GEMM (FP32 accumulate) for "
+                           "D >= tc_min_dim, FP32 below; FP32 difference form for near ties",
+                           "tc_min_dim": plan.get("tc_min_dim"),
                            "parallelism": "replicas" if world > 1 else "single",
-                           "l2": "flushed (256 MB write) before every timed step",
-                           "plan": plan},
+                           "l2": "flushed (256 MB write) before every timed step", "plan": plan},
                 "outer_gen_ms": total_max / args.steps,
-                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                        "ms_per_step": sum(e2e_ms) / len(e2e_ms), "call": "metade_outer_generation (CUDA graph)"},
+                "e2e": e2e,
                 "gpu_launches": launches,
-                "roofline": {"bound": "alu", "kernel": "k_fused_small<20>", "achieved": achieved / 1e9,
-                             "peak": peak_ops / 1e9, "unit": "Gop/s", "frac": achieved / peak_ops,
-                             "traffic": SMALL_KERNEL_DRAM_BYTES, "traffic_unit": "bytes per launch",
-                             "kernel_ms": sum(kern_ms) / len(kern_ms),
-                             "kernel_share": sum(kern_ms) / total_ms,
-                             "peak_source": "152 SMs x 128 lanes x %.0f MHz (max SM clock)" % sm_max},
+                "roofline": roof[0],
+                "roofline_by_kernel": roof[1],
+                "kernels": kernels,
+                "final_error": fe,
                 "plain_fp32": plain,
                 "speedup_vs_plain": (value / plain["value"]) if plain else None,
+                "moderate": moderate,
                 "cpu_baseline": cpu,
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
-    b.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def rooflines(wl, b, plan, prof, thetas, gens, steps, total_ms, clocks):
+    """Roofline of each measured kernel kind of the step, and the dominant one
+    (largest share of the step).  ALU-bound fused kernels (small-D, tile):
+    alu_ops lane operations of their executors over their event time, against
+    152 SMs x 128 lanes x the maximum SM clock.  The tensor-core GEMM: 2 NP D^2
+    algorithmic flops per executor-generation over its event time, against the
+    measured BF16 peak (sustained: it runs inside a long step).  The trial and
+    selection kernels of the tensor-core path are HBM/L2-bound: their
+    algorithmic bytes per generation (trial: read the target row, write the
+    FP32 trial row and the BF16 operand row; selection: read both rows, write
+    the accepted ones -- counted as all) over their time, against the measured
+    copy bandwidth."""
+    import numpy as np
+    peaks = load_peaks()
+    sm_max = float((clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = 152 * 128 * sm_max * 1e6
+    bf16_peak = float(peaks.get("bf16_tflops_sustained", 1700.0)) * 1e12
+    hbm = float(peaks.get("hbm_gbs", 6800.0)) * 1e9
+    dims = b.dims
+    on_tc = np.zeros(b.n_inst, dtype=bool)
+    tcmin = plan.get("tc_min_dim") or 129
+    if "tensor_core" in plan:
+        on_tc = dims >= tcmin
+    small = dims <= 32
+    tile = ~small & ~on_tc
+    dpads = (dims + 3) // 4 * 4
+    th = [t.cpu().numpy() for t in thetas]
+    out = {}
+
+    def alu(kind, mask, name):
+        if not prof[kind][1] or not mask.any():
+            return
+        ms = prof[kind][0]
+        ops = sum(alu_ops(t[mask], wl.inst_np[mask], dims[mask]) * gens for t in th)
+        out[name] = {"bound": "alu", "achieved": ops / (ms / 1e3) / 1e9, "peak": alu_peak / 1e9, "unit": "Gop/s",
+                     "frac": ops / (ms / 1e3) / alu_peak, "ms_per_step": ms / steps,
+                     "share": ms / total_ms,
+                     "peak_source": "152 SMs x 128 lanes x %.0f MHz (max SM clock), of derived peak" % sm_max}
+
+    alu("fused_small", small, "k_fused_small")
+    alu("fused_tile", tile & (dpads <= 128), "k_fused_tile")
+    alu("fused_tile_stream", tile & (dpads > 128), "k_fused_tile_stream")
+    if on_tc.any() and prof["tc_gemm"][1]:
+        rows = wl.inst_np[on_tc].astype(np.float64)
+        dd = dims[on_tc].astype(np.float64)
+        flops = 2.0 * float((rows * dd * dd).sum())  # per generation
+        ms = prof["tc_gemm"][0] / prof["tc_gemm"][1]
+        out["k_rot_tc"] = {"bound": "tensor", "achieved": flops / (ms / 1e3) / 1e12, "peak": bf16_peak / 1e12,
+                           "unit": "TFLOP/s", "frac": flops / (ms / 1e3) / bf16_peak,
+                           "ms_per_step": prof["tc_gemm"][0] / steps, "share": prof["tc_gemm"][0] / total_ms,
+                           "launch_ms": ms, "flops_per_launch": flops,
+                           "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained, of measured"}
+        dpad = (dd + 3) // 4 * 4
+        kp = np.ceil(dd / 64) * 64
+        for kind, name, per_row in (("tc_trial", "k_tc_trial", 4 * dpad + 4 * dpad + 2 * kp),
+                                    ("tc_select", "k_tc_select", 4 * dpad + 4 * dpad + 4 * dpad + 12)):
+            if not prof[kind][1]:
+                continue
+            byts = float((rows * per_row).sum())
+            ms = prof[kind][0] / prof[kind][1]
+            out[name] = {"bound": "hbm", "achieved": byts / (ms / 1e3) / 1e9, "peak": hbm / 1e9, "unit": "GB/s",
+                         "frac": byts / (ms / 1e3) / hbm, "ms_per_step": prof[kind][0] / steps,
+                         "share": prof[kind][0] / total_ms, "launch_ms": ms, "bytes_per_launch": byts,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs, of measured"}
+    dom = max(out.items(), key=lambda kv: kv[1]["share"]) if out else (None, {})
+    head = dict(dom[1])
+    head["kernel"] = dom[0]
+    head["traffic"] = None
+    return head, out
+
+
+def run_moderate(args):
+    """The moderate workload alone (6 runs x 100 executors x NP 100 x D 20,
+    500 generations per evolver generation), with e2e and the plain arm."""
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    out = measure_moderate(args, dev, stream, rank, world, tie_fp64=0, e2e=True, plain=not args.no_plain)
+    out["metric"] = METRIC
+    out["warmup"] = args.warmup
+    print(json.dumps(out), flush=True)
+
+
+def run_equal_error(args):
+    """The metric's comparison at an equal FE budget on the full workload:
+    whole MetaDE runs (--outer-gens evolver generations of 200 executor
+    generations, one-shot evaluation) over --eq-seeds seeds, with the batched
+    mixed-precision path (BF16 GEMM for D >= 129, FP32 below), the batched
+    FP32 path and the plain FP32 path (one executor per launch per
+    generation).  Per run and arm: the median over seeds of the run's best
+    meta-fitness (the evolver's stored y*) and of the FP64 final error of the
+    last evolver generation's best individual (metade_eval, < 1e-8 as 0), and
+    the Wilcoxon rank-sum p-value against plain FP32 (Sec. IV-A's test at
+    0.05).  Also the wall time of one whole run per arm."""
+    import numpy as np
+    import torch
+    import paper_2502_10470_gb300 as M
+    import synth
+    from scipy.stats import ranksums
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    wl = synth.full()
+    probs = [(p.dim, p.obj, p.shift, p.rot) for p in wl.problems]
+    gens = wl.inner_gens
+    arms = (("batched_bf16", M.METADE_PATH_BATCHED, M.METADE_BF16),
+            ("batched_fp32", M.METADE_PATH_BATCHED, M.METADE_FP32),
+            ("plain_fp32", M.METADE_PATH_PLAIN, M.METADE_FP32))
+    res = {}
+    for name, path, prec in arms:
+        ystar, ferr, wall = [], [], []
+        for seed in range(args.eq_seeds):
+            b = M.Batch(probs, wl.inst_np, wl.inst_prob, wl.inst_group, seed=seed, one_shot=1, n_out=wl.n_out,
+                        path=path, prec=prec, device=dev, stream=stream.cuda_stream, tc_min_dim=129)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, ofit = b.run_metade(args.outer_gens, gens, use_graph=path == M.METADE_PATH_BATCHED)
+            wall.append(time.perf_counter() - t0)
+            ystar.append(ofit.min(axis=1).astype(np.float64))
+            ferr.append(np.array(final_errors(b, wl)["per_run"]))
+            b.close()
+        res[name] = {"ystar": np.array(ystar), "ferr": np.array(ferr), "wall_s_per_run": float(np.median(wall))}
+    out = {}
+    trunc = lambda a: np.where(a < ERROR_FLOOR, 0.0, a)
+    for name, _, _ in arms:
+        r = res[name]
+        out[name] = {"wall_s_per_metade_run": r["wall_s_per_run"],
+                     "ystar_median_per_run": [float(v) for v in np.median(trunc(r["ystar"]), axis=0)],
+                     "final_error_fp64_median_per_run": [float(v) for v in np.median(r["ferr"], axis=0)]}
+        if name != "plain_fp32":
+            pv = [float(ranksums(trunc(r["ystar"][:, g]), trunc(res["plain_fp32"]["ystar"][:, g]))[1])
+                  for g in range(wl.n_groups)]
+            pf = [float(ranksums(r["ferr"][:, g], res["plain_fp32"]["ferr"][:, g])[1]) for g in range(wl.n_groups)]
+            out[name]["ranksum_p_vs_plain_ystar"] = pv
+            out[name]["ranksum_p_vs_plain_final_error"] = pf
+            out[name]["runs_different_at_0.05"] = int(sum(1 for v in pf if v < 0.05))
+    line = {"metric": "equal-FE-budget comparison: median final error, batched mixed precision vs plain FP32",
+            "workload": wl.name, "seeds": args.eq_seeds, "outer_gens": args.outer_gens,
+            "inner_gens_per_outer_generation": gens,
+            "fe_per_run": [int(wl.inst_np[g * wl.n_out]) * wl.n_out * gens * args.outer_gens
+                           for g in range(wl.n_groups)],
+            "problems": [{"dim": p.dim, "obj": synth_name(p.obj)} for p in wl.problems],
+            "results": out}
+    print(json.dumps(line), flush=True)
 
 
 # ------------------------------------------------------- precision study
@@ -460,7 +785,7 @@ def run_precision(args):
     pop0, fit0 = ref.pop.clone(), ref.fit.clone()
     n = ref.n_indiv
     f64x = torch.empty(n, dtype=torch.float64, device=dev)
-    M.metade_eval(ref.ctx, pop0, M.METADE_FP64, f64x)
+    M.metade_eval_pop(ref.ctx, pop0, M.METADE_FP64, f64x)
     ident = np.tile(np.array([0.0, 1.0, 4, 4, 1, 1], dtype=np.float32), (wl.n_inst, 1))  # trial = target
     inf = torch.full_like(fit0, float("inf"))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -480,7 +805,7 @@ def run_precision(args):
         M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 0, 1, None, None)
         fxp = b.fit.clone()
         f64u = torch.empty(n, dtype=torch.float64, device=dev)
-        M.metade_eval(ref.ctx, trial, M.METADE_FP64, f64u)
+        M.metade_eval_pop(ref.ctx, trial, M.METADE_FP64, f64u)
         if M.metade_sync(b.ctx) != 0 or M.metade_sync(ref.ctx) != 0:
             raise RuntimeError("device status")
         rel = ((ft.double() - f64u).abs() / f64u.abs()).cpu().numpy()
@@ -1005,6 +1330,12 @@ def main(argv=None):
     if args.profile_case:
         PROFILE_CASES[args.profile_case]()
         print("profile case %s done" % args.profile_case)
+        return
+    if args.workload == "moderate":
+        run_moderate(args)
+        return
+    if args.workload == "equal_error":
+        run_equal_error(args)
         return
     if args.workload == "precision":
         run_precision(args)

@@ -73,7 +73,8 @@ typedef enum {
 } metade_status;
 
 /* Precision of the rotation z = R (u - o).  FP32: CUDA cores.  BF16, BF16X3
- * and FP8E4M3 apply to executors with D >= 256, which run on the tensor cores
+ * and FP8E4M3 apply to executors with D >= metade_config.tc_min_dim (129
+ * unless set or autotuned), which run on the tensor cores
  * (tcgen05) with FP32 accumulation: BF16 operands; split BF16 (hi*hi + hi*lo +
  * lo*hi, about FP32 accuracy); or e4m3 operands with a per-row scale of u - o
  * and a per-problem scale of R (each maps the largest magnitude to 448),
@@ -108,12 +109,16 @@ typedef struct {
     int32_t one_shot;          /* 1: executors of a run share one random stream (Sec. III-C) */
     int32_t p_best_pct;        /* pbest pool, percent of NP (0 -> 10, Sec. II-A) */
     int32_t n_out;             /* evolver population per run; 0 = no evolver */
-    metade_prec prec;          /* rotation precision for D >= 256 (FP32 below): FP32, BF16, BF16X3, FP8E4M3 */
+    metade_prec prec;          /* rotation precision for D >= tc_min_dim (FP32 below): FP32, BF16, BF16X3, FP8E4M3 */
     metade_path path;
     int32_t tie_fp64;          /* selection ties: 0 = FP32 difference form, 1 = FP64 re-evaluation */
     void *stream;              /* cudaStream_t all calls are issued on (NULL = legacy) */
     int32_t evolver;           /* 0 = DE/rand/1/bin (Alg. 3); 1 = PSO (w = 0.729, c1 = c2 = 1.49);
                                   2 = CSO (n_out <= 4096); 3 = NES (xNES) */
+    int32_t tc_min_dim;        /* prec BF16 / BF16X3 / FP8E4M3: executors with D >= tc_min_dim run on
+                                  the tensor cores, the others in FP32 on the CUDA cores.  0 = let
+                                  metade_autotune choose between 129 and 256 by speed (129 until it
+                                  runs); > 0 fixes it.  Ignored with FP32.  Negative: EINVAL */
 } metade_config;
 
 typedef struct metade_ctx metade_ctx;
@@ -173,10 +178,25 @@ METADE_API metade_status metade_inner_step(metade_ctx *ctx, float *pop, float *f
                                 uint32_t epoch, uint32_t gen0, int32_t n_gens, float *best_f,
                                 int32_t *best_i);
 
+/* Evaluate caller-given points (Sec. IV-A reports the final error
+ * f(x_best) - f*; with f* = 0 that is f(x_best) in FP64):
+ *   x      device float32 [n][ldx], point r at x + r * ldx, its first D
+ *          coordinates used, D the dimension of executor inst[r]'s problem;
+ *          16-byte aligned, ldx a multiple of 4 (>= 4)
+ *   inst   device int32 [n], the executor whose problem evaluates point r
+ *   f_out  device [n]: float for prec FP32, double for FP64 (the objective
+ *          evaluated entirely in FP64 from the float32 coordinates)
+ * n = 0 is a no-op.  Host errors (NULL pointers, ldx, alignment, n < 0, no
+ * executors) return EINVAL; other precisions EUNSUPPORTED.  An executor id
+ * outside [0, n_inst) or a dimension above ldx, found on the device, latches
+ * EINVAL in the sticky status and writes NaN for that point.  MLP problems
+ * are evaluated with their own objective. */
+METADE_API metade_status metade_eval(metade_ctx *ctx, const float *x, int64_t n, const int32_t *inst, int32_t ldx,
+                                     metade_prec prec, void *f_out);
+
 /* Evaluate every population row: prec FP32 writes float f_out[n_indiv],
- * FP64 writes double f_out[n_indiv] (used for the final error f(x) - f*,
- * f* = 0).  Other precisions return EUNSUPPORTED. */
-METADE_API metade_status metade_eval(metade_ctx *ctx, const float *pop, metade_prec prec, void *f_out);
+ * FP64 writes double f_out[n_indiv].  Other precisions return EUNSUPPORTED. */
+METADE_API metade_status metade_eval_pop(metade_ctx *ctx, const float *pop, metade_prec prec, void *f_out);
 
 /* Evolver (Alg. 3).  Its population is float32 [n_groups][n_out][6] with
  * fitness [n_groups][n_out]; executor k = g * n_out + j evaluates vector j
@@ -222,7 +242,8 @@ METADE_API metade_status metade_outer_step(metade_ctx *ctx, float *opop, float *
  * initialisation (epoch 0 under one-shot evaluation, else outer_gen),
  * n_inner_gens executor generations, the best-fitness reduction into
  * best_f/best_i, phase 1.  With use_graph != 0 the sequence is captured
- * once as a CUDA graph (per argument set) and replayed. */
+ * once as a CUDA graph (per argument set) and replayed; on the plain path
+ * (the no-graph baseline) it is always launched directly. */
 METADE_API metade_status metade_outer_generation(metade_ctx *ctx, float *opop, float *ofit, float *trial,
                                       float *theta, float *pop, float *fit, float *best_f,
                                       int32_t *best_i, uint32_t outer_gen, int32_t n_inner_gens,
@@ -242,8 +263,9 @@ METADE_API metade_status metade_draw_record(metade_ctx *ctx, const float *fit, c
  * exists for callers that cannot allocate device memory themselves (their
  * device heap belongs to a host framework or allocator, or they must not grow
  * the process's device footprint).  The caller passes every input and output:
- *   pop [np][round_up(dim,4)] float32 (pad columns zero), fit [np] -- updated
- *   in place; theta [6] decoded (F, CR, bl, br, dn, cs); shift [dim];
+ *   pop [np][round_up(dim,4)] float32 (pad columns zero), 16-byte aligned
+ *   (rows are accessed as float4; an unaligned pop returns METADE_EINVAL),
+ *   fit [np] -- updated in place; theta [6] decoded (F, CR, bl, br, dn, cs); shift [dim];
  *   rot [dim][dim] row-major; stream_id is Philox counter word 0; p_best_pct
  *   as in metade_config (0 -> 10); stream is a cudaStream_t (NULL = legacy).
  * Scratch (trial rows, trial fitness, pbest pool) lives in one file-scope
@@ -253,11 +275,14 @@ METADE_API metade_status metade_draw_record(metade_ctx *ctx, const float *fit, c
  * np outside 4..1024, dim outside 1..1536 and bad objective ids.  The first
  * call made on a device (with that device current) looks up the array's
  * device address with cudaGetSymbolAddress; make that first call before any
- * stream capture.  All calls share the array and it keeps the last call's
+ * stream capture.  The address is cached for the process's life: after
+ * cudaDeviceReset on a device, do not call this entry point on it again.  All calls share the array and it keeps the last call's
  * contents (every element a call reads is written earlier in that call, so
  * nothing is cleared); calls that overlap on the GPU race on it.  An invalid
  * theta, or np too small for the strategy, leaves pop and fit unchanged.
- * Asynchronous on `stream`; returns METADE_ECUDA if a launch fails. */
+ * Asynchronous on `stream`; returns METADE_ECUDA if a launch fails (checked
+ * with cudaPeekAtLastError, so an error left pending by earlier work is
+ * reported too, and not cleared). */
 METADE_API metade_status metade_plain_step_noalloc(float *pop, float *fit, const float *theta,
                                                    const float *shift, const float *rot, int32_t np,
                                                    int32_t dim, int32_t obj, float lo, float hi,
@@ -288,8 +313,10 @@ METADE_API metade_status metade_plan_info(const metade_ctx *ctx, char *buf, size
  * of launches since the last read -- kinds: 0 fused small-D kernel, 1 fused
  * general kernel, 2 tensor-core rotation GEMM, 3 whole tensor-core generation,
  * 4 fused tile kernel with R^T streamed (128 < D_pad <= 256), 5 fused tile
- * kernel with R^T resident (D_pad <= 128), 6 MLP-objective generations --
- * then clears them.  ms and count are host arrays of 7 (may be NULL). */
+ * kernel with R^T resident (D_pad <= 128), 6 MLP-objective generations, and
+ * the other kernels of a tensor-core generation: 7 prologue (best, pbest
+ * pool), 8 trial rows and GEMM operands, 9 selection, 10 near ties -- then
+ * clears them.  ms and count are host arrays of 11 (may be NULL). */
 METADE_API metade_status metade_profile(metade_ctx *ctx, int32_t enable);
 METADE_API metade_status metade_profile_read(metade_ctx *ctx, double *ms, int64_t *count);
 

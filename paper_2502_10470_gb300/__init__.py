@@ -28,7 +28,7 @@ REC_FIELDS = 18
 
 EXPORTED = [
     "metade_create", "metade_destroy", "metade_layout", "metade_offsets", "metade_set_stream",
-    "metade_init", "metade_inner_step", "metade_eval", "metade_outer_init", "metade_outer_step",
+    "metade_init", "metade_inner_step", "metade_eval", "metade_eval_pop", "metade_outer_init", "metade_outer_step",
     "metade_outer_generation", "metade_draw_record", "metade_sync", "metade_plan_info",
     "metade_launch_count", "metade_strerror", "metade_plain_step_noalloc", "metade_profile",
     "metade_profile_read", "metade_autotune", "metade_wait_check",
@@ -64,6 +64,7 @@ class metade_config(C.Structure):
         ("tie_fp64", C.c_int32),
         ("stream", C.c_void_p),
         ("evolver", C.c_int32),
+        ("tc_min_dim", C.c_int32),
     ]
 
 
@@ -86,7 +87,8 @@ def _lib():
         L.metade_set_stream.argtypes = [P, P]
         L.metade_init.argtypes = [P, P, P, U32]
         L.metade_inner_step.argtypes = [P, P, P, P, U32, U32, I32, P, P]
-        L.metade_eval.argtypes = [P, P, C.c_int, P]
+        L.metade_eval.argtypes = [P, P, C.c_int64, P, I32, C.c_int, P]
+        L.metade_eval_pop.argtypes = [P, P, C.c_int, P]
         L.metade_outer_init.argtypes = [P, P, P]
         L.metade_outer_step.argtypes = [P, P, P, P, P, P, U32, I32]
         L.metade_outer_generation.argtypes = [P, P, P, P, P, P, P, P, P, U32, I32, I32]
@@ -134,7 +136,7 @@ def _i32p(a: np.ndarray):
 # ---------------------------------------------------------------- C names
 def metade_create(prob_dim, prob_obj, shift, rot, inst_np, inst_prob, inst_group=None, *, lo=-100.0, hi=100.0,
                   seed=0, one_shot=0, p_best_pct=10, n_out=0, prec=METADE_FP32, path=METADE_PATH_BATCHED,
-                  tie_fp64=0, stream=None, evolver=EVOLVER_DE) -> int:
+                  tie_fp64=0, stream=None, evolver=EVOLVER_DE, tc_min_dim=0) -> int:
     """shift/rot: device float32 tensors (concatenated o_p and row-major R_p)."""
     pd, po, nps, ip = _i32(prob_dim), _i32(prob_obj), _i32(inst_np), _i32(inst_prob)
     ig = _i32(inst_group) if inst_group is not None else None
@@ -158,6 +160,7 @@ def metade_create(prob_dim, prob_obj, shift, rot, inst_np, inst_prob, inst_group
     cfg.tie_fp64 = int(tie_fp64)
     cfg.stream = stream
     cfg.evolver = int(evolver)
+    cfg.tc_min_dim = int(tc_min_dim)
     out = C.c_void_p()
     _check(_lib().metade_create(C.byref(cfg), C.byref(out)), "metade_create")
     return out.value
@@ -194,8 +197,14 @@ def metade_inner_step(ctx: int, pop, fit, theta, epoch: int, gen0: int, n_gens: 
                                     _ptr(best_i)), "metade_inner_step")
 
 
-def metade_eval(ctx: int, pop, prec: int, f_out) -> None:
-    _check(_lib().metade_eval(ctx, _ptr(pop), prec, _ptr(f_out)), "metade_eval")
+def metade_eval(ctx: int, x, n: int, inst, ldx: int, prec: int, f_out) -> None:
+    """Caller-given points: x [n][ldx] float32, inst [n] int32 executor ids."""
+    _check(_lib().metade_eval(ctx, _ptr(x), int(n), _ptr(inst), int(ldx), prec, _ptr(f_out)), "metade_eval")
+
+
+def metade_eval_pop(ctx: int, pop, prec: int, f_out) -> None:
+    """Every population row, in the fitness layout."""
+    _check(_lib().metade_eval_pop(ctx, _ptr(pop), prec, _ptr(f_out)), "metade_eval_pop")
 
 
 def metade_outer_init(ctx: int, opop, ofit) -> None:
@@ -246,7 +255,7 @@ def metade_autotune(ctx: int, pop, fit, theta, n_gens: int = 3) -> None:
 
 
 PROFILE_KINDS = ["fused_small", "fused_general", "tc_gemm", "tc_generation", "fused_tile_stream", "fused_tile",
-                 "mlp_generations"]
+                 "mlp_generations", "tc_prologue", "tc_trial", "tc_select", "tc_ties"]
 
 
 def metade_profile(ctx: int, enable: bool) -> None:
@@ -293,7 +302,7 @@ class Batch:
 
     def __init__(self, problems: Sequence, inst_np, inst_prob, inst_group=None, *, seed=0, one_shot=0,
                  p_best_pct=10, n_out=0, path=METADE_PATH_BATCHED, prec=METADE_FP32, lo=-100.0, hi=100.0,
-                 tie_fp64=0, device="cuda", stream=None, evolver=EVOLVER_DE):
+                 tie_fp64=0, device="cuda", stream=None, evolver=EVOLVER_DE, tc_min_dim=0):
         import torch
         self.torch = torch
         self.device = torch.device(device)
@@ -312,7 +321,8 @@ class Batch:
         self.stream = stream
         self.ctx = metade_create(dims, objs, self.shift_d, self.rot_d, self.inst_np, self.inst_prob, inst_group,
                                  lo=lo, hi=hi, seed=seed, one_shot=one_shot, p_best_pct=p_best_pct, n_out=n_out,
-                                 prec=prec, path=path, tie_fp64=tie_fp64, stream=stream, evolver=evolver)
+                                 prec=prec, path=path, tie_fp64=tie_fp64, stream=stream, evolver=evolver,
+                                 tc_min_dim=tc_min_dim)
         self.dims = np.array([dims[p] for p in self.inst_prob], dtype=np.int32)
         self.pop_floats, self.n_indiv, self.n_groups = metade_layout(self.ctx)
         self.pop_off, self.fit_off, self.dpad = metade_offsets(self.ctx, self.n_inst)

@@ -16,7 +16,11 @@ using namespace metade;
 namespace {
 
 constexpr int kMaxDim = 1536;
-constexpr int kTcMinDim = 256;  // reduced-precision executors at least this wide use the tensor cores
+// Reduced-precision executors at least this wide use the tensor cores unless
+// the configuration fixes another width: 129 is the first D whose padded row
+// (D_pad > 128) no longer lets the fused tile kernel keep R^T in shared memory.
+constexpr int kTcDefaultMinDim = 129;
+constexpr int kTcAltMinDim = 256;  // the other width metade_autotune tries
 constexpr int kMaxNp = 1024;
 constexpr size_t kSmemLimit = 227 * 1024;
 
@@ -34,7 +38,11 @@ enum ProfKind {
     kProfFusedTileStream = 4,
     kProfFusedTile = 5,
     kProfFusedMlp = 6,
-    kProfKinds = 7
+    kProfTcPrologue = 7,
+    kProfTcTrial = 8,
+    kProfTcSelect = 9,
+    kProfTcTies = 10,
+    kProfKinds = 11
 };
 
 struct ProfRec {
@@ -79,13 +87,18 @@ struct metade_ctx {
     int* topk = nullptr;
     int* status = nullptr;
     uint32_t* gen_dev = nullptr;
+    unsigned* bar = nullptr;  // plain path: grid-barrier arrival count
     int* work = nullptr;
     std::vector<Bucket> buckets;
     std::vector<GraphEntry> graphs;
     int64_t launches = 0;
     bool prof_on = false;
     std::vector<ProfRec> prof;
+    std::vector<cudaEvent_t> prof_events;  // every event the records refer to (destroyed on read)
     // large-D executors on the tensor cores (prec BF16 / BF16X3)
+    int tc_min_dim = kTcDefaultMinDim;  // executors with D >= this run on the GEMM pipeline
+    bool tc_auto = false;               // metade_autotune picks tc_min_dim
+    std::string tc_tuned;               // autotuner record: width -> ms
     bool tc = false;
     TcPlan tcp;
     std::vector<char> is_tc;
@@ -266,9 +279,175 @@ metade_status build_plan(metade_ctx* c) {
         order.insert(order.end(), general.begin(), general.end());
         c->buckets.push_back(b);
     }
+    cudaFree(c->work);
+    c->work = nullptr;
     if (!order.empty()) {
         CK(dalloc(&c->work, order.size()));
         CK(cudaMemcpy(c->work, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice));
+    }
+    return METADE_OK;
+}
+
+// Release the tensor-core pipeline's buffers (before re-planning, or at destroy).
+void free_tc(metade_ctx* c) {
+    cudaFree(c->tc_execs);
+    cudaFree(c->tc_row_exec);
+    cudaFree(c->tc_tiles);
+    cudaFree(c->tc_brow);
+    cudaFree(c->tc_topk);
+    cudaFree(c->tc_ties);
+    cudaFree(c->aq);
+    cudaFree(c->aq_lo);
+    cudaFree(c->bq);
+    cudaFree(c->bq_lo);
+    cudaFree(c->ascale);
+    cudaFree(c->bscale);
+    cudaFree(c->amax);
+    c->tc_execs = c->tc_row_exec = c->tc_tiles = c->tc_topk = c->tc_ties = nullptr;
+    c->tc_brow = nullptr;
+    c->aq = c->aq_lo = c->bq = c->bq_lo = nullptr;
+    c->ascale = c->bscale = nullptr;
+    c->amax = nullptr;
+    c->tc = false;
+    c->tcp = TcPlan{};
+    c->is_tc.assign(c->n_inst, 0);
+}
+
+// Executors on the per-generation GEMM pipeline: with BF16 / bf16x3 / FP8,
+// every executor with D >= tc_min_dim (tensor cores); with FP32, the ones
+// too wide for the tile kernels (D_pad > 256, CUDA-core GEMM).  Their operand
+// rows are ordered by problem, then executor (InstDesc.tc_row = first row),
+// so that a 128-row M tile of the tensor-core GEMM can span consecutive
+// executors of one problem: they share the B operand (the problem's R), and
+// the tiles stay full however small each population is.  The FP32 GEMM keeps
+// 64-row tiles per executor.  Re-uploads the descriptor table.
+metade_status setup_tc(metade_ctx* c) {
+    free_tc(c);
+    for (InstDesc& d : c->hdesc)
+        if (d.obj != kMlp) {
+            d.on_tc = 0;
+            d.tc_row = 0;
+        }
+    const bool fp8 = c->prec == METADE_FP8E4M3;
+    const bool simt = c->prec == METADE_FP32 && c->path == METADE_PATH_BATCHED;
+    const bool reduced = c->prec == METADE_BF16 || c->prec == METADE_BF16X3 || fp8;
+    const int kalign = fp8 ? 128 : 64;  // K elements per 128-byte operand tile (unused by the FP32 GEMM)
+    std::vector<int> tc_execs, tc_row_exec, tc_tiles;
+    std::vector<long long> tc_brow(c->n_prob, -1);
+    long long tc_brows = 0;
+    int tc_kp = 0, tc_max_dpad = 0;
+    if (reduced || simt) {
+        for (int k = 0; k < c->n_inst; ++k) {
+            const InstDesc& d = c->hdesc[k];
+            if (d.obj == kMlp || (simt ? d.dpad <= 256 : d.dim < c->tc_min_dim)) continue;
+            tc_execs.push_back(k);
+        }
+        std::stable_sort(tc_execs.begin(), tc_execs.end(),
+                         [&](int x, int y) { return c->hdesc[x].prob < c->hdesc[y].prob; });
+        int prob_row0 = 0;  // first operand row of the current problem
+        for (size_t q = 0; q < tc_execs.size(); ++q) {
+            const int k = tc_execs[q];
+            InstDesc& d = c->hdesc[k];
+            c->is_tc[k] = 1;
+            d.tc_row = (int)tc_row_exec.size();
+            d.on_tc = 1;
+            for (int i = 0; i < d.np; ++i) tc_row_exec.push_back(k);
+            if (simt)
+                for (int m0 = 0; m0 < d.np; m0 += 64) {
+                    tc_tiles.push_back(k);
+                    tc_tiles.push_back(m0);
+                }
+            tc_kp = std::max(tc_kp, (d.dim + kalign - 1) / kalign * kalign);
+            tc_max_dpad = std::max(tc_max_dpad, d.dpad);
+            if (tc_brow[d.prob] < 0) {
+                tc_brow[d.prob] = tc_brows;
+                tc_brows += (d.dim + 255) / 256 * 256;
+            }
+            // tensor cores: (first row, rows) tiles over the problem's rows, cut after its last executor
+            if (q == 0 || c->hdesc[tc_execs[q - 1]].prob != d.prob) prob_row0 = d.tc_row;
+            const bool last_of_prob = q + 1 == tc_execs.size() || c->hdesc[tc_execs[q + 1]].prob != d.prob;
+            if (!simt && last_of_prob) {
+                const int r0 = prob_row0, r1 = (int)tc_row_exec.size();
+                for (int r = r0; r < r1; r += 128) {
+                    tc_tiles.push_back(r);
+                    tc_tiles.push_back(std::min(128, r1 - r));
+                }
+            }
+        }
+        c->tc = !tc_execs.empty();
+    }
+    if (c->n_inst > 0 &&
+        cudaMemcpy(c->desc, c->hdesc.data(), sizeof(InstDesc) * c->n_inst, cudaMemcpyHostToDevice) != cudaSuccess)
+        return METADE_ECUDA;
+    if (!c->tc) return METADE_OK;
+    const bool split = c->prec == METADE_BF16X3;
+    const size_t nrows = tc_row_exec.size();
+    const size_t esz = fp8 ? 1 : 2;  // operand element bytes
+    if (dalloc(&c->tc_execs, tc_execs.size()) || dalloc(&c->tc_row_exec, nrows) ||
+        dalloc(&c->tc_tiles, tc_tiles.size()) || dalloc(&c->tc_brow, (size_t)c->n_prob) ||
+        dalloc(&c->tc_topk, (size_t)c->n_indiv) || dalloc(&c->tc_ties, nrows + 1) ||
+        (!simt && (dalloc(&c->aq, nrows * tc_kp * esz) || dalloc(&c->bq, (size_t)tc_brows * tc_kp * esz))) ||
+        (split && (dalloc(&c->aq_lo, nrows * tc_kp * esz) || dalloc(&c->bq_lo, (size_t)tc_brows * tc_kp * esz))) ||
+        (fp8 && (dalloc(&c->ascale, nrows) || dalloc(&c->bscale, (size_t)c->n_prob) || dalloc(&c->amax, 1))))
+        return METADE_ENOMEM;
+    if (cudaMemcpy(c->tc_execs, tc_execs.data(), sizeof(int) * tc_execs.size(), cudaMemcpyHostToDevice) ||
+        cudaMemcpy(c->tc_row_exec, tc_row_exec.data(), sizeof(int) * nrows, cudaMemcpyHostToDevice) ||
+        cudaMemcpy(c->tc_tiles, tc_tiles.data(), sizeof(int) * tc_tiles.size(), cudaMemcpyHostToDevice) ||
+        cudaMemcpy(c->tc_brow, tc_brow.data(), sizeof(long long) * c->n_prob, cudaMemcpyHostToDevice))
+        return METADE_ECUDA;
+    if (!simt) {
+        std::vector<char> packed(c->n_prob, 0);
+        for (int k : tc_execs) {
+            const InstDesc& d = c->hdesc[k];
+            if (packed[d.prob]) continue;
+            packed[d.prob] = 1;
+            if (launch_tc_pack_rot(c->rot, d.rot_off, d.dim, d.dpad, tc_kp, (d.dim + 255) / 256 * 256, c->bq,
+                                   split ? c->bq_lo : nullptr, tc_brow[d.prob], fp8 ? 1 : 0, c->amax,
+                                   fp8 ? c->bscale + d.prob : nullptr, c->st))
+                return METADE_ECUDA;
+            c->launches += 1;
+        }
+    }
+    if (cudaStreamSynchronize(c->st)) return METADE_ECUDA;
+    TcPlan& t = c->tcp;
+    t.execs = c->tc_execs;
+    t.n_exec = (int)tc_execs.size();
+    t.row_exec = c->tc_row_exec;
+    t.n_rows = (int)nrows;
+    t.tiles = c->tc_tiles;
+    t.n_tiles = (int)tc_tiles.size() / 2;
+    t.brow = c->tc_brow;
+    t.topk_all = c->tc_topk;
+    t.uscr = c->uscr;
+    t.fu = c->fuscr;
+    t.aq = c->aq;
+    t.aq_lo = c->aq_lo;
+    t.bq = c->bq;
+    t.bq_lo = c->bq_lo;
+    t.ascale = c->ascale;
+    t.bscale = c->bscale;
+    t.fp8 = fp8 ? 1 : 0;
+    t.simt = simt ? 1 : 0;
+    t.tie_list = c->tc_ties + 1;
+    t.tie_count = c->tc_ties;
+    t.tie_ctas = std::max(1, device_sms()) * 2;
+    t.kp = tc_kp;
+    t.split = split ? 1 : 0;
+    t.max_dpad = tc_max_dpad;
+    // a tie keeps four rows of max_dpad in shared memory (FP64 with tie_fp64)
+    if ((size_t)4 * tc_max_dpad * (c->tie_fp64 ? sizeof(double) : sizeof(float)) > kSmemLimit)
+        return METADE_EUNSUPPORTED;
+    if (simt) {
+        // no operands, no tensor maps: k_rot_simt reads the trial rows and R^T itself
+    } else if (!tc_make_map(&t.mapA, c->aq, (long long)nrows, tc_kp, 128, (int)esz) ||
+               !tc_make_map(&t.mapB, c->bq, tc_brows, tc_kp, 256, (int)esz) ||
+               (split && (!tc_make_map(&t.mapAlo, c->aq_lo, (long long)nrows, tc_kp, 128, (int)esz) ||
+                          !tc_make_map(&t.mapBlo, c->bq_lo, tc_brows, tc_kp, 256, (int)esz)))) {
+        return METADE_ECUDA;
+    }
+    if (!split && !simt) {
+        t.mapAlo = t.mapA;
+        t.mapBlo = t.mapB;
     }
     return METADE_OK;
 }
@@ -284,7 +463,29 @@ bool prof_pair(metade_ctx* c, cudaStream_t st, int kind, cudaEvent_t* a, cudaEve
         cudaEventDestroy(*a);
         return false;
     }
+    c->prof_events.push_back(*a);
+    c->prof_events.push_back(*b);
     c->prof.push_back(ProfRec{kind, *a, *b});
+    return true;
+}
+
+// Events between the kernels of one tensor-core generation (prologue, trial,
+// GEMM, selection, ties): ev[0..5], with a record per kernel and one for the
+// whole generation.
+bool prof_tc(metade_ctx* c, cudaStream_t st, cudaEvent_t* ev) {
+    if (!c->prof_on) return false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return false;
+    for (int i = 0; i < 6; ++i) {
+        if (cudaEventCreate(&ev[i]) != cudaSuccess) {
+            for (int j = 0; j < i; ++j) cudaEventDestroy(ev[j]);
+            return false;
+        }
+    }
+    for (int i = 0; i < 6; ++i) c->prof_events.push_back(ev[i]);
+    const int kinds[5] = {kProfTcPrologue, kProfTcTrial, kProfTcGemm, kProfTcSelect, kProfTcTies};
+    for (int i = 0; i < 5; ++i) c->prof.push_back(ProfRec{kinds[i], ev[i], ev[i + 1]});
+    c->prof.push_back(ProfRec{kProfTcGeneration, ev[0], ev[5]});
     return true;
 }
 
@@ -293,11 +494,20 @@ metade_status run_inner(metade_ctx* c, cudaStream_t st, float* pop, float* fit, 
                         int64_t* launches) {
     if (c->n_inst == 0) return METADE_OK;
     if (c->path == METADE_PATH_PLAIN || n_gens == 0) {
+        // the grid barriers of this call's launches count up from zero
+        if (n_gens > 0) CK(cudaMemsetAsync(c->bar, 0, sizeof(unsigned), st));
+        unsigned base = 0;
         for (int g = 0; g < n_gens; ++g) {
             StepArgs a = step_args(c, pop, fit, theta, epoch, epoch_dev, gen0 + (uint32_t)g, 1, nullptr, nullptr);
             for (int k = 0; k < c->n_inst; ++k) {
-                CK(launch_plain_generation(a, k, c->hdesc[k], c->uscr, c->fuscr, c->topk, st));
-                *launches += 3;
+                const unsigned nb = (unsigned)((c->hdesc[k].np + 7) / 8);
+                if (base > 0xFFFFFFFFu - 2 * nb) {  // restart the count before it wraps
+                    CK(cudaMemsetAsync(c->bar, 0, sizeof(unsigned), st));
+                    base = 0;
+                }
+                CK(launch_plain_generation(a, k, c->hdesc[k], c->uscr, c->fuscr, c->topk, c->bar, base, st));
+                base += 2 * nb;
+                *launches += 1;
             }
         }
         if (best_f || best_i) {
@@ -322,12 +532,9 @@ metade_status run_inner(metade_ctx* c, cudaStream_t st, float* pop, float* fit, 
     if (c->tc) {
         for (int g = 0; g < n_gens; ++g) {
             StepArgs t = step_args(c, pop, fit, theta, epoch, epoch_dev, gen0 + (uint32_t)g, 1, nullptr, nullptr);
-            cudaEvent_t g0, g1, e0, e1;
-            const bool pg = prof_pair(c, st, kProfTcGemm, &g0, &g1);
-            const bool pe = prof_pair(c, st, kProfTcGeneration, &e0, &e1);
-            if (pe) cudaEventRecord(e0, st);
-            CK(launch_tc_generation(t, c->tcp, st, pg ? g0 : nullptr, pg ? g1 : nullptr));
-            if (pe) cudaEventRecord(e1, st);
+            cudaEvent_t ev[6];
+            const bool pe = prof_tc(c, st, ev);
+            CK(launch_tc_generation(t, c->tcp, st, pe ? ev : nullptr));
             *launches += 5;
         }
     }
@@ -435,10 +642,7 @@ void metade_destroy(metade_ctx* c) {
     if (!c) return;
     if (c->st) cudaStreamSynchronize(c->st);
     for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
-    for (auto& r : c->prof) {
-        cudaEventDestroy(r.a);
-        cudaEventDestroy(r.b);
-    }
+    for (cudaEvent_t e : c->prof_events) cudaEventDestroy(e);
     cudaFree(c->desc);
     cudaFree(c->row_inst);
     cudaFree(c->rot);
@@ -449,20 +653,9 @@ void metade_destroy(metade_ctx* c) {
     cudaFree(c->topk);
     cudaFree(c->status);
     cudaFree(c->gen_dev);
+    cudaFree(c->bar);
     cudaFree(c->work);
-    cudaFree(c->tc_execs);
-    cudaFree(c->tc_row_exec);
-    cudaFree(c->tc_tiles);
-    cudaFree(c->tc_brow);
-    cudaFree(c->tc_topk);
-    cudaFree(c->tc_ties);
-    cudaFree(c->aq);
-    cudaFree(c->aq_lo);
-    cudaFree(c->bq);
-    cudaFree(c->bq_lo);
-    cudaFree(c->ascale);
-    cudaFree(c->bscale);
-    cudaFree(c->amax);
+    free_tc(c);
     cudaFree(c->mlp_x);
     cudaFree(c->mlp_y);
     cudaFree(c->mlp_execs);
@@ -499,6 +692,7 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
     }
 
     if (cfg->evolver < 0 || cfg->evolver > 3) return METADE_EINVAL;
+    if (cfg->tc_min_dim < 0) return METADE_EINVAL;
     if (cfg->evolver == 2 && cfg->n_out > 4096) return METADE_EINVAL;  // the pairing lives in shared memory
 
     metade_ctx* c = new metade_ctx();
@@ -586,39 +780,6 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
         mlp_execs.push_back(k);
         for (int i = 0; i < d.np; ++i) mlp_row_exec.push_back(k);
     }
-    // executors on the tensor cores: operand row offsets (InstDesc.tc_row), tiles
-    c->is_tc.assign(c->n_inst, 0);
-    std::vector<int> tc_execs, tc_row_exec, tc_tiles;
-    std::vector<long long> tc_brow(c->n_prob, -1);
-    long long tc_brows = 0;
-    int tc_kp = 0, tc_max_dpad = 0;
-    const bool fp8 = c->prec == METADE_FP8E4M3;
-    const int kalign = fp8 ? 128 : 64;  // K elements per 128-byte operand tile (unused by the FP32 GEMM)
-    // FP32 contexts send executors too wide for the tile kernels (D_pad > 256)
-    // through the same pipeline with the GEMM on the CUDA cores
-    const bool simt = c->prec == METADE_FP32 && c->path == METADE_PATH_BATCHED;
-    if (c->prec == METADE_BF16 || c->prec == METADE_BF16X3 || fp8 || simt) {
-        for (int k = 0; k < c->n_inst; ++k) {
-            InstDesc& d = c->hdesc[k];
-            if (d.obj == kMlp || (simt ? d.dpad <= 256 : d.dim < kTcMinDim)) continue;
-            c->is_tc[k] = 1;
-            d.tc_row = (int)tc_row_exec.size();
-            d.on_tc = 1;
-            tc_execs.push_back(k);
-            for (int i = 0; i < d.np; ++i) tc_row_exec.push_back(k);
-            for (int m0 = 0; m0 < d.np; m0 += simt ? 64 : 128) {
-                tc_tiles.push_back(k);
-                tc_tiles.push_back(m0);
-            }
-            tc_kp = std::max(tc_kp, (d.dim + kalign - 1) / kalign * kalign);
-            tc_max_dpad = std::max(tc_max_dpad, d.dpad);
-            if (tc_brow[d.prob] < 0) {
-                tc_brow[d.prob] = tc_brows;
-                tc_brows += (d.dim + 255) / 256 * 256;
-            }
-        }
-        c->tc = !tc_execs.empty();
-    }
     c->pop_floats = po;
     c->n_indiv = fo;
 
@@ -630,7 +791,7 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
     if (e != cudaSuccess) return fail(METADE_ECUDA);
     if (dalloc(&c->desc, c->n_inst) || dalloc(&c->row_inst, row_inst.size()) || dalloc(&c->rot, rpad) ||
         dalloc(&c->rotT, rpad) || dalloc(&c->shift, spad) || dalloc(&c->uscr, po) || dalloc(&c->fuscr, fo) ||
-        dalloc(&c->topk, c->max_np) || dalloc(&c->status, 1) || dalloc(&c->gen_dev, 1))
+        dalloc(&c->topk, c->max_np) || dalloc(&c->status, 1) || dalloc(&c->gen_dev, 1) || dalloc(&c->bar, 1))
         return fail(METADE_ENOMEM);
     if (cudaMemset(c->status, 0, sizeof(int)) || cudaMemset(c->gen_dev, 0, sizeof(uint32_t)) ||
         cudaMemset(c->uscr, 0, sizeof(float) * (size_t)std::max(po, 1LL)))
@@ -692,73 +853,13 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
             for (int k : mlp_execs) m.max_dpad = std::max(m.max_dpad, c->hdesc[k].dpad);
             if ((size_t)8 * m.max_dpad * sizeof(float) > kSmemLimit) return fail(METADE_EUNSUPPORTED);
         }
-        metade_status s = build_plan(c);
-        if (s != METADE_OK) return fail(s);
     }
-    if (c->tc) {
-        const bool split = c->prec == METADE_BF16X3;
-        const size_t nrows = tc_row_exec.size();
-        const size_t esz = fp8 ? 1 : 2;  // operand element bytes
-        if (dalloc(&c->tc_execs, tc_execs.size()) || dalloc(&c->tc_row_exec, nrows) ||
-            dalloc(&c->tc_tiles, tc_tiles.size()) || dalloc(&c->tc_brow, (size_t)c->n_prob) ||
-            dalloc(&c->tc_topk, (size_t)c->n_indiv) || dalloc(&c->tc_ties, nrows + 1) ||
-            (!simt && (dalloc(&c->aq, nrows * tc_kp * esz) || dalloc(&c->bq, (size_t)tc_brows * tc_kp * esz))) ||
-            (split && (dalloc(&c->aq_lo, nrows * tc_kp * esz) || dalloc(&c->bq_lo, (size_t)tc_brows * tc_kp * esz))) ||
-            (fp8 && (dalloc(&c->ascale, nrows) || dalloc(&c->bscale, (size_t)c->n_prob) || dalloc(&c->amax, 1))))
-            return fail(METADE_ENOMEM);
-        if (cudaMemcpy(c->tc_execs, tc_execs.data(), sizeof(int) * tc_execs.size(), cudaMemcpyHostToDevice) ||
-            cudaMemcpy(c->tc_row_exec, tc_row_exec.data(), sizeof(int) * nrows, cudaMemcpyHostToDevice) ||
-            cudaMemcpy(c->tc_tiles, tc_tiles.data(), sizeof(int) * tc_tiles.size(), cudaMemcpyHostToDevice) ||
-            cudaMemcpy(c->tc_brow, tc_brow.data(), sizeof(long long) * c->n_prob, cudaMemcpyHostToDevice))
-            return fail(METADE_ECUDA);
-        for (int p = 0; p < c->n_prob && !simt; ++p) {
-            if (tc_brow[p] < 0) continue;
-            const int D = cfg->prob_dim[p], Dp = (D + 3) & ~3;
-            if (launch_tc_pack_rot(c->rot, rot_off[p], D, Dp, tc_kp, (D + 255) / 256 * 256, c->bq, split ? c->bq_lo : nullptr,
-                                   tc_brow[p], fp8 ? 1 : 0, c->amax, fp8 ? c->bscale + p : nullptr, c->st))
-                return fail(METADE_ECUDA);
-        }
-        if (cudaStreamSynchronize(c->st)) return fail(METADE_ECUDA);
-        TcPlan& t = c->tcp;
-        t.execs = c->tc_execs;
-        t.n_exec = (int)tc_execs.size();
-        t.row_exec = c->tc_row_exec;
-        t.n_rows = (int)nrows;
-        t.tiles = c->tc_tiles;
-        t.n_tiles = (int)tc_tiles.size() / 2;
-        t.brow = c->tc_brow;
-        t.topk_all = c->tc_topk;
-        t.uscr = c->uscr;
-        t.fu = c->fuscr;
-        t.aq = c->aq;
-        t.aq_lo = c->aq_lo;
-        t.bq = c->bq;
-        t.bq_lo = c->bq_lo;
-        t.ascale = c->ascale;
-        t.bscale = c->bscale;
-        t.fp8 = fp8 ? 1 : 0;
-        t.simt = simt ? 1 : 0;
-        t.tie_list = c->tc_ties + 1;
-        t.tie_count = c->tc_ties;
-        t.tie_ctas = std::max(1, device_sms()) * 2;
-        t.kp = tc_kp;
-        t.split = split ? 1 : 0;
-        t.max_dpad = tc_max_dpad;
-        // a tie keeps four rows of max_dpad in shared memory (FP64 with tie_fp64)
-        if ((size_t)4 * tc_max_dpad * (c->tie_fp64 ? sizeof(double) : sizeof(float)) > kSmemLimit)
-            return fail(METADE_EUNSUPPORTED);
-        if (simt) {
-            // no operands, no tensor maps: k_rot_simt reads the trial rows and R^T itself
-        } else if (!tc_make_map(&t.mapA, c->aq, (long long)nrows, tc_kp, 128, (int)esz) ||
-            !tc_make_map(&t.mapB, c->bq, tc_brows, tc_kp, 256, (int)esz) ||
-            (split && (!tc_make_map(&t.mapAlo, c->aq_lo, (long long)nrows, tc_kp, 128, (int)esz) ||
-                       !tc_make_map(&t.mapBlo, c->bq_lo, tc_brows, tc_kp, 256, (int)esz))))
-            return fail(METADE_ECUDA);
-        if (!split && !simt) {
-            t.mapAlo = t.mapA;
-            t.mapBlo = t.mapB;
-        }
-        c->launches += 1;
+    c->tc_auto = cfg->tc_min_dim == 0;
+    c->tc_min_dim = cfg->tc_min_dim > 0 ? cfg->tc_min_dim : kTcDefaultMinDim;
+    if (c->n_inst > 0) {
+        metade_status s = setup_tc(c);
+        if (s == METADE_OK) s = build_plan(c);
+        if (s != METADE_OK) return fail(s);
     }
     *out = c;
     return METADE_OK;
@@ -801,7 +902,20 @@ metade_status metade_inner_step(metade_ctx* c, float* pop, float* fit, const flo
     return run_inner(c, c->st, pop, fit, theta, epoch, nullptr, gen0, n_gens, best_f, best_i, &c->launches);
 }
 
-metade_status metade_eval(metade_ctx* c, const float* pop, metade_prec prec, void* f_out) {
+metade_status metade_eval(metade_ctx* c, const float* x, int64_t n, const int32_t* inst, int32_t ldx,
+                          metade_prec prec, void* f_out) {
+    if (!c || n < 0) return METADE_EINVAL;
+    if (prec != METADE_FP32 && prec != METADE_FP64) return METADE_EUNSUPPORTED;
+    if (n == 0) return METADE_OK;
+    if (!x || !inst || !f_out || ldx < 4 || (ldx & 3) || ((uintptr_t)x & 15)) return METADE_EINVAL;
+    if (c->n_inst == 0) return METADE_EINVAL;  // no executor a point could belong to
+    CK(launch_eval(c->desc, nullptr, n, x, c->rotT, c->shift, prec == METADE_FP64, f_out, false, c->max_dpad, c->st,
+                   false, c->mlp_x, c->mlp_y, inst, ldx, c->n_inst, c->status));
+    c->launches += 1;
+    return METADE_OK;
+}
+
+metade_status metade_eval_pop(metade_ctx* c, const float* pop, metade_prec prec, void* f_out) {
     if (!c || (c->n_inst > 0 && (!pop || !f_out))) return METADE_EINVAL;
     if (prec != METADE_FP32 && prec != METADE_FP64) return METADE_EUNSUPPORTED;
     if (c->n_inst == 0) return METADE_OK;
@@ -847,7 +961,8 @@ metade_status metade_outer_generation(metade_ctx* c, float* opop, float* ofit, f
     k_set_u32<<<1, 1, 0, c->st>>>(c->gen_dev, outer_gen);
     CK(cudaGetLastError());
     c->launches += 1;
-    if (!use_graph)
+    // the plain path is the no-graph baseline: always launched directly
+    if (!use_graph || c->path == METADE_PATH_PLAIN)
         return enqueue_outer_generation(c, c->st, opop, ofit, trial, theta, pop, fit, best_f, best_i, n_inner,
                                         &c->launches);
     std::vector<uintptr_t> key = {(uintptr_t)opop, (uintptr_t)ofit, (uintptr_t)trial, (uintptr_t)theta,
@@ -909,7 +1024,16 @@ metade_status metade_sync(metade_ctx* c) {
 
 metade_status metade_autotune(metade_ctx* c, const float* pop, const float* fit, const float* theta, int32_t n_gens) {
     if (!c || n_gens < 1 || (c->n_inst > 0 && (!pop || !fit || !theta))) return METADE_EINVAL;
-    if (c->path != METADE_PATH_BATCHED || c->buckets.empty()) return METADE_OK;
+    if (c->path != METADE_PATH_BATCHED || c->n_inst == 0) return METADE_OK;
+    const bool reduced = c->prec == METADE_BF16 || c->prec == METADE_BF16X3 || c->prec == METADE_FP8E4M3;
+    bool mid = false;  // executors whose place (tensor cores or CUDA cores) the width decides
+    for (const InstDesc& d : c->hdesc)
+        mid = mid || (d.obj != kMlp && d.dim >= kTcDefaultMinDim && d.dim < kTcAltMinDim);
+    const bool tune_width = c->tc_auto && reduced && mid;
+    if (c->buckets.empty() && !tune_width) return METADE_OK;
+    // the plan changes: graphs captured with the old one are dropped
+    for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+    c->graphs.clear();
     float* tpop = nullptr;
     float* tfit = nullptr;
     if (dalloc(&tpop, (size_t)c->pop_floats) || dalloc(&tfit, (size_t)c->n_indiv)) {
@@ -919,6 +1043,46 @@ metade_status metade_autotune(metade_ctx* c, const float* pop, const float* fit,
     cudaEvent_t e0, e1;
     metade_status st = METADE_OK;
     if (cudaEventCreate(&e0) || cudaEventCreate(&e1)) st = METADE_ECUDA;
+    if (st == METADE_OK && tune_width) {
+        // the tensor-core width: n_gens whole generations of every executor per candidate
+        const bool prof = c->prof_on;
+        c->prof_on = false;
+        int best_w = c->tc_min_dim;
+        float best_ms = -1.f;
+        c->tc_tuned.clear();
+        for (int w : {kTcDefaultMinDim, kTcAltMinDim}) {
+            c->tc_min_dim = w;
+            st = setup_tc(c);
+            if (st == METADE_OK) st = build_plan(c);
+            if (st != METADE_OK) break;
+            int64_t nl = 0;
+            if (cudaMemcpyAsync(tpop, pop, sizeof(float) * (size_t)c->pop_floats, cudaMemcpyDeviceToDevice, c->st) ||
+                cudaMemcpyAsync(tfit, fit, sizeof(float) * (size_t)c->n_indiv, cudaMemcpyDeviceToDevice, c->st) ||
+                cudaEventRecord(e0, c->st)) {
+                st = METADE_ECUDA;
+                break;
+            }
+            st = run_inner(c, c->st, tpop, tfit, theta, 0, nullptr, 0, n_gens, nullptr, nullptr, &nl);
+            if (st != METADE_OK) break;
+            if (cudaEventRecord(e1, c->st) || cudaEventSynchronize(e1)) {
+                st = METADE_ECUDA;
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            char tmp[64];
+            snprintf(tmp, sizeof(tmp), "%s\"%d\": %.4f", c->tc_tuned.empty() ? "" : ", ", w, ms);
+            c->tc_tuned += tmp;
+            if (best_ms < 0.f || ms < best_ms) {
+                best_ms = ms;
+                best_w = w;
+            }
+        }
+        c->prof_on = prof;
+        c->tc_min_dim = best_w;
+        if (st == METADE_OK) st = setup_tc(c);
+        if (st == METADE_OK) st = build_plan(c);
+    }
     for (Bucket& b : c->buckets) {
         if (st != METADE_OK) break;
         std::vector<int> cands = b.plan.kind == 0 ? std::vector<int>{32, 64, 128, 256}
@@ -991,6 +1155,13 @@ metade_status metade_plan_info(const metade_ctx* c, char* buf, size_t len) {
         s += "}";
     }
     s += "]";
+    {
+        char tmp[160];
+        snprintf(tmp, sizeof(tmp), ", \"tc_min_dim\": %d, \"tc_min_dim_auto\": %s", c->tc_min_dim,
+                 c->tc_auto ? "true" : "false");
+        s += tmp;
+        if (!c->tc_tuned.empty()) s += ", \"tc_autotune_ms\": {" + c->tc_tuned + "}";
+    }
     if (c->tc) {
         char tmp[256];
         snprintf(tmp, sizeof(tmp),
@@ -1034,10 +1205,10 @@ metade_status metade_profile_read(metade_ctx* c, double* ms, int64_t* count) {
             tot[r.kind] += t;
             n[r.kind] += 1;
         }
-        cudaEventDestroy(r.a);
-        cudaEventDestroy(r.b);
     }
     c->prof.clear();
+    for (cudaEvent_t e : c->prof_events) cudaEventDestroy(e);
+    c->prof_events.clear();
     for (int k = 0; k < kProfKinds; ++k) {
         if (ms) ms[k] = tot[k];
         if (count) count[k] = n[k];

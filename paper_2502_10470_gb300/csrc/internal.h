@@ -40,20 +40,27 @@ cudaError_t launch_init(const InstDesc* desc, int n_inst, int max_np, int max_dp
 
 // Evaluate every row (row_inst maps rows to executors).  f64 selects FP64;
 // skip_tc leaves the rows of executors on the tensor-core and MLP paths
-// untouched (those paths evaluate them).
+// untouched (those paths evaluate them).  With pt_inst, n_rows caller-given
+// points instead: point r at pop + r * ldx, executor pt_inst[r] (bad ids or
+// dimensions above ldx latch EINVAL in *status and give NaN).
 cudaError_t launch_eval(const InstDesc* desc, const int* row_inst, long long n_rows, const float* pop,
                         const float* rotT, const float* shift, bool f64, void* f_out, bool nan_inf,
                         int max_dpad, cudaStream_t st, bool skip_tc, const float* mlp_x = nullptr,
-                        const float* mlp_y = nullptr);
+                        const float* mlp_y = nullptr, const int* pt_inst = nullptr, int ldx = 0, int n_inst = 0,
+                        int* status = nullptr);
 
 cudaError_t launch_record(const StepArgs& a, int n_inst, int max_np, int* rec, cudaStream_t st);
 
 cudaError_t launch_best(const InstDesc* desc, int n_inst, const float* fit, float* best_f, int* best_i,
                         cudaStream_t st);
 
-// Plain path: one executor, one generation, three launches.
+// Plain path: one executor, one generation, one cooperative launch
+// (ceil(NP / 8) CTAs).  *bar counts grid-barrier arrivals from zero over the
+// caller's sequence of launches; `base` is the count before this launch
+// (each launch adds 2 ceil(NP / 8)).
 cudaError_t launch_plain_generation(const StepArgs& a, int k, const InstDesc& d, float* u_scratch,
-                                    float* fu_scratch, int* topk_scratch, cudaStream_t st);
+                                    float* fu_scratch, int* topk_scratch, unsigned* bar, unsigned base,
+                                    cudaStream_t st);
 
 // Batched path: executors listed in `work` (schedule order), all n_gens generations.
 struct FusedPlan {
@@ -104,7 +111,8 @@ struct TcPlan {
     int n_exec;
     const int* row_exec;     // device [n_rows] operand row -> executor (InstDesc.tc_row = first row)
     int n_rows;
-    const int* tiles;        // device [n_tiles][2] (executor, first individual)
+    const int* tiles;        // device [n_tiles][2]: tensor cores (first operand row, rows <= 128) over the
+                             // rows of one problem; FP32 GEMM (executor, first individual) of 64-row tiles
     int n_tiles;
     const long long* brow;   // device [n_prob] first B row of each problem
     int* topk_all;           // device [n_indiv] pbest pools
@@ -134,8 +142,9 @@ cudaError_t launch_tc_eval(const InstDesc* desc, const TcPlan& p, const float* p
 size_t rot_simt_smem();
 cudaError_t launch_rot_simt(const InstDesc* desc, const int* tiles, int n_tiles, const float* rows, const float* shift,
                             const float* rotT, float* f_out, cudaStream_t st);
-cudaError_t launch_tc_generation(const StepArgs& a, const TcPlan& p, cudaStream_t st, cudaEvent_t gemm0 = nullptr,
-                                 cudaEvent_t gemm1 = nullptr);
+// ev (may be null): six events recorded before the prologue, trial, GEMM,
+// selection and tie kernels and after the last.
+cudaError_t launch_tc_generation(const StepArgs& a, const TcPlan& p, cudaStream_t st, cudaEvent_t* ev = nullptr);
 
 // Evolver.
 cudaError_t launch_outer_init(int n_groups, int n_out, Key key, float* opop, float* ofit, cudaStream_t st);

@@ -79,23 +79,37 @@ cudaError_t launch_init(const InstDesc* desc, int n_inst, int max_np, int max_dp
 }
 
 // ---------------------------------------------------------------- eval
-// Warp per row.  Dynamic shared: per warp 4 * max_dpad floats.
+// Warp per row.  Dynamic shared: per warp 4 * max_dpad floats.  Population
+// rows (pt_inst == nullptr): row r of the fitness layout, executor
+// row_inst[r].  Caller-given points (pt_inst != nullptr): point r is
+// pop[r * ldx ..], of executor pt_inst[r]; an executor id outside
+// [0, n_inst) or a dimension above ldx latches EINVAL (1) in *status and
+// yields NaN.
 template <bool F64>
 __global__ void __launch_bounds__(256) k_eval(const InstDesc* __restrict__ desc, const int* __restrict__ row_inst,
                                               long long n_rows, const float* __restrict__ pop,
                                               const float* __restrict__ rotT, const float* __restrict__ shift,
                                               void* f_out, int nan_inf, int scratch, int skip_tc,
-                                              const float* __restrict__ mlp_x, const float* __restrict__ mlp_y) {
+                                              const float* __restrict__ mlp_x, const float* __restrict__ mlp_y,
+                                              const int* __restrict__ pt_inst, int ldx, int n_inst, int* status) {
     extern __shared__ __align__(16) float sm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float* wb = sm + (size_t)warp * scratch;
     for (long long row = (long long)blockIdx.x * (blockDim.x >> 5) + warp; row < n_rows;
          row += (long long)gridDim.x * (blockDim.x >> 5)) {
-        const int k = row_inst[row];
+        const int k = pt_inst ? pt_inst[row] : row_inst[row];
+        if (pt_inst && (k < 0 || k >= n_inst || desc[k].dim > ldx)) {  // warp-uniform
+            if (lane == 0) {
+                set_status(status, 1);
+                if (F64) reinterpret_cast<double*>(f_out)[row] = __longlong_as_double(0x7FF8000000000000LL);
+                else reinterpret_cast<float*>(f_out)[row] = __int_as_float(0x7FC00000);
+            }
+            continue;
+        }
         const InstDesc d = desc[k];
         if (skip_tc && (d.on_tc || d.obj == kMlp)) continue;  // warp-uniform: one row per warp
         const long long i = row - d.fit_off;
-        const float* x = pop + d.pop_off + i * d.dpad;
+        const float* x = pt_inst ? pop + row * (long long)ldx : pop + d.pop_off + i * d.dpad;
         const float* o = shift + d.shift_off;
         const float* RT = rotT + d.rot_off;
         if (d.obj == kMlp) {  // warp-uniform; lanes take inputs n = lane, lane + 32, ...
@@ -158,7 +172,8 @@ static int num_sms() {
 
 cudaError_t launch_eval(const InstDesc* desc, const int* row_inst, long long n_rows, const float* pop,
                         const float* rotT, const float* shift, bool f64, void* f_out, bool nan_inf, int max_dpad,
-                        cudaStream_t st, bool skip_tc, const float* mlp_x, const float* mlp_y) {
+                        cudaStream_t st, bool skip_tc, const float* mlp_x, const float* mlp_y, const int* pt_inst,
+                        int ldx, int n_inst, int* status) {
     if (n_rows <= 0) return cudaSuccess;
     const int scratch = 4 * max_dpad;  // floats per warp: two buffers of max_dpad doubles
     const size_t smem = (size_t)8 * scratch * sizeof(float);
@@ -168,11 +183,13 @@ cudaError_t launch_eval(const InstDesc* desc, const int* row_inst, long long n_r
     if (f64) {
         cudaFuncSetAttribute(k_eval<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_eval<true><<<(unsigned)blocks, 256, smem, st>>>(desc, row_inst, n_rows, pop, rotT, shift, f_out,
-                                                          nan_inf, scratch, skip_tc ? 1 : 0, mlp_x, mlp_y);
+                                                          nan_inf, scratch, skip_tc ? 1 : 0, mlp_x, mlp_y,
+                                                          pt_inst, ldx, n_inst, status);
     } else {
         cudaFuncSetAttribute(k_eval<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_eval<false><<<(unsigned)blocks, 256, smem, st>>>(desc, row_inst, n_rows, pop, rotT, shift, f_out,
-                                                           nan_inf, scratch, skip_tc ? 1 : 0, mlp_x, mlp_y);
+                                                           nan_inf, scratch, skip_tc ? 1 : 0, mlp_x, mlp_y,
+                                                           pt_inst, ldx, n_inst, status);
     }
     return cudaGetLastError();
 }
@@ -239,50 +256,91 @@ cudaError_t launch_best(const InstDesc* desc, int n_inst, const float* fit, floa
 
 // ---------------------------------------------------------- plain path
 // The FP32 baseline: one executor per launch, one generation per launch,
-// everything through global memory, no fusion, no graph, no tuning.
-__global__ void k_plain_prologue(StepArgs a, int k, int* topk) {
+// everything through global memory, no fusion, no graph, no tuning.  The
+// launch is cooperative (all its CTAs resident at once), so the generation's
+// three phases -- pbest pool, trials with their evaluation, selection -- are
+// separated by grid-wide barriers inside the one launch: every trial is built
+// from the generation-start population before any row is replaced.
+
+// Polls of the grid barrier before it gives up: with a 100 ns back-off per
+// poll, well over 0.1 s, far beyond any phase of one plain generation.
+constexpr uint32_t kGridWaitLimit = 1u << 21;
+
+// Grid-wide barrier of a cooperative launch.  Thread 0 of every CTA arrives
+// by one atomic increment of *count (after a fence, so the CTA's writes are
+// visible first) and polls until *count reaches `target`: the arrivals of
+// this barrier and of the call's earlier ones.  Gives up after
+// kGridWaitLimit polls, latching METADE_ETIMEOUT (4), and the CTA returns.
+__device__ bool grid_barrier(unsigned* count, unsigned target, int* status) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(count, 1u);
+        bool ok = false;
+        for (uint32_t it = 0; it < kGridWaitLimit; ++it) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+            if (v >= target) {
+                ok = true;
+                break;
+            }
+            __nanosleep(100);
+        }
+        if (!ok) set_status(status, 4);
+        __threadfence();
+        ok_s = ok ? 1 : 0;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+// Grid: ceil(NP / 8) CTAs of 256 threads (a warp per individual).  Dynamic
+// shared memory: 4 dpad floats per warp.  bar counts barrier arrivals within
+// the caller's sequence of launches; this launch's barriers wait for
+// base + gridDim.x and base + 2 gridDim.x.
+__global__ void __launch_bounds__(256) k_plain_gen(StepArgs a, int k, int* topk, float* uscr, float* fuscr,
+                                                   unsigned* bar, unsigned base) {
+    extern __shared__ __align__(16) float sm[];
     const InstDesc d = a.desc[k];
     const Strat s = load_strat(a.theta + 6 * k, d.np);
-    if (!s.ok) {
-        if (threadIdx.x == 0) set_status(a.status, 1);
+    // An invalid theta (the same decision in every CTA), or a barrier of an
+    // earlier launch that gave up: no work, but every CTA still counts its two
+    // arrivals so that the barriers of later launches keep their targets.
+    const bool skip = !s.ok || *(volatile int*)a.status == 4;
+    if (skip) {
+        if (threadIdx.x == 0) atomicAdd(bar, 2u);
+        if (!s.ok && blockIdx.x == 0 && threadIdx.x == 0) set_status(a.status, 1);
         return;
     }
-    block_topk(a.fit + d.fit_off, d.np, d.kp, topk);
-}
+    // phase 1: best and the pbest pool from the generation-start fitness
+    if (blockIdx.x == 0) block_topk(a.fit + d.fit_off, d.np, d.kp, topk);
+    if (!grid_barrier(bar, base + gridDim.x, a.status)) return;
 
-__global__ void __launch_bounds__(256) k_plain_trial(StepArgs a, int k, const int* __restrict__ topk, float* uscr,
-                                                     float* fuscr) {
-    extern __shared__ __align__(16) float sm[];
-    const InstDesc d = a.desc[k];
-    const Strat s = load_strat(a.theta + 6 * k, d.np);
-    if (!s.ok) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (i >= d.np) return;
-    float* db = sm + (size_t)warp * 2 * d.dpad;
-    float* zb = db + d.dpad;
-    const Ctr c = make_ctr(a.key, (uint32_t)d.stream, a.gen0, (uint32_t)i, a.epoch_dev ? *a.epoch_dev : a.epoch);
-    Indiv v;
-    indiv_setup(s, c, i, d.np, d.dim, d.kp, topk, topk[0], v);
-    const int L = s.cs == 2 ? exp_length(c, d.dim, s.cri) : 0;
-    const float* X = a.pop + d.pop_off;
-    warp_trial(s, c, v, i, d.dim, L, X, d.dpad, a.shift + d.shift_off, a.lo, a.hi,
-               uscr + d.pop_off + (long long)i * d.dpad, db);
-    __syncwarp();
-    warp_rotate<float>(d.dim, a.rotT + d.rot_off, d.dpad, db, zb);
-    __syncwarp();
-    const float f = warp_objective<float>(d.obj, d.dim, zb);
-    if (lane == 0) fuscr[d.fit_off + i] = nan_to_inf(f);
-}
+    const float* o = a.shift + d.shift_off;
+    const float* RT = a.rotT + d.rot_off;
+    // phase 2: trial and its FP32 evaluation, a warp per individual
+    if (i < d.np) {
+        float* db = sm + (size_t)warp * 4 * d.dpad;
+        float* zb = db + d.dpad;
+        const Ctr c = make_ctr(a.key, (uint32_t)d.stream, a.gen0, (uint32_t)i, a.epoch_dev ? *a.epoch_dev : a.epoch);
+        Indiv v;
+        indiv_setup(s, c, i, d.np, d.dim, d.kp, topk, topk[0], v);
+        const int L = s.cs == 2 ? exp_length(c, d.dim, s.cri) : 0;
+        warp_trial(s, c, v, i, d.dim, L, a.pop + d.pop_off, d.dpad, o, a.lo, a.hi,
+                   uscr + d.pop_off + (long long)i * d.dpad, db);
+        __syncwarp();
+        warp_rotate<float>(d.dim, RT, d.dpad, db, zb);
+        __syncwarp();
+        const float f = warp_objective<float>(d.obj, d.dim, zb);
+        if (lane == 0) fuscr[d.fit_off + i] = nan_to_inf(f);
+        __syncwarp();
+    }
+    if (!grid_barrier(bar, base + 2 * gridDim.x, a.status)) return;
 
-__global__ void __launch_bounds__(256) k_plain_select(StepArgs a, int k, const float* __restrict__ uscr,
-                                                      const float* __restrict__ fuscr) {
-    extern __shared__ __align__(16) float sm[];
-    const InstDesc d = a.desc[k];
-    const Strat s = load_strat(a.theta + 6 * k, d.np);
-    if (!s.ok) return;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i = blockIdx.x * (blockDim.x >> 5) + warp;
+    // phase 3: greedy selection (near ties decided precisely) and row copy
     if (i >= d.np) return;
     float* X = a.pop + d.pop_off + (long long)i * d.dpad;
     const float* U = uscr + d.pop_off + (long long)i * d.dpad;
@@ -295,8 +353,6 @@ __global__ void __launch_bounds__(256) k_plain_select(StepArgs a, int k, const f
         for (int j = lane; j < d.dim; j += 32) diff = diff || (U[j] != X[j]);
         if (!__any_sync(kFull, diff)) tie = false, fn = fx;  // trial == target
     }
-    const float* o = a.shift + d.shift_off;
-    const float* RT = a.rotT + d.rot_off;
     if (tie && a.tie_fp64) {
         double* db = reinterpret_cast<double*>(sm + (size_t)warp * 4 * d.dpad);
         const double eu = nan_to_inf(warp_eval64(d.obj, d.dim, U, o, RT, d.dpad, db, db + d.dpad));
@@ -321,18 +377,17 @@ __global__ void __launch_bounds__(256) k_plain_select(StepArgs a, int k, const f
 }
 
 cudaError_t launch_plain_generation(const StepArgs& a, int k, const InstDesc& d, float* uscr, float* fuscr,
-                                    int* topk, cudaStream_t st) {
-    k_plain_prologue<<<1, 256, 0, st>>>(a, k, topk);
+                                    int* topk, unsigned* bar, unsigned base, cudaStream_t st) {
     const int blocks = (d.np + 7) / 8;
-    const size_t smem_t = (size_t)8 * 2 * d.dpad * sizeof(float);
-    const size_t smem_s = (size_t)8 * 4 * d.dpad * sizeof(float);
-    if (smem_s > 48 * 1024) {
-        cudaFuncSetAttribute(k_plain_trial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
-        cudaFuncSetAttribute(k_plain_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s);
+    const size_t smem = (size_t)8 * 4 * d.dpad * sizeof(float);
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(k_plain_gen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
     }
-    k_plain_trial<<<blocks, 256, smem_t, st>>>(a, k, topk, uscr, fuscr);
-    k_plain_select<<<blocks, 256, smem_s, st>>>(a, k, uscr, fuscr);
-    return cudaGetLastError();
+    StepArgs aa = a;
+    int kk = k;
+    void* args[] = {&aa, &kk, &topk, &uscr, &fuscr, &bar, &base};
+    return cudaLaunchCooperativeKernel((const void*)k_plain_gen, dim3(blocks), dim3(256), args, smem, st);
 }
 
 // ------------------------------------------------ batched path, small D

@@ -19,7 +19,11 @@
 // stand-in symbol, not a device address.  The device address is obtained with
 // cudaGetSymbolAddress once per device, with that device current, on the
 // first call made while it is current; that first call should therefore come
-// before any stream capture.
+// before any stream capture.  The address is cached for the life of the
+// process: after cudaDeviceReset (or anything else that destroys the device's
+// primary context and unloads the library's device code) the cached address
+// is stale, so a process that resets a device must not call this entry point
+// on that device again.
 #include <cstring>
 #include <mutex>
 
@@ -167,6 +171,7 @@ extern "C" METADE_API metade_status metade_plain_step_noalloc(float* pop, float*
                                                               uint64_t seed, uint32_t stream_id, uint32_t epoch,
                                                               uint32_t gen, int32_t p_best_pct, void* stream) {
     if (!pop || !fit || !theta || !shift || !rot) return METADE_EINVAL;
+    if (reinterpret_cast<uintptr_t>(pop) & 15) return METADE_EINVAL;  // rows are read and written as float4
     if (np < 4 || np > 1024 || dim < 1 || dim > 1536 || obj < 0 || obj > 5 || epoch > 0xFFFFu) return METADE_EINVAL;
     if (!(lo < hi) || p_best_pct < 0 || p_best_pct > 100) return METADE_EINVAL;
     const int dpad = (dim + 3) & ~3;
@@ -208,8 +213,12 @@ extern "C" METADE_API metade_status metade_plain_step_noalloc(float* pop, float*
             cudaFuncSetAttribute(k_na_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))
             return METADE_ECUDA;
     }
+    // each launch is checked with cudaPeekAtLastError, which leaves the error
+    // state of other code untouched (cudaGetLastError would clear it)
     k_na_prologue<<<1, 256, 0, st>>>(a);
+    if (cudaPeekAtLastError() != cudaSuccess) return METADE_ECUDA;
     k_na_trial<<<blocks, 256, smem, st>>>(a);
+    if (cudaPeekAtLastError() != cudaSuccess) return METADE_ECUDA;
     k_na_select<<<blocks, 256, smem, st>>>(a);
-    return cudaGetLastError() == cudaSuccess ? METADE_OK : METADE_ECUDA;
+    return cudaPeekAtLastError() == cudaSuccess ? METADE_OK : METADE_ECUDA;
 }

@@ -191,7 +191,8 @@ __global__ void k_wait_check(uint32_t rounds, int arrive, long long* out, int* s
 
 struct TcGemmArgs {
     const InstDesc* desc;
-    const int* tiles;         // [n_tiles][2]: executor, first individual of the 128-row tile
+    const int* tiles;         // [n_tiles][2]: first operand row of the tile, rows (<= 128), all of one problem
+    const int* row_exec;      // operand row -> executor
     const long long* brow;    // per problem: first row of its padded R in the B operand
     float* fu;                // out: f(u) per individual (fitness index)
     int kt;                   // K tiles (128 bytes: 64 BF16 or 128 e4m3 elements)
@@ -214,7 +215,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     k_rot_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
              const __grid_constant__ CUtensorMap tmAlo, const __grid_constant__ CUtensorMap tmBlo, TcGemmArgs a) {
     extern __shared__ uint8_t smraw[];
-    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], acc_full[2], acc_empty[2], part_ready[4][2];
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], acc_full[2], acc_empty[2], part_ready[4][2], drain;
     __shared__ __align__(16) float part[2][kParts - 1][kBM][8];
     __shared__ uint32_t tmem_base;
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
@@ -223,9 +224,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int nst = a.split ? 2 : kStages;  // pipeline depth that fits shared memory
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    const int k = a.tiles[2 * blockIdx.x], m0 = a.tiles[2 * blockIdx.x + 1];
-    const InstDesc d = a.desc[k];
-    const int arow = d.tc_row + m0;  // first operand row of the tile
+    const int arow = a.tiles[2 * blockIdx.x], nr = a.tiles[2 * blockIdx.x + 1];  // first operand row, rows
+    const InstDesc d = a.desc[a.row_exec[arow]];  // dim, objective and problem are those of every row of the tile
     const int brow0 = (int)a.brow[d.prob];
     const int nchunks = (d.dim + kBN - 1) / kBN;
     const int total = nchunks * a.kt;
@@ -246,6 +246,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             mbar_init(&acc_empty[b], kEpiWarps);  // one arrival per epilogue warp
             for (int q = 0; q < 4; ++q) mbar_init(&part_ready[q][b], kParts - 1);
         }
+        mbar_init(&drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tc_fence_before();
@@ -328,6 +329,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 set_status(a.status, kStatusTimeout);
                 // drain copies still in flight into this CTA's shared memory (bounded)
                 for (int it = consumed; it < issued; ++it) mbar_wait(&full[it % nst], (uint32_t)(it / nst) & 1u);
+                // and every MMA already issued: a commit tracks all of this thread's earlier tcgen05
+                // operations, so once `drain` completes (bounded) none still writes TMEM or reads
+                // shared memory when the CTA frees them
+                mma_commit(&drain);
+                mbar_wait(&drain, 0u);
             }
         }
         __syncwarp();
@@ -337,7 +343,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         ObjR acc;                           // part 0: the row's running state; parts 1..: the chunk's
         const int row = 32 * qd + lane;     // tile row of this thread
         // FP8: dequantisation factor of this row (rows past the executor are not used)
-        const float zs = (a.fp8 && m0 + row < d.np) ? a.ascale[arow + row] * a.bscale[d.prob] : 1.0f;
+        const float zs = (a.fp8 && row < nr) ? a.ascale[arow + row] * a.bscale[d.prob] : 1.0f;
         bool eok = true;
         for (int c = 0; c < nchunks; ++c) {
             const int b = c & 1;
@@ -409,8 +415,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         if (!eok) {
             if (lane == 0) set_status(a.status, kStatusTimeout);
-        } else if (half == 0 && m0 + row < d.np) {
-            a.fu[d.fit_off + m0 + row] = nan_to_inf(acc.finish(d.obj, d.dim));
+        } else if (half == 0 && row < nr) {
+            const InstDesc& e = a.desc[a.row_exec[arow + row]];  // this row's executor
+            a.fu[e.fit_off + (arow + row - e.tc_row)] = nan_to_inf(acc.finish(d.obj, d.dim));
         }
     }
     tc_fence_before();
@@ -760,6 +767,7 @@ cudaError_t launch_tc_eval(const InstDesc* desc, const TcPlan& p, const float* p
     TcGemmArgs g;
     g.desc = desc;
     g.tiles = p.tiles;
+    g.row_exec = p.row_exec;
     g.brow = p.brow;
     g.fu = fit;  // the epilogue writes f of each row straight into the fitness array
     g.kt = p.kp / (p.fp8 ? kBK8 : kBK);
@@ -778,9 +786,10 @@ cudaError_t launch_wait_check(uint32_t rounds, int arrive, long long* out, int* 
     return cudaGetLastError();
 }
 
-cudaError_t launch_tc_generation(const StepArgs& a, const TcPlan& p, cudaStream_t st, cudaEvent_t gemm0,
-                                 cudaEvent_t gemm1) {
+cudaError_t launch_tc_generation(const StepArgs& a, const TcPlan& p, cudaStream_t st, cudaEvent_t* ev) {
+    if (ev) cudaEventRecord(ev[0], st);
     k_tc_prologue<<<p.n_exec, 256, 0, st>>>(a, p.execs, p.topk_all);
+    if (ev) cudaEventRecord(ev[1], st);
     const int blocks = (p.n_rows + 7) / 8;
     size_t smem_t = (size_t)8 * p.max_dpad * sizeof(float);
     const size_t smem_s = (size_t)4 * p.max_dpad * (a.tie_fp64 ? sizeof(double) : sizeof(float));
@@ -789,7 +798,7 @@ cudaError_t launch_tc_generation(const StepArgs& a, const TcPlan& p, cudaStream_
     k_tc_trial<<<blocks, 256, smem_t, st>>>(a, p.row_exec, p.n_rows, p.topk_all, p.uscr, p.aq, p.split ? p.aq_lo : nullptr,
                                             p.kp, p.max_dpad, p.fp8, p.ascale);
     if (p.simt) {
-        if (gemm0) cudaEventRecord(gemm0, st);
+        if (ev) cudaEventRecord(ev[2], st);
         e = launch_rot_simt(a.desc, p.tiles, p.n_tiles, p.uscr, a.shift, a.rotT, p.fu, st);
         if (e != cudaSuccess) return e;
     } else {
@@ -799,6 +808,7 @@ cudaError_t launch_tc_generation(const StepArgs& a, const TcPlan& p, cudaStream_
         TcGemmArgs g;
         g.desc = a.desc;
         g.tiles = p.tiles;
+        g.row_exec = p.row_exec;
         g.brow = p.brow;
         g.fu = p.fu;
         g.kt = p.kp / (p.fp8 ? kBK8 : kBK);
@@ -807,18 +817,19 @@ cudaError_t launch_tc_generation(const StepArgs& a, const TcPlan& p, cudaStream_
         g.ascale = p.ascale;
         g.bscale = p.bscale;
         g.status = a.status;
-        if (gemm0) cudaEventRecord(gemm0, st);
+        if (ev) cudaEventRecord(ev[2], st);
         k_rot_tc<<<p.n_tiles, kTcThreads, smem_g, st>>>(p.mapA, p.mapB, p.split ? p.mapAlo : p.mapA, p.split ? p.mapBlo : p.mapB,
                                                  g);
     }
-    if (gemm1) cudaEventRecord(gemm1, st);
+    if (ev) cudaEventRecord(ev[3], st);
     e = cudaMemsetAsync(p.tie_count, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     k_tc_select<<<blocks, 256, 0, st>>>(a, p.row_exec, p.n_rows, p.uscr, p.fu, p.tie_list, p.tie_count);
+    if (ev) cudaEventRecord(ev[4], st);
     e = cudaFuncSetAttribute(k_tc_ties, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s);
     if (e != cudaSuccess) return e;
-    k_tc_ties<<<p.tie_ctas, 256, smem_s, st>>>(a, p.row_exec, p.uscr, p.tie_list,
-                                                                                p.tie_count, p.max_dpad);
+    k_tc_ties<<<p.tie_ctas, 256, smem_s, st>>>(a, p.row_exec, p.uscr, p.tie_list, p.tie_count, p.max_dpad);
+    if (ev) cudaEventRecord(ev[5], st);
     return cudaGetLastError();
 }
 

@@ -38,7 +38,7 @@ def test_mlp_init_eval_and_teacher_optimum():
     assert plan["mlp"]["executors"] == 2 and plan["mlp"]["rows"] == 104
     M.metade_init(b.ctx, b.pop, b.fit, 0)
     f64 = torch.empty(b.n_indiv, dtype=torch.float64, device="cuda")
-    M.metade_eval(b.ctx, b.pop, M.METADE_FP64, f64)
+    M.metade_eval_pop(b.ctx, b.pop, M.METADE_FP64, f64)
     assert M.metade_sync(b.ctx) == M.METADE_OK
     pops, fits = b.get_population()
     f64 = f64.cpu().numpy()
@@ -52,7 +52,7 @@ def test_mlp_init_eval_and_teacher_optimum():
         pops[k][3] = wl.problems[k].shift
     b.set_population(pops, fits)
     f32 = torch.empty(b.n_indiv, dtype=torch.float32, device="cuda")
-    M.metade_eval(b.ctx, b.pop, M.METADE_FP32, f32)
+    M.metade_eval_pop(b.ctx, b.pop, M.METADE_FP32, f32)
     b.sync()
     f32 = f32.cpu().numpy()
     for k in (0, 1):

@@ -91,8 +91,8 @@ def test_eval_fp32_and_fp64(near):
     b.set_population(pops)
     f32 = torch.zeros(b.n_indiv, dtype=torch.float32, device="cuda")
     f64 = torch.zeros(b.n_indiv, dtype=torch.float64, device="cuda")
-    M.metade_eval(b.ctx, b.pop, M.METADE_FP32, f32)
-    M.metade_eval(b.ctx, b.pop, M.METADE_FP64, f64)
+    M.metade_eval_pop(b.ctx, b.pop, M.METADE_FP32, f32)
+    M.metade_eval_pop(b.ctx, b.pop, M.METADE_FP64, f64)
     b.sync()
     f32, f64 = f32.cpu().numpy(), f64.cpu().numpy()
     for k in range(wl.n_inst):
@@ -101,6 +101,69 @@ def test_eval_fp32_and_fp64(near):
         sl = slice(b.fit_off[k], b.fit_off[k] + int(wl.inst_np[k]))
         check_fitness_fp32(f32[sl], pops[k], p, floor=1e-3 if near else 0.0)
         assert rel_err(f64[sl], want, 1e-12).max() < 1e-9, (k, p.obj, p.dim)
+    b.close()
+
+
+def test_eval_caller_points_fp64_and_fp32():
+    """metade_eval on caller-given points (the final error f(x_best) - f* of
+    Sec. IV-A is one such call): 300 points of random executors in one
+    [n][ldx] buffer.  FP64 against the oracle's FP64 objective within 1e-12
+    relative; FP32 bit-equal to the whole-population evaluation of the same
+    rows (same kernel arithmetic); an executor id out of range latches EINVAL
+    and yields NaN without touching the other points."""
+    import torch
+    import paper_2502_10470_gb300 as M
+    wl = _ragged_many()
+    b = make_batch(wl, 0)
+    rng = np.random.default_rng(12)
+    n = 300
+    inst = rng.integers(0, wl.n_inst, n).astype(np.int32)
+    ldx = int(np.max(b.dpad)) + 4
+    x = np.zeros((n, ldx), dtype=np.float32)
+    for r in range(n):
+        d = int(b.dims[inst[r]])
+        x[r, :d] = synth.random_population(rng, 1, d)[0]
+    xd = torch.from_numpy(x).cuda()
+    idd = torch.from_numpy(inst).cuda()
+    f64 = torch.zeros(n, dtype=torch.float64, device="cuda")
+    f32 = torch.zeros(n, dtype=torch.float32, device="cuda")
+    M.metade_eval(b.ctx, xd, n, idd, ldx, M.METADE_FP64, f64)
+    M.metade_eval(b.ctx, xd, n, idd, ldx, M.METADE_FP32, f32)
+    b.sync()
+    f64, f32 = f64.cpu().numpy(), f32.cpu().numpy()
+    for r in range(n):
+        p = wl.problems[int(wl.inst_prob[inst[r]])]
+        want = oracle.eval_pop(p.obj, x[r:r + 1, :p.dim], p.shift, p.rot)[0]
+        assert abs(f64[r] - want) <= 1e-12 * max(abs(want), 1e-12), (r, p.obj, p.dim, f64[r], want)
+    # FP32: the same rows placed in the population and evaluated there
+    pops = [synth.random_population(rng, int(wl.inst_np[k]), int(b.dims[k])) for k in range(wl.n_inst)]
+    first = {}
+    for r in range(n):
+        k = int(inst[r])
+        if k not in first:
+            first[k] = r
+            pops[k][0] = x[r, :int(b.dims[k])]
+    b.set_population(pops)
+    fp = torch.zeros(b.n_indiv, dtype=torch.float32, device="cuda")
+    M.metade_eval_pop(b.ctx, b.pop, M.METADE_FP32, fp)
+    b.sync()
+    fp = fp.cpu().numpy()
+    for k, r in first.items():
+        assert fp[b.fit_off[k]] == f32[r]
+    # a bad executor id: EINVAL on the device, NaN for that point only
+    bad = idd.clone()
+    bad[7] = wl.n_inst
+    out = torch.zeros(n, dtype=torch.float64, device="cuda")
+    M.metade_eval(b.ctx, xd, n, bad, ldx, M.METADE_FP64, out)
+    assert M.metade_sync(b.ctx) == M.METADE_EINVAL
+    out = out.cpu().numpy()
+    assert np.isnan(out[7]) and np.array_equal(np.delete(out, 7), np.delete(f64, 7))
+    # host-side checks: ldx not a multiple of 4, unsupported precision
+    with pytest.raises(M.MetadeError):
+        M.metade_eval(b.ctx, xd, n, idd, ldx - 1, M.METADE_FP64, out)
+    with pytest.raises(M.MetadeError):
+        M.metade_eval(b.ctx, xd, n, idd, ldx, M.METADE_BF16, out)
+    M.metade_eval(b.ctx, xd, 0, idd, ldx, M.METADE_FP64, out)  # n = 0: nothing to do
     b.close()
 
 
@@ -602,6 +665,24 @@ def test_zero_generations_and_empty_batch():
     M.metade_inner_step(e.ctx, e.pop, e.fit, e.theta, 0, 0, 3, None, None)
     assert M.metade_sync(e.ctx) == M.METADE_OK
     e.close()
+
+
+def test_plain_path_one_launch_per_executor_generation():
+    """The plain FP32 arm is one cooperative launch per executor per
+    generation (its three phases separated by grid barriers inside the
+    launch); the generation still matches the oracle (the parity tests above
+    run the plain path too)."""
+    import paper_2502_10470_gb300 as M
+    wl = _wl_small()
+    b = make_batch(wl, 1)
+    pops, fits = random_state(wl, seed=6)
+    b.set_population(pops, fits)
+    b.set_theta(wl.theta)
+    l0 = M.metade_launch_count(b.ctx)
+    M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 0, 3, None, None)
+    assert M.metade_launch_count(b.ctx) - l0 == 3 * wl.n_inst
+    assert M.metade_sync(b.ctx) == M.METADE_OK
+    b.close()
 
 
 def test_bad_configs_rejected_on_host():

@@ -31,7 +31,7 @@ PIPE = pytest.mark.parametrize("prec", [0, 1, 2, 3], ids=["fp32-simt", "bf16", "
 
 
 def _on_pipeline(wl, prec):
-    return sum(1 for p in wl.problems if (((p.dim + 3) // 4) * 4 > 256 if prec == 0 else p.dim >= 256))
+    return sum(1 for p in wl.problems if (((p.dim + 3) // 4) * 4 > 256 if prec == 0 else p.dim >= 129))
 
 
 def _wl(seed=41):
@@ -226,4 +226,125 @@ def test_tc_epilogue_all_objectives_multi_chunk(prec):
     for k, p in enumerate(probs):
         frac = check_fitness(fits[k], pops[k], p, TOL[prec], UNIT[prec])
         print("D", p.dim, "obj", p.obj, "beyond rtol:", frac)
+    b.close()
+
+
+# ------------------------------------------------ 128 < D < 256 on the tensor cores
+def _wl_mid(seed=53):
+    """Widths between the tile kernels' reach and 256 (D = 129, 200, 255),
+    three executors per problem with ragged populations (17 + 61 + 130 = 208
+    rows), so that a 128-row GEMM tile spans several executors of one problem
+    and the problem's last tile is partial."""
+    rng = np.random.default_rng(seed)
+    dims, objs = [129, 200, 255, 200], [2, 3, 5, 1]
+    probs = [synth.make_problem(rng, d, o) for d, o in zip(dims, objs)]
+    nps = [17, 61, 130]
+    inst_prob = np.repeat(np.arange(len(probs)), len(nps)).astype(np.int32)
+    inst_np = np.tile(np.array(nps, dtype=np.int32), len(probs))
+    n = len(inst_np)
+    th = synth.random_theta(rng, n)
+    th[:, 5] = np.arange(n) % 3 + 1
+    wl = synth.Workload(name="tc-mid", problems=probs, inst_np=inst_np, inst_prob=inst_prob,
+                        inst_group=np.arange(n, dtype=np.int32), n_groups=n, n_out=0, inner_gens=1, outer_gens=1,
+                        seed=4, one_shot=0, theta=th)
+    wl.theta = feasible_theta(wl.theta, wl.inst_np)
+    return wl
+
+
+@PRECS
+def test_tc_mid_width_one_step_against_oracle(prec):
+    """D = 129, 200 and 255 run on the tensor cores by default (D_pad > 128):
+    one step from a shared state, trials against the oracle at TRIAL_ATOL and
+    fitness within the precision's budget against FP64 at the GPU's trials.
+    The GEMM's tiles cross executor boundaries here, so a fitness written to
+    the wrong executor or row fails the comparison."""
+    import paper_2502_10470_gb300 as M
+    wl = _wl_mid()
+    b = make_batch(wl, M.METADE_PATH_BATCHED, prec=prec)
+    plan = json.loads(M.metade_plan_info(b.ctx))
+    assert plan["tc_min_dim"] == 129
+    assert plan["tensor_core"]["executors"] == wl.n_inst
+    assert plan["tensor_core"]["tiles"] == 2 * len(wl.problems)  # 208 rows per problem: tiles of 128 + 80
+    pops, fits = random_state(wl, seed=8, fit_inf=True)
+    b.set_population(pops, fits)
+    b.set_theta(wl.theta)
+    M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 2, 5, 1, b.best_f, b.best_i)
+    assert M.metade_sync(b.ctx) == M.METADE_OK
+    npops, nfits = b.get_population()
+    for k in range(wl.n_inst):
+        p = wl.problems[int(wl.inst_prob[k])]
+        out = oracle.pde_step(pops[k], fits[k], wl.theta[k], p.obj, p.shift, p.rot, seed=wl.seed, stream=k,
+                              epoch=2, gen=5)
+        assert np.abs(npops[k] - out["trial"]).max() < TRIAL_ATOL
+        frac = check_fitness(nfits[k], npops[k], p, TOL[prec], UNIT[prec])
+        print("executor", k, "D", p.dim, "obj", p.obj, "beyond rtol:", frac)
+    bf = b.best_f.cpu().numpy()
+    for k in range(wl.n_inst):
+        assert bf[k] == nfits[k].min()
+    b.close()
+
+
+@pytest.mark.parametrize("prec", [1, 3], ids=["bf16", "bf16x3"])
+def test_tc_mid_width_selection_over_generations(prec):
+    """Three generations with stored fitness on the mid-width workload: the
+    best never rises, and every selection whose fitness gap exceeds the
+    precision's tolerance matches the oracle's FP64 decision."""
+    import paper_2502_10470_gb300 as M
+    wl = _wl_mid(seed=59)
+    b = make_batch(wl, M.METADE_PATH_BATCHED, prec=prec)
+    pops, fits = random_state(wl, seed=9)
+    b.set_population(pops, fits)
+    b.set_theta(wl.theta)
+    last = [f.min() for f in fits]
+    for g in range(3):
+        pops, fits = b.get_population()
+        M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, g, 1, b.best_f, b.best_i)
+        assert M.metade_sync(b.ctx) == M.METADE_OK
+        npops, nfits = b.get_population()
+        for k in range(wl.n_inst):
+            p = wl.problems[int(wl.inst_prob[k])]
+            out = oracle.pde_step(pops[k], fits[k], wl.theta[k], p.obj, p.shift, p.rot, seed=wl.seed, stream=k,
+                                  epoch=0, gen=g)
+            decided = rel_err(out["ftrial"], fits[k]) > GAP[prec]
+            acc = np.any(npops[k] != pops[k], axis=1) | (nfits[k] != fits[k])
+            np.testing.assert_array_equal(acc[decided], out["accept"].astype(bool)[decided])
+            assert nfits[k].min() <= last[k]
+            last[k] = nfits[k].min()
+    b.close()
+
+
+def test_tc_min_dim_places_executors_and_autotune_picks_a_width():
+    """tc_min_dim = 256 keeps D < 256 on the FP32 kernels: bit-identical to an
+    FP32 context.  tc_min_dim = 0 lets metade_autotune time both widths (129
+    and 256) and keep the faster; the plan reports both timings."""
+    import paper_2502_10470_gb300 as M
+    wl = _wl_mid(seed=61)
+    pops, fits = random_state(wl, seed=3)
+    outs = {}
+    for name, kw in (("fp32", dict(prec=0)), ("bf16-256", dict(prec=1, tc_min_dim=256))):
+        b = make_batch(wl, M.METADE_PATH_BATCHED, **kw)
+        if name == "bf16-256":
+            plan = json.loads(M.metade_plan_info(b.ctx))
+            assert plan["tc_min_dim"] == 256 and "tensor_core" not in plan
+        b.set_population(pops, fits)
+        b.set_theta(wl.theta)
+        M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 0, 3, None, None)
+        assert M.metade_sync(b.ctx) == M.METADE_OK
+        outs[name] = b.get_population()
+        b.close()
+    for k in range(wl.n_inst):
+        np.testing.assert_array_equal(outs["fp32"][0][k], outs["bf16-256"][0][k])
+        np.testing.assert_array_equal(outs["fp32"][1][k], outs["bf16-256"][1][k])
+    b = make_batch(wl, M.METADE_PATH_BATCHED, prec=1, tc_min_dim=0)
+    b.set_population(pops, fits)
+    b.set_theta(wl.theta)
+    M.metade_autotune(b.ctx, b.pop, b.fit, b.theta, 2)
+    plan = json.loads(M.metade_plan_info(b.ctx))
+    assert plan["tc_min_dim_auto"] and plan["tc_min_dim"] in (129, 256)
+    assert set(plan["tc_autotune_ms"]) == {"129", "256"}
+    p2, f2 = b.get_population()  # tuning ran on copies
+    for k in range(wl.n_inst):
+        np.testing.assert_array_equal(p2[k], pops[k])
+    M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 0, 2, None, None)
+    assert M.metade_sync(b.ctx) == M.METADE_OK
     b.close()

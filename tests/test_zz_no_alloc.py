@@ -35,6 +35,8 @@ def test_noalloc_matches_inner_step_on_two_calls(np_, dim, obj):
     rot = torch.tensor(p.rot.reshape(-1), device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
     for gen in (0, 1):
+        start_pop = pop.view(np_, dpad)[:, :dim].cpu().numpy()
+        start_fit = fit.cpu().numpy()
         M.metade_inner_step(ref.ctx, ref.pop, ref.fit, ref.theta, 0, gen, 1, None, None)
         st = M.metade_plain_step_noalloc(pop, fit, th, shift, rot, np_, dim, obj, -100.0, 100.0, 5, 0, 0, gen,
                                          10, stream)
@@ -49,6 +51,15 @@ def test_noalloc_matches_inner_step_on_two_calls(np_, dim, obj):
         assert np.all(np.abs(got_fit - want_fit) <= FIT_RTOL * np.maximum(np.abs(want_fit), 1.0))
         check_fitness_fp32(got_fit, got_pop, p)
         assert not np.array_equal(got_pop, pop0)  # the generation did something
+        # and against the FP64 oracle's generation from the same state: the
+        # selection wherever the fitness gap is clear, the accepted trials
+        out = oracle.pde_step(start_pop, start_fit, theta, obj, p.shift, p.rot, seed=5, stream=0, epoch=0, gen=gen)
+        took = np.any(got_pop != start_pop, axis=1)
+        gap = np.abs(out["ftrial"] - start_fit) / np.maximum(np.abs(start_fit), 1.0)
+        decided = gap > 2e-5
+        np.testing.assert_array_equal(took[decided], out["accept"].astype(bool)[decided])
+        both = took & out["accept"].astype(bool)
+        assert np.abs(got_pop[both] - out["trial"][both]).max(initial=0.0) < TRIAL_ATOL
     ref.close()
 
 
@@ -60,4 +71,8 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     st = M.metade_plain_step_noalloc(t, t, t, t, t, 1024, 1536, 0, -100.0, 100.0, 0, 0, 0, 0, 10, None)
     assert st == M.METADE_EINVAL
     st = M.metade_plain_step_noalloc(t, t, t, t, t, 3, 4, 0, -100.0, 100.0, 0, 0, 0, 0, 10, None)
+    assert st == M.METADE_EINVAL
+    # pop is read and written as float4 rows: a pointer off a 16-byte boundary is rejected on the host
+    big = torch.zeros(16 * 8 + 1, device="cuda")
+    st = M.metade_plain_step_noalloc(big[1:], t, t, t, t, 16, 8, 0, -100.0, 100.0, 0, 0, 0, 0, 10, None)
     assert st == M.METADE_EINVAL
