@@ -119,6 +119,12 @@ typedef struct {
                                   the tensor cores, the others in FP32 on the CUDA cores.  0 = let
                                   metade_autotune choose between 129 and 256 by speed (129 until it
                                   runs); > 0 fixes it.  Ignored with FP32.  Negative: EINVAL */
+    int32_t tc_unfused;        /* 0: BF16 tensor-core executors with D <= 256 (and FP32 difference-form
+                                  ties) run one fused kernel per generation (draws, trial, BF16 operand
+                                  in shared memory, tcgen05 GEMM, objective, selection, near ties) and
+                                  a commit kernel; 1: the five-kernel pipeline every other tensor-core
+                                  configuration uses (prologue, trial, GEMM, selection, ties), with
+                                  bit-identical results -- for comparison */
 } metade_config;
 
 typedef struct metade_ctx metade_ctx;

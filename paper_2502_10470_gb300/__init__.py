@@ -65,6 +65,7 @@ class metade_config(C.Structure):
         ("stream", C.c_void_p),
         ("evolver", C.c_int32),
         ("tc_min_dim", C.c_int32),
+        ("tc_unfused", C.c_int32),
     ]
 
 
@@ -136,7 +137,7 @@ def _i32p(a: np.ndarray):
 # ---------------------------------------------------------------- C names
 def metade_create(prob_dim, prob_obj, shift, rot, inst_np, inst_prob, inst_group=None, *, lo=-100.0, hi=100.0,
                   seed=0, one_shot=0, p_best_pct=10, n_out=0, prec=METADE_FP32, path=METADE_PATH_BATCHED,
-                  tie_fp64=0, stream=None, evolver=EVOLVER_DE, tc_min_dim=0) -> int:
+                  tie_fp64=0, stream=None, evolver=EVOLVER_DE, tc_min_dim=0, tc_unfused=0) -> int:
     """shift/rot: device float32 tensors (concatenated o_p and row-major R_p)."""
     pd, po, nps, ip = _i32(prob_dim), _i32(prob_obj), _i32(inst_np), _i32(inst_prob)
     ig = _i32(inst_group) if inst_group is not None else None
@@ -161,6 +162,7 @@ def metade_create(prob_dim, prob_obj, shift, rot, inst_np, inst_prob, inst_group
     cfg.stream = stream
     cfg.evolver = int(evolver)
     cfg.tc_min_dim = int(tc_min_dim)
+    cfg.tc_unfused = int(tc_unfused)
     out = C.c_void_p()
     _check(_lib().metade_create(C.byref(cfg), C.byref(out)), "metade_create")
     return out.value
@@ -255,7 +257,7 @@ def metade_autotune(ctx: int, pop, fit, theta, n_gens: int = 3) -> None:
 
 
 PROFILE_KINDS = ["fused_small", "fused_general", "tc_gemm", "tc_generation", "fused_tile_stream", "fused_tile",
-                 "mlp_generations", "tc_prologue", "tc_trial", "tc_select", "tc_ties"]
+                 "mlp_generations", "tc_prologue", "tc_trial", "tc_select", "tc_ties", "tc_fused", "tc_commit"]
 
 
 def metade_profile(ctx: int, enable: bool) -> None:
@@ -302,7 +304,7 @@ class Batch:
 
     def __init__(self, problems: Sequence, inst_np, inst_prob, inst_group=None, *, seed=0, one_shot=0,
                  p_best_pct=10, n_out=0, path=METADE_PATH_BATCHED, prec=METADE_FP32, lo=-100.0, hi=100.0,
-                 tie_fp64=0, device="cuda", stream=None, evolver=EVOLVER_DE, tc_min_dim=0):
+                 tie_fp64=0, device="cuda", stream=None, evolver=EVOLVER_DE, tc_min_dim=0, tc_unfused=0):
         import torch
         self.torch = torch
         self.device = torch.device(device)
@@ -322,7 +324,7 @@ class Batch:
         self.ctx = metade_create(dims, objs, self.shift_d, self.rot_d, self.inst_np, self.inst_prob, inst_group,
                                  lo=lo, hi=hi, seed=seed, one_shot=one_shot, p_best_pct=p_best_pct, n_out=n_out,
                                  prec=prec, path=path, tie_fp64=tie_fp64, stream=stream, evolver=evolver,
-                                 tc_min_dim=tc_min_dim)
+                                 tc_min_dim=tc_min_dim, tc_unfused=tc_unfused)
         self.dims = np.array([dims[p] for p in self.inst_prob], dtype=np.int32)
         self.pop_floats, self.n_indiv, self.n_groups = metade_layout(self.ctx)
         self.pop_off, self.fit_off, self.dpad = metade_offsets(self.ctx, self.n_inst)

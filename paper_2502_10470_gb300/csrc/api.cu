@@ -42,7 +42,9 @@ enum ProfKind {
     kProfTcTrial = 8,
     kProfTcSelect = 9,
     kProfTcTies = 10,
-    kProfKinds = 11
+    kProfTcFused = 11,
+    kProfTcCommit = 12,
+    kProfKinds = 13
 };
 
 struct ProfRec {
@@ -97,6 +99,7 @@ struct metade_ctx {
     std::vector<cudaEvent_t> prof_events;  // every event the records refer to (destroyed on read)
     // large-D executors on the tensor cores (prec BF16 / BF16X3)
     int tc_min_dim = kTcDefaultMinDim;  // executors with D >= this run on the GEMM pipeline
+    int tc_unfused = 0;                 // 1: the per-kernel pipeline even where the fused kernel applies
     bool tc_auto = false;               // metade_autotune picks tc_min_dim
     std::string tc_tuned;               // autotuner record: width -> ms
     bool tc = false;
@@ -434,6 +437,10 @@ metade_status setup_tc(metade_ctx* c) {
     t.kp = tc_kp;
     t.split = split ? 1 : 0;
     t.max_dpad = tc_max_dpad;
+    // BF16 with FP32 difference-form ties and operands of at most 256 elements:
+    // one fused kernel per generation
+    t.fused = (c->prec == METADE_BF16 && !c->tie_fp64 && !c->tc_unfused && tc_fused_fits(tc_kp)) ? 1 : 0;
+    t.gen_ctas = std::max(1, device_sms());
     // a tie keeps four rows of max_dpad in shared memory (FP64 with tie_fp64)
     if ((size_t)4 * tc_max_dpad * (c->tie_fp64 ? sizeof(double) : sizeof(float)) > kSmemLimit)
         return METADE_EUNSUPPORTED;
@@ -472,20 +479,23 @@ bool prof_pair(metade_ctx* c, cudaStream_t st, int kind, cudaEvent_t* a, cudaEve
 // Events between the kernels of one tensor-core generation (prologue, trial,
 // GEMM, selection, ties): ev[0..5], with a record per kernel and one for the
 // whole generation.
-bool prof_tc(metade_ctx* c, cudaStream_t st, cudaEvent_t* ev) {
+// The fused generation has four events: ranking, k_tc_gen, commit.
+bool prof_tc(metade_ctx* c, cudaStream_t st, cudaEvent_t* ev, bool fused) {
     if (!c->prof_on) return false;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return false;
-    for (int i = 0; i < 6; ++i) {
+    const int n = fused ? 4 : 6;
+    for (int i = 0; i < n; ++i) {
         if (cudaEventCreate(&ev[i]) != cudaSuccess) {
             for (int j = 0; j < i; ++j) cudaEventDestroy(ev[j]);
             return false;
         }
     }
-    for (int i = 0; i < 6; ++i) c->prof_events.push_back(ev[i]);
+    for (int i = 0; i < n; ++i) c->prof_events.push_back(ev[i]);
     const int kinds[5] = {kProfTcPrologue, kProfTcTrial, kProfTcGemm, kProfTcSelect, kProfTcTies};
-    for (int i = 0; i < 5; ++i) c->prof.push_back(ProfRec{kinds[i], ev[i], ev[i + 1]});
-    c->prof.push_back(ProfRec{kProfTcGeneration, ev[0], ev[5]});
+    const int fkinds[3] = {kProfTcPrologue, kProfTcFused, kProfTcCommit};
+    for (int i = 0; i < n - 1; ++i) c->prof.push_back(ProfRec{fused ? fkinds[i] : kinds[i], ev[i], ev[i + 1]});
+    c->prof.push_back(ProfRec{kProfTcGeneration, ev[0], ev[n - 1]});
     return true;
 }
 
@@ -533,7 +543,12 @@ metade_status run_inner(metade_ctx* c, cudaStream_t st, float* pop, float* fit, 
         for (int g = 0; g < n_gens; ++g) {
             StepArgs t = step_args(c, pop, fit, theta, epoch, epoch_dev, gen0 + (uint32_t)g, 1, nullptr, nullptr);
             cudaEvent_t ev[6];
-            const bool pe = prof_tc(c, st, ev);
+            const bool pe = prof_tc(c, st, ev, c->tcp.fused != 0);
+            if (c->tcp.fused) {
+                CK(launch_tc_fused_generation(t, c->tcp, g == 0, g == n_gens - 1, st, pe ? ev : nullptr));
+                *launches += g == 0 ? 3 : 2;
+                continue;
+            }
             CK(launch_tc_generation(t, c->tcp, st, pe ? ev : nullptr));
             *launches += 5;
         }
@@ -854,6 +869,7 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
             if ((size_t)8 * m.max_dpad * sizeof(float) > kSmemLimit) return fail(METADE_EUNSUPPORTED);
         }
     }
+    c->tc_unfused = cfg->tc_unfused ? 1 : 0;
     c->tc_auto = cfg->tc_min_dim == 0;
     c->tc_min_dim = cfg->tc_min_dim > 0 ? cfg->tc_min_dim : kTcDefaultMinDim;
     if (c->n_inst > 0) {
@@ -1167,7 +1183,7 @@ metade_status metade_plan_info(const metade_ctx* c, char* buf, size_t len) {
         snprintf(tmp, sizeof(tmp),
                  ", \"tensor_core\": {\"kernel\": \"%s\", \"precision\": \"%s\", \"executors\": %d, "
                  "\"tiles\": %d, \"kp\": %d, \"tile\": [%d, 256, %d]}",
-                 c->tcp.simt ? "k_rot_simt" : "k_rot_tc",
+                 c->tcp.simt ? "k_rot_simt" : c->tcp.fused ? "k_tc_gen" : "k_rot_tc",
                  c->tcp.simt ? "fp32" : c->tcp.fp8 ? "fp8e4m3" : c->tcp.split ? "bf16x3" : "bf16", c->tcp.n_exec,
                  c->tcp.n_tiles, c->tcp.kp, c->tcp.simt ? 64 : 128, c->tcp.simt ? 16 : 64);
         s += tmp;

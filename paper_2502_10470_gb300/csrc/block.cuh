@@ -365,15 +365,56 @@ __device__ __forceinline__ float warp_diff(int obj, int dim, const float* z, con
 // chunks.  X: generation-start rows (stride ldx), U: trial row out (global
 // or shared, 16-byte aligned), dbuf: u - o (shared).  Returns nothing; the
 // warp must __syncwarp before reading dbuf.
+// One 4-coordinate chunk j4..j4+3 of a trial: mutation from the loaded base
+// rows (a = x_bl, b = x_br, x = x_i) and the summed difference vectors
+// (sum = sum_q x_plus - x_minus, added in q order), then crossover (binomial
+// words w, exponential start/length, arithmetic K), clip to [lo, hi].  u
+// gets the trial coordinates (0 past dim), d the shifted ones u - o (0 past
+// dim).  Every trial kernel goes through this one function, so trials are
+// bit-identical whichever kernel builds them.
+__device__ __forceinline__ void trial_chunk(const Strat& s, float K, int jrand, int nstart, int L, int dim, int j4,
+                                            const float4& a, const float4& b, const float4& x, const float4& sum,
+                                            const uint4& w, const float* o, float lo, float hi, float (&uo)[4],
+                                            float (&dd)[4]) {
+    const float F = s.F;
+    const bool dir = s.bl != s.br;
+    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+    const float xv[4] = {x.x, x.y, x.z, x.w}, sv[4] = {sum.x, sum.y, sum.z, sum.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int j = j4 + q;
+        float vj = av[q];
+        if (dir) vj += F * (bv[q] - av[q]);
+        vj += F * sv[q];
+        float u;
+        if (s.cs == 3) {
+            u = xv[q] + K * (vj - xv[q]);
+        } else {
+            bool take;
+            if (s.cs == 1) {
+                take = ((word_of(w, q) >> 8) < s.cri) || (j == jrand);
+            } else {
+                int off = j - nstart;
+                if (off < 0) off += dim;
+                take = off < L;
+            }
+            u = take ? vj : xv[q];
+        }
+        u = fminf(fmaxf(u, lo), hi);
+        if (j >= dim) u = 0.0f;
+        uo[q] = u;
+        dd[q] = (j < dim) ? (u - o[j]) : 0.0f;
+    }
+}
+
 __device__ __forceinline__ void warp_trial(const Strat& s, const Ctr& c, const Indiv& v, int i, int dim, int L,
                                            const float* X, long long ldx, const float* o, float lo, float hi,
                                            float* U, float* dbuf) {
     const int lane = threadIdx.x & 31;
-    const float F = s.F, K = (float)v.kraw * (1.0f / 16777216.0f);
+    const float K = (float)v.kraw * (1.0f / 16777216.0f);
     const float* xl = X + (long long)v.ibl * ldx;
     const float* xr = X + (long long)v.ibr * ldx;
     const float* xi = X + (long long)i * ldx;
-    const bool dir = s.bl != s.br;
     for (int j4 = lane * 4; j4 < dim; j4 += 128) {
         const float4 a = *reinterpret_cast<const float4*>(xl + j4);
         const float4 b = *reinterpret_cast<const float4*>(xr + j4);
@@ -385,34 +426,8 @@ __device__ __forceinline__ void warp_trial(const Strat& s, const Ctr& c, const I
             sum.x += p.x - m.x; sum.y += p.y - m.y; sum.z += p.z - m.z; sum.w += p.w - m.w;
         }
         const uint4 w = (s.cs == 1) ? c.slot(4 + (uint32_t)(j4 >> 2)) : make_uint4(0, 0, 0, 0);
-        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
-        const float xv[4] = {x.x, x.y, x.z, x.w}, sv[4] = {sum.x, sum.y, sum.z, sum.w};
         float uo[4], dd[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int j = j4 + q;
-            float vj = av[q];
-            if (dir) vj += F * (bv[q] - av[q]);
-            vj += F * sv[q];
-            float u;
-            if (s.cs == 3) {
-                u = xv[q] + K * (vj - xv[q]);
-            } else {
-                bool take;
-                if (s.cs == 1) {
-                    take = ((word_of(w, q) >> 8) < s.cri) || (j == v.jrand);
-                } else {
-                    int off = j - v.nstart;
-                    if (off < 0) off += dim;
-                    take = off < L;
-                }
-                u = take ? vj : xv[q];
-            }
-            u = fminf(fmaxf(u, lo), hi);
-            if (j >= dim) u = 0.0f;
-            uo[q] = u;
-            dd[q] = (j < dim) ? (u - o[j]) : 0.0f;
-        }
+        trial_chunk(s, K, v.jrand, v.nstart, L, dim, j4, a, b, x, sum, w, o, lo, hi, uo, dd);
         *reinterpret_cast<float4*>(U + j4) = make_float4(uo[0], uo[1], uo[2], uo[3]);
         *reinterpret_cast<float4*>(dbuf + j4) = make_float4(dd[0], dd[1], dd[2], dd[3]);
     }

@@ -4,7 +4,9 @@ that hold at any size.
 
 - moderate: 600 executors x NP 100 x D 20, one-shot, the tuned batched plan
   (the headline benchmark's workload);
-- precision: 64 executors x NP 512 x D 1000 on the tensor cores (BF16, FP8).
+- precision: 64 executors x NP 512 x D 1000 on the tensor cores (BF16, FP8);
+- full: 8 runs x 128 executors, NP 50..200, D 20..200, BF16 on the tensor
+  cores for D >= the autotuned width (the headline benchmark's workload).
 """
 import numpy as np
 import pytest
@@ -112,6 +114,80 @@ def test_precision_full_size_generation_sampled(prec, tol, unit, gap):
     theta = wl.theta.astype(np.float32)
     for k in (0, 33, 63):
         _compare_step(wl, k, pops, fits, theta, npops, nfits, gap, tol, unit)
+    b.close()
+
+
+def _full():
+    """The headline workload (8 runs x 128 executors, NP 50..200, D 20..200),
+    BF16 context, autotuned plan, after the evolver's first trials."""
+    import paper_2502_10470_gb300 as M
+    wl = synth.full()
+    probs = [(p.dim, p.obj, p.shift, p.rot) for p in wl.problems]
+    b = M.Batch(probs, wl.inst_np, wl.inst_prob, wl.inst_group, seed=wl.seed, one_shot=1, n_out=wl.n_out,
+                prec=M.METADE_BF16)
+    M.metade_outer_init(b.ctx, b.opop, b.ofit)
+    M.metade_outer_step(b.ctx, b.opop, b.ofit, b.trial, b.theta, None, 0, 0)
+    M.metade_init(b.ctx, b.pop, b.fit, 0)
+    M.metade_autotune(b.ctx, b.pop, b.fit, b.theta, 3)
+    b.sync()
+    return wl, b
+
+
+def _full_budget(p, tc_min_dim):
+    """(fitness rtol, operand unit, decisive gap) of an executor of the full
+    workload: BF16 on the tensor cores, FP32 elsewhere."""
+    return (4e-3, 2.0 ** -8, 0.1) if p.dim >= tc_min_dim else (FIT_RTOL, 0.0, 2 * FIT_RTOL)
+
+
+def test_full_workload_generation_sampled():
+    """The headline workload in the benchmark's launch configuration, one
+    generation: two executors of every run (all rows) against the oracle's
+    generation from the same state, with the budget of the precision each
+    executor runs in."""
+    import json
+    import paper_2502_10470_gb300 as M
+    wl, b = _full()
+    tcmin = json.loads(M.metade_plan_info(b.ctx))["tc_min_dim"]
+    pops, fits = b.get_population()
+    theta = b.theta.cpu().numpy()
+    M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 0, 1, b.best_f, b.best_i)
+    assert M.metade_sync(b.ctx) == M.METADE_OK
+    npops, nfits = b.get_population()
+    n = 0
+    for g in range(wl.n_groups):
+        for k in (g * wl.n_out + 5, g * wl.n_out + 97):
+            p = wl.problems[int(wl.inst_prob[k])]
+            tol, unit, gap = _full_budget(p, tcmin)
+            n += _compare_step(wl, k, pops, fits, theta, npops, nfits, gap, tol, unit)
+    assert n > 500
+    b.close()
+
+
+def test_full_workload_200_generations_properties():
+    """The benchmark's launch: 200 generations of all 1024 executors in one
+    call.  Every executor: rows inside the box, best_f / best_i the minimum of
+    its stored fitness, a best that never rose.  Sampled executors of every
+    run: stored fitness against the FP64 objective of the stored row within
+    the precision's budget (BF16 rows carry the GEMM's rounding; an accepted
+    near tie stores f(x) + difference)."""
+    import json
+    import paper_2502_10470_gb300 as M
+    wl, b = _full()
+    tcmin = json.loads(M.metade_plan_info(b.ctx))["tc_min_dim"]
+    pops0, fits0 = b.get_population()
+    M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 0, 200, b.best_f, b.best_i)
+    assert M.metade_sync(b.ctx) == M.METADE_OK
+    npops, nfits = b.get_population()
+    best_f, best_i = b.best_f.cpu().numpy(), b.best_i.cpu().numpy()
+    for k in range(wl.n_inst):
+        assert np.all(npops[k] >= wl.lo) and np.all(npops[k] <= wl.hi)
+        assert best_f[k] == nfits[k].min() and best_i[k] == int(np.argmin(nfits[k]))
+        assert best_f[k] <= fits0[k].min()
+    for g in range(wl.n_groups):
+        k = g * wl.n_out + 11
+        p = wl.problems[int(wl.inst_prob[k])]
+        tol, unit, _ = _full_budget(p, tcmin)
+        check_fitness(nfits[k], npops[k], p, max(tol, 1e-4), unit, floor=1e-30)
     b.close()
 
 

@@ -156,14 +156,15 @@ def test_eval_caller_points_fp64_and_fp32():
     out = torch.zeros(n, dtype=torch.float64, device="cuda")
     M.metade_eval(b.ctx, xd, n, bad, ldx, M.METADE_FP64, out)
     assert M.metade_sync(b.ctx) == M.METADE_EINVAL
-    out = out.cpu().numpy()
-    assert np.isnan(out[7]) and np.array_equal(np.delete(out, 7), np.delete(f64, 7))
+    got = out.cpu().numpy()
+    assert np.isnan(got[7]) and np.array_equal(np.delete(got, 7), np.delete(f64, 7))
     # host-side checks: ldx not a multiple of 4, unsupported precision
     with pytest.raises(M.MetadeError):
         M.metade_eval(b.ctx, xd, n, idd, ldx - 1, M.METADE_FP64, out)
     with pytest.raises(M.MetadeError):
         M.metade_eval(b.ctx, xd, n, idd, ldx, M.METADE_BF16, out)
     M.metade_eval(b.ctx, xd, 0, idd, ldx, M.METADE_FP64, out)  # n = 0: nothing to do
+    assert M.metade_sync(b.ctx) == M.METADE_OK
     b.close()
 
 

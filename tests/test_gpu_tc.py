@@ -348,3 +348,53 @@ def test_tc_min_dim_places_executors_and_autotune_picks_a_width():
     M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 0, 2, None, None)
     assert M.metade_sync(b.ctx) == M.METADE_OK
     b.close()
+
+
+def test_tc_fused_generation_equals_the_pipeline():
+    """The fused generation kernel (k_tc_gen + k_tc_commit) against the
+    five-kernel pipeline (tc_unfused = 1) on the same state: the same trial
+    arithmetic, the same GEMM operands and epilogue, the same FP32 tie
+    rotations and difference forms, so populations and fitness must be
+    bit-identical -- over three generations of random states (D 129..255,
+    tiles across executors), and over a near-tie step (grid copies, then
+    trials 2^-20 away) where most selections go through the tie path."""
+    import paper_2502_10470_gb300 as M
+    wl = _wl_mid(seed=67)
+    pops, fits = random_state(wl, seed=11)
+    outs = []
+    for unfused in (0, 1):
+        b = make_batch(wl, M.METADE_PATH_BATCHED, prec=1, tc_unfused=unfused)
+        assert json.loads(M.metade_plan_info(b.ctx))["tensor_core"]["kernel"] == ("k_rot_tc" if unfused else "k_tc_gen")
+        b.set_population(pops, fits)
+        b.set_theta(wl.theta)
+        M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 0, 3, b.best_f, b.best_i)
+        assert M.metade_sync(b.ctx) == M.METADE_OK
+        outs.append((b.get_population(), b.best_f.cpu().numpy(), b.best_i.cpu().numpy()))
+        b.close()
+    for k in range(wl.n_inst):
+        np.testing.assert_array_equal(outs[0][0][0][k], outs[1][0][0][k])
+        np.testing.assert_array_equal(outs[0][0][1][k], outs[1][0][1][k])
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
+    np.testing.assert_array_equal(outs[0][2], outs[1][2])
+    # near ties: D = 200 and 256 executors on a grid
+    rng = np.random.default_rng(79)
+    n, NP = 6, 64
+    probs = [synth.make_problem(rng, 200 if k % 2 else 256, k) for k in range(n)]
+    wt = synth.Workload(name="tc-ties-fused", problems=probs, inst_np=np.full(n, NP, dtype=np.int32),
+                        inst_prob=np.arange(n, dtype=np.int32), inst_group=np.arange(n, dtype=np.int32),
+                        n_groups=n, n_out=0, inner_gens=1, outer_gens=1, seed=13, one_shot=0)
+    grid = [(rng.integers(-12, 13, (NP, p.dim)) * 8.0).astype(np.float32) for p in probs]
+    res = []
+    for unfused in (0, 1):
+        b = make_batch(wt, M.METADE_PATH_BATCHED, prec=1, tc_unfused=unfused)
+        b.set_population(grid, [np.full(NP, np.inf, dtype=np.float32)] * n)
+        b.set_theta(np.tile(np.array([0.0, 1.0, 1, 1, 1, 1], dtype=np.float32), (n, 1)))
+        M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 0, 1, None, None)
+        b.set_theta(np.tile(np.array([2.0 ** -20, 0.0, 4, 4, 1, 1], dtype=np.float32), (n, 1)))
+        M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 1, 2, None, None)
+        assert M.metade_sync(b.ctx) == M.METADE_OK
+        res.append(b.get_population())
+        b.close()
+    for k in range(n):
+        np.testing.assert_array_equal(res[0][0][k], res[1][0][k])
+        np.testing.assert_array_equal(res[0][1][k], res[1][1][k])
