@@ -1,12 +1,15 @@
 // tc_fused.cu -- one generation of the tensor-core executors in one kernel
 // (BF16 operands, D <= 256), followed by a small commit kernel.
 //
-// k_tc_gen is persistent (one CTA per SM, 544 threads) and walks the 128-row
+// k_tc_gen is persistent (one CTA per SM, 512 threads) and walks the 128-row
 // M tiles of the GEMM (rows of one problem, possibly several executors).  Per
 // tile:
-//   1. draws      four warps, a thread per row: the Philox index draws,
-//                 exponential length and K of every row into a field-major
-//                 record in shared memory;
+//   1. draws      lanes 0..7 of every epilogue warp take one row each: the
+//                 Philox index draws and K into a field-major record in shared
+//                 memory; then each warp draws the exponential-crossover
+//                 lengths of its 8 rows with all 32 lanes (a lane per four
+//                 coordinate uniforms, the first one at or above CR found by a
+//                 ballot);
 //   2. trial      all 16 epilogue warps, a lane per (row, 4-coordinate chunk),
 //                 8 rows x 4 consecutive chunks per warp step: mutation,
 //                 crossover and clip (the same trial_chunk arithmetic as every
@@ -14,7 +17,7 @@
 //                 the BF16 operand u - o straight into the A tile in shared
 //                 memory, in the UMMA 128-byte-swizzled K-major layout (A never
 //                 touches global memory);
-//   3. MMA        one thread issues tcgen05.mma (M 128, N 256, K 16, FP32
+//   3. MMA        thread 0 issues tcgen05.mma (M 128, N 256, K 16, FP32
 //                 accumulate in TMEM) over the K tiles; B, the problem's padded
 //                 BF16 R rows, is loaded by TMA once per problem and stays in
 //                 shared memory while the CTA's tiles belong to that problem;
@@ -24,8 +27,10 @@
 //   5. selection  a thread per row compares f(u) with the stored f(x); clear
 //                 cases write the decision, near ties are listed;
 //   6. ties       the tile's near ties, up to 16 at once: z = R (x - o) and
-//                 dz = R (u - x) in FP32 on the CUDA cores (R^T streamed from
-//                 L2 once per batch), then the FP32 difference form.
+//                 dz = R (u - x) in FP32 on the CUDA cores (R^T streamed through
+//                 shared memory by cp.async, once per batch), then the FP32
+//                 difference form; a trial identical to its target is
+//                 recognised from the staged u - x and accepted as it is.
 // The decision goes to fu[fitness index]: the new fitness when the trial is
 // accepted, NaN when it is rejected.  k_tc_commit (a CTA per executor) then
 // copies the accepted rows, stores their fitness and ranks the pbest pool of
@@ -50,6 +55,8 @@ constexpr int kMaxKt = 4;        // K tiles of 64 BF16 elements: D <= 256
 constexpr int kTieBatch = 16;    // near ties rotated together
 constexpr int kVec = 256;        // stride of a staged tie vector (floats)
 constexpr int kRejected = -1;    // bit pattern of the "rejected" mark in fu (a NaN)
+constexpr int kRtRows = 16;      // R^T rows per cp.async stage of the tie rotation
+constexpr int kGenThreads = 32 * kEpiWarps;  // 16 warps; thread 0 also issues the TMA loads and MMAs
 
 // record fields, [field][kRows]
 enum {
@@ -73,6 +80,12 @@ struct GenArgs {
     int kt;                   // K tiles of the operands
 };
 
+// 16-byte cp.async; src_bytes 0 fills the destination with zeros
+__device__ __forceinline__ void cp_async16z(float* dst, const float* src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+
 __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -90,7 +103,7 @@ __device__ __forceinline__ uint2 pack_bf16x4(const float (&d)[4]) {
     return make_uint2(*reinterpret_cast<const uint32_t*>(&lo), *reinterpret_cast<const uint32_t*>(&hi));
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1) k_tc_gen(const __grid_constant__ CUtensorMap tmB, GenArgs g) {
+__global__ void __launch_bounds__(kGenThreads, 1) k_tc_gen(const __grid_constant__ CUtensorMap tmB, GenArgs g) {
     extern __shared__ uint8_t smraw[];
     __shared__ __align__(8) uint64_t bfull, mma_done, drain;
     __shared__ uint32_t tmem_base;
@@ -105,7 +118,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gen(const __grid_constant_
     float* tv = reinterpret_cast<float*>(As);  // tie vectors reuse the A tile once the MMAs are done
     const StepArgs& a = g.a;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool producer = warp == kEpiWarps;
+    const bool issuer = tid == 0;  // TMA loads and MMAs
     const uint32_t epoch = a.epoch_dev ? *a.epoch_dev : a.epoch;
 
     if (warp == 0) {
@@ -128,13 +141,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gen(const __grid_constant_
 
     int cur_prob = -1;
     uint32_t bphase = 0, mphase = 0;
-    bool b_in_flight = false;  // producer lane 0: a B load not yet waited on
+    bool b_in_flight = false;  // thread 0: a B load not yet waited on
     for (int t = blockIdx.x; t < g.n_tiles; t += gridDim.x) {
         const int arow = g.tiles[2 * t], nr = g.tiles[2 * t + 1];
         const InstDesc d = a.desc[g.row_exec[arow]];  // dim, objective and problem of every row of the tile
         // B: the problem's R rows, once per problem (the previous tile's MMAs are complete)
         const bool load_b = d.prob != cur_prob;
-        if (load_b && producer && lane == 0) {
+        if (load_b && issuer) {
             mbar_expect_tx(&bfull, (uint32_t)(g.kt * kBT));
             const int brow0 = (int)g.brow[d.prob];
             for (int kk = 0; kk < g.kt; ++kk) tma_load_2d(Bs + (size_t)kk * kBT, &tmB, &bfull, kk * kBK, brow0);
@@ -142,50 +155,98 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gen(const __grid_constant_
         }
         cur_prob = d.prob;
 
-        // 1. draws: a thread per row
-        if (tid < kRows) {
-            const int r = tid;
-            int valid = 0;
-            if (r < nr) {
-                const int k = g.row_exec[arow + r];
-                const InstDesc e = a.desc[k];
-                const int i = arow + r - e.tc_row;
-                const Strat s = load_strat(a.theta + 6 * k, e.np);
-                if (s.ok) {
-                    valid = 1;
-                    const int* topk = g.topk_all + e.fit_off;
-                    const Ctr c = make_ctr(a.key, (uint32_t)e.stream, a.gen0, (uint32_t)i, epoch);
-                    Indiv v;
-                    indiv_setup(s, c, i, e.np, e.dim, e.kp, topk, topk[0], v);
-                    rec[F_IBL * kRows + r] = v.ibl;
-                    rec[F_IBR * kRows + r] = v.ibr;
+        // 1. draws: warp w takes rows 8 w .. 8 w + 7; lanes 0..7 run a row's
+        // index draws, then the warp's 32 lanes draw the exponential lengths of
+        // its rows together (lane l: the uniforms of coordinates 4 l .. 4 l + 3)
+        {
+            const int r = 8 * warp + (lane & 7);
+            int cs2 = 0;  // this lane's row uses exponential crossover
+            if (lane < 8) {
+                int valid = 0;
+                if (r < nr) {
+                    const int k = g.row_exec[arow + r];
+                    const InstDesc e = a.desc[k];
+                    const int i = arow + r - e.tc_row;
+                    const Strat s = load_strat(a.theta + 6 * k, e.np);
+                    if (s.ok) {
+                        valid = 1;
+                        cs2 = s.cs == 2;
+                        const int* topk = g.topk_all + e.fit_off;
+                        const Ctr c = make_ctr(a.key, (uint32_t)e.stream, a.gen0, (uint32_t)i, epoch);
+                        Indiv v;
+                        indiv_setup(s, c, i, e.np, e.dim, e.kp, topk, topk[0], v);
+                        rec[F_IBL * kRows + r] = v.ibl;
+                        rec[F_IBR * kRows + r] = v.ibr;
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        rec[(F_P0 + q) * kRows + r] = q < s.dn ? diff_plus(v, s.a, q) : 0;
-                        rec[(F_M0 + q) * kRows + r] = q < s.dn ? diff_minus(v, s.a, q) : 0;
+                        for (int q = 0; q < 4; ++q) {
+                            rec[(F_P0 + q) * kRows + r] = q < s.dn ? diff_plus(v, s.a, q) : 0;
+                            rec[(F_M0 + q) * kRows + r] = q < s.dn ? diff_minus(v, s.a, q) : 0;
+                        }
+                        rec[F_JR * kRows + r] = v.jrand;
+                        rec[F_NS * kRows + r] = v.nstart;
+                        rec[F_L * kRows + r] = 0;
+                        rec[F_K * kRows + r] = (int)v.kraw;
+                        rec[F_FIDX * kRows + r] = e.fit_off + i;
+                        rec[F_POPLO * kRows + r] = (int)(uint32_t)e.pop_off;
+                        rec[F_POPHI * kRows + r] = (int)(e.pop_off >> 32);
+                        rec[F_F * kRows + r] = __float_as_int(s.F);
+                        rec[F_CRI * kRows + r] = (int)s.cri;
+                        rec[F_PACK * kRows + r] = s.cs | (s.dn << 4) | ((s.bl != s.br ? 1 : 0) << 8);
+                        rec[F_I * kRows + r] = i;
+                        rec[F_STREAM * kRows + r] = e.stream;
                     }
-                    rec[F_JR * kRows + r] = v.jrand;
-                    rec[F_NS * kRows + r] = v.nstart;
-                    rec[F_L * kRows + r] = s.cs == 2 ? exp_length(c, e.dim, s.cri) : 0;
-                    rec[F_K * kRows + r] = (int)v.kraw;
-                    rec[F_FIDX * kRows + r] = e.fit_off + i;
-                    rec[F_POPLO * kRows + r] = (int)(uint32_t)e.pop_off;
-                    rec[F_POPHI * kRows + r] = (int)(e.pop_off >> 32);
-                    rec[F_F * kRows + r] = __float_as_int(s.F);
-                    rec[F_CRI * kRows + r] = (int)s.cri;
-                    rec[F_PACK * kRows + r] = s.cs | (s.dn << 4) | ((s.bl != s.br ? 1 : 0) << 8);
-                    rec[F_I * kRows + r] = i;
-                    rec[F_STREAM * kRows + r] = e.stream;
+                }
+                rec[F_VALID * kRows + r] = valid;
+            }
+            // exponential length L = 1 + min(t*, D - 1), t* the first coordinate
+            // uniform U_t (slot 4 + t / 4, word t % 4) not below CR
+            const unsigned exp_rows = __ballot_sync(kFull, cs2 != 0) & 0xFFu;
+            __syncwarp();
+            for (int base = 0; exp_rows && (base == 0 || base < d.dim - 1); base += 128) {  // t = base + 4 lane + q
+                uint4 w8[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {  // the Philox chains of the 8 rows interleave
+                    w8[q] = make_uint4(0, 0, 0, 0);
+                    if ((exp_rows >> q) & 1u) {
+                        const int rq = 8 * warp + q;
+                        const Ctr c = make_ctr(a.key, (uint32_t)rec[F_STREAM * kRows + rq], a.gen0,
+                                               (uint32_t)rec[F_I * kRows + rq], epoch);
+                        w8[q] = c.slot(4 + (uint32_t)((base >> 2) + lane));
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    if (!((exp_rows >> q) & 1u)) continue;  // warp-uniform
+                    const int rq = 8 * warp + q;
+                    if (base > 0 && rec[F_L * kRows + rq] != 0) continue;  // ended in an earlier round
+                    const uint32_t cri = (uint32_t)rec[F_CRI * kRows + rq];
+                    int first = 4;  // first failing word of this lane
+#pragma unroll
+                    for (int wq = 3; wq >= 0; --wq) {
+                        const int t = base + 4 * lane + wq;
+                        if (t <= d.dim - 2 && (word_of(w8[q], wq) >> 8) >= cri) first = wq;
+                    }
+                    const unsigned fails = __ballot_sync(kFull, first < 4);
+                    int L = 0;
+                    if (fails) {
+                        const int fl = __ffs(fails) - 1;
+                        const int fq = __shfl_sync(kFull, first, fl);
+                        L = 1 + base + 4 * fl + fq;
+                    } else if (base + 128 >= d.dim - 1) {
+                        L = d.dim;  // every uniform below CR: the whole row
+                    }
+                    if (lane == 0) rec[F_L * kRows + rq] = L;
+                    __syncwarp();
                 }
             }
-            rec[F_VALID * kRows + r] = valid;
         }
         __syncthreads();
 
         // 2. trial rows and the A tile: lane = (row 8 * unit + lane / 4, chunk 4 * unit' + lane % 4)
-        if (!producer) {
+        {
             const int nchb = g.kt * 4;  // blocks of 4 chunks (16 elements) along K
             const int units = (kRows / 8) * nchb;
+#pragma unroll 2
             for (int u = warp; u < units; u += kEpiWarps) {
                 const int r = 8 * (u / nchb) + (lane >> 2);
                 const int j4 = 4 * (4 * (u % nchb) + (lane & 3));
@@ -204,15 +265,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gen(const __grid_constant_
                     s.bl = 0;
                     s.br = (pack >> 8) & 1;  // trial_chunk reads bl != br as "has a directional term"
                     const int i = rec[F_I * kRows + r];
-                    const float4 av = *reinterpret_cast<const float4*>(X + rec[F_IBL * kRows + r] * ld + j4);
-                    const float4 bv = *reinterpret_cast<const float4*>(X + rec[F_IBR * kRows + r] * ld + j4);
-                    const float4 xv = *reinterpret_cast<const float4*>(X + (long long)i * ld + j4);
+                    // the population is read-only during the kernel: non-coherent loads, which the
+                    // compiler may issue ahead of the previous unit's stores
+                    const float4 av = __ldg(reinterpret_cast<const float4*>(X + rec[F_IBL * kRows + r] * ld + j4));
+                    const float4 bv = __ldg(reinterpret_cast<const float4*>(X + rec[F_IBR * kRows + r] * ld + j4));
+                    const float4 xv = __ldg(reinterpret_cast<const float4*>(X + (long long)i * ld + j4));
                     float4 p[4], m[4];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         if (q < s.dn) {
-                            p[q] = *reinterpret_cast<const float4*>(X + rec[(F_P0 + q) * kRows + r] * ld + j4);
-                            m[q] = *reinterpret_cast<const float4*>(X + rec[(F_M0 + q) * kRows + r] * ld + j4);
+                            p[q] = __ldg(reinterpret_cast<const float4*>(X + rec[(F_P0 + q) * kRows + r] * ld + j4));
+                            m[q] = __ldg(reinterpret_cast<const float4*>(X + rec[(F_M0 + q) * kRows + r] * ld + j4));
                         }
                     }
                     float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -242,7 +305,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gen(const __grid_constant_
         __syncthreads();
 
         // 3. MMA: one thread, over the K tiles, into one accumulator of kBN columns
-        if (producer && lane == 0) {
+        if (issuer) {
             bool ok = true;
             if (b_in_flight) {
                 ok = mbar_wait(&bfull, bphase);
@@ -269,7 +332,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gen(const __grid_constant_
         const int qd = warp & 3, prt = warp >> 2;
         const int row = 32 * qd + lane;
         ObjR acc;
-        if (!producer) {
+        {
             const bool got = __all_sync(kFull, mbar_wait(&mma_done, mphase) ? 1 : 0) != 0;
             if (!got && lane == 0) {
                 set_status(a.status, kStatusTimeout);
@@ -314,7 +377,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gen(const __grid_constant_
         // 5. selection: the part-0 thread of each row
         if (tid == 0) ntie_s = 0;
         float fnew = 0.f;
-        if (!producer && prt == 0) {
+        if (prt == 0) {
             for (int j = 0; j < kParts - 1; ++j) {
                 const float* sl = part + ((size_t)j * kRows + row) * 8;
                 const float4 x0 = *reinterpret_cast<const float4*>(sl), x1 = *reinterpret_cast<const float4*>(sl + 4);
@@ -329,26 +392,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gen(const __grid_constant_
             fnew = nan_to_inf(acc.finish(d.obj, d.dim));
         }
         __syncthreads();  // ntie_s = 0 before any tie is listed
-        if (!producer && prt == 0 && rec[F_VALID * kRows + row] && !abort_s) {
+        if (prt == 0 && rec[F_VALID * kRows + row] && !abort_s) {
             const int fidx = rec[F_FIDX * kRows + row];
             const float fx = a.fit[fidx];
-            float fn = fnew;
-            bool tie = near_tie(fn, fx, tie_band(d.dim));
-            if (tie) {  // a trial identical to its target is accepted as it is
-                const long long po = (long long)(((unsigned long long)(uint32_t)rec[F_POPHI * kRows + row] << 32) |
-                                                 (uint32_t)rec[F_POPLO * kRows + row]);
-                const long long off = po + (long long)rec[F_I * kRows + row] * d.dpad;
-                const float* X = a.pop + off;
-                const float* U = g.uscr + off;
-                bool diff = false;
-                for (int j = 0; j < d.dpad && !diff; j += 4) {
-                    const float4 x4 = *reinterpret_cast<const float4*>(X + j);
-                    const float4 u4 = *reinterpret_cast<const float4*>(U + j);
-                    diff = x4.x != u4.x || x4.y != u4.y || x4.z != u4.z || x4.w != u4.w;
-                }
-                if (!diff) tie = false, fn = fx;
-            }
-            if (tie) {
+            const float fn = fnew;
+            // near ties (including trials identical to their targets, recognised
+            // in the tie phase from the staged u - x) are decided below
+            if (near_tie(fn, fx, tie_band(d.dim))) {
                 const int q = atomicAdd(&ntie_s, 1);
                 tie_row[q] = row;
                 tie_fx[q] = fx;
@@ -358,38 +408,61 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gen(const __grid_constant_
         }
         __syncthreads();
 
-        // 6. near ties, kTieBatch at a time: z = R (x - o), dz = R (u - x) in FP32
+        // 6. near ties, kTieBatch at a time: z = R (x - o) and dz = R (u - x) in
+        // FP32 (k ascending in every fma chain, like every FP32 rotation), R^T
+        // streamed through shared memory 16 rows at a time by cp.async (double
+        // buffered), each thread one row of z for half of the batch
         const int nt = abort_s ? 0 : ntie_s;
         const float* o = a.shift + d.shift_off;
         const float* RT = a.rotT + d.rot_off;
+        float* vx = tv;                          // [kTieBatch][kVec] x - o, then z
+        float* vl = tv + kTieBatch * kVec;       // u - x, then dz
+        float* sR = tv + 2 * kTieBatch * kVec;   // [2][kRtRows][kVec] R^T rows
+        const int nchunk = (d.dim + kRtRows - 1) / kRtRows;
         for (int b0 = 0; b0 < nt; b0 += kTieBatch) {
             const int nb = min(kTieBatch, nt - b0);
-            float* vx = tv;                         // [kTieBatch][kVec] x - o
-            float* vl = tv + kTieBatch * kVec;      // u - x
-            float* zx = tv + 2 * kTieBatch * kVec;  // z
-            float* dz = tv + 3 * kTieBatch * kVec;  // dz
+            auto stage_rt = [&](int ch) {  // R^T rows ch * 16 .. into buffer ch & 1 (zero past dim)
+                float* dst = sR + (size_t)(ch & 1) * kRtRows * kVec;
+                const int f4 = d.dpad >> 2;
+                for (int e = tid; e < kRtRows * f4; e += blockDim.x) {
+                    const int cc = e / f4, x4 = e - cc * f4, c = ch * kRtRows + cc;
+                    cp_async16z(dst + cc * kVec + 4 * x4, RT + (size_t)min(c, d.dim - 1) * d.dpad + 4 * x4,
+                                c < d.dim ? 16 : 0);
+                }
+                asm volatile("cp.async.commit_group;" ::: "memory");
+            };
+            stage_rt(0);
             for (int e = tid; e < nb * kVec; e += blockDim.x) {
                 const int q = e / kVec, c = e - q * kVec;
-                if (c < d.dim) {
+                if (c < d.dpad) {
                     const int r = tie_row[b0 + q];
                     const long long po = (long long)(((unsigned long long)(uint32_t)rec[F_POPHI * kRows + r] << 32) |
                                                      (uint32_t)rec[F_POPLO * kRows + r]);
                     const long long off = po + (long long)rec[F_I * kRows + r] * d.dpad;
                     const float xc = a.pop[off + c];
-                    vx[q * kVec + c] = xc - o[c];
+                    vx[q * kVec + c] = c < d.dim ? xc - o[c] : 0.f;
                     vl[q * kVec + c] = g.uscr[off + c] - xc;
                 }
             }
-            __syncthreads();
-            {
-                const int r = tid & (kVec - 1), h = tid >> 8;  // row of z, half of the batch
-                if (h < 2 && r < d.dim) {
-                    float az[kTieBatch / 2], ad[kTieBatch / 2];
+            const int r = tid & (kVec - 1), h = tid >> 8;  // row of z, half of the batch (h < 2)
+            const int q0 = h * (kTieBatch / 2);
+            float az[kTieBatch / 2], ad[kTieBatch / 2];
 #pragma unroll
-                    for (int q = 0; q < kTieBatch / 2; ++q) az[q] = ad[q] = 0.f;
-                    const int q0 = h * (kTieBatch / 2);
-                    for (int c = 0; c < d.dim; ++c) {
-                        const float rt = RT[(size_t)c * d.dpad + r];
+            for (int q = 0; q < kTieBatch / 2; ++q) az[q] = ad[q] = 0.f;
+            for (int ch = 0; ch < nchunk; ++ch) {
+                if (ch + 1 < nchunk) {
+                    stage_rt(ch + 1);
+                    asm volatile("cp.async.wait_group 1;" ::: "memory");
+                } else {
+                    asm volatile("cp.async.wait_group 0;" ::: "memory");
+                }
+                __syncthreads();
+                if (h < 2 && r < d.dim) {
+                    const float* rc = sR + (size_t)(ch & 1) * kRtRows * kVec;
+                    const int cend = min(kRtRows, d.dim - ch * kRtRows);
+                    for (int cc = 0; cc < cend; ++cc) {
+                        const int c = ch * kRtRows + cc;
+                        const float rt = rc[cc * kVec + r];
 #pragma unroll
                         for (int q = 0; q < kTieBatch / 2; ++q) {
                             if (q0 + q < nb) {
@@ -398,23 +471,37 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gen(const __grid_constant_
                             }
                         }
                     }
+                }
+                __syncthreads();  // the buffer is refilled two chunks later
+            }
+            if (h < 2 && r < d.dim) {  // every thread has read vx / vl: z and dz replace them
 #pragma unroll
-                    for (int q = 0; q < kTieBatch / 2; ++q) {
-                        if (q0 + q < nb) {
-                            zx[(q0 + q) * kVec + r] = az[q];
-                            dz[(q0 + q) * kVec + r] = ad[q];
-                        }
+                for (int q = 0; q < kTieBatch / 2; ++q) {
+                    if (q0 + q < nb) {
+                        vx[(q0 + q) * kVec + r] = az[q];
+                        vl[(q0 + q) * kVec + r] = ad[q];
                     }
                 }
             }
             __syncthreads();
             if (warp < nb) {
-                const float df = warp_diff(d.obj, d.dim, zx + warp * kVec, dz + warp * kVec);
-                if (lane == 0) {
-                    const int r = tie_row[b0 + warp];
-                    const float fx = tie_fx[b0 + warp];
-                    g.fu[rec[F_FIDX * kRows + r]] = df <= 0.0f ? fx + df : __int_as_float(kRejected);
+                // a trial identical to its target (u - x == 0 everywhere, pad included) is
+                // accepted without evaluation; otherwise the FP32 difference form decides
+                const int rr = tie_row[b0 + warp];
+                const long long po = (long long)(((unsigned long long)(uint32_t)rec[F_POPHI * kRows + rr] << 32) |
+                                                 (uint32_t)rec[F_POPLO * kRows + rr]);
+                const long long off = po + (long long)rec[F_I * kRows + rr] * d.dpad;
+                bool diff = false;
+                for (int c = lane; c < d.dpad; c += 32) diff = diff || (g.uscr[off + c] != a.pop[off + c]);
+                const float fx = tie_fx[b0 + warp];
+                float dec;
+                if (!__any_sync(kFull, diff)) {
+                    dec = fx;
+                } else {
+                    const float df = warp_diff(d.obj, d.dim, vx + warp * kVec, vl + warp * kVec);
+                    dec = df <= 0.0f ? fx + df : __int_as_float(kRejected);
                 }
+                if (lane == 0) g.fu[rec[F_FIDX * kRows + rr]] = dec;
             }
             __syncthreads();
         }
@@ -425,7 +512,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gen(const __grid_constant_
         tc_fence_after();
     }
     // leave with no copy or MMA of this CTA in flight (bounded waits)
-    if (producer && lane == 0) {
+    if (issuer) {
         if (b_in_flight) mbar_wait(&bfull, bphase);
         mma_commit(&drain);
         mbar_wait(&drain, 0u);
@@ -500,7 +587,7 @@ cudaError_t launch_tc_fused_generation(const StepArgs& a, const TcPlan& p, bool 
     cudaError_t e = cudaFuncSetAttribute(k_tc_gen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = p.n_tiles < p.gen_ctas ? p.n_tiles : p.gen_ctas;
-    k_tc_gen<<<grid, kTcThreads, smem, st>>>(p.mapB, g);
+    k_tc_gen<<<grid, kGenThreads, smem, st>>>(p.mapB, g);
     if (ev) cudaEventRecord(ev[2], st);
     k_tc_commit<<<p.n_exec, 256, 0, st>>>(a, p.execs, p.topk_all, p.uscr, p.fu, last ? 0 : 1);
     if (ev) cudaEventRecord(ev[3], st);
