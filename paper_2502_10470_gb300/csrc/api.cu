@@ -42,9 +42,8 @@ enum ProfKind {
     kProfTcTrial = 8,
     kProfTcSelect = 9,
     kProfTcTies = 10,
-    kProfTcFused = 11,
-    kProfTcCommit = 12,
-    kProfKinds = 13
+    kProfTcSel = 11,
+    kProfKinds = 12
 };
 
 struct ProfRec {
@@ -438,7 +437,7 @@ metade_status setup_tc(metade_ctx* c) {
     t.split = split ? 1 : 0;
     t.max_dpad = tc_max_dpad;
     // BF16 with FP32 difference-form ties and operands of at most 256 elements:
-    // one fused kernel per generation
+    // three kernels per generation, GEMM, selection, ties and commit in one
     t.fused = (c->prec == METADE_BF16 && !c->tie_fp64 && !c->tc_unfused && tc_fused_fits(tc_kp)) ? 1 : 0;
     t.gen_ctas = std::max(1, device_sms());
     // a tie keeps four rows of max_dpad in shared memory (FP64 with tie_fp64)
@@ -479,7 +478,7 @@ bool prof_pair(metade_ctx* c, cudaStream_t st, int kind, cudaEvent_t* a, cudaEve
 // Events between the kernels of one tensor-core generation (prologue, trial,
 // GEMM, selection, ties): ev[0..5], with a record per kernel and one for the
 // whole generation.
-// The fused generation has four events: ranking, k_tc_gen, commit.
+// The three-kernel generation has four events: ranking, trial, selection.
 bool prof_tc(metade_ctx* c, cudaStream_t st, cudaEvent_t* ev, bool fused) {
     if (!c->prof_on) return false;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -493,7 +492,7 @@ bool prof_tc(metade_ctx* c, cudaStream_t st, cudaEvent_t* ev, bool fused) {
     }
     for (int i = 0; i < n; ++i) c->prof_events.push_back(ev[i]);
     const int kinds[5] = {kProfTcPrologue, kProfTcTrial, kProfTcGemm, kProfTcSelect, kProfTcTies};
-    const int fkinds[3] = {kProfTcPrologue, kProfTcFused, kProfTcCommit};
+    const int fkinds[3] = {kProfTcPrologue, kProfTcTrial, kProfTcSel};
     for (int i = 0; i < n - 1; ++i) c->prof.push_back(ProfRec{fused ? fkinds[i] : kinds[i], ev[i], ev[i + 1]});
     c->prof.push_back(ProfRec{kProfTcGeneration, ev[0], ev[n - 1]});
     return true;
@@ -545,8 +544,8 @@ metade_status run_inner(metade_ctx* c, cudaStream_t st, float* pop, float* fit, 
             cudaEvent_t ev[6];
             const bool pe = prof_tc(c, st, ev, c->tcp.fused != 0);
             if (c->tcp.fused) {
-                CK(launch_tc_fused_generation(t, c->tcp, g == 0, g == n_gens - 1, st, pe ? ev : nullptr));
-                *launches += g == 0 ? 3 : 2;
+                CK(launch_tc_fused_generation(t, c->tcp, st, pe ? ev : nullptr));
+                *launches += 3;
                 continue;
             }
             CK(launch_tc_generation(t, c->tcp, st, pe ? ev : nullptr));
@@ -1183,7 +1182,7 @@ metade_status metade_plan_info(const metade_ctx* c, char* buf, size_t len) {
         snprintf(tmp, sizeof(tmp),
                  ", \"tensor_core\": {\"kernel\": \"%s\", \"precision\": \"%s\", \"executors\": %d, "
                  "\"tiles\": %d, \"kp\": %d, \"tile\": [%d, 256, %d]}",
-                 c->tcp.simt ? "k_rot_simt" : c->tcp.fused ? "k_tc_gen" : "k_rot_tc",
+                 c->tcp.simt ? "k_rot_simt" : c->tcp.fused ? "k_tc_sel" : "k_rot_tc",
                  c->tcp.simt ? "fp32" : c->tcp.fp8 ? "fp8e4m3" : c->tcp.split ? "bf16x3" : "bf16", c->tcp.n_exec,
                  c->tcp.n_tiles, c->tcp.kp, c->tcp.simt ? 64 : 128, c->tcp.simt ? 16 : 64);
         s += tmp;

@@ -127,8 +127,8 @@ struct TcPlan {
     int* tie_count;          // device counter
     int tie_ctas;            // CTAs of the tie kernel
     int kp, split, max_dpad;
-    int fused;               // 1: one k_tc_gen + k_tc_commit per generation (BF16, kp <= 256)
-    int gen_ctas;            // CTAs of k_tc_gen (one per SM)
+    int fused;               // 1: k_tc_rank + k_tc_trial2 + k_tc_sel per generation (BF16, kp <= 256)
+    int gen_ctas;            // CTAs of k_tc_sel (one per SM)
     CUtensorMap mapA, mapB, mapAlo, mapBlo;
 };
 bool tc_make_map(CUtensorMap* map, const void* base, long long rows, int kp, int box_rows, int esz);
@@ -144,14 +144,13 @@ cudaError_t launch_tc_eval(const InstDesc* desc, const TcPlan& p, const float* p
 size_t rot_simt_smem();
 cudaError_t launch_rot_simt(const InstDesc* desc, const int* tiles, int n_tiles, const float* rows, const float* shift,
                             const float* rotT, float* f_out, cudaStream_t st);
-// The fused generation (tc_fused.cu): whether the shared memory of k_tc_gen
-// holds operands of kp BF16 elements, and one generation of every
-// tensor-core executor -- k_tc_rank (first generation of a call: the pbest
-// pools), k_tc_gen, k_tc_commit (which ranks the next generation's pools
-// unless `last`).  ev (may be null): four events, before each launch and
-// after the last.
+// The three-kernel generation (tc_fused.cu): whether the shared memory of
+// k_tc_sel holds operands of kp BF16 elements, and one generation of every
+// tensor-core executor -- k_tc_rank (pbest pools), k_tc_trial2 (trial and
+// operand rows), k_tc_sel (GEMM, objective, selection, near ties, commit).
+// ev (may be null): four events, before each launch and after the last.
 bool tc_fused_fits(int kp);
-cudaError_t launch_tc_fused_generation(const StepArgs& a, const TcPlan& p, bool first, bool last, cudaStream_t st,
+cudaError_t launch_tc_fused_generation(const StepArgs& a, const TcPlan& p, cudaStream_t st,
                                        cudaEvent_t* ev = nullptr);
 // ev (may be null): six events recorded before the prologue, trial, GEMM,
 // selection and tie kernels and after the last.

@@ -1,44 +1,42 @@
-// tc_fused.cu -- one generation of the tensor-core executors in one kernel
-// (BF16 operands, D <= 256), followed by a small commit kernel.
+// tc_fused.cu -- one generation of the BF16 tensor-core executors (D <= 256)
+// in three kernels, for the executors whose rotation is a small dense GEMM.
 //
-// k_tc_gen is persistent (one CTA per SM, 512 threads) and walks the 128-row
-// M tiles of the GEMM (rows of one problem, possibly several executors).  Per
-// tile:
-//   1. draws      lanes 0..7 of every epilogue warp take one row each: the
-//                 Philox index draws and K into a field-major record in shared
-//                 memory; then each warp draws the exponential-crossover
-//                 lengths of its 8 rows with all 32 lanes (a lane per four
-//                 coordinate uniforms, the first one at or above CR found by a
-//                 ballot);
-//   2. trial      all 16 epilogue warps, a lane per (row, 4-coordinate chunk),
-//                 8 rows x 4 consecutive chunks per warp step: mutation,
-//                 crossover and clip (the same trial_chunk arithmetic as every
-//                 other trial kernel), the FP32 trial row to global memory and
-//                 the BF16 operand u - o straight into the A tile in shared
-//                 memory, in the UMMA 128-byte-swizzled K-major layout (A never
-//                 touches global memory);
-//   3. MMA        thread 0 issues tcgen05.mma (M 128, N 256, K 16, FP32
-//                 accumulate in TMEM) over the K tiles; B, the problem's padded
-//                 BF16 R rows, is loaded by TMA once per problem and stays in
-//                 shared memory while the CTA's tiles belong to that problem;
-//   4. epilogue   16 warps read TMEM (tcgen05.ld), each a quarter of the
-//                 columns of 32 rows, accumulate the objective and compose the
-//                 quarters in column order (as the general GEMM does);
-//   5. selection  a thread per row compares f(u) with the stored f(x); clear
-//                 cases write the decision, near ties are listed;
-//   6. ties       the tile's near ties, up to 16 at once: z = R (x - o) and
-//                 dz = R (u - x) in FP32 on the CUDA cores (R^T streamed through
-//                 shared memory by cp.async, once per batch), then the FP32
-//                 difference form; a trial identical to its target is
-//                 recognised from the staged u - x and accepted as it is.
-// The decision goes to fu[fitness index]: the new fitness when the trial is
-// accepted, NaN when it is rejected.  k_tc_commit (a CTA per executor) then
-// copies the accepted rows, stores their fitness and ranks the pbest pool of
-// the next generation; generational semantics hold because no row of the
-// population changes before every trial of the generation is built.
+//   k_tc_rank   block per executor: best and the pbest pool from the stored
+//               fitness (the generation-start ranking every trial uses);
+//   k_tc_trial2 a CTA of 256 threads per 32 operand rows.  Draws first:
+//               lanes 0..3 of each warp run a row's Philox index draws, then
+//               the warp's 32 lanes draw the exponential-crossover lengths of
+//               its four rows together (a lane per four coordinate uniforms,
+//               the first one at or above CR found by a ballot).  Then a lane
+//               per (row, 4-coordinate chunk), 8 rows x 4 consecutive chunks
+//               per warp step: mutation, crossover and clip (trial_chunk, the
+//               arithmetic every trial kernel shares), the FP32 trial row and
+//               the BF16 operand u - o, K-padded, to global memory.  Many small
+//               CTAs per SM keep many row gathers in flight;
+//   k_tc_sel    persistent, one CTA of 512 threads per SM, over the 128-row M
+//               tiles (rows of one problem, possibly of several executors):
+//               TMA loads of the A tile and, once per problem, of B (the
+//               problem's padded BF16 R rows, kept in shared memory while the
+//               CTA's tiles belong to that problem); thread 0 issues
+//               tcgen05.mma (M 128, N 256, K 16, FP32 accumulate in TMEM);
+//               16 warps read TMEM (tcgen05.ld), each a quarter of the
+//               columns of 32 rows, accumulate the objective and compose the
+//               quarters in column order; a thread per row then selects:
+//               clear acceptances are committed at once (rows copied by the
+//               whole CTA), near ties are listed and decided 16 at a time from
+//               z = R (x - o) and dz = R (u - x) in FP32 on the CUDA cores (R
+//               rows staged through shared memory by cp.async, float4 loads,
+//               every fma chain in ascending k like every other FP32
+//               rotation) and the FP32 difference form; a trial identical to
+//               its target is recognised from the staged u - x and accepted as
+//               it is.
+// Committing inside k_tc_sel keeps generational semantics: every trial row
+// of the generation was built by k_tc_trial2 before k_tc_sel starts, and
+// k_tc_sel reads a population row only for that row's own decision.
+// Results are bit-identical to the five-kernel pipeline of tc_rotate.cu.
 //
 // Every mbarrier wait is bounded; on timeout the kernel latches
-// METADE_ETIMEOUT, waits (bounded) for its own TMA copy and MMAs, frees TMEM
+// METADE_ETIMEOUT, waits (bounded) for its own TMA copies and MMAs, frees TMEM
 // and returns.
 #include "block.cuh"
 #include "internal.h"
@@ -50,34 +48,27 @@ namespace {
 
 using namespace tc;
 
-constexpr int kRows = 128;       // rows per M tile (TMEM lanes)
-constexpr int kMaxKt = 4;        // K tiles of 64 BF16 elements: D <= 256
-constexpr int kTieBatch = 16;    // near ties rotated together
-constexpr int kVec = 256;        // stride of a staged tie vector (floats)
-constexpr int kRejected = -1;    // bit pattern of the "rejected" mark in fu (a NaN)
-constexpr int kRtRows = 16;      // R^T rows per cp.async stage of the tie rotation
-constexpr int kGenThreads = 32 * kEpiWarps;  // 16 warps; thread 0 also issues the TMA loads and MMAs
+constexpr int kRows = 128;                   // rows per M tile (TMEM lanes)
+constexpr int kMaxKt = 4;                    // K tiles of 64 BF16 elements: D <= 256
+constexpr int kSelThreads = 32 * kEpiWarps;  // 16 warps; thread 0 also issues the TMA loads and MMAs
+constexpr int kTieBatch = 16;                // near ties rotated together
+constexpr int kVec = 256;                    // stride of a staged tie vector (floats)
+constexpr int kRc = 16;                      // R columns per cp.async stage of the tie rotation
+constexpr int kRcs = kRc + 4;                // row stride of a stage: float4 loads of 8 rows hit 32 banks
+constexpr int kTRows = 32;                   // rows per CTA of k_tc_trial2
+constexpr int kTThreads = 256;
 
-// record fields, [field][kRows]
+constexpr size_t kASize = (size_t)kMaxKt * kAT;                                  // 64 KB
+constexpr size_t kPartSize = (size_t)(kParts - 1) * kRows * 8 * sizeof(float);  // 12 KB
+// the tie phase reuses A and the part-exchange area (they follow each other)
+constexpr size_t kTieSize = (size_t)2 * kTieBatch * kVec * sizeof(float) + (size_t)2 * kVec * kRcs * sizeof(float);
+static_assert(kTieSize <= kASize + kPartSize, "tie buffers exceed the A tile and the exchange area");
+static_assert((kASize + kPartSize) % 1024 == 0, "B must start 1024-byte aligned");
+
+// record fields of k_tc_trial2, [field][kTRows]
 enum {
     F_VALID, F_IBL, F_IBR, F_P0, F_P1, F_P2, F_P3, F_M0, F_M1, F_M2, F_M3, F_JR, F_NS, F_L, F_K,
-    F_FIDX, F_POPLO, F_POPHI, F_F, F_CRI, F_PACK, F_I, F_STREAM, kFields
-};
-
-constexpr size_t kASize = (size_t)kMaxKt * kAT;                      // 64 KB
-constexpr size_t kRecSize = (size_t)kFields * kRows * sizeof(int);   // 11.5 KB
-constexpr size_t kPartSize = (size_t)(kParts - 1) * kRows * 8 * sizeof(float);  // 12 KB
-
-struct GenArgs {
-    StepArgs a;
-    const int* tiles;         // [n_tiles][2]: first operand row, rows
-    int n_tiles;
-    const int* row_exec;      // operand row -> executor
-    const long long* brow;    // per problem: first B row
-    const int* topk_all;      // pbest pools (fitness layout)
-    float* uscr;              // trial rows (population layout)
-    float* fu;                // decisions (fitness layout)
-    int kt;                   // K tiles of the operands
+    F_POPLO, F_POPHI, F_F, F_CRI, F_PACK, F_I, F_STREAM, F_DIM, F_DPAD, F_SHIFT, kFields
 };
 
 // 16-byte cp.async; src_bytes 0 fills the destination with zeros
@@ -86,40 +77,201 @@ __device__ __forceinline__ void cp_async16z(float* dst, const float* src, int sr
                  : "memory");
 }
 
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// byte offset of 4 consecutive BF16 elements (k0, a multiple of 4) of row r in
-// the 128-byte-swizzled K-major A tile: K tile k0 / 64, row r at r * 128,
-// 16-byte unit (k0 % 64) / 8 at position unit ^ (r % 8), half (k0 % 8) / 4
-__device__ __forceinline__ uint32_t a_off(int r, int k0) {
-    return (uint32_t)((k0 >> 6) * kAT + r * 128 + ((((k0 & 63) >> 3) ^ (r & 7)) << 4) + ((k0 & 4) << 1));
-}
-
 __device__ __forceinline__ uint2 pack_bf16x4(const float (&d)[4]) {
     const __nv_bfloat162 lo = __floats2bfloat162_rn(d[0], d[1]);
     const __nv_bfloat162 hi = __floats2bfloat162_rn(d[2], d[3]);
     return make_uint2(*reinterpret_cast<const uint32_t*>(&lo), *reinterpret_cast<const uint32_t*>(&hi));
 }
 
-__global__ void __launch_bounds__(kGenThreads, 1) k_tc_gen(const __grid_constant__ CUtensorMap tmB, GenArgs g) {
+// ------------------------------------------------------------ k_tc_trial2
+__global__ void __launch_bounds__(kTThreads, 4) k_tc_trial2(StepArgs a, const int* __restrict__ row_exec, int n_rows,
+                                                         const int* __restrict__ topk_all, float* uscr, uint8_t* aq,
+                                                         int kp) {
+    __shared__ int rec[kFields * kTRows];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int r0 = blockIdx.x * kTRows;
+    const uint32_t epoch = a.epoch_dev ? *a.epoch_dev : a.epoch;
+
+    // draws: warp w takes rows 4 w .. 4 w + 3
+    {
+        const int r = 4 * warp + (lane & 3);
+        int cs2 = 0;
+        if (lane < 4) {
+            int valid = 0;
+            if (r0 + r < n_rows) {
+                const int k = row_exec[r0 + r];
+                const InstDesc e = a.desc[k];
+                const int i = r0 + r - e.tc_row;
+                const Strat s = load_strat(a.theta + 6 * k, e.np);
+                if (s.ok) {
+                    valid = 1;
+                    cs2 = s.cs == 2;
+                    const int* topk = topk_all + e.fit_off;
+                    const Ctr c = make_ctr(a.key, (uint32_t)e.stream, a.gen0, (uint32_t)i, epoch);
+                    Indiv v;
+                    indiv_setup(s, c, i, e.np, e.dim, e.kp, topk, topk[0], v);
+                    rec[F_IBL * kTRows + r] = v.ibl;
+                    rec[F_IBR * kTRows + r] = v.ibr;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        rec[(F_P0 + q) * kTRows + r] = q < s.dn ? diff_plus(v, s.a, q) : 0;
+                        rec[(F_M0 + q) * kTRows + r] = q < s.dn ? diff_minus(v, s.a, q) : 0;
+                    }
+                    rec[F_JR * kTRows + r] = v.jrand;
+                    rec[F_NS * kTRows + r] = v.nstart;
+                    rec[F_L * kTRows + r] = 0;
+                    rec[F_K * kTRows + r] = (int)v.kraw;
+                    rec[F_POPLO * kTRows + r] = (int)(uint32_t)e.pop_off;
+                    rec[F_POPHI * kTRows + r] = (int)(e.pop_off >> 32);
+                    rec[F_F * kTRows + r] = __float_as_int(s.F);
+                    rec[F_CRI * kTRows + r] = (int)s.cri;
+                    rec[F_PACK * kTRows + r] = s.cs | (s.dn << 4) | ((s.bl != s.br ? 1 : 0) << 8);
+                    rec[F_I * kTRows + r] = i;
+                    rec[F_STREAM * kTRows + r] = e.stream;
+                    rec[F_DIM * kTRows + r] = e.dim;
+                    rec[F_DPAD * kTRows + r] = e.dpad;
+                    rec[F_SHIFT * kTRows + r] = e.shift_off;
+                }
+            }
+            rec[F_VALID * kTRows + r] = valid;
+        }
+        // exponential length L = 1 + min(t*, D - 1), t* the first coordinate
+        // uniform U_t (slot 4 + t / 4, word t % 4) not below CR
+        const unsigned exp_rows = __ballot_sync(kFull, cs2 != 0) & 0xFu;
+        __syncwarp();
+        if (exp_rows) {
+            int dmax = 0;  // the widest exponential row of the warp bounds the rounds
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if ((exp_rows >> q) & 1u) dmax = max(dmax, rec[F_DIM * kTRows + 4 * warp + q]);
+            for (int base = 0; base == 0 || base < dmax - 1; base += 128) {  // t = base + 4 lane + word
+                uint4 w4[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {  // the Philox chains of the four rows interleave
+                    w4[q] = make_uint4(0, 0, 0, 0);
+                    if ((exp_rows >> q) & 1u) {
+                        const int rq = 4 * warp + q;
+                        const Ctr c = make_ctr(a.key, (uint32_t)rec[F_STREAM * kTRows + rq], a.gen0,
+                                               (uint32_t)rec[F_I * kTRows + rq], epoch);
+                        w4[q] = c.slot(4 + (uint32_t)((base >> 2) + lane));
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (!((exp_rows >> q) & 1u)) continue;  // warp-uniform
+                    const int rq = 4 * warp + q;
+                    const int dim = rec[F_DIM * kTRows + rq];
+                    if (rec[F_L * kTRows + rq] != 0 || (base > 0 && base >= dim - 1)) continue;  // done
+                    const uint32_t cri = (uint32_t)rec[F_CRI * kTRows + rq];
+                    int first = 4;  // first failing word of this lane
+#pragma unroll
+                    for (int wq = 3; wq >= 0; --wq) {
+                        const int t = base + 4 * lane + wq;
+                        if (t <= dim - 2 && (word_of(w4[q], wq) >> 8) >= cri) first = wq;
+                    }
+                    const unsigned fails = __ballot_sync(kFull, first < 4);
+                    int L = 0;
+                    if (fails) {
+                        const int fl = __ffs(fails) - 1;
+                        const int fq = __shfl_sync(kFull, first, fl);
+                        L = 1 + base + 4 * fl + fq;
+                    } else if (base + 128 >= dim - 1) {
+                        L = dim;  // every uniform below CR: the whole row
+                    }
+                    if (lane == 0) rec[F_L * kTRows + rq] = L;
+                    __syncwarp();
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // trial rows and operand rows: lane = (row 8 * unit + lane / 4, chunk 4 * unit' + lane % 4)
+    const int nchb = kp / 16;  // blocks of 4 chunks along K
+    const int units = (kTRows / 8) * nchb;
+    for (int u = warp; u < units; u += kTThreads / 32) {
+        const int r = 8 * (u / nchb) + (lane >> 2);
+        const int j4 = 4 * (4 * (u % nchb) + (lane & 3));
+        if (r0 + r >= n_rows) continue;
+        float dd[4] = {0.f, 0.f, 0.f, 0.f};
+        const int dpad = rec[F_DPAD * kTRows + r];
+        if (rec[F_VALID * kTRows + r] && j4 < dpad) {
+            const long long po = (long long)(((unsigned long long)(uint32_t)rec[F_POPHI * kTRows + r] << 32) |
+                                             (uint32_t)rec[F_POPLO * kTRows + r]);
+            const float* X = a.pop + po;
+            const long long ld = dpad;
+            const int pack = rec[F_PACK * kTRows + r];
+            Strat s;
+            s.F = __int_as_float(rec[F_F * kTRows + r]);
+            s.cri = (uint32_t)rec[F_CRI * kTRows + r];
+            s.cs = pack & 15;
+            s.dn = (pack >> 4) & 15;
+            s.bl = 0;
+            s.br = (pack >> 8) & 1;  // trial_chunk reads bl != br as "has a directional term"
+            const int i = rec[F_I * kTRows + r];
+            // the population is read-only here: non-coherent loads
+            const float4 av = __ldg(reinterpret_cast<const float4*>(X + rec[F_IBL * kTRows + r] * ld + j4));
+            const float4 bv = __ldg(reinterpret_cast<const float4*>(X + rec[F_IBR * kTRows + r] * ld + j4));
+            const float4 xv = __ldg(reinterpret_cast<const float4*>(X + (long long)i * ld + j4));
+            float4 p[4], m[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (q < s.dn) {
+                    p[q] = __ldg(reinterpret_cast<const float4*>(X + rec[(F_P0 + q) * kTRows + r] * ld + j4));
+                    m[q] = __ldg(reinterpret_cast<const float4*>(X + rec[(F_M0 + q) * kTRows + r] * ld + j4));
+                }
+            }
+            uint4 w = make_uint4(0, 0, 0, 0);
+            if (s.cs == 1) {
+                const Ctr c = make_ctr(a.key, (uint32_t)rec[F_STREAM * kTRows + r], a.gen0, (uint32_t)i, epoch);
+                w = c.slot(4 + (uint32_t)(j4 >> 2));
+            }
+            float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (q < s.dn) {
+                    sum.x += p[q].x - m[q].x; sum.y += p[q].y - m[q].y;
+                    sum.z += p[q].z - m[q].z; sum.w += p[q].w - m[q].w;
+                }
+            }
+            const float K = (float)(uint32_t)rec[F_K * kTRows + r] * (1.0f / 16777216.0f);
+            float uo[4];
+            trial_chunk(s, K, rec[F_JR * kTRows + r], rec[F_NS * kTRows + r], rec[F_L * kTRows + r],
+                        rec[F_DIM * kTRows + r], j4, av, bv, xv, sum, w, a.shift + rec[F_SHIFT * kTRows + r], a.lo,
+                        a.hi, uo, dd);
+            *reinterpret_cast<float4*>(uscr + po + (long long)i * ld + j4) = make_float4(uo[0], uo[1], uo[2], uo[3]);
+        }
+        *reinterpret_cast<uint2*>(aq + ((size_t)(r0 + r) * kp + j4) * 2) = pack_bf16x4(dd);
+    }
+}
+
+// --------------------------------------------------------------- k_tc_sel
+struct SelArgs {
+    StepArgs a;
+    const int* tiles;         // [n_tiles][2]: first operand row, rows (all of one problem)
+    int n_tiles;
+    const int* row_exec;      // operand row -> executor
+    const long long* brow;    // per problem: first B row
+    const float* uscr;        // trial rows (population layout)
+    int kt;                   // K tiles of the operands
+};
+
+__global__ void __launch_bounds__(kSelThreads, 1) k_tc_sel(const __grid_constant__ CUtensorMap tmA,
+                                                           const __grid_constant__ CUtensorMap tmB, SelArgs g) {
     extern __shared__ uint8_t smraw[];
-    __shared__ __align__(8) uint64_t bfull, mma_done, drain;
+    __shared__ __align__(8) uint64_t afull, bfull, mma_done, drain;
     __shared__ uint32_t tmem_base;
-    __shared__ int abort_s, ntie_s;
-    __shared__ int tie_row[kRows];
+    __shared__ int abort_s, ntie_s, nacc_s;
+    __shared__ int tie_row[kRows], acc_row[kRows];
     __shared__ float tie_fx[kRows];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
     uint8_t* As = sm;
-    uint8_t* Bs = sm + kASize;
-    int* rec = reinterpret_cast<int*>(Bs + (size_t)g.kt * kBT);
-    float* part = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(rec) + kRecSize);
-    float* tv = reinterpret_cast<float*>(As);  // tie vectors reuse the A tile once the MMAs are done
+    float* part = reinterpret_cast<float*>(sm + kASize);
+    uint8_t* Bs = sm + kASize + kPartSize;
+    float* tv = reinterpret_cast<float*>(As);  // tie vectors: the A tile and the exchange area, once free
     const StepArgs& a = g.a;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool issuer = tid == 0;  // TMA loads and MMAs
-    const uint32_t epoch = a.epoch_dev ? *a.epoch_dev : a.epoch;
+    const bool issuer = tid == 0;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -128,6 +280,7 @@ __global__ void __launch_bounds__(kGenThreads, 1) k_tc_gen(const __grid_constant
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
+        mbar_init(&afull, 1);
         mbar_init(&bfull, 1);
         mbar_init(&mma_done, 1);
         mbar_init(&drain, 1);
@@ -140,174 +293,27 @@ __global__ void __launch_bounds__(kGenThreads, 1) k_tc_gen(const __grid_constant
     const uint32_t taddr = tmem_base;
 
     int cur_prob = -1;
-    uint32_t bphase = 0, mphase = 0;
-    bool b_in_flight = false;  // thread 0: a B load not yet waited on
+    uint32_t aphase = 0, bphase = 0, mphase = 0;
+    bool a_in_flight = false, b_in_flight = false;  // thread 0: loads not yet waited on
     for (int t = blockIdx.x; t < g.n_tiles; t += gridDim.x) {
         const int arow = g.tiles[2 * t], nr = g.tiles[2 * t + 1];
         const InstDesc d = a.desc[g.row_exec[arow]];  // dim, objective and problem of every row of the tile
-        // B: the problem's R rows, once per problem (the previous tile's MMAs are complete)
-        const bool load_b = d.prob != cur_prob;
-        if (load_b && issuer) {
-            mbar_expect_tx(&bfull, (uint32_t)(g.kt * kBT));
-            const int brow0 = (int)g.brow[d.prob];
-            for (int kk = 0; kk < g.kt; ++kk) tma_load_2d(Bs + (size_t)kk * kBT, &tmB, &bfull, kk * kBK, brow0);
-            b_in_flight = true;
-        }
-        cur_prob = d.prob;
 
-        // 1. draws: warp w takes rows 8 w .. 8 w + 7; lanes 0..7 run a row's
-        // index draws, then the warp's 32 lanes draw the exponential lengths of
-        // its rows together (lane l: the uniforms of coordinates 4 l .. 4 l + 3)
-        {
-            const int r = 8 * warp + (lane & 7);
-            int cs2 = 0;  // this lane's row uses exponential crossover
-            if (lane < 8) {
-                int valid = 0;
-                if (r < nr) {
-                    const int k = g.row_exec[arow + r];
-                    const InstDesc e = a.desc[k];
-                    const int i = arow + r - e.tc_row;
-                    const Strat s = load_strat(a.theta + 6 * k, e.np);
-                    if (s.ok) {
-                        valid = 1;
-                        cs2 = s.cs == 2;
-                        const int* topk = g.topk_all + e.fit_off;
-                        const Ctr c = make_ctr(a.key, (uint32_t)e.stream, a.gen0, (uint32_t)i, epoch);
-                        Indiv v;
-                        indiv_setup(s, c, i, e.np, e.dim, e.kp, topk, topk[0], v);
-                        rec[F_IBL * kRows + r] = v.ibl;
-                        rec[F_IBR * kRows + r] = v.ibr;
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            rec[(F_P0 + q) * kRows + r] = q < s.dn ? diff_plus(v, s.a, q) : 0;
-                            rec[(F_M0 + q) * kRows + r] = q < s.dn ? diff_minus(v, s.a, q) : 0;
-                        }
-                        rec[F_JR * kRows + r] = v.jrand;
-                        rec[F_NS * kRows + r] = v.nstart;
-                        rec[F_L * kRows + r] = 0;
-                        rec[F_K * kRows + r] = (int)v.kraw;
-                        rec[F_FIDX * kRows + r] = e.fit_off + i;
-                        rec[F_POPLO * kRows + r] = (int)(uint32_t)e.pop_off;
-                        rec[F_POPHI * kRows + r] = (int)(e.pop_off >> 32);
-                        rec[F_F * kRows + r] = __float_as_int(s.F);
-                        rec[F_CRI * kRows + r] = (int)s.cri;
-                        rec[F_PACK * kRows + r] = s.cs | (s.dn << 4) | ((s.bl != s.br ? 1 : 0) << 8);
-                        rec[F_I * kRows + r] = i;
-                        rec[F_STREAM * kRows + r] = e.stream;
-                    }
-                }
-                rec[F_VALID * kRows + r] = valid;
-            }
-            // exponential length L = 1 + min(t*, D - 1), t* the first coordinate
-            // uniform U_t (slot 4 + t / 4, word t % 4) not below CR
-            const unsigned exp_rows = __ballot_sync(kFull, cs2 != 0) & 0xFFu;
-            __syncwarp();
-            for (int base = 0; exp_rows && (base == 0 || base < d.dim - 1); base += 128) {  // t = base + 4 lane + q
-                uint4 w8[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {  // the Philox chains of the 8 rows interleave
-                    w8[q] = make_uint4(0, 0, 0, 0);
-                    if ((exp_rows >> q) & 1u) {
-                        const int rq = 8 * warp + q;
-                        const Ctr c = make_ctr(a.key, (uint32_t)rec[F_STREAM * kRows + rq], a.gen0,
-                                               (uint32_t)rec[F_I * kRows + rq], epoch);
-                        w8[q] = c.slot(4 + (uint32_t)((base >> 2) + lane));
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    if (!((exp_rows >> q) & 1u)) continue;  // warp-uniform
-                    const int rq = 8 * warp + q;
-                    if (base > 0 && rec[F_L * kRows + rq] != 0) continue;  // ended in an earlier round
-                    const uint32_t cri = (uint32_t)rec[F_CRI * kRows + rq];
-                    int first = 4;  // first failing word of this lane
-#pragma unroll
-                    for (int wq = 3; wq >= 0; --wq) {
-                        const int t = base + 4 * lane + wq;
-                        if (t <= d.dim - 2 && (word_of(w8[q], wq) >> 8) >= cri) first = wq;
-                    }
-                    const unsigned fails = __ballot_sync(kFull, first < 4);
-                    int L = 0;
-                    if (fails) {
-                        const int fl = __ffs(fails) - 1;
-                        const int fq = __shfl_sync(kFull, first, fl);
-                        L = 1 + base + 4 * fl + fq;
-                    } else if (base + 128 >= d.dim - 1) {
-                        L = d.dim;  // every uniform below CR: the whole row
-                    }
-                    if (lane == 0) rec[F_L * kRows + rq] = L;
-                    __syncwarp();
-                }
-            }
-        }
-        __syncthreads();
-
-        // 2. trial rows and the A tile: lane = (row 8 * unit + lane / 4, chunk 4 * unit' + lane % 4)
-        {
-            const int nchb = g.kt * 4;  // blocks of 4 chunks (16 elements) along K
-            const int units = (kRows / 8) * nchb;
-#pragma unroll 2
-            for (int u = warp; u < units; u += kEpiWarps) {
-                const int r = 8 * (u / nchb) + (lane >> 2);
-                const int j4 = 4 * (4 * (u % nchb) + (lane & 3));
-                float dd[4] = {0.f, 0.f, 0.f, 0.f};
-                if (rec[F_VALID * kRows + r] && j4 < d.dpad) {
-                    const long long po = (long long)(((unsigned long long)(uint32_t)rec[F_POPHI * kRows + r] << 32) |
-                                                     (uint32_t)rec[F_POPLO * kRows + r]);
-                    const float* X = a.pop + po;
-                    const long long ld = d.dpad;
-                    const int pack = rec[F_PACK * kRows + r];
-                    Strat s;
-                    s.F = __int_as_float(rec[F_F * kRows + r]);
-                    s.cri = (uint32_t)rec[F_CRI * kRows + r];
-                    s.cs = pack & 15;
-                    s.dn = (pack >> 4) & 15;
-                    s.bl = 0;
-                    s.br = (pack >> 8) & 1;  // trial_chunk reads bl != br as "has a directional term"
-                    const int i = rec[F_I * kRows + r];
-                    // the population is read-only during the kernel: non-coherent loads, which the
-                    // compiler may issue ahead of the previous unit's stores
-                    const float4 av = __ldg(reinterpret_cast<const float4*>(X + rec[F_IBL * kRows + r] * ld + j4));
-                    const float4 bv = __ldg(reinterpret_cast<const float4*>(X + rec[F_IBR * kRows + r] * ld + j4));
-                    const float4 xv = __ldg(reinterpret_cast<const float4*>(X + (long long)i * ld + j4));
-                    float4 p[4], m[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        if (q < s.dn) {
-                            p[q] = __ldg(reinterpret_cast<const float4*>(X + rec[(F_P0 + q) * kRows + r] * ld + j4));
-                            m[q] = __ldg(reinterpret_cast<const float4*>(X + rec[(F_M0 + q) * kRows + r] * ld + j4));
-                        }
-                    }
-                    float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        if (q < s.dn) {
-                            sum.x += p[q].x - m[q].x; sum.y += p[q].y - m[q].y;
-                            sum.z += p[q].z - m[q].z; sum.w += p[q].w - m[q].w;
-                        }
-                    }
-                    uint4 w = make_uint4(0, 0, 0, 0);
-                    if (s.cs == 1) {
-                        const Ctr c = make_ctr(a.key, (uint32_t)rec[F_STREAM * kRows + r], a.gen0, (uint32_t)i, epoch);
-                        w = c.slot(4 + (uint32_t)(j4 >> 2));
-                    }
-                    const float K = (float)(uint32_t)rec[F_K * kRows + r] * (1.0f / 16777216.0f);
-                    float uo[4];
-                    trial_chunk(s, K, rec[F_JR * kRows + r], rec[F_NS * kRows + r], rec[F_L * kRows + r], d.dim, j4,
-                                av, bv, xv, sum, w, a.shift + d.shift_off, a.lo, a.hi, uo, dd);
-                    *reinterpret_cast<float4*>(g.uscr + po + (long long)i * ld + j4) =
-                        make_float4(uo[0], uo[1], uo[2], uo[3]);
-                }
-                *reinterpret_cast<uint2*>(As + a_off(r, j4)) = pack_bf16x4(dd);
-            }
-            fence_proxy_async();  // the generic-proxy writes of A become visible to the tensor cores
-        }
-        __syncthreads();
-
-        // 3. MMA: one thread, over the K tiles, into one accumulator of kBN columns
+        // 1. loads (the previous tile's MMAs are complete and its tie vectors no longer needed) and MMAs
         if (issuer) {
-            bool ok = true;
-            if (b_in_flight) {
+            mbar_expect_tx(&afull, (uint32_t)(g.kt * kAT));
+            for (int kk = 0; kk < g.kt; ++kk) tma_load_2d(As + (size_t)kk * kAT, &tmA, &afull, kk * kBK, arow);
+            a_in_flight = true;
+            if (d.prob != cur_prob) {
+                mbar_expect_tx(&bfull, (uint32_t)(g.kt * kBT));
+                const int brow0 = (int)g.brow[d.prob];
+                for (int kk = 0; kk < g.kt; ++kk) tma_load_2d(Bs + (size_t)kk * kBT, &tmB, &bfull, kk * kBK, brow0);
+                b_in_flight = true;
+            }
+            bool ok = mbar_wait(&afull, aphase);
+            aphase ^= 1u;
+            a_in_flight = false;
+            if (ok && b_in_flight) {
                 ok = mbar_wait(&bfull, bphase);
                 bphase ^= 1u;
                 b_in_flight = false;
@@ -327,8 +333,9 @@ __global__ void __launch_bounds__(kGenThreads, 1) k_tc_gen(const __grid_constant
                 abort_s = 1;
             }
         }
+        cur_prob = d.prob;
 
-        // 4. epilogue: warp w reads TMEM lanes 32 (w % 4).. and column part w / 4
+        // 2. epilogue: warp w reads TMEM lanes 32 (w % 4).. and column part w / 4
         const int qd = warp & 3, prt = warp >> 2;
         const int row = 32 * qd + lane;
         ObjR acc;
@@ -372,12 +379,11 @@ __global__ void __launch_bounds__(kGenThreads, 1) k_tc_gen(const __grid_constant
             }
         }
         mphase ^= 1u;
+        if (tid == 0) ntie_s = nacc_s = 0;
         __syncthreads();
 
-        // 5. selection: the part-0 thread of each row
-        if (tid == 0) ntie_s = 0;
-        float fnew = 0.f;
-        if (prt == 0) {
+        // 3. selection: the part-0 thread of each row; clear acceptances are listed for the row copy
+        if (prt == 0 && row < nr && !abort_s) {
             for (int j = 0; j < kParts - 1; ++j) {
                 const float* sl = part + ((size_t)j * kRows + row) * 8;
                 const float4 x0 = *reinterpret_cast<const float4*>(sl), x1 = *reinterpret_cast<const float4*>(sl + 4);
@@ -389,130 +395,168 @@ __global__ void __launch_bounds__(kGenThreads, 1) k_tc_gen(const __grid_constant
                 rb.first = __float_as_int(x1.z) == 0;
                 obj_compose(d.obj, acc, rb, x1.x, x1.y, __float_as_int(x1.z));
             }
-            fnew = nan_to_inf(acc.finish(d.obj, d.dim));
-        }
-        __syncthreads();  // ntie_s = 0 before any tie is listed
-        if (prt == 0 && rec[F_VALID * kRows + row] && !abort_s) {
-            const int fidx = rec[F_FIDX * kRows + row];
-            const float fx = a.fit[fidx];
-            const float fn = fnew;
-            // near ties (including trials identical to their targets, recognised
-            // in the tie phase from the staged u - x) are decided below
-            if (near_tie(fn, fx, tie_band(d.dim))) {
-                const int q = atomicAdd(&ntie_s, 1);
-                tie_row[q] = row;
-                tie_fx[q] = fx;
-            } else {
-                g.fu[fidx] = fn <= fx ? fn : __int_as_float(kRejected);
+            const float fn = nan_to_inf(acc.finish(d.obj, d.dim));
+            const int k = g.row_exec[arow + row];
+            const InstDesc e = a.desc[k];
+            if (load_strat(a.theta + 6 * k, e.np).ok) {  // rows of an invalid theta stay as they are
+                const int fidx = e.fit_off + (arow + row - e.tc_row);
+                const float fx = a.fit[fidx];
+                if (near_tie(fn, fx, tie_band(d.dim))) {
+                    const int q = atomicAdd(&ntie_s, 1);
+                    tie_row[q] = row;
+                    tie_fx[q] = fx;
+                } else if (fn <= fx) {
+                    acc_row[atomicAdd(&nacc_s, 1)] = row;
+                    a.fit[fidx] = fn;
+                }
             }
         }
         __syncthreads();
+        // accepted rows into the population, the whole CTA copying float4s
+        {
+            const int f4 = d.dpad >> 2, n = nacc_s * f4;
+            for (int e2 = tid; e2 < n; e2 += kSelThreads) {
+                const int q = e2 / f4, c4 = e2 - q * f4;
+                const int gr = arow + acc_row[q];
+                const InstDesc e = a.desc[g.row_exec[gr]];
+                const long long off = e.pop_off + (long long)(gr - e.tc_row) * d.dpad + 4 * c4;
+                *reinterpret_cast<float4*>(a.pop + off) = __ldg(reinterpret_cast<const float4*>(g.uscr + off));
+            }
+        }
 
-        // 6. near ties, kTieBatch at a time: z = R (x - o) and dz = R (u - x) in
-        // FP32 (k ascending in every fma chain, like every FP32 rotation), R^T
-        // streamed through shared memory 16 rows at a time by cp.async (double
-        // buffered), each thread one row of z for half of the batch
+        // 4. near ties, kTieBatch at a time: z = R (x - o) and dz = R (u - x) in FP32
         const int nt = abort_s ? 0 : ntie_s;
         const float* o = a.shift + d.shift_off;
-        const float* RT = a.rotT + d.rot_off;
+        const float* Rr = a.rot + d.rot_off;  // R rows [dim][dpad]
         float* vx = tv;                          // [kTieBatch][kVec] x - o, then z
         float* vl = tv + kTieBatch * kVec;       // u - x, then dz
-        float* sR = tv + 2 * kTieBatch * kVec;   // [2][kRtRows][kVec] R^T rows
-        const int nchunk = (d.dim + kRtRows - 1) / kRtRows;
+        float* sR = tv + 2 * kTieBatch * kVec;   // [2][kVec][kRcs]: R columns c0 .. c0 + 15 of every row
+        const int nchunk = (d.dim + kRc - 1) / kRc;
         for (int b0 = 0; b0 < nt; b0 += kTieBatch) {
             const int nb = min(kTieBatch, nt - b0);
-            auto stage_rt = [&](int ch) {  // R^T rows ch * 16 .. into buffer ch & 1 (zero past dim)
-                float* dst = sR + (size_t)(ch & 1) * kRtRows * kVec;
-                const int f4 = d.dpad >> 2;
-                for (int e = tid; e < kRtRows * f4; e += blockDim.x) {
-                    const int cc = e / f4, x4 = e - cc * f4, c = ch * kRtRows + cc;
-                    cp_async16z(dst + cc * kVec + 4 * x4, RT + (size_t)min(c, d.dim - 1) * d.dpad + 4 * x4,
-                                c < d.dim ? 16 : 0);
+            __syncthreads();  // the previous user of the buffers (row copy or last batch) is done
+            auto stage = [&](int ch) {  // R[r][ch * 16 ..] for every row r < dim into buffer ch & 1
+                float* dst = sR + (size_t)(ch & 1) * kVec * kRcs;
+                const int c0 = ch * kRc;
+                for (int e2 = tid; e2 < d.dim * (kRc / 4); e2 += kSelThreads) {
+                    const int rr = e2 >> 2, c = c0 + 4 * (e2 & 3);
+                    const bool in = c < d.dpad;
+                    cp_async16z(dst + rr * kRcs + 4 * (e2 & 3), Rr + (size_t)rr * d.dpad + (in ? c : 0), in ? 16 : 0);
                 }
                 asm volatile("cp.async.commit_group;" ::: "memory");
             };
-            stage_rt(0);
-            for (int e = tid; e < nb * kVec; e += blockDim.x) {
-                const int q = e / kVec, c = e - q * kVec;
+            stage(0);
+            for (int e2 = tid; e2 < nb * kVec; e2 += kSelThreads) {
+                const int q = e2 / kVec, c = e2 - q * kVec;
                 if (c < d.dpad) {
-                    const int r = tie_row[b0 + q];
-                    const long long po = (long long)(((unsigned long long)(uint32_t)rec[F_POPHI * kRows + r] << 32) |
-                                                     (uint32_t)rec[F_POPLO * kRows + r]);
-                    const long long off = po + (long long)rec[F_I * kRows + r] * d.dpad;
+                    const int gr = arow + tie_row[b0 + q];
+                    const InstDesc e = a.desc[g.row_exec[gr]];
+                    const long long off = e.pop_off + (long long)(gr - e.tc_row) * d.dpad;
                     const float xc = a.pop[off + c];
                     vx[q * kVec + c] = c < d.dim ? xc - o[c] : 0.f;
                     vl[q * kVec + c] = g.uscr[off + c] - xc;
                 }
             }
-            const int r = tid & (kVec - 1), h = tid >> 8;  // row of z, half of the batch (h < 2)
-            const int q0 = h * (kTieBatch / 2);
-            float az[kTieBatch / 2], ad[kTieBatch / 2];
+            // thread (row r, half h): ties h, h + 2, h + 4, ... of the batch
+            const int r = tid & (kVec - 1), h = tid >> 8;
+            float az[kTieBatch / 2], adz[kTieBatch / 2];
 #pragma unroll
-            for (int q = 0; q < kTieBatch / 2; ++q) az[q] = ad[q] = 0.f;
+            for (int q = 0; q < kTieBatch / 2; ++q) az[q] = adz[q] = 0.f;
+            const int mine = (nb - h + 1) >> 1;  // ties of this half (warp-uniform)
             for (int ch = 0; ch < nchunk; ++ch) {
                 if (ch + 1 < nchunk) {
-                    stage_rt(ch + 1);
+                    stage(ch + 1);
                     asm volatile("cp.async.wait_group 1;" ::: "memory");
                 } else {
                     asm volatile("cp.async.wait_group 0;" ::: "memory");
                 }
                 __syncthreads();
-                if (h < 2 && r < d.dim) {
-                    const float* rc = sR + (size_t)(ch & 1) * kRtRows * kVec;
-                    const int cend = min(kRtRows, d.dim - ch * kRtRows);
-                    for (int cc = 0; cc < cend; ++cc) {
-                        const int c = ch * kRtRows + cc;
-                        const float rt = rc[cc * kVec + r];
+                if (r < d.dim) {
+                    const float* rc = sR + (size_t)(ch & 1) * kVec * kRcs + r * kRcs;
+                    const int c0 = ch * kRc;
+                    const int cend = min(kRc, d.dim - c0);
+                    if (cend == kRc) {  // four float4 steps, k ascending within each
 #pragma unroll
-                        for (int q = 0; q < kTieBatch / 2; ++q) {
-                            if (q0 + q < nb) {
-                                az[q] = fmaf(rt, vx[(q0 + q) * kVec + c], az[q]);
-                                ad[q] = fmaf(rt, vl[(q0 + q) * kVec + c], ad[q]);
+                        for (int c4 = 0; c4 < kRc / 4; ++c4) {
+                            const float4 rt = *reinterpret_cast<const float4*>(rc + 4 * c4);
+#pragma unroll
+                            for (int j = 0; j < kTieBatch / 2; ++j) {
+                                if (j < mine) {
+                                    const int q = h + 2 * j;
+                                    const float4 x4 = *reinterpret_cast<const float4*>(vx + q * kVec + c0 + 4 * c4);
+                                    const float4 l4 = *reinterpret_cast<const float4*>(vl + q * kVec + c0 + 4 * c4);
+                                    az[j] = fmaf(rt.x, x4.x, az[j]);
+                                    az[j] = fmaf(rt.y, x4.y, az[j]);
+                                    az[j] = fmaf(rt.z, x4.z, az[j]);
+                                    az[j] = fmaf(rt.w, x4.w, az[j]);
+                                    adz[j] = fmaf(rt.x, l4.x, adz[j]);
+                                    adz[j] = fmaf(rt.y, l4.y, adz[j]);
+                                    adz[j] = fmaf(rt.z, l4.z, adz[j]);
+                                    adz[j] = fmaf(rt.w, l4.w, adz[j]);
+                                }
+                            }
+                        }
+                    } else {  // the last, partial chunk: one column at a time
+                        for (int cc = 0; cc < cend; ++cc) {
+                            const float rt = rc[cc];
+#pragma unroll
+                            for (int j = 0; j < kTieBatch / 2; ++j) {
+                                if (j < mine) {
+                                    const int q = h + 2 * j;
+                                    az[j] = fmaf(rt, vx[q * kVec + c0 + cc], az[j]);
+                                    adz[j] = fmaf(rt, vl[q * kVec + c0 + cc], adz[j]);
+                                }
                             }
                         }
                     }
                 }
                 __syncthreads();  // the buffer is refilled two chunks later
             }
-            if (h < 2 && r < d.dim) {  // every thread has read vx / vl: z and dz replace them
+            if (r < d.dim) {  // every thread has read vx / vl: z and dz replace them
 #pragma unroll
-                for (int q = 0; q < kTieBatch / 2; ++q) {
-                    if (q0 + q < nb) {
-                        vx[(q0 + q) * kVec + r] = az[q];
-                        vl[(q0 + q) * kVec + r] = ad[q];
+                for (int j = 0; j < kTieBatch / 2; ++j) {
+                    if (j < mine) {
+                        vx[(h + 2 * j) * kVec + r] = az[j];
+                        vl[(h + 2 * j) * kVec + r] = adz[j];
                     }
                 }
             }
             __syncthreads();
-            if (warp < nb) {
-                // a trial identical to its target (u - x == 0 everywhere, pad included) is
-                // accepted without evaluation; otherwise the FP32 difference form decides
-                const int rr = tie_row[b0 + warp];
-                const long long po = (long long)(((unsigned long long)(uint32_t)rec[F_POPHI * kRows + rr] << 32) |
-                                                 (uint32_t)rec[F_POPLO * kRows + rr]);
-                const long long off = po + (long long)rec[F_I * kRows + rr] * d.dpad;
+            if (warp < nb) {  // warp per tie: decide and commit
+                const int gr = arow + tie_row[b0 + warp];
+                const InstDesc e = a.desc[g.row_exec[gr]];
+                const int i = gr - e.tc_row;
+                const long long off = e.pop_off + (long long)i * d.dpad;
                 bool diff = false;
                 for (int c = lane; c < d.dpad; c += 32) diff = diff || (g.uscr[off + c] != a.pop[off + c]);
                 const float fx = tie_fx[b0 + warp];
-                float dec;
-                if (!__any_sync(kFull, diff)) {
-                    dec = fx;
+                bool take;
+                float fn;
+                if (!__any_sync(kFull, diff)) {  // a trial identical to its target: accepted as it is
+                    take = true;
+                    fn = fx;
                 } else {
                     const float df = warp_diff(d.obj, d.dim, vx + warp * kVec, vl + warp * kVec);
-                    dec = df <= 0.0f ? fx + df : __int_as_float(kRejected);
+                    take = df <= 0.0f;
+                    fn = fx + df;
                 }
-                if (lane == 0) g.fu[rec[F_FIDX * kRows + rr]] = dec;
+                if (take) {
+                    for (int c = 4 * lane; c < d.dpad; c += 128)
+                        *reinterpret_cast<float4*>(a.pop + off + c) =
+                            __ldg(reinterpret_cast<const float4*>(g.uscr + off + c));
+                    if (lane == 0) a.fit[e.fit_off + i] = fn;
+                }
             }
-            __syncthreads();
         }
         if (abort_s) break;  // uniform: read after a barrier
-        // the next tile's MMAs overwrite TMEM and A only after this barrier
+        // the next tile's loads overwrite A and TMEM only after this barrier
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
     }
     // leave with no copy or MMA of this CTA in flight (bounded waits)
     if (issuer) {
+        if (a_in_flight) mbar_wait(&afull, aphase);
         if (b_in_flight) mbar_wait(&bfull, bphase);
         mma_commit(&drain);
         mbar_wait(&drain, 0u);
@@ -524,33 +568,7 @@ __global__ void __launch_bounds__(kGenThreads, 1) k_tc_gen(const __grid_constant
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kBN) : "memory");
 }
 
-// Accepted rows into the population, their fitness, then the pbest pool of
-// the next generation (block per executor; a warp per row for the copy).
-__global__ void __launch_bounds__(256) k_tc_commit(StepArgs a, const int* __restrict__ execs, int* topk_all,
-                                                   const float* __restrict__ uscr, const float* __restrict__ fu,
-                                                   int rank_next) {
-    const int k = execs[blockIdx.x];
-    const InstDesc d = a.desc[k];
-    const Strat s = load_strat(a.theta + 6 * k, d.np);
-    if (!s.ok) {
-        if (threadIdx.x == 0) set_status(a.status, 1);
-        return;
-    }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = warp; i < d.np; i += blockDim.x >> 5) {
-        const float f = fu[d.fit_off + i];
-        if (isnan(f)) continue;  // rejected (warp-uniform)
-        float* X = a.pop + d.pop_off + (long long)i * d.dpad;
-        const float* U = uscr + d.pop_off + (long long)i * d.dpad;
-        for (int j = lane * 4; j < d.dpad; j += 128)
-            *reinterpret_cast<float4*>(X + j) = *reinterpret_cast<const float4*>(U + j);
-        if (lane == 0) a.fit[d.fit_off + i] = f;
-    }
-    if (!rank_next) return;
-    __syncthreads();
-    block_topk(a.fit + d.fit_off, d.np, d.kp, topk_all + d.fit_off);
-}
-
+// best and the pbest pool of every tensor-core executor (block per executor)
 __global__ void k_tc_rank(StepArgs a, const int* __restrict__ execs, int* topk_all) {
     const int k = execs[blockIdx.x];
     const InstDesc d = a.desc[k];
@@ -562,34 +580,32 @@ __global__ void k_tc_rank(StepArgs a, const int* __restrict__ execs, int* topk_a
     block_topk(a.fit + d.fit_off, d.np, d.kp, topk_all + d.fit_off);
 }
 
-size_t gen_smem(int kt) { return 1024 + kASize + (size_t)kt * kBT + kRecSize + kPartSize; }
+size_t sel_smem(int kt) { return 1024 + kASize + kPartSize + (size_t)kt * kBT; }
 
 }  // namespace
 
-bool tc_fused_fits(int kp) { return kp <= kMaxKt * kBK && gen_smem(kp / kBK) <= 227 * 1024; }
+bool tc_fused_fits(int kp) { return kp <= kMaxKt * kBK && sel_smem(kp / kBK) <= 227 * 1024; }
 
-cudaError_t launch_tc_fused_generation(const StepArgs& a, const TcPlan& p, bool first, bool last, cudaStream_t st,
-                                       cudaEvent_t* ev) {
+cudaError_t launch_tc_fused_generation(const StepArgs& a, const TcPlan& p, cudaStream_t st, cudaEvent_t* ev) {
     if (ev) cudaEventRecord(ev[0], st);
-    if (first) k_tc_rank<<<p.n_exec, 256, 0, st>>>(a, p.execs, p.topk_all);
+    k_tc_rank<<<p.n_exec, 256, 0, st>>>(a, p.execs, p.topk_all);
     if (ev) cudaEventRecord(ev[1], st);
-    GenArgs g;
+    k_tc_trial2<<<(p.n_rows + kTRows - 1) / kTRows, kTThreads, 0, st>>>(a, p.row_exec, p.n_rows, p.topk_all, p.uscr,
+                                                                       static_cast<uint8_t*>(p.aq), p.kp);
+    if (ev) cudaEventRecord(ev[2], st);
+    SelArgs g;
     g.a = a;
     g.tiles = p.tiles;
     g.n_tiles = p.n_tiles;
     g.row_exec = p.row_exec;
     g.brow = p.brow;
-    g.topk_all = p.topk_all;
     g.uscr = p.uscr;
-    g.fu = p.fu;
     g.kt = p.kp / kBK;
-    const size_t smem = gen_smem(g.kt);
-    cudaError_t e = cudaFuncSetAttribute(k_tc_gen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = sel_smem(g.kt);
+    cudaError_t e = cudaFuncSetAttribute(k_tc_sel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = p.n_tiles < p.gen_ctas ? p.n_tiles : p.gen_ctas;
-    k_tc_gen<<<grid, kGenThreads, smem, st>>>(p.mapB, g);
-    if (ev) cudaEventRecord(ev[2], st);
-    k_tc_commit<<<p.n_exec, 256, 0, st>>>(a, p.execs, p.topk_all, p.uscr, p.fu, last ? 0 : 1);
+    k_tc_sel<<<grid, kSelThreads, smem, st>>>(p.mapA, p.mapB, g);
     if (ev) cudaEventRecord(ev[3], st);
     return cudaGetLastError();
 }

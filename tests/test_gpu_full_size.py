@@ -129,6 +129,8 @@ def _full():
     M.metade_outer_step(b.ctx, b.opop, b.ofit, b.trial, b.theta, None, 0, 0)
     M.metade_init(b.ctx, b.pop, b.fit, 0)
     M.metade_autotune(b.ctx, b.pop, b.fit, b.theta, 3)
+    # the tuned width decides each executor's evaluation precision: initialise again under it
+    M.metade_init(b.ctx, b.pop, b.fit, 0)
     b.sync()
     return wl, b
 

@@ -351,9 +351,9 @@ def test_tc_min_dim_places_executors_and_autotune_picks_a_width():
 
 
 def test_tc_fused_generation_equals_the_pipeline():
-    """The fused generation kernel (k_tc_gen + k_tc_commit) against the
-    five-kernel pipeline (tc_unfused = 1) on the same state: the same trial
-    arithmetic, the same GEMM operands and epilogue, the same FP32 tie
+    """The three-kernel generation (k_tc_rank, k_tc_trial2, k_tc_sel) against
+    the five-kernel pipeline (tc_unfused = 1) on the same state: the same
+    trial arithmetic, the same GEMM operands and epilogue, the same FP32 tie
     rotations and difference forms, so populations and fitness must be
     bit-identical -- over three generations of random states (D 129..255,
     tiles across executors), and over a near-tie step (grid copies, then
@@ -364,7 +364,7 @@ def test_tc_fused_generation_equals_the_pipeline():
     outs = []
     for unfused in (0, 1):
         b = make_batch(wl, M.METADE_PATH_BATCHED, prec=1, tc_unfused=unfused)
-        assert json.loads(M.metade_plan_info(b.ctx))["tensor_core"]["kernel"] == ("k_rot_tc" if unfused else "k_tc_gen")
+        assert json.loads(M.metade_plan_info(b.ctx))["tensor_core"]["kernel"] == ("k_rot_tc" if unfused else "k_tc_sel")
         b.set_population(pops, fits)
         b.set_theta(wl.theta)
         M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 0, 3, b.best_f, b.best_i)
