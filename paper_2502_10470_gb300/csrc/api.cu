@@ -387,7 +387,7 @@ metade_status setup_tc(metade_ctx* c) {
     const size_t esz = fp8 ? 1 : 2;  // operand element bytes
     if (dalloc(&c->tc_execs, tc_execs.size()) || dalloc(&c->tc_row_exec, nrows) ||
         dalloc(&c->tc_tiles, tc_tiles.size()) || dalloc(&c->tc_brow, (size_t)c->n_prob) ||
-        dalloc(&c->tc_topk, (size_t)c->n_indiv) || dalloc(&c->tc_ties, nrows + 1) ||
+        dalloc(&c->tc_topk, (size_t)c->n_indiv) || dalloc(&c->tc_ties, nrows + 2) ||
         (!simt && (dalloc(&c->aq, nrows * tc_kp * esz) || dalloc(&c->bq, (size_t)tc_brows * tc_kp * esz))) ||
         (split && (dalloc(&c->aq_lo, nrows * tc_kp * esz) || dalloc(&c->bq_lo, (size_t)tc_brows * tc_kp * esz))) ||
         (fp8 && (dalloc(&c->ascale, nrows) || dalloc(&c->bscale, (size_t)c->n_prob) || dalloc(&c->amax, 1))))
@@ -430,8 +430,9 @@ metade_status setup_tc(metade_ctx* c) {
     t.bscale = c->bscale;
     t.fp8 = fp8 ? 1 : 0;
     t.simt = simt ? 1 : 0;
-    t.tie_list = c->tc_ties + 1;
+    t.tie_list = c->tc_ties + 2;
     t.tie_count = c->tc_ties;
+    t.next_tile = c->tc_ties + 1;
     t.tie_ctas = std::max(1, device_sms()) * 2;
     t.kp = tc_kp;
     t.split = split ? 1 : 0;

@@ -128,6 +128,7 @@ struct TcPlan {
     int tie_ctas;            // CTAs of the tie kernel
     int kp, split, max_dpad;
     int fused;               // 1: k_tc_rank + k_tc_trial2 + k_tc_sel per generation (BF16, kp <= 256)
+    int* next_tile;          // device counter of k_tc_sel's tile queue
     int gen_ctas;            // CTAs of k_tc_sel (one per SM)
     CUtensorMap mapA, mapB, mapAlo, mapBlo;
 };

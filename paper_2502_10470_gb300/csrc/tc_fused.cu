@@ -14,7 +14,8 @@
 //               the BF16 operand u - o, K-padded, to global memory.  Many small
 //               CTAs per SM keep many row gathers in flight;
 //   k_tc_sel    persistent, one CTA of 512 threads per SM, over the 128-row M
-//               tiles (rows of one problem, possibly of several executors):
+//               tiles (rows of one problem, possibly of several executors),
+//               handed out by an atomic counter:
 //               TMA loads of the A tile and, once per problem, of B (the
 //               problem's padded BF16 R rows, kept in shared memory while the
 //               CTA's tiles belong to that problem); thread 0 issues
@@ -250,6 +251,7 @@ struct SelArgs {
     StepArgs a;
     const int* tiles;         // [n_tiles][2]: first operand row, rows (all of one problem)
     int n_tiles;
+    int* next_tile;           // tiles handed out beyond the first gridDim.x (zeroed by k_tc_rank)
     const int* row_exec;      // operand row -> executor
     const long long* brow;    // per problem: first B row
     const float* uscr;        // trial rows (population layout)
@@ -261,7 +263,7 @@ __global__ void __launch_bounds__(kSelThreads, 1) k_tc_sel(const __grid_constant
     extern __shared__ uint8_t smraw[];
     __shared__ __align__(8) uint64_t afull, bfull, mma_done, drain;
     __shared__ uint32_t tmem_base;
-    __shared__ int abort_s, ntie_s, nacc_s;
+    __shared__ int abort_s, ntie_s, nacc_s, tile_s;
     __shared__ int tie_row[kRows], acc_row[kRows];
     __shared__ float tie_fx[kRows];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
@@ -295,7 +297,9 @@ __global__ void __launch_bounds__(kSelThreads, 1) k_tc_sel(const __grid_constant
     int cur_prob = -1;
     uint32_t aphase = 0, bphase = 0, mphase = 0;
     bool a_in_flight = false, b_in_flight = false;  // thread 0: loads not yet waited on
-    for (int t = blockIdx.x; t < g.n_tiles; t += gridDim.x) {
+    // tiles: blockIdx.x first, then from a shared counter (near ties make some tiles far costlier
+    // than others, so a static assignment leaves SMs idle behind the unlucky ones)
+    for (int t = blockIdx.x; t < g.n_tiles;) {
         const int arow = g.tiles[2 * t], nr = g.tiles[2 * t + 1];
         const InstDesc d = a.desc[g.row_exec[arow]];  // dim, objective and problem of every row of the tile
 
@@ -549,10 +553,12 @@ __global__ void __launch_bounds__(kSelThreads, 1) k_tc_sel(const __grid_constant
             }
         }
         if (abort_s) break;  // uniform: read after a barrier
+        if (tid == 0) tile_s = (int)gridDim.x + atomicAdd(g.next_tile, 1);
         // the next tile's loads overwrite A and TMEM only after this barrier
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
+        t = tile_s;
     }
     // leave with no copy or MMA of this CTA in flight (bounded waits)
     if (issuer) {
@@ -568,8 +574,10 @@ __global__ void __launch_bounds__(kSelThreads, 1) k_tc_sel(const __grid_constant
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kBN) : "memory");
 }
 
-// best and the pbest pool of every tensor-core executor (block per executor)
-__global__ void k_tc_rank(StepArgs a, const int* __restrict__ execs, int* topk_all) {
+// best and the pbest pool of every tensor-core executor (block per executor);
+// block 0 also zeroes the tile counter of the k_tc_sel launch that follows
+__global__ void k_tc_rank(StepArgs a, const int* __restrict__ execs, int* topk_all, int* next_tile) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *next_tile = 0;
     const int k = execs[blockIdx.x];
     const InstDesc d = a.desc[k];
     const Strat s = load_strat(a.theta + 6 * k, d.np);
@@ -588,7 +596,7 @@ bool tc_fused_fits(int kp) { return kp <= kMaxKt * kBK && sel_smem(kp / kBK) <= 
 
 cudaError_t launch_tc_fused_generation(const StepArgs& a, const TcPlan& p, cudaStream_t st, cudaEvent_t* ev) {
     if (ev) cudaEventRecord(ev[0], st);
-    k_tc_rank<<<p.n_exec, 256, 0, st>>>(a, p.execs, p.topk_all);
+    k_tc_rank<<<p.n_exec, 256, 0, st>>>(a, p.execs, p.topk_all, p.next_tile);
     if (ev) cudaEventRecord(ev[1], st);
     k_tc_trial2<<<(p.n_rows + kTRows - 1) / kTRows, kTThreads, 0, st>>>(a, p.row_exec, p.n_rows, p.topk_all, p.uscr,
                                                                        static_cast<uint8_t*>(p.aq), p.kp);
@@ -597,6 +605,7 @@ cudaError_t launch_tc_fused_generation(const StepArgs& a, const TcPlan& p, cudaS
     g.a = a;
     g.tiles = p.tiles;
     g.n_tiles = p.n_tiles;
+    g.next_tile = p.next_tile;
     g.row_exec = p.row_exec;
     g.brow = p.brow;
     g.uscr = p.uscr;
