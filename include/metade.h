@@ -120,11 +120,12 @@ typedef struct {
                                   metade_autotune choose between 129 and 256 by speed (129 until it
                                   runs); > 0 fixes it.  Ignored with FP32.  Negative: EINVAL */
     int32_t tc_unfused;        /* 0: BF16 tensor-core executors with D <= 256 (and FP32 difference-form
-                                  ties) run three kernels per generation: ranking, trial rows, and one
-                                  kernel for the tcgen05 GEMM with objective, selection, near ties and
-                                  the commit of accepted rows; 1: the five-kernel pipeline every other
-                                  tensor-core configuration uses (prologue, trial, GEMM, selection,
-                                  ties), with bit-identical results -- for comparison */
+                                  ties) run four kernels per generation: ranking, trial rows, one
+                                  kernel for the tcgen05 GEMM with objective, selection and the commit
+                                  of accepted rows, and one for the near ties, batched per problem;
+                                  1: the five-kernel pipeline every other tensor-core configuration
+                                  uses (prologue, trial, GEMM, selection, ties), with bit-identical
+                                  results -- for comparison */
 } metade_config;
 
 typedef struct metade_ctx metade_ctx;
@@ -322,9 +323,8 @@ METADE_API metade_status metade_plan_info(const metade_ctx *ctx, char *buf, size
  * kernel with R^T resident (D_pad <= 128), 6 MLP-objective generations, and
  * the other kernels of a tensor-core generation: 7 prologue (best, pbest
  * pool), 8 trial rows and GEMM operands, 9 selection, 10 near ties, 11 the
- * GEMM with objective, selection, near ties and commit of the BF16 D <= 256
- * path -- then clears them.  ms and count are host arrays of 12 (may be
- * NULL). */
+ * GEMM with objective, selection and commit of the BF16 D <= 256 path --
+ * then clears them.  ms and count are host arrays of 12 (may be NULL). */
 METADE_API metade_status metade_profile(metade_ctx *ctx, int32_t enable);
 METADE_API metade_status metade_profile_read(metade_ctx *ctx, double *ms, int64_t *count);
 

@@ -110,6 +110,7 @@ struct metade_ctx {
     long long* tc_brow = nullptr;
     int* tc_topk = nullptr;
     int* tc_ties = nullptr;
+    int* tc_tp = nullptr;  // problem -> path index, first rows, tie counts
     uint8_t *aq = nullptr, *aq_lo = nullptr, *bq = nullptr, *bq_lo = nullptr;  // BF16 pairs or e4m3 bytes
     float *ascale = nullptr, *bscale = nullptr;                                // FP8 dequantisation factors
     unsigned* amax = nullptr;                                                  // FP8: max|R| scratch
@@ -305,6 +306,8 @@ void free_tc(metade_ctx* c) {
     cudaFree(c->ascale);
     cudaFree(c->bscale);
     cudaFree(c->amax);
+    cudaFree(c->tc_tp);
+    c->tc_tp = nullptr;
     c->tc_execs = c->tc_row_exec = c->tc_tiles = c->tc_topk = c->tc_ties = nullptr;
     c->tc_brow = nullptr;
     c->aq = c->aq_lo = c->bq = c->bq_lo = nullptr;
@@ -335,6 +338,7 @@ metade_status setup_tc(metade_ctx* c) {
     const bool reduced = c->prec == METADE_BF16 || c->prec == METADE_BF16X3 || fp8;
     const int kalign = fp8 ? 128 : 64;  // K elements per 128-byte operand tile (unused by the FP32 GEMM)
     std::vector<int> tc_execs, tc_row_exec, tc_tiles;
+    std::vector<int> prob_tp(c->n_prob, -1), tp_row0;  // problems on the path, their first rows
     std::vector<long long> tc_brow(c->n_prob, -1);
     long long tc_brows = 0;
     int tc_kp = 0, tc_max_dpad = 0;
@@ -366,7 +370,11 @@ metade_status setup_tc(metade_ctx* c) {
                 tc_brows += (d.dim + 255) / 256 * 256;
             }
             // tensor cores: (first row, rows) tiles over the problem's rows, cut after its last executor
-            if (q == 0 || c->hdesc[tc_execs[q - 1]].prob != d.prob) prob_row0 = d.tc_row;
+            if (q == 0 || c->hdesc[tc_execs[q - 1]].prob != d.prob) {
+                prob_row0 = d.tc_row;
+                prob_tp[d.prob] = (int)tp_row0.size();
+                tp_row0.push_back(prob_row0);
+            }
             const bool last_of_prob = q + 1 == tc_execs.size() || c->hdesc[tc_execs[q + 1]].prob != d.prob;
             if (!simt && last_of_prob) {
                 const int r0 = prob_row0, r1 = (int)tc_row_exec.size();
@@ -390,8 +398,14 @@ metade_status setup_tc(metade_ctx* c) {
         dalloc(&c->tc_topk, (size_t)c->n_indiv) || dalloc(&c->tc_ties, nrows + 2) ||
         (!simt && (dalloc(&c->aq, nrows * tc_kp * esz) || dalloc(&c->bq, (size_t)tc_brows * tc_kp * esz))) ||
         (split && (dalloc(&c->aq_lo, nrows * tc_kp * esz) || dalloc(&c->bq_lo, (size_t)tc_brows * tc_kp * esz))) ||
-        (fp8 && (dalloc(&c->ascale, nrows) || dalloc(&c->bscale, (size_t)c->n_prob) || dalloc(&c->amax, 1))))
+        (fp8 && (dalloc(&c->ascale, nrows) || dalloc(&c->bscale, (size_t)c->n_prob) || dalloc(&c->amax, 1))) ||
+        dalloc(&c->tc_tp, (size_t)c->n_prob + 2 * tp_row0.size() + 1))
         return METADE_ENOMEM;
+    std::vector<int> tp_host(prob_tp);
+    tp_host.insert(tp_host.end(), tp_row0.begin(), tp_row0.end());
+    tp_host.resize((size_t)c->n_prob + 2 * tp_row0.size() + 1, 0);
+    if (cudaMemcpy(c->tc_tp, tp_host.data(), sizeof(int) * tp_host.size(), cudaMemcpyHostToDevice))
+        return METADE_ECUDA;
     if (cudaMemcpy(c->tc_execs, tc_execs.data(), sizeof(int) * tc_execs.size(), cudaMemcpyHostToDevice) ||
         cudaMemcpy(c->tc_row_exec, tc_row_exec.data(), sizeof(int) * nrows, cudaMemcpyHostToDevice) ||
         cudaMemcpy(c->tc_tiles, tc_tiles.data(), sizeof(int) * tc_tiles.size(), cudaMemcpyHostToDevice) ||
@@ -433,12 +447,18 @@ metade_status setup_tc(metade_ctx* c) {
     t.tie_list = c->tc_ties + 2;
     t.tie_count = c->tc_ties;
     t.next_tile = c->tc_ties + 1;
+    t.n_tp = (int)tp_row0.size();
+    t.prob_tp = c->tc_tp;
+    t.tp_row0 = c->tc_tp + c->n_prob;
+    t.tie_cnt = c->tc_tp + c->n_prob + t.n_tp;
+    t.chunk_ctr = c->tc_tp + c->n_prob + 2 * t.n_tp;
     t.tie_ctas = std::max(1, device_sms()) * 2;
     t.kp = tc_kp;
     t.split = split ? 1 : 0;
     t.max_dpad = tc_max_dpad;
     // BF16 with FP32 difference-form ties and operands of at most 256 elements:
-    // three kernels per generation, GEMM, selection, ties and commit in one
+    // four kernels per generation (ranking, trial rows, GEMM with selection and
+    // commit, near ties)
     t.fused = (c->prec == METADE_BF16 && !c->tie_fp64 && !c->tc_unfused && tc_fused_fits(tc_kp)) ? 1 : 0;
     t.gen_ctas = std::max(1, device_sms());
     // a tie keeps four rows of max_dpad in shared memory (FP64 with tie_fp64)
@@ -479,12 +499,12 @@ bool prof_pair(metade_ctx* c, cudaStream_t st, int kind, cudaEvent_t* a, cudaEve
 // Events between the kernels of one tensor-core generation (prologue, trial,
 // GEMM, selection, ties): ev[0..5], with a record per kernel and one for the
 // whole generation.
-// The three-kernel generation has four events: ranking, trial, selection.
+// The four-kernel generation has five events: ranking, trial, selection, ties.
 bool prof_tc(metade_ctx* c, cudaStream_t st, cudaEvent_t* ev, bool fused) {
     if (!c->prof_on) return false;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return false;
-    const int n = fused ? 4 : 6;
+    const int n = fused ? 5 : 6;
     for (int i = 0; i < n; ++i) {
         if (cudaEventCreate(&ev[i]) != cudaSuccess) {
             for (int j = 0; j < i; ++j) cudaEventDestroy(ev[j]);
@@ -493,7 +513,7 @@ bool prof_tc(metade_ctx* c, cudaStream_t st, cudaEvent_t* ev, bool fused) {
     }
     for (int i = 0; i < n; ++i) c->prof_events.push_back(ev[i]);
     const int kinds[5] = {kProfTcPrologue, kProfTcTrial, kProfTcGemm, kProfTcSelect, kProfTcTies};
-    const int fkinds[3] = {kProfTcPrologue, kProfTcTrial, kProfTcSel};
+    const int fkinds[4] = {kProfTcPrologue, kProfTcTrial, kProfTcSel, kProfTcTies};
     for (int i = 0; i < n - 1; ++i) c->prof.push_back(ProfRec{fused ? fkinds[i] : kinds[i], ev[i], ev[i + 1]});
     c->prof.push_back(ProfRec{kProfTcGeneration, ev[0], ev[n - 1]});
     return true;
@@ -546,7 +566,7 @@ metade_status run_inner(metade_ctx* c, cudaStream_t st, float* pop, float* fit, 
             const bool pe = prof_tc(c, st, ev, c->tcp.fused != 0);
             if (c->tcp.fused) {
                 CK(launch_tc_fused_generation(t, c->tcp, st, pe ? ev : nullptr));
-                *launches += 3;
+                *launches += 4;
                 continue;
             }
             CK(launch_tc_generation(t, c->tcp, st, pe ? ev : nullptr));

@@ -127,8 +127,13 @@ struct TcPlan {
     int* tie_count;          // device counter
     int tie_ctas;            // CTAs of the tie kernel
     int kp, split, max_dpad;
-    int fused;               // 1: k_tc_rank + k_tc_trial2 + k_tc_sel per generation (BF16, kp <= 256)
+    int fused;               // 1: k_tc_rank, k_tc_trial2, k_tc_sel, k_tc_ties2 per generation (BF16, kp <= 256)
     int* next_tile;          // device counter of k_tc_sel's tile queue
+    int n_tp;                // problems with executors on this path
+    const int* prob_tp;      // device [n_prob]: index among them (-1: none)
+    const int* tp_row0;      // device [n_tp]: first operand row of each (start of its tie list)
+    int* tie_cnt;            // device [n_tp]: near ties listed per problem
+    int* chunk_ctr;          // device counter of k_tc_ties2's chunk queue
     int gen_ctas;            // CTAs of k_tc_sel (one per SM)
     CUtensorMap mapA, mapB, mapAlo, mapBlo;
 };
@@ -145,11 +150,12 @@ cudaError_t launch_tc_eval(const InstDesc* desc, const TcPlan& p, const float* p
 size_t rot_simt_smem();
 cudaError_t launch_rot_simt(const InstDesc* desc, const int* tiles, int n_tiles, const float* rows, const float* shift,
                             const float* rotT, float* f_out, cudaStream_t st);
-// The three-kernel generation (tc_fused.cu): whether the shared memory of
+// The four-kernel generation (tc_fused.cu): whether the shared memory of
 // k_tc_sel holds operands of kp BF16 elements, and one generation of every
 // tensor-core executor -- k_tc_rank (pbest pools), k_tc_trial2 (trial and
-// operand rows), k_tc_sel (GEMM, objective, selection, near ties, commit).
-// ev (may be null): four events, before each launch and after the last.
+// operand rows), k_tc_sel (GEMM, objective, selection, commit), k_tc_ties2
+// (near ties).  ev (may be null): five events, before each launch and after
+// the last.
 bool tc_fused_fits(int kp);
 cudaError_t launch_tc_fused_generation(const StepArgs& a, const TcPlan& p, cudaStream_t st,
                                        cudaEvent_t* ev = nullptr);

@@ -1,5 +1,5 @@
 // tc_fused.cu -- one generation of the BF16 tensor-core executors (D <= 256)
-// in three kernels, for the executors whose rotation is a small dense GEMM.
+// in four kernels, for the executors whose rotation is a small dense GEMM.
 //
 //   k_tc_rank   block per executor: best and the pbest pool from the stored
 //               fitness (the generation-start ranking every trial uses);
@@ -8,8 +8,9 @@
 //               the warp's 32 lanes draw the exponential-crossover lengths of
 //               its four rows together (a lane per four coordinate uniforms,
 //               the first one at or above CR found by a ballot).  Then a lane
-//               per (row, 4-coordinate chunk), 8 rows x 4 consecutive chunks
-//               per warp step: mutation, crossover and clip (trial_chunk, the
+//               per (row, 4-coordinate chunk), the row's fields in registers,
+//               8 rows x 4 consecutive chunks per warp step: mutation,
+//               crossover and clip (trial_chunk, the
 //               arithmetic every trial kernel shares), the FP32 trial row and
 //               the BF16 operand u - o, K-padded, to global memory.  Many small
 //               CTAs per SM keep many row gathers in flight;
@@ -24,16 +25,19 @@
 //               columns of 32 rows, accumulate the objective and compose the
 //               quarters in column order; a thread per row then selects:
 //               clear acceptances are committed at once (rows copied by the
-//               whole CTA), near ties are listed and decided 16 at a time from
-//               z = R (x - o) and dz = R (u - x) in FP32 on the CUDA cores (R
-//               rows staged through shared memory by cp.async, float4 loads,
-//               every fma chain in ascending k like every other FP32
-//               rotation) and the FP32 difference form; a trial identical to
-//               its target is recognised from the staged u - x and accepted as
-//               it is.
-// Committing inside k_tc_sel keeps generational semantics: every trial row
-// of the generation was built by k_tc_trial2 before k_tc_sel starts, and
-// k_tc_sel reads a population row only for that row's own decision.
+//               whole CTA), near ties go to their problem's tie list;
+//   k_tc_ties2  the generation's near ties, 16 of one problem per chunk,
+//               chunks spread over every SM by an atomic counter: z = R (x -
+//               o) and dz = R (u - x) in FP32 on the CUDA cores (R rows staged
+//               through shared memory by cp.async, float4 loads, every fma
+//               chain in ascending k like every other FP32 rotation), the
+//               FP32 difference form, and the commit; a trial identical to its
+//               target is recognised from the staged u - x and accepted as it
+//               is.  (Ties cluster: an executor whose F is near 0 has a tie in
+//               almost every row, which one CTA per tile could not absorb.)
+// Committing inside k_tc_sel and k_tc_ties2 keeps generational semantics:
+// every trial row of the generation was built by k_tc_trial2 before they
+// start, and each reads a population row only for that row's own decision.
 // Results are bit-identical to the five-kernel pipeline of tc_rotate.cu.
 //
 // Every mbarrier wait is bounded; on timeout the kernel latches
@@ -187,46 +191,63 @@ __global__ void __launch_bounds__(kTThreads, 4) k_tc_trial2(StepArgs a, const in
     }
     __syncthreads();
 
-    // trial rows and operand rows: lane = (row 8 * unit + lane / 4, chunk 4 * unit' + lane % 4)
-    const int nchb = kp / 16;  // blocks of 4 chunks along K
-    const int units = (kTRows / 8) * nchb;
-    for (int u = warp; u < units; u += kTThreads / 32) {
-        const int r = 8 * (u / nchb) + (lane >> 2);
-        const int j4 = 4 * (4 * (u % nchb) + (lane & 3));
-        if (r0 + r >= n_rows) continue;
+    // trial rows and operand rows: warp w takes rows 8 (w % 4) + lane / 4 and the
+    // 16-element column blocks w / 4, w / 4 + 2, ...; lane % 4 picks the chunk of
+    // four elements, so four lanes cover 64 contiguous bytes of a row.  A lane
+    // keeps its row's fields in registers across its chunks.
+    const int r = 8 * (warp & 3) + (lane >> 2);
+    if (r0 + r >= n_rows) return;  // no barrier follows
+    const int nchb = kp / 16;      // blocks of 4 chunks along K
+    uint8_t* arow = aq + (size_t)(r0 + r) * kp * 2;
+    const int dpad = rec[F_DPAD * kTRows + r];
+    if (!rec[F_VALID * kTRows + r]) {  // rows of an invalid theta: a zero operand row
+        for (int cb = warp >> 2; cb < nchb; cb += 2)
+            *reinterpret_cast<uint2*>(arow + (size_t)(4 * (4 * cb + (lane & 3))) * 2) = make_uint2(0u, 0u);
+        return;
+    }
+    const long long po = (long long)(((unsigned long long)(uint32_t)rec[F_POPHI * kTRows + r] << 32) |
+                                     (uint32_t)rec[F_POPLO * kTRows + r]);
+    const float* X = a.pop + po;
+    const int pack = rec[F_PACK * kTRows + r];
+    Strat s;
+    s.F = __int_as_float(rec[F_F * kTRows + r]);
+    s.cri = (uint32_t)rec[F_CRI * kTRows + r];
+    s.cs = pack & 15;
+    s.dn = (pack >> 4) & 15;
+    s.bl = 0;
+    s.br = (pack >> 8) & 1;  // trial_chunk reads bl != br as "has a directional term"
+    const int i = rec[F_I * kTRows + r];
+    // parent rows as float offsets from X (an executor holds at most 1024 x 1536 floats)
+    const int ol = rec[F_IBL * kTRows + r] * dpad, orr = rec[F_IBR * kTRows + r] * dpad, oi = i * dpad;
+    int op[4], om[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        op[q] = rec[(F_P0 + q) * kTRows + r] * dpad;
+        om[q] = rec[(F_M0 + q) * kTRows + r] * dpad;
+    }
+    const int jr = rec[F_JR * kTRows + r], ns = rec[F_NS * kTRows + r], L = rec[F_L * kTRows + r];
+    const int dim = rec[F_DIM * kTRows + r];
+    const float* o = a.shift + rec[F_SHIFT * kTRows + r];
+    const float K = (float)(uint32_t)rec[F_K * kTRows + r] * (1.0f / 16777216.0f);
+    const Ctr c = make_ctr(a.key, (uint32_t)rec[F_STREAM * kTRows + r], a.gen0, (uint32_t)i, epoch);
+    float* U = uscr + po + oi;
+    for (int cb = warp >> 2; cb < nchb; cb += 2) {
+        const int j4 = 4 * (4 * cb + (lane & 3));
         float dd[4] = {0.f, 0.f, 0.f, 0.f};
-        const int dpad = rec[F_DPAD * kTRows + r];
-        if (rec[F_VALID * kTRows + r] && j4 < dpad) {
-            const long long po = (long long)(((unsigned long long)(uint32_t)rec[F_POPHI * kTRows + r] << 32) |
-                                             (uint32_t)rec[F_POPLO * kTRows + r]);
-            const float* X = a.pop + po;
-            const long long ld = dpad;
-            const int pack = rec[F_PACK * kTRows + r];
-            Strat s;
-            s.F = __int_as_float(rec[F_F * kTRows + r]);
-            s.cri = (uint32_t)rec[F_CRI * kTRows + r];
-            s.cs = pack & 15;
-            s.dn = (pack >> 4) & 15;
-            s.bl = 0;
-            s.br = (pack >> 8) & 1;  // trial_chunk reads bl != br as "has a directional term"
-            const int i = rec[F_I * kTRows + r];
+        if (j4 < dpad) {
             // the population is read-only here: non-coherent loads
-            const float4 av = __ldg(reinterpret_cast<const float4*>(X + rec[F_IBL * kTRows + r] * ld + j4));
-            const float4 bv = __ldg(reinterpret_cast<const float4*>(X + rec[F_IBR * kTRows + r] * ld + j4));
-            const float4 xv = __ldg(reinterpret_cast<const float4*>(X + (long long)i * ld + j4));
+            const float4 av = __ldg(reinterpret_cast<const float4*>(X + ol + j4));
+            const float4 bv = __ldg(reinterpret_cast<const float4*>(X + orr + j4));
+            const float4 xv = __ldg(reinterpret_cast<const float4*>(X + oi + j4));
             float4 p[4], m[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 if (q < s.dn) {
-                    p[q] = __ldg(reinterpret_cast<const float4*>(X + rec[(F_P0 + q) * kTRows + r] * ld + j4));
-                    m[q] = __ldg(reinterpret_cast<const float4*>(X + rec[(F_M0 + q) * kTRows + r] * ld + j4));
+                    p[q] = __ldg(reinterpret_cast<const float4*>(X + op[q] + j4));
+                    m[q] = __ldg(reinterpret_cast<const float4*>(X + om[q] + j4));
                 }
             }
-            uint4 w = make_uint4(0, 0, 0, 0);
-            if (s.cs == 1) {
-                const Ctr c = make_ctr(a.key, (uint32_t)rec[F_STREAM * kTRows + r], a.gen0, (uint32_t)i, epoch);
-                w = c.slot(4 + (uint32_t)(j4 >> 2));
-            }
+            const uint4 w = s.cs == 1 ? c.slot(4 + (uint32_t)(j4 >> 2)) : make_uint4(0, 0, 0, 0);
             float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -235,14 +256,11 @@ __global__ void __launch_bounds__(kTThreads, 4) k_tc_trial2(StepArgs a, const in
                     sum.z += p[q].z - m[q].z; sum.w += p[q].w - m[q].w;
                 }
             }
-            const float K = (float)(uint32_t)rec[F_K * kTRows + r] * (1.0f / 16777216.0f);
             float uo[4];
-            trial_chunk(s, K, rec[F_JR * kTRows + r], rec[F_NS * kTRows + r], rec[F_L * kTRows + r],
-                        rec[F_DIM * kTRows + r], j4, av, bv, xv, sum, w, a.shift + rec[F_SHIFT * kTRows + r], a.lo,
-                        a.hi, uo, dd);
-            *reinterpret_cast<float4*>(uscr + po + (long long)i * ld + j4) = make_float4(uo[0], uo[1], uo[2], uo[3]);
+            trial_chunk(s, K, jr, ns, L, dim, j4, av, bv, xv, sum, w, o, a.lo, a.hi, uo, dd);
+            *reinterpret_cast<float4*>(U + j4) = make_float4(uo[0], uo[1], uo[2], uo[3]);
         }
-        *reinterpret_cast<uint2*>(aq + ((size_t)(r0 + r) * kp + j4) * 2) = pack_bf16x4(dd);
+        *reinterpret_cast<uint2*>(arow + (size_t)j4 * 2) = pack_bf16x4(dd);
     }
 }
 
@@ -252,6 +270,10 @@ struct SelArgs {
     const int* tiles;         // [n_tiles][2]: first operand row, rows (all of one problem)
     int n_tiles;
     int* next_tile;           // tiles handed out beyond the first gridDim.x (zeroed by k_tc_rank)
+    const int* prob_tp;       // problem -> index among the problems on this path
+    const int* tp_row0;       // per such problem: its first operand row (start of its tie list)
+    int* tie_cnt;             // per such problem: near ties listed (zeroed by k_tc_rank)
+    int* tie_list;            // operand rows of the near ties, by problem
     const int* row_exec;      // operand row -> executor
     const long long* brow;    // per problem: first B row
     const float* uscr;        // trial rows (population layout)
@@ -263,14 +285,12 @@ __global__ void __launch_bounds__(kSelThreads, 1) k_tc_sel(const __grid_constant
     extern __shared__ uint8_t smraw[];
     __shared__ __align__(8) uint64_t afull, bfull, mma_done, drain;
     __shared__ uint32_t tmem_base;
-    __shared__ int abort_s, ntie_s, nacc_s, tile_s;
-    __shared__ int tie_row[kRows], acc_row[kRows];
-    __shared__ float tie_fx[kRows];
+    __shared__ int abort_s, nacc_s, tile_s;
+    __shared__ int acc_row[kRows];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
     uint8_t* As = sm;
     float* part = reinterpret_cast<float*>(sm + kASize);
     uint8_t* Bs = sm + kASize + kPartSize;
-    float* tv = reinterpret_cast<float*>(As);  // tie vectors: the A tile and the exchange area, once free
     const StepArgs& a = g.a;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool issuer = tid == 0;
@@ -383,10 +403,11 @@ __global__ void __launch_bounds__(kSelThreads, 1) k_tc_sel(const __grid_constant
             }
         }
         mphase ^= 1u;
-        if (tid == 0) ntie_s = nacc_s = 0;
+        if (tid == 0) nacc_s = 0;
         __syncthreads();
 
-        // 3. selection: the part-0 thread of each row; clear acceptances are listed for the row copy
+        // 3. selection: the part-0 thread of each row; clear acceptances are listed for the row copy,
+        // near ties go to the problem's tie list (k_tc_ties2)
         if (prt == 0 && row < nr && !abort_s) {
             for (int j = 0; j < kParts - 1; ++j) {
                 const float* sl = part + ((size_t)j * kRows + row) * 8;
@@ -406,9 +427,8 @@ __global__ void __launch_bounds__(kSelThreads, 1) k_tc_sel(const __grid_constant
                 const int fidx = e.fit_off + (arow + row - e.tc_row);
                 const float fx = a.fit[fidx];
                 if (near_tie(fn, fx, tie_band(d.dim))) {
-                    const int q = atomicAdd(&ntie_s, 1);
-                    tie_row[q] = row;
-                    tie_fx[q] = fx;
+                    const int tp = g.prob_tp[d.prob];
+                    g.tie_list[g.tp_row0[tp] + atomicAdd(&g.tie_cnt[tp], 1)] = arow + row;
                 } else if (fn <= fx) {
                     acc_row[atomicAdd(&nacc_s, 1)] = row;
                     a.fit[fidx] = fn;
@@ -428,130 +448,6 @@ __global__ void __launch_bounds__(kSelThreads, 1) k_tc_sel(const __grid_constant
             }
         }
 
-        // 4. near ties, kTieBatch at a time: z = R (x - o) and dz = R (u - x) in FP32
-        const int nt = abort_s ? 0 : ntie_s;
-        const float* o = a.shift + d.shift_off;
-        const float* Rr = a.rot + d.rot_off;  // R rows [dim][dpad]
-        float* vx = tv;                          // [kTieBatch][kVec] x - o, then z
-        float* vl = tv + kTieBatch * kVec;       // u - x, then dz
-        float* sR = tv + 2 * kTieBatch * kVec;   // [2][kVec][kRcs]: R columns c0 .. c0 + 15 of every row
-        const int nchunk = (d.dim + kRc - 1) / kRc;
-        for (int b0 = 0; b0 < nt; b0 += kTieBatch) {
-            const int nb = min(kTieBatch, nt - b0);
-            __syncthreads();  // the previous user of the buffers (row copy or last batch) is done
-            auto stage = [&](int ch) {  // R[r][ch * 16 ..] for every row r < dim into buffer ch & 1
-                float* dst = sR + (size_t)(ch & 1) * kVec * kRcs;
-                const int c0 = ch * kRc;
-                for (int e2 = tid; e2 < d.dim * (kRc / 4); e2 += kSelThreads) {
-                    const int rr = e2 >> 2, c = c0 + 4 * (e2 & 3);
-                    const bool in = c < d.dpad;
-                    cp_async16z(dst + rr * kRcs + 4 * (e2 & 3), Rr + (size_t)rr * d.dpad + (in ? c : 0), in ? 16 : 0);
-                }
-                asm volatile("cp.async.commit_group;" ::: "memory");
-            };
-            stage(0);
-            for (int e2 = tid; e2 < nb * kVec; e2 += kSelThreads) {
-                const int q = e2 / kVec, c = e2 - q * kVec;
-                if (c < d.dpad) {
-                    const int gr = arow + tie_row[b0 + q];
-                    const InstDesc e = a.desc[g.row_exec[gr]];
-                    const long long off = e.pop_off + (long long)(gr - e.tc_row) * d.dpad;
-                    const float xc = a.pop[off + c];
-                    vx[q * kVec + c] = c < d.dim ? xc - o[c] : 0.f;
-                    vl[q * kVec + c] = g.uscr[off + c] - xc;
-                }
-            }
-            // thread (row r, half h): ties h, h + 2, h + 4, ... of the batch
-            const int r = tid & (kVec - 1), h = tid >> 8;
-            float az[kTieBatch / 2], adz[kTieBatch / 2];
-#pragma unroll
-            for (int q = 0; q < kTieBatch / 2; ++q) az[q] = adz[q] = 0.f;
-            const int mine = (nb - h + 1) >> 1;  // ties of this half (warp-uniform)
-            for (int ch = 0; ch < nchunk; ++ch) {
-                if (ch + 1 < nchunk) {
-                    stage(ch + 1);
-                    asm volatile("cp.async.wait_group 1;" ::: "memory");
-                } else {
-                    asm volatile("cp.async.wait_group 0;" ::: "memory");
-                }
-                __syncthreads();
-                if (r < d.dim) {
-                    const float* rc = sR + (size_t)(ch & 1) * kVec * kRcs + r * kRcs;
-                    const int c0 = ch * kRc;
-                    const int cend = min(kRc, d.dim - c0);
-                    if (cend == kRc) {  // four float4 steps, k ascending within each
-#pragma unroll
-                        for (int c4 = 0; c4 < kRc / 4; ++c4) {
-                            const float4 rt = *reinterpret_cast<const float4*>(rc + 4 * c4);
-#pragma unroll
-                            for (int j = 0; j < kTieBatch / 2; ++j) {
-                                if (j < mine) {
-                                    const int q = h + 2 * j;
-                                    const float4 x4 = *reinterpret_cast<const float4*>(vx + q * kVec + c0 + 4 * c4);
-                                    const float4 l4 = *reinterpret_cast<const float4*>(vl + q * kVec + c0 + 4 * c4);
-                                    az[j] = fmaf(rt.x, x4.x, az[j]);
-                                    az[j] = fmaf(rt.y, x4.y, az[j]);
-                                    az[j] = fmaf(rt.z, x4.z, az[j]);
-                                    az[j] = fmaf(rt.w, x4.w, az[j]);
-                                    adz[j] = fmaf(rt.x, l4.x, adz[j]);
-                                    adz[j] = fmaf(rt.y, l4.y, adz[j]);
-                                    adz[j] = fmaf(rt.z, l4.z, adz[j]);
-                                    adz[j] = fmaf(rt.w, l4.w, adz[j]);
-                                }
-                            }
-                        }
-                    } else {  // the last, partial chunk: one column at a time
-                        for (int cc = 0; cc < cend; ++cc) {
-                            const float rt = rc[cc];
-#pragma unroll
-                            for (int j = 0; j < kTieBatch / 2; ++j) {
-                                if (j < mine) {
-                                    const int q = h + 2 * j;
-                                    az[j] = fmaf(rt, vx[q * kVec + c0 + cc], az[j]);
-                                    adz[j] = fmaf(rt, vl[q * kVec + c0 + cc], adz[j]);
-                                }
-                            }
-                        }
-                    }
-                }
-                __syncthreads();  // the buffer is refilled two chunks later
-            }
-            if (r < d.dim) {  // every thread has read vx / vl: z and dz replace them
-#pragma unroll
-                for (int j = 0; j < kTieBatch / 2; ++j) {
-                    if (j < mine) {
-                        vx[(h + 2 * j) * kVec + r] = az[j];
-                        vl[(h + 2 * j) * kVec + r] = adz[j];
-                    }
-                }
-            }
-            __syncthreads();
-            if (warp < nb) {  // warp per tie: decide and commit
-                const int gr = arow + tie_row[b0 + warp];
-                const InstDesc e = a.desc[g.row_exec[gr]];
-                const int i = gr - e.tc_row;
-                const long long off = e.pop_off + (long long)i * d.dpad;
-                bool diff = false;
-                for (int c = lane; c < d.dpad; c += 32) diff = diff || (g.uscr[off + c] != a.pop[off + c]);
-                const float fx = tie_fx[b0 + warp];
-                bool take;
-                float fn;
-                if (!__any_sync(kFull, diff)) {  // a trial identical to its target: accepted as it is
-                    take = true;
-                    fn = fx;
-                } else {
-                    const float df = warp_diff(d.obj, d.dim, vx + warp * kVec, vl + warp * kVec);
-                    take = df <= 0.0f;
-                    fn = fx + df;
-                }
-                if (take) {
-                    for (int c = 4 * lane; c < d.dpad; c += 128)
-                        *reinterpret_cast<float4*>(a.pop + off + c) =
-                            __ldg(reinterpret_cast<const float4*>(g.uscr + off + c));
-                    if (lane == 0) a.fit[e.fit_off + i] = fn;
-                }
-            }
-        }
         if (abort_s) break;  // uniform: read after a barrier
         if (tid == 0) tile_s = (int)gridDim.x + atomicAdd(g.next_tile, 1);
         // the next tile's loads overwrite A and TMEM only after this barrier
@@ -574,10 +470,183 @@ __global__ void __launch_bounds__(kSelThreads, 1) k_tc_sel(const __grid_constant
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kBN) : "memory");
 }
 
+// -------------------------------------------------------------- k_tc_ties2
+struct TieArgs {
+    StepArgs a;
+    const int* row_exec;      // operand row -> executor
+    int n_tp;                 // problems on this path
+    const int* tp_row0;       // per problem: its first operand row (start of its tie list)
+    const int* tie_cnt;       // per problem: near ties listed by k_tc_sel
+    const int* tie_list;      // operand rows of the near ties, by problem
+    int* chunk_ctr;           // chunks handed out (zeroed by k_tc_rank)
+    const float* uscr;        // trial rows (population layout)
+};
+
+// The near ties of the generation, kTieBatch ties of one problem per chunk,
+// chunks handed out by an atomic counter over every CTA of the GPU: z = R (x
+// - o) and dz = R (u - x) in FP32, R rows staged through shared memory 16
+// columns at a time by cp.async (double buffered), a thread per (row of z,
+// half of the chunk's ties) with float4 loads along k, every fma chain in
+// ascending k; then a warp per tie forms the FP32 difference form f(u) -
+// f(x), decides and commits.  A trial identical to its target (u - x == 0
+// everywhere, pad included) is accepted as it is.
+__global__ void __launch_bounds__(kSelThreads, 2) k_tc_ties2(TieArgs g) {
+    extern __shared__ uint8_t smraw[];
+    __shared__ int tp_s, j0_s;
+    float* tv = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smraw) + 15) & ~(uintptr_t)15);
+    const StepArgs& a = g.a;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    float* vx = tv;                          // [kTieBatch][kVec] x - o, then z
+    float* vl = tv + kTieBatch * kVec;       // u - x, then dz
+    float* sR = tv + 2 * kTieBatch * kVec;   // [2][kVec][kRcs]: R columns c0 .. c0 + 15 of every row
+    for (;;) {
+        if (tid == 0) {  // chunk c -> (problem, first tie), problems in order
+            const int c = atomicAdd(g.chunk_ctr, 1);
+            int acc = 0, tp = -1, j0 = 0;
+            for (int q = 0; q < g.n_tp; ++q) {
+                const int n = (g.tie_cnt[q] + kTieBatch - 1) / kTieBatch;
+                if (c < acc + n) {
+                    tp = q;
+                    j0 = (c - acc) * kTieBatch;
+                    break;
+                }
+                acc += n;
+            }
+            tp_s = tp;
+            j0_s = j0;
+        }
+        __syncthreads();
+        const int tp = tp_s, j0 = j0_s;
+        if (tp < 0) break;
+        const int nb = min(kTieBatch, g.tie_cnt[tp] - j0);
+        const int* rows = g.tie_list + g.tp_row0[tp] + j0;
+        const InstDesc d = a.desc[g.row_exec[rows[0]]];  // dim, objective and problem of every tie of the chunk
+        const float* o = a.shift + d.shift_off;
+        const float* Rr = a.rot + d.rot_off;  // R rows [dim][dpad]
+        const int nchunk = (d.dim + kRc - 1) / kRc;
+        auto stage = [&](int ch) {  // R[r][ch * 16 ..] for every row r < dim into buffer ch & 1
+            float* dst = sR + (size_t)(ch & 1) * kVec * kRcs;
+            const int c0 = ch * kRc;
+            for (int e2 = tid; e2 < d.dim * (kRc / 4); e2 += kSelThreads) {
+                const int rr = e2 >> 2, c = c0 + 4 * (e2 & 3);
+                const bool in = c < d.dpad;
+                cp_async16z(dst + rr * kRcs + 4 * (e2 & 3), Rr + (size_t)rr * d.dpad + (in ? c : 0), in ? 16 : 0);
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        stage(0);
+        for (int e2 = tid; e2 < nb * kVec; e2 += kSelThreads) {
+            const int q = e2 / kVec, c = e2 - q * kVec;
+            if (c < d.dpad) {
+                const int gr = rows[q];
+                const InstDesc e = a.desc[g.row_exec[gr]];
+                const long long off = e.pop_off + (long long)(gr - e.tc_row) * d.dpad;
+                const float xc = a.pop[off + c];
+                vx[q * kVec + c] = c < d.dim ? xc - o[c] : 0.f;
+                vl[q * kVec + c] = g.uscr[off + c] - xc;
+            }
+        }
+        // thread (row r, half h): ties h, h + 2, h + 4, ... of the chunk
+        const int r = tid & (kVec - 1), h = tid >> 8;
+        float az[kTieBatch / 2], adz[kTieBatch / 2];
+#pragma unroll
+        for (int q = 0; q < kTieBatch / 2; ++q) az[q] = adz[q] = 0.f;
+        const int mine = (nb - h + 1) >> 1;  // ties of this half (warp-uniform)
+        for (int ch = 0; ch < nchunk; ++ch) {
+            if (ch + 1 < nchunk) {
+                stage(ch + 1);
+                asm volatile("cp.async.wait_group 1;" ::: "memory");
+            } else {
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
+            }
+            __syncthreads();
+            if (r < d.dim) {
+                const float* rc = sR + (size_t)(ch & 1) * kVec * kRcs + r * kRcs;
+                const int c0 = ch * kRc;
+                const int cend = min(kRc, d.dim - c0);
+                if (cend == kRc) {  // four float4 steps, k ascending within each
+#pragma unroll
+                    for (int c4 = 0; c4 < kRc / 4; ++c4) {
+                        const float4 rt = *reinterpret_cast<const float4*>(rc + 4 * c4);
+#pragma unroll
+                        for (int j = 0; j < kTieBatch / 2; ++j) {
+                            if (j < mine) {
+                                const int q = h + 2 * j;
+                                const float4 x4 = *reinterpret_cast<const float4*>(vx + q * kVec + c0 + 4 * c4);
+                                const float4 l4 = *reinterpret_cast<const float4*>(vl + q * kVec + c0 + 4 * c4);
+                                az[j] = fmaf(rt.x, x4.x, az[j]);
+                                az[j] = fmaf(rt.y, x4.y, az[j]);
+                                az[j] = fmaf(rt.z, x4.z, az[j]);
+                                az[j] = fmaf(rt.w, x4.w, az[j]);
+                                adz[j] = fmaf(rt.x, l4.x, adz[j]);
+                                adz[j] = fmaf(rt.y, l4.y, adz[j]);
+                                adz[j] = fmaf(rt.z, l4.z, adz[j]);
+                                adz[j] = fmaf(rt.w, l4.w, adz[j]);
+                            }
+                        }
+                    }
+                } else {  // the last, partial chunk: one column at a time
+                    for (int cc = 0; cc < cend; ++cc) {
+                        const float rt = rc[cc];
+#pragma unroll
+                        for (int j = 0; j < kTieBatch / 2; ++j) {
+                            if (j < mine) {
+                                const int q = h + 2 * j;
+                                az[j] = fmaf(rt, vx[q * kVec + c0 + cc], az[j]);
+                                adz[j] = fmaf(rt, vl[q * kVec + c0 + cc], adz[j]);
+                            }
+                        }
+                    }
+                }
+            }
+            __syncthreads();  // the buffer is refilled two chunks later
+        }
+        if (r < d.dim) {  // every thread has read vx / vl: z and dz replace them
+#pragma unroll
+            for (int j = 0; j < kTieBatch / 2; ++j) {
+                if (j < mine) {
+                    vx[(h + 2 * j) * kVec + r] = az[j];
+                    vl[(h + 2 * j) * kVec + r] = adz[j];
+                }
+            }
+        }
+        __syncthreads();
+        if (warp < nb) {  // warp per tie: decide and commit
+            const int gr = rows[warp];
+            const InstDesc e = a.desc[g.row_exec[gr]];
+            const int i = gr - e.tc_row;
+            const long long off = e.pop_off + (long long)i * d.dpad;
+            bool diff = false;
+            for (int c = lane; c < d.dpad; c += 32) diff = diff || (g.uscr[off + c] != a.pop[off + c]);
+            const float fx = a.fit[e.fit_off + i];
+            bool take;
+            float fn;
+            if (!__any_sync(kFull, diff)) {  // a trial identical to its target: accepted as it is
+                take = true;
+                fn = fx;
+            } else {
+                const float df = warp_diff(d.obj, d.dim, vx + warp * kVec, vl + warp * kVec);
+                take = df <= 0.0f;
+                fn = fx + df;
+            }
+            if (take) {
+                for (int c = 4 * lane; c < d.dpad; c += 128)
+                    *reinterpret_cast<float4*>(a.pop + off + c) = *reinterpret_cast<const float4*>(g.uscr + off + c);
+                if (lane == 0) a.fit[e.fit_off + i] = fn;
+            }
+        }
+        __syncthreads();  // the buffers and the chunk record are reused
+    }
+}
+
 // best and the pbest pool of every tensor-core executor (block per executor);
 // block 0 also zeroes the tile counter of the k_tc_sel launch that follows
-__global__ void k_tc_rank(StepArgs a, const int* __restrict__ execs, int* topk_all, int* next_tile) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) *next_tile = 0;
+__global__ void k_tc_rank(StepArgs a, const int* __restrict__ execs, int* topk_all, int* next_tile, int* chunk_ctr,
+                          int* tie_cnt, int n_tp) {
+    if (blockIdx.x == 0) {  // the queues of k_tc_sel and k_tc_ties2 of this generation
+        if (threadIdx.x == 0) *next_tile = *chunk_ctr = 0;
+        for (int q = threadIdx.x; q < n_tp; q += blockDim.x) tie_cnt[q] = 0;
+    }
     const int k = execs[blockIdx.x];
     const InstDesc d = a.desc[k];
     const Strat s = load_strat(a.theta + 6 * k, d.np);
@@ -589,6 +658,7 @@ __global__ void k_tc_rank(StepArgs a, const int* __restrict__ execs, int* topk_a
 }
 
 size_t sel_smem(int kt) { return 1024 + kASize + kPartSize + (size_t)kt * kBT; }
+constexpr size_t kTieSmem = 16 + kTieSize;
 
 }  // namespace
 
@@ -596,7 +666,7 @@ bool tc_fused_fits(int kp) { return kp <= kMaxKt * kBK && sel_smem(kp / kBK) <= 
 
 cudaError_t launch_tc_fused_generation(const StepArgs& a, const TcPlan& p, cudaStream_t st, cudaEvent_t* ev) {
     if (ev) cudaEventRecord(ev[0], st);
-    k_tc_rank<<<p.n_exec, 256, 0, st>>>(a, p.execs, p.topk_all, p.next_tile);
+    k_tc_rank<<<p.n_exec, 256, 0, st>>>(a, p.execs, p.topk_all, p.next_tile, p.chunk_ctr, p.tie_cnt, p.n_tp);
     if (ev) cudaEventRecord(ev[1], st);
     k_tc_trial2<<<(p.n_rows + kTRows - 1) / kTRows, kTThreads, 0, st>>>(a, p.row_exec, p.n_rows, p.topk_all, p.uscr,
                                                                        static_cast<uint8_t*>(p.aq), p.kp);
@@ -606,6 +676,10 @@ cudaError_t launch_tc_fused_generation(const StepArgs& a, const TcPlan& p, cudaS
     g.tiles = p.tiles;
     g.n_tiles = p.n_tiles;
     g.next_tile = p.next_tile;
+    g.prob_tp = p.prob_tp;
+    g.tp_row0 = p.tp_row0;
+    g.tie_cnt = p.tie_cnt;
+    g.tie_list = p.tie_list;
     g.row_exec = p.row_exec;
     g.brow = p.brow;
     g.uscr = p.uscr;
@@ -616,6 +690,19 @@ cudaError_t launch_tc_fused_generation(const StepArgs& a, const TcPlan& p, cudaS
     const int grid = p.n_tiles < p.gen_ctas ? p.n_tiles : p.gen_ctas;
     k_tc_sel<<<grid, kSelThreads, smem, st>>>(p.mapA, p.mapB, g);
     if (ev) cudaEventRecord(ev[3], st);
+    TieArgs ta;
+    ta.a = a;
+    ta.row_exec = p.row_exec;
+    ta.n_tp = p.n_tp;
+    ta.tp_row0 = p.tp_row0;
+    ta.tie_cnt = p.tie_cnt;
+    ta.tie_list = p.tie_list;
+    ta.chunk_ctr = p.chunk_ctr;
+    ta.uscr = p.uscr;
+    e = cudaFuncSetAttribute(k_tc_ties2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTieSmem);
+    if (e != cudaSuccess) return e;
+    k_tc_ties2<<<2 * p.gen_ctas, kSelThreads, kTieSmem, st>>>(ta);
+    if (ev) cudaEventRecord(ev[4], st);
     return cudaGetLastError();
 }
 
