@@ -1092,6 +1092,14 @@ metade_status metade_autotune(metade_ctx* c, const float* pop, const float* fit,
             if (st == METADE_OK) st = build_plan(c);
             if (st != METADE_OK) break;
             int64_t nl = 0;
+            // one untimed generation first: the first launch of a kernel also loads it
+            if (cudaMemcpyAsync(tpop, pop, sizeof(float) * (size_t)c->pop_floats, cudaMemcpyDeviceToDevice, c->st) ||
+                cudaMemcpyAsync(tfit, fit, sizeof(float) * (size_t)c->n_indiv, cudaMemcpyDeviceToDevice, c->st)) {
+                st = METADE_ECUDA;
+                break;
+            }
+            st = run_inner(c, c->st, tpop, tfit, theta, 0, nullptr, 0, 1, nullptr, nullptr, &nl);
+            if (st != METADE_OK) break;
             if (cudaMemcpyAsync(tpop, pop, sizeof(float) * (size_t)c->pop_floats, cudaMemcpyDeviceToDevice, c->st) ||
                 cudaMemcpyAsync(tfit, fit, sizeof(float) * (size_t)c->n_indiv, cudaMemcpyDeviceToDevice, c->st) ||
                 cudaEventRecord(e0, c->st)) {

@@ -4,10 +4,10 @@
 //   k_tc_rank   block per executor: best and the pbest pool from the stored
 //               fitness (the generation-start ranking every trial uses);
 //   k_tc_trial2 a CTA of 256 threads per 32 operand rows.  Draws first:
-//               lanes 0..3 of each warp run a row's Philox index draws, then
-//               the warp's 32 lanes draw the exponential-crossover lengths of
-//               its four rows together (a lane per four coordinate uniforms,
-//               the first one at or above CR found by a ballot).  Then a lane
+//               warp 0 runs the Philox index draws, a lane per row, then each
+//               warp draws the exponential-crossover lengths of four rows with
+//               its 32 lanes (a lane per four coordinate uniforms, the first
+//               one at or above CR found by a ballot).  Then a lane
 //               per (row, 4-coordinate chunk), the row's fields in registers,
 //               8 rows x 4 consecutive chunks per warp step: mutation,
 //               crossover and clip (trial_chunk, the
@@ -97,11 +97,10 @@ __global__ void __launch_bounds__(kTThreads, 4) k_tc_trial2(StepArgs a, const in
     const int r0 = blockIdx.x * kTRows;
     const uint32_t epoch = a.epoch_dev ? *a.epoch_dev : a.epoch;
 
-    // draws: warp w takes rows 4 w .. 4 w + 3
-    {
-        const int r = 4 * warp + (lane & 3);
-        int cs2 = 0;
-        if (lane < 4) {
+    // draws: warp 0, a lane per row; then the exponential lengths, warp w for rows 4 w .. 4 w + 3
+    if (warp == 0) {
+        const int r = lane;
+        {
             int valid = 0;
             if (r0 + r < n_rows) {
                 const int k = row_exec[r0 + r];
@@ -110,7 +109,6 @@ __global__ void __launch_bounds__(kTThreads, 4) k_tc_trial2(StepArgs a, const in
                 const Strat s = load_strat(a.theta + 6 * k, e.np);
                 if (s.ok) {
                     valid = 1;
-                    cs2 = s.cs == 2;
                     const int* topk = topk_all + e.fit_off;
                     const Ctr c = make_ctr(a.key, (uint32_t)e.stream, a.gen0, (uint32_t)i, epoch);
                     Indiv v;
@@ -140,10 +138,14 @@ __global__ void __launch_bounds__(kTThreads, 4) k_tc_trial2(StepArgs a, const in
             }
             rec[F_VALID * kTRows + r] = valid;
         }
+    }
+    __syncthreads();
+    {
         // exponential length L = 1 + min(t*, D - 1), t* the first coordinate
         // uniform U_t (slot 4 + t / 4, word t % 4) not below CR
-        const unsigned exp_rows = __ballot_sync(kFull, cs2 != 0) & 0xFu;
-        __syncwarp();
+        const int r = 4 * warp + (lane & 3);
+        const bool cs2 = lane < 4 && rec[F_VALID * kTRows + r] && (rec[F_PACK * kTRows + r] & 15) == 2;
+        const unsigned exp_rows = __ballot_sync(kFull, cs2) & 0xFu;
         if (exp_rows) {
             int dmax = 0;  // the widest exponential row of the warp bounds the rounds
 #pragma unroll
@@ -493,6 +495,8 @@ struct TieArgs {
 __global__ void __launch_bounds__(kSelThreads, 2) k_tc_ties2(TieArgs g) {
     extern __shared__ uint8_t smraw[];
     __shared__ int tp_s, j0_s;
+    __shared__ long long toff_s[kTieBatch];
+    __shared__ int tfid_s[kTieBatch];
     float* tv = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smraw) + 15) & ~(uintptr_t)15);
     const StepArgs& a = g.a;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -520,6 +524,13 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_tc_ties2(TieArgs g) {
         if (tp < 0) break;
         const int nb = min(kTieBatch, g.tie_cnt[tp] - j0);
         const int* rows = g.tie_list + g.tp_row0[tp] + j0;
+        if (tid < nb) {  // each tie's row offset in the population and fitness index
+            const int gr = rows[tid];
+            const InstDesc e = a.desc[g.row_exec[gr]];
+            const int i = gr - e.tc_row;
+            toff_s[tid] = e.pop_off + (long long)i * e.dpad;
+            tfid_s[tid] = e.fit_off + i;
+        }
         const InstDesc d = a.desc[g.row_exec[rows[0]]];  // dim, objective and problem of every tie of the chunk
         const float* o = a.shift + d.shift_off;
         const float* Rr = a.rot + d.rot_off;  // R rows [dim][dpad]
@@ -535,12 +546,11 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_tc_ties2(TieArgs g) {
             asm volatile("cp.async.commit_group;" ::: "memory");
         };
         stage(0);
+        __syncthreads();  // toff_s
         for (int e2 = tid; e2 < nb * kVec; e2 += kSelThreads) {
             const int q = e2 / kVec, c = e2 - q * kVec;
             if (c < d.dpad) {
-                const int gr = rows[q];
-                const InstDesc e = a.desc[g.row_exec[gr]];
-                const long long off = e.pop_off + (long long)(gr - e.tc_row) * d.dpad;
+                const long long off = toff_s[q];
                 const float xc = a.pop[off + c];
                 vx[q * kVec + c] = c < d.dim ? xc - o[c] : 0.f;
                 vl[q * kVec + c] = g.uscr[off + c] - xc;
@@ -612,13 +622,11 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_tc_ties2(TieArgs g) {
         }
         __syncthreads();
         if (warp < nb) {  // warp per tie: decide and commit
-            const int gr = rows[warp];
-            const InstDesc e = a.desc[g.row_exec[gr]];
-            const int i = gr - e.tc_row;
-            const long long off = e.pop_off + (long long)i * d.dpad;
+            const long long off = toff_s[warp];
+            const int fidx = tfid_s[warp];
             bool diff = false;
             for (int c = lane; c < d.dpad; c += 32) diff = diff || (g.uscr[off + c] != a.pop[off + c]);
-            const float fx = a.fit[e.fit_off + i];
+            const float fx = a.fit[fidx];
             bool take;
             float fn;
             if (!__any_sync(kFull, diff)) {  // a trial identical to its target: accepted as it is
@@ -632,7 +640,7 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_tc_ties2(TieArgs g) {
             if (take) {
                 for (int c = 4 * lane; c < d.dpad; c += 128)
                     *reinterpret_cast<float4*>(a.pop + off + c) = *reinterpret_cast<const float4*>(g.uscr + off + c);
-                if (lane == 0) a.fit[e.fit_off + i] = fn;
+                if (lane == 0) a.fit[fidx] = fn;
             }
         }
         __syncthreads();  // the buffers and the chunk record are reused
