@@ -14,9 +14,9 @@
 //               arithmetic every trial kernel shares), the FP32 trial row and
 //               the BF16 operand u - o, K-padded, to global memory.  Many small
 //               CTAs per SM keep many row gathers in flight;
-//   k_tc_sel    persistent, one CTA of 512 threads per SM, over the 128-row M
-//               tiles (rows of one problem, possibly of several executors),
-//               handed out by an atomic counter:
+//   k_tc_sel    persistent, one CTA of 512 threads per SM, over a contiguous
+//               block of the 128-row M tiles (rows of one problem, possibly of
+//               several executors):
 //               TMA loads of the A tile and, once per problem, of B (the
 //               problem's padded BF16 R rows, kept in shared memory while the
 //               CTA's tiles belong to that problem); thread 0 issues
@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(kSelThreads, 1) k_tc_sel(const __grid_constant
     extern __shared__ uint8_t smraw[];
     __shared__ __align__(8) uint64_t afull, bfull, mma_done, drain;
     __shared__ uint32_t tmem_base;
-    __shared__ int abort_s, nacc_s, tile_s;
+    __shared__ int abort_s, nacc_s;
     __shared__ int acc_row[kRows];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
     uint8_t* As = sm;
@@ -319,9 +319,11 @@ __global__ void __launch_bounds__(kSelThreads, 1) k_tc_sel(const __grid_constant
     int cur_prob = -1;
     uint32_t aphase = 0, bphase = 0, mphase = 0;
     bool a_in_flight = false, b_in_flight = false;  // thread 0: loads not yet waited on
-    // tiles: blockIdx.x first, then from a shared counter (near ties make some tiles far costlier
-    // than others, so a static assignment leaves SMs idle behind the unlucky ones)
-    for (int t = blockIdx.x; t < g.n_tiles;) {
+    // a contiguous block of tiles per CTA: tiles of one problem are adjacent, so B is loaded
+    // about once per problem (every tile costs about the same: near ties are decided elsewhere)
+    const int t_begin = (int)(((long long)g.n_tiles * blockIdx.x) / gridDim.x);
+    const int t_end = (int)(((long long)g.n_tiles * (blockIdx.x + 1)) / gridDim.x);
+    for (int t = t_begin; t < t_end; ++t) {
         const int arow = g.tiles[2 * t], nr = g.tiles[2 * t + 1];
         const InstDesc d = a.desc[g.row_exec[arow]];  // dim, objective and problem of every row of the tile
 
@@ -451,12 +453,10 @@ __global__ void __launch_bounds__(kSelThreads, 1) k_tc_sel(const __grid_constant
         }
 
         if (abort_s) break;  // uniform: read after a barrier
-        if (tid == 0) tile_s = (int)gridDim.x + atomicAdd(g.next_tile, 1);
         // the next tile's loads overwrite A and TMEM only after this barrier
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
-        t = tile_s;
     }
     // leave with no copy or MMA of this CTA in flight (bounded waits)
     if (issuer) {
@@ -624,8 +624,8 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_tc_ties2(TieArgs g) {
         if (warp < nb) {  // warp per tie: decide and commit
             const long long off = toff_s[warp];
             const int fidx = tfid_s[warp];
-            bool diff = false;
-            for (int c = lane; c < d.dpad; c += 32) diff = diff || (g.uscr[off + c] != a.pop[off + c]);
+            bool diff = false;  // every load issued: no short circuit
+            for (int c = lane; c < d.dpad; c += 32) diff |= g.uscr[off + c] != a.pop[off + c];
             const float fx = a.fit[fidx];
             bool take;
             float fn;
