@@ -117,7 +117,7 @@ typedef struct {
                                   2 = CSO (n_out <= 4096); 3 = NES (xNES) */
     int32_t tc_min_dim;        /* prec BF16 / BF16X3 / FP8E4M3: executors with D >= tc_min_dim run on
                                   the tensor cores, the others in FP32 on the CUDA cores.  0 = let
-                                  metade_autotune choose between 129 and 256 by speed (129 until it
+                                  metade_autotune choose among 33, 129 and 256 by speed (129 until it
                                   runs); > 0 fixes it.  Ignored with FP32.  Negative: EINVAL */
     int32_t tc_unfused;        /* 0: BF16 tensor-core executors with D <= 256 (and FP32 difference-form
                                   ties) run four kernels per generation: ranking, trial rows, one
@@ -299,7 +299,11 @@ METADE_API metade_status metade_plain_step_noalloc(float *pop, float *fit, const
 /* Wait for the context's stream; return and clear the sticky device status. */
 METADE_API metade_status metade_sync(metade_ctx *ctx);
 
-/* Autotuner: for every bucket of the batched path, time each candidate block
+/* Autotuner: with cfg.tc_min_dim = 0 and BF16 / BF16X3 / FP8E4M3, first the
+ * tensor-core width (33, 129 or 256: one untimed and n_gens timed
+ * generations of every executor per width, on copies, keeping the fastest;
+ * this changes which executors are evaluated in reduced precision).  Then,
+ * for every bucket of the batched path, time each candidate block
  * shape (small-D kernel: 32, 64, 128, 256 threads; tile kernel: 128 or 256
  * threads with R^T resident, 256 with R^T streamed; general kernel: 128, 256,
  * 512 threads) on device copies of (pop, fit) for n_gens generations with the

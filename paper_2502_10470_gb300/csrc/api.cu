@@ -20,7 +20,8 @@ constexpr int kMaxDim = 1536;
 // the configuration fixes another width: 129 is the first D whose padded row
 // (D_pad > 128) no longer lets the fused tile kernel keep R^T in shared memory.
 constexpr int kTcDefaultMinDim = 129;
-constexpr int kTcAltMinDim = 256;  // the other width metade_autotune tries
+constexpr int kTcAltMinDim = 256;  // the widths metade_autotune also tries: every executor wider than the
+constexpr int kTcLowMinDim = 33;   // small-D kernel's reach, and only those of 256 and more
 constexpr int kMaxNp = 1024;
 constexpr size_t kSmemLimit = 227 * 1024;
 
@@ -1064,7 +1065,7 @@ metade_status metade_autotune(metade_ctx* c, const float* pop, const float* fit,
     const bool reduced = c->prec == METADE_BF16 || c->prec == METADE_BF16X3 || c->prec == METADE_FP8E4M3;
     bool mid = false;  // executors whose place (tensor cores or CUDA cores) the width decides
     for (const InstDesc& d : c->hdesc)
-        mid = mid || (d.obj != kMlp && d.dim >= kTcDefaultMinDim && d.dim < kTcAltMinDim);
+        mid = mid || (d.obj != kMlp && d.dim >= kTcLowMinDim && d.dim < kTcAltMinDim);
     const bool tune_width = c->tc_auto && reduced && mid;
     if (c->buckets.empty() && !tune_width) return METADE_OK;
     // the plan changes: graphs captured with the old one are dropped
@@ -1086,7 +1087,7 @@ metade_status metade_autotune(metade_ctx* c, const float* pop, const float* fit,
         int best_w = c->tc_min_dim;
         float best_ms = -1.f;
         c->tc_tuned.clear();
-        for (int w : {kTcDefaultMinDim, kTcAltMinDim}) {
+        for (int w : {kTcLowMinDim, kTcDefaultMinDim, kTcAltMinDim}) {
             c->tc_min_dim = w;
             st = setup_tc(c);
             if (st == METADE_OK) st = build_plan(c);

@@ -199,9 +199,10 @@ __global__ void __launch_bounds__(kTThreads, 4) k_tc_trial2(StepArgs a, const in
     // keeps its row's fields in registers across its chunks.
     const int r = 8 * (warp & 3) + (lane >> 2);
     if (r0 + r >= n_rows) return;  // no barrier follows
-    const int nchb = kp / 16;      // blocks of 4 chunks along K
     uint8_t* arow = aq + (size_t)(r0 + r) * kp * 2;
     const int dpad = rec[F_DPAD * kTRows + r];
+    // blocks of 4 chunks along K, up to the row's own K tiles (k_tc_sel reads no further)
+    const int nchb = ((dpad + kBK - 1) / kBK) * (kBK / 16);
     if (!rec[F_VALID * kTRows + r]) {  // rows of an invalid theta: a zero operand row
         for (int cb = warp >> 2; cb < nchb; cb += 2)
             *reinterpret_cast<uint2*>(arow + (size_t)(4 * (4 * cb + (lane & 3))) * 2) = make_uint2(0u, 0u);
@@ -279,7 +280,7 @@ struct SelArgs {
     const int* row_exec;      // operand row -> executor
     const long long* brow;    // per problem: first B row
     const float* uscr;        // trial rows (population layout)
-    int kt;                   // K tiles of the operands
+    int kt;                   // K tiles of the widest problem (shared memory is cut for it)
 };
 
 __global__ void __launch_bounds__(kSelThreads, 1) k_tc_sel(const __grid_constant__ CUtensorMap tmA,
@@ -326,16 +327,17 @@ __global__ void __launch_bounds__(kSelThreads, 1) k_tc_sel(const __grid_constant
     for (int t = t_begin; t < t_end; ++t) {
         const int arow = g.tiles[2 * t], nr = g.tiles[2 * t + 1];
         const InstDesc d = a.desc[g.row_exec[arow]];  // dim, objective and problem of every row of the tile
+        const int kt = (d.dpad + kBK - 1) / kBK;     // the problem's own K tiles (the rest of K is zero)
 
         // 1. loads (the previous tile's MMAs are complete and its tie vectors no longer needed) and MMAs
         if (issuer) {
-            mbar_expect_tx(&afull, (uint32_t)(g.kt * kAT));
-            for (int kk = 0; kk < g.kt; ++kk) tma_load_2d(As + (size_t)kk * kAT, &tmA, &afull, kk * kBK, arow);
+            mbar_expect_tx(&afull, (uint32_t)(kt * kAT));
+            for (int kk = 0; kk < kt; ++kk) tma_load_2d(As + (size_t)kk * kAT, &tmA, &afull, kk * kBK, arow);
             a_in_flight = true;
             if (d.prob != cur_prob) {
-                mbar_expect_tx(&bfull, (uint32_t)(g.kt * kBT));
+                mbar_expect_tx(&bfull, (uint32_t)(kt * kBT));
                 const int brow0 = (int)g.brow[d.prob];
-                for (int kk = 0; kk < g.kt; ++kk) tma_load_2d(Bs + (size_t)kk * kBT, &tmB, &bfull, kk * kBK, brow0);
+                for (int kk = 0; kk < kt; ++kk) tma_load_2d(Bs + (size_t)kk * kBT, &tmB, &bfull, kk * kBK, brow0);
                 b_in_flight = true;
             }
             bool ok = mbar_wait(&afull, aphase);
@@ -348,7 +350,7 @@ __global__ void __launch_bounds__(kSelThreads, 1) k_tc_sel(const __grid_constant
             }
             if (ok) {
                 tc_fence_after();
-                for (int kk = 0; kk < g.kt; ++kk) {
+                for (int kk = 0; kk < kt; ++kk) {
                     const uint64_t ad = sdesc_sw128(smem_u32(As + (size_t)kk * kAT));
                     const uint64_t bd = sdesc_sw128(smem_u32(Bs + (size_t)kk * kBT));
 #pragma unroll

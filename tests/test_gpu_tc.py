@@ -340,8 +340,8 @@ def test_tc_min_dim_places_executors_and_autotune_picks_a_width():
     b.set_theta(wl.theta)
     M.metade_autotune(b.ctx, b.pop, b.fit, b.theta, 2)
     plan = json.loads(M.metade_plan_info(b.ctx))
-    assert plan["tc_min_dim_auto"] and plan["tc_min_dim"] in (129, 256)
-    assert set(plan["tc_autotune_ms"]) == {"129", "256"}
+    assert plan["tc_min_dim_auto"] and plan["tc_min_dim"] in (33, 129, 256)
+    assert set(plan["tc_autotune_ms"]) == {"33", "129", "256"}
     p2, f2 = b.get_population()  # tuning ran on copies
     for k in range(wl.n_inst):
         np.testing.assert_array_equal(p2[k], pops[k])
