@@ -28,8 +28,8 @@
 //               whole CTA), near ties go to their problem's tie list;
 //   k_tc_ties2  the generation's near ties, 16 of one problem per chunk,
 //               chunks spread over every SM by an atomic counter: z = R (x -
-//               o) and dz = R (u - x) in FP32 on the CUDA cores (R rows staged
-//               through shared memory by cp.async, float4 loads, every fma
+//               o) and dz = R (u - x) in FP32 on the CUDA cores (R staged
+//               through an 8-stage cp.async ring, float4 loads, every fma
 //               chain in ascending k like every other FP32 rotation), the
 //               FP32 difference form, and the commit; a trial identical to its
 //               target is recognised from the staged u - x and accepted as it
@@ -60,14 +60,14 @@ constexpr int kTieBatch = 16;                // near ties rotated together
 constexpr int kVec = 256;                    // stride of a staged tie vector (floats)
 constexpr int kRc = 16;                      // R columns per cp.async stage of the tie rotation
 constexpr int kRcs = kRc + 4;                // row stride of a stage: float4 loads of 8 rows hit 32 banks
+constexpr int kRing = 8;                     // stages of the tie kernel's R ring (k_tc_ties2)
 constexpr int kTRows = 32;                   // rows per CTA of k_tc_trial2
 constexpr int kTThreads = 256;
 
 constexpr size_t kASize = (size_t)kMaxKt * kAT;                                  // 64 KB
 constexpr size_t kPartSize = (size_t)(kParts - 1) * kRows * 8 * sizeof(float);  // 12 KB
-// the tie phase reuses A and the part-exchange area (they follow each other)
-constexpr size_t kTieSize = (size_t)2 * kTieBatch * kVec * sizeof(float) + (size_t)2 * kVec * kRcs * sizeof(float);
-static_assert(kTieSize <= kASize + kPartSize, "tie buffers exceed the A tile and the exchange area");
+constexpr size_t kTie2Size =
+    (size_t)2 * kTieBatch * kVec * sizeof(float) + (size_t)kRing * kVec * kRcs * sizeof(float);  // 192 KB
 static_assert((kASize + kPartSize) % 1024 == 0, "B must start 1024-byte aligned");
 
 // record fields of k_tc_trial2, [field][kTRows]
@@ -487,14 +487,15 @@ struct TieArgs {
 };
 
 // The near ties of the generation, kTieBatch ties of one problem per chunk,
-// chunks handed out by an atomic counter over every CTA of the GPU: z = R (x
-// - o) and dz = R (u - x) in FP32, R rows staged through shared memory 16
-// columns at a time by cp.async (double buffered), a thread per (row of z,
-// half of the chunk's ties) with float4 loads along k, every fma chain in
-// ascending k; then a warp per tie forms the FP32 difference form f(u) -
-// f(x), decides and commits.  A trial identical to its target (u - x == 0
-// everywhere, pad included) is accepted as it is.
-__global__ void __launch_bounds__(kSelThreads, 2) k_tc_ties2(TieArgs g) {
+// chunks handed out by an atomic counter over every CTA of the GPU (one per
+// SM): z = R (x - o) and dz = R (u - x) in FP32, R staged through shared
+// memory 16 columns at a time by cp.async in a ring of kRing stages (so the
+// copies of half a D = 256 rotation are in flight together), a thread per
+// (row of z, half of the chunk's ties) with float4 loads along k, every fma
+// chain in ascending k; then a warp per tie forms the FP32 difference form
+// f(u) - f(x), decides and commits.  A trial identical to its target
+// (u - x == 0 everywhere, pad included) is accepted as it is.
+__global__ void __launch_bounds__(kSelThreads, 1) k_tc_ties2(TieArgs g) {
     extern __shared__ uint8_t smraw[];
     __shared__ int tp_s, j0_s;
     __shared__ long long toff_s[kTieBatch];
@@ -504,7 +505,7 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_tc_ties2(TieArgs g) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     float* vx = tv;                          // [kTieBatch][kVec] x - o, then z
     float* vl = tv + kTieBatch * kVec;       // u - x, then dz
-    float* sR = tv + 2 * kTieBatch * kVec;   // [2][kVec][kRcs]: R columns c0 .. c0 + 15 of every row
+    float* sR = tv + 2 * kTieBatch * kVec;   // [kRing][kVec][kRcs]: R columns c0 .. c0 + 15 of every row
     for (;;) {
         if (tid == 0) {  // chunk c -> (problem, first tie), problems in order
             const int c = atomicAdd(g.chunk_ctr, 1);
@@ -537,17 +538,20 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_tc_ties2(TieArgs g) {
         const float* o = a.shift + d.shift_off;
         const float* Rr = a.rot + d.rot_off;  // R rows [dim][dpad]
         const int nchunk = (d.dim + kRc - 1) / kRc;
-        auto stage = [&](int ch) {  // R[r][ch * 16 ..] for every row r < dim into buffer ch & 1
-            float* dst = sR + (size_t)(ch & 1) * kVec * kRcs;
-            const int c0 = ch * kRc;
-            for (int e2 = tid; e2 < d.dim * (kRc / 4); e2 += kSelThreads) {
-                const int rr = e2 >> 2, c = c0 + 4 * (e2 & 3);
-                const bool in = c < d.dpad;
-                cp_async16z(dst + rr * kRcs + 4 * (e2 & 3), Rr + (size_t)rr * d.dpad + (in ? c : 0), in ? 16 : 0);
+        auto stage = [&](int ch) {  // R[r][ch * 16 ..] for every row r < dim into stage ch % kRing
+            if (ch < nchunk) {
+                float* dst = sR + (size_t)(ch % kRing) * kVec * kRcs;
+                const int c0 = ch * kRc;
+                for (int e2 = tid; e2 < d.dim * (kRc / 4); e2 += kSelThreads) {
+                    const int rr = e2 >> 2, c = c0 + 4 * (e2 & 3);
+                    const bool in = c < d.dpad;
+                    cp_async16z(dst + rr * kRcs + 4 * (e2 & 3), Rr + (size_t)rr * d.dpad + (in ? c : 0),
+                                in ? 16 : 0);
+                }
             }
-            asm volatile("cp.async.commit_group;" ::: "memory");
+            asm volatile("cp.async.commit_group;" ::: "memory");  // one group per stage, empty past the end
         };
-        stage(0);
+        for (int ch = 0; ch < kRing - 1; ++ch) stage(ch);
         __syncthreads();  // toff_s
         for (int e2 = tid; e2 < nb * kVec; e2 += kSelThreads) {
             const int q = e2 / kVec, c = e2 - q * kVec;
@@ -565,15 +569,11 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_tc_ties2(TieArgs g) {
         for (int q = 0; q < kTieBatch / 2; ++q) az[q] = adz[q] = 0.f;
         const int mine = (nb - h + 1) >> 1;  // ties of this half (warp-uniform)
         for (int ch = 0; ch < nchunk; ++ch) {
-            if (ch + 1 < nchunk) {
-                stage(ch + 1);
-                asm volatile("cp.async.wait_group 1;" ::: "memory");
-            } else {
-                asm volatile("cp.async.wait_group 0;" ::: "memory");
-            }
+            stage(ch + kRing - 1);  // the stage read at ch - 1 is free: every thread passed the barrier after it
+            asm volatile("cp.async.wait_group %0;" ::"n"(kRing - 1) : "memory");  // stage ch has landed
             __syncthreads();
             if (r < d.dim) {
-                const float* rc = sR + (size_t)(ch & 1) * kVec * kRcs + r * kRcs;
+                const float* rc = sR + (size_t)(ch % kRing) * kVec * kRcs + r * kRcs;
                 const int c0 = ch * kRc;
                 const int cend = min(kRc, d.dim - c0);
                 if (cend == kRc) {  // four float4 steps, k ascending within each
@@ -611,8 +611,9 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_tc_ties2(TieArgs g) {
                     }
                 }
             }
-            __syncthreads();  // the buffer is refilled two chunks later
+            __syncthreads();  // the stage is refilled kRing - 1 chunks later
         }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");  // only empty groups remain
         if (r < d.dim) {  // every thread has read vx / vl: z and dz replace them
 #pragma unroll
             for (int j = 0; j < kTieBatch / 2; ++j) {
@@ -668,7 +669,7 @@ __global__ void k_tc_rank(StepArgs a, const int* __restrict__ execs, int* topk_a
 }
 
 size_t sel_smem(int kt) { return 1024 + kASize + kPartSize + (size_t)kt * kBT; }
-constexpr size_t kTieSmem = 16 + kTieSize;
+constexpr size_t kTieSmem = 16 + kTie2Size;
 
 }  // namespace
 
@@ -711,7 +712,7 @@ cudaError_t launch_tc_fused_generation(const StepArgs& a, const TcPlan& p, cudaS
     ta.uscr = p.uscr;
     e = cudaFuncSetAttribute(k_tc_ties2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTieSmem);
     if (e != cudaSuccess) return e;
-    k_tc_ties2<<<2 * p.gen_ctas, kSelThreads, kTieSmem, st>>>(ta);
+    k_tc_ties2<<<p.gen_ctas, kSelThreads, kTieSmem, st>>>(ta);
     if (ev) cudaEventRecord(ev[4], st);
     return cudaGetLastError();
 }
