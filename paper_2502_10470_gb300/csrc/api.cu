@@ -112,6 +112,7 @@ struct metade_ctx {
     int* tc_topk = nullptr;
     int* tc_ties = nullptr;
     int* tc_tp = nullptr;  // problem -> path index, first rows, tie counts
+    long long* tc_tie_off = nullptr;  // population offsets of listed near ties
     uint8_t *aq = nullptr, *aq_lo = nullptr, *bq = nullptr, *bq_lo = nullptr;  // BF16 pairs or e4m3 bytes
     float *ascale = nullptr, *bscale = nullptr;                                // FP8 dequantisation factors
     unsigned* amax = nullptr;                                                  // FP8: max|R| scratch
@@ -308,7 +309,9 @@ void free_tc(metade_ctx* c) {
     cudaFree(c->bscale);
     cudaFree(c->amax);
     cudaFree(c->tc_tp);
+    cudaFree(c->tc_tie_off);
     c->tc_tp = nullptr;
+    c->tc_tie_off = nullptr;
     c->tc_execs = c->tc_row_exec = c->tc_tiles = c->tc_topk = c->tc_ties = nullptr;
     c->tc_brow = nullptr;
     c->aq = c->aq_lo = c->bq = c->bq_lo = nullptr;
@@ -400,7 +403,7 @@ metade_status setup_tc(metade_ctx* c) {
         (!simt && (dalloc(&c->aq, nrows * tc_kp * esz) || dalloc(&c->bq, (size_t)tc_brows * tc_kp * esz))) ||
         (split && (dalloc(&c->aq_lo, nrows * tc_kp * esz) || dalloc(&c->bq_lo, (size_t)tc_brows * tc_kp * esz))) ||
         (fp8 && (dalloc(&c->ascale, nrows) || dalloc(&c->bscale, (size_t)c->n_prob) || dalloc(&c->amax, 1))) ||
-        dalloc(&c->tc_tp, (size_t)c->n_prob + 2 * tp_row0.size() + 1))
+        dalloc(&c->tc_tp, (size_t)c->n_prob + 2 * tp_row0.size() + 1) || dalloc(&c->tc_tie_off, nrows))
         return METADE_ENOMEM;
     std::vector<int> tp_host(prob_tp);
     tp_host.insert(tp_host.end(), tp_row0.begin(), tp_row0.end());
@@ -448,6 +451,7 @@ metade_status setup_tc(metade_ctx* c) {
     t.tie_list = c->tc_ties + 2;
     t.tie_count = c->tc_ties;
     t.next_tile = c->tc_ties + 1;
+    t.tie_off = c->tc_tie_off;
     t.n_tp = (int)tp_row0.size();
     t.prob_tp = c->tc_tp;
     t.tp_row0 = c->tc_tp + c->n_prob;

@@ -123,7 +123,8 @@ struct TcPlan {
     float* bscale;           // FP8: per problem, max|R| / 448
     int fp8;                 // 1: e4m3 operands (kind::f8f6f4)
     int simt;                // 1: FP32 GEMM on the CUDA cores (k_rot_simt, 64-row tiles, no operands)
-    int* tie_list;           // device [n_rows] rows whose selection is a near tie
+    int* tie_list;           // device [n_rows] rows whose selection is a near tie (fused path: fitness index)
+    long long* tie_off;      // device [n_rows] fused path: population offset of each near tie's row
     int* tie_count;          // device counter
     int tie_ctas;            // CTAs of the tie kernel
     int kp, split, max_dpad;

@@ -29,7 +29,7 @@
 //   k_tc_ties2  the generation's near ties, 16 of one problem per chunk,
 //               chunks spread over every SM by an atomic counter: z = R (x -
 //               o) and dz = R (u - x) in FP32 on the CUDA cores (R staged
-//               through an 8-stage cp.async ring, float4 loads, every fma
+//               through a 3-stage cp.async ring, float4 loads, every fma
 //               chain in ascending k like every other FP32 rotation), the
 //               FP32 difference form, and the commit; a trial identical to its
 //               target is recognised from the staged u - x and accepted as it
@@ -60,14 +60,15 @@ constexpr int kTieBatch = 16;                // near ties rotated together
 constexpr int kVec = 256;                    // stride of a staged tie vector (floats)
 constexpr int kRc = 16;                      // R columns per cp.async stage of the tie rotation
 constexpr int kRcs = kRc + 4;                // row stride of a stage: float4 loads of 8 rows hit 32 banks
-constexpr int kRing = 8;                     // stages of the tie kernel's R ring (k_tc_ties2)
+constexpr int kRing = 3;                     // stages of the tie kernel's R ring (k_tc_ties2)
+constexpr int kMaxTpSmem = 2048;             // problems whose chunk prefix k_tc_ties2 keeps in shared memory
 constexpr int kTRows = 32;                   // rows per CTA of k_tc_trial2
 constexpr int kTThreads = 256;
 
 constexpr size_t kASize = (size_t)kMaxKt * kAT;                                  // 64 KB
 constexpr size_t kPartSize = (size_t)(kParts - 1) * kRows * 8 * sizeof(float);  // 12 KB
 constexpr size_t kTie2Size =
-    (size_t)2 * kTieBatch * kVec * sizeof(float) + (size_t)kRing * kVec * kRcs * sizeof(float);  // 192 KB
+    (size_t)2 * kTieBatch * kVec * sizeof(float) + (size_t)kRing * kVec * kRcs * sizeof(float);  // 92 KB
 static_assert((kASize + kPartSize) % 1024 == 0, "B must start 1024-byte aligned");
 
 // record fields of k_tc_trial2, [field][kTRows]
@@ -276,7 +277,8 @@ struct SelArgs {
     const int* prob_tp;       // problem -> index among the problems on this path
     const int* tp_row0;       // per such problem: its first operand row (start of its tie list)
     int* tie_cnt;             // per such problem: near ties listed (zeroed by k_tc_rank)
-    int* tie_list;            // operand rows of the near ties, by problem
+    int* tie_list;            // fitness index of each near tie, by problem
+    long long* tie_off;       // population offset of each near tie's row, by problem
     const int* row_exec;      // operand row -> executor
     const long long* brow;    // per problem: first B row
     const float* uscr;        // trial rows (population layout)
@@ -434,7 +436,9 @@ __global__ void __launch_bounds__(kSelThreads, 1) k_tc_sel(const __grid_constant
                 const float fx = a.fit[fidx];
                 if (near_tie(fn, fx, tie_band(d.dim))) {
                     const int tp = g.prob_tp[d.prob];
-                    g.tie_list[g.tp_row0[tp] + atomicAdd(&g.tie_cnt[tp], 1)] = arow + row;
+                    const int q = g.tp_row0[tp] + atomicAdd(&g.tie_cnt[tp], 1);
+                    g.tie_list[q] = fidx;
+                    g.tie_off[q] = e.pop_off + (long long)(arow + row - e.tc_row) * d.dpad;
                 } else if (fn <= fx) {
                     acc_row[atomicAdd(&nacc_s, 1)] = row;
                     a.fit[fidx] = fn;
@@ -481,43 +485,67 @@ struct TieArgs {
     int n_tp;                 // problems on this path
     const int* tp_row0;       // per problem: its first operand row (start of its tie list)
     const int* tie_cnt;       // per problem: near ties listed by k_tc_sel
-    const int* tie_list;      // operand rows of the near ties, by problem
+    const int* tie_list;      // fitness index of each near tie, by problem
+    const long long* tie_off; // population offset of each near tie's row, by problem
     int* chunk_ctr;           // chunks handed out (zeroed by k_tc_rank)
     const float* uscr;        // trial rows (population layout)
 };
 
 // The near ties of the generation, kTieBatch ties of one problem per chunk,
-// chunks handed out by an atomic counter over every CTA of the GPU (one per
+// chunks handed out by an atomic counter over every CTA of the GPU (two per
 // SM): z = R (x - o) and dz = R (u - x) in FP32, R staged through shared
-// memory 16 columns at a time by cp.async in a ring of kRing stages (so the
-// copies of half a D = 256 rotation are in flight together), a thread per
+// memory 16 columns at a time by cp.async in a ring of kRing stages, a
+// thread per
 // (row of z, half of the chunk's ties) with float4 loads along k, every fma
 // chain in ascending k; then a warp per tie forms the FP32 difference form
 // f(u) - f(x), decides and commits.  A trial identical to its target
 // (u - x == 0 everywhere, pad included) is accepted as it is.
-__global__ void __launch_bounds__(kSelThreads, 1) k_tc_ties2(TieArgs g) {
+__global__ void __launch_bounds__(kSelThreads, 2) k_tc_ties2(TieArgs g) {
     extern __shared__ uint8_t smraw[];
-    __shared__ int tp_s, j0_s;
-    __shared__ long long toff_s[kTieBatch];
-    __shared__ int tfid_s[kTieBatch];
+    __shared__ int tp_s, j0_s, ncum_s[kMaxTpSmem + 1];
     float* tv = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smraw) + 15) & ~(uintptr_t)15);
     const StepArgs& a = g.a;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     float* vx = tv;                          // [kTieBatch][kVec] x - o, then z
     float* vl = tv + kTieBatch * kVec;       // u - x, then dz
     float* sR = tv + 2 * kTieBatch * kVec;   // [kRing][kVec][kRcs]: R columns c0 .. c0 + 15 of every row
+    // chunks per problem (every count is final: k_tc_sel has ended), summed in problem order
+    const bool cum_smem = g.n_tp <= kMaxTpSmem;
+    if (cum_smem) {
+        for (int q = tid; q < g.n_tp; q += blockDim.x) ncum_s[q + 1] = (g.tie_cnt[q] + kTieBatch - 1) / kTieBatch;
+        __syncthreads();
+        if (tid == 0) {
+            ncum_s[0] = 0;
+            for (int q = 0; q < g.n_tp; ++q) ncum_s[q + 1] += ncum_s[q];
+        }
+        __syncthreads();
+    }
     for (;;) {
-        if (tid == 0) {  // chunk c -> (problem, first tie), problems in order
+        if (tid == 0) {  // chunk c -> (problem, first tie)
             const int c = atomicAdd(g.chunk_ctr, 1);
-            int acc = 0, tp = -1, j0 = 0;
-            for (int q = 0; q < g.n_tp; ++q) {
-                const int n = (g.tie_cnt[q] + kTieBatch - 1) / kTieBatch;
-                if (c < acc + n) {
-                    tp = q;
-                    j0 = (c - acc) * kTieBatch;
-                    break;
+            int tp = -1, j0 = 0;
+            if (cum_smem) {
+                if (c < ncum_s[g.n_tp]) {  // the last problem whose first chunk is <= c
+                    int lo = 0, hi = g.n_tp - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (ncum_s[mid] <= c) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    tp = lo;
+                    j0 = (c - ncum_s[lo]) * kTieBatch;
                 }
-                acc += n;
+            } else {
+                int acc = 0;
+                for (int q = 0; q < g.n_tp; ++q) {
+                    const int n = (g.tie_cnt[q] + kTieBatch - 1) / kTieBatch;
+                    if (c < acc + n) {
+                        tp = q;
+                        j0 = (c - acc) * kTieBatch;
+                        break;
+                    }
+                    acc += n;
+                }
             }
             tp_s = tp;
             j0_s = j0;
@@ -526,15 +554,9 @@ __global__ void __launch_bounds__(kSelThreads, 1) k_tc_ties2(TieArgs g) {
         const int tp = tp_s, j0 = j0_s;
         if (tp < 0) break;
         const int nb = min(kTieBatch, g.tie_cnt[tp] - j0);
-        const int* rows = g.tie_list + g.tp_row0[tp] + j0;
-        if (tid < nb) {  // each tie's row offset in the population and fitness index
-            const int gr = rows[tid];
-            const InstDesc e = a.desc[g.row_exec[gr]];
-            const int i = gr - e.tc_row;
-            toff_s[tid] = e.pop_off + (long long)i * e.dpad;
-            tfid_s[tid] = e.fit_off + i;
-        }
-        const InstDesc d = a.desc[g.row_exec[rows[0]]];  // dim, objective and problem of every tie of the chunk
+        const int* tfid = g.tie_list + g.tp_row0[tp] + j0;     // fitness index of each tie
+        const long long* toff = g.tie_off + g.tp_row0[tp] + j0;  // its row's population offset
+        const InstDesc d = a.desc[g.row_exec[g.tp_row0[tp]]];  // dim, objective and problem of every tie
         const float* o = a.shift + d.shift_off;
         const float* Rr = a.rot + d.rot_off;  // R rows [dim][dpad]
         const int nchunk = (d.dim + kRc - 1) / kRc;
@@ -552,14 +574,18 @@ __global__ void __launch_bounds__(kSelThreads, 1) k_tc_ties2(TieArgs g) {
             asm volatile("cp.async.commit_group;" ::: "memory");  // one group per stage, empty past the end
         };
         for (int ch = 0; ch < kRing - 1; ++ch) stage(ch);
-        __syncthreads();  // toff_s
-        for (int e2 = tid; e2 < nb * kVec; e2 += kSelThreads) {
-            const int q = e2 / kVec, c = e2 - q * kVec;
-            if (c < d.dpad) {
-                const long long off = toff_s[q];
-                const float xc = a.pop[off + c];
-                vx[q * kVec + c] = c < d.dim ? xc - o[c] : 0.f;
-                vl[q * kVec + c] = g.uscr[off + c] - xc;
+        {  // x - o and u - x of every tie, float4 at a time (pad columns of x, u and o are zero)
+            const int f4 = d.dpad >> 2;
+            for (int e2 = tid; e2 < nb * f4; e2 += kSelThreads) {
+                const int q = e2 / f4, c = 4 * (e2 - q * f4);
+                const long long off = toff[q];
+                const float4 x4 = *reinterpret_cast<const float4*>(a.pop + off + c);
+                const float4 u4 = __ldg(reinterpret_cast<const float4*>(g.uscr + off + c));
+                const float4 o4 = __ldg(reinterpret_cast<const float4*>(o + c));
+                *reinterpret_cast<float4*>(vx + q * kVec + c) = make_float4(x4.x - o4.x, x4.y - o4.y, x4.z - o4.z,
+                                                                            x4.w - o4.w);
+                *reinterpret_cast<float4*>(vl + q * kVec + c) = make_float4(u4.x - x4.x, u4.y - x4.y, u4.z - x4.z,
+                                                                            u4.w - x4.w);
             }
         }
         // thread (row r, half h): ties h, h + 2, h + 4, ... of the chunk
@@ -625,8 +651,8 @@ __global__ void __launch_bounds__(kSelThreads, 1) k_tc_ties2(TieArgs g) {
         }
         __syncthreads();
         if (warp < nb) {  // warp per tie: decide and commit
-            const long long off = toff_s[warp];
-            const int fidx = tfid_s[warp];
+            const long long off = toff[warp];
+            const int fidx = tfid[warp];
             bool diff = false;  // every load issued: no short circuit
             for (int c = lane; c < d.dpad; c += 32) diff |= g.uscr[off + c] != a.pop[off + c];
             const float fx = a.fit[fidx];
@@ -691,6 +717,7 @@ cudaError_t launch_tc_fused_generation(const StepArgs& a, const TcPlan& p, cudaS
     g.tp_row0 = p.tp_row0;
     g.tie_cnt = p.tie_cnt;
     g.tie_list = p.tie_list;
+    g.tie_off = p.tie_off;
     g.row_exec = p.row_exec;
     g.brow = p.brow;
     g.uscr = p.uscr;
@@ -708,11 +735,12 @@ cudaError_t launch_tc_fused_generation(const StepArgs& a, const TcPlan& p, cudaS
     ta.tp_row0 = p.tp_row0;
     ta.tie_cnt = p.tie_cnt;
     ta.tie_list = p.tie_list;
+    ta.tie_off = p.tie_off;
     ta.chunk_ctr = p.chunk_ctr;
     ta.uscr = p.uscr;
     e = cudaFuncSetAttribute(k_tc_ties2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTieSmem);
     if (e != cudaSuccess) return e;
-    k_tc_ties2<<<p.gen_ctas, kSelThreads, kTieSmem, st>>>(ta);
+    k_tc_ties2<<<2 * p.gen_ctas, kSelThreads, kTieSmem, st>>>(ta);
     if (ev) cudaEventRecord(ev[4], st);
     return cudaGetLastError();
 }
