@@ -26,8 +26,9 @@
 //               quarters in column order; a thread per row then selects:
 //               clear acceptances are committed at once (rows copied by the
 //               whole CTA), near ties go to their problem's tie list;
-//   k_tc_ties2  the generation's near ties, 16 of one problem per chunk,
-//               chunks spread over every SM by an atomic counter: z = R (x -
+//   k_tc_ties2  the generation's near ties, 2 to 16 of one problem per chunk
+//               (about one chunk per CTA), chunks spread over every SM by an
+//               atomic counter: z = R (x -
 //               o) and dz = R (u - x) in FP32 on the CUDA cores (R staged
 //               through a 3-stage cp.async ring, float4 loads, every fma
 //               chain in ascending k like every other FP32 rotation), the
@@ -491,8 +492,9 @@ struct TieArgs {
     const float* uscr;        // trial rows (population layout)
 };
 
-// The near ties of the generation, kTieBatch ties of one problem per chunk,
-// chunks handed out by an atomic counter over every CTA of the GPU (two per
+// The near ties of the generation, up to kTieBatch ties of one problem per
+// chunk (fewer when ties are few), chunks handed out by an atomic counter
+// over every CTA of the GPU (two per
 // SM): z = R (x - o) and dz = R (u - x) in FP32, R staged through shared
 // memory 16 columns at a time by cp.async in a ring of kRing stages, a
 // thread per
@@ -502,17 +504,27 @@ struct TieArgs {
 // (u - x == 0 everywhere, pad included) is accepted as it is.
 __global__ void __launch_bounds__(kSelThreads, 2) k_tc_ties2(TieArgs g) {
     extern __shared__ uint8_t smraw[];
-    __shared__ int tp_s, j0_s, ncum_s[kMaxTpSmem + 1];
+    __shared__ int tp_s, j0_s, bsz_s, ncum_s[kMaxTpSmem + 1];
     float* tv = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smraw) + 15) & ~(uintptr_t)15);
     const StepArgs& a = g.a;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     float* vx = tv;                          // [kTieBatch][kVec] x - o, then z
     float* vl = tv + kTieBatch * kVec;       // u - x, then dz
     float* sR = tv + 2 * kTieBatch * kVec;   // [kRing][kVec][kRcs]: R columns c0 .. c0 + 15 of every row
-    // chunks per problem (every count is final: k_tc_sel has ended), summed in problem order
+    // chunk size: the ties of the generation spread over every CTA in about one round (few
+    // ties: small chunks, so no SM waits behind another's long chunk), between 2 and
+    // kTieBatch; every CTA derives the same size from the same final counts (k_tc_sel has ended)
+    if (tid == 0) {
+        long long total = 0;
+        for (int q = 0; q < g.n_tp; ++q) total += g.tie_cnt[q];
+        bsz_s = (int)min((long long)kTieBatch, max(2LL, (total + gridDim.x - 1) / gridDim.x));
+    }
+    __syncthreads();
+    const int bsz = bsz_s;
+    // chunks per problem, summed in problem order
     const bool cum_smem = g.n_tp <= kMaxTpSmem;
     if (cum_smem) {
-        for (int q = tid; q < g.n_tp; q += blockDim.x) ncum_s[q + 1] = (g.tie_cnt[q] + kTieBatch - 1) / kTieBatch;
+        for (int q = tid; q < g.n_tp; q += blockDim.x) ncum_s[q + 1] = (g.tie_cnt[q] + bsz - 1) / bsz;
         __syncthreads();
         if (tid == 0) {
             ncum_s[0] = 0;
@@ -533,15 +545,15 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_tc_ties2(TieArgs g) {
                         else hi = mid - 1;
                     }
                     tp = lo;
-                    j0 = (c - ncum_s[lo]) * kTieBatch;
+                    j0 = (c - ncum_s[lo]) * bsz;
                 }
             } else {
                 int acc = 0;
                 for (int q = 0; q < g.n_tp; ++q) {
-                    const int n = (g.tie_cnt[q] + kTieBatch - 1) / kTieBatch;
+                    const int n = (g.tie_cnt[q] + bsz - 1) / bsz;
                     if (c < acc + n) {
                         tp = q;
-                        j0 = (c - acc) * kTieBatch;
+                        j0 = (c - acc) * bsz;
                         break;
                     }
                     acc += n;
@@ -553,7 +565,7 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_tc_ties2(TieArgs g) {
         __syncthreads();
         const int tp = tp_s, j0 = j0_s;
         if (tp < 0) break;
-        const int nb = min(kTieBatch, g.tie_cnt[tp] - j0);
+        const int nb = min(bsz, g.tie_cnt[tp] - j0);
         const int* tfid = g.tie_list + g.tp_row0[tp] + j0;     // fitness index of each tie
         const long long* toff = g.tie_off + g.tp_row0[tp] + j0;  // its row's population offset
         const InstDesc d = a.desc[g.row_exec[g.tp_row0[tp]]];  // dim, objective and problem of every tie
