@@ -609,16 +609,24 @@ def run_ours(args):
 
 def rooflines(wl, b, plan, prof, thetas, gens, steps, total_ms, clocks):
     """Roofline of each measured kernel kind of the step, and the dominant one
-    (largest share of the step).  ALU-bound fused kernels (small-D, tile):
-    alu_ops lane operations of their executors over their event time, against
-    152 SMs x 128 lanes x the maximum SM clock.  The tensor-core GEMM: 2 NP D^2
-    algorithmic flops per executor-generation over its event time, against the
-    measured BF16 peak (sustained: it runs inside a long step).  The trial and
-    selection kernels of the tensor-core path are HBM/L2-bound: their
-    algorithmic bytes per generation (trial: read the target row, write the
-    FP32 trial row and the BF16 operand row; selection: read both rows, write
-    the accepted ones -- counted as all) over their time, against the measured
-    copy bandwidth."""
+    (largest share of the step).
+
+    - ALU-bound fused kernels (small-D, tile): alu_ops lane operations of
+      their executors over their event time, against 152 SMs x 128 lanes x
+      the maximum SM clock.
+    - The tensor-core GEMM (k_rot_tc, or k_tc_sel, which holds the GEMM with
+      the objective, selection and commit): 2 NP D^2 algorithmic flops per
+      executor-generation over its event time, against the measured BF16 peak
+      (sustained: it runs inside a long step).
+    - The trial kernel (k_tc_trial2, or k_tc_trial): HBM-bound; algorithmic
+      bytes per row and generation = read the target row (4 D_pad), write the
+      FP32 trial row (4 D_pad) and the BF16 operand row (2 x its K extent:
+      round_up(D_pad, 64) on the four-kernel path, the context's K on the
+      five-kernel one); the random parent rows are re-reads, not counted.
+    - The selection kernel of the five-kernel pipeline (k_tc_select):
+      HBM-bound; both rows read, the accepted ones written (counted as all).
+    The near-tie kernels are left out: their work depends on how many
+    selections are near ties, which the host does not see."""
     import numpy as np
     peaks = load_peaks()
     sm_max = float((clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0))
@@ -628,9 +636,11 @@ def rooflines(wl, b, plan, prof, thetas, gens, steps, total_ms, clocks):
     dims = b.dims
     on_tc = np.zeros(b.n_inst, dtype=bool)
     tcmin = plan.get("tc_min_dim") or 129
-    if "tensor_core" in plan:
+    tcinfo = plan.get("tensor_core") or {}
+    if tcinfo:
         on_tc = dims >= tcmin
-    small = dims <= 32
+    fused = tcinfo.get("kernel") == "k_tc_sel"
+    small = (dims <= 32) & ~on_tc
     tile = ~small & ~on_tc
     dpads = (dims + 3) // 4 * 4
     th = [t.cpu().numpy() for t in thetas]
@@ -649,20 +659,25 @@ def rooflines(wl, b, plan, prof, thetas, gens, steps, total_ms, clocks):
     alu("fused_small", small, "k_fused_small")
     alu("fused_tile", tile & (dpads <= 128), "k_fused_tile")
     alu("fused_tile_stream", tile & (dpads > 128), "k_fused_tile_stream")
-    if on_tc.any() and prof["tc_gemm"][1]:
+    gemm_kind = "tc_sel" if fused else "tc_gemm"
+    if on_tc.any() and prof[gemm_kind][1]:
         rows = wl.inst_np[on_tc].astype(np.float64)
         dd = dims[on_tc].astype(np.float64)
         flops = 2.0 * float((rows * dd * dd).sum())  # per generation
-        ms = prof["tc_gemm"][0] / prof["tc_gemm"][1]
-        out["k_rot_tc"] = {"bound": "tensor", "achieved": flops / (ms / 1e3) / 1e12, "peak": bf16_peak / 1e12,
-                           "unit": "TFLOP/s", "frac": flops / (ms / 1e3) / bf16_peak,
-                           "ms_per_step": prof["tc_gemm"][0] / steps, "share": prof["tc_gemm"][0] / total_ms,
-                           "launch_ms": ms, "flops_per_launch": flops,
-                           "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained, of measured"}
-        dpad = (dd + 3) // 4 * 4
-        kp = np.ceil(dd / 64) * 64
-        for kind, name, per_row in (("tc_trial", "k_tc_trial", 4 * dpad + 4 * dpad + 2 * kp),
-                                    ("tc_select", "k_tc_select", 4 * dpad + 4 * dpad + 4 * dpad + 12)):
+        ms = prof[gemm_kind][0] / prof[gemm_kind][1]
+        name = "k_tc_sel" if fused else "k_rot_tc"
+        out[name] = {"bound": "tensor", "achieved": flops / (ms / 1e3) / 1e12, "peak": bf16_peak / 1e12,
+                     "unit": "TFLOP/s", "frac": flops / (ms / 1e3) / bf16_peak,
+                     "ms_per_step": prof[gemm_kind][0] / steps, "share": prof[gemm_kind][0] / total_ms,
+                     "launch_ms": ms, "flops_per_launch": flops,
+                     "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained, of measured"}
+    if on_tc.any():
+        rows = wl.inst_np[on_tc].astype(np.float64)
+        dp = dpads[on_tc].astype(np.float64)
+        kcols = np.ceil(dp / 64) * 64 if fused else float(tcinfo.get("kp", 0))
+        trial = ("tc_trial", "k_tc_trial2" if fused else "k_tc_trial", 4 * dp + 4 * dp + 2 * kcols)
+        kinds = [trial] if fused else [trial, ("tc_select", "k_tc_select", 4 * dp + 4 * dp + 4 * dp + 12)]
+        for kind, name, per_row in kinds:
             if not prof[kind][1]:
                 continue
             byts = float((rows * per_row).sum())
@@ -671,7 +686,14 @@ def rooflines(wl, b, plan, prof, thetas, gens, steps, total_ms, clocks):
                          "frac": byts / (ms / 1e3) / hbm, "ms_per_step": prof[kind][0] / steps,
                          "share": prof[kind][0] / total_ms, "launch_ms": ms, "bytes_per_launch": byts,
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs, of measured"}
-    dom = max(out.items(), key=lambda kv: kv[1]["share"]) if out else (None, {})
+    # kernels with no roofline entry, by time: reported so that the dominant one is visible
+    for kind in ("tc_ties", "tc_prologue"):
+        if prof[kind][1]:
+            out.setdefault("k_tc_ties2" if kind == "tc_ties" and fused else
+                           ("k_tc_ties" if kind == "tc_ties" else ("k_tc_rank" if fused else "k_tc_prologue")),
+                           {"bound": None, "ms_per_step": prof[kind][0] / steps, "share": prof[kind][0] / total_ms})
+    ranked = [kv for kv in out.items() if kv[1].get("bound")]
+    dom = max(ranked, key=lambda kv: kv[1]["share"]) if ranked else (None, {})
     head = dict(dom[1])
     head["kernel"] = dom[0]
     head["traffic"] = None
