@@ -14,16 +14,18 @@
 //               arithmetic every trial kernel shares), the FP32 trial row and
 //               the BF16 operand u - o, K-padded, to global memory.  Many small
 //               CTAs per SM keep many row gathers in flight;
-//   k_tc_sel    persistent, one CTA of 512 threads per SM, over a contiguous
-//               block of the 128-row M tiles (rows of one problem, possibly of
-//               several executors):
-//               TMA loads of the A tile and, once per problem, of B (the
+//   k_tc_sel    persistent, one CTA per SM, over a contiguous block of the
+//               128-row M tiles (rows of one problem, possibly of several
+//               executors), warp-specialised: a producer warp issues the TMA
+//               loads of the A tile and, once per problem, of B (the
 //               problem's padded BF16 R rows, kept in shared memory while the
-//               CTA's tiles belong to that problem); thread 0 issues
-//               tcgen05.mma (M 128, N 256, K 16, FP32 accumulate in TMEM);
-//               16 warps read TMEM (tcgen05.ld), each a quarter of the
-//               columns of 32 rows, accumulate the objective and compose the
-//               quarters in column order; a thread per row then selects:
+//               CTA's tiles belong to that problem) and the tcgen05.mma
+//               (M 128, N 256, K 16, FP32 accumulate) into one of two TMEM
+//               accumulators, so the loads and MMAs of tile j + 1 run during
+//               the epilogue of tile j; 16 epilogue warps read TMEM
+//               (tcgen05.ld), each a quarter of the columns of 32 rows,
+//               accumulate the objective and compose the quarters in column
+//               order; a thread per row then selects:
 //               clear acceptances are committed at once (rows copied by the
 //               whole CTA), near ties go to their problem's tie list;
 //   k_tc_ties2  the generation's near ties, 2 to 16 of one problem per chunk
@@ -286,12 +288,15 @@ struct SelArgs {
     int kt;                   // K tiles of the widest problem (shared memory is cut for it)
 };
 
-__global__ void __launch_bounds__(kSelThreads, 1) k_tc_sel(const __grid_constant__ CUtensorMap tmA,
-                                                           const __grid_constant__ CUtensorMap tmB, SelArgs g) {
+// Named barrier of the 16 epilogue warps (the producer warp does not take part).
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kSelThreads) : "memory"); }
+
+__global__ void __launch_bounds__(kSelThreads + 32, 1) k_tc_sel(const __grid_constant__ CUtensorMap tmA,
+                                                                const __grid_constant__ CUtensorMap tmB, SelArgs g) {
     extern __shared__ uint8_t smraw[];
-    __shared__ __align__(8) uint64_t afull, bfull, mma_done, drain;
+    __shared__ __align__(8) uint64_t afull, bfull, acc_full[2], acc_empty[2], drain;
     __shared__ uint32_t tmem_base;
-    __shared__ int abort_s, nacc_s;
+    __shared__ int ep_abort_s, nacc_s;
     __shared__ int acc_row[kRows];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
     uint8_t* As = sm;
@@ -299,85 +304,99 @@ __global__ void __launch_bounds__(kSelThreads, 1) k_tc_sel(const __grid_constant
     uint8_t* Bs = sm + kASize + kPartSize;
     const StepArgs& a = g.a;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool issuer = tid == 0;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                     "r"(kBN)
+                     "r"(2 * kBN)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
         mbar_init(&afull, 1);
         mbar_init(&bfull, 1);
-        mbar_init(&mma_done, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], kEpiWarps);  // one arrival per epilogue warp
+        }
         mbar_init(&drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        abort_s = 0;
+        ep_abort_s = 0;
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t taddr = tmem_base;
-
-    int cur_prob = -1;
-    uint32_t aphase = 0, bphase = 0, mphase = 0;
-    bool a_in_flight = false, b_in_flight = false;  // thread 0: loads not yet waited on
     // a contiguous block of tiles per CTA: tiles of one problem are adjacent, so B is loaded
     // about once per problem (every tile costs about the same: near ties are decided elsewhere)
     const int t_begin = (int)(((long long)g.n_tiles * blockIdx.x) / gridDim.x);
     const int t_end = (int)(((long long)g.n_tiles * (blockIdx.x + 1)) / gridDim.x);
-    for (int t = t_begin; t < t_end; ++t) {
-        const int arow = g.tiles[2 * t], nr = g.tiles[2 * t + 1];
-        const InstDesc d = a.desc[g.row_exec[arow]];  // dim, objective and problem of every row of the tile
-        const int kt = (d.dpad + kBK - 1) / kBK;     // the problem's own K tiles (the rest of K is zero)
 
-        // 1. loads (the previous tile's MMAs are complete and its tie vectors no longer needed) and MMAs
-        if (issuer) {
-            mbar_expect_tx(&afull, (uint32_t)(kt * kAT));
-            for (int kk = 0; kk < kt; ++kk) tma_load_2d(As + (size_t)kk * kAT, &tmA, &afull, kk * kBK, arow);
-            a_in_flight = true;
-            if (d.prob != cur_prob) {
-                mbar_expect_tx(&bfull, (uint32_t)(kt * kBT));
-                const int brow0 = (int)g.brow[d.prob];
-                for (int kk = 0; kk < kt; ++kk) tma_load_2d(Bs + (size_t)kk * kBT, &tmB, &bfull, kk * kBK, brow0);
-                b_in_flight = true;
-            }
-            bool ok = mbar_wait(&afull, aphase);
-            aphase ^= 1u;
-            a_in_flight = false;
-            if (ok && b_in_flight) {
-                ok = mbar_wait(&bfull, bphase);
-                bphase ^= 1u;
-                b_in_flight = false;
-            }
-            if (ok) {
+    if (warp == kEpiWarps) {
+        // producer: A of tile j (and B at a new problem) once the MMAs of tile j - 1 are done with
+        // the shared memory, then the MMAs of tile j into accumulator j % 2 once the epilogue has
+        // released it (tile j - 2), so they overlap the epilogue of tile j - 1
+        if (lane == 0) {
+            int cur_prob = -1;
+            uint32_t aphase = 0, bphase = 0;
+            bool ok = true, a_fly = false, b_fly = false;
+            for (int t = t_begin; t < t_end && ok; ++t) {
+                const int j = t - t_begin, b = j & 1;
+                const int arow = g.tiles[2 * t];
+                const InstDesc d = a.desc[g.row_exec[arow]];
+                const int kt = (d.dpad + kBK - 1) / kBK;
+                if (j > 0 && !mbar_wait(&acc_full[(j - 1) & 1], (uint32_t)((j - 1) >> 1) & 1u)) {
+                    ok = false;
+                    break;
+                }
+                mbar_expect_tx(&afull, (uint32_t)(kt * kAT));
+                for (int kk = 0; kk < kt; ++kk) tma_load_2d(As + (size_t)kk * kAT, &tmA, &afull, kk * kBK, arow);
+                a_fly = true;
+                if (d.prob != cur_prob) {
+                    mbar_expect_tx(&bfull, (uint32_t)(kt * kBT));
+                    const int brow0 = (int)g.brow[d.prob];
+                    for (int kk = 0; kk < kt; ++kk)
+                        tma_load_2d(Bs + (size_t)kk * kBT, &tmB, &bfull, kk * kBK, brow0);
+                    b_fly = true;
+                    cur_prob = d.prob;
+                }
+                ok = mbar_wait(&afull, aphase);
+                aphase ^= 1u;
+                a_fly = false;
+                if (ok && b_fly) {
+                    ok = mbar_wait(&bfull, bphase);
+                    bphase ^= 1u;
+                    b_fly = false;
+                }
+                if (ok && j >= 2) ok = mbar_wait(&acc_empty[b], (uint32_t)((j - 2) >> 1) & 1u);
+                if (!ok) break;
                 tc_fence_after();
+                const uint32_t dacc = taddr + (uint32_t)(b * kBN);
                 for (int kk = 0; kk < kt; ++kk) {
                     const uint64_t ad = sdesc_sw128(smem_u32(As + (size_t)kk * kAT));
                     const uint64_t bd = sdesc_sw128(smem_u32(Bs + (size_t)kk * kBT));
 #pragma unroll
-                    for (int j = 0; j < kBK / 16; ++j)
-                        mma_bf16(taddr, ad + 2 * j, bd + 2 * j, (kk > 0 || j > 0) ? 1u : 0u);
+                    for (int q = 0; q < kBK / 16; ++q) mma_bf16(dacc, ad + 2 * q, bd + 2 * q, (kk > 0 || q > 0) ? 1u : 0u);
                 }
-                mma_commit(&mma_done);
-            } else {
-                set_status(a.status, kStatusTimeout);
-                abort_s = 1;
+                mma_commit(&acc_full[b]);
             }
+            if (!ok) set_status(a.status, kStatusTimeout);
+            // leave with no copy or MMA of this CTA in flight (bounded waits)
+            if (a_fly) mbar_wait(&afull, aphase);
+            if (b_fly) mbar_wait(&bfull, bphase);
+            mma_commit(&drain);
+            mbar_wait(&drain, 0u);
         }
-        cur_prob = d.prob;
-
-        // 2. epilogue: warp w reads TMEM lanes 32 (w % 4).. and column part w / 4
+        __syncwarp();
+    } else {
+        // epilogue warps: warp w reads TMEM lanes 32 (w % 4).. and column part w / 4
         const int qd = warp & 3, prt = warp >> 2;
         const int row = 32 * qd + lane;
-        ObjR acc;
-        {
-            const bool got = __all_sync(kFull, mbar_wait(&mma_done, mphase) ? 1 : 0) != 0;
-            if (!got && lane == 0) {
-                set_status(a.status, kStatusTimeout);
-                abort_s = 1;
-            }
+        for (int t = t_begin; t < t_end; ++t) {
+            const int j = t - t_begin, b = j & 1;
+            const int arow = g.tiles[2 * t], nr = g.tiles[2 * t + 1];
+            const InstDesc d = a.desc[g.row_exec[arow]];  // dim, objective and problem of every row of the tile
+            ObjR acc;
+            const bool got = __all_sync(kFull, mbar_wait(&acc_full[b], (uint32_t)(j >> 1) & 1u) ? 1 : 0) != 0;
             tc_fence_after();
             constexpr int kBpp = kBN / 32 / kParts;  // 32-column blocks per part
             float zf = 0.f, q1 = 0.f, qrun = 0.f;
@@ -387,15 +406,15 @@ __global__ void __launch_bounds__(kSelThreads, 1) k_tc_sel(const __grid_constant
                     const int col0 = 32 * pb;
                     if (col0 >= d.dim) break;  // uniform across the warp
                     float v[32];
-                    tmem_ld32(taddr + ((uint32_t)(32 * qd) << 16) + (uint32_t)col0, v);
+                    tmem_ld32(taddr + ((uint32_t)(32 * qd) << 16) + (uint32_t)(b * kBN + col0), v);
                     if (prt) {
                         if (nb == 0) zf = v[0];
                         const int mcols = min(32, d.dim - col0);
                         if (d.obj == kSchwefel12) {
 #pragma unroll
-                            for (int j = 0; j < 32; ++j)
-                                if (j < mcols) {
-                                    qrun += v[j];
+                            for (int q = 0; q < 32; ++q)
+                                if (q < mcols) {
+                                    qrun += v[q];
                                     q1 += qrun;
                                 }
                         }
@@ -405,50 +424,56 @@ __global__ void __launch_bounds__(kSelThreads, 1) k_tc_sel(const __grid_constant
                 }
             }
             tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {  // this warp has read the accumulator: the producer may reuse it
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[b])) : "memory");
+                if (!got) {
+                    set_status(a.status, kStatusTimeout);
+                    ep_abort_s = 1;
+                }
+            }
             if (prt) {
                 float* sl = part + ((size_t)(prt - 1) * kRows + row) * 8;
                 *reinterpret_cast<float4*>(sl) = make_float4(acc.s0, acc.s1, acc.prev, acc.pre);
                 *reinterpret_cast<float4*>(sl + 4) = make_float4(zf, q1, __int_as_float(nb), 0.f);
             }
-        }
-        mphase ^= 1u;
-        if (tid == 0) nacc_s = 0;
-        __syncthreads();
+            if (tid == 0) nacc_s = 0;
+            epi_sync();
+            if (ep_abort_s) break;  // uniform: read after the barrier
 
-        // 3. selection: the part-0 thread of each row; clear acceptances are listed for the row copy,
-        // near ties go to the problem's tie list (k_tc_ties2)
-        if (prt == 0 && row < nr && !abort_s) {
-            for (int j = 0; j < kParts - 1; ++j) {
-                const float* sl = part + ((size_t)j * kRows + row) * 8;
-                const float4 x0 = *reinterpret_cast<const float4*>(sl), x1 = *reinterpret_cast<const float4*>(sl + 4);
-                ObjR rb;
-                rb.s0 = x0.x;
-                rb.s1 = x0.y;
-                rb.prev = x0.z;
-                rb.pre = x0.w;
-                rb.first = __float_as_int(x1.z) == 0;
-                obj_compose(d.obj, acc, rb, x1.x, x1.y, __float_as_int(x1.z));
-            }
-            const float fn = nan_to_inf(acc.finish(d.obj, d.dim));
-            const int k = g.row_exec[arow + row];
-            const InstDesc e = a.desc[k];
-            if (load_strat(a.theta + 6 * k, e.np).ok) {  // rows of an invalid theta stay as they are
-                const int fidx = e.fit_off + (arow + row - e.tc_row);
-                const float fx = a.fit[fidx];
-                if (near_tie(fn, fx, tie_band(d.dim))) {
-                    const int tp = g.prob_tp[d.prob];
-                    const int q = g.tp_row0[tp] + atomicAdd(&g.tie_cnt[tp], 1);
-                    g.tie_list[q] = fidx;
-                    g.tie_off[q] = e.pop_off + (long long)(arow + row - e.tc_row) * d.dpad;
-                } else if (fn <= fx) {
-                    acc_row[atomicAdd(&nacc_s, 1)] = row;
-                    a.fit[fidx] = fn;
+            // selection: the part-0 thread of each row; clear acceptances are listed for the row
+            // copy, near ties go to the problem's tie list (k_tc_ties2)
+            if (prt == 0 && row < nr) {
+                for (int q = 0; q < kParts - 1; ++q) {
+                    const float* sl = part + ((size_t)q * kRows + row) * 8;
+                    const float4 x0 = *reinterpret_cast<const float4*>(sl), x1 = *reinterpret_cast<const float4*>(sl + 4);
+                    ObjR rb;
+                    rb.s0 = x0.x;
+                    rb.s1 = x0.y;
+                    rb.prev = x0.z;
+                    rb.pre = x0.w;
+                    rb.first = __float_as_int(x1.z) == 0;
+                    obj_compose(d.obj, acc, rb, x1.x, x1.y, __float_as_int(x1.z));
+                }
+                const float fn = nan_to_inf(acc.finish(d.obj, d.dim));
+                const int k = g.row_exec[arow + row];
+                const InstDesc e = a.desc[k];
+                if (load_strat(a.theta + 6 * k, e.np).ok) {  // rows of an invalid theta stay as they are
+                    const int fidx = e.fit_off + (arow + row - e.tc_row);
+                    const float fx = a.fit[fidx];
+                    if (near_tie(fn, fx, tie_band(d.dim))) {
+                        const int tp = g.prob_tp[d.prob];
+                        const int q = g.tp_row0[tp] + atomicAdd(&g.tie_cnt[tp], 1);
+                        g.tie_list[q] = fidx;
+                        g.tie_off[q] = e.pop_off + (long long)(arow + row - e.tc_row) * d.dpad;
+                    } else if (fn <= fx) {
+                        acc_row[atomicAdd(&nacc_s, 1)] = row;
+                        a.fit[fidx] = fn;
+                    }
                 }
             }
-        }
-        __syncthreads();
-        // accepted rows into the population, the whole CTA copying float4s
-        {
+            epi_sync();
+            // accepted rows into the population, the 16 warps copying float4s
             const int f4 = d.dpad >> 2, n = nacc_s * f4;
             for (int e2 = tid; e2 < n; e2 += kSelThreads) {
                 const int q = e2 / f4, c4 = e2 - q * f4;
@@ -457,26 +482,14 @@ __global__ void __launch_bounds__(kSelThreads, 1) k_tc_sel(const __grid_constant
                 const long long off = e.pop_off + (long long)(gr - e.tc_row) * d.dpad + 4 * c4;
                 *reinterpret_cast<float4*>(a.pop + off) = __ldg(reinterpret_cast<const float4*>(g.uscr + off));
             }
+            epi_sync();  // acc_row and the exchange area are reused by the next tile
         }
-
-        if (abort_s) break;  // uniform: read after a barrier
-        // the next tile's loads overwrite A and TMEM only after this barrier
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-    }
-    // leave with no copy or MMA of this CTA in flight (bounded waits)
-    if (issuer) {
-        if (a_in_flight) mbar_wait(&afull, aphase);
-        if (b_in_flight) mbar_wait(&bfull, bphase);
-        mma_commit(&drain);
-        mbar_wait(&drain, 0u);
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kBN) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(2 * kBN) : "memory");
 }
 
 // -------------------------------------------------------------- k_tc_ties2
@@ -738,7 +751,7 @@ cudaError_t launch_tc_fused_generation(const StepArgs& a, const TcPlan& p, cudaS
     cudaError_t e = cudaFuncSetAttribute(k_tc_sel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = p.n_tiles < p.gen_ctas ? p.n_tiles : p.gen_ctas;
-    k_tc_sel<<<grid, kSelThreads, smem, st>>>(p.mapA, p.mapB, g);
+    k_tc_sel<<<grid, kSelThreads + 32, smem, st>>>(p.mapA, p.mapB, g);
     if (ev) cudaEventRecord(ev[3], st);
     TieArgs ta;
     ta.a = a;
