@@ -400,8 +400,6 @@ __global__ void __launch_bounds__(kT3Threads) k_tc_trial3(StepArgs a, const int*
     }
 }
 
-size_t trial3_smem(int np, int dpad) { return (size_t)np * dpad * sizeof(float) + (size_t)kGFields * np * sizeof(int); }
-
 // --------------------------------------------------------------- k_tc_sel
 struct SelArgs {
     StepArgs a;
@@ -856,6 +854,8 @@ constexpr size_t kTieSmem = 16 + kTie2Size;
 }  // namespace
 
 bool tc_fused_fits(int kp) { return kp <= kMaxKt * kBK && sel_smem(kp / kBK) <= 227 * 1024; }
+
+size_t trial3_smem(int np, int dpad) { return (size_t)np * dpad * sizeof(float) + (size_t)kGFields * np * sizeof(int); }
 
 cudaError_t launch_tc_fused_generation(const StepArgs& a, const TcPlan& p, cudaStream_t st, cudaEvent_t* ev) {
     if (ev) cudaEventRecord(ev[0], st);
