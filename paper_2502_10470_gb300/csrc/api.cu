@@ -466,13 +466,7 @@ metade_status setup_tc(metade_ctx* c) {
     // commit, near ties)
     t.fused = (c->prec == METADE_BF16 && !c->tie_fp64 && !c->tc_unfused && tc_fused_fits(tc_kp)) ? 1 : 0;
     t.gen_ctas = std::max(1, device_sms());
-    // the executor-resident trial kernel when the largest population fits in shared memory
-    t.trial3_smem = 0;
-    if (t.fused) {
-        size_t m = 0;
-        for (int k : tc_execs) m = std::max(m, trial3_smem(c->hdesc[k].np, c->hdesc[k].dpad));
-        if (m <= kSmemLimit) t.trial3_smem = m;
-    }
+
     // a tie keeps four rows of max_dpad in shared memory (FP64 with tie_fp64)
     if ((size_t)4 * tc_max_dpad * (c->tie_fp64 ? sizeof(double) : sizeof(float)) > kSmemLimit)
         return METADE_EUNSUPPORTED;

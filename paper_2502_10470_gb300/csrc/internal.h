@@ -136,7 +136,6 @@ struct TcPlan {
     int* tie_cnt;            // device [n_tp]: near ties listed per problem
     int* chunk_ctr;          // device counter of k_tc_ties2's chunk queue
     int gen_ctas;            // CTAs of k_tc_sel (one per SM)
-    size_t trial3_smem;      // > 0: k_tc_trial3 (population in shared memory) with this much, else k_tc_trial2
     CUtensorMap mapA, mapB, mapAlo, mapBlo;
 };
 bool tc_make_map(CUtensorMap* map, const void* base, long long rows, int kp, int box_rows, int esz);
@@ -159,8 +158,6 @@ cudaError_t launch_rot_simt(const InstDesc* desc, const int* tiles, int n_tiles,
 // (near ties).  ev (may be null): five events, before each launch and after
 // the last.
 bool tc_fused_fits(int kp);
-// dynamic shared memory of the executor-resident trial kernel for an executor of np x dpad
-size_t trial3_smem(int np, int dpad);
 cudaError_t launch_tc_fused_generation(const StepArgs& a, const TcPlan& p, cudaStream_t st,
                                        cudaEvent_t* ev = nullptr);
 // ev (may be null): six events recorded before the prologue, trial, GEMM,

@@ -271,135 +271,6 @@ __global__ void __launch_bounds__(kTThreads, 4) k_tc_trial2(StepArgs a, const in
     }
 }
 
-// ------------------------------------------------------------ k_tc_trial3
-// Record fields of k_tc_trial3, [field][np]: the row's parents and draws
-// (the strategy is the executor's, held in registers).
-enum { G_IBL, G_IBR, G_P0, G_P1, G_P2, G_P3, G_M0, G_M1, G_M2, G_M3, G_JR, G_NS, G_L, G_K, kGFields };
-constexpr int kT3Threads = 512;
-
-// One executor per CTA, its whole population staged in shared memory by
-// coalesced float4 loads, so every random parent row of every trial is read
-// from shared memory instead of L2 (the gathers of k_tc_trial2 are about
-// (3 + 2 dn) x the population per generation).  Draws: a lane per row (all
-// 16 warps), then the exponential lengths of each warp's 32 rows four at a
-// time with the warp's 32 lanes.  Trial: warp w takes rows 8 u + lane / 4
-// for u = w, w + 16, ... and, per row block, every 16-element K block (lane
-// % 4 the chunk); the arithmetic is trial_chunk's.  Dynamic shared memory:
-// np x dpad floats of population, then kGFields x np ints.
-__global__ void __launch_bounds__(kT3Threads) k_tc_trial3(StepArgs a, const int* __restrict__ execs,
-                                                          const int* __restrict__ topk_all, float* uscr,
-                                                          uint8_t* aq, int kp) {
-    extern __shared__ __align__(16) float sx[];
-    const int k = execs[blockIdx.x];
-    const InstDesc d = a.desc[k];
-    const Strat s = load_strat(a.theta + 6 * k, d.np);
-    if (!s.ok) return;  // k_tc_rank latched the status; k_tc_sel leaves these rows alone
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int np = d.np, dp = d.dpad, dim = d.dim;
-    int* rec = reinterpret_cast<int*>(sx + (size_t)np * dp);
-    const uint32_t epoch = a.epoch_dev ? *a.epoch_dev : a.epoch;
-    const float* gpop = a.pop + d.pop_off;
-    const int f4 = dp >> 2;
-    for (int e = tid; e < np * f4; e += kT3Threads)
-        reinterpret_cast<float4*>(sx)[e] = __ldg(reinterpret_cast<const float4*>(gpop) + e);
-    // draws, a lane per row
-    const int* topk = topk_all + d.fit_off;
-    for (int i = tid; i < np; i += kT3Threads) {
-        const Ctr c = make_ctr(a.key, (uint32_t)d.stream, a.gen0, (uint32_t)i, epoch);
-        Indiv v;
-        indiv_setup(s, c, i, np, dim, d.kp, topk, topk[0], v);
-        rec[G_IBL * np + i] = v.ibl;
-        rec[G_IBR * np + i] = v.ibr;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            rec[(G_P0 + q) * np + i] = q < s.dn ? diff_plus(v, s.a, q) : 0;
-            rec[(G_M0 + q) * np + i] = q < s.dn ? diff_minus(v, s.a, q) : 0;
-        }
-        rec[G_JR * np + i] = v.jrand;
-        rec[G_NS * np + i] = v.nstart;
-        rec[G_K * np + i] = (int)v.kraw;
-    }
-    if (s.cs == 2) {  // exponential lengths: L = 1 + min(t*, D - 1), t* the first uniform U_t not below CR
-        for (int i0 = 32 * warp; i0 < np; i0 += kT3Threads) {
-            for (int q0 = 0; q0 < 32 && i0 + q0 < np; q0 += 4) {
-                int Ls[4] = {0, 0, 0, 0};
-                for (int base = 0; base == 0 || base < dim - 1; base += 128) {  // t = base + 4 lane + word
-                    uint4 w4[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {  // four rows' Philox chains interleave
-                        w4[q] = make_uint4(0, 0, 0, 0);
-                        if (i0 + q0 + q < np && Ls[q] == 0) {
-                            const Ctr c = make_ctr(a.key, (uint32_t)d.stream, a.gen0, (uint32_t)(i0 + q0 + q), epoch);
-                            w4[q] = c.slot(4 + (uint32_t)((base >> 2) + lane));
-                        }
-                    }
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        if (i0 + q0 + q >= np || Ls[q] != 0) continue;  // warp-uniform
-                        int first = 4;
-#pragma unroll
-                        for (int wq = 3; wq >= 0; --wq) {
-                            const int t = base + 4 * lane + wq;
-                            if (t <= dim - 2 && (word_of(w4[q], wq) >> 8) >= s.cri) first = wq;
-                        }
-                        const unsigned fails = __ballot_sync(kFull, first < 4);
-                        if (fails) {
-                            const int fl = __ffs(fails) - 1;
-                            Ls[q] = 1 + base + 4 * fl + __shfl_sync(kFull, first, fl);
-                        } else if (base + 128 >= dim - 1) {
-                            Ls[q] = dim;  // every uniform below CR: the whole row
-                        }
-                    }
-                }
-                if (lane < 4 && i0 + q0 + lane < np) rec[G_L * np + i0 + q0 + lane] = Ls[lane];
-            }
-        }
-    }
-    __syncthreads();
-    // trial rows and operand rows
-    const int nchb = ((dp + kBK - 1) / kBK) * (kBK / 16);  // blocks of 4 chunks, up to the K extent
-    const float* o = a.shift + d.shift_off;
-    for (int rb = warp; rb * 8 < np; rb += kT3Threads / 32) {
-        const int i = 8 * rb + (lane >> 2);
-        if (i >= np) continue;
-        const float* xl = sx + rec[G_IBL * np + i] * dp;
-        const float* xr = sx + rec[G_IBR * np + i] * dp;
-        const float* xi = sx + i * dp;
-        int op[4], om[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            op[q] = rec[(G_P0 + q) * np + i] * dp;
-            om[q] = rec[(G_M0 + q) * np + i] * dp;
-        }
-        const int jr = rec[G_JR * np + i], ns = rec[G_NS * np + i];
-        const int L = s.cs == 2 ? rec[G_L * np + i] : 0;
-        const float K = (float)(uint32_t)rec[G_K * np + i] * (1.0f / 16777216.0f);
-        const Ctr c = make_ctr(a.key, (uint32_t)d.stream, a.gen0, (uint32_t)i, epoch);
-        float* U = uscr + d.pop_off + (long long)i * dp;
-        uint8_t* arow = aq + (size_t)(d.tc_row + i) * kp * 2;
-        for (int cb = 0; cb < nchb; ++cb) {
-            const int j4 = 4 * (4 * cb + (lane & 3));
-            float dd[4] = {0.f, 0.f, 0.f, 0.f};
-            if (j4 < dp) {
-                const float4 av = *reinterpret_cast<const float4*>(xl + j4);
-                const float4 bv = *reinterpret_cast<const float4*>(xr + j4);
-                const float4 xv = *reinterpret_cast<const float4*>(xi + j4);
-                float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
-                for (int q = 0; q < s.dn; ++q) {
-                    const float4 p = *reinterpret_cast<const float4*>(sx + op[q] + j4);
-                    const float4 m = *reinterpret_cast<const float4*>(sx + om[q] + j4);
-                    sum.x += p.x - m.x; sum.y += p.y - m.y; sum.z += p.z - m.z; sum.w += p.w - m.w;
-                }
-                const uint4 w = s.cs == 1 ? c.slot(4 + (uint32_t)(j4 >> 2)) : make_uint4(0, 0, 0, 0);
-                float uo[4];
-                trial_chunk(s, K, jr, ns, L, dim, j4, av, bv, xv, sum, w, o, a.lo, a.hi, uo, dd);
-                *reinterpret_cast<float4*>(U + j4) = make_float4(uo[0], uo[1], uo[2], uo[3]);
-            }
-            *reinterpret_cast<uint2*>(arow + (size_t)j4 * 2) = pack_bf16x4(dd);
-        }
-    }
-}
-
 // --------------------------------------------------------------- k_tc_sel
 struct SelArgs {
     StepArgs a;
@@ -855,22 +726,12 @@ constexpr size_t kTieSmem = 16 + kTie2Size;
 
 bool tc_fused_fits(int kp) { return kp <= kMaxKt * kBK && sel_smem(kp / kBK) <= 227 * 1024; }
 
-size_t trial3_smem(int np, int dpad) { return (size_t)np * dpad * sizeof(float) + (size_t)kGFields * np * sizeof(int); }
-
 cudaError_t launch_tc_fused_generation(const StepArgs& a, const TcPlan& p, cudaStream_t st, cudaEvent_t* ev) {
     if (ev) cudaEventRecord(ev[0], st);
     k_tc_rank<<<p.n_exec, 256, 0, st>>>(a, p.execs, p.topk_all, p.next_tile, p.chunk_ctr, p.tie_cnt, p.n_tp);
     if (ev) cudaEventRecord(ev[1], st);
-    if (p.trial3_smem > 0) {  // every executor's population fits in shared memory
-        cudaError_t e3 = cudaFuncSetAttribute(k_tc_trial3, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)p.trial3_smem);
-        if (e3 != cudaSuccess) return e3;
-        k_tc_trial3<<<p.n_exec, kT3Threads, p.trial3_smem, st>>>(a, p.execs, p.topk_all, p.uscr,
-                                                                 static_cast<uint8_t*>(p.aq), p.kp);
-    } else {
-        k_tc_trial2<<<(p.n_rows + kTRows - 1) / kTRows, kTThreads, 0, st>>>(a, p.row_exec, p.n_rows, p.topk_all,
-                                                                           p.uscr, static_cast<uint8_t*>(p.aq), p.kp);
-    }
+    k_tc_trial2<<<(p.n_rows + kTRows - 1) / kTRows, kTThreads, 0, st>>>(a, p.row_exec, p.n_rows, p.topk_all, p.uscr,
+                                                                       static_cast<uint8_t*>(p.aq), p.kp);
     if (ev) cudaEventRecord(ev[2], st);
     SelArgs g;
     g.a = a;
