@@ -225,9 +225,7 @@ metade_status build_plan(metade_ctx* c) {
         b.plan.dmax = dm;
         b.plan.threads = std::min(256, std::max(32, (mnp + 31) / 32 * 32));
         b.plan.grid = (int)small[dm].size();
-        // cache every row's z when it still fits: a near tie then rotates u - x only
-        b.plan.zcache = fused_smem_small(dm, mnp, true) <= kSmemLimit ? 1 : 0;
-        b.plan.smem = fused_smem_small(dm, mnp, b.plan.zcache != 0);
+        b.plan.smem = fused_smem_small(dm, mnp);
         b.plan.rot_smem = 0;
         b.plan.pop_smem = 1;
         b.plan.max_np = mnp;
@@ -249,7 +247,6 @@ metade_status build_plan(metade_ctx* c) {
         }
         Bucket b;
         b.plan.kind = 3;
-        b.plan.zcache = 0;
         b.plan.dmax = 0;
         b.plan.threads = 256;
         b.plan.grid = (int)tv.size();
@@ -273,7 +270,6 @@ metade_status build_plan(metade_ctx* c) {
         }
         Bucket b;
         b.plan.kind = 1;
-        b.plan.zcache = 0;
         b.plan.dmax = 0;
         b.plan.threads = 256;
         b.plan.grid = (int)general.size();
@@ -1196,14 +1192,14 @@ metade_status metade_plan_info(const metade_ctx* c, char* buf, size_t len) {
         char tmp[256];
         snprintf(tmp, sizeof(tmp),
                  "%s{\"kernel\": \"%s\", \"dmax\": %d, \"threads\": %d, \"grid\": %d, \"smem\": %zu, "
-                 "\"rot_smem\": %d, \"pop_smem\": %d, \"zcache\": %d, \"executors\": %d",
+                 "\"rot_smem\": %d, \"pop_smem\": %d, \"executors\": %d",
                  b ? ", " : "",
                  k.plan.kind == 0   ? "fused_small"
                  : k.plan.kind == 3 ? (k.plan.rot_smem ? "fused_tile" : "fused_tile_stream")
                                     : "fused_general",
                  k.plan.dmax,
                  k.plan.threads,
-                 k.plan.grid, k.plan.smem, k.plan.rot_smem, k.plan.pop_smem, k.plan.zcache, k.n_work);
+                 k.plan.grid, k.plan.smem, k.plan.rot_smem, k.plan.pop_smem, k.n_work);
         s += tmp;
         if (!k.tuned.empty()) s += ", \"autotune_ms\": {" + k.tuned + "}";
         s += "}";

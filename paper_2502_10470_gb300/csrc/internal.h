@@ -73,11 +73,10 @@ struct FusedPlan {
     int rot_smem;  // general, tile: R^T staged in shared memory (tile: else streamed by chunks)
     int pop_smem;  // small: the population resident in shared memory for all fused generations
     int max_np, max_dpad;  // general: bucket maxima the shared layout is cut for
-    int zcache;    // small: z = R (x - o) of every row cached in shared memory (near ties rotate u - x only)
 };
 cudaError_t launch_fused(const StepArgs& a, const int* work, int n_work, const FusedPlan& p, float* u_scratch,
                          cudaStream_t st);
-size_t fused_smem_small(int dmax, int max_np, bool zcache = false);
+size_t fused_smem_small(int dmax, int max_np);
 size_t fused_smem_general(int max_np, int max_dpad, int threads, bool rot_in_smem);
 int small_dmax_for(int dim);  // 0 when the small kernel does not apply
 size_t fused_smem_tile(int max_np, int max_dpad, int threads, bool rot_smem);

@@ -494,70 +494,6 @@ __device__ __noinline__ float diff_small(int obj, int dim, const float* u, const
     return diff_finish(obj, acc, dim);
 }
 
-// The same difference as diff_small with z = R (x - o) taken from the cache
-// of the stored row (written when the row was evaluated, by the same fma
-// chain, so it is bit-identical to recomputing it): one rotation instead of
-// two.
-template <int DMAX>
-__device__ __noinline__ float diff_small_zc(int obj, int dim, const float* u, const float* x, const float* zx,
-                                            const float* R) {
-    float dl[DMAX];
-#pragma unroll
-    for (int c4 = 0; c4 < DMAX / 4; ++c4) {  // whole chunks below dim; padding columns are zero
-        float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (4 * c4 < dim) {
-            const float4 xv = reinterpret_cast<const float4*>(x)[c4], uv = reinterpret_cast<const float4*>(u)[c4];
-            b = make_float4(uv.x - xv.x, uv.y - xv.y, uv.z - xv.z, uv.w - xv.w);
-        }
-        dl[4 * c4] = b.x; dl[4 * c4 + 1] = b.y; dl[4 * c4 + 2] = b.z; dl[4 * c4 + 3] = b.w;
-    }
-    DiffAcc acc;
-    diff_init(acc);
-    for (int r = 0; r < dim; ++r) {
-        const float4* Rr = reinterpret_cast<const float4*>(R + r * DMAX);
-        float dz = 0.f;
-#pragma unroll
-        for (int c4 = 0; c4 < DMAX / 4; ++c4) {
-            const float4 q = Rr[c4];
-            dz = fmaf(q.x, dl[4 * c4], dz);
-            dz = fmaf(q.y, dl[4 * c4 + 1], dz);
-            dz = fmaf(q.z, dl[4 * c4 + 2], dz);
-            dz = fmaf(q.w, dl[4 * c4 + 3], dz);
-        }
-        diff_push(obj, acc, zx[r], dz);
-    }
-    return diff_finish(obj, acc, dim);
-}
-
-// z = R (x - o) of one stored row into zx[0..dim), by one thread: the fma
-// chain of diff_small's z (and of small_eval's, for a trial that becomes x).
-template <int DMAX>
-__device__ __forceinline__ void small_z(int dim, const float* x, const float* o, const float* R, float* zx) {
-    float dx[DMAX];
-#pragma unroll
-    for (int c4 = 0; c4 < DMAX / 4; ++c4) {
-        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (4 * c4 < dim) {
-            const float4 xv = reinterpret_cast<const float4*>(x)[c4], ov = reinterpret_cast<const float4*>(o)[c4];
-            a = make_float4(xv.x - ov.x, xv.y - ov.y, xv.z - ov.z, xv.w - ov.w);
-        }
-        dx[4 * c4] = a.x; dx[4 * c4 + 1] = a.y; dx[4 * c4 + 2] = a.z; dx[4 * c4 + 3] = a.w;
-    }
-    for (int r = 0; r < dim; ++r) {
-        const float4* Rr = reinterpret_cast<const float4*>(R + r * DMAX);
-        float z = 0.f;
-#pragma unroll
-        for (int c4 = 0; c4 < DMAX / 4; ++c4) {
-            const float4 q = Rr[c4];
-            z = fmaf(q.x, dx[4 * c4], z);
-            z = fmaf(q.y, dx[4 * c4 + 1], z);
-            z = fmaf(q.z, dx[4 * c4 + 2], z);
-            z = fmaf(q.w, dx[4 * c4 + 3], z);
-        }
-        zx[r] = z;
-    }
-}
-
 // FP64 re-evaluation of a near tie by one thread, kept out of line: it is
 // rare, and inlined it would spread the fused loop's code.  Returns the
 // decision and, when taken, the stored value min(f32(f64 f(u)), f(x)) in fn.
@@ -572,9 +508,8 @@ __device__ __noinline__ bool tie_fp64_small(int obj, int dim, int dmax, const fl
 // f(u) of one individual from z = R (u - o), rows four at a time, the
 // objective a template parameter: one objective dispatch per individual
 // rather than one per four rows (1% faster on the small-D kernel).
-template <int DMAX, int OBJ, bool ZC>
-__device__ __forceinline__ float small_eval(int dim, const float* R, const float (&dreg)[DMAX], const float* isq,
-                                            float* zout) {
+template <int DMAX, int OBJ>
+__device__ __forceinline__ float small_eval(int dim, const float* R, const float (&dreg)[DMAX], const float* isq) {
     ObjR acc;
     int r = 0;
     for (; r + 4 <= dim; r += 4) {
@@ -593,12 +528,6 @@ __device__ __forceinline__ float small_eval(int dim, const float* R, const float
             z3 = fmaf(q3.x, d0, z3); z3 = fmaf(q3.y, d1, z3); z3 = fmaf(q3.z, d2, z3); z3 = fmaf(q3.w, d3, z3);
         }
         acc.push4_t<OBJ>(z0, z1, z2, z3, isq + r);
-        if (ZC) {
-            zout[r] = z0;
-            zout[r + 1] = z1;
-            zout[r + 2] = z2;
-            zout[r + 3] = z3;
-        }
     }
     for (; r < dim; ++r) {
         const float4* Rr = reinterpret_cast<const float4*>(R + r * DMAX);
@@ -612,7 +541,6 @@ __device__ __forceinline__ float small_eval(int dim, const float* R, const float
             z = fmaf(rr.w, dreg[4 * c4 + 3], z);
         }
         acc.push_t<OBJ>(z, isq[r]);
-        if (ZC) zout[r] = z;
     }
     return acc.finish(OBJ, dim);
 }
@@ -621,10 +549,7 @@ __host__ __device__ inline int small_stride(int dpad) { return ((dpad >> 2) & 1)
 
 // One executor, all fused generations, everything resident in shared memory;
 // the objective is a template parameter so the hot loop has no objective branch.
-// ZC: z = R (x - o) of every stored row is cached in shared memory (and the
-// trial's z kept beside it), so a near tie's FP32 difference form needs only
-// the rotation of u - x.
-template <int DMAX, bool ZC>
+template <int DMAX>
 __device__ __forceinline__ void small_executor(const StepArgs& a, int k, const InstDesc& d, const Strat& s,
                                                float* sm) {
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -645,9 +570,6 @@ __device__ __forceinline__ void small_executor(const StepArgs& a, int k, const I
     float* candf = reinterpret_cast<float*>(cand + np);
     int* inpool = reinterpret_cast<int*>(candf + np);
     int* ncand = inpool + np;
-    // z caches (ZC): stored rows, then trials, [np][DMAX] each, 16-byte aligned
-    float* Zx = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(ncand + 1) + 15) & ~(uintptr_t)15);
-    float* Zu = Zx + (size_t)np * DMAX;
     const uint32_t epoch = a.epoch_dev ? *a.epoch_dev : a.epoch;
     float* gpop = a.pop + d.pop_off;
     const int chunks = dp >> 2;
@@ -671,11 +593,6 @@ __device__ __forceinline__ void small_executor(const StepArgs& a, int k, const I
     }
     if (tid == 0) *ncand = 0;
     __syncthreads();
-    if (ZC && !a.tie_fp64) {
-        for (int i = tid; i < np; i += nt) small_z<DMAX>(dim, X + i * ds, o, R, Zx + (size_t)i * DMAX);
-        __syncthreads();
-    }
-    const bool zc = ZC && !a.tie_fp64;
     const bool pb = s.uses_pbest();
     for (int g = 0; g < a.n_gens; ++g) {
         const uint32_t gen = a.gen0 + (uint32_t)g;
@@ -716,14 +633,13 @@ __device__ __forceinline__ void small_executor(const StepArgs& a, int k, const I
             float dreg[DMAX];
             thread_trial<DMAX>(s, c, v, i, dim, ds, L, X, o, a.lo, a.hi, U, dreg);
             float fv;
-            float* zo = Zu + (size_t)i * DMAX;
             switch (d.obj) {
-            case kSphere: fv = small_eval<DMAX, kSphere, ZC>(dim, R, dreg, isq, zo); break;
-            case kRosenbrock: fv = small_eval<DMAX, kRosenbrock, ZC>(dim, R, dreg, isq, zo); break;
-            case kRastrigin: fv = small_eval<DMAX, kRastrigin, ZC>(dim, R, dreg, isq, zo); break;
-            case kGriewank: fv = small_eval<DMAX, kGriewank, ZC>(dim, R, dreg, isq, zo); break;
-            case kAckley: fv = small_eval<DMAX, kAckley, ZC>(dim, R, dreg, isq, zo); break;
-            default: fv = small_eval<DMAX, kSchwefel12, ZC>(dim, R, dreg, isq, zo); break;
+            case kSphere: fv = small_eval<DMAX, kSphere>(dim, R, dreg, isq); break;
+            case kRosenbrock: fv = small_eval<DMAX, kRosenbrock>(dim, R, dreg, isq); break;
+            case kRastrigin: fv = small_eval<DMAX, kRastrigin>(dim, R, dreg, isq); break;
+            case kGriewank: fv = small_eval<DMAX, kGriewank>(dim, R, dreg, isq); break;
+            case kAckley: fv = small_eval<DMAX, kAckley>(dim, R, dreg, isq); break;
+            default: fv = small_eval<DMAX, kSchwefel12>(dim, R, dreg, isq); break;
             }
             fu[i] = nan_to_inf(fv);
         }
@@ -748,8 +664,7 @@ __device__ __forceinline__ void small_executor(const StepArgs& a, int k, const I
                 if (a.tie_fp64) {
                     take = tie_fp64_small(d.obj, dim, DMAX, U + i * ds, X + i * ds, o, R, fx, fn);
                 } else {
-                    const float df = zc ? diff_small_zc<DMAX>(d.obj, dim, U + i * ds, X + i * ds, Zx + (size_t)i * DMAX, R)
-                                        : diff_small<DMAX>(d.obj, dim, U + i * ds, X + i * ds, o, R);
+                    const float df = diff_small<DMAX>(d.obj, dim, U + i * ds, X + i * ds, o, R);
                     take = df <= 0.0f;
                     if (take) fn = fx + df;
                 }
@@ -766,10 +681,6 @@ __device__ __forceinline__ void small_executor(const StepArgs& a, int k, const I
                     *reinterpret_cast<float4*>(X + i * ds + 4 * q) =
                         *reinterpret_cast<const float4*>(U + i * ds + 4 * q);
                 f[i] = fn;
-                if (zc)  // the new row's z (the trial's, by the same chain)
-                    for (int q = 0; q < DMAX / 4; ++q)
-                        reinterpret_cast<float4*>(Zx + (size_t)i * DMAX)[q] =
-                            reinterpret_cast<const float4*>(Zu + (size_t)i * DMAX)[q];
             }
         }
         __syncthreads();
@@ -786,7 +697,7 @@ __device__ __forceinline__ void small_executor(const StepArgs& a, int k, const I
     __syncthreads();
 }
 
-template <int DMAX, bool ZC>
+template <int DMAX>
 __global__ void __launch_bounds__(256, 2) k_fused_small(StepArgs a, const int* __restrict__ work, int n_work) {
     extern __shared__ __align__(16) float sm[];
     for (int w = blockIdx.x; w < n_work; w += gridDim.x) {
@@ -797,7 +708,7 @@ __global__ void __launch_bounds__(256, 2) k_fused_small(StepArgs a, const int* _
             if (threadIdx.x == 0) set_status(a.status, 1);
             continue;
         }
-        small_executor<DMAX, ZC>(a, k, d, s, sm);
+        small_executor<DMAX>(a, k, d, s, sm);
     }
 }
 
@@ -812,11 +723,10 @@ int small_dmax_for(int dim) {
     return 0;
 }
 
-size_t fused_smem_small(int dmax, int max_np, bool zcache) {
+size_t fused_smem_small(int dmax, int max_np) {
     const int ds = small_stride(dmax);
     return sizeof(float) * ((size_t)2 * max_np * ds + (size_t)dmax * dmax + 2 * dmax + 2 * (size_t)max_np) +
-           sizeof(int) * ((size_t)4 * max_np + 64 + 1) +
-           (zcache ? 16 + sizeof(float) * (size_t)2 * max_np * dmax : 0);
+           sizeof(int) * ((size_t)4 * max_np + 64 + 1);
 }
 
 // ---------------------------------------------- batched path, general D
@@ -935,17 +845,9 @@ size_t fused_smem_general(int max_np, int max_dpad, int threads, bool rot_in_sme
 
 template <int DMAX>
 static cudaError_t launch_small(const StepArgs& a, const int* work, int n_work, const FusedPlan& p, cudaStream_t st) {
-    if (p.zcache) {
-        cudaError_t e =
-            cudaFuncSetAttribute(k_fused_small<DMAX, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
-        if (e != cudaSuccess) return e;
-        k_fused_small<DMAX, true><<<p.grid, p.threads, p.smem, st>>>(a, work, n_work);
-    } else {
-        cudaError_t e =
-            cudaFuncSetAttribute(k_fused_small<DMAX, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
-        if (e != cudaSuccess) return e;
-        k_fused_small<DMAX, false><<<p.grid, p.threads, p.smem, st>>>(a, work, n_work);
-    }
+    cudaError_t e = cudaFuncSetAttribute(k_fused_small<DMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    if (e != cudaSuccess) return e;
+    k_fused_small<DMAX><<<p.grid, p.threads, p.smem, st>>>(a, work, n_work);
     return cudaGetLastError();
 }
 
