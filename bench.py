@@ -541,7 +541,8 @@ def run_ours(args):
     value = whole_job_rate(units, args.steps, world, total_max)
     plan = json.loads(M.metade_plan_info(b.ctx))
     kernels = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
-               for k, v in prof.items() if v[1]}
+               for k, v in prof.items() if v[1] and k != "near_ties"}
+    near_ties_per_step = prof["near_ties"][1] / args.steps  # selections decided by the near-tie path
     roof = rooflines(wl, b, plan, prof, thetas, gens, args.steps, total, clocks)
     fe = final_errors(b, wl)
     e2e = measure_e2e(b, wl, gens, og + 1, args.steps, dev, stream, world, units)
@@ -595,7 +596,7 @@ def run_ours(args):
                 "gpu_launches": launches,
                 "roofline": roof[0],
                 "roofline_by_kernel": roof[1],
-                "kernels": kernels,
+                "kernels": kernels, "near_ties_per_step": near_ties_per_step,
                 "final_error": fe,
                 "plain_fp32": plain,
                 "speedup_vs_plain": (value / plain["value"]) if plain else None,
@@ -833,6 +834,9 @@ def run_precision(args):
         rel = ((ft.double() - f64u).abs() / f64u.abs()).cpu().numpy()
         relx = ((fxp.double() - f64x).abs() / f64x.abs()).cpu().numpy()
         mism = float(((ft.double() <= fxp.double()) != (f64u <= f64x)).float().mean().item())
+        # near ties at the first generation: |f(u) - f(x)| <= band f(x), band = max(1e-6, 2^-21 sqrt(D))
+        band = max(1e-6, 2.0 ** -21 * float(np.sqrt(wl.dims().max())))
+        ties0 = float(((ft - fxp).abs() <= band * fxp).float().mean().item())
         b.set_theta(wl.theta)
         b.pop.copy_(pop0)
         b.fit.copy_(fit0)
@@ -851,15 +855,49 @@ def run_precision(args):
             ms.append((e0, e1))
         torch.cuda.synchronize()
         prof = M.metade_profile_read(b.ctx)
+        M.metade_profile(b.ctx, False)
         gen_ms = float(np.mean([a.elapsed_time(c) for a, c in ms]))
+        # from the initial state: the first 20 generations, then 180 more (one call each, L2 not flushed
+        # between the generations of a call; the state, 131 MB of population, exceeds L2), then the
+        # same 200 generations again with per-kernel events
+        runs = {}
+        for profiled in (False, True):
+            b.pop.copy_(pop0)
+            b.fit.copy_(fit0)
+            flush.zero_()
+            torch.cuda.synchronize()
+            if profiled:
+                M.metade_profile(b.ctx, True)
+                M.metade_profile_read(b.ctx)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(stream)
+            M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 0, 20, None, None)
+            ev[1].record(stream)
+            M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 20, 180, None, None)
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            runs[profiled] = (ev[0].elapsed_time(ev[1]) / 20, ev[0].elapsed_time(ev[2]) / 200,
+                              M.metade_profile_read(b.ctx) if profiled else None)
+            M.metade_profile(b.ctx, False)
+        if M.metade_sync(b.ctx) != 0:
+            raise RuntimeError("device status")
         r = {"ms_per_generation": gen_ms, "indiv_gens_per_s": n / (gen_ms / 1e3),
+             "first20_ms_per_generation": runs[False][0], "gens200_ms_per_generation": runs[False][1],
+             "gens200_kernel_ms_per_generation": {k: v[0] / 200 for k, v in runs[True][2].items()
+                                                  if v[1] and k not in ("tc_generation", "near_ties")},
+             "gens200_near_ties_per_generation": runs[True][2]["near_ties"][1] / 200,
+             "near_ties_per_generation": prof["near_ties"][1] / max(1, args.steps),
              "fitness_rel_err_vs_fp64": {"median": float(np.median(rel)), "p99": float(np.quantile(rel, 0.99)),
                                          "max": float(rel.max())},
              "target_fitness_rel_err_max": float(relx.max()),
-             "selection_mismatch_rate_vs_fp64": mism,
+             "selection_mismatch_rate_vs_fp64": mism, "near_tie_rate_first_generation": ties0,
              "plan": json.loads(M.metade_plan_info(b.ctx))}
-        if prof["tc_gemm"][1]:
-            gms = prof["tc_gemm"][0] / prof["tc_gemm"][1]
+        # the GEMM: k_rot_tc of the five-kernel pipeline, or the four-kernel generation's GEMM kernel
+        # (k_rot_tc selecting in its epilogue), whose time includes the selection and the commit
+        gkind = "tc_gemm" if prof["tc_gemm"][1] else "tc_sel"
+        if prof[gkind][1]:
+            gms = prof[gkind][0] / prof[gkind][1]
+            r["tc_gemm_kernel"] = "k_rot_tc" + (" (selection epilogue)" if gkind == "tc_sel" else "")
             r["tc_gemm_ms"] = gms
             r["tc_gemm_tflops_algorithmic"] = gemm_flops / (gms / 1e3) / 1e12
             r["tc_gemm_tflops_issued"] = (3 if name == "bf16x3" else 1) * gemm_flops / (gms / 1e3) / 1e12
@@ -877,7 +915,8 @@ def run_precision(args):
     line = {"metric": "precision study: individual-gens/s, GEMM TFLOP/s, fitness error and selection mismatch vs FP64",
             "workload": "precision-%dx512xD1000" % wl.n_inst, "steps": args.steps, "warmup": args.warmup,
             "gemm_gflop_per_generation": gemm_flops / 1e9, "results": out,
-            "roofline": {"bound": "tensor", "kernel": "k_rot_tc (bf16)", "achieved": bf.get("tc_gemm_tflops_algorithmic"),
+            "roofline": {"bound": "tensor", "kernel": bf.get("tc_gemm_kernel", "k_rot_tc") + " bf16",
+                         "achieved": bf.get("tc_gemm_tflops_algorithmic"),
                          "peak": peak, "unit": "TFLOP/s",
                          "frac": (bf.get("tc_gemm_tflops_algorithmic") or 0) / peak, "traffic": None,
                          "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured"},
@@ -938,7 +977,7 @@ def run_batching(args):
         prof = M.metade_profile_read(b.ctx)
         t = float(np.mean([a.elapsed_time(c) for a, c in ms]))
         out[name] = {"ms_per_step": t, "indiv_gens_per_s": units / (t / 1e3), "steps": steps,
-                     "kernels_ms_per_step": {k: v[0] / steps for k, v in prof.items() if v[1]},
+                     "kernels_ms_per_step": {k: v[0] / steps for k, v in prof.items() if v[1] and k != "near_ties"},
                      "plan": json.loads(M.metade_plan_info(b.ctx))}
         b.close()
     line = {"metric": "batching study: individual-gens/s, batched vs plain FP32", "workload": wl.name,

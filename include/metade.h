@@ -327,8 +327,10 @@ METADE_API metade_status metade_plan_info(const metade_ctx *ctx, char *buf, size
  * kernel with R^T resident (D_pad <= 128), 6 MLP-objective generations, and
  * the other kernels of a tensor-core generation: 7 prologue (best, pbest
  * pool), 8 trial rows and GEMM operands, 9 selection, 10 near ties, 11 the
- * GEMM with objective, selection and commit of the BF16 D <= 256 path --
- * then clears them.  ms and count are host arrays of 12 (may be NULL). */
+ * GEMM with objective, selection and commit of the BF16 four-kernel
+ * generation -- then clears them.  Kind 12 counts selections of tensor-core
+ * executors decided by the near-tie path (ms 0; counted whether or not
+ * profiling is on).  ms and count are host arrays of 13 (may be NULL). */
 METADE_API metade_status metade_profile(metade_ctx *ctx, int32_t enable);
 METADE_API metade_status metade_profile_read(metade_ctx *ctx, double *ms, int64_t *count);
 

@@ -257,7 +257,7 @@ def metade_autotune(ctx: int, pop, fit, theta, n_gens: int = 3) -> None:
 
 
 PROFILE_KINDS = ["fused_small", "fused_general", "tc_gemm", "tc_generation", "fused_tile_stream", "fused_tile",
-                 "mlp_generations", "tc_prologue", "tc_trial", "tc_select", "tc_ties", "tc_sel"]
+                 "mlp_generations", "tc_prologue", "tc_trial", "tc_select", "tc_ties", "tc_sel", "near_ties"]
 
 
 def metade_profile(ctx: int, enable: bool) -> None:

@@ -44,7 +44,8 @@ enum ProfKind {
     kProfTcSelect = 9,
     kProfTcTies = 10,
     kProfTcSel = 11,
-    kProfKinds = 12
+    kProfNearTies = 12,  // a count only: selections decided by the near-tie path
+    kProfKinds = 13
 };
 
 struct ProfRec {
@@ -113,6 +114,9 @@ struct metade_ctx {
     int* tc_ties = nullptr;
     int* tc_tp = nullptr;  // problem -> path index, first rows, tie counts
     long long* tc_tie_off = nullptr;  // population offsets of listed near ties
+    unsigned long long* tie_total = nullptr;  // near ties decided by the tensor-core path since the last read
+    int* tc_tie_done = nullptr;       // wide four-kernel generation: row groups finished per tie chunk
+    float* tc_tie_zs = nullptr;       // wide four-kernel generation: z and dz of each listed tie
     uint8_t *aq = nullptr, *aq_lo = nullptr, *bq = nullptr, *bq_lo = nullptr;  // BF16 pairs or e4m3 bytes
     float *ascale = nullptr, *bscale = nullptr;                                // FP8 dequantisation factors
     unsigned* amax = nullptr;                                                  // FP8: max|R| scratch
@@ -310,8 +314,12 @@ void free_tc(metade_ctx* c) {
     cudaFree(c->amax);
     cudaFree(c->tc_tp);
     cudaFree(c->tc_tie_off);
+    cudaFree(c->tc_tie_done);
+    cudaFree(c->tc_tie_zs);
     c->tc_tp = nullptr;
     c->tc_tie_off = nullptr;
+    c->tc_tie_done = nullptr;
+    c->tc_tie_zs = nullptr;
     c->tc_execs = c->tc_row_exec = c->tc_tiles = c->tc_topk = c->tc_ties = nullptr;
     c->tc_brow = nullptr;
     c->aq = c->aq_lo = c->bq = c->bq_lo = nullptr;
@@ -461,11 +469,29 @@ metade_status setup_tc(metade_ctx* c) {
     t.kp = tc_kp;
     t.split = split ? 1 : 0;
     t.max_dpad = tc_max_dpad;
-    // BF16 with FP32 difference-form ties and operands of at most 256 elements:
-    // four kernels per generation (ranking, trial rows, GEMM with selection and
-    // commit, near ties)
-    t.fused = (c->prec == METADE_BF16 && !c->tie_fp64 && !c->tc_unfused && tc_fused_fits(tc_kp)) ? 1 : 0;
+    // BF16 with FP32 difference-form ties: four kernels per generation (ranking,
+    // trial rows, GEMM with selection and commit, near ties); the persistent
+    // k_tc_sel holds operands of at most 256 elements, k_rot_tc selects for wider ones
+    if (c->prec == METADE_BF16 && !c->tie_fp64 && !c->tc_unfused) t.fused = tc_fused_fits(tc_kp) ? 1 : 2;
+    else t.fused = 0;
     t.gen_ctas = std::max(1, device_sms());
+    if (!c->tie_total) {  // kept across plans: the count runs until the next profile read
+        if (dalloc(&c->tie_total, 1)) return METADE_ENOMEM;
+        if (cudaMemset(c->tie_total, 0, sizeof(unsigned long long)) != cudaSuccess) return METADE_ECUDA;
+    }
+    t.tie_total = c->tie_total;
+    t.tie_done = nullptr;
+    t.tie_zs = nullptr;
+    t.wide_ctas = 0;
+    if (t.fused == 2) {  // the row-split tie kernel's scratch: a chunk counter and z, dz per list slot
+        const size_t vs = (size_t)((tc_max_dpad + 3) & ~3);
+        if (dalloc(&c->tc_tie_done, nrows) || dalloc(&c->tc_tie_zs, nrows * 2 * vs)) return METADE_ENOMEM;
+        if (cudaMemset(c->tc_tie_done, 0, sizeof(int) * nrows) != cudaSuccess) return METADE_ECUDA;
+        t.tie_done = c->tc_tie_done;
+        t.tie_zs = c->tc_tie_zs;
+        t.wide_ctas = tc_ties_wide_ctas(tc_max_dpad);
+        if (t.wide_ctas <= 0) return METADE_ECUDA;
+    }
 
     // a tie keeps four rows of max_dpad in shared memory (FP64 with tie_fp64)
     if ((size_t)4 * tc_max_dpad * (c->tie_fp64 ? sizeof(double) : sizeof(float)) > kSmemLimit)
@@ -697,6 +723,7 @@ void metade_destroy(metade_ctx* c) {
     cudaFree(c->bar);
     cudaFree(c->work);
     free_tc(c);
+    cudaFree(c->tie_total);
     cudaFree(c->mlp_x);
     cudaFree(c->mlp_y);
     cudaFree(c->mlp_execs);
@@ -1216,10 +1243,10 @@ metade_status metade_plan_info(const metade_ctx* c, char* buf, size_t len) {
         char tmp[256];
         snprintf(tmp, sizeof(tmp),
                  ", \"tensor_core\": {\"kernel\": \"%s\", \"precision\": \"%s\", \"executors\": %d, "
-                 "\"tiles\": %d, \"kp\": %d, \"tile\": [%d, 256, %d]}",
-                 c->tcp.simt ? "k_rot_simt" : c->tcp.fused ? "k_tc_sel" : "k_rot_tc",
+                 "\"tiles\": %d, \"kp\": %d, \"tile\": [%d, 256, %d], \"kernels_per_generation\": %d}",
+                 c->tcp.simt ? "k_rot_simt" : c->tcp.fused == 1 ? "k_tc_sel" : "k_rot_tc",
                  c->tcp.simt ? "fp32" : c->tcp.fp8 ? "fp8e4m3" : c->tcp.split ? "bf16x3" : "bf16", c->tcp.n_exec,
-                 c->tcp.n_tiles, c->tcp.kp, c->tcp.simt ? 64 : 128, c->tcp.simt ? 16 : 64);
+                 c->tcp.n_tiles, c->tcp.kp, c->tcp.simt ? 64 : 128, c->tcp.simt ? 16 : 64, c->tcp.fused ? 4 : 5);
         s += tmp;
     }
     if (c->mlpp.n_rows > 0) {
@@ -1259,6 +1286,12 @@ metade_status metade_profile_read(metade_ctx* c, double* ms, int64_t* count) {
     c->prof.clear();
     for (cudaEvent_t e : c->prof_events) cudaEventDestroy(e);
     c->prof_events.clear();
+    if (c->tie_total) {
+        unsigned long long h = 0;
+        CK(cudaMemcpy(&h, c->tie_total, sizeof(h), cudaMemcpyDeviceToHost));
+        CK(cudaMemset(c->tie_total, 0, sizeof(h)));
+        n[kProfNearTies] = (int64_t)h;
+    }
     for (int k = 0; k < kProfKinds; ++k) {
         if (ms) ms[k] = tot[k];
         if (count) count[k] = n[k];

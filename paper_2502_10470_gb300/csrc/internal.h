@@ -128,7 +128,8 @@ struct TcPlan {
     int* tie_count;          // device counter
     int tie_ctas;            // CTAs of the tie kernel
     int kp, split, max_dpad;
-    int fused;               // 1: k_tc_rank, k_tc_trial2, k_tc_sel, k_tc_ties2 per generation (BF16, kp <= 256)
+    int fused;               // BF16 with FP32 ties, four kernels per generation: 1 k_tc_rank, k_tc_trial2,
+                             // k_tc_sel, k_tc_ties2 (kp <= 256); 2 the same with k_rot_tc selecting (kp > 256)
     int* next_tile;          // device counter of k_tc_sel's tile queue
     int n_tp;                // problems with executors on this path
     const int* prob_tp;      // device [n_prob]: index among them (-1: none)
@@ -136,6 +137,10 @@ struct TcPlan {
     int* tie_cnt;            // device [n_tp]: near ties listed per problem
     int* chunk_ctr;          // device counter of k_tc_ties2's chunk queue
     int gen_ctas;            // CTAs of k_tc_sel (one per SM)
+    unsigned long long* tie_total;  // device counter: near ties decided (read and cleared by the profile read)
+    int* tie_done;           // device [n_rows] plan mode 2: row groups finished per tie chunk (kept at zero)
+    float* tie_zs;           // device [n_rows][2][round_up(max_dpad, 4)] plan mode 2: z and dz of listed ties
+    int wide_ctas;           // plan mode 2: CTAs of k_tc_ties_wide (as many as are resident at once)
     CUtensorMap mapA, mapB, mapAlo, mapBlo;
 };
 bool tc_make_map(CUtensorMap* map, const void* base, long long rows, int kp, int box_rows, int esz);
@@ -155,9 +160,18 @@ cudaError_t launch_rot_simt(const InstDesc* desc, const int* tiles, int n_tiles,
 // k_tc_sel holds operands of kp BF16 elements, and one generation of every
 // tensor-core executor -- k_tc_rank (pbest pools), k_tc_trial2 (trial and
 // operand rows), k_tc_sel (GEMM, objective, selection, commit), k_tc_ties2
-// (near ties).  ev (may be null): five events, before each launch and after
-// the last.
+// (near ties) in plan mode 1; for operands wider than 256 (plan mode 2)
+// k_tc_rank, k_tc_trial, k_rot_tc in selection mode and k_tc_ties_wide.
+// ev (may be null): five events, before each launch and after the last.
 bool tc_fused_fits(int kp);
+// CTAs of k_tc_ties_wide resident on the device at once for vectors of max_dpad (0 on a CUDA error)
+int tc_ties_wide_ctas(int max_dpad);
+// k_tc_trial alone (trial rows and BF16 operand rows, a warp per row): the
+// trial kernel of plan mode 2
+cudaError_t launch_tc_trial_rows(const StepArgs& a, const TcPlan& p, cudaStream_t st);
+// k_rot_tc with the selection in its epilogue (BF16): decisions against the stored
+// fitness, clear acceptances committed, near ties listed per problem for k_tc_ties2
+cudaError_t launch_rot_tc_select(const StepArgs& a, const TcPlan& p, cudaStream_t st);
 cudaError_t launch_tc_fused_generation(const StepArgs& a, const TcPlan& p, cudaStream_t st,
                                        cudaEvent_t* ev = nullptr);
 // ev (may be null): six events recorded before the prologue, trial, GEMM,

@@ -503,6 +503,7 @@ struct TieArgs {
     const long long* tie_off; // population offset of each near tie's row, by problem
     int* chunk_ctr;           // chunks handed out (zeroed by k_tc_rank)
     const float* uscr;        // trial rows (population layout)
+    unsigned long long* tie_total;  // near ties decided, summed over generations (block 0 adds)
 };
 
 // The near ties of the generation, up to kTieBatch ties of one problem per
@@ -531,6 +532,7 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_tc_ties2(TieArgs g) {
         long long total = 0;
         for (int q = 0; q < g.n_tp; ++q) total += g.tie_cnt[q];
         bsz_s = (int)min((long long)kTieBatch, max(2LL, (total + gridDim.x - 1) / gridDim.x));
+        if (blockIdx.x == 0) atomicAdd(g.tie_total, (unsigned long long)total);
     }
     __syncthreads();
     const int bsz = bsz_s;
@@ -701,6 +703,265 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_tc_ties2(TieArgs g) {
     }
 }
 
+// ---------------------------------------------------------- k_tc_ties_wide
+constexpr int kWThreads = 128;                // threads of k_tc_ties_wide
+constexpr int kWRows = 4;                     // consecutive rows of z per thread
+constexpr int kWGroup = kWThreads * kWRows;   // rows of z per work item
+constexpr int kWMaxTies = 8;                  // near ties of one problem per chunk at most
+constexpr int kWCk = 16;                      // columns of R^T per stage
+constexpr int kWStages = 3;                   // stages of the cp.async ring
+constexpr int kWStageR = kWCk * kWGroup;      // floats of R^T per stage (32 KB)
+constexpr int kWStageV = 2 * kWMaxTies * kWCk + kWCk;  // x and u of every tie, then o, for the stage's columns
+constexpr int kWStage = kWStageR + kWStageV;  // floats per stage
+static_assert(kWStage % 4 == 0, "stages start 16-byte aligned");
+
+struct TieWArgs {
+    StepArgs a;
+    const int* row_exec;      // operand row -> executor
+    int n_tp;                 // problems on this path
+    const int* tp_row0;       // per problem: start of its tie list
+    const int* tie_cnt;       // per problem: near ties listed by the GEMM kernel
+    const int* tie_list;      // fitness index of each near tie, by problem
+    const long long* tie_off; // population offset of each near tie's row, by problem
+    int* item_ctr;            // work items handed out (zeroed by k_tc_rank)
+    int* done;                // per chunk (at its first list slot): row groups finished; the last one resets it
+    float* zs;                // [list slot][2][vs]: z and dz of each near tie
+    const float* uscr;        // trial rows (population layout)
+    int vs;                   // floats per vector of z: round_up(the widest D_pad, 4)
+    int ngmax;                // row groups of the widest problem
+    unsigned long long* tie_total;  // near ties decided, summed over generations (block 0 adds)
+};
+
+// Near ties of problems wider than 256, for the four-kernel generation whose
+// GEMM kernel is k_rot_tc.  A work item is (chunk of up to kWMaxTies ties of
+// one problem, group of 512 rows of z).  R^T is streamed 16 columns at a time
+// through a 3-stage cp.async ring, together with those columns of x, u and o
+// of every tie of the chunk (x - o and u - x are formed once per stage); a
+// thread owns four consecutive rows and forms their z = R (x - o) and
+// dz = R (u - x) for every tie in FP32, a float4 of R^T against a float4 of
+// x - o (and u - x) per tie, so each shared-memory load feeds sixteen fmas.
+// Every fma chain runs in ascending k like every other FP32 rotation; the
+// columns past D are zero in all three operands (fma(0, 0, acc) == acc for an
+// accumulator that starts at +0), so the results are bit-identical to a plain
+// loop over k < D.  The stage loop is instantiated for 1, 2, 4 and 8 ties.  The rows go to a
+// global scratch; the CTA that finishes a chunk's last row group (a counter
+// per chunk) reads z and dz back through L2, and a warp per tie forms the
+// FP32 difference form, decides and commits.  A trial identical to its
+// target is accepted as it is.  Splitting the rows over CTAs keeps every SM
+// streaming R even when a generation has few ties.
+// The stage loop of k_tc_ties_wide for NB ties (a power of two >= the
+// chunk's ties; the rest are zero-filled and their rows not stored): no
+// branch inside, so the loads of a step are issued ahead of its fmas.
+template <int NB, typename Issue>
+__device__ __forceinline__ void wide_sweep(int nst, int nb, const float* ring, float* sx, float* sl, Issue& issue,
+                                           float* zs, int slot0, int vs, int r0, int dim) {
+    const int tid = threadIdx.x;
+    float az[NB][kWRows], adz[NB][kWRows];
+#pragma unroll
+    for (int t = 0; t < NB; ++t)
+#pragma unroll
+        for (int j = 0; j < kWRows; ++j) az[t][j] = adz[t][j] = 0.f;
+    for (int st = 0; st < nst; ++st) {
+        issue(st + kWStages - 1);  // the stage read at st - 1 is free: every thread passed the barrier after it
+        asm volatile("cp.async.wait_group %0;" ::"n"(kWStages - 1) : "memory");  // stage st has landed
+        __syncthreads();
+        const float* buf = ring + (size_t)(st % kWStages) * kWStage;
+        {  // x - o and u - x of the stage's columns, a thread per (tie, column)
+            const int t = tid / kWCk, k = tid - t * kWCk;
+            const float* v = buf + kWStageR;
+            const float x = v[t * kWCk + k], u = v[kWMaxTies * kWCk + t * kWCk + k], oo = v[2 * kWMaxTies * kWCk + k];
+            sx[t * kWCk + k] = x - oo;
+            sl[t * kWCk + k] = u - x;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int c4 = 0; c4 < kWCk / 4; ++c4) {
+            float4 rt[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                rt[k] = *reinterpret_cast<const float4*>(buf + (4 * c4 + k) * kWGroup + kWRows * tid);
+#pragma unroll
+            for (int t = 0; t < NB; ++t) {
+                const float4 x4 = *reinterpret_cast<const float4*>(sx + t * kWCk + 4 * c4);
+                const float4 l4 = *reinterpret_cast<const float4*>(sl + t * kWCk + 4 * c4);
+                const float xk[4] = {x4.x, x4.y, x4.z, x4.w}, lk[4] = {l4.x, l4.y, l4.z, l4.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    az[t][0] = fmaf(rt[k].x, xk[k], az[t][0]);
+                    az[t][1] = fmaf(rt[k].y, xk[k], az[t][1]);
+                    az[t][2] = fmaf(rt[k].z, xk[k], az[t][2]);
+                    az[t][3] = fmaf(rt[k].w, xk[k], az[t][3]);
+                    adz[t][0] = fmaf(rt[k].x, lk[k], adz[t][0]);
+                    adz[t][1] = fmaf(rt[k].y, lk[k], adz[t][1]);
+                    adz[t][2] = fmaf(rt[k].z, lk[k], adz[t][2]);
+                    adz[t][3] = fmaf(rt[k].w, lk[k], adz[t][3]);
+                }
+            }
+        }
+        __syncthreads();  // the stage is refilled kWStages - 1 steps later; sx, sl at the next step
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");  // only empty groups remain
+    if (r0 < dim) {
+#pragma unroll
+        for (int t = 0; t < NB; ++t) {
+            if (t < nb) {
+                float* zt = zs + (size_t)(slot0 + t) * 2 * vs + r0;
+                *reinterpret_cast<float4*>(zt) = make_float4(az[t][0], az[t][1], az[t][2], az[t][3]);
+                *reinterpret_cast<float4*>(zt + vs) = make_float4(adz[t][0], adz[t][1], adz[t][2], adz[t][3]);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kWThreads, 2) k_tc_ties_wide(TieWArgs g) {
+    extern __shared__ uint8_t smraw[];
+    __shared__ int tp_s, j0_s, rg_s, bsz_s, last_s, ncum_s[kMaxTpSmem + 1];
+    __shared__ __align__(16) float sx[kWMaxTies * kWCk], sl[kWMaxTies * kWCk];  // x - o, u - x of the stage
+    float* ring = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smraw) + 15) & ~(uintptr_t)15);
+    const StepArgs& a = g.a;
+    const int vs = g.vs;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    auto groups = [&](int tp) { return (a.desc[g.row_exec[g.tp_row0[tp]]].dim + kWGroup - 1) / kWGroup; };
+    if (tid == 0) {  // chunk size: about one round of items over the grid, 1 .. kWMaxTies ties
+        long long total = 0;
+        for (int q = 0; q < g.n_tp; ++q) total += g.tie_cnt[q];
+        bsz_s = (int)min((long long)kWMaxTies, max(1LL, (total * g.ngmax + gridDim.x - 1) / gridDim.x));
+        if (blockIdx.x == 0) atomicAdd(g.tie_total, (unsigned long long)total);
+    }
+    __syncthreads();
+    const int bsz = bsz_s;
+    const bool cum_smem = g.n_tp <= kMaxTpSmem;  // items per problem, summed in problem order
+    if (cum_smem) {
+        for (int q = tid; q < g.n_tp; q += blockDim.x) ncum_s[q + 1] = (g.tie_cnt[q] + bsz - 1) / bsz * groups(q);
+        __syncthreads();
+        if (tid == 0) {
+            ncum_s[0] = 0;
+            for (int q = 0; q < g.n_tp; ++q) ncum_s[q + 1] += ncum_s[q];
+        }
+        __syncthreads();
+    }
+    for (;;) {
+        if (tid == 0) {  // item w -> (problem, first tie of the chunk, row group)
+            const int w = atomicAdd(g.item_ctr, 1);
+            int tp = -1, e = 0;
+            if (cum_smem) {
+                if (w < ncum_s[g.n_tp]) {
+                    int lo = 0, hi = g.n_tp - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (ncum_s[mid] <= w) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    tp = lo;
+                    e = w - ncum_s[lo];
+                }
+            } else {
+                int acc = 0;
+                for (int q = 0; q < g.n_tp; ++q) {
+                    const int n = (g.tie_cnt[q] + bsz - 1) / bsz * groups(q);
+                    if (w < acc + n) {
+                        tp = q;
+                        e = w - acc;
+                        break;
+                    }
+                    acc += n;
+                }
+            }
+            tp_s = tp;
+            if (tp >= 0) {
+                const int ng = groups(tp);
+                j0_s = (e / ng) * bsz;
+                rg_s = e - (e / ng) * ng;
+            }
+        }
+        __syncthreads();
+        const int tp = tp_s;
+        if (tp < 0) break;
+        const int j0 = j0_s, rg = rg_s;
+        const int nb = min(bsz, g.tie_cnt[tp] - j0);
+        const int slot0 = g.tp_row0[tp] + j0;  // list slot of the chunk's first tie
+        const long long* toff = g.tie_off + slot0;
+        const InstDesc d = a.desc[g.row_exec[g.tp_row0[tp]]];
+        const int ng = (d.dim + kWGroup - 1) / kWGroup;
+        const float* o = a.shift + d.shift_off;
+        const float* RT = a.rotT + d.rot_off;  // R^T [dim][dpad]
+        const int rbase = rg * kWGroup;        // first row of the item
+        const int nst = (d.dim + kWCk - 1) / kWCk;
+        // stage st: R^T[c][rbase ..] for its 16 columns c, and x, u, o in those columns;
+        // anything past D (columns) or D_pad (rows) is zero-filled
+        auto issue = [&](int st) {
+            if (st < nst) {
+                float* buf = ring + (size_t)(st % kWStages) * kWStage;
+                const int c0 = st * kWCk;
+                for (int e2 = tid; e2 < kWCk * (kWGroup / 4); e2 += kWThreads) {
+                    const int k = e2 / (kWGroup / 4), i4 = 4 * (e2 - k * (kWGroup / 4));
+                    const bool ok = c0 + k < d.dim && rbase + i4 < d.dpad;
+                    cp_async16z(buf + k * kWGroup + i4, ok ? RT + (size_t)(c0 + k) * d.dpad + rbase + i4 : RT,
+                                ok ? 16 : 0);
+                }
+                if (tid < 2 * kWMaxTies * (kWCk / 4) + kWCk / 4) {  // x, u of each tie, then o: 16 bytes each
+                    const int part = tid / (kWMaxTies * (kWCk / 4));  // 0 x, 1 u, 2 o
+                    const int rem = tid - part * (kWMaxTies * (kWCk / 4));
+                    const int t = rem / (kWCk / 4), col = c0 + 4 * (rem % (kWCk / 4));
+                    const bool ok = col < d.dpad && (part == 2 || t < nb);
+                    const float* src = part == 2 ? o + col
+                                       : (part == 0 ? a.pop : g.uscr) + (ok ? toff[t] : 0) + col;
+                    cp_async16z(buf + kWStageR + part * kWMaxTies * kWCk + 4 * rem, ok ? src : o, ok ? 16 : 0);
+                }
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");  // one group per stage, empty past the end
+        };
+        for (int st = 0; st < kWStages - 1; ++st) issue(st);
+        const int r0 = rbase + kWRows * tid;  // this thread's first row (rows r0 .. r0 + 3 < D_pad)
+        if (nb <= 1) wide_sweep<1>(nst, nb, ring, sx, sl, issue, g.zs, slot0, vs, r0, d.dim);
+        else if (nb <= 2) wide_sweep<2>(nst, nb, ring, sx, sl, issue, g.zs, slot0, vs, r0, d.dim);
+        else if (nb <= 4) wide_sweep<4>(nst, nb, ring, sx, sl, issue, g.zs, slot0, vs, r0, d.dim);
+        else wide_sweep<8>(nst, nb, ring, sx, sl, issue, g.zs, slot0, vs, r0, d.dim);
+        __threadfence();  // this group's rows are visible before the chunk's counter moves
+        __syncthreads();
+        if (tid == 0) last_s = atomicAdd(&g.done[slot0], 1) == ng - 1;
+        __syncthreads();
+        if (last_s) {  // every row group of the chunk is in: decide its ties
+            __threadfence();
+            float* vz = ring;                       // [nb][vs] z, then [nb][vs] dz (over the ring)
+            float* vd = ring + (size_t)kWMaxTies * vs;
+            const int f4 = d.dpad >> 2;
+            for (int e2 = tid; e2 < nb * f4; e2 += kWThreads) {  // through L2 (not L1)
+                const int q = e2 / f4, c = 4 * (e2 - q * f4);
+                const float* zt = g.zs + (size_t)(slot0 + q) * 2 * vs + c;
+                *reinterpret_cast<float4*>(vz + q * vs + c) = __ldcg(reinterpret_cast<const float4*>(zt));
+                *reinterpret_cast<float4*>(vd + q * vs + c) = __ldcg(reinterpret_cast<const float4*>(zt + vs));
+            }
+            __syncthreads();
+            for (int t = warp; t < nb; t += kWThreads / 32) {  // a warp per tie
+                const long long off = toff[t];
+                const int fidx = g.tie_list[slot0 + t];
+                bool diff = false;  // every load issued: no short circuit
+                for (int c = lane; c < d.dpad; c += 32) diff |= g.uscr[off + c] != a.pop[off + c];
+                const float fx = a.fit[fidx];
+                bool take;
+                float fn;
+                if (!__any_sync(kFull, diff)) {  // a trial identical to its target: accepted as it is
+                    take = true;
+                    fn = fx;
+                } else {
+                    const float df = warp_diff(d.obj, d.dim, vz + t * vs, vd + t * vs);
+                    take = df <= 0.0f;
+                    fn = fx + df;
+                }
+                if (take) {
+                    for (int c = 4 * lane; c < d.dpad; c += 128)
+                        *reinterpret_cast<float4*>(a.pop + off + c) =
+                            *reinterpret_cast<const float4*>(g.uscr + off + c);
+                    if (lane == 0) a.fit[fidx] = fn;
+                }
+            }
+            if (tid == 0) g.done[slot0] = 0;  // ready for the next generation
+        }
+        __syncthreads();  // the ring and the item record are reused
+    }
+}
+
 // best and the pbest pool of every tensor-core executor (block per executor);
 // block 0 also zeroes the tile counter of the k_tc_sel launch that follows
 __global__ void k_tc_rank(StepArgs a, const int* __restrict__ execs, int* topk_all, int* next_tile, int* chunk_ctr,
@@ -721,37 +982,85 @@ __global__ void k_tc_rank(StepArgs a, const int* __restrict__ execs, int* topk_a
 
 size_t sel_smem(int kt) { return 1024 + kASize + kPartSize + (size_t)kt * kBT; }
 constexpr size_t kTieSmem = 16 + kTie2Size;
+// the ring, or (for the chunk's decision) z and dz of kWMaxTies ties, whichever is larger
+size_t wide_smem(int vs) {
+    return 16 + std::max((size_t)kWStages * kWStage, (size_t)2 * kWMaxTies * vs) * sizeof(float);
+}
+int wide_vs(int max_dpad) { return (max_dpad + 3) & ~3; }
 
 }  // namespace
 
 bool tc_fused_fits(int kp) { return kp <= kMaxKt * kBK && sel_smem(kp / kBK) <= 227 * 1024; }
 
+int tc_ties_wide_ctas(int max_dpad) {
+    const size_t smem = wide_smem(wide_vs(max_dpad));
+    if (cudaFuncSetAttribute(k_tc_ties_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+    int per_sm = 0, dev = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_ties_wide, kWThreads, smem) != cudaSuccess ||
+        cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))
+        return 0;
+    return per_sm * sms;
+}
+
 cudaError_t launch_tc_fused_generation(const StepArgs& a, const TcPlan& p, cudaStream_t st, cudaEvent_t* ev) {
     if (ev) cudaEventRecord(ev[0], st);
     k_tc_rank<<<p.n_exec, 256, 0, st>>>(a, p.execs, p.topk_all, p.next_tile, p.chunk_ctr, p.tie_cnt, p.n_tp);
     if (ev) cudaEventRecord(ev[1], st);
+    cudaError_t e;
+    if (p.fused == 2) {  // operands wider than 256: warp-per-row trials, k_rot_tc selecting, row-split ties
+        e = launch_tc_trial_rows(a, p, st);
+        if (e != cudaSuccess) return e;
+        if (ev) cudaEventRecord(ev[2], st);
+        e = launch_rot_tc_select(a, p, st);
+        if (e != cudaSuccess) return e;
+        if (ev) cudaEventRecord(ev[3], st);
+        TieWArgs tw;
+        tw.a = a;
+        tw.row_exec = p.row_exec;
+        tw.n_tp = p.n_tp;
+        tw.tp_row0 = p.tp_row0;
+        tw.tie_cnt = p.tie_cnt;
+        tw.tie_list = p.tie_list;
+        tw.tie_off = p.tie_off;
+        tw.item_ctr = p.chunk_ctr;
+        tw.done = p.tie_done;
+        tw.zs = p.tie_zs;
+        tw.uscr = p.uscr;
+        tw.tie_total = p.tie_total;
+        tw.vs = wide_vs(p.max_dpad);
+        tw.ngmax = (p.max_dpad + kWGroup - 1) / kWGroup;
+        const size_t smem = wide_smem(tw.vs);
+        e = cudaFuncSetAttribute(k_tc_ties_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_tc_ties_wide<<<p.wide_ctas, kWThreads, smem, st>>>(tw);
+        if (ev) cudaEventRecord(ev[4], st);
+        return cudaGetLastError();
+    }
     k_tc_trial2<<<(p.n_rows + kTRows - 1) / kTRows, kTThreads, 0, st>>>(a, p.row_exec, p.n_rows, p.topk_all, p.uscr,
                                                                        static_cast<uint8_t*>(p.aq), p.kp);
     if (ev) cudaEventRecord(ev[2], st);
-    SelArgs g;
-    g.a = a;
-    g.tiles = p.tiles;
-    g.n_tiles = p.n_tiles;
-    g.next_tile = p.next_tile;
-    g.prob_tp = p.prob_tp;
-    g.tp_row0 = p.tp_row0;
-    g.tie_cnt = p.tie_cnt;
-    g.tie_list = p.tie_list;
-    g.tie_off = p.tie_off;
-    g.row_exec = p.row_exec;
-    g.brow = p.brow;
-    g.uscr = p.uscr;
-    g.kt = p.kp / kBK;
-    const size_t smem = sel_smem(g.kt);
-    cudaError_t e = cudaFuncSetAttribute(k_tc_sel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const int grid = p.n_tiles < p.gen_ctas ? p.n_tiles : p.gen_ctas;
-    k_tc_sel<<<grid, kSelThreads + 32, smem, st>>>(p.mapA, p.mapB, g);
+    {
+        SelArgs g;
+        g.a = a;
+        g.tiles = p.tiles;
+        g.n_tiles = p.n_tiles;
+        g.next_tile = p.next_tile;
+        g.prob_tp = p.prob_tp;
+        g.tp_row0 = p.tp_row0;
+        g.tie_cnt = p.tie_cnt;
+        g.tie_list = p.tie_list;
+        g.tie_off = p.tie_off;
+        g.row_exec = p.row_exec;
+        g.brow = p.brow;
+        g.uscr = p.uscr;
+        g.kt = p.kp / kBK;
+        const size_t smem = sel_smem(g.kt);
+        e = cudaFuncSetAttribute(k_tc_sel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        const int grid = p.n_tiles < p.gen_ctas ? p.n_tiles : p.gen_ctas;
+        k_tc_sel<<<grid, kSelThreads + 32, smem, st>>>(p.mapA, p.mapB, g);
+    }
     if (ev) cudaEventRecord(ev[3], st);
     TieArgs ta;
     ta.a = a;
@@ -763,6 +1072,7 @@ cudaError_t launch_tc_fused_generation(const StepArgs& a, const TcPlan& p, cudaS
     ta.tie_off = p.tie_off;
     ta.chunk_ctr = p.chunk_ctr;
     ta.uscr = p.uscr;
+    ta.tie_total = p.tie_total;
     e = cudaFuncSetAttribute(k_tc_ties2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTieSmem);
     if (e != cudaSuccess) return e;
     k_tc_ties2<<<2 * p.gen_ctas, kSelThreads, kTieSmem, st>>>(ta);

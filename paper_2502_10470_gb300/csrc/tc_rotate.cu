@@ -66,6 +66,18 @@ struct TcGemmArgs {
     const float* ascale;      // FP8: per operand row, max|d| / 448
     const float* bscale;      // FP8: per problem, max|R| / 448
     int* status;
+    // selection in the epilogue (sel = 1, BF16 with FP32-difference ties): the row's decision
+    // against the stored fitness, clear acceptances committed, near ties listed for k_tc_ties2
+    int sel;
+    float* pop;               // population (rows committed here)
+    float* fit;               // stored fitness
+    const float* uscr;        // trial rows
+    const float* theta;       // decoded theta per executor (rows of an invalid theta are left alone)
+    const int* prob_tp;       // problem -> index among the problems on the path
+    const int* tp_row0;       // per such problem: start of its tie list
+    int* tie_cnt;             // per such problem: near ties listed
+    int* tie_list;            // fitness index of each near tie
+    long long* tie_off;       // population offset of each near tie's row
 };
 
 // kTcThreads threads.  Warps 0 .. kEpiWarps-1 run the epilogue: warp w reads
@@ -83,6 +95,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages], acc_full[2], acc_empty[2], part_ready[4][2], drain;
     __shared__ __align__(16) float part[2][kParts - 1][kBM][8];
     __shared__ uint32_t tmem_base;
+    __shared__ int nacc_s, acc_row[kBM];  // selection mode: rows whose trial is accepted
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
     const int nops = a.split ? 2 : 1;  // operand sets per stage (hi, and lo when split)
     const int stage_bytes = nops * (kAT + kBT);
@@ -93,7 +106,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const InstDesc d = a.desc[a.row_exec[arow]];  // dim, objective and problem are those of every row of the tile
     const int brow0 = (int)a.brow[d.prob];
     const int nchunks = (d.dim + kBN - 1) / kBN;
-    const int total = nchunks * a.kt;
+    const int kel = a.fp8 ? kBK8 : kBK;  // K elements per 128-byte tile (x is in elements, 128 bytes apart)
+    // K tiles of this tile's problem: operand columns past its D_pad are zero (or not written)
+    const int kt = min(a.kt, (d.dpad + kel - 1) / kel);
+    const int total = nchunks * kt;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -113,15 +129,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         mbar_init(&drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        nacc_s = 0;
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t taddr = tmem_base;
 
-    const int kel = a.fp8 ? kBK8 : kBK;  // K elements per 128-byte tile (x is in elements, 128 bytes apart)
     auto load = [&](int it) {
-        const int s = it % nst, c = it / a.kt, kk = it - c * a.kt;
+        const int s = it % nst, c = it / kt, kk = it - c * kt;
         uint8_t* st = sm + s * stage_bytes;
         mbar_expect_tx(&full[s], (uint32_t)stage_bytes);
         tma_load_2d(st, &tmA, &full[s], kk * kel, arow);
@@ -148,8 +164,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     break;
                 }
                 tc_fence_after();
-                for (int kk = 0; kk < a.kt; ++kk) {
-                    const int it = c * a.kt + kk, s = it % nst;
+                for (int kk = 0; kk < kt; ++kk) {
+                    const int it = c * kt + kk, s = it % nst;
                     if (!mbar_wait(&full[s], (uint32_t)(it / nst) & 1u)) {
                         ok = false;
                         break;
@@ -281,13 +297,39 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (!eok) {
             if (lane == 0) set_status(a.status, kStatusTimeout);
         } else if (half == 0 && row < nr) {
-            const InstDesc& e = a.desc[a.row_exec[arow + row]];  // this row's executor
-            a.fu[e.fit_off + (arow + row - e.tc_row)] = nan_to_inf(acc.finish(d.obj, d.dim));
+            const int k = a.row_exec[arow + row];
+            const InstDesc& e = a.desc[k];  // this row's executor
+            const float fn = nan_to_inf(acc.finish(d.obj, d.dim));
+            const int fidx = e.fit_off + (arow + row - e.tc_row);
+            if (!a.sel) {
+                a.fu[fidx] = fn;
+            } else if (load_strat(a.theta + 6 * k, e.np).ok) {  // rows of an invalid theta stay as they are
+                const float fx = a.fit[fidx];
+                if (near_tie(fn, fx, tie_band(d.dim))) {
+                    const int tp = a.prob_tp[d.prob];
+                    const int q = a.tp_row0[tp] + atomicAdd(&a.tie_cnt[tp], 1);
+                    a.tie_list[q] = fidx;
+                    a.tie_off[q] = e.pop_off + (long long)(arow + row - e.tc_row) * d.dpad;
+                } else if (fn <= fx) {
+                    acc_row[atomicAdd(&nacc_s, 1)] = row;
+                    a.fit[fidx] = fn;
+                }
+            }
         }
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    if (a.sel) {  // accepted rows into the population, every thread copying float4s
+        const int f4 = d.dpad >> 2, n = nacc_s * f4;
+        for (int e2 = tid; e2 < n; e2 += blockDim.x) {
+            const int q = e2 / f4, c4 = e2 - q * f4;
+            const int gr = arow + acc_row[q];
+            const InstDesc& e = a.desc[a.row_exec[gr]];
+            const long long off = e.pop_off + (long long)(gr - e.tc_row) * d.dpad + 4 * c4;
+            *reinterpret_cast<float4*>(a.pop + off) = *reinterpret_cast<const float4*>(a.uscr + off);
+        }
+    }
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(2 * kBN) : "memory");
 }
@@ -441,11 +483,13 @@ __device__ __forceinline__ void tc_tie_rows(int dim, int dpad, const float* __re
 
 __global__ void __launch_bounds__(256) k_tc_ties(StepArgs a, const int* __restrict__ row_exec,
                                                  const float* __restrict__ uscr, const int* __restrict__ tie_list,
-                                                 const int* __restrict__ tie_count, int ws) {
+                                                 const int* __restrict__ tie_count, int ws,
+                                                 unsigned long long* tie_total) {
     extern __shared__ __align__(16) float smz[];
     __shared__ int take_s;
     __shared__ float fn_s;
     const int n = *tie_count;
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(tie_total, (unsigned long long)n);
     for (int t = blockIdx.x; t < n; t += gridDim.x) {
         const int r = tie_list[t];
         const int k = row_exec[r];
@@ -641,8 +685,48 @@ cudaError_t launch_tc_eval(const InstDesc* desc, const TcPlan& p, const float* p
     g.ascale = p.ascale;
     g.bscale = p.bscale;
     g.status = status;
+    g.sel = 0;
     k_rot_tc<<<p.n_tiles, kTcThreads, smem_g, st>>>(p.mapA, p.mapB, p.split ? p.mapAlo : p.mapA, p.split ? p.mapBlo : p.mapB,
                                              g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_trial_rows(const StepArgs& a, const TcPlan& p, cudaStream_t st) {
+    const size_t smem_t = (size_t)8 * p.max_dpad * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_tc_trial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
+    if (e != cudaSuccess) return e;
+    k_tc_trial<<<(p.n_rows + 7) / 8, 256, smem_t, st>>>(a, p.row_exec, p.n_rows, p.topk_all, p.uscr, p.aq, nullptr,
+                                                        p.kp, p.max_dpad, 0, p.ascale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rot_tc_select(const StepArgs& a, const TcPlan& p, cudaStream_t st) {
+    const size_t smem_g = tc_gemm_smem(false);
+    cudaError_t e = cudaFuncSetAttribute(k_rot_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_g);
+    if (e != cudaSuccess) return e;
+    TcGemmArgs g;
+    g.desc = a.desc;
+    g.tiles = p.tiles;
+    g.row_exec = p.row_exec;
+    g.brow = p.brow;
+    g.fu = p.fu;
+    g.kt = p.kp / kBK;
+    g.split = 0;
+    g.fp8 = 0;
+    g.ascale = p.ascale;
+    g.bscale = p.bscale;
+    g.status = a.status;
+    g.sel = 1;
+    g.pop = a.pop;
+    g.fit = a.fit;
+    g.uscr = p.uscr;
+    g.theta = a.theta;
+    g.prob_tp = p.prob_tp;
+    g.tp_row0 = p.tp_row0;
+    g.tie_cnt = p.tie_cnt;
+    g.tie_list = p.tie_list;
+    g.tie_off = p.tie_off;
+    k_rot_tc<<<p.n_tiles, kTcThreads, smem_g, st>>>(p.mapA, p.mapB, p.mapA, p.mapB, g);
     return cudaGetLastError();
 }
 
@@ -682,6 +766,7 @@ cudaError_t launch_tc_generation(const StepArgs& a, const TcPlan& p, cudaStream_
         g.ascale = p.ascale;
         g.bscale = p.bscale;
         g.status = a.status;
+        g.sel = 0;
         if (ev) cudaEventRecord(ev[2], st);
         k_rot_tc<<<p.n_tiles, kTcThreads, smem_g, st>>>(p.mapA, p.mapB, p.split ? p.mapAlo : p.mapA, p.split ? p.mapBlo : p.mapB,
                                                  g);
@@ -693,7 +778,8 @@ cudaError_t launch_tc_generation(const StepArgs& a, const TcPlan& p, cudaStream_
     if (ev) cudaEventRecord(ev[4], st);
     e = cudaFuncSetAttribute(k_tc_ties, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s);
     if (e != cudaSuccess) return e;
-    k_tc_ties<<<p.tie_ctas, 256, smem_s, st>>>(a, p.row_exec, p.uscr, p.tie_list, p.tie_count, p.max_dpad);
+    k_tc_ties<<<p.tie_ctas, 256, smem_s, st>>>(a, p.row_exec, p.uscr, p.tie_list, p.tie_count, p.max_dpad,
+                                               p.tie_total);
     if (ev) cudaEventRecord(ev[5], st);
     return cudaGetLastError();
 }

@@ -398,3 +398,53 @@ def test_tc_fused_generation_equals_the_pipeline():
     for k in range(n):
         np.testing.assert_array_equal(res[0][0][k], res[1][0][k])
         np.testing.assert_array_equal(res[0][1][k], res[1][1][k])
+
+
+def test_tc_wide_four_kernel_generation_equals_the_pipeline():
+    """Operands wider than 256 elements: the four-kernel generation (k_tc_rank,
+    k_tc_trial2, k_rot_tc selecting in its epilogue, k_tc_ties2 over row groups
+    of 256) against the five-kernel pipeline (tc_unfused = 1), bit-identical
+    over three generations of random states (D 256..520, K extents differing
+    between tiles), and over a near-tie step on grids at D 129..1536, where the
+    tie kernel stages the fewest ties per chunk and z spans six row groups."""
+    import paper_2502_10470_gb300 as M
+    wl = _wl(seed=71)
+    pops, fits = random_state(wl, seed=13)
+    outs = []
+    for unfused in (0, 1):
+        b = make_batch(wl, M.METADE_PATH_BATCHED, prec=1, tc_unfused=unfused)
+        tc = json.loads(M.metade_plan_info(b.ctx))["tensor_core"]
+        assert tc["kernel"] == "k_rot_tc" and tc["kernels_per_generation"] == (5 if unfused else 4)
+        b.set_population(pops, fits)
+        b.set_theta(wl.theta)
+        M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 0, 3, b.best_f, b.best_i)
+        assert M.metade_sync(b.ctx) == M.METADE_OK
+        outs.append((b.get_population(), b.best_f.cpu().numpy(), b.best_i.cpu().numpy()))
+        b.close()
+    for k in range(wl.n_inst):
+        np.testing.assert_array_equal(outs[0][0][0][k], outs[1][0][0][k])
+        np.testing.assert_array_equal(outs[0][0][1][k], outs[1][0][1][k])
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
+    np.testing.assert_array_equal(outs[0][2], outs[1][2])
+    rng = np.random.default_rng(83)
+    dims = [300, 1536, 129, 1000, 520, 256]
+    n, NP = len(dims), 40
+    probs = [synth.make_problem(rng, d, k) for k, d in enumerate(dims)]
+    wt = synth.Workload(name="tc-ties-wide", problems=probs, inst_np=np.full(n, NP, dtype=np.int32),
+                        inst_prob=np.arange(n, dtype=np.int32), inst_group=np.arange(n, dtype=np.int32),
+                        n_groups=n, n_out=0, inner_gens=1, outer_gens=1, seed=17, one_shot=0)
+    grid = [(rng.integers(-12, 13, (NP, p.dim)) * 8.0).astype(np.float32) for p in probs]
+    res = []
+    for unfused in (0, 1):
+        b = make_batch(wt, M.METADE_PATH_BATCHED, prec=1, tc_unfused=unfused)
+        b.set_population(grid, [np.full(NP, np.inf, dtype=np.float32)] * n)
+        b.set_theta(np.tile(np.array([0.0, 1.0, 1, 1, 1, 1], dtype=np.float32), (n, 1)))
+        M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 0, 1, None, None)
+        b.set_theta(np.tile(np.array([2.0 ** -20, 0.0, 4, 4, 1, 1], dtype=np.float32), (n, 1)))
+        M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 1, 2, None, None)
+        assert M.metade_sync(b.ctx) == M.METADE_OK
+        res.append(b.get_population())
+        b.close()
+    for k in range(n):
+        np.testing.assert_array_equal(res[0][0][k], res[1][0][k])
+        np.testing.assert_array_equal(res[0][1][k], res[1][1][k])
