@@ -1243,17 +1243,20 @@ def _case_tile_d100():
 
 
 def _case_tc_d1000():
-    """The precision study's 64 x 512 x D1000 state, one generation in BF16
-    and one in bf16x3: two k_rot_tc launches (and one of each tc kernel)."""
+    """The precision study's 64 x 512 x D1000 state: initialisation (one
+    k_rot_tc evaluation launch) and 40 BF16 generations (k_tc_rank,
+    k_tc_trial, k_rot_tc selecting, k_tc_ties_wide once each per
+    generation; the near ties grow from about 300 to several hundred), then
+    one bf16x3 generation of the five-kernel pipeline."""
     import paper_2502_10470_gb300 as M
     import synth
     wl = synth.precision()
     probs = [(p.dim, p.obj, p.shift, p.rot) for p in wl.problems]
-    for prec in (M.METADE_BF16, M.METADE_BF16X3):
+    for prec, gens in ((M.METADE_BF16, 40), (M.METADE_BF16X3, 1)):
         b = M.Batch(probs, wl.inst_np, wl.inst_prob, seed=0, one_shot=0, prec=prec)
         b.set_theta(wl.theta)
         M.metade_init(b.ctx, b.pop, b.fit, 0)
-        M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 0, 1, None, None)
+        M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 0, gens, None, None)
         if M.metade_sync(b.ctx) != M.METADE_OK:
             raise SystemExit("device status not OK")
         b.close()

@@ -64,15 +64,32 @@ __device__ __forceinline__ void block_topk(const float* f, int np, int kp, int* 
         bool done = !active;
         for (int j0 = 0; j0 < np; j0 += 32) {
             if (__all_sync(kFull, done)) break;
-            const int jn = min(32, np - j0);
-            for (int jj = 0; jj < jn; ++jj) {
-                const int j = j0 + jj;
-                rank += better(f[j], j, fi, i) ? 1 : 0;
+            if (j0 + 32 <= np) {  // a whole block of 32: the loads issue back to back
+#pragma unroll 8
+                for (int jj = 0; jj < 32; ++jj) rank += better(f[j0 + jj], j0 + jj, fi, i) ? 1 : 0;
+            } else {
+                for (int j = j0; j < np; ++j) rank += better(f[j], j, fi, i) ? 1 : 0;
             }
             done = done || rank >= kp;
         }
         if (active && rank < kp) topk[rank] = i;
     }
+}
+
+// block_topk of fitness in global memory, on a copy in shared memory: each
+// thread's rank scan reads the whole array, which from global memory is bound
+// by its latency.  np <= kTopkStage (larger arrays are scanned where they
+// are).  Contains __syncthreads; callers __syncthreads before reading topk.
+constexpr int kTopkStage = 1024;
+__device__ __forceinline__ void block_topk_staged(const float* f, int np, int kp, int* topk) {
+    __shared__ float sf[kTopkStage];
+    if (np > kTopkStage) {
+        block_topk(f, np, kp, topk);
+        return;
+    }
+    for (int i = threadIdx.x; i < np; i += blockDim.x) sf[i] = f[i];
+    __syncthreads();
+    block_topk(sf, np, kp, topk);
 }
 
 // ------------------------------------------------------ warp reductions
@@ -361,10 +378,6 @@ __device__ __forceinline__ float warp_diff(int obj, int dim, const float* z, con
     return d0;
 }
 
-// Trial vector of individual i built by one warp: lanes own 4-coordinate
-// chunks.  X: generation-start rows (stride ldx), U: trial row out (global
-// or shared, 16-byte aligned), dbuf: u - o (shared).  Returns nothing; the
-// warp must __syncwarp before reading dbuf.
 // One 4-coordinate chunk j4..j4+3 of a trial: mutation from the loaded base
 // rows (a = x_bl, b = x_br, x = x_i) and the summed difference vectors
 // (sum = sum_q x_plus - x_minus, added in q order), then crossover (binomial
@@ -407,9 +420,14 @@ __device__ __forceinline__ void trial_chunk(const Strat& s, float K, int jrand, 
     }
 }
 
-__device__ __forceinline__ void warp_trial(const Strat& s, const Ctr& c, const Indiv& v, int i, int dim, int L,
-                                           const float* X, long long ldx, const float* o, float lo, float hi,
-                                           float* U, float* dbuf) {
+// Trial vector of individual i built by one warp, four coordinates per lane
+// and step: mutation, crossover and clip (trial_chunk).  X: generation-start
+// rows (stride ldx); U: trial row out (global or shared, 16-byte aligned);
+// u - o of the four coordinates (zero past dim) is handed to sink(j4, dd).
+template <typename Sink>
+__device__ __forceinline__ void warp_trial_to(const Strat& s, const Ctr& c, const Indiv& v, int i, int dim, int L,
+                                              const float* X, long long ldx, const float* o, float lo, float hi,
+                                              float* U, Sink&& sink) {
     const int lane = threadIdx.x & 31;
     const float K = (float)v.kraw * (1.0f / 16777216.0f);
     const float* xl = X + (long long)v.ibl * ldx;
@@ -429,8 +447,18 @@ __device__ __forceinline__ void warp_trial(const Strat& s, const Ctr& c, const I
         float uo[4], dd[4];
         trial_chunk(s, K, v.jrand, v.nstart, L, dim, j4, a, b, x, sum, w, o, lo, hi, uo, dd);
         *reinterpret_cast<float4*>(U + j4) = make_float4(uo[0], uo[1], uo[2], uo[3]);
-        *reinterpret_cast<float4*>(dbuf + j4) = make_float4(dd[0], dd[1], dd[2], dd[3]);
+        sink(j4, dd);
     }
+}
+
+// warp_trial_to with u - o stored to dbuf (shared, dim rounded up to 4); the
+// warp must __syncwarp before reading dbuf
+__device__ __forceinline__ void warp_trial(const Strat& s, const Ctr& c, const Indiv& v, int i, int dim, int L,
+                                           const float* X, long long ldx, const float* o, float lo, float hi,
+                                           float* U, float* dbuf) {
+    warp_trial_to(s, c, v, i, dim, L, X, ldx, o, lo, hi, U, [&](int j4, const float (&dd)[4]) {
+        *reinterpret_cast<float4*>(dbuf + j4) = make_float4(dd[0], dd[1], dd[2], dd[3]);
+    });
 }
 
 }  // namespace metade

@@ -48,7 +48,7 @@ __global__ void k_mlp_prologue(StepArgs a, const int* __restrict__ execs, int* t
         if (threadIdx.x == 0) set_status(a.status, 1);
         return;
     }
-    block_topk(a.fit + d.fit_off, d.np, d.kp, topk_all + d.fit_off);  // topk[0] is the best
+    block_topk_staged(a.fit + d.fit_off, d.np, d.kp, topk_all + d.fit_off);  // topk[0] is the best
 }
 
 __global__ void __launch_bounds__(256) k_mlp_trial(StepArgs a, const int* __restrict__ row_exec, int n_rows,

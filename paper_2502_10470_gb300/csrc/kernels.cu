@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(256) k_plain_gen(StepArgs a, int k, int* topk,
         return;
     }
     // phase 1: best and the pbest pool from the generation-start fitness
-    if (blockIdx.x == 0) block_topk(a.fit + d.fit_off, d.np, d.kp, topk);
+    if (blockIdx.x == 0) block_topk_staged(a.fit + d.fit_off, d.np, d.kp, topk);
     if (!grid_barrier(bar, base + gridDim.x, a.status)) return;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

@@ -102,7 +102,7 @@ struct NaArgs {
 __global__ void k_na_prologue(NaArgs a) {
     const Strat s = load_strat(a.theta, a.d.np);
     if (!s.ok) return;
-    block_topk(a.fit, a.d.np, a.d.kp, a.topk);
+    block_topk_staged(a.fit, a.d.np, a.d.kp, a.topk);
 }
 
 __global__ void __launch_bounds__(256) k_na_trial(NaArgs a) {

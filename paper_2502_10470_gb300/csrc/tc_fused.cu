@@ -93,7 +93,7 @@ __device__ __forceinline__ uint2 pack_bf16x4(const float (&d)[4]) {
 }
 
 // ------------------------------------------------------------ k_tc_trial2
-__global__ void __launch_bounds__(kTThreads, 4) k_tc_trial2(StepArgs a, const int* __restrict__ row_exec, int n_rows,
+__global__ void __launch_bounds__(kTThreads, 3) k_tc_trial2(StepArgs a, const int* __restrict__ row_exec, int n_rows,
                                                          const int* __restrict__ topk_all, float* uscr, uint8_t* aq,
                                                          int kp) {
     __shared__ int rec[kFields * kTRows];
@@ -704,8 +704,8 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_tc_ties2(TieArgs g) {
 }
 
 // ---------------------------------------------------------- k_tc_ties_wide
-constexpr int kWThreads = 128;                // threads of k_tc_ties_wide
-constexpr int kWRows = 4;                     // consecutive rows of z per thread
+constexpr int kWThreads = 256;                // threads of k_tc_ties_wide
+constexpr int kWRows = 2;                     // consecutive rows of z per thread
 constexpr int kWGroup = kWThreads * kWRows;   // rows of z per work item
 constexpr int kWMaxTies = 8;                  // near ties of one problem per chunk at most
 constexpr int kWCk = 16;                      // columns of R^T per stage
@@ -714,6 +714,7 @@ constexpr int kWStageR = kWCk * kWGroup;      // floats of R^T per stage (32 KB)
 constexpr int kWStageV = 2 * kWMaxTies * kWCk + kWCk;  // x and u of every tie, then o, for the stage's columns
 constexpr int kWStage = kWStageR + kWStageV;  // floats per stage
 static_assert(kWStage % 4 == 0, "stages start 16-byte aligned");
+static_assert(kWRows == 2, "the sweep loads two rows of R^T per column as a float2");
 
 struct TieWArgs {
     StepArgs a;
@@ -737,9 +738,9 @@ struct TieWArgs {
 // one problem, group of 512 rows of z).  R^T is streamed 16 columns at a time
 // through a 3-stage cp.async ring, together with those columns of x, u and o
 // of every tie of the chunk (x - o and u - x are formed once per stage); a
-// thread owns four consecutive rows and forms their z = R (x - o) and
-// dz = R (u - x) for every tie in FP32, a float4 of R^T against a float4 of
-// x - o (and u - x) per tie, so each shared-memory load feeds sixteen fmas.
+// thread owns two consecutive rows and forms their z = R (x - o) and
+// dz = R (u - x) for every tie in FP32, a float2 of R^T per column against a
+// float4 of x - o (and u - x) per tie and four columns.
 // Every fma chain runs in ascending k like every other FP32 rotation; the
 // columns past D are zero in all three operands (fma(0, 0, acc) == acc for an
 // accumulator that starts at +0), so the results are bit-identical to a plain
@@ -766,7 +767,7 @@ __device__ __forceinline__ void wide_sweep(int nst, int nb, const float* ring, f
         asm volatile("cp.async.wait_group %0;" ::"n"(kWStages - 1) : "memory");  // stage st has landed
         __syncthreads();
         const float* buf = ring + (size_t)(st % kWStages) * kWStage;
-        {  // x - o and u - x of the stage's columns, a thread per (tie, column)
+        if (tid < kWMaxTies * kWCk) {  // x - o and u - x of the stage's columns, a thread per (tie, column)
             const int t = tid / kWCk, k = tid - t * kWCk;
             const float* v = buf + kWStageR;
             const float x = v[t * kWCk + k], u = v[kWMaxTies * kWCk + t * kWCk + k], oo = v[2 * kWMaxTies * kWCk + k];
@@ -776,10 +777,13 @@ __device__ __forceinline__ void wide_sweep(int nst, int nb, const float* ring, f
         __syncthreads();
 #pragma unroll
         for (int c4 = 0; c4 < kWCk / 4; ++c4) {
-            float4 rt[4];
+            float rt[4][kWRows];  // R^T[c][this thread's rows] for the four columns c of the step
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-                rt[k] = *reinterpret_cast<const float4*>(buf + (4 * c4 + k) * kWGroup + kWRows * tid);
+            for (int k = 0; k < 4; ++k) {
+                const float2 r2 = *reinterpret_cast<const float2*>(buf + (4 * c4 + k) * kWGroup + kWRows * tid);
+                rt[k][0] = r2.x;
+                rt[k][1] = r2.y;
+            }
 #pragma unroll
             for (int t = 0; t < NB; ++t) {
                 const float4 x4 = *reinterpret_cast<const float4*>(sx + t * kWCk + 4 * c4);
@@ -787,14 +791,11 @@ __device__ __forceinline__ void wide_sweep(int nst, int nb, const float* ring, f
                 const float xk[4] = {x4.x, x4.y, x4.z, x4.w}, lk[4] = {l4.x, l4.y, l4.z, l4.w};
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    az[t][0] = fmaf(rt[k].x, xk[k], az[t][0]);
-                    az[t][1] = fmaf(rt[k].y, xk[k], az[t][1]);
-                    az[t][2] = fmaf(rt[k].z, xk[k], az[t][2]);
-                    az[t][3] = fmaf(rt[k].w, xk[k], az[t][3]);
-                    adz[t][0] = fmaf(rt[k].x, lk[k], adz[t][0]);
-                    adz[t][1] = fmaf(rt[k].y, lk[k], adz[t][1]);
-                    adz[t][2] = fmaf(rt[k].z, lk[k], adz[t][2]);
-                    adz[t][3] = fmaf(rt[k].w, lk[k], adz[t][3]);
+#pragma unroll
+                    for (int j = 0; j < kWRows; ++j) {
+                        az[t][j] = fmaf(rt[k][j], xk[k], az[t][j]);
+                        adz[t][j] = fmaf(rt[k][j], lk[k], adz[t][j]);
+                    }
                 }
             }
         }
@@ -806,8 +807,8 @@ __device__ __forceinline__ void wide_sweep(int nst, int nb, const float* ring, f
         for (int t = 0; t < NB; ++t) {
             if (t < nb) {
                 float* zt = zs + (size_t)(slot0 + t) * 2 * vs + r0;
-                *reinterpret_cast<float4*>(zt) = make_float4(az[t][0], az[t][1], az[t][2], az[t][3]);
-                *reinterpret_cast<float4*>(zt + vs) = make_float4(adz[t][0], adz[t][1], adz[t][2], adz[t][3]);
+                *reinterpret_cast<float2*>(zt) = make_float2(az[t][0], az[t][1]);
+                *reinterpret_cast<float2*>(zt + vs) = make_float2(adz[t][0], adz[t][1]);
             }
         }
     }
@@ -912,7 +913,7 @@ __global__ void __launch_bounds__(kWThreads, 2) k_tc_ties_wide(TieWArgs g) {
             asm volatile("cp.async.commit_group;" ::: "memory");  // one group per stage, empty past the end
         };
         for (int st = 0; st < kWStages - 1; ++st) issue(st);
-        const int r0 = rbase + kWRows * tid;  // this thread's first row (rows r0 .. r0 + 3 < D_pad)
+        const int r0 = rbase + kWRows * tid;  // this thread's first row (rows r0, r0 + 1 < D_pad)
         if (nb <= 1) wide_sweep<1>(nst, nb, ring, sx, sl, issue, g.zs, slot0, vs, r0, d.dim);
         else if (nb <= 2) wide_sweep<2>(nst, nb, ring, sx, sl, issue, g.zs, slot0, vs, r0, d.dim);
         else if (nb <= 4) wide_sweep<4>(nst, nb, ring, sx, sl, issue, g.zs, slot0, vs, r0, d.dim);
@@ -977,7 +978,7 @@ __global__ void k_tc_rank(StepArgs a, const int* __restrict__ execs, int* topk_a
         if (threadIdx.x == 0) set_status(a.status, 1);
         return;
     }
-    block_topk(a.fit + d.fit_off, d.np, d.kp, topk_all + d.fit_off);
+    block_topk_staged(a.fit + d.fit_off, d.np, d.kp, topk_all + d.fit_off);
 }
 
 size_t sel_smem(int kt) { return 1024 + kASize + kPartSize + (size_t)kt * kBT; }

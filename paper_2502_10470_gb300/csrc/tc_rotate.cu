@@ -355,13 +355,43 @@ __device__ __forceinline__ void pack_operand_row(const float* v, int dim, int kp
             row[j] = j < dim ? (uint8_t)__nv_cvt_float_to_fp8(v[j] * sc, __NV_SATFINITE, __NV_E4M3) : (uint8_t)0;
         return;
     }
+    // four elements per lane and step (kp is a multiple of 64, v holds round_up(dim, 4) floats)
     __nv_bfloat16* row = reinterpret_cast<__nv_bfloat16*>(q) + r * kp;
     __nv_bfloat16* row_lo = q_lo ? reinterpret_cast<__nv_bfloat16*>(q_lo) + r * kp : nullptr;
-    for (int j = lane; j < kp; j += 32) {
-        const float x = j < dim ? v[j] : 0.0f;
-        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-        row[j] = hi;
-        if (row_lo) row_lo[j] = __float2bfloat16_rn(x - __bfloat162float(hi));
+    for (int j = 4 * lane; j < kp; j += 128) {
+        float x[4];
+        if (j < dim) {
+            const float4 x4 = *reinterpret_cast<const float4*>(v + j);
+            x[0] = x4.x;
+            x[1] = j + 1 < dim ? x4.y : 0.0f;
+            x[2] = j + 2 < dim ? x4.z : 0.0f;
+            x[3] = j + 3 < dim ? x4.w : 0.0f;
+        } else {
+            x[0] = x[1] = x[2] = x[3] = 0.0f;
+        }
+        const __nv_bfloat162 h01 = __floats2bfloat162_rn(x[0], x[1]), h23 = __floats2bfloat162_rn(x[2], x[3]);
+        *reinterpret_cast<uint2*>(row + j) = make_uint2(*reinterpret_cast<const uint32_t*>(&h01),
+                                                        *reinterpret_cast<const uint32_t*>(&h23));
+        if (row_lo) {  // lo = bf16(x - hi)
+            const __nv_bfloat162 l01 = __floats2bfloat162_rn(x[0] - __low2float(h01), x[1] - __high2float(h01));
+            const __nv_bfloat162 l23 = __floats2bfloat162_rn(x[2] - __low2float(h23), x[3] - __high2float(h23));
+            *reinterpret_cast<uint2*>(row_lo + j) = make_uint2(*reinterpret_cast<const uint32_t*>(&l01),
+                                                               *reinterpret_cast<const uint32_t*>(&l23));
+        }
+    }
+}
+
+// Four BF16 operand elements at row[j..j+3] (8-byte aligned), and their lo
+// residuals bf16(x - hi) at row_lo when it is set.
+__device__ __forceinline__ void store_bf16x4(__nv_bfloat16* row, __nv_bfloat16* row_lo, int j, const float (&x)[4]) {
+    const __nv_bfloat162 h01 = __floats2bfloat162_rn(x[0], x[1]), h23 = __floats2bfloat162_rn(x[2], x[3]);
+    *reinterpret_cast<uint2*>(row + j) = make_uint2(*reinterpret_cast<const uint32_t*>(&h01),
+                                                    *reinterpret_cast<const uint32_t*>(&h23));
+    if (row_lo) {
+        const __nv_bfloat162 l01 = __floats2bfloat162_rn(x[0] - __low2float(h01), x[1] - __high2float(h01));
+        const __nv_bfloat162 l23 = __floats2bfloat162_rn(x[2] - __low2float(h23), x[3] - __high2float(h23));
+        *reinterpret_cast<uint2*>(row_lo + j) = make_uint2(*reinterpret_cast<const uint32_t*>(&l01),
+                                                           *reinterpret_cast<const uint32_t*>(&l23));
     }
 }
 
@@ -374,7 +404,7 @@ __global__ void k_tc_prologue(StepArgs a, const int* __restrict__ execs, int* to
         if (threadIdx.x == 0) set_status(a.status, 1);
         return;
     }
-    block_topk(a.fit + d.fit_off, d.np, d.kp, topk_all + d.fit_off);
+    block_topk_staged(a.fit + d.fit_off, d.np, d.kp, topk_all + d.fit_off);
 }
 
 // Trial rows (FP32, into the scratch U) and the GEMM operand d = u - o: BF16
@@ -382,7 +412,7 @@ __global__ void k_tc_prologue(StepArgs a, const int* __restrict__ execs, int* to
 // zero-padded to kp elements.
 // Warps of one block may belong to different executors: per-warp shared
 // scratch is strided by the bucket's widest row (ws floats).
-__global__ void __launch_bounds__(256) k_tc_trial(StepArgs a, const int* __restrict__ row_exec, int n_rows,
+__global__ void __launch_bounds__(256, 3) k_tc_trial(StepArgs a, const int* __restrict__ row_exec, int n_rows,
                                                   const int* __restrict__ topk_all, float* uscr, void* aq, void* aq_lo,
                                                   int kp, int ws, int fp8, float* ascale) {
     extern __shared__ __align__(16) float smt[];
@@ -394,17 +424,32 @@ __global__ void __launch_bounds__(256) k_tc_trial(StepArgs a, const int* __restr
     const int i = r - d.tc_row;
     const Strat s = load_strat(a.theta + 6 * k, d.np);
     if (!s.ok) return;
-    float* db = smt + (size_t)warp * ws;
     const uint32_t epoch = a.epoch_dev ? *a.epoch_dev : a.epoch;
     const Ctr c = make_ctr(a.key, (uint32_t)d.stream, a.gen0, (uint32_t)i, epoch);
     const int* topk = topk_all + d.fit_off;
     Indiv v;
     indiv_setup(s, c, i, d.np, d.dim, d.kp, topk, topk[0], v);
     const int L = s.cs == 2 ? exp_length(c, d.dim, s.cri) : 0;
-    warp_trial(s, c, v, i, d.dim, L, a.pop + d.pop_off, d.dpad, a.shift + d.shift_off, a.lo, a.hi,
-               uscr + d.pop_off + (long long)i * d.dpad, db);
-    __syncwarp();
-    pack_operand_row(db, d.dim, kp, aq, aq_lo, r, fp8, ascale + r);
+    float* U = uscr + d.pop_off + (long long)i * d.dpad;
+    // operand: none (FP32 GEMM on the CUDA cores), FP8 (the row's scale needs max |u - o| first, so u - o
+    // is staged in shared memory, ws floats per warp), or BF16 packed by each lane as it builds its four
+    // coordinates (hi, and lo = bf16(d - hi) when split).  One call site: the trial code is inlined once.
+    const int mode = !aq ? 0 : (fp8 ? 1 : 2);
+    float* db = smt + (size_t)warp * ws;
+    __nv_bfloat16* row = mode == 2 ? reinterpret_cast<__nv_bfloat16*>(aq) + (long long)r * kp : nullptr;
+    __nv_bfloat16* row_lo = mode == 2 && aq_lo ? reinterpret_cast<__nv_bfloat16*>(aq_lo) + (long long)r * kp : nullptr;
+    warp_trial_to(s, c, v, i, d.dim, L, a.pop + d.pop_off, d.dpad, a.shift + d.shift_off, a.lo, a.hi, U,
+                  [&](int j4, const float (&dd)[4]) {
+                      if (mode == 2) store_bf16x4(row, row_lo, j4, dd);
+                      else if (mode == 1) *reinterpret_cast<float4*>(db + j4) = make_float4(dd[0], dd[1], dd[2], dd[3]);
+                  });
+    if (mode == 1) {
+        __syncwarp();
+        pack_operand_row(db, d.dim, kp, aq, aq_lo, r, fp8, ascale + r);
+    } else if (mode == 2) {
+        const float zero[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int j = d.dpad + 4 * (threadIdx.x & 31); j < kp; j += 128) store_bf16x4(row, row_lo, j, zero);
+    }
 }
 
 // Greedy selection and row copy.  Near ties are only listed here; k_tc_ties
@@ -692,11 +737,8 @@ cudaError_t launch_tc_eval(const InstDesc* desc, const TcPlan& p, const float* p
 }
 
 cudaError_t launch_tc_trial_rows(const StepArgs& a, const TcPlan& p, cudaStream_t st) {
-    const size_t smem_t = (size_t)8 * p.max_dpad * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(k_tc_trial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
-    if (e != cudaSuccess) return e;
-    k_tc_trial<<<(p.n_rows + 7) / 8, 256, smem_t, st>>>(a, p.row_exec, p.n_rows, p.topk_all, p.uscr, p.aq, nullptr,
-                                                        p.kp, p.max_dpad, 0, p.ascale);
+    k_tc_trial<<<(p.n_rows + 7) / 8, 256, 0, st>>>(a, p.row_exec, p.n_rows, p.topk_all, p.uscr, p.aq, nullptr,
+                                                   p.kp, p.max_dpad, 0, p.ascale);
     return cudaGetLastError();
 }
 
@@ -740,7 +782,7 @@ cudaError_t launch_tc_generation(const StepArgs& a, const TcPlan& p, cudaStream_
     k_tc_prologue<<<p.n_exec, 256, 0, st>>>(a, p.execs, p.topk_all);
     if (ev) cudaEventRecord(ev[1], st);
     const int blocks = (p.n_rows + 7) / 8;
-    size_t smem_t = (size_t)8 * p.max_dpad * sizeof(float);
+    const size_t smem_t = p.fp8 ? (size_t)8 * p.max_dpad * sizeof(float) : 0;  // FP8 stages u - o per warp
     const size_t smem_s = (size_t)4 * p.max_dpad * (a.tie_fp64 ? sizeof(double) : sizeof(float));
     cudaError_t e = cudaFuncSetAttribute(k_tc_trial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
     if (e != cudaSuccess) return e;
