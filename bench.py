@@ -76,6 +76,10 @@ def parse_args(argv=None):
     ap.add_argument("--no-moderate", action="store_true", help="skip the moderate secondary key")
     ap.add_argument("--seeds", type=int, default=5, help="whole MetaDE runs of the full workload")
     ap.add_argument("--n-inst", type=int, default=64, help="executors of the precision study")
+    ap.add_argument("--tc-min-dim", type=int, default=0,
+                    help="width of the per-generation GEMM pipeline for the headline and batching studies "
+                         "(0: metade_autotune picks it)")
+    ap.add_argument("--tune-gens", type=int, default=5, help="generations metade_autotune times per candidate")
     ap.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES),
                     help="run one small untimed case for an ncu capture and exit")
     return ap.parse_args(argv)
@@ -486,7 +490,8 @@ def run_ours(args):
 
     def make(path, prec):
         return M.Batch(probs, wl.inst_np, wl.inst_prob, wl.inst_group, seed=wl.seed + rank, one_shot=1,
-                       n_out=wl.n_out, path=path, prec=prec, device=dev, stream=stream.cuda_stream)
+                       n_out=wl.n_out, path=path, prec=prec, device=dev, stream=stream.cuda_stream,
+                       tc_min_dim=args.tc_min_dim if path == M.METADE_PATH_BATCHED else 0)
 
     def barrier():
         torch.cuda.synchronize()
@@ -506,7 +511,7 @@ def run_ours(args):
     # autotune (tensor-core width, block shapes) on a real state: the first evolver generation's executors
     M.metade_outer_step(b.ctx, b.opop, b.ofit, b.trial, b.theta, None, 0, 0)
     M.metade_init(b.ctx, b.pop, b.fit, 0)
-    M.metade_autotune(b.ctx, b.pop, b.fit, b.theta, 5)
+    M.metade_autotune(b.ctx, b.pop, b.fit, b.theta, args.tune_gens)
     og = 0
     for _ in range(args.warmup):
         step(b, og)
@@ -953,11 +958,11 @@ def run_batching(args):
         if name == "plain" and args.no_plain:
             continue
         b = M.Batch(probs, wl.inst_np, wl.inst_prob, wl.inst_group, seed=wl.seed, one_shot=0, path=path, device=dev,
-                    stream=stream.cuda_stream)
+                    stream=stream.cuda_stream, tc_min_dim=args.tc_min_dim)
         b.set_theta(wl.theta)
         M.metade_init(b.ctx, b.pop, b.fit, 0)
         if path == M.METADE_PATH_BATCHED:
-            M.metade_autotune(b.ctx, b.pop, b.fit, b.theta, 5)
+            M.metade_autotune(b.ctx, b.pop, b.fit, b.theta, args.tune_gens)
         for w in range(1 if name == "plain" else args.warmup):
             M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, w * gens, gens, b.best_f, b.best_i)
         torch.cuda.synchronize()

@@ -118,7 +118,11 @@ typedef struct {
     int32_t tc_min_dim;        /* prec BF16 / BF16X3 / FP8E4M3: executors with D >= tc_min_dim run on
                                   the tensor cores, the others in FP32 on the CUDA cores.  0 = let
                                   metade_autotune choose among 33, 129 and 256 by speed (129 until it
-                                  runs); > 0 fixes it.  Ignored with FP32.  Negative: EINVAL */
+                                  runs); > 0 fixes it.  FP32: executors with D >= tc_min_dim (and every
+                                  one with D > 256) run the same per-generation pipeline with its GEMM
+                                  in FP32 on the CUDA cores, the others in the fused kernels; 0 = let
+                                  metade_autotune choose among 33, 129 and 257 (257 until it runs).
+                                  Negative: EINVAL */
     int32_t tc_unfused;        /* 0: BF16 tensor-core executors with D <= 256 (and FP32 difference-form
                                   ties) run four kernels per generation: ranking, trial rows, one
                                   kernel for the tcgen05 GEMM with objective, selection and the commit
@@ -299,10 +303,12 @@ METADE_API metade_status metade_plain_step_noalloc(float *pop, float *fit, const
 /* Wait for the context's stream; return and clear the sticky device status. */
 METADE_API metade_status metade_sync(metade_ctx *ctx);
 
-/* Autotuner: with cfg.tc_min_dim = 0 and BF16 / BF16X3 / FP8E4M3, first the
- * tensor-core width (33, 129 or 256: one untimed and n_gens timed
- * generations of every executor per width, on copies, keeping the fastest;
- * this changes which executors are evaluated in reduced precision).  Then,
+/* Autotuner: with cfg.tc_min_dim = 0, first the width of the per-generation
+ * GEMM pipeline (33, 129 or 256 with BF16 / BF16X3 / FP8E4M3; 33, 129 or 257
+ * with FP32): one untimed and n_gens timed generations of every executor per
+ * width, on copies, keeping the fastest; in reduced precision this changes
+ * which executors are evaluated in reduced precision, in FP32 only the order
+ * of the FP32 sums.  Then,
  * for every bucket of the batched path, time each candidate block
  * shape (small-D kernel: 32, 64, 128, 256 threads; tile kernel: 128 or 256
  * threads with R^T resident, 256 with R^T streamed; general kernel: 128, 256,
@@ -353,6 +359,10 @@ METADE_API metade_status metade_wait_check(int32_t arrive, uint32_t rounds, int3
 METADE_API int64_t metade_launch_count(const metade_ctx *ctx);
 
 METADE_API const char *metade_strerror(metade_status s);
+
+/* Name of the CUDA error behind the last METADE_ECUDA a call returned on this
+ * host thread ("cudaSuccess" if none was recorded). */
+METADE_API const char *metade_last_cuda_error(void);
 
 #ifdef __cplusplus
 }

@@ -31,7 +31,7 @@ EXPORTED = [
     "metade_init", "metade_inner_step", "metade_eval", "metade_eval_pop", "metade_outer_init", "metade_outer_step",
     "metade_outer_generation", "metade_draw_record", "metade_sync", "metade_plan_info",
     "metade_launch_count", "metade_strerror", "metade_plain_step_noalloc", "metade_profile",
-    "metade_profile_read", "metade_autotune", "metade_wait_check",
+    "metade_profile_read", "metade_autotune", "metade_wait_check", "metade_last_cuda_error",
 ]
 
 
@@ -39,6 +39,8 @@ class MetadeError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = status
         msg = _lib().metade_strerror(status).decode() if _LIB is not None else str(status)
+        if status == METADE_ECUDA and _LIB is not None:
+            msg += " " + _lib().metade_last_cuda_error().decode()
         super().__init__("%s: %s (status %d)" % (what, msg, status))
 
 
@@ -106,8 +108,10 @@ def _lib():
         L.metade_wait_check.argtypes = [I32, U32, P, P]
         L.metade_strerror.argtypes = [C.c_int]
         L.metade_strerror.restype = C.c_char_p
+        L.metade_last_cuda_error.argtypes = []
+        L.metade_last_cuda_error.restype = C.c_char_p
         for name in EXPORTED:
-            if name not in ("metade_destroy", "metade_launch_count", "metade_strerror"):
+            if name not in ("metade_destroy", "metade_launch_count", "metade_strerror", "metade_last_cuda_error"):
                 getattr(L, name).restype = C.c_int
         _LIB = L
     return _LIB

@@ -22,6 +22,9 @@ constexpr int kMaxDim = 1536;
 constexpr int kTcDefaultMinDim = 129;
 constexpr int kTcAltMinDim = 256;  // the widths metade_autotune also tries: every executor wider than the
 constexpr int kTcLowMinDim = 33;   // small-D kernel's reach, and only those of 256 and more
+// FP32: executors with D >= the width (or D_pad > 256) run the per-generation pipeline with the FP32
+// GEMM on the CUDA cores (k_rot_simt); the fused kernels keep the others.  257 unless set or tuned.
+constexpr int kSimtDefaultMinDim = 257;
 constexpr int kMaxNp = 1024;
 constexpr size_t kSmemLimit = 227 * 1024;
 
@@ -73,6 +76,9 @@ struct metade_ctx {
     int evolver = 0;  // 0 DE/rand/1/bin (Alg. 3), 1 PSO, 2 CSO, 3 NES (xNES)
     cudaStream_t st = nullptr;
     cudaStream_t cap = nullptr;  // private stream for graph capture
+    static constexpr int kSide = 3;
+    cudaStream_t side[kSide] = {};  // forked streams: size buckets run beside the per-generation pipelines
+    cudaEvent_t fork_ev = nullptr, join_ev[kSide] = {};
     std::vector<InstDesc> hdesc;
     std::vector<long long> pop_off;
     std::vector<long long> fit_off;
@@ -127,7 +133,13 @@ struct metade_ctx {
 
 namespace {
 
-metade_status cuda_status(cudaError_t e) { return e == cudaSuccess ? METADE_OK : METADE_ECUDA; }
+thread_local cudaError_t g_last_cuda = cudaSuccess;  // behind the last METADE_ECUDA of this thread
+
+metade_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return METADE_OK;
+    g_last_cuda = e;
+    return METADE_ECUDA;
+}
 
 #define CK(x)                                                \
     do {                                                     \
@@ -332,7 +344,8 @@ void free_tc(metade_ctx* c) {
 
 // Executors on the per-generation GEMM pipeline: with BF16 / bf16x3 / FP8,
 // every executor with D >= tc_min_dim (tensor cores); with FP32, the ones
-// too wide for the tile kernels (D_pad > 256, CUDA-core GEMM).  Their operand
+// with D >= tc_min_dim and every one too wide for the tile kernels (D_pad >
+// 256), with the GEMM on the CUDA cores.  Their operand
 // rows are ordered by problem, then executor (InstDesc.tc_row = first row),
 // so that a 128-row M tile of the tensor-core GEMM can span consecutive
 // executors of one problem: they share the B operand (the problem's R), and
@@ -357,7 +370,7 @@ metade_status setup_tc(metade_ctx* c) {
     if (reduced || simt) {
         for (int k = 0; k < c->n_inst; ++k) {
             const InstDesc& d = c->hdesc[k];
-            if (d.obj == kMlp || (simt ? d.dpad <= 256 : d.dim < c->tc_min_dim)) continue;
+            if (d.obj == kMlp || (d.dim < c->tc_min_dim && (!simt || d.dpad <= 256))) continue;
             tc_execs.push_back(k);
         }
         std::stable_sort(tc_execs.begin(), tc_execs.end(),
@@ -579,16 +592,39 @@ metade_status run_inner(metade_ctx* c, cudaStream_t st, float* pop, float* fit, 
         return METADE_OK;
     }
     StepArgs a = step_args(c, pop, fit, theta, epoch, epoch_dev, gen0, n_gens, best_f, best_i);
+    // The work of one call falls into independent units: each size bucket (one launch for all its
+    // generations), the tensor-core pipeline and the MLP pipeline (launches per generation).  They
+    // touch disjoint executors and scratch rows, so with more than one unit the buckets and the MLP
+    // pipeline run on forked streams beside the tensor-core pipeline on `st` (inside a capture:
+    // parallel branches of the graph), and `st` waits for all of them before the best reduction.
+    const int units = (int)c->buckets.size() + (c->tc ? 1 : 0) + (c->mlpp.n_rows > 0 ? 1 : 0);
+    int nside = 0;  // side streams forked so far
+    auto unit_stream = [&](int q, cudaStream_t* out) -> cudaError_t {  // the q-th unit placed beside `st`
+        *out = st;  // (st may be the legacy stream, 0)
+        if (units <= 1) return cudaSuccess;
+        const int sq = q % metade_ctx::kSide;
+        if (sq >= nside) {
+            cudaError_t e = nside == 0 ? cudaEventRecord(c->fork_ev, st) : cudaSuccess;
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side[sq], c->fork_ev, 0);
+            if (e != cudaSuccess) return e;
+            nside = sq + 1;
+        }
+        *out = c->side[sq];
+        return cudaSuccess;
+    };
+    int q_unit = 0;
     for (const Bucket& b : c->buckets) {
+        cudaStream_t bs;
+        CK(unit_stream(q_unit++, &bs));
         cudaEvent_t e0, e1;
-        const bool pr = prof_pair(c, st,
+        const bool pr = prof_pair(c, bs,
                                   b.plan.kind == 0   ? kProfFusedSmall
                                   : b.plan.kind == 3 ? (b.plan.rot_smem ? kProfFusedTile : kProfFusedTileStream)
                                                      : kProfFusedGeneral,
                                   &e0, &e1);
-        if (pr) cudaEventRecord(e0, st);
-        CK(launch_fused(a, c->work + b.work_off, b.n_work, b.plan, c->uscr, st));
-        if (pr) cudaEventRecord(e1, st);
+        if (pr) cudaEventRecord(e0, bs);
+        CK(launch_fused(a, c->work + b.work_off, b.n_work, b.plan, c->uscr, bs));
+        if (pr) cudaEventRecord(e1, bs);
         *launches += 1;
     }
     if (c->tc) {
@@ -606,15 +642,21 @@ metade_status run_inner(metade_ctx* c, cudaStream_t st, float* pop, float* fit, 
         }
     }
     if (c->mlpp.n_rows > 0) {  // MLP executors: four launches per generation
+        cudaStream_t ms = st;
+        if (c->tc) CK(unit_stream(q_unit++, &ms));
         cudaEvent_t e0, e1;
-        const bool pr = prof_pair(c, st, kProfFusedMlp, &e0, &e1);
-        if (pr) cudaEventRecord(e0, st);
+        const bool pr = prof_pair(c, ms, kProfFusedMlp, &e0, &e1);
+        if (pr) cudaEventRecord(e0, ms);
         for (int g = 0; g < n_gens; ++g) {
             StepArgs t = step_args(c, pop, fit, theta, epoch, epoch_dev, gen0 + (uint32_t)g, 1, nullptr, nullptr);
-            CK(launch_mlp_generation(t, c->mlpp, st));
+            CK(launch_mlp_generation(t, c->mlpp, ms));
             *launches += 4;
         }
-        if (pr) cudaEventRecord(e1, st);
+        if (pr) cudaEventRecord(e1, ms);
+    }
+    for (int sq = 0; sq < nside; ++sq) {  // join
+        CK(cudaEventRecord(c->join_ev[sq], c->side[sq]));
+        CK(cudaStreamWaitEvent(st, c->join_ev[sq], 0));
     }
     // the per-generation paths leave best_f / best_i to one reduction over
     // every executor (the fused kernels write their own too)
@@ -692,6 +734,8 @@ metade_status enqueue_outer_generation(metade_ctx* c, cudaStream_t st, float* op
 
 extern "C" {
 
+const char* metade_last_cuda_error(void) { return cudaGetErrorName(g_last_cuda); }
+
 const char* metade_strerror(metade_status s) {
     switch (s) {
     case METADE_OK: return "ok";
@@ -730,6 +774,11 @@ void metade_destroy(metade_ctx* c) {
     cudaFree(c->mlp_row_exec);
     cudaFree(c->mlp_topk);
     if (c->cap) cudaStreamDestroy(c->cap);
+    for (int q = 0; q < metade_ctx::kSide; ++q) {
+        if (c->side[q]) cudaStreamDestroy(c->side[q]);
+        if (c->join_ev[q]) cudaEventDestroy(c->join_ev[q]);
+    }
+    if (c->fork_ev) cudaEventDestroy(c->fork_ev);
     delete c;
 }
 
@@ -857,6 +906,12 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
     };
     cudaError_t e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) return fail(METADE_ECUDA);
+    e = cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming);
+    for (int q = 0; q < metade_ctx::kSide && e == cudaSuccess; ++q) {
+        e = cudaStreamCreateWithFlags(&c->side[q], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join_ev[q], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return fail(METADE_ECUDA);
     if (dalloc(&c->desc, c->n_inst) || dalloc(&c->row_inst, row_inst.size()) || dalloc(&c->rot, rpad) ||
         dalloc(&c->rotT, rpad) || dalloc(&c->shift, spad) || dalloc(&c->uscr, po) || dalloc(&c->fuscr, fo) ||
         dalloc(&c->topk, c->max_np) || dalloc(&c->status, 1) || dalloc(&c->gen_dev, 1) || dalloc(&c->bar, 1))
@@ -924,7 +979,8 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
     }
     c->tc_unfused = cfg->tc_unfused ? 1 : 0;
     c->tc_auto = cfg->tc_min_dim == 0;
-    c->tc_min_dim = cfg->tc_min_dim > 0 ? cfg->tc_min_dim : kTcDefaultMinDim;
+    c->tc_min_dim = cfg->tc_min_dim > 0 ? cfg->tc_min_dim
+                    : (c->prec == METADE_FP32 ? kSimtDefaultMinDim : kTcDefaultMinDim);
     if (c->n_inst > 0) {
         metade_status s = setup_tc(c);
         if (s == METADE_OK) s = build_plan(c);
@@ -1094,11 +1150,12 @@ metade_status metade_sync(metade_ctx* c) {
 metade_status metade_autotune(metade_ctx* c, const float* pop, const float* fit, const float* theta, int32_t n_gens) {
     if (!c || n_gens < 1 || (c->n_inst > 0 && (!pop || !fit || !theta))) return METADE_EINVAL;
     if (c->path != METADE_PATH_BATCHED || c->n_inst == 0) return METADE_OK;
-    const bool reduced = c->prec == METADE_BF16 || c->prec == METADE_BF16X3 || c->prec == METADE_FP8E4M3;
-    bool mid = false;  // executors whose place (tensor cores or CUDA cores) the width decides
+    const bool fp32 = c->prec == METADE_FP32;
+    const int alt_w = fp32 ? kSimtDefaultMinDim : kTcAltMinDim;
+    bool mid = false;  // executors whose place (per-generation GEMM pipeline or fused kernels) the width decides
     for (const InstDesc& d : c->hdesc)
-        mid = mid || (d.obj != kMlp && d.dim >= kTcLowMinDim && d.dim < kTcAltMinDim);
-    const bool tune_width = c->tc_auto && reduced && mid;
+        mid = mid || (d.obj != kMlp && d.dim >= kTcLowMinDim && d.dim < alt_w);
+    const bool tune_width = c->tc_auto && mid;
     if (c->buckets.empty() && !tune_width) return METADE_OK;
     // the plan changes: graphs captured with the old one are dropped
     for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
@@ -1119,7 +1176,7 @@ metade_status metade_autotune(metade_ctx* c, const float* pop, const float* fit,
         int best_w = c->tc_min_dim;
         float best_ms = -1.f;
         c->tc_tuned.clear();
-        for (int w : {kTcLowMinDim, kTcDefaultMinDim, kTcAltMinDim}) {
+        for (int w : {kTcLowMinDim, kTcDefaultMinDim, alt_w}) {
             c->tc_min_dim = w;
             st = setup_tc(c);
             if (st == METADE_OK) st = build_plan(c);

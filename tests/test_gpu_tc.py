@@ -448,3 +448,46 @@ def test_tc_wide_four_kernel_generation_equals_the_pipeline():
     for k in range(n):
         np.testing.assert_array_equal(res[0][0][k], res[1][0][k])
         np.testing.assert_array_equal(res[0][1][k], res[1][1][k])
+
+
+def test_fp32_width_runs_the_cuda_core_gemm_pipeline():
+    """FP32 with tc_min_dim = 129: the D = 129 .. 255 executors leave the fused
+    tile kernels for the per-generation pipeline with the FP32 GEMM on the
+    CUDA cores (k_rot_simt, 64-row tiles of each executor).  One step against
+    the oracle (trials at TRIAL_ATOL, FP32 fitness), then two generations with
+    stored fitness whose clear selections match the oracle's; the default
+    FP32 width (257) keeps them in the tile kernels."""
+    import paper_2502_10470_gb300 as M
+    wl = _wl_mid(seed=89)
+    d0 = make_batch(wl, M.METADE_PATH_BATCHED, prec=0)
+    plan = json.loads(M.metade_plan_info(d0.ctx))
+    assert plan["tc_min_dim"] == 257 and "tensor_core" not in plan
+    d0.close()
+    b = make_batch(wl, M.METADE_PATH_BATCHED, prec=0, tc_min_dim=129)
+    plan = json.loads(M.metade_plan_info(b.ctx))
+    assert plan["tensor_core"]["kernel"] == "k_rot_simt" and plan["tensor_core"]["executors"] == wl.n_inst
+    pops, fits = random_state(wl, seed=12, fit_inf=True)
+    b.set_population(pops, fits)
+    b.set_theta(wl.theta)
+    M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 1, 3, 1, None, None)
+    assert M.metade_sync(b.ctx) == M.METADE_OK
+    npops, nfits = b.get_population()
+    for k in range(wl.n_inst):
+        p = wl.problems[int(wl.inst_prob[k])]
+        out = oracle.pde_step(pops[k], fits[k], wl.theta[k], p.obj, p.shift, p.rot, seed=wl.seed, stream=k,
+                              epoch=1, gen=3)
+        assert np.abs(npops[k] - out["trial"]).max() < TRIAL_ATOL
+        check_fitness(nfits[k], npops[k], p, TOL[0], UNIT[0])
+    for g in range(4, 6):
+        pops, fits = b.get_population()
+        M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 1, g, 1, None, None)
+        assert M.metade_sync(b.ctx) == M.METADE_OK
+        npops, nfits = b.get_population()
+        for k in range(wl.n_inst):
+            p = wl.problems[int(wl.inst_prob[k])]
+            out = oracle.pde_step(pops[k], fits[k], wl.theta[k], p.obj, p.shift, p.rot, seed=wl.seed, stream=k,
+                                  epoch=1, gen=g)
+            decided = rel_err(out["ftrial"], fits[k]) > GAP[0]
+            acc = np.any(npops[k] != pops[k], axis=1) | (nfits[k] != fits[k])
+            np.testing.assert_array_equal(acc[decided], out["accept"].astype(bool)[decided])
+    b.close()
