@@ -496,7 +496,7 @@ metade_status setup_tc(metade_ctx* c) {
     t.tie_done = nullptr;
     t.tie_zs = nullptr;
     t.wide_ctas = 0;
-    if (t.fused == 2) {  // the row-split tie kernel's scratch: a chunk counter and z, dz per list slot
+    if (!c->tie_fp64 && tc_max_dpad > 256) {  // the row-split tie kernel's scratch: chunk counters, z and dz
         const size_t vs = (size_t)((tc_max_dpad + 3) & ~3);
         if (dalloc(&c->tc_tie_done, nrows) || dalloc(&c->tc_tie_zs, nrows * 2 * vs)) return METADE_ENOMEM;
         if (cudaMemset(c->tc_tie_done, 0, sizeof(int) * nrows) != cudaSuccess) return METADE_ECUDA;

@@ -106,6 +106,15 @@ cudaError_t launch_fused_tile(const StepArgs& a, const int* work, int n_work, co
                               cudaStream_t st);
 
 // Large-D executors on the tensor cores (tc_rotate.cu).
+// Per-problem near-tie lists of the tensor-core path (device arrays of a
+// TcPlan); tie_cnt null: one flat list instead.
+struct TieLists {
+    const int* prob_tp;   // problem -> index among the problems on the path
+    const int* tp_row0;   // per such problem: start of its list
+    int* tie_cnt;         // per such problem: ties listed
+    long long* tie_off;   // population offset of each listed tie's row
+};
+
 struct TcPlan {
     const int* execs;        // device [n_exec] executors of the bucket
     int n_exec;
@@ -169,6 +178,14 @@ int tc_ties_wide_ctas(int max_dpad);
 // k_tc_trial alone (trial rows and BF16 operand rows, a warp per row): the
 // trial kernel of plan mode 2
 cudaError_t launch_tc_trial_rows(const StepArgs& a, const TcPlan& p, cudaStream_t st);
+// k_tc_trial2 alone (32 rows per CTA): trial rows, and BF16 operand rows of kp
+// elements when aq is set
+cudaError_t launch_tc_trial_rows32(const StepArgs& a, const TcPlan& p, void* aq, cudaStream_t st);
+// k_tc_rank alone: pbest pools, and the queues and per-problem tie counts of the generation zeroed
+cudaError_t launch_tc_rank(const StepArgs& a, const TcPlan& p, cudaStream_t st);
+// The near ties listed per problem, FP32 difference form: k_tc_ties2 when every
+// D_pad <= 256, else k_tc_ties_wide (whose scratch the plan must hold)
+cudaError_t launch_tc_ties_batched(const StepArgs& a, const TcPlan& p, cudaStream_t st);
 // k_rot_tc with the selection in its epilogue (BF16): decisions against the stored
 // fitness, clear acceptances committed, near ties listed per problem for k_tc_ties2
 cudaError_t launch_rot_tc_select(const StepArgs& a, const TcPlan& p, cudaStream_t st);

@@ -203,11 +203,12 @@ __global__ void __launch_bounds__(kTThreads, 3) k_tc_trial2(StepArgs a, const in
     // keeps its row's fields in registers across its chunks.
     const int r = 8 * (warp & 3) + (lane >> 2);
     if (r0 + r >= n_rows) return;  // no barrier follows
-    uint8_t* arow = aq + (size_t)(r0 + r) * kp * 2;
+    uint8_t* arow = aq ? aq + (size_t)(r0 + r) * kp * 2 : nullptr;  // null: FP32 GEMM, no operand rows
     const int dpad = rec[F_DPAD * kTRows + r];
     // blocks of 4 chunks along K, up to the row's own K tiles (k_tc_sel reads no further)
     const int nchb = ((dpad + kBK - 1) / kBK) * (kBK / 16);
     if (!rec[F_VALID * kTRows + r]) {  // rows of an invalid theta: a zero operand row
+        if (!arow) return;
         for (int cb = warp >> 2; cb < nchb; cb += 2)
             *reinterpret_cast<uint2*>(arow + (size_t)(4 * (4 * cb + (lane & 3))) * 2) = make_uint2(0u, 0u);
         return;
@@ -267,7 +268,7 @@ __global__ void __launch_bounds__(kTThreads, 3) k_tc_trial2(StepArgs a, const in
             trial_chunk(s, K, jr, ns, L, dim, j4, av, bv, xv, sum, w, o, a.lo, a.hi, uo, dd);
             *reinterpret_cast<float4*>(U + j4) = make_float4(uo[0], uo[1], uo[2], uo[3]);
         }
-        *reinterpret_cast<uint2*>(arow + (size_t)j4 * 2) = pack_bf16x4(dd);
+        if (arow) *reinterpret_cast<uint2*>(arow + (size_t)j4 * 2) = pack_bf16x4(dd);
     }
 }
 
@@ -1004,18 +1005,20 @@ int tc_ties_wide_ctas(int max_dpad) {
     return per_sm * sms;
 }
 
-cudaError_t launch_tc_fused_generation(const StepArgs& a, const TcPlan& p, cudaStream_t st, cudaEvent_t* ev) {
-    if (ev) cudaEventRecord(ev[0], st);
+cudaError_t launch_tc_trial_rows32(const StepArgs& a, const TcPlan& p, void* aq, cudaStream_t st) {
+    k_tc_trial2<<<(p.n_rows + kTRows - 1) / kTRows, kTThreads, 0, st>>>(a, p.row_exec, p.n_rows, p.topk_all, p.uscr,
+                                                                       static_cast<uint8_t*>(aq), p.kp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_rank(const StepArgs& a, const TcPlan& p, cudaStream_t st) {
     k_tc_rank<<<p.n_exec, 256, 0, st>>>(a, p.execs, p.topk_all, p.next_tile, p.chunk_ctr, p.tie_cnt, p.n_tp);
-    if (ev) cudaEventRecord(ev[1], st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_ties_batched(const StepArgs& a, const TcPlan& p, cudaStream_t st) {
     cudaError_t e;
-    if (p.fused == 2) {  // operands wider than 256: warp-per-row trials, k_rot_tc selecting, row-split ties
-        e = launch_tc_trial_rows(a, p, st);
-        if (e != cudaSuccess) return e;
-        if (ev) cudaEventRecord(ev[2], st);
-        e = launch_rot_tc_select(a, p, st);
-        if (e != cudaSuccess) return e;
-        if (ev) cudaEventRecord(ev[3], st);
+    if (p.max_dpad > kVec) {
         TieWArgs tw;
         tw.a = a;
         tw.row_exec = p.row_exec;
@@ -1035,6 +1038,39 @@ cudaError_t launch_tc_fused_generation(const StepArgs& a, const TcPlan& p, cudaS
         e = cudaFuncSetAttribute(k_tc_ties_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         k_tc_ties_wide<<<p.wide_ctas, kWThreads, smem, st>>>(tw);
+        return cudaGetLastError();
+    }
+    TieArgs ta;
+    ta.a = a;
+    ta.row_exec = p.row_exec;
+    ta.n_tp = p.n_tp;
+    ta.tp_row0 = p.tp_row0;
+    ta.tie_cnt = p.tie_cnt;
+    ta.tie_list = p.tie_list;
+    ta.tie_off = p.tie_off;
+    ta.chunk_ctr = p.chunk_ctr;
+    ta.uscr = p.uscr;
+    ta.tie_total = p.tie_total;
+    e = cudaFuncSetAttribute(k_tc_ties2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTieSmem);
+    if (e != cudaSuccess) return e;
+    k_tc_ties2<<<2 * p.gen_ctas, kSelThreads, kTieSmem, st>>>(ta);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_fused_generation(const StepArgs& a, const TcPlan& p, cudaStream_t st, cudaEvent_t* ev) {
+    if (ev) cudaEventRecord(ev[0], st);
+    k_tc_rank<<<p.n_exec, 256, 0, st>>>(a, p.execs, p.topk_all, p.next_tile, p.chunk_ctr, p.tie_cnt, p.n_tp);
+    if (ev) cudaEventRecord(ev[1], st);
+    cudaError_t e;
+    if (p.fused == 2) {  // operands wider than 256: warp-per-row trials, k_rot_tc selecting, row-split ties
+        e = launch_tc_trial_rows(a, p, st);
+        if (e != cudaSuccess) return e;
+        if (ev) cudaEventRecord(ev[2], st);
+        e = launch_rot_tc_select(a, p, st);
+        if (e != cudaSuccess) return e;
+        if (ev) cudaEventRecord(ev[3], st);
+        e = launch_tc_ties_batched(a, p, st);
+        if (e != cudaSuccess) return e;
         if (ev) cudaEventRecord(ev[4], st);
         return cudaGetLastError();
     }
@@ -1063,20 +1099,8 @@ cudaError_t launch_tc_fused_generation(const StepArgs& a, const TcPlan& p, cudaS
         k_tc_sel<<<grid, kSelThreads + 32, smem, st>>>(p.mapA, p.mapB, g);
     }
     if (ev) cudaEventRecord(ev[3], st);
-    TieArgs ta;
-    ta.a = a;
-    ta.row_exec = p.row_exec;
-    ta.n_tp = p.n_tp;
-    ta.tp_row0 = p.tp_row0;
-    ta.tie_cnt = p.tie_cnt;
-    ta.tie_list = p.tie_list;
-    ta.tie_off = p.tie_off;
-    ta.chunk_ctr = p.chunk_ctr;
-    ta.uscr = p.uscr;
-    ta.tie_total = p.tie_total;
-    e = cudaFuncSetAttribute(k_tc_ties2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTieSmem);
+    e = launch_tc_ties_batched(a, p, st);
     if (e != cudaSuccess) return e;
-    k_tc_ties2<<<2 * p.gen_ctas, kSelThreads, kTieSmem, st>>>(ta);
     if (ev) cudaEventRecord(ev[4], st);
     return cudaGetLastError();
 }

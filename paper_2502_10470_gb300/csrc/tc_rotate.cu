@@ -452,12 +452,14 @@ __global__ void __launch_bounds__(256, 3) k_tc_trial(StepArgs a, const int* __re
     }
 }
 
-// Greedy selection and row copy.  Near ties are only listed here; k_tc_ties
-// decides them with a whole CTA each (a warp alone would stream two D x D
+// Greedy selection and row copy.  Near ties are only listed here: with FP32
+// difference-form ties per problem (fitness index and row offset, tl set) for
+// the batched tie kernels, else in one list of operand rows for k_tc_ties,
+// which decides each with a whole CTA (a warp alone would stream two D x D
 // rotations from L2 one row group at a time).
 __global__ void __launch_bounds__(256) k_tc_select(StepArgs a, const int* __restrict__ row_exec, int n_rows,
                                                    const float* __restrict__ uscr, const float* __restrict__ fu,
-                                                   int* tie_list, int* tie_count) {
+                                                   int* tie_list, int* tie_count, TieLists tl) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int r = blockIdx.x * (blockDim.x >> 5) + warp;
     if (r >= n_rows) return;
@@ -477,7 +479,16 @@ __global__ void __launch_bounds__(256) k_tc_select(StepArgs a, const int* __rest
         if (!__any_sync(kFull, diff)) tie = false, fn = fx;  // trial == target
     }
     if (tie) {
-        if (lane == 0) tie_list[atomicAdd(tie_count, 1)] = r;
+        if (lane == 0) {
+            if (tl.tie_cnt) {  // per problem, for the batched tie kernels: fitness index and row offset
+                const int tp = tl.prob_tp[d.prob];
+                const int q = tl.tp_row0[tp] + atomicAdd(&tl.tie_cnt[tp], 1);
+                tie_list[q] = d.fit_off + i;
+                tl.tie_off[q] = d.pop_off + (long long)i * d.dpad;
+            } else {
+                tie_list[atomicAdd(tie_count, 1)] = r;
+            }
+        }
         return;
     }
     if (fn <= fx) {
@@ -778,16 +789,27 @@ cudaError_t launch_wait_check(uint32_t rounds, int arrive, long long* out, int* 
 }
 
 cudaError_t launch_tc_generation(const StepArgs& a, const TcPlan& p, cudaStream_t st, cudaEvent_t* ev) {
+    const bool batched = !a.tie_fp64;  // FP32 difference-form ties: listed per problem, batched kernels
     if (ev) cudaEventRecord(ev[0], st);
-    k_tc_prologue<<<p.n_exec, 256, 0, st>>>(a, p.execs, p.topk_all);
+    if (batched) {
+        cudaError_t e0 = launch_tc_rank(a, p, st);  // also zeroes the per-problem tie counts
+        if (e0 != cudaSuccess) return e0;
+    } else {
+        k_tc_prologue<<<p.n_exec, 256, 0, st>>>(a, p.execs, p.topk_all);
+    }
     if (ev) cudaEventRecord(ev[1], st);
     const int blocks = (p.n_rows + 7) / 8;
     const size_t smem_t = p.fp8 ? (size_t)8 * p.max_dpad * sizeof(float) : 0;  // FP8 stages u - o per warp
     const size_t smem_s = (size_t)4 * p.max_dpad * (a.tie_fp64 ? sizeof(double) : sizeof(float));
     cudaError_t e = cudaFuncSetAttribute(k_tc_trial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
     if (e != cudaSuccess) return e;
-    k_tc_trial<<<blocks, 256, smem_t, st>>>(a, p.row_exec, p.n_rows, p.topk_all, p.uscr, p.aq, p.split ? p.aq_lo : nullptr,
-                                            p.kp, p.max_dpad, p.fp8, p.ascale);
+    if (p.simt && p.max_dpad <= 256) {  // narrow FP32 rows: 32 rows per CTA, a lane per (row, 4 coordinates)
+        e = launch_tc_trial_rows32(a, p, nullptr, st);
+        if (e != cudaSuccess) return e;
+    } else {
+        k_tc_trial<<<blocks, 256, smem_t, st>>>(a, p.row_exec, p.n_rows, p.topk_all, p.uscr, p.aq,
+                                                p.split ? p.aq_lo : nullptr, p.kp, p.max_dpad, p.fp8, p.ascale);
+    }
     if (p.simt) {
         if (ev) cudaEventRecord(ev[2], st);
         e = launch_rot_simt(a.desc, p.tiles, p.n_tiles, p.uscr, a.shift, a.rotT, p.fu, st);
@@ -814,14 +836,27 @@ cudaError_t launch_tc_generation(const StepArgs& a, const TcPlan& p, cudaStream_
                                                  g);
     }
     if (ev) cudaEventRecord(ev[3], st);
-    e = cudaMemsetAsync(p.tie_count, 0, sizeof(int), st);
-    if (e != cudaSuccess) return e;
-    k_tc_select<<<blocks, 256, 0, st>>>(a, p.row_exec, p.n_rows, p.uscr, p.fu, p.tie_list, p.tie_count);
+    TieLists tl{};
+    if (batched) {
+        tl.prob_tp = p.prob_tp;
+        tl.tp_row0 = p.tp_row0;
+        tl.tie_cnt = p.tie_cnt;
+        tl.tie_off = p.tie_off;
+    } else {
+        e = cudaMemsetAsync(p.tie_count, 0, sizeof(int), st);
+        if (e != cudaSuccess) return e;
+    }
+    k_tc_select<<<blocks, 256, 0, st>>>(a, p.row_exec, p.n_rows, p.uscr, p.fu, p.tie_list, p.tie_count, tl);
     if (ev) cudaEventRecord(ev[4], st);
-    e = cudaFuncSetAttribute(k_tc_ties, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s);
-    if (e != cudaSuccess) return e;
-    k_tc_ties<<<p.tie_ctas, 256, smem_s, st>>>(a, p.row_exec, p.uscr, p.tie_list, p.tie_count, p.max_dpad,
-                                               p.tie_total);
+    if (batched) {
+        e = launch_tc_ties_batched(a, p, st);
+        if (e != cudaSuccess) return e;
+    } else {
+        e = cudaFuncSetAttribute(k_tc_ties, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s);
+        if (e != cudaSuccess) return e;
+        k_tc_ties<<<p.tie_ctas, 256, smem_s, st>>>(a, p.row_exec, p.uscr, p.tie_list, p.tie_count, p.max_dpad,
+                                                   p.tie_total);
+    }
     if (ev) cudaEventRecord(ev[5], st);
     return cudaGetLastError();
 }
