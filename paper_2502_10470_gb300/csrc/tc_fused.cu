@@ -287,6 +287,7 @@ struct SelArgs {
     const long long* brow;    // per problem: first B row
     const float* uscr;        // trial rows (population layout)
     int kt;                   // K tiles of the widest problem (shared memory is cut for it)
+    const int* part;          // [gridDim.x + 1]: first tile of each CTA
 };
 
 // Named barrier of the 16 epilogue warps (the producer warp does not take part).
@@ -327,10 +328,9 @@ __global__ void __launch_bounds__(kSelThreads + 32, 1) k_tc_sel(const __grid_con
     __syncthreads();
     tc_fence_after();
     const uint32_t taddr = tmem_base;
-    // a contiguous block of tiles per CTA: tiles of one problem are adjacent, so B is loaded
-    // about once per problem (every tile costs about the same: near ties are decided elsewhere)
-    const int t_begin = (int)(((long long)g.n_tiles * blockIdx.x) / gridDim.x);
-    const int t_end = (int)(((long long)g.n_tiles * (blockIdx.x + 1)) / gridDim.x);
+    // a contiguous block of tiles per CTA, of about equal cost (rows x (D_pad + 32), split on the
+    // host): tiles of one problem are adjacent, so B is loaded about once per problem
+    const int t_begin = g.part[blockIdx.x], t_end = g.part[blockIdx.x + 1];
 
     if (warp == kEpiWarps) {
         // producer: A of tile j (and B at a new problem) once the MMAs of tile j - 1 are done with
@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(kSelThreads + 32, 1) k_tc_sel(const __grid_con
         if (lane == 0) {
             int cur_prob = -1;
             uint32_t aphase = 0, bphase = 0;
-            bool ok = true, a_fly = false, b_fly = false;
+            bool ok = true, a_fly = false, b_fly = false, mma_any = false;
             for (int t = t_begin; t < t_end && ok; ++t) {
                 const int j = t - t_begin, b = j & 1;
                 const int arow = g.tiles[2 * t];
@@ -379,13 +379,17 @@ __global__ void __launch_bounds__(kSelThreads + 32, 1) k_tc_sel(const __grid_con
                     for (int q = 0; q < kBK / 16; ++q) mma_bf16(dacc, ad + 2 * q, bd + 2 * q, (kk > 0 || q > 0) ? 1u : 0u);
                 }
                 mma_commit(&acc_full[b]);
+                mma_any = true;
             }
             if (!ok) set_status(a.status, kStatusTimeout);
-            // leave with no copy or MMA of this CTA in flight (bounded waits)
+            // leave with no copy or MMA of this CTA in flight (bounded waits); a CTA without
+            // tiles (the cost split may leave some empty) issued none
             if (a_fly) mbar_wait(&afull, aphase);
             if (b_fly) mbar_wait(&bfull, bphase);
-            mma_commit(&drain);
-            mbar_wait(&drain, 0u);
+            if (mma_any) {
+                mma_commit(&drain);
+                mbar_wait(&drain, 0u);
+            }
         }
         __syncwarp();
     } else {
@@ -1092,11 +1096,11 @@ cudaError_t launch_tc_fused_generation(const StepArgs& a, const TcPlan& p, cudaS
         g.brow = p.brow;
         g.uscr = p.uscr;
         g.kt = p.kp / kBK;
+        g.part = p.sel_part;
         const size_t smem = sel_smem(g.kt);
         e = cudaFuncSetAttribute(k_tc_sel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        const int grid = p.n_tiles < p.gen_ctas ? p.n_tiles : p.gen_ctas;
-        k_tc_sel<<<grid, kSelThreads + 32, smem, st>>>(p.mapA, p.mapB, g);
+        k_tc_sel<<<p.gen_ctas, kSelThreads + 32, smem, st>>>(p.mapA, p.mapB, g);  // CTAs past the tiles: no work
     }
     if (ev) cudaEventRecord(ev[3], st);
     e = launch_tc_ties_batched(a, p, st);
