@@ -1301,19 +1301,21 @@ def _case_simt_d1000():
 
 def _case_tc_d200():
     """The full workload (8 runs x 128 executors) in BF16 with the
-    tensor-core width 129, so the five D = 200 runs (640 executors, 78080
-    rows) take the three-kernel tensor-core path: initialisation and two
-    generations (k_tc_rank, k_tc_trial2, k_tc_sel twice each)."""
+    tensor-core width 33 that the autotuner picks for it, so the D = 100 and
+    D = 200 runs (seven of eight, 896 executors, rows ordered widest problem
+    first) take the four-kernel generation: initialisation and 40
+    generations (k_tc_rank, k_tc_trial2, k_tc_sel and k_tc_ties2 once each
+    per generation; the size-bucket kernel of the D = 20 run beside them)."""
     import paper_2502_10470_gb300 as M
     import synth
     wl = synth.full()
     probs = [(p.dim, p.obj, p.shift, p.rot) for p in wl.problems]
     b = M.Batch(probs, wl.inst_np, wl.inst_prob, wl.inst_group, seed=wl.seed, one_shot=1, n_out=wl.n_out,
-                prec=M.METADE_BF16, tc_min_dim=129)
+                prec=M.METADE_BF16, tc_min_dim=33)
     M.metade_outer_init(b.ctx, b.opop, b.ofit)
     M.metade_outer_step(b.ctx, b.opop, b.ofit, b.trial, b.theta, None, 0, 0)
     M.metade_init(b.ctx, b.pop, b.fit, 0)
-    M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 0, 2, b.best_f, b.best_i)
+    M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 0, 40, b.best_f, b.best_i)
     if M.metade_sync(b.ctx) != M.METADE_OK:
         raise SystemExit("device status not OK")
     b.close()

@@ -121,7 +121,6 @@ struct metade_ctx {
     int* tc_tp = nullptr;  // problem -> path index, first rows, tie counts
     long long* tc_tie_off = nullptr;  // population offsets of listed near ties
     unsigned long long* tie_total = nullptr;  // near ties decided by the tensor-core path since the last read
-    int* tc_sel_part = nullptr;       // k_tc_sel: first tile of each persistent CTA (and the tile count)
     int* tc_tie_done = nullptr;       // wide four-kernel generation: row groups finished per tie chunk
     float* tc_tie_zs = nullptr;       // wide four-kernel generation: z and dz of each listed tie
     uint8_t *aq = nullptr, *aq_lo = nullptr, *bq = nullptr, *bq_lo = nullptr;  // BF16 pairs or e4m3 bytes
@@ -329,8 +328,6 @@ void free_tc(metade_ctx* c) {
     cudaFree(c->tc_tie_off);
     cudaFree(c->tc_tie_done);
     cudaFree(c->tc_tie_zs);
-    cudaFree(c->tc_sel_part);
-    c->tc_sel_part = nullptr;
     c->tc_tp = nullptr;
     c->tc_tie_off = nullptr;
     c->tc_tie_done = nullptr;
@@ -433,28 +430,7 @@ metade_status setup_tc(metade_ctx* c) {
         (fp8 && (dalloc(&c->ascale, nrows) || dalloc(&c->bscale, (size_t)c->n_prob) || dalloc(&c->amax, 1))) ||
         dalloc(&c->tc_tp, (size_t)c->n_prob + 2 * tp_row0.size() + 1) || dalloc(&c->tc_tie_off, nrows))
         return METADE_ENOMEM;
-    // k_tc_sel's persistent CTAs take contiguous blocks of tiles of about equal cost: a tile costs
-    // about its rows x (D_pad + 32) (the epilogue's columns, the commit's row copies, the K tiles)
     const int sel_ctas = std::max(1, device_sms());
-    {
-        const size_t nt = tc_tiles.size() / 2;
-        std::vector<double> cum(nt + 1, 0.0);
-        for (size_t q = 0; q < nt && !simt; ++q) {
-            const InstDesc& d = c->hdesc[tc_row_exec[tc_tiles[2 * q]]];
-            cum[q + 1] = cum[q] + (double)tc_tiles[2 * q + 1] * (d.dpad + 32);
-        }
-        std::vector<int> part(sel_ctas + 1, 0);
-        size_t q = 0;
-        for (int b = 1; b < sel_ctas; ++b) {  // the first tile whose cost prefix reaches b / sel_ctas of the total
-            const double target = cum[nt] * b / sel_ctas;
-            while (q < nt && cum[q] < target) ++q;
-            part[b] = (int)q;
-        }
-        part[sel_ctas] = (int)nt;
-        if (dalloc(&c->tc_sel_part, part.size())) return METADE_ENOMEM;
-        if (cudaMemcpy(c->tc_sel_part, part.data(), sizeof(int) * part.size(), cudaMemcpyHostToDevice))
-            return METADE_ECUDA;
-    }
     std::vector<int> tp_host(prob_tp);
     tp_host.insert(tp_host.end(), tp_row0.begin(), tp_row0.end());
     tp_host.resize((size_t)c->n_prob + 2 * tp_row0.size() + 1, 0);
@@ -517,7 +493,6 @@ metade_status setup_tc(metade_ctx* c) {
     if (c->prec == METADE_BF16 && !c->tie_fp64 && !c->tc_unfused) t.fused = tc_fused_fits(tc_kp) ? 1 : 2;
     else t.fused = 0;
     t.gen_ctas = sel_ctas;
-    t.sel_part = c->tc_sel_part;
     if (!c->tie_total) {  // kept across plans: the count runs until the next profile read
         if (dalloc(&c->tie_total, 1)) return METADE_ENOMEM;
         if (cudaMemset(c->tie_total, 0, sizeof(unsigned long long)) != cudaSuccess) return METADE_ECUDA;

@@ -146,7 +146,6 @@ struct TcPlan {
     int* tie_cnt;            // device [n_tp]: near ties listed per problem
     int* chunk_ctr;          // device counter of k_tc_ties2's chunk queue
     int gen_ctas;            // CTAs of k_tc_sel (one per SM)
-    const int* sel_part;     // device [gen_ctas + 1]: first tile of each k_tc_sel CTA, blocks of about equal cost
     unsigned long long* tie_total;  // device counter: near ties decided (read and cleared by the profile read)
     int* tie_done;           // device [n_rows] plan mode 2: row groups finished per tie chunk (kept at zero)
     float* tie_zs;           // device [n_rows][2][round_up(max_dpad, 4)] plan mode 2: z and dz of listed ties

@@ -14,10 +14,11 @@
 //               arithmetic every trial kernel shares), the FP32 trial row and
 //               the BF16 operand u - o, K-padded, to global memory.  Many small
 //               CTAs per SM keep many row gathers in flight;
-//   k_tc_sel    persistent, one CTA per SM, over a contiguous block of the
-//               128-row M tiles (rows of one problem, possibly of several
-//               executors), warp-specialised: a producer warp issues the TMA
-//               loads of the A tile and, once per problem, of B (the
+//   k_tc_sel    persistent, one CTA per SM, taking the 128-row M tiles
+//               (rows of one problem, possibly of several executors) in
+//               order from a counter, warp-specialised: a producer warp
+//               issues the TMA loads of the A tile and, where the problem
+//               changes, of B (the
 //               problem's padded BF16 R rows, kept in shared memory while the
 //               CTA's tiles belong to that problem) and the tcgen05.mma
 //               (M 128, N 256, K 16, FP32 accumulate) into one of two TMEM
@@ -287,7 +288,6 @@ struct SelArgs {
     const long long* brow;    // per problem: first B row
     const float* uscr;        // trial rows (population layout)
     int kt;                   // K tiles of the widest problem (shared memory is cut for it)
-    const int* part;          // [gridDim.x + 1]: first tile of each CTA
 };
 
 // Named barrier of the 16 epilogue warps (the producer warp does not take part).
@@ -296,9 +296,9 @@ __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n
 __global__ void __launch_bounds__(kSelThreads + 32, 1) k_tc_sel(const __grid_constant__ CUtensorMap tmA,
                                                                 const __grid_constant__ CUtensorMap tmB, SelArgs g) {
     extern __shared__ uint8_t smraw[];
-    __shared__ __align__(8) uint64_t afull, bfull, acc_full[2], acc_empty[2], drain;
+    __shared__ __align__(8) uint64_t afull, bfull, acc_full[2], acc_empty[2], drain, tile_ready[2];
     __shared__ uint32_t tmem_base;
-    __shared__ int ep_abort_s, nacc_s;
+    __shared__ int ep_abort_s, nacc_s, tile_of[2];  // tile in accumulator b (-1: no more tiles)
     __shared__ int acc_row[kRows];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
     uint8_t* As = sm;
@@ -319,6 +319,7 @@ __global__ void __launch_bounds__(kSelThreads + 32, 1) k_tc_sel(const __grid_con
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
             mbar_init(&acc_empty[b], kEpiWarps);  // one arrival per epilogue warp
+            mbar_init(&tile_ready[b], 1);
         }
         mbar_init(&drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -328,9 +329,10 @@ __global__ void __launch_bounds__(kSelThreads + 32, 1) k_tc_sel(const __grid_con
     __syncthreads();
     tc_fence_after();
     const uint32_t taddr = tmem_base;
-    // a contiguous block of tiles per CTA, of about equal cost (rows x (D_pad + 32), split on the
-    // host): tiles of one problem are adjacent, so B is loaded about once per problem
-    const int t_begin = g.part[blockIdx.x], t_end = g.part[blockIdx.x + 1];
+    // Tiles are handed out in order (blockIdx.x first, then an atomic counter): tiles differ in
+    // cost (D, the objective, the accepted rows to copy), and consecutive tiles mostly belong to
+    // one problem (its tiles are adjacent), so B is reloaded only where the problem changes.  The
+    // producer posts each tile's index per accumulator (tile_ready), -1 when none is left.
 
     if (warp == kEpiWarps) {
         // producer: A of tile j (and B at a new problem) once the MMAs of tile j - 1 are done with
@@ -340,8 +342,21 @@ __global__ void __launch_bounds__(kSelThreads + 32, 1) k_tc_sel(const __grid_con
             int cur_prob = -1;
             uint32_t aphase = 0, bphase = 0;
             bool ok = true, a_fly = false, b_fly = false, mma_any = false;
-            for (int t = t_begin; t < t_end && ok; ++t) {
-                const int j = t - t_begin, b = j & 1;
+            int j = 0;
+            bool posted = false;  // tile j's index is posted
+            for (;; ++j) {
+                const int b = j & 1;
+                posted = false;
+                const int t = j == 0 ? (int)blockIdx.x : (int)gridDim.x + atomicAdd(g.next_tile, 1);
+                // accumulator b's slot is free once the epilogue released tile j - 2
+                if (j >= 2 && !mbar_wait(&acc_empty[b], (uint32_t)((j - 2) >> 1) & 1u)) {
+                    ok = false;
+                    break;
+                }
+                posted = true;
+                tile_of[b] = t < g.n_tiles ? t : -1;
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tile_ready[b])) : "memory");
+                if (t >= g.n_tiles) break;
                 const int arow = g.tiles[2 * t];
                 const InstDesc d = a.desc[g.row_exec[arow]];
                 const int kt = (d.dpad + kBK - 1) / kBK;
@@ -368,7 +383,6 @@ __global__ void __launch_bounds__(kSelThreads + 32, 1) k_tc_sel(const __grid_con
                     bphase ^= 1u;
                     b_fly = false;
                 }
-                if (ok && j >= 2) ok = mbar_wait(&acc_empty[b], (uint32_t)((j - 2) >> 1) & 1u);
                 if (!ok) break;
                 tc_fence_after();
                 const uint32_t dacc = taddr + (uint32_t)(b * kBN);
@@ -381,9 +395,18 @@ __global__ void __launch_bounds__(kSelThreads + 32, 1) k_tc_sel(const __grid_con
                 mma_commit(&acc_full[b]);
                 mma_any = true;
             }
-            if (!ok) set_status(a.status, kStatusTimeout);
-            // leave with no copy or MMA of this CTA in flight (bounded waits); a CTA without
-            // tiles (the cost split may leave some empty) issued none
+            if (!ok) {
+                set_status(a.status, kStatusTimeout);
+                // a tile that was posted ends the epilogue by its own bounded wait on acc_full; an
+                // unposted slot gets -1, so the epilogue stops there (it read the slot's old index
+                // before releasing tile j - 2, or never got that far)
+                if (!posted) {
+                    tile_of[j & 1] = -1;
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tile_ready[j & 1]))
+                                 : "memory");
+                }
+            }
+            // leave with no copy or MMA of this CTA in flight (bounded waits)
             if (a_fly) mbar_wait(&afull, aphase);
             if (b_fly) mbar_wait(&bfull, bphase);
             if (mma_any) {
@@ -396,8 +419,14 @@ __global__ void __launch_bounds__(kSelThreads + 32, 1) k_tc_sel(const __grid_con
         // epilogue warps: warp w reads TMEM lanes 32 (w % 4).. and column part w / 4
         const int qd = warp & 3, prt = warp >> 2;
         const int row = 32 * qd + lane;
-        for (int t = t_begin; t < t_end; ++t) {
-            const int j = t - t_begin, b = j & 1;
+        for (int j = 0;; ++j) {
+            const int b = j & 1;
+            if (!__all_sync(kFull, mbar_wait(&tile_ready[b], (uint32_t)(j >> 1) & 1u) ? 1 : 0)) {  // bounded
+                if (lane == 0) set_status(a.status, kStatusTimeout);
+                break;
+            }
+            const int t = tile_of[b];
+            if (t < 0) break;  // the same for every epilogue warp
             const int arow = g.tiles[2 * t], nr = g.tiles[2 * t + 1];
             const InstDesc d = a.desc[g.row_exec[arow]];  // dim, objective and problem of every row of the tile
             ObjR acc;
@@ -513,14 +542,13 @@ struct TieArgs {
 
 // The near ties of the generation, up to kTieBatch ties of one problem per
 // chunk (fewer when ties are few), chunks handed out by an atomic counter
-// over every CTA of the GPU (two per
-// SM): z = R (x - o) and dz = R (u - x) in FP32, R staged through shared
-// memory 16 columns at a time by cp.async in a ring of kRing stages, a
-// thread per
-// (row of z, half of the chunk's ties) with float4 loads along k, every fma
-// chain in ascending k; then a warp per tie forms the FP32 difference form
-// f(u) - f(x), decides and commits.  A trial identical to its target
-// (u - x == 0 everywhere, pad included) is accepted as it is.
+// over every CTA of the GPU (two per SM): z = R (x - o) and dz = R (u - x)
+// in FP32, R staged through shared memory 16 columns at a time by cp.async
+// in a ring of kRing stages, a thread per (row of z, group of the chunk's
+// ties; the narrower the problem, the more groups) with float4 loads along
+// k, every fma chain in ascending k; then a warp per tie forms the FP32
+// difference form f(u) - f(x), decides and commits.  A trial identical to
+// its target (u - x == 0 everywhere, pad included) is accepted as it is.
 __global__ void __launch_bounds__(kSelThreads, 2) k_tc_ties2(TieArgs g) {
     extern __shared__ uint8_t smraw[];
     __shared__ int tp_s, j0_s, bsz_s, ncum_s[kMaxTpSmem + 1];
@@ -530,13 +558,16 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_tc_ties2(TieArgs g) {
     float* vx = tv;                          // [kTieBatch][kVec] x - o, then z
     float* vl = tv + kTieBatch * kVec;       // u - x, then dz
     float* sR = tv + 2 * kTieBatch * kVec;   // [kRing][kVec][kRcs]: R columns c0 .. c0 + 15 of every row
-    // chunk size: the ties of the generation spread over every CTA in about one round (few
-    // ties: small chunks, so no SM waits behind another's long chunk), between 2 and
+    // chunk size: as few whole rounds of chunks over the grid as full chunks need, filled evenly
+    // (few ties: small chunks, so no SM waits behind another's long chunk), between 2 and
     // kTieBatch; every CTA derives the same size from the same final counts (k_tc_sel has ended)
     if (tid == 0) {
         long long total = 0;
         for (int q = 0; q < g.n_tp; ++q) total += g.tie_cnt[q];
-        bsz_s = (int)min((long long)kTieBatch, max(2LL, (total + gridDim.x - 1) / gridDim.x));
+        // rounds of chunks over the grid at full chunks, then the chunk that fills those rounds evenly
+        const long long rounds = max(1LL, (total + (long long)gridDim.x * kTieBatch - 1) / ((long long)gridDim.x * kTieBatch));
+        const long long per = (long long)gridDim.x * rounds;
+        bsz_s = (int)min((long long)kTieBatch, max(2LL, (total + per - 1) / per));
         if (blockIdx.x == 0) atomicAdd(g.tie_total, (unsigned long long)total);
     }
     __syncthreads();
@@ -620,12 +651,17 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_tc_ties2(TieArgs g) {
                                                                             u4.w - x4.w);
             }
         }
-        // thread (row r, half h): ties h, h + 2, h + 4, ... of the chunk
-        const int r = tid & (kVec - 1), h = tid >> 8;
+        // thread (row r, group h) of G = 512 / vrow groups, vrow = the rows rounded up to a power of
+        // two (32 .. 256): ties h, h + G, h + 2 G, ... of the chunk, so narrow problems keep every
+        // thread busy (G <= 16 = kTieBatch: at most eight ties per thread, G = 2 at D > 128)
+        int lg = 5;
+        while ((1 << lg) < d.dim) ++lg;
+        const int G = kSelThreads >> lg;
+        const int r = tid & ((1 << lg) - 1), h = tid >> lg;
         float az[kTieBatch / 2], adz[kTieBatch / 2];
 #pragma unroll
         for (int q = 0; q < kTieBatch / 2; ++q) az[q] = adz[q] = 0.f;
-        const int mine = (nb - h + 1) >> 1;  // ties of this half (warp-uniform)
+        const int mine = (nb - h + G - 1) / G;  // ties of this group (warp-uniform: vrow >= 32)
         for (int ch = 0; ch < nchunk; ++ch) {
             stage(ch + kRing - 1);  // the stage read at ch - 1 is free: every thread passed the barrier after it
             asm volatile("cp.async.wait_group %0;" ::"n"(kRing - 1) : "memory");  // stage ch has landed
@@ -641,7 +677,7 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_tc_ties2(TieArgs g) {
 #pragma unroll
                         for (int j = 0; j < kTieBatch / 2; ++j) {
                             if (j < mine) {
-                                const int q = h + 2 * j;
+                                const int q = h + G * j;
                                 const float4 x4 = *reinterpret_cast<const float4*>(vx + q * kVec + c0 + 4 * c4);
                                 const float4 l4 = *reinterpret_cast<const float4*>(vl + q * kVec + c0 + 4 * c4);
                                 az[j] = fmaf(rt.x, x4.x, az[j]);
@@ -661,7 +697,7 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_tc_ties2(TieArgs g) {
 #pragma unroll
                         for (int j = 0; j < kTieBatch / 2; ++j) {
                             if (j < mine) {
-                                const int q = h + 2 * j;
+                                const int q = h + G * j;
                                 az[j] = fmaf(rt, vx[q * kVec + c0 + cc], az[j]);
                                 adz[j] = fmaf(rt, vl[q * kVec + c0 + cc], adz[j]);
                             }
@@ -676,8 +712,8 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_tc_ties2(TieArgs g) {
 #pragma unroll
             for (int j = 0; j < kTieBatch / 2; ++j) {
                 if (j < mine) {
-                    vx[(h + 2 * j) * kVec + r] = az[j];
-                    vl[(h + 2 * j) * kVec + r] = adz[j];
+                    vx[(h + G * j) * kVec + r] = az[j];
+                    vl[(h + G * j) * kVec + r] = adz[j];
                 }
             }
         }
@@ -831,7 +867,10 @@ __global__ void __launch_bounds__(kWThreads, 2) k_tc_ties_wide(TieWArgs g) {
     if (tid == 0) {  // chunk size: about one round of items over the grid, 1 .. kWMaxTies ties
         long long total = 0;
         for (int q = 0; q < g.n_tp; ++q) total += g.tie_cnt[q];
-        bsz_s = (int)min((long long)kWMaxTies, max(1LL, (total * g.ngmax + gridDim.x - 1) / gridDim.x));
+        const long long work = total * g.ngmax;  // (tie, row group) pairs
+        const long long rounds = max(1LL, (work + (long long)gridDim.x * kWMaxTies - 1) / ((long long)gridDim.x * kWMaxTies));
+        const long long per = (long long)gridDim.x * rounds;
+        bsz_s = (int)min((long long)kWMaxTies, max(1LL, (work + per - 1) / per));
         if (blockIdx.x == 0) atomicAdd(g.tie_total, (unsigned long long)total);
     }
     __syncthreads();
@@ -1096,11 +1135,11 @@ cudaError_t launch_tc_fused_generation(const StepArgs& a, const TcPlan& p, cudaS
         g.brow = p.brow;
         g.uscr = p.uscr;
         g.kt = p.kp / kBK;
-        g.part = p.sel_part;
         const size_t smem = sel_smem(g.kt);
         e = cudaFuncSetAttribute(k_tc_sel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_tc_sel<<<p.gen_ctas, kSelThreads + 32, smem, st>>>(p.mapA, p.mapB, g);  // CTAs past the tiles: no work
+        const int grid = p.n_tiles < p.gen_ctas ? p.n_tiles : p.gen_ctas;
+        k_tc_sel<<<grid, kSelThreads + 32, smem, st>>>(p.mapA, p.mapB, g);
     }
     if (ev) cudaEventRecord(ev[3], st);
     e = launch_tc_ties_batched(a, p, st);

@@ -112,24 +112,29 @@ def _bf16_bits(x32):
     return ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) & 0xFFFF
 
 
-@pytest.mark.parametrize("tie_fp64", [0, 1], ids=["difference", "fp64"])
-def test_tc_near_ties_decided_like_fp64(tie_fp64):
+@pytest.mark.parametrize("D,tie_fp64", [(256, 0), (256, 1), (40, 0), (100, 0), (200, 0), (600, 0)],
+                         ids=["D256-difference", "D256-fp64", "D40-difference", "D100-difference",
+                              "D200-difference", "D600-difference"])
+def test_tc_near_ties_decided_like_fp64(D, tie_fp64):
     """Near ties on the tensor-core path.  A first step with F = 0, CR = 1 and
     stored fitness +inf makes every trial a copy of another grid point and
     stores its BF16 fitness.  A second step moves one coordinate by
     2^-20 (x_r0 - x_r1), exact in float32; where that coordinate's BF16
     operand u_j - o_j rounds as before, the GEMM sees the same row, so f(u)
     equals the stored f(x) and the pair must be listed as a tie and decided
-    like the sign of the FP64 difference of the oracle."""
+    like the sign of the FP64 difference of the oracle.  D = 40, 100 and
+    200 take the four-kernel generation (tc_min_dim 33) whose batched tie
+    kernel groups 8, 4 and 2 ties per row of z; D = 600 its row-split tie
+    kernel; D = 256 both tie modes."""
     import torch
     import paper_2502_10470_gb300 as M
-    rng = np.random.default_rng(77)
-    n, NP, D = 6, 64, 256
+    rng = np.random.default_rng(77 + D)
+    n, NP = 6, 64
     probs = [synth.make_problem(rng, D, k) for k in range(n)]
     wl = synth.Workload(name="tc-ties", problems=probs, inst_np=np.full(n, NP, dtype=np.int32),
                         inst_prob=np.arange(n, dtype=np.int32), inst_group=np.arange(n, dtype=np.int32),
                         n_groups=n, n_out=0, inner_gens=1, outer_gens=1, seed=12, one_shot=0)
-    b = make_batch(wl, M.METADE_PATH_BATCHED, prec=1, tie_fp64=tie_fp64)
+    b = make_batch(wl, M.METADE_PATH_BATCHED, prec=1, tie_fp64=tie_fp64, tc_min_dim=33)
     assert json.loads(M.metade_plan_info(b.ctx))["tensor_core"]["executors"] == n
     grid = [(rng.integers(-12, 13, (NP, D)) * 8.0).astype(np.float32) for _ in range(n)]
     b.set_population(grid, [np.full(NP, np.inf, dtype=np.float32)] * n)
