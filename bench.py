@@ -573,6 +573,12 @@ def run_ours(args):
                  "path": "one cooperative launch per executor per generation, FP32, no graph, no tuning"}
         p.close()
 
+    # the literal tie rule on this workload: the same evolver generation's executors, the first
+    # TIE_GENS inner generations with FP64 tie re-evaluation against the default difference form
+    tie64 = None
+    if not args.no_moderate:
+        tie64 = measure_tie_rule(wl, probs, dev, stream, rank, plan.get("tc_min_dim") or 129, gens)
+
     moderate = None
     if not args.no_moderate:
         ms = min(args.steps, 20)
@@ -601,7 +607,7 @@ def run_ours(args):
                 "gpu_launches": launches,
                 "roofline": roof[0],
                 "roofline_by_kernel": roof[1],
-                "kernels": kernels, "near_ties_per_step": near_ties_per_step,
+                "kernels": kernels, "near_ties_per_step": near_ties_per_step, "tie_fp64": tie64,
                 "final_error": fe,
                 "plain_fp32": plain,
                 "speedup_vs_plain": (value / plain["value"]) if plain else None,
@@ -611,6 +617,47 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+TIE_GENS = 20  # inner generations the literal tie rule is timed over (its FP64 ties cost seconds per step)
+
+
+def measure_tie_rule(wl, probs, dev, stream, rank, tc_min_dim, gens):
+    """The same state (the evolver's first generation of executors, after
+    initialisation) run for TIE_GENS inner generations twice: near ties by
+    the FP32 difference form (the default) and by FP64 re-evaluation of both
+    vectors (tie_fp64 = 1, the literal rule; the tensor-core executors then
+    take the five-kernel pipeline with a CTA per tie).  CUDA-event time per
+    inner generation and the near ties decided, for each."""
+    import torch
+    import paper_2502_10470_gb300 as M
+    out = {"inner_gens": TIE_GENS, "of": gens, "tc_min_dim": tc_min_dim,
+           "state": "initialised executors of the evolver's first generation"}
+    for key, t64 in (("difference_form", 0), ("fp64", 1)):
+        b = M.Batch(probs, wl.inst_np, wl.inst_prob, wl.inst_group, seed=wl.seed + rank, one_shot=1,
+                    n_out=wl.n_out, prec=M.METADE_BF16, device=dev, stream=stream.cuda_stream,
+                    tc_min_dim=tc_min_dim, tie_fp64=t64)
+        M.metade_outer_init(b.ctx, b.opop, b.ofit)
+        M.metade_outer_step(b.ctx, b.opop, b.ofit, b.trial, b.theta, None, 0, 0)
+        M.metade_init(b.ctx, b.pop, b.fit, 0)
+        M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 0, 1, None, None)  # loads the kernels
+        M.metade_init(b.ctx, b.pop, b.fit, 0)
+        torch.cuda.synchronize()
+        M.metade_profile(b.ctx, True)
+        M.metade_profile_read(b.ctx)
+        M.metade_profile(b.ctx, False)  # the tie count runs regardless
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 0, TIE_GENS, None, None)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if M.metade_sync(b.ctx) != 0:
+            raise RuntimeError("device status (tie rule)")
+        ties = M.metade_profile_read(b.ctx)["near_ties"][1]
+        out[key] = {"ms_per_inner_gen": e0.elapsed_time(e1) / TIE_GENS, "near_ties_per_inner_gen": ties / TIE_GENS}
+        b.close()
+    out["fp64_over_difference"] = out["fp64"]["ms_per_inner_gen"] / out["difference_form"]["ms_per_inner_gen"]
+    return out
 
 
 def rooflines(wl, b, plan, prof, thetas, gens, steps, total_ms, clocks):

@@ -544,9 +544,9 @@ struct TieArgs {
 // chunk (fewer when ties are few), chunks handed out by an atomic counter
 // over every CTA of the GPU (two per SM): z = R (x - o) and dz = R (u - x)
 // in FP32, R staged through shared memory 16 columns at a time by cp.async
-// in a ring of kRing stages, a thread per (row of z, group of the chunk's
-// ties; the narrower the problem, the more groups) with float4 loads along
-// k, every fma chain in ascending k; then a warp per tie forms the FP32
+// in a ring of kRing stages, a thread per (two rows of z, group of the
+// chunk's ties; the narrower the problem, the more groups) with float4 loads
+// along k, every fma chain in ascending k; then a warp per tie forms the FP32
 // difference form f(u) - f(x), decides and commits.  A trial identical to
 // its target (u - x == 0 everywhere, pad included) is accepted as it is.
 __global__ void __launch_bounds__(kSelThreads, 2) k_tc_ties2(TieArgs g) {
@@ -651,55 +651,71 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_tc_ties2(TieArgs g) {
                                                                             u4.w - x4.w);
             }
         }
-        // thread (row r, group h) of G = 512 / vrow groups, vrow = the rows rounded up to a power of
-        // two (32 .. 256): ties h, h + G, h + 2 G, ... of the chunk, so narrow problems keep every
-        // thread busy (G <= 16 = kTieBatch: at most eight ties per thread, G = 2 at D > 128)
-        int lg = 5;
+        // thread (rows r and r + half, group h): half = vrow / 2 threads per group, vrow = the rows
+        // rounded up to a power of two (64 .. 256), G = 512 / half groups (4 .. 16); group h takes
+        // ties h, h + G, ... of the chunk (at most four), so narrow problems keep every thread busy
+        // and each shared-memory load of x - o or u - x feeds two rows
+        int lg = 6;
         while ((1 << lg) < d.dim) ++lg;
-        const int G = kSelThreads >> lg;
-        const int r = tid & ((1 << lg) - 1), h = tid >> lg;
-        float az[kTieBatch / 2], adz[kTieBatch / 2];
+        const int half = 1 << (lg - 1);
+        const int G = kSelThreads / half;
+        const int r = tid & (half - 1), h = tid / half;  // h is uniform over a warp (half >= 32)
+        const bool row1 = r + half < d.dim;
+        float az[kTieBatch / 4][2], adz[kTieBatch / 4][2];
 #pragma unroll
-        for (int q = 0; q < kTieBatch / 2; ++q) az[q] = adz[q] = 0.f;
-        const int mine = (nb - h + G - 1) / G;  // ties of this group (warp-uniform: vrow >= 32)
+        for (int q = 0; q < kTieBatch / 4; ++q) az[q][0] = az[q][1] = adz[q][0] = adz[q][1] = 0.f;
+        const int mine = (nb - h + G - 1) / G;  // ties of this group
         for (int ch = 0; ch < nchunk; ++ch) {
             stage(ch + kRing - 1);  // the stage read at ch - 1 is free: every thread passed the barrier after it
             asm volatile("cp.async.wait_group %0;" ::"n"(kRing - 1) : "memory");  // stage ch has landed
             __syncthreads();
-            if (r < d.dim) {
-                const float* rc = sR + (size_t)(ch % kRing) * kVec * kRcs + r * kRcs;
+            if (r < d.dim) {  // (rows r + half >= D compute from stale stage rows; they are not stored)
+                const float* rc0 = sR + (size_t)(ch % kRing) * kVec * kRcs + r * kRcs;
+                const float* rc1 = rc0 + half * kRcs;
                 const int c0 = ch * kRc;
                 const int cend = min(kRc, d.dim - c0);
                 if (cend == kRc) {  // four float4 steps, k ascending within each
 #pragma unroll
                     for (int c4 = 0; c4 < kRc / 4; ++c4) {
-                        const float4 rt = *reinterpret_cast<const float4*>(rc + 4 * c4);
+                        const float4 ra = *reinterpret_cast<const float4*>(rc0 + 4 * c4);
+                        const float4 rb = *reinterpret_cast<const float4*>(rc1 + 4 * c4);
 #pragma unroll
-                        for (int j = 0; j < kTieBatch / 2; ++j) {
+                        for (int j = 0; j < kTieBatch / 4; ++j) {
                             if (j < mine) {
                                 const int q = h + G * j;
                                 const float4 x4 = *reinterpret_cast<const float4*>(vx + q * kVec + c0 + 4 * c4);
                                 const float4 l4 = *reinterpret_cast<const float4*>(vl + q * kVec + c0 + 4 * c4);
-                                az[j] = fmaf(rt.x, x4.x, az[j]);
-                                az[j] = fmaf(rt.y, x4.y, az[j]);
-                                az[j] = fmaf(rt.z, x4.z, az[j]);
-                                az[j] = fmaf(rt.w, x4.w, az[j]);
-                                adz[j] = fmaf(rt.x, l4.x, adz[j]);
-                                adz[j] = fmaf(rt.y, l4.y, adz[j]);
-                                adz[j] = fmaf(rt.z, l4.z, adz[j]);
-                                adz[j] = fmaf(rt.w, l4.w, adz[j]);
+                                az[j][0] = fmaf(ra.x, x4.x, az[j][0]);
+                                az[j][1] = fmaf(rb.x, x4.x, az[j][1]);
+                                adz[j][0] = fmaf(ra.x, l4.x, adz[j][0]);
+                                adz[j][1] = fmaf(rb.x, l4.x, adz[j][1]);
+                                az[j][0] = fmaf(ra.y, x4.y, az[j][0]);
+                                az[j][1] = fmaf(rb.y, x4.y, az[j][1]);
+                                adz[j][0] = fmaf(ra.y, l4.y, adz[j][0]);
+                                adz[j][1] = fmaf(rb.y, l4.y, adz[j][1]);
+                                az[j][0] = fmaf(ra.z, x4.z, az[j][0]);
+                                az[j][1] = fmaf(rb.z, x4.z, az[j][1]);
+                                adz[j][0] = fmaf(ra.z, l4.z, adz[j][0]);
+                                adz[j][1] = fmaf(rb.z, l4.z, adz[j][1]);
+                                az[j][0] = fmaf(ra.w, x4.w, az[j][0]);
+                                az[j][1] = fmaf(rb.w, x4.w, az[j][1]);
+                                adz[j][0] = fmaf(ra.w, l4.w, adz[j][0]);
+                                adz[j][1] = fmaf(rb.w, l4.w, adz[j][1]);
                             }
                         }
                     }
                 } else {  // the last, partial chunk: one column at a time
                     for (int cc = 0; cc < cend; ++cc) {
-                        const float rt = rc[cc];
+                        const float ra = rc0[cc], rb = rc1[cc];
 #pragma unroll
-                        for (int j = 0; j < kTieBatch / 2; ++j) {
+                        for (int j = 0; j < kTieBatch / 4; ++j) {
                             if (j < mine) {
                                 const int q = h + G * j;
-                                az[j] = fmaf(rt, vx[q * kVec + c0 + cc], az[j]);
-                                adz[j] = fmaf(rt, vl[q * kVec + c0 + cc], adz[j]);
+                                const float xk = vx[q * kVec + c0 + cc], lk = vl[q * kVec + c0 + cc];
+                                az[j][0] = fmaf(ra, xk, az[j][0]);
+                                az[j][1] = fmaf(rb, xk, az[j][1]);
+                                adz[j][0] = fmaf(ra, lk, adz[j][0]);
+                                adz[j][1] = fmaf(rb, lk, adz[j][1]);
                             }
                         }
                     }
@@ -710,10 +726,15 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_tc_ties2(TieArgs g) {
         asm volatile("cp.async.wait_group 0;" ::: "memory");  // only empty groups remain
         if (r < d.dim) {  // every thread has read vx / vl: z and dz replace them
 #pragma unroll
-            for (int j = 0; j < kTieBatch / 2; ++j) {
+            for (int j = 0; j < kTieBatch / 4; ++j) {
                 if (j < mine) {
-                    vx[(h + G * j) * kVec + r] = az[j];
-                    vl[(h + G * j) * kVec + r] = adz[j];
+                    const int q = h + G * j;
+                    vx[q * kVec + r] = az[j][0];
+                    vl[q * kVec + r] = adz[j][0];
+                    if (row1) {
+                        vx[q * kVec + r + half] = az[j][1];
+                        vl[q * kVec + r + half] = adz[j][1];
+                    }
                 }
             }
         }
