@@ -620,6 +620,9 @@ def run_ours(args):
 
 
 TIE_GENS = 20  # inner generations the literal tie rule is timed over (its FP64 ties cost seconds per step)
+# (kernel, tensor-core width) -> DRAM bytes per launch on the full workload, from an ncu capture of the
+# current kernel (read 77.8 MB: the population once; write 87.2 MB: trial and operand rows)
+TRAFFIC_BYTES = {("k_tc_trial2", 33): 165.0e6}
 
 
 def measure_tie_rule(wl, probs, dev, stream, rank, tc_min_dim, gens):
@@ -749,7 +752,13 @@ def rooflines(wl, b, plan, prof, thetas, gens, steps, total_ms, clocks):
     dom = max(ranked, key=lambda kv: kv[1]["share"]) if ranked else (None, {})
     head = dict(dom[1])
     head["kernel"] = dom[0]
-    head["traffic"] = None
+    # DRAM bytes per launch from one ncu capture of the same kernel on the same rows (this workload at
+    # the width the autotuner picks for it), while the kernel is the one captured; otherwise unknown
+    known = TRAFFIC_BYTES.get((dom[0], int(tcmin))) if wl.name == WORKLOAD else None
+    head["traffic"] = known
+    if known is not None:
+        head["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch "
+                                  "(bench.py --profile-case tc-d200, generation 40)")
     return head, out
 
 

@@ -290,7 +290,9 @@ METADE_API metade_status metade_draw_record(metade_ctx *ctx, const float *fit, c
  * cudaDeviceReset on a device, do not call this entry point on it again.  All calls share the array and it keeps the last call's
  * contents (every element a call reads is written earlier in that call, so
  * nothing is cleared); calls that overlap on the GPU race on it.  An invalid
- * theta, or np too small for the strategy, leaves pop and fit unchanged.
+ * theta, or np too small for the strategy, leaves pop and fit unchanged; the
+ * call's first kernel records which in a device word that
+ * metade_plain_step_noalloc_status reads.
  * Asynchronous on `stream`; returns METADE_ECUDA if a launch fails (checked
  * with cudaPeekAtLastError, so an error left pending by earlier work is
  * reported too, and not cleared). */
@@ -299,6 +301,13 @@ METADE_API metade_status metade_plain_step_noalloc(float *pop, float *fit, const
                                                    int32_t dim, int32_t obj, float lo, float hi,
                                                    uint64_t seed, uint32_t stream_id, uint32_t epoch,
                                                    uint32_t gen, int32_t p_best_pct, void *stream);
+
+/* The outcome of the last metade_plain_step_noalloc on the current device, once
+ * it has run: *status = 0 for a real generation, 1 for one skipped because
+ * theta was invalid or np too small for its strategy.  Waits for the device
+ * (a synchronous copy from the library's device word).  The word is shared by
+ * every call, like the scratch array. */
+METADE_API metade_status metade_plain_step_noalloc_status(int32_t *status);
 
 /* Wait for the context's stream; return and clear the sticky device status. */
 METADE_API metade_status metade_sync(metade_ctx *ctx);

@@ -32,6 +32,7 @@ EXPORTED = [
     "metade_outer_generation", "metade_draw_record", "metade_sync", "metade_plan_info",
     "metade_launch_count", "metade_strerror", "metade_plain_step_noalloc", "metade_profile",
     "metade_profile_read", "metade_autotune", "metade_wait_check", "metade_last_cuda_error",
+    "metade_plain_step_noalloc_status",
 ]
 
 
@@ -100,6 +101,7 @@ def _lib():
         L.metade_plan_info.argtypes = [P, C.c_char_p, C.c_size_t]
         L.metade_launch_count.argtypes = [P]
         L.metade_launch_count.restype = C.c_int64
+        L.metade_plain_step_noalloc_status.argtypes = [P]
         L.metade_plain_step_noalloc.argtypes = [P, P, P, P, P, I32, I32, I32, C.c_float, C.c_float, C.c_uint64,
                                                 U32, U32, U32, I32, P]
         L.metade_profile.argtypes = [P, I32]
@@ -254,6 +256,13 @@ def metade_plain_step_noalloc(pop, fit, theta, shift, rot, np_: int, dim: int, o
     """One plain generation of one executor with no allocation; returns the status."""
     return _lib().metade_plain_step_noalloc(_ptr(pop), _ptr(fit), _ptr(theta), _ptr(shift), _ptr(rot), np_, dim,
                                             obj, lo, hi, seed, stream_id, epoch, gen, p_best_pct, stream)
+
+
+def metade_plain_step_noalloc_status() -> int:
+    """0 if the last allocation-free generation on this device ran, 1 if its theta skipped it (waits)."""
+    v = C.c_int32(0)
+    _check(_lib().metade_plain_step_noalloc_status(C.byref(v)), "metade_plain_step_noalloc_status")
+    return int(v.value)
 
 
 def metade_autotune(ctx: int, pop, fit, theta, n_gens: int = 3) -> None:

@@ -38,6 +38,7 @@ constexpr long long kScratchFloats = 1LL << 20;  // 4 MiB per device
 constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) float g_noalloc_scratch[kScratchFloats];
+__device__ int g_noalloc_status;  // the last call: 0 generation run, 1 skipped (invalid theta)
 
 std::mutex g_mu;
 float* g_scratch_dev[kMaxDevices] = {nullptr};
@@ -101,6 +102,7 @@ struct NaArgs {
 
 __global__ void k_na_prologue(NaArgs a) {
     const Strat s = load_strat(a.theta, a.d.np);
+    if (threadIdx.x == 0) g_noalloc_status = s.ok ? 0 : 1;
     if (!s.ok) return;
     block_topk_staged(a.fit, a.d.np, a.d.kp, a.topk);
 }
@@ -221,4 +223,12 @@ extern "C" METADE_API metade_status metade_plain_step_noalloc(float* pop, float*
     if (cudaPeekAtLastError() != cudaSuccess) return METADE_ECUDA;
     k_na_select<<<blocks, 256, smem, st>>>(a);
     return cudaPeekAtLastError() == cudaSuccess ? METADE_OK : METADE_ECUDA;
+}
+
+extern "C" METADE_API metade_status metade_plain_step_noalloc_status(int32_t* status) {
+    if (!status) return METADE_EINVAL;
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_noalloc_status, sizeof(int)) != cudaSuccess) return METADE_ECUDA;
+    *status = v;
+    return METADE_OK;
 }

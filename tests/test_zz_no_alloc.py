@@ -51,6 +51,7 @@ def test_noalloc_matches_inner_step_on_two_calls(np_, dim, obj):
         assert np.all(np.abs(got_fit - want_fit) <= FIT_RTOL * np.maximum(np.abs(want_fit), 1.0))
         check_fitness_fp32(got_fit, got_pop, p)
         assert not np.array_equal(got_pop, pop0)  # the generation did something
+        assert M.metade_plain_step_noalloc_status() == 0
         # and against the FP64 oracle's generation from the same state: the
         # selection wherever the fitness gap is clear, the accepted trials
         out = oracle.pde_step(start_pop, start_fit, theta, obj, p.shift, p.rot, seed=5, stream=0, epoch=0, gen=gen)
@@ -76,3 +77,30 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     big = torch.zeros(16 * 8 + 1, device="cuda")
     st = M.metade_plain_step_noalloc(big[1:], t, t, t, t, 16, 8, 0, -100.0, 100.0, 0, 0, 0, 0, 10, None)
     assert st == M.METADE_EINVAL
+
+
+def test_noalloc_reports_a_skipped_generation():
+    """An invalid theta (np too small for dn = 4 difference pairs) leaves pop
+    and fit unchanged, and the status word says the generation was skipped;
+    a valid one afterwards says it ran."""
+    import torch
+    import paper_2502_10470_gb300 as M
+    rng = np.random.default_rng(3)
+    p = synth.make_problem(rng, 8, 0)
+    np_, dpad = 6, 8
+    pop = torch.tensor(synth.random_population(rng, np_, 8), device="cuda").reshape(-1).contiguous()
+    import oracle
+    fit = torch.tensor(oracle.eval_pop(0, pop.view(np_, dpad).cpu().numpy(), p.shift, p.rot).astype(np.float32),
+                       device="cuda")
+    shift = torch.tensor(p.shift, device="cuda")
+    rot = torch.tensor(p.rot.reshape(-1), device="cuda")
+    before = pop.clone()
+    bad = torch.tensor([0.5, 0.5, 1, 1, 4, 1], dtype=torch.float32, device="cuda")  # 9 distinct draws, NP 6
+    assert M.metade_plain_step_noalloc(pop, fit, bad, shift, rot, np_, 8, 0, -100.0, 100.0, 1, 0, 0, 0, 10,
+                                       None) == M.METADE_OK
+    assert M.metade_plain_step_noalloc_status() == 1
+    assert torch.equal(pop, before)
+    good = torch.tensor([0.5, 0.9, 1, 1, 1, 1], dtype=torch.float32, device="cuda")
+    assert M.metade_plain_step_noalloc(pop, fit, good, shift, rot, np_, 8, 0, -100.0, 100.0, 1, 0, 0, 1, 10,
+                                       None) == M.METADE_OK
+    assert M.metade_plain_step_noalloc_status() == 0
