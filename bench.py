@@ -79,7 +79,9 @@ def parse_args(argv=None):
     ap.add_argument("--tc-min-dim", type=int, default=0,
                     help="width of the per-generation GEMM pipeline for the headline and batching studies "
                          "(0: metade_autotune picks it)")
-    ap.add_argument("--tune-gens", type=int, default=5, help="generations metade_autotune times per candidate")
+    ap.add_argument("--tune-gens", type=int, default=0,
+                    help="generations metade_autotune times per candidate (0: the generations of one step, so the "
+                         "choice sees the late, near-tie-heavy generations too)")
     ap.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES),
                     help="run one small untimed case for an ncu capture and exit")
     return ap.parse_args(argv)
@@ -511,7 +513,7 @@ def run_ours(args):
     # autotune (tensor-core width, block shapes) on a real state: the first evolver generation's executors
     M.metade_outer_step(b.ctx, b.opop, b.ofit, b.trial, b.theta, None, 0, 0)
     M.metade_init(b.ctx, b.pop, b.fit, 0)
-    M.metade_autotune(b.ctx, b.pop, b.fit, b.theta, args.tune_gens)
+    M.metade_autotune(b.ctx, b.pop, b.fit, b.theta, args.tune_gens or gens)
     og = 0
     for _ in range(args.warmup):
         step(b, og)
@@ -1018,7 +1020,7 @@ def run_batching(args):
         b.set_theta(wl.theta)
         M.metade_init(b.ctx, b.pop, b.fit, 0)
         if path == M.METADE_PATH_BATCHED:
-            M.metade_autotune(b.ctx, b.pop, b.fit, b.theta, args.tune_gens)
+            M.metade_autotune(b.ctx, b.pop, b.fit, b.theta, args.tune_gens or gens)
         for w in range(1 if name == "plain" else args.warmup):
             M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, w * gens, gens, b.best_f, b.best_i)
         torch.cuda.synchronize()

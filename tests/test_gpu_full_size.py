@@ -194,8 +194,9 @@ def test_full_workload_200_generations_properties():
 
 
 def test_batching_full_size_generation_sampled():
-    """512 ragged executors (NP 20..400, D 10..100: the small-D and tile
-    kernels), tuned plan, one generation: executors of every size class and
+    """512 ragged executors (NP 20..400, D 10..100: the small-D kernel and,
+    by the autotuned FP32 width, the tile kernels or the CUDA-core GEMM
+    pipeline), tuned plan, one generation: executors of every size class and
     objective against the oracle's generation."""
     import paper_2502_10470_gb300 as M
     from gpu_util import feasible_theta
