@@ -1230,39 +1230,49 @@ def run_mlp(args):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     probs = [(p.dim, p.obj, p.shift, p.rot) for p in wl.problems]
-    b = M.Batch(probs, wl.inst_np, wl.inst_prob, wl.inst_group, seed=wl.seed, one_shot=0, lo=wl.lo, hi=wl.hi,
-                device=dev, stream=stream.cuda_stream)
-    b.set_theta(wl.theta)
-    M.metade_init(b.ctx, b.pop, b.fit, 0)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    g0 = 0
-    for _ in range(args.warmup):
-        M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, g0, gens, b.best_f, b.best_i)
-        g0 += gens
-    torch.cuda.synchronize()
-    sampler = ClockSampler(0)
-    sampler.start()
-    M.metade_profile(b.ctx, True)
-    M.metade_profile_read(b.ctx)
-    evs = []
-    for _ in range(args.steps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, g0, gens, b.best_f, b.best_i)
-        e1.record(stream)
-        evs.append((e0, e1))
-        g0 += gens
-    torch.cuda.synchronize()
-    clocks = sampler.stop()
-    prof = M.metade_profile_read(b.ctx)
-    if M.metade_sync(b.ctx) != M.METADE_OK:
-        raise RuntimeError("device status")
-    ms = float(np.mean([a.elapsed_time(c) for a, c in evs]))
+
+    def timed(prec):
+        """(CUDA-event ms per step, ms of the MLP generations, median best, plan, clocks) of one precision."""
+        b = M.Batch(probs, wl.inst_np, wl.inst_prob, wl.inst_group, seed=wl.seed, one_shot=0, lo=wl.lo, hi=wl.hi,
+                    device=dev, stream=stream.cuda_stream, prec=prec)
+        b.set_theta(wl.theta)
+        M.metade_init(b.ctx, b.pop, b.fit, 0)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        g0 = 0
+        for _ in range(args.warmup):
+            M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, g0, gens, b.best_f, b.best_i)
+            g0 += gens
+        torch.cuda.synchronize()
+        sampler = ClockSampler(0)
+        sampler.start()
+        M.metade_profile(b.ctx, True)
+        M.metade_profile_read(b.ctx)
+        evs = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, g0, gens, b.best_f, b.best_i)
+            e1.record(stream)
+            evs.append((e0, e1))
+            g0 += gens
+        torch.cuda.synchronize()
+        clk = sampler.stop()
+        prof = M.metade_profile_read(b.ctx)
+        if M.metade_sync(b.ctx) != M.METADE_OK:
+            raise RuntimeError("device status")
+        ms_ = float(np.mean([a.elapsed_time(c) for a, c in evs]))
+        kms_ = prof["mlp_generations"][0] / max(1, prof["mlp_generations"][1])
+        best_ = float(np.median(b.best_f.cpu().numpy()))
+        plan_ = json.loads(M.metade_plan_info(b.ctx)).get("mlp")
+        b.close()
+        return ms_, kms_, best_, plan_, clk
+
+    ms, kms, best_med, _, clocks = timed(M.METADE_FP32)
+    ms16, kms16, best16, plan16, _ = timed(M.METADE_BF16)
     units = float(wl.inst_np.sum()) * gens
     h = (wl.problems[0].dim - 2) // 19
     flops = units * 256 * 36 * h
-    kms = prof["mlp_generations"][0] / max(1, prof["mlp_generations"][1])
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -1270,7 +1280,7 @@ def run_mlp(args):
         pass
     sm_max = float((clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0))
     peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
-    best = b.best_f.cpu().numpy()
+    bf16_peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
     line = {"metric": "MLP workload: individual-gens/s (MLP-objective path)", "workload": wl.name,
             "value": units / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
             "generations_per_step": gens, "dtype": "f32", "data": "synthetic",
@@ -1281,10 +1291,19 @@ def run_mlp(args):
             "cpu_baseline": {"value": cpu_units / cpu_dt, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "%d executors x NP 100 x 1 generation of the MLP workload, FP64 C oracle, "
                                        "%d spawn processes, %.1f s wall" % (len(tasks), cores, cpu_dt)},
-            "best_f_median": float(np.median(best)), "clocks": clocks,
+            "best_f_median": best_med, "clocks": clocks,
+            "bf16_tensor_cores": {
+                "kernel": plan16["kernels"][2] if plan16 else None, "ms_per_step": ms16,
+                "value": units / (ms16 / 1e3), "speedup_vs_fp32": ms / ms16, "best_f_median": best16,
+                "forward_tflops": flops / (kms16 / 1e3) / 1e12,
+                "layer1_tensor": {"bound": "tensor", "achieved": units * 256 * 32 * h / (kms16 / 1e3) / 1e12,
+                                  "peak": bf16_peak, "unit": "TFLOP/s",
+                                  "frac": units * 256 * 32 * h / (kms16 / 1e3) / 1e12 / bf16_peak,
+                                  "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained, of measured"},
+                "note": "the first layer (2 x 256 x 16 x h flops per evaluation) on tcgen05 in BF16; tanh, the "
+                        "second layer and the error on the CUDA cores in FP32, which bound the kernel"},
             "l2": "flushed before every timed step"}
     print(json.dumps(line), flush=True)
-    b.close()
 
 
 def _case_tile_d100():

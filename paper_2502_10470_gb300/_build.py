@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libmetade.so")
 OBJDIR = os.path.join(HERE, "_build")
-SOURCES = ["kernels.cu", "k_tile.cu", "k_mlp.cu", "k_gemm32.cu", "tc_rotate.cu", "tc_fused.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["kernels.cu", "k_tile.cu", "k_mlp.cu", "k_mlp_tc.cu", "k_gemm32.cu", "tc_rotate.cu", "tc_fused.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]

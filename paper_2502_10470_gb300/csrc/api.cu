@@ -684,7 +684,7 @@ metade_status run_init(metade_ctx* c, cudaStream_t st, float* pop, float* fit, u
                    c->tc || c->mlpp.n_rows > 0, c->mlp_x, c->mlp_y));
     *launches += 2;
     if (c->mlpp.n_rows > 0) {
-        CK(launch_mlp_eval(c->desc, c->mlpp, pop, fit, st));
+        CK(launch_mlp_eval(c->desc, c->mlpp, pop, fit, c->status, st));
         *launches += 1;
     }
     if (c->tc) {
@@ -979,6 +979,9 @@ metade_status metade_create(const metade_config* cfg, metade_ctx** out) {
             m.y = c->mlp_y;
             m.max_dpad = 0;
             for (int k : mlp_execs) m.max_dpad = std::max(m.max_dpad, c->hdesc[k].dpad);
+            // BF16 / bf16x3 contexts evaluate the first layer on the tensor cores; FP32 and FP8 on the CUDA cores
+            m.tc = c->prec == METADE_BF16 ? 1 : c->prec == METADE_BF16X3 ? 2 : 0;
+            m.sms = std::max(1, device_sms());
             if ((size_t)8 * m.max_dpad * sizeof(float) > kSmemLimit) return fail(METADE_EUNSUPPORTED);
         }
     }
@@ -1312,11 +1315,12 @@ metade_status metade_plan_info(const metade_ctx* c, char* buf, size_t len) {
         s += tmp;
     }
     if (c->mlpp.n_rows > 0) {
-        char tmp[160];
+        char tmp[256];
         snprintf(tmp, sizeof(tmp),
-                 ", \"mlp\": {\"kernels\": [\"k_mlp_prologue\", \"k_mlp_trial\", \"k_mlp_eval\", \"k_mlp_select\"], "
-                 "\"executors\": %d, \"rows\": %d}",
-                 c->mlpp.n_exec, c->mlpp.n_rows);
+                 ", \"mlp\": {\"kernels\": [\"k_mlp_prologue\", \"k_mlp_trial\", \"%s\", \"k_mlp_select\"], "
+                 "\"precision\": \"%s\", \"executors\": %d, \"rows\": %d}",
+                 c->mlpp.tc ? "k_mlp_tc" : "k_mlp_eval",
+                 c->mlpp.tc == 1 ? "bf16" : c->mlpp.tc == 2 ? "bf16x3" : "fp32", c->mlpp.n_exec, c->mlpp.n_rows);
         s += tmp;
     }
     s += "}";

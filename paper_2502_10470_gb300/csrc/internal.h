@@ -92,14 +92,21 @@ struct MlpPlan {
     const float* x;        // inputs [256][16]
     const float* y;        // targets of every MLP problem ([256][2] at InstDesc.aux)
     int max_dpad;
+    int tc;                // evaluation: 0 FP32 CUDA cores (k_mlp_eval), 1 BF16 / 2 bf16x3 tensor cores (k_mlp_tc)
+    int sms;               // CTAs of k_mlp_tc (one per SM)
 };
 // The GEMM pipeline's bounded mbarrier wait on its own (rounds 0: the
 // pipeline's limit); out[0] completed, out[1] SM cycles; timeout latched in *status.
 cudaError_t launch_wait_check(uint32_t rounds, int arrive, long long* out, int* status, cudaStream_t st);
 
 cudaError_t launch_mlp_generation(const StepArgs& a, const MlpPlan& p, cudaStream_t st);
-// f of the rows `rows` (population layout) of every MLP executor into f_out (fitness layout)
-cudaError_t launch_mlp_eval(const InstDesc* desc, const MlpPlan& p, const float* rows, float* f_out, cudaStream_t st);
+// f of the rows `rows` (population layout) of every MLP executor into f_out (fitness layout), in
+// the plan's precision (a timeout of the tensor-core kernel is latched in *status)
+cudaError_t launch_mlp_eval(const InstDesc* desc, const MlpPlan& p, const float* rows, float* f_out, int* status,
+                            cudaStream_t st);
+// the tensor-core evaluation alone (k_mlp_tc.cu)
+cudaError_t launch_mlp_eval_tc(const InstDesc* desc, const MlpPlan& p, const float* rows, float* f_out, int* status,
+                               cudaStream_t st);
 cudaError_t launch_mlp_inputs(float* X, cudaStream_t st);
 cudaError_t launch_mlp_targets(const float* X, const float* teacher, int h, float* Y, cudaStream_t st);
 cudaError_t launch_fused_tile(const StepArgs& a, const int* work, int n_work, const FusedPlan& p, float* u_scratch,

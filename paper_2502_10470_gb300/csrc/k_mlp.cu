@@ -134,15 +134,22 @@ cudaError_t launch_mlp_generation(const StepArgs& a, const MlpPlan& p, cudaStrea
     if (e != cudaSuccess) return e;
     k_mlp_trial<<<blocks, 256, smem_t, st>>>(a, p.row_exec, p.n_rows, p.topk_all, p.uscr, p.max_dpad);
     const size_t smem_e = (size_t)p.max_dpad * sizeof(float);
-    e = cudaFuncSetAttribute(k_mlp_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_e);
-    if (e != cudaSuccess) return e;
-    k_mlp_eval<<<p.n_rows, kMlpN / 2, smem_e, st>>>(a.desc, p.row_exec, p.uscr, p.x, p.y, p.fu);
+    if (p.tc) {
+        e = launch_mlp_eval_tc(a.desc, p, p.uscr, p.fu, a.status, st);
+        if (e != cudaSuccess) return e;
+    } else {
+        e = cudaFuncSetAttribute(k_mlp_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_e);
+        if (e != cudaSuccess) return e;
+        k_mlp_eval<<<p.n_rows, kMlpN / 2, smem_e, st>>>(a.desc, p.row_exec, p.uscr, p.x, p.y, p.fu);
+    }
     k_mlp_select<<<blocks, 256, 0, st>>>(a, p.row_exec, p.n_rows, p.uscr, p.fu);
     return cudaGetLastError();
 }
 
-cudaError_t launch_mlp_eval(const InstDesc* desc, const MlpPlan& p, const float* rows, float* f_out, cudaStream_t st) {
+cudaError_t launch_mlp_eval(const InstDesc* desc, const MlpPlan& p, const float* rows, float* f_out, int* status,
+                            cudaStream_t st) {
     if (p.n_rows <= 0) return cudaSuccess;
+    if (p.tc) return launch_mlp_eval_tc(desc, p, rows, f_out, status, st);
     const size_t smem_e = (size_t)p.max_dpad * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k_mlp_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_e);
     if (e != cudaSuccess) return e;
