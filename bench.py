@@ -1360,6 +1360,24 @@ def _case_mlp_d1522():
     b.close()
 
 
+def _case_mlp_tc_d1522():
+    """The MLP workload in a BF16 context: initialisation and two
+    generations, so three k_mlp_tc launches (the initial evaluation and one
+    per generation)."""
+    import paper_2502_10470_gb300 as M
+    import synth
+    wl = synth.mlp()
+    probs = [(p.dim, p.obj, p.shift, p.rot) for p in wl.problems]
+    b = M.Batch(probs, wl.inst_np, wl.inst_prob, wl.inst_group, seed=wl.seed, one_shot=0, lo=wl.lo, hi=wl.hi,
+                prec=M.METADE_BF16)
+    b.set_theta(wl.theta)
+    M.metade_init(b.ctx, b.pop, b.fit, 0)
+    M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 0, 2, None, None)
+    if M.metade_sync(b.ctx) != M.METADE_OK:
+        raise SystemExit("device status not OK")
+    b.close()
+
+
 def _case_simt_d1000():
     """The precision study's 64 x 512 x D1000 state in FP32: initialisation
     and one generation, two k_rot_simt launches."""
@@ -1490,7 +1508,8 @@ def run_oracle_timing(args):
 
 
 PROFILE_CASES = {"tile-d100": _case_tile_d100, "tc-d1000": _case_tc_d1000, "mlp-d1522": _case_mlp_d1522,
-                 "simt-d1000": _case_simt_d1000, "tc-d200": _case_tc_d200}
+                 "simt-d1000": _case_simt_d1000, "tc-d200": _case_tc_d200,
+                 "mlp-tc-d1522": _case_mlp_tc_d1522}
 
 
 def main(argv=None):
