@@ -78,7 +78,11 @@ typedef enum {
  * (tcgen05) with FP32 accumulation: BF16 operands; split BF16 (hi*hi + hi*lo +
  * lo*hi, about FP32 accuracy); or e4m3 operands with a per-row scale of u - o
  * and a per-problem scale of R (each maps the largest magnitude to 448),
- * undone in the GEMM epilogue.  FP64 is only for metade_eval. */
+ * undone in the GEMM epilogue.  Executors of the MLP objective (6) never join
+ * the rotation GEMM: with BF16 or BF16X3 their network's first layer runs on
+ * the tensor cores in that precision (the rest in FP32; BF16 with the
+ * hardware tanh approximation), with FP32 or FP8E4M3 all of it in FP32 on
+ * the CUDA cores.  FP64 is only for metade_eval. */
 typedef enum {
     METADE_FP32 = 0,
     METADE_BF16 = 1,
