@@ -169,9 +169,10 @@ cudaError_t launch_tc_eval(const InstDesc* desc, const TcPlan& p, const float* p
                            const float* rotT, float* fit, int* status, cudaStream_t st);
 // FP32 rotation GEMM + objective on the CUDA cores (k_gemm32.cu): f of the
 // rows `rows` (population layout) of every 64-row tile into f_out
-size_t rot_simt_smem();
+// (columns of Z per chunk: the narrowest of 64, 128, 256 that covers max_dpad)
+size_t rot_simt_smem(int max_dpad);
 cudaError_t launch_rot_simt(const InstDesc* desc, const int* tiles, int n_tiles, const float* rows, const float* shift,
-                            const float* rotT, float* f_out, cudaStream_t st);
+                            const float* rotT, float* f_out, int max_dpad, cudaStream_t st);
 // The four-kernel generation (tc_fused.cu): whether the shared memory of
 // k_tc_sel holds operands of kp BF16 elements, and one generation of every
 // tensor-core executor -- k_tc_rank (pbest pools), k_tc_trial2 (trial and

@@ -1,15 +1,17 @@
 // k_gemm32.cu -- k_rot_simt: the rotation GEMM and objective on the CUDA
-// cores in FP32, for executors too wide for the tile kernels (D_pad > 256)
-// when the context computes in FP32.  It takes the place of k_rot_tc in the
-// tensor-core pipeline (prologue, trial, GEMM + objective, selection, ties).
+// cores in FP32, for the executors an FP32 context puts on the per-generation
+// pipeline (every one with D_pad > 256, and those at or above the FP32
+// width).  It takes the place of k_rot_tc in the tensor-core pipeline
+// (prologue, trial, GEMM + objective, selection, ties).
 //
 // One CTA (256 threads) per 64-row tile of an executor.  The CTA walks the
-// columns of Z in chunks of 256; for each chunk it streams K in chunks of 16
-// through two shared-memory buffers: while the current chunk is multiplied,
-// R^T [16][256] of the next one arrives by cp.async and its (u - o)^T
-// [16][64] values (formed from the trial rows) wait in registers.  Every
-// thread accumulates four 4x4 blocks of Z (rows 4 tx.., columns
-// 4 (ty0 + 16 j)..) in registers.  k ascends in every fma
+// columns of Z in chunks of SN = 256 (64 or 128 when no executor on the path
+// is wider); for each chunk it streams K in chunks of 16 through two
+// shared-memory buffers: while the current chunk is multiplied, R^T [16][SN]
+// of the next one arrives by cp.async and its (u - o)^T [16][64] values
+// (formed from the trial rows) wait in registers.  Every thread accumulates
+// SN / 64 4x4 blocks of Z (rows 4 tx.., columns 4 (ty0 + 16 j)..) in
+// registers.  k ascends in every fma
 // chain, so z is bit-identical to the other FP32 rotations.  The chunk of Z
 // then goes to shared memory and four lanes per row push it, in column order,
 // into the objective's running state (group_obj_push), which carries across
@@ -22,10 +24,8 @@ namespace metade {
 
 namespace {
 constexpr int kSM = 64;         // rows per tile
-constexpr int kSN = 256;        // columns of Z per chunk
 constexpr int kSK = 16;         // K per stage
 constexpr int kSAP = kSM + 4;   // row length of the (u - o)^T stage
-constexpr int kSZP = kSN + 4;   // row length of the Z chunk
 
 // 16-byte cp.async; src_bytes 0 fills the destination with zeros
 __device__ __forceinline__ void cpa16(float* dst, const float* src, int src_bytes) {
@@ -42,9 +42,13 @@ __device__ __forceinline__ void push_chunk(GroupObj& g, const float* zr, int col
 }
 }  // namespace
 
+// SN columns of Z per chunk (64, 128 or 256: the narrowest that covers the widest executor, so
+// narrow executors do not compute columns past D); the chunk's row length in shared memory is SN + 4.
+template <int SN>
 __global__ void __launch_bounds__(256, 2) k_rot_simt(const InstDesc* __restrict__ desc, const int* __restrict__ tiles,
                                                      const float* __restrict__ rows, const float* __restrict__ shift,
                                                      const float* __restrict__ rotT, float* f_out) {
+    constexpr int kSN = SN, kSZP = SN + 4, kJ = SN / 64;  // 4x4 column blocks per thread
     extern __shared__ __align__(16) float sm[];
     float* As = sm;                        // 2 x [kSK][kSAP]
     float* Bs = As + 2 * kSK * kSAP;       // 2 x [kSK][kSN]
@@ -76,7 +80,7 @@ __global__ void __launch_bounds__(256, 2) k_rot_simt(const InstDesc* __restrict_
     };
     auto issue_b = [&](float* dst, int k0, int col0) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < kJ; ++q) {
             const int e = tid + 256 * q, kk = e / (kSN / 4), c4 = e - kk * (kSN / 4), col = col0 + 4 * c4;
             const bool in = k0 + kk < dim && col < dp;
             cpa16(dst + kk * kSN + 4 * c4, in ? RT + (long long)(k0 + kk) * dp + col : RT, in ? 16 : 0);
@@ -85,9 +89,9 @@ __global__ void __launch_bounds__(256, 2) k_rot_simt(const InstDesc* __restrict_
     };
     GroupObj g;
     for (int col0 = 0; col0 < dim; col0 += kSN) {
-        float acc[4][4][4];
+        float acc[kJ][4][4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+        for (int j = 0; j < kJ; ++j)
 #pragma unroll
             for (int p = 0; p < 4; ++p)
 #pragma unroll
@@ -114,7 +118,7 @@ __global__ void __launch_bounds__(256, 2) k_rot_simt(const InstDesc* __restrict_
                 const float4 av = *reinterpret_cast<const float4*>(Ac + kk * kSAP + 4 * tx);
                 const float ar[4] = {av.x, av.y, av.z, av.w};
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
+                for (int j = 0; j < kJ; ++j) {
                     const float4 rv = *reinterpret_cast<const float4*>(Bc + kk * kSN + 4 * (ty0 + 16 * j));
                     const float rr[4] = {rv.x, rv.y, rv.z, rv.w};
 #pragma unroll
@@ -130,7 +134,7 @@ __global__ void __launch_bounds__(256, 2) k_rot_simt(const InstDesc* __restrict_
             __syncthreads();  // the next chunk is in place; this one is free for the chunk after
         }
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+        for (int j = 0; j < kJ; ++j)
 #pragma unroll
             for (int p = 0; p < 4; ++p)
                 *reinterpret_cast<float4*>(Zs + (4 * tx + p) * kSZP + 4 * (ty0 + 16 * j)) =
@@ -152,16 +156,32 @@ __global__ void __launch_bounds__(256, 2) k_rot_simt(const InstDesc* __restrict_
     if (os == 0 && orow < nv) f_out[d.fit_off + m0 + orow] = nan_to_inf(f);
 }
 
-size_t rot_simt_smem() { return (size_t)(2 * kSK * kSAP + 2 * kSK * kSN + kSM * kSZP) * sizeof(float); }
+int simt_sn(int max_dpad) { return max_dpad <= 64 ? 64 : max_dpad <= 128 ? 128 : 256; }
+
+size_t rot_simt_smem(int max_dpad) {
+    const int sn = simt_sn(max_dpad);
+    return (size_t)(2 * kSK * kSAP + 2 * kSK * sn + kSM * (sn + 4)) * sizeof(float);
+}
+
+template <int SN>
+static cudaError_t launch_rot_simt_sn(const InstDesc* desc, const int* tiles, int n_tiles, const float* rows,
+                                      const float* shift, const float* rotT, float* f_out, size_t smem,
+                                      cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(k_rot_simt<SN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_rot_simt<SN><<<n_tiles, 256, smem, st>>>(desc, tiles, rows, shift, rotT, f_out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_rot_simt(const InstDesc* desc, const int* tiles, int n_tiles, const float* rows, const float* shift,
-                            const float* rotT, float* f_out, cudaStream_t st) {
+                            const float* rotT, float* f_out, int max_dpad, cudaStream_t st) {
     if (n_tiles <= 0) return cudaSuccess;
-    const size_t smem = rot_simt_smem();
-    cudaError_t e = cudaFuncSetAttribute(k_rot_simt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_rot_simt<<<n_tiles, 256, smem, st>>>(desc, tiles, rows, shift, rotT, f_out);
-    return cudaGetLastError();
+    const size_t smem = rot_simt_smem(max_dpad);
+    switch (simt_sn(max_dpad)) {
+    case 64: return launch_rot_simt_sn<64>(desc, tiles, n_tiles, rows, shift, rotT, f_out, smem, st);
+    case 128: return launch_rot_simt_sn<128>(desc, tiles, n_tiles, rows, shift, rotT, f_out, smem, st);
+    default: return launch_rot_simt_sn<256>(desc, tiles, n_tiles, rows, shift, rotT, f_out, smem, st);
+    }
 }
 
 }  // namespace metade

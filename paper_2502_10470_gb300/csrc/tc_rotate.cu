@@ -720,7 +720,7 @@ cudaError_t launch_tc_pack_rot(const float* rot, long long rot_off, int dim, int
 cudaError_t launch_tc_eval(const InstDesc* desc, const TcPlan& p, const float* pop, const float* shift,
                            const float* rotT, float* fit, int* status, cudaStream_t st) {
     if (p.n_rows <= 0) return cudaSuccess;
-    if (p.simt) return launch_rot_simt(desc, p.tiles, p.n_tiles, pop, shift, rotT, fit, st);
+    if (p.simt) return launch_rot_simt(desc, p.tiles, p.n_tiles, pop, shift, rotT, fit, p.max_dpad, st);
     const size_t smem_p = (size_t)8 * p.max_dpad * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k_tc_pack_pop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p);
     if (e != cudaSuccess) return e;
@@ -812,7 +812,7 @@ cudaError_t launch_tc_generation(const StepArgs& a, const TcPlan& p, cudaStream_
     }
     if (p.simt) {
         if (ev) cudaEventRecord(ev[2], st);
-        e = launch_rot_simt(a.desc, p.tiles, p.n_tiles, p.uscr, a.shift, a.rotT, p.fu, st);
+        e = launch_rot_simt(a.desc, p.tiles, p.n_tiles, p.uscr, a.shift, a.rotT, p.fu, p.max_dpad, st);
         if (e != cudaSuccess) return e;
     } else {
         const size_t smem_g = tc_gemm_smem(p.split);
