@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(kSelThreads + 32, 1) k_tc_sel(const __grid_con
     __shared__ __align__(8) uint64_t afull, bfull, acc_full[2], acc_empty[2], drain, tile_ready[2];
     __shared__ uint32_t tmem_base;
     __shared__ int ep_abort_s, nacc_s, tile_of[2];  // tile in accumulator b (-1: no more tiles)
-    __shared__ int acc_row[kRows];
+    __shared__ long long acc_off[kRows];  // population offsets of the tile's accepted rows
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
     uint8_t* As = sm;
     float* part = reinterpret_cast<float*>(sm + kASize);
@@ -429,6 +429,20 @@ __global__ void __launch_bounds__(kSelThreads + 32, 1) k_tc_sel(const __grid_con
             if (t < 0) break;  // the same for every epilogue warp
             const int arow = g.tiles[2 * t], nr = g.tiles[2 * t + 1];
             const InstDesc d = a.desc[g.row_exec[arow]];  // dim, objective and problem of every row of the tile
+            // the row's executor fields and stored fitness, fetched before the TMEM work so that these
+            // dependent loads overlap it (part-0 threads, which select)
+            bool rok = false;
+            int fidx = 0;
+            long long roff = 0;
+            float fx = 0.f;
+            if (prt == 0 && row < nr) {
+                const int k = g.row_exec[arow + row];
+                const InstDesc e = a.desc[k];
+                rok = load_strat(a.theta + 6 * k, e.np).ok;  // rows of an invalid theta stay as they are
+                fidx = e.fit_off + (arow + row - e.tc_row);
+                roff = e.pop_off + (long long)(arow + row - e.tc_row) * d.dpad;
+                if (rok) fx = a.fit[fidx];
+            }
             ObjR acc;
             const bool got = __all_sync(kFull, mbar_wait(&acc_full[b], (uint32_t)(j >> 1) & 1u) ? 1 : 0) != 0;
             tc_fence_after();
@@ -490,18 +504,14 @@ __global__ void __launch_bounds__(kSelThreads + 32, 1) k_tc_sel(const __grid_con
                     obj_compose(d.obj, acc, rb, x1.x, x1.y, __float_as_int(x1.z));
                 }
                 const float fn = nan_to_inf(acc.finish(d.obj, d.dim));
-                const int k = g.row_exec[arow + row];
-                const InstDesc e = a.desc[k];
-                if (load_strat(a.theta + 6 * k, e.np).ok) {  // rows of an invalid theta stay as they are
-                    const int fidx = e.fit_off + (arow + row - e.tc_row);
-                    const float fx = a.fit[fidx];
+                if (rok) {
                     if (near_tie(fn, fx, tie_band(d.dim))) {
                         const int tp = g.prob_tp[d.prob];
                         const int q = g.tp_row0[tp] + atomicAdd(&g.tie_cnt[tp], 1);
                         g.tie_list[q] = fidx;
-                        g.tie_off[q] = e.pop_off + (long long)(arow + row - e.tc_row) * d.dpad;
+                        g.tie_off[q] = roff;
                     } else if (fn <= fx) {
-                        acc_row[atomicAdd(&nacc_s, 1)] = row;
+                        acc_off[atomicAdd(&nacc_s, 1)] = roff;
                         a.fit[fidx] = fn;
                     }
                 }
@@ -511,12 +521,10 @@ __global__ void __launch_bounds__(kSelThreads + 32, 1) k_tc_sel(const __grid_con
             const int f4 = d.dpad >> 2, n = nacc_s * f4;
             for (int e2 = tid; e2 < n; e2 += kSelThreads) {
                 const int q = e2 / f4, c4 = e2 - q * f4;
-                const int gr = arow + acc_row[q];
-                const InstDesc e = a.desc[g.row_exec[gr]];
-                const long long off = e.pop_off + (long long)(gr - e.tc_row) * d.dpad + 4 * c4;
+                const long long off = acc_off[q] + 4 * c4;
                 *reinterpret_cast<float4*>(a.pop + off) = __ldg(reinterpret_cast<const float4*>(g.uscr + off));
             }
-            epi_sync();  // acc_row and the exchange area are reused by the next tile
+            epi_sync();  // acc_off and the exchange area are reused by the next tile
         }
     }
     tc_fence_before();

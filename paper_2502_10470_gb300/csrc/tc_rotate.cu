@@ -95,7 +95,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages], acc_full[2], acc_empty[2], part_ready[4][2], drain;
     __shared__ __align__(16) float part[2][kParts - 1][kBM][8];
     __shared__ uint32_t tmem_base;
-    __shared__ int nacc_s, acc_row[kBM];  // selection mode: rows whose trial is accepted
+    __shared__ int nacc_s;
+    __shared__ long long acc_off[kBM];  // selection mode: population offsets of the accepted rows
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
     const int nops = a.split ? 2 : 1;  // operand sets per stage (hi, and lo when split)
     const int stage_bytes = nops * (kAT + kBT);
@@ -225,6 +226,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int row = 32 * qd + lane;     // tile row of this thread
         // FP8: dequantisation factor of this row (rows past the executor are not used)
         const float zs = (a.fp8 && row < nr) ? a.ascale[arow + row] * a.bscale[d.prob] : 1.0f;
+        // selection mode: the row's executor fields and stored fitness, fetched before the chunks so that
+        // these dependent loads overlap the epilogue's work
+        bool rok = false;
+        int fidx = 0;
+        long long roff = 0;
+        float fx = 0.f;
+        if (a.sel && half == 0 && row < nr) {
+            const int k = a.row_exec[arow + row];
+            const InstDesc e = a.desc[k];
+            rok = load_strat(a.theta + 6 * k, e.np).ok;  // rows of an invalid theta are left alone
+            fidx = e.fit_off + (arow + row - e.tc_row);
+            roff = e.pop_off + (long long)(arow + row - e.tc_row) * d.dpad;
+            if (rok) fx = a.fit[fidx];
+        }
         bool eok = true;
         for (int c = 0; c < nchunks; ++c) {
             const int b = c & 1;
@@ -297,21 +312,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (!eok) {
             if (lane == 0) set_status(a.status, kStatusTimeout);
         } else if (half == 0 && row < nr) {
-            const int k = a.row_exec[arow + row];
-            const InstDesc& e = a.desc[k];  // this row's executor
             const float fn = nan_to_inf(acc.finish(d.obj, d.dim));
-            const int fidx = e.fit_off + (arow + row - e.tc_row);
             if (!a.sel) {
-                a.fu[fidx] = fn;
-            } else if (load_strat(a.theta + 6 * k, e.np).ok) {  // rows of an invalid theta stay as they are
-                const float fx = a.fit[fidx];
+                const int k = a.row_exec[arow + row];
+                const InstDesc& e = a.desc[k];  // this row's executor
+                a.fu[e.fit_off + (arow + row - e.tc_row)] = fn;
+            } else if (rok) {
                 if (near_tie(fn, fx, tie_band(d.dim))) {
                     const int tp = a.prob_tp[d.prob];
                     const int q = a.tp_row0[tp] + atomicAdd(&a.tie_cnt[tp], 1);
                     a.tie_list[q] = fidx;
-                    a.tie_off[q] = e.pop_off + (long long)(arow + row - e.tc_row) * d.dpad;
+                    a.tie_off[q] = roff;
                 } else if (fn <= fx) {
-                    acc_row[atomicAdd(&nacc_s, 1)] = row;
+                    acc_off[atomicAdd(&nacc_s, 1)] = roff;
                     a.fit[fidx] = fn;
                 }
             }
@@ -324,9 +337,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int f4 = d.dpad >> 2, n = nacc_s * f4;
         for (int e2 = tid; e2 < n; e2 += blockDim.x) {
             const int q = e2 / f4, c4 = e2 - q * f4;
-            const int gr = arow + acc_row[q];
-            const InstDesc& e = a.desc[a.row_exec[gr]];
-            const long long off = e.pop_off + (long long)(gr - e.tc_row) * d.dpad + 4 * c4;
+            const long long off = acc_off[q] + 4 * c4;
             *reinterpret_cast<float4*>(a.pop + off) = *reinterpret_cast<const float4*>(a.uscr + off);
         }
     }
