@@ -299,6 +299,7 @@ __global__ void __launch_bounds__(kSelThreads + 32, 1) k_tc_sel(const __grid_con
     __shared__ __align__(8) uint64_t afull, bfull, acc_full[2], acc_empty[2], drain, tile_ready[2];
     __shared__ uint32_t tmem_base;
     __shared__ int ep_abort_s, nacc_s, tile_of[2];  // tile in accumulator b (-1: no more tiles)
+    __shared__ int tinfo[2][6];  // that tile's first row, rows, D, D_pad, objective, problem (posted with it)
     __shared__ long long acc_off[kRows];  // population offsets of the tile's accepted rows
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
     uint8_t* As = sm;
@@ -354,11 +355,21 @@ __global__ void __launch_bounds__(kSelThreads + 32, 1) k_tc_sel(const __grid_con
                     break;
                 }
                 posted = true;
+                int arow = 0;
+                InstDesc d{};
+                if (t < g.n_tiles) {
+                    arow = g.tiles[2 * t];
+                    d = a.desc[g.row_exec[arow]];  // dim, objective and problem of every row of the tile
+                    tinfo[b][0] = arow;
+                    tinfo[b][1] = g.tiles[2 * t + 1];
+                    tinfo[b][2] = d.dim;
+                    tinfo[b][3] = d.dpad;
+                    tinfo[b][4] = d.obj;
+                    tinfo[b][5] = d.prob;
+                }
                 tile_of[b] = t < g.n_tiles ? t : -1;
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tile_ready[b])) : "memory");
                 if (t >= g.n_tiles) break;
-                const int arow = g.tiles[2 * t];
-                const InstDesc d = a.desc[g.row_exec[arow]];
                 const int kt = (d.dpad + kBK - 1) / kBK;
                 if (j > 0 && !mbar_wait(&acc_full[(j - 1) & 1], (uint32_t)((j - 1) >> 1) & 1u)) {
                     ok = false;
@@ -427,8 +438,10 @@ __global__ void __launch_bounds__(kSelThreads + 32, 1) k_tc_sel(const __grid_con
             }
             const int t = tile_of[b];
             if (t < 0) break;  // the same for every epilogue warp
-            const int arow = g.tiles[2 * t], nr = g.tiles[2 * t + 1];
-            const InstDesc d = a.desc[g.row_exec[arow]];  // dim, objective and problem of every row of the tile
+            const int arow = tinfo[b][0], nr = tinfo[b][1];
+            struct {
+                int dim, dpad, obj, prob;
+            } d = {tinfo[b][2], tinfo[b][3], tinfo[b][4], tinfo[b][5]};  // of every row of the tile
             // the row's executor fields and stored fitness, fetched before the TMEM work so that these
             // dependent loads overlap it (part-0 threads, which select)
             bool rok = false;
