@@ -9,7 +9,7 @@
 //               its 32 lanes (a lane per four coordinate uniforms, the first
 //               one at or above CR found by a ballot).  Then a lane
 //               per (row, 4-coordinate chunk), the row's fields in registers,
-//               8 rows x 4 consecutive chunks per warp step: mutation,
+//               4 rows x 8 consecutive chunks per warp step: mutation,
 //               crossover and clip (trial_chunk, the
 //               arithmetic every trial kernel shares), the FP32 trial row and
 //               the BF16 operand u - o, K-padded, to global memory.  Many small
@@ -198,20 +198,20 @@ __global__ void __launch_bounds__(kTThreads, 3) k_tc_trial2(StepArgs a, const in
     }
     __syncthreads();
 
-    // trial rows and operand rows: warp w takes rows 8 (w % 4) + lane / 4 and the
-    // 16-element column blocks w / 4, w / 4 + 2, ...; lane % 4 picks the chunk of
-    // four elements, so four lanes cover 64 contiguous bytes of a row.  A lane
-    // keeps its row's fields in registers across its chunks.
-    const int r = 8 * (warp & 3) + (lane >> 2);
+    // trial rows and operand rows: warp w takes rows 4 w + lane / 8 and every
+    // 32-element column block of them; lane % 8 picks the chunk of four elements,
+    // so eight lanes read and write a whole 128-byte line of a row at a time.  A
+    // lane keeps its row's fields in registers across its chunks.
+    const int r = 4 * warp + (lane >> 3);
     if (r0 + r >= n_rows) return;  // no barrier follows
     uint8_t* arow = aq ? aq + (size_t)(r0 + r) * kp * 2 : nullptr;  // null: FP32 GEMM, no operand rows
     const int dpad = rec[F_DPAD * kTRows + r];
-    // blocks of 4 chunks along K, up to the row's own K tiles (k_tc_sel reads no further)
-    const int nchb = ((dpad + kBK - 1) / kBK) * (kBK / 16);
+    // blocks of 8 chunks along K, up to the row's own K tiles (k_tc_sel reads no further)
+    const int nchb = ((dpad + kBK - 1) / kBK) * (kBK / 32);
     if (!rec[F_VALID * kTRows + r]) {  // rows of an invalid theta: a zero operand row
         if (!arow) return;
-        for (int cb = warp >> 2; cb < nchb; cb += 2)
-            *reinterpret_cast<uint2*>(arow + (size_t)(4 * (4 * cb + (lane & 3))) * 2) = make_uint2(0u, 0u);
+        for (int cb = 0; cb < nchb; ++cb)
+            *reinterpret_cast<uint2*>(arow + (size_t)(4 * (8 * cb + (lane & 7))) * 2) = make_uint2(0u, 0u);
         return;
     }
     const long long po = (long long)(((unsigned long long)(uint32_t)rec[F_POPHI * kTRows + r] << 32) |
@@ -240,8 +240,8 @@ __global__ void __launch_bounds__(kTThreads, 3) k_tc_trial2(StepArgs a, const in
     const float K = (float)(uint32_t)rec[F_K * kTRows + r] * (1.0f / 16777216.0f);
     const Ctr c = make_ctr(a.key, (uint32_t)rec[F_STREAM * kTRows + r], a.gen0, (uint32_t)i, epoch);
     float* U = uscr + po + oi;
-    for (int cb = warp >> 2; cb < nchb; cb += 2) {
-        const int j4 = 4 * (4 * cb + (lane & 3));
+    for (int cb = 0; cb < nchb; ++cb) {
+        const int j4 = 4 * (8 * cb + (lane & 7));
         float dd[4] = {0.f, 0.f, 0.f, 0.f};
         if (j4 < dpad) {
             // the population is read-only here: non-coherent loads
