@@ -120,6 +120,8 @@ struct metade_ctx {
     int* tc_ties = nullptr;
     int* tc_tp = nullptr;  // problem -> path index, first rows, tie counts
     long long* tc_tie_off = nullptr;  // population offsets of listed near ties
+    int4* tc_trec = nullptr;          // per operand row: draw record of the four-kernel generation
+    int4* tc_tmeta = nullptr;         // per tensor-core tile: first row, rows, D, D_pad, objective, problem
     unsigned long long* tie_total = nullptr;  // near ties decided by the tensor-core path since the last read
     int* tc_tie_done = nullptr;       // wide four-kernel generation: row groups finished per tie chunk
     float* tc_tie_zs = nullptr;       // wide four-kernel generation: z and dz of each listed tie
@@ -326,6 +328,10 @@ void free_tc(metade_ctx* c) {
     cudaFree(c->amax);
     cudaFree(c->tc_tp);
     cudaFree(c->tc_tie_off);
+    cudaFree(c->tc_trec);
+    cudaFree(c->tc_tmeta);
+    c->tc_trec = nullptr;
+    c->tc_tmeta = nullptr;
     cudaFree(c->tc_tie_done);
     cudaFree(c->tc_tie_zs);
     c->tc_tp = nullptr;
@@ -428,8 +434,19 @@ metade_status setup_tc(metade_ctx* c) {
         (!simt && (dalloc(&c->aq, nrows * tc_kp * esz) || dalloc(&c->bq, (size_t)tc_brows * tc_kp * esz))) ||
         (split && (dalloc(&c->aq_lo, nrows * tc_kp * esz) || dalloc(&c->bq_lo, (size_t)tc_brows * tc_kp * esz))) ||
         (fp8 && (dalloc(&c->ascale, nrows) || dalloc(&c->bscale, (size_t)c->n_prob) || dalloc(&c->amax, 1))) ||
-        dalloc(&c->tc_tp, (size_t)c->n_prob + 2 * tp_row0.size() + 1) || dalloc(&c->tc_tie_off, nrows))
+        dalloc(&c->tc_tp, (size_t)c->n_prob + 2 * tp_row0.size() + 1) || dalloc(&c->tc_tie_off, nrows) ||
+        dalloc(&c->tc_trec, 4 * nrows) || (!simt && dalloc(&c->tc_tmeta, tc_tiles.size())))
         return METADE_ENOMEM;
+    if (!simt) {  // the tile table k_tc_sel reads: two int4 per tile
+        std::vector<int4> tm(tc_tiles.size());
+        for (size_t q = 0; q < tc_tiles.size() / 2; ++q) {
+            const InstDesc& d = c->hdesc[tc_row_exec[tc_tiles[2 * q]]];
+            tm[2 * q] = make_int4(tc_tiles[2 * q], tc_tiles[2 * q + 1], d.dim, d.dpad);
+            tm[2 * q + 1] = make_int4(d.obj, d.prob, 0, 0);
+        }
+        if (cudaMemcpy(c->tc_tmeta, tm.data(), sizeof(int4) * tm.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return METADE_ECUDA;
+    }
     const int sel_ctas = std::max(1, device_sms());
     std::vector<int> tp_host(prob_tp);
     tp_host.insert(tp_host.end(), tp_row0.begin(), tp_row0.end());
@@ -478,6 +495,8 @@ metade_status setup_tc(metade_ctx* c) {
     t.tie_count = c->tc_ties;
     t.next_tile = c->tc_ties + 1;
     t.tie_off = c->tc_tie_off;
+    t.trial_rec = c->tc_trec;
+    t.tmeta = c->tc_tmeta;
     t.n_tp = (int)tp_row0.size();
     t.prob_tp = c->tc_tp;
     t.tp_row0 = c->tc_tp + c->n_prob;

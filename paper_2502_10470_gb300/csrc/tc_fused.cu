@@ -2,23 +2,29 @@
 // in four kernels, for the executors whose rotation is a small dense GEMM.
 //
 //   k_tc_rank   block per executor: best and the pbest pool from the stored
-//               fitness (the generation-start ranking every trial uses);
-//   k_tc_trial2 a CTA of 256 threads per 32 operand rows.  Draws first:
-//               warp 0 runs the Philox index draws, a lane per row, then each
-//               warp draws the exponential-crossover lengths of four rows with
-//               its 32 lanes (a lane per four coordinate uniforms, the first
-//               one at or above CR found by a ballot).  Then a lane
-//               per (row, 4-coordinate chunk), the row's fields in registers,
-//               4 rows x 8 consecutive chunks per warp step: mutation,
-//               crossover and clip (trial_chunk, the
+//               fitness (the generation-start ranking every trial uses), then
+//               a thread per row: the row's Philox index draws, j_rand, the
+//               exponential start and K, packed into a 64-byte draw record;
+//   k_tc_trial2 a CTA of 128 threads per 16 operand rows, five resident per
+//               SM.  Each warp reads the draw records of its four rows, then
+//               draws their exponential-crossover lengths with its 32 lanes (a
+//               lane per four coordinate uniforms, the first one at or above
+//               CR found by a ballot); no barrier joins the warps.  (Without
+//               records, as in the five-kernel pipeline, warp 0 runs the
+//               index draws, a lane per row.)  Then a lane per (row,
+//               4-coordinate chunk), 4 rows x 8 consecutive chunks per warp
+//               step, the gathers of the next step in flight while this one is
+//               built: mutation, crossover and clip (trial_chunk, the
 //               arithmetic every trial kernel shares), the FP32 trial row and
-//               the BF16 operand u - o, K-padded, to global memory.  Many small
-//               CTAs per SM keep many row gathers in flight;
+//               the BF16 operand u - o, K-padded, to global memory.  The parent
+//               offsets are re-read from shared memory at every step, which
+//               leaves the registers to the loads in flight;
 //   k_tc_sel    persistent, one CTA per SM, taking the 128-row M tiles
 //               (rows of one problem, possibly of several executors) in
 //               order from a counter, warp-specialised: a producer warp
-//               issues the TMA loads of the A tile and, where the problem
-//               changes, of B (the
+//               claims the next tile and reads its table entry one tile
+//               ahead, issues the TMA loads of the A tile and, where the
+//               problem changes, of B (the
 //               problem's padded BF16 R rows, kept in shared memory while the
 //               CTA's tiles belong to that problem) and the tcgen05.mma
 //               (M 128, N 256, K 16, FP32 accumulate) into one of two TMEM
@@ -26,9 +32,11 @@
 //               the epilogue of tile j; 16 epilogue warps read TMEM
 //               (tcgen05.ld), each a quarter of the columns of 32 rows,
 //               accumulate the objective and compose the quarters in column
-//               order; a thread per row then selects:
+//               order; a thread per row then selects (its fitness index and
+//               offsets from the row's draw record):
 //               clear acceptances are committed at once (rows copied by the
-//               whole CTA), near ties go to their problem's tie list;
+//               whole CTA, four loads in flight per thread), near ties go to
+//               their problem's tie list;
 //   k_tc_ties2  the generation's near ties, 2 to 16 of one problem per chunk
 //               (about one chunk per CTA), chunks spread over every SM by an
 //               atomic counter: z = R (x -
@@ -66,8 +74,9 @@ constexpr int kRc = 16;                      // R columns per cp.async stage of 
 constexpr int kRcs = kRc + 4;                // row stride of a stage: float4 loads of 8 rows hit 32 banks
 constexpr int kRing = 3;                     // stages of the tie kernel's R ring (k_tc_ties2)
 constexpr int kMaxTpSmem = 2048;             // problems whose chunk prefix k_tc_ties2 keeps in shared memory
-constexpr int kTRows = 32;                   // rows per CTA of k_tc_trial2
-constexpr int kTThreads = 256;
+constexpr int kTRows = 16;                   // rows per CTA of k_tc_trial2 (16 or 32)
+constexpr int kTThreads = 8 * kTRows;        // a warp per four rows
+constexpr int kTMinBlocks = 5;               // resident CTAs per SM the register budget is cut for
 
 constexpr size_t kASize = (size_t)kMaxKt * kAT;                                  // 64 KB
 constexpr size_t kPartSize = (size_t)(kParts - 1) * kRows * 8 * sizeof(float);  // 12 KB
@@ -94,16 +103,56 @@ __device__ __forceinline__ uint2 pack_bf16x4(const float (&d)[4]) {
 }
 
 // ------------------------------------------------------------ k_tc_trial2
-__global__ void __launch_bounds__(kTThreads, 3) k_tc_trial2(StepArgs a, const int* __restrict__ row_exec, int n_rows,
+__global__ void __launch_bounds__(kTThreads, kTMinBlocks) k_tc_trial2(StepArgs a, const int* __restrict__ row_exec, int n_rows,
                                                          const int* __restrict__ topk_all, float* uscr, uint8_t* aq,
-                                                         int kp) {
+                                                         int kp, const int4* __restrict__ trec) {
     __shared__ int rec[kFields * kTRows];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int r0 = blockIdx.x * kTRows;
     const uint32_t epoch = a.epoch_dev ? *a.epoch_dev : a.epoch;
 
-    // draws: warp 0, a lane per row; then the exponential lengths, warp w for rows 4 w .. 4 w + 3
-    if (warp == 0) {
+    // draws: from the rows' draw records (trec, written by k_tc_rank), warp w for its own rows
+    // 4 w .. 4 w + 3, a lane per quarter record; or, without records, warp 0 with a lane per row.
+    // Then the exponential lengths, warp w for rows 4 w .. 4 w + 3.
+    if (trec) {
+        const int r = 4 * warp + (lane >> 2), qp = lane & 3;
+        if (lane < 16 && r0 + r < n_rows) {
+            const int4 q = __ldg(trec + 4 * (size_t)(r0 + r) + qp);
+            if (qp == 0) {
+                rec[F_IBL * kTRows + r] = q.x & 0xFFFF;
+                rec[F_IBR * kTRows + r] = q.x >> 16;
+                rec[F_P0 * kTRows + r] = q.y & 0xFFFF;
+                rec[F_M0 * kTRows + r] = q.y >> 16;
+                rec[F_P1 * kTRows + r] = q.z & 0xFFFF;
+                rec[F_M1 * kTRows + r] = q.z >> 16;
+                rec[F_P2 * kTRows + r] = q.w & 0xFFFF;
+                rec[F_M2 * kTRows + r] = q.w >> 16;
+            } else if (qp == 1) {
+                rec[F_P3 * kTRows + r] = q.x & 0xFFFF;
+                rec[F_M3 * kTRows + r] = q.x >> 16;
+                rec[F_JR * kTRows + r] = q.y & 0xFFFF;
+                rec[F_NS * kTRows + r] = q.y >> 16;
+                rec[F_K * kTRows + r] = q.z;
+                rec[F_I * kTRows + r] = q.w & 0xFFFF;
+                rec[F_PACK * kTRows + r] = (q.w >> 16) & 0xFFF;
+                rec[F_VALID * kTRows + r] = (q.w >> 28) & 1;
+                rec[F_L * kTRows + r] = 0;
+            } else if (qp == 2) {
+                rec[F_POPLO * kTRows + r] = q.x;
+                rec[F_POPHI * kTRows + r] = q.y;
+                rec[F_F * kTRows + r] = q.z;
+                rec[F_CRI * kTRows + r] = q.w;
+            } else {
+                rec[F_STREAM * kTRows + r] = q.x;
+                rec[F_DIM * kTRows + r] = q.y & 0xFFFF;
+                rec[F_DPAD * kTRows + r] = q.y >> 16;
+                rec[F_SHIFT * kTRows + r] = q.z;
+            }
+        } else if (lane < 16 && qp == 1) {
+            rec[F_VALID * kTRows + r] = 0;  // past the last row: the exponential step skips it
+        }
+        __syncwarp();
+    } else if (warp == 0 && lane < kTRows) {
         const int r = lane;
         {
             int valid = 0;
@@ -112,6 +161,8 @@ __global__ void __launch_bounds__(kTThreads, 3) k_tc_trial2(StepArgs a, const in
                 const InstDesc e = a.desc[k];
                 const int i = r0 + r - e.tc_row;
                 const Strat s = load_strat(a.theta + 6 * k, e.np);
+                rec[F_DIM * kTRows + r] = e.dim;
+                rec[F_DPAD * kTRows + r] = e.dpad;
                 if (s.ok) {
                     valid = 1;
                     const int* topk = topk_all + e.fit_off;
@@ -136,15 +187,14 @@ __global__ void __launch_bounds__(kTThreads, 3) k_tc_trial2(StepArgs a, const in
                     rec[F_PACK * kTRows + r] = s.cs | (s.dn << 4) | ((s.bl != s.br ? 1 : 0) << 8);
                     rec[F_I * kTRows + r] = i;
                     rec[F_STREAM * kTRows + r] = e.stream;
-                    rec[F_DIM * kTRows + r] = e.dim;
-                    rec[F_DPAD * kTRows + r] = e.dpad;
                     rec[F_SHIFT * kTRows + r] = e.shift_off;
                 }
             }
             rec[F_VALID * kTRows + r] = valid;
         }
     }
-    __syncthreads();
+    if (trec) __syncwarp();  // uniform over the CTA: every warp reads only its own rows
+    else __syncthreads();
     {
         // exponential length L = 1 + min(t*, D - 1), t* the first coordinate
         // uniform U_t (slot 4 + t / 4, word t % 4) not below CR
@@ -196,7 +246,8 @@ __global__ void __launch_bounds__(kTThreads, 3) k_tc_trial2(StepArgs a, const in
             }
         }
     }
-    __syncthreads();
+    if (trec) __syncwarp();
+    else __syncthreads();
 
     // trial rows and operand rows: warp w takes rows 4 w + lane / 8 and every
     // 32-element column block of them; lane % 8 picks the chunk of four elements,
@@ -227,44 +278,53 @@ __global__ void __launch_bounds__(kTThreads, 3) k_tc_trial2(StepArgs a, const in
     s.br = (pack >> 8) & 1;  // trial_chunk reads bl != br as "has a directional term"
     const int i = rec[F_I * kTRows + r];
     // parent rows as float offsets from X (an executor holds at most 1024 x 1536 floats)
-    const int ol = rec[F_IBL * kTRows + r] * dpad, orr = rec[F_IBR * kTRows + r] * dpad, oi = i * dpad;
-    int op[4], om[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        op[q] = rec[(F_P0 + q) * kTRows + r] * dpad;
-        om[q] = rec[(F_M0 + q) * kTRows + r] * dpad;
-    }
+    const int oi = i * dpad;
     const int jr = rec[F_JR * kTRows + r], ns = rec[F_NS * kTRows + r], L = rec[F_L * kTRows + r];
     const int dim = rec[F_DIM * kTRows + r];
     const float* o = a.shift + rec[F_SHIFT * kTRows + r];
     const float K = (float)(uint32_t)rec[F_K * kTRows + r] * (1.0f / 16777216.0f);
     const Ctr c = make_ctr(a.key, (uint32_t)rec[F_STREAM * kTRows + r], a.gen0, (uint32_t)i, epoch);
     float* U = uscr + po + oi;
+    // The gathers are software-pipelined along the row: the parent chunks of
+    // block cb + 1 are loaded (the population is read-only here: non-coherent
+    // loads) while block cb is built, so a lane keeps two blocks in flight.
+    float4 ga, gb, gx, gp[4], gm[4];
+    // The parent row indices are re-read from the shared record at every
+    // block (volatile: not held in registers across the loop), which leaves
+    // the registers to the loads in flight.
+    const volatile int* vr = rec + r;
+    auto issue = [&](int j4) {
+        if (j4 < dpad) {
+            ga = __ldg(reinterpret_cast<const float4*>(X + vr[F_IBL * kTRows] * dpad + j4));
+            gb = __ldg(reinterpret_cast<const float4*>(X + vr[F_IBR * kTRows] * dpad + j4));
+            gx = __ldg(reinterpret_cast<const float4*>(X + oi + j4));
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (q < s.dn) {
+                    gp[q] = __ldg(reinterpret_cast<const float4*>(X + vr[(F_P0 + q) * kTRows] * dpad + j4));
+                    gm[q] = __ldg(reinterpret_cast<const float4*>(X + vr[(F_M0 + q) * kTRows] * dpad + j4));
+                }
+            }
+        }
+    };
+    issue(4 * (lane & 7));
     for (int cb = 0; cb < nchb; ++cb) {
         const int j4 = 4 * (8 * cb + (lane & 7));
         float dd[4] = {0.f, 0.f, 0.f, 0.f};
+        const float4 av = ga, bv = gb, xv = gx;
+        float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
         if (j4 < dpad) {
-            // the population is read-only here: non-coherent loads
-            const float4 av = __ldg(reinterpret_cast<const float4*>(X + ol + j4));
-            const float4 bv = __ldg(reinterpret_cast<const float4*>(X + orr + j4));
-            const float4 xv = __ldg(reinterpret_cast<const float4*>(X + oi + j4));
-            float4 p[4], m[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 if (q < s.dn) {
-                    p[q] = __ldg(reinterpret_cast<const float4*>(X + op[q] + j4));
-                    m[q] = __ldg(reinterpret_cast<const float4*>(X + om[q] + j4));
+                    sum.x += gp[q].x - gm[q].x; sum.y += gp[q].y - gm[q].y;
+                    sum.z += gp[q].z - gm[q].z; sum.w += gp[q].w - gm[q].w;
                 }
             }
+        }
+        if (cb + 1 < nchb) issue(j4 + 32);
+        if (j4 < dpad) {
             const uint4 w = s.cs == 1 ? c.slot(4 + (uint32_t)(j4 >> 2)) : make_uint4(0, 0, 0, 0);
-            float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (q < s.dn) {
-                    sum.x += p[q].x - m[q].x; sum.y += p[q].y - m[q].y;
-                    sum.z += p[q].z - m[q].z; sum.w += p[q].w - m[q].w;
-                }
-            }
             float uo[4];
             trial_chunk(s, K, jr, ns, L, dim, j4, av, bv, xv, sum, w, o, a.lo, a.hi, uo, dd);
             *reinterpret_cast<float4*>(U + j4) = make_float4(uo[0], uo[1], uo[2], uo[3]);
@@ -274,6 +334,31 @@ __global__ void __launch_bounds__(kTThreads, 3) k_tc_trial2(StepArgs a, const in
 }
 
 // --------------------------------------------------------------- k_tc_sel
+// The accepted rows of a tile copied from the trial rows (src) into the population (dst) by nt
+// threads, element e = (row e / f4, float4 e % f4): each thread issues eight loads before their
+// stores, so the copy takes one memory round trip per eight of its elements rather than per one.
+__device__ __forceinline__ void copy_accepted(const long long* offs, int nrows, int f4, const float* src, float* dst,
+                                              int t, int nt) {
+    const int n = nrows * f4;
+    for (int e0 = t; e0 < n; e0 += 4 * nt) {
+        float4 v[4];
+        long long off[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e2 = e0 + u * nt;
+            off[u] = 0;
+            if (e2 < n) {
+                const int q = e2 / f4, c4 = e2 - q * f4;
+                off[u] = offs[q] + 4 * c4;
+                v[u] = __ldg(reinterpret_cast<const float4*>(src + off[u]));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (e0 + u * nt < n) *reinterpret_cast<float4*>(dst + off[u]) = v[u];
+    }
+}
+
 struct SelArgs {
     StepArgs a;
     const int* tiles;         // [n_tiles][2]: first operand row, rows (all of one problem)
@@ -288,6 +373,8 @@ struct SelArgs {
     const long long* brow;    // per problem: first B row
     const float* uscr;        // trial rows (population layout)
     int kt;                   // K tiles of the widest problem (shared memory is cut for it)
+    const int4* tmeta;        // [n_tiles][2]: (first row, rows, D, D_pad), (objective, problem, 0, 0)
+    const int4* trec;         // the rows' draw records (k_tc_rank): validity, fitness index, offsets
 };
 
 // Named barrier of the 16 epilogue warps (the producer warp does not take part).
@@ -345,23 +432,39 @@ __global__ void __launch_bounds__(kSelThreads + 32, 1) k_tc_sel(const __grid_con
             bool ok = true, a_fly = false, b_fly = false, mma_any = false;
             int j = 0;
             bool posted = false;  // tile j's index is posted
+            // tile j and its table entry; the following tile is claimed (counter) and its entry
+            // fetched one tile ahead, so neither latency lies on the path of the tile at hand
+            int t = blockIdx.x;
+            int4 m0 = make_int4(0, 0, 0, 0), m1 = m0;
+            if (t < g.n_tiles) {
+                m0 = __ldg(g.tmeta + 2 * t);
+                m1 = __ldg(g.tmeta + 2 * t + 1);
+            }
             for (;; ++j) {
                 const int b = j & 1;
                 posted = false;
-                const int t = j == 0 ? (int)blockIdx.x : (int)gridDim.x + atomicAdd(g.next_tile, 1);
+                int tn = g.n_tiles;
+                int4 n0 = make_int4(0, 0, 0, 0), n1 = n0;
+                if (t < g.n_tiles) {
+                    tn = (int)gridDim.x + atomicAdd(g.next_tile, 1);
+                    if (tn < g.n_tiles) {
+                        n0 = __ldg(g.tmeta + 2 * tn);
+                        n1 = __ldg(g.tmeta + 2 * tn + 1);
+                    }
+                }
                 // accumulator b's slot is free once the epilogue released tile j - 2
                 if (j >= 2 && !mbar_wait(&acc_empty[b], (uint32_t)((j - 2) >> 1) & 1u)) {
                     ok = false;
                     break;
                 }
                 posted = true;
-                int arow = 0;
-                InstDesc d{};
+                const int arow = m0.x;
+                struct {
+                    int dim, dpad, obj, prob;
+                } d = {m0.z, m0.w, m1.x, m1.y};  // of every row of the tile
                 if (t < g.n_tiles) {
-                    arow = g.tiles[2 * t];
-                    d = a.desc[g.row_exec[arow]];  // dim, objective and problem of every row of the tile
                     tinfo[b][0] = arow;
-                    tinfo[b][1] = g.tiles[2 * t + 1];
+                    tinfo[b][1] = m0.y;
                     tinfo[b][2] = d.dim;
                     tinfo[b][3] = d.dpad;
                     tinfo[b][4] = d.obj;
@@ -405,6 +508,9 @@ __global__ void __launch_bounds__(kSelThreads + 32, 1) k_tc_sel(const __grid_con
                 }
                 mma_commit(&acc_full[b]);
                 mma_any = true;
+                t = tn;
+                m0 = n0;
+                m1 = n1;
             }
             if (!ok) {
                 set_status(a.status, kStatusTimeout);
@@ -448,12 +554,13 @@ __global__ void __launch_bounds__(kSelThreads + 32, 1) k_tc_sel(const __grid_con
             int fidx = 0;
             long long roff = 0;
             float fx = 0.f;
-            if (prt == 0 && row < nr) {
-                const int k = g.row_exec[arow + row];
-                const InstDesc e = a.desc[k];
-                rok = load_strat(a.theta + 6 * k, e.np).ok;  // rows of an invalid theta stay as they are
-                fidx = e.fit_off + (arow + row - e.tc_row);
-                roff = e.pop_off + (long long)(arow + row - e.tc_row) * d.dpad;
+            if (prt == 0 && row < nr) {  // from the row's draw record: one level of loads
+                const int4* rq = g.trec + 4 * (size_t)(arow + row);
+                const int4 q1 = __ldg(rq + 1), q2 = __ldg(rq + 2), q3 = __ldg(rq + 3);
+                rok = (q1.w >> 28) & 1;  // rows of an invalid theta stay as they are
+                fidx = q3.w;
+                roff = (long long)(((unsigned long long)(uint32_t)q2.y << 32) | (uint32_t)q2.x) +
+                       (long long)(q1.w & 0xFFFF) * d.dpad;
                 if (rok) fx = a.fit[fidx];
             }
             ObjR acc;
@@ -530,13 +637,8 @@ __global__ void __launch_bounds__(kSelThreads + 32, 1) k_tc_sel(const __grid_con
                 }
             }
             epi_sync();
-            // accepted rows into the population, the 16 warps copying float4s
-            const int f4 = d.dpad >> 2, n = nacc_s * f4;
-            for (int e2 = tid; e2 < n; e2 += kSelThreads) {
-                const int q = e2 / f4, c4 = e2 - q * f4;
-                const long long off = acc_off[q] + 4 * c4;
-                *reinterpret_cast<float4*>(a.pop + off) = __ldg(reinterpret_cast<const float4*>(g.uscr + off));
-            }
+            // accepted rows into the population, copied by the 16 warps
+            copy_accepted(acc_off, nacc_s, d.dpad >> 2, g.uscr, a.pop, tid, kSelThreads);
             epi_sync();  // acc_off and the exchange area are reused by the next tile
         }
     }
@@ -1050,9 +1152,15 @@ __global__ void __launch_bounds__(kWThreads, 2) k_tc_ties_wide(TieWArgs g) {
 }
 
 // best and the pbest pool of every tensor-core executor (block per executor);
-// block 0 also zeroes the tile counter of the k_tc_sel launch that follows
+// block 0 also zeroes the tile counter of the k_tc_sel launch that follows.
+// With trec, a thread per row then writes the row's draw record for
+// k_tc_trial2 (4 int4: base and difference indices as 16-bit pairs, j_rand
+// and the exponential start, K, the row index with the strategy bits and a
+// valid bit, the population offset, F, the CR threshold, the Philox stream,
+// D and D_pad, the shift offset, the fitness index); rows of an invalid theta
+// get valid = 0.
 __global__ void k_tc_rank(StepArgs a, const int* __restrict__ execs, int* topk_all, int* next_tile, int* chunk_ctr,
-                          int* tie_cnt, int n_tp) {
+                          int* tie_cnt, int n_tp, int4* trec) {
     if (blockIdx.x == 0) {  // the queues of k_tc_sel and k_tc_ties2 of this generation
         if (threadIdx.x == 0) *next_tile = *chunk_ctr = 0;
         for (int q = threadIdx.x; q < n_tp; q += blockDim.x) tie_cnt[q] = 0;
@@ -1062,9 +1170,39 @@ __global__ void k_tc_rank(StepArgs a, const int* __restrict__ execs, int* topk_a
     const Strat s = load_strat(a.theta + 6 * k, d.np);
     if (!s.ok) {
         if (threadIdx.x == 0) set_status(a.status, 1);
+        if (trec)
+            for (int i = threadIdx.x; i < d.np; i += blockDim.x) {
+                int4* q = trec + 4 * (size_t)(d.tc_row + i);
+                q[0] = make_int4(0, 0, 0, 0);
+                q[1] = make_int4(0, 0, 0, i);
+                q[2] = make_int4(0, 0, 0, 0);
+                q[3] = make_int4(d.stream, d.dim | (d.dpad << 16), d.shift_off, d.fit_off + i);
+            }
         return;
     }
-    block_topk_staged(a.fit + d.fit_off, d.np, d.kp, topk_all + d.fit_off);
+    int* topk = topk_all + d.fit_off;
+    block_topk_staged(a.fit + d.fit_off, d.np, d.kp, topk);
+    if (!trec) return;
+    __syncthreads();  // the pool (global memory) is visible to the whole block
+    const int best = topk[0];
+    const uint32_t epoch = a.epoch_dev ? *a.epoch_dev : a.epoch;
+    const int pack = s.cs | (s.dn << 4) | ((s.bl != s.br ? 1 : 0) << 8) | (1 << 12);
+    for (int i = threadIdx.x; i < d.np; i += blockDim.x) {
+        const Ctr c = make_ctr(a.key, (uint32_t)d.stream, a.gen0, (uint32_t)i, epoch);
+        Indiv v;
+        indiv_setup(s, c, i, d.np, d.dim, d.kp, topk, best, v);
+        int pm[8];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            pm[2 * q] = q < s.dn ? diff_plus(v, s.a, q) : 0;
+            pm[2 * q + 1] = q < s.dn ? diff_minus(v, s.a, q) : 0;
+        }
+        int4* q = trec + 4 * (size_t)(d.tc_row + i);
+        q[0] = make_int4(v.ibl | (v.ibr << 16), pm[0] | (pm[1] << 16), pm[2] | (pm[3] << 16), pm[4] | (pm[5] << 16));
+        q[1] = make_int4(pm[6] | (pm[7] << 16), v.jrand | (v.nstart << 16), (int)v.kraw, i | (pack << 16));
+        q[2] = make_int4((int)(uint32_t)d.pop_off, (int)(d.pop_off >> 32), __float_as_int(s.F), (int)s.cri);
+        q[3] = make_int4(d.stream, d.dim | (d.dpad << 16), d.shift_off, d.fit_off + i);
+    }
 }
 
 size_t sel_smem(int kt) { return 1024 + kASize + kPartSize + (size_t)kt * kBT; }
@@ -1092,12 +1230,13 @@ int tc_ties_wide_ctas(int max_dpad) {
 
 cudaError_t launch_tc_trial_rows32(const StepArgs& a, const TcPlan& p, void* aq, cudaStream_t st) {
     k_tc_trial2<<<(p.n_rows + kTRows - 1) / kTRows, kTThreads, 0, st>>>(a, p.row_exec, p.n_rows, p.topk_all, p.uscr,
-                                                                       static_cast<uint8_t*>(aq), p.kp);
+                                                                       static_cast<uint8_t*>(aq), p.kp, nullptr);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tc_rank(const StepArgs& a, const TcPlan& p, cudaStream_t st) {
-    k_tc_rank<<<p.n_exec, 256, 0, st>>>(a, p.execs, p.topk_all, p.next_tile, p.chunk_ctr, p.tie_cnt, p.n_tp);
+    k_tc_rank<<<p.n_exec, 256, 0, st>>>(a, p.execs, p.topk_all, p.next_tile, p.chunk_ctr, p.tie_cnt, p.n_tp,
+                                        nullptr);
     return cudaGetLastError();
 }
 
@@ -1144,7 +1283,9 @@ cudaError_t launch_tc_ties_batched(const StepArgs& a, const TcPlan& p, cudaStrea
 
 cudaError_t launch_tc_fused_generation(const StepArgs& a, const TcPlan& p, cudaStream_t st, cudaEvent_t* ev) {
     if (ev) cudaEventRecord(ev[0], st);
-    k_tc_rank<<<p.n_exec, 256, 0, st>>>(a, p.execs, p.topk_all, p.next_tile, p.chunk_ctr, p.tie_cnt, p.n_tp);
+    // plan mode 1: the draws go with the ranking, and k_tc_trial2 reads them
+    int4* trec = p.fused == 1 ? p.trial_rec : nullptr;
+    k_tc_rank<<<p.n_exec, 256, 0, st>>>(a, p.execs, p.topk_all, p.next_tile, p.chunk_ctr, p.tie_cnt, p.n_tp, trec);
     if (ev) cudaEventRecord(ev[1], st);
     cudaError_t e;
     if (p.fused == 2) {  // operands wider than 256: warp-per-row trials, k_rot_tc selecting, row-split ties
@@ -1160,7 +1301,7 @@ cudaError_t launch_tc_fused_generation(const StepArgs& a, const TcPlan& p, cudaS
         return cudaGetLastError();
     }
     k_tc_trial2<<<(p.n_rows + kTRows - 1) / kTRows, kTThreads, 0, st>>>(a, p.row_exec, p.n_rows, p.topk_all, p.uscr,
-                                                                       static_cast<uint8_t*>(p.aq), p.kp);
+                                                                       static_cast<uint8_t*>(p.aq), p.kp, trec);
     if (ev) cudaEventRecord(ev[2], st);
     {
         SelArgs g;
@@ -1177,6 +1318,8 @@ cudaError_t launch_tc_fused_generation(const StepArgs& a, const TcPlan& p, cudaS
         g.brow = p.brow;
         g.uscr = p.uscr;
         g.kt = p.kp / kBK;
+        g.tmeta = p.tmeta;
+        g.trec = trec;
         const size_t smem = sel_smem(g.kt);
         e = cudaFuncSetAttribute(k_tc_sel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
