@@ -22,9 +22,8 @@
 //   k_tc_sel    persistent, one CTA per SM, taking the 128-row M tiles
 //               (rows of one problem, possibly of several executors) in
 //               order from a counter, warp-specialised: a producer warp
-//               claims the next tile and reads its table entry one tile
-//               ahead, issues the TMA loads of the A tile and, where the
-//               problem changes, of B (the
+//               reads the tile's entry of the tile table, issues the TMA
+//               loads of the A tile and, where the problem changes, of B (the
 //               problem's padded BF16 R rows, kept in shared memory while the
 //               CTA's tiles belong to that problem) and the tcgen05.mma
 //               (M 128, N 256, K 16, FP32 accumulate) into one of two TMEM
@@ -432,25 +431,16 @@ __global__ void __launch_bounds__(kSelThreads + 32, 1) k_tc_sel(const __grid_con
             bool ok = true, a_fly = false, b_fly = false, mma_any = false;
             int j = 0;
             bool posted = false;  // tile j's index is posted
-            // tile j and its table entry; the following tile is claimed (counter) and its entry
-            // fetched one tile ahead, so neither latency lies on the path of the tile at hand
-            int t = blockIdx.x;
-            int4 m0 = make_int4(0, 0, 0, 0), m1 = m0;
-            if (t < g.n_tiles) {
-                m0 = __ldg(g.tmeta + 2 * t);
-                m1 = __ldg(g.tmeta + 2 * t + 1);
-            }
             for (;; ++j) {
                 const int b = j & 1;
                 posted = false;
-                int tn = g.n_tiles;
-                int4 n0 = make_int4(0, 0, 0, 0), n1 = n0;
+                // tile j, claimed when it is due (claiming one tile ahead measured slower), and its
+                // entry of the tile table
+                const int t = j == 0 ? (int)blockIdx.x : (int)gridDim.x + atomicAdd(g.next_tile, 1);
+                int4 m0 = make_int4(0, 0, 0, 0), m1 = m0;
                 if (t < g.n_tiles) {
-                    tn = (int)gridDim.x + atomicAdd(g.next_tile, 1);
-                    if (tn < g.n_tiles) {
-                        n0 = __ldg(g.tmeta + 2 * tn);
-                        n1 = __ldg(g.tmeta + 2 * tn + 1);
-                    }
+                    m0 = __ldg(g.tmeta + 2 * t);
+                    m1 = __ldg(g.tmeta + 2 * t + 1);
                 }
                 // accumulator b's slot is free once the epilogue released tile j - 2
                 if (j >= 2 && !mbar_wait(&acc_empty[b], (uint32_t)((j - 2) >> 1) & 1u)) {
@@ -508,9 +498,6 @@ __global__ void __launch_bounds__(kSelThreads + 32, 1) k_tc_sel(const __grid_con
                 }
                 mma_commit(&acc_full[b]);
                 mma_any = true;
-                t = tn;
-                m0 = n0;
-                m1 = n1;
             }
             if (!ok) {
                 set_status(a.status, kStatusTimeout);
@@ -1159,7 +1146,7 @@ __global__ void __launch_bounds__(kWThreads, 2) k_tc_ties_wide(TieWArgs g) {
 // valid bit, the population offset, F, the CR threshold, the Philox stream,
 // D and D_pad, the shift offset, the fitness index); rows of an invalid theta
 // get valid = 0.
-__global__ void k_tc_rank(StepArgs a, const int* __restrict__ execs, int* topk_all, int* next_tile, int* chunk_ctr,
+__global__ void __launch_bounds__(256, 8) k_tc_rank(StepArgs a, const int* __restrict__ execs, int* topk_all, int* next_tile, int* chunk_ctr,
                           int* tie_cnt, int n_tp, int4* trec) {
     if (blockIdx.x == 0) {  // the queues of k_tc_sel and k_tc_ties2 of this generation
         if (threadIdx.x == 0) *next_tile = *chunk_ctr = 0;
