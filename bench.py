@@ -623,8 +623,9 @@ def run_ours(args):
 
 TIE_GENS = 20  # inner generations the literal tie rule is timed over (its FP64 ties cost seconds per step)
 # (kernel, tensor-core width) -> DRAM bytes per launch on the full workload, from an ncu capture of the
-# current kernel (read 77.8 MB: the population once; write 87.2 MB: trial and operand rows)
-TRAFFIC_BYTES = {("k_tc_trial2", 33): 165.0e6}
+# current kernel (read 84.4 MB: the population once and the draw records; write 81.4 MB: trial and operand
+# rows, part of them still in L2 when the kernel ends)
+TRAFFIC_BYTES = {("k_tc_trial2", 33): 165.78e6}
 
 
 def measure_tie_rule(wl, probs, dev, stream, rank, tc_min_dim, gens):
