@@ -221,6 +221,31 @@ __device__ __forceinline__ int exp_length(const Ctr& c, int dim, uint32_t cri) {
     return L;
 }
 
+// exp_length by a whole warp (every lane returns L): lane l tests the uniforms
+// t = base + 4 l .. base + 4 l + 3 (slot 4 + t / 4), 128 per round, and a
+// ballot finds the first t <= D - 2 whose uniform is not below CR; then
+// L = 1 + t, or D when there is none.  The same L as exp_length, in
+// ceil((L - 1) / 128) rounds of one Philox call per lane instead of a chain
+// of up to D / 4 calls.  Call with all 32 lanes, the same c, dim and cri.
+__device__ __forceinline__ int warp_exp_length(const Ctr& c, int dim, uint32_t cri) {
+    const int lane = threadIdx.x & 31;
+    for (int base = 0; base < dim - 1; base += 128) {
+        const uint4 w = c.slot(4 + (uint32_t)(base >> 2) + (uint32_t)lane);
+        int first = 4;  // this lane's first failing word
+#pragma unroll
+        for (int q = 3; q >= 0; --q) {
+            const int t = base + 4 * lane + q;
+            if (t <= dim - 2 && (word_of(w, q) >> 8) >= cri) first = q;
+        }
+        const unsigned fails = __ballot_sync(0xFFFFFFFFu, first < 4);
+        if (fails) {
+            const int fl = __ffs(fails) - 1;
+            return 1 + base + 4 * fl + __shfl_sync(0xFFFFFFFFu, first, fl);
+        }
+    }
+    return dim;
+}
+
 // ----------------------------------------------------------- objectives
 // FP32 forms are algebraically equal to the textbook definitions but avoid
 // cancellation near the optimum:

@@ -188,11 +188,12 @@ int tc_ties_wide_ctas(int max_dpad);
 // k_tc_trial alone (trial rows and BF16 operand rows, a warp per row): the
 // trial kernel of plan mode 2
 cudaError_t launch_tc_trial_rows(const StepArgs& a, const TcPlan& p, cudaStream_t st);
-// k_tc_trial2 alone (32 rows per CTA): trial rows, and BF16 operand rows of kp
-// elements when aq is set
-cudaError_t launch_tc_trial_rows32(const StepArgs& a, const TcPlan& p, void* aq, cudaStream_t st);
-// k_tc_rank alone: pbest pools, and the queues and per-problem tie counts of the generation zeroed
-cudaError_t launch_tc_rank(const StepArgs& a, const TcPlan& p, cudaStream_t st);
+// k_tc_trial2 alone (16 rows per CTA): trial rows, and BF16 operand rows of kp
+// elements when aq is set; trec: the draw records k_tc_rank wrote (null: drawn here)
+cudaError_t launch_tc_trial_rows32(const StepArgs& a, const TcPlan& p, void* aq, const int4* trec, cudaStream_t st);
+// k_tc_rank alone: pbest pools, and the queues and per-problem tie counts of the generation zeroed;
+// with trec, the rows' draw records as well
+cudaError_t launch_tc_rank(const StepArgs& a, const TcPlan& p, int4* trec, cudaStream_t st);
 // The near ties listed per problem, FP32 difference form: k_tc_ties2 when every
 // D_pad <= 256, else k_tc_ties_wide (whose scratch the plan must hold)
 cudaError_t launch_tc_ties_batched(const StepArgs& a, const TcPlan& p, cudaStream_t st);

@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(256) k_mlp_trial(StepArgs a, const int* __rest
     const int* topk = topk_all + d.fit_off;
     Indiv v;
     indiv_setup(s, c, i, d.np, d.dim, d.kp, topk, topk[0], v);
-    const int L = s.cs == 2 ? exp_length(c, d.dim, s.cri) : 0;
+    const int L = s.cs == 2 ? warp_exp_length(c, d.dim, s.cri) : 0;  // uniform over the warp (one row)
     warp_trial(s, c, v, i, d.dim, L, a.pop + d.pop_off, d.dpad, a.shift + d.shift_off, a.lo, a.hi,
                uscr + d.pop_off + (long long)i * d.dpad, smt + (size_t)warp * ws);
 }

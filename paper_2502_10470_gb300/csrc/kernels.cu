@@ -782,7 +782,7 @@ __global__ void __launch_bounds__(512) k_fused_general(StepArgs a, const int* __
                 const Ctr c = make_ctr(a.key, (uint32_t)d.stream, gen, (uint32_t)i, epoch);
                 Indiv v;
                 indiv_setup(s, c, i, np, dim, d.kp, pb ? topk : nullptr, best, v);
-                const int L = s.cs == 2 ? exp_length(c, dim, s.cri) : 0;
+                const int L = s.cs == 2 ? warp_exp_length(c, dim, s.cri) : 0;  // uniform over the warp
                 warp_trial(s, c, v, i, dim, L, X, dp, o, a.lo, a.hi, Ug + (long long)i * dp, db);
                 __syncwarp();
                 warp_rotate<float>(dim, RT, dp, db, zb);

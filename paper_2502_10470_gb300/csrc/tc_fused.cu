@@ -1215,15 +1215,15 @@ int tc_ties_wide_ctas(int max_dpad) {
     return per_sm * sms;
 }
 
-cudaError_t launch_tc_trial_rows32(const StepArgs& a, const TcPlan& p, void* aq, cudaStream_t st) {
+cudaError_t launch_tc_trial_rows32(const StepArgs& a, const TcPlan& p, void* aq, const int4* trec, cudaStream_t st) {
     k_tc_trial2<<<(p.n_rows + kTRows - 1) / kTRows, kTThreads, 0, st>>>(a, p.row_exec, p.n_rows, p.topk_all, p.uscr,
-                                                                       static_cast<uint8_t*>(aq), p.kp, nullptr);
+                                                                       static_cast<uint8_t*>(aq), p.kp, trec);
     return cudaGetLastError();
 }
 
-cudaError_t launch_tc_rank(const StepArgs& a, const TcPlan& p, cudaStream_t st) {
+cudaError_t launch_tc_rank(const StepArgs& a, const TcPlan& p, int4* trec, cudaStream_t st) {
     k_tc_rank<<<p.n_exec, 256, 0, st>>>(a, p.execs, p.topk_all, p.next_tile, p.chunk_ctr, p.tie_cnt, p.n_tp,
-                                        nullptr);
+                                        trec);
     return cudaGetLastError();
 }
 

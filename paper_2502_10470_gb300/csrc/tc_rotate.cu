@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(256, 3) k_tc_trial(StepArgs a, const int* __re
     const int* topk = topk_all + d.fit_off;
     Indiv v;
     indiv_setup(s, c, i, d.np, d.dim, d.kp, topk, topk[0], v);
-    const int L = s.cs == 2 ? exp_length(c, d.dim, s.cri) : 0;
+    const int L = s.cs == 2 ? warp_exp_length(c, d.dim, s.cri) : 0;  // uniform over the warp (one row)
     float* U = uscr + d.pop_off + (long long)i * d.dpad;
     // operand: none (FP32 GEMM on the CUDA cores), FP8 (the row's scale needs max |u - o| first, so u - o
     // is staged in shared memory, ws floats per warp), or BF16 packed by each lane as it builds its four
@@ -801,9 +801,12 @@ cudaError_t launch_wait_check(uint32_t rounds, int arrive, long long* out, int* 
 
 cudaError_t launch_tc_generation(const StepArgs& a, const TcPlan& p, cudaStream_t st, cudaEvent_t* ev) {
     const bool batched = !a.tie_fp64;  // FP32 difference-form ties: listed per problem, batched kernels
+    // narrow FP32 rows: k_tc_rank draws every row's indices into its draw record for k_tc_trial2
+    const bool rows32 = p.simt && p.max_dpad <= 256;
+    int4* trec = batched && rows32 ? p.trial_rec : nullptr;
     if (ev) cudaEventRecord(ev[0], st);
     if (batched) {
-        cudaError_t e0 = launch_tc_rank(a, p, st);  // also zeroes the per-problem tie counts
+        cudaError_t e0 = launch_tc_rank(a, p, trec, st);  // also zeroes the per-problem tie counts
         if (e0 != cudaSuccess) return e0;
     } else {
         k_tc_prologue<<<p.n_exec, 256, 0, st>>>(a, p.execs, p.topk_all);
@@ -814,8 +817,8 @@ cudaError_t launch_tc_generation(const StepArgs& a, const TcPlan& p, cudaStream_
     const size_t smem_s = (size_t)4 * p.max_dpad * (a.tie_fp64 ? sizeof(double) : sizeof(float));
     cudaError_t e = cudaFuncSetAttribute(k_tc_trial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
     if (e != cudaSuccess) return e;
-    if (p.simt && p.max_dpad <= 256) {  // narrow FP32 rows: 32 rows per CTA, a lane per (row, 4 coordinates)
-        e = launch_tc_trial_rows32(a, p, nullptr, st);
+    if (rows32) {  // narrow FP32 rows: 16 rows per CTA, a lane per (row, 4 coordinates)
+        e = launch_tc_trial_rows32(a, p, nullptr, trec, st);
         if (e != cudaSuccess) return e;
     } else {
         k_tc_trial<<<blocks, 256, smem_t, st>>>(a, p.row_exec, p.n_rows, p.topk_all, p.uscr, p.aq,
