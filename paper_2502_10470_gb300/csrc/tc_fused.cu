@@ -1138,7 +1138,8 @@ __global__ void __launch_bounds__(kWThreads, 2) k_tc_ties_wide(TieWArgs g) {
     }
 }
 
-// best and the pbest pool of every tensor-core executor (block per executor);
+// best and the pbest pool of every tensor-core executor (block per executor;
+// best alone, by an argmin, when the strategy draws no pbest);
 // block 0 also zeroes the tile counter of the k_tc_sel launch that follows.
 // With trec, a thread per row then writes the row's draw record for
 // k_tc_trial2 (4 int4: base and difference indices as 16-bit pairs, j_rand
@@ -1168,7 +1169,13 @@ __global__ void __launch_bounds__(256, 8) k_tc_rank(StepArgs a, const int* __res
         return;
     }
     int* topk = topk_all + d.fit_off;
-    block_topk_staged(a.fit + d.fit_off, d.np, d.kp, topk);
+    __shared__ int red[64];
+    if (s.uses_pbest()) {
+        block_topk_staged(a.fit + d.fit_off, d.np, d.kp, topk);
+    } else {  // best alone, in topk[0]: such a strategy never uses the pool entry indiv_setup reads
+        const int b = block_argmin(a.fit + d.fit_off, d.np, red);
+        if (threadIdx.x == 0) topk[0] = b;
+    }
     if (!trec) return;
     __syncthreads();  // the pool (global memory) is visible to the whole block
     const int best = topk[0];

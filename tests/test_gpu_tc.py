@@ -496,3 +496,41 @@ def test_fp32_width_runs_the_cuda_core_gemm_pipeline():
             acc = np.any(npops[k] != pops[k], axis=1) | (nfits[k] != fits[k])
             np.testing.assert_array_equal(acc[decided], out["accept"].astype(bool)[decided])
     b.close()
+
+
+@pytest.mark.parametrize("prec", [1, 0], ids=["bf16-four-kernel", "fp32-cuda-core-gemm"])
+def test_invalid_theta_rows_are_left_alone_by_the_draw_record_path(prec):
+    """An executor with an invalid theta among valid ones, on the paths whose
+    draws go through k_tc_rank's draw records (the BF16 four-kernel generation,
+    and the FP32 pipeline's narrow rows at tc_min_dim = 129): the sticky status
+    is METADE_EINVAL, the invalid executor's rows and fitness are unchanged,
+    and every other executor ends exactly as in a run where that executor is
+    valid (executors draw from their own Philox streams and share no rows).
+    Then a run with every theta valid leaves the status OK."""
+    import paper_2502_10470_gb300 as M
+    wl = _wl_mid(seed=97)
+    pops, fits = random_state(wl, seed=5)
+    bad = 4  # the second executor of the D = 200 problem
+    kw = dict(prec=prec) if prec else dict(prec=0, tc_min_dim=129)
+    outs = []
+    for invalid in (True, False):
+        b = make_batch(wl, M.METADE_PATH_BATCHED, **kw)
+        plan = json.loads(M.metade_plan_info(b.ctx))
+        assert plan["tensor_core"]["kernel"] == ("k_tc_sel" if prec else "k_rot_simt")
+        b.set_population(pops, fits)
+        th = wl.theta.copy()
+        if invalid:
+            th[bad, 4] = 9  # dn outside {1..4}
+        b.set_theta(th)
+        M.metade_inner_step(b.ctx, b.pop, b.fit, b.theta, 0, 0, 3, None, None)
+        assert M.metade_sync(b.ctx) == (M.METADE_EINVAL if invalid else M.METADE_OK)
+        outs.append(b.get_population())
+        b.close()
+    (pa, fa), (pb, fb) = outs
+    np.testing.assert_array_equal(pa[bad], pops[bad])
+    np.testing.assert_array_equal(fa[bad], fits[bad])
+    for k in range(wl.n_inst):
+        if k != bad:
+            np.testing.assert_array_equal(pa[k], pb[k])
+            np.testing.assert_array_equal(fa[k], fb[k])
+    assert any(not np.array_equal(pb[k], pops[k]) for k in range(wl.n_inst) if k != bad)  # the runs did work
