@@ -345,7 +345,8 @@ METADE_API metade_status metade_plan_info(const metade_ctx *ctx, char *buf, size
  * 4 fused tile kernel with R^T streamed (128 < D_pad <= 256), 5 fused tile
  * kernel with R^T resident (D_pad <= 128), 6 MLP-objective generations, and
  * the other kernels of a tensor-core generation: 7 prologue (best, pbest
- * pool), 8 trial rows and GEMM operands, 9 selection, 10 near ties, 11 the
+ * pool, and the rows' index draws where the trial kernel reads them from
+ * it), 8 trial rows and GEMM operands, 9 selection, 10 near ties, 11 the
  * GEMM with objective, selection and commit of the BF16 four-kernel
  * generation -- then clears them.  Kind 12 counts selections of tensor-core
  * executors decided by the near-tie path (ms 0; counted whether or not

@@ -120,7 +120,7 @@ struct metade_ctx {
     int* tc_ties = nullptr;
     int* tc_tp = nullptr;  // problem -> path index, first rows, tie counts
     long long* tc_tie_off = nullptr;  // population offsets of listed near ties
-    int4* tc_trec = nullptr;          // per operand row: draw record of the four-kernel generation
+    int4* tc_trec = nullptr;          // per operand row: draw record (k_tc_rank -> k_tc_trial2, k_tc_sel)
     int4* tc_tmeta = nullptr;         // per tensor-core tile: first row, rows, D, D_pad, objective, problem
     unsigned long long* tie_total = nullptr;  // near ties decided by the tensor-core path since the last read
     int* tc_tie_done = nullptr;       // wide four-kernel generation: row groups finished per tie chunk

@@ -157,7 +157,8 @@ struct TcPlan {
     int* tie_done;           // device [n_rows] plan mode 2: row groups finished per tie chunk (kept at zero)
     float* tie_zs;           // device [n_rows][2][round_up(max_dpad, 4)] plan mode 2: z and dz of listed ties
     int wide_ctas;           // plan mode 2: CTAs of k_tc_ties_wide (as many as are resident at once)
-    int4* trial_rec;         // device [n_rows][4] plan mode 1: draw records (k_tc_rank -> k_tc_trial2, k_tc_sel)
+    int4* trial_rec;         // device [n_rows][4] draw records (k_tc_rank -> k_tc_trial2; k_tc_sel in plan mode 1),
+                             // written where k_tc_trial2 builds the rows: plan mode 1, narrow FP32 rows
     const int4* tmeta;       // device [n_tiles][2] tensor cores: (first row, rows, D, D_pad), (objective, problem)
     CUtensorMap mapA, mapB, mapAlo, mapBlo;
 };
