@@ -569,6 +569,14 @@ struct ObjR {
         for (int j = 0; j < 32; ++j)
             if (col0 + j < dim) push_t<OBJ>(v[j], OBJ == kGriewank ? rsqrtf((float)(col0 + j + 1)) * kInv2Pi : 0.f);
     }
+    // push32_t for Griewank with the factors of coordinates col0 .. col0 + 31
+    // read from kj[0 ..] (a table holding rsqrtf(j + 1) * kInv2Pi, the values
+    // push32_t computes, so the state is the same)
+    __device__ __forceinline__ void push32_griewank(const float (&v)[32], int col0, int dim, const float* kj) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (col0 + j < dim) push_t<kGriewank>(v[j], kj[j]);
+    }
     __device__ __forceinline__ void push32(int obj, const float (&v)[32], int col0, int dim) {
         switch (obj) {
         case kSphere: push32_t<kSphere>(v, col0, dim); break;

@@ -387,6 +387,7 @@ __global__ void __launch_bounds__(kSelThreads + 32, 1) k_tc_sel(const __grid_con
     __shared__ int ep_abort_s, nacc_s, tile_of[2];  // tile in accumulator b (-1: no more tiles)
     __shared__ int tinfo[2][6];  // that tile's first row, rows, D, D_pad, objective, problem (posted with it)
     __shared__ long long acc_off[kRows];  // population offsets of the tile's accepted rows
+    __shared__ float gk[kBN];             // Griewank's factor 1 / (2 pi sqrt(j + 1)) of column j
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
     uint8_t* As = sm;
     float* part = reinterpret_cast<float*>(sm + kASize);
@@ -412,6 +413,7 @@ __global__ void __launch_bounds__(kSelThreads + 32, 1) k_tc_sel(const __grid_con
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         ep_abort_s = 0;
     }
+    for (int j = tid; j < kBN; j += blockDim.x) gk[j] = rsqrtf((float)(j + 1)) * kInv2Pi;
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -575,7 +577,8 @@ __global__ void __launch_bounds__(kSelThreads + 32, 1) k_tc_sel(const __grid_con
                         }
                         nb += mcols;
                     }
-                    acc.push32(d.obj, v, col0, d.dim);
+                    if (d.obj == kGriewank) acc.push32_griewank(v, col0, d.dim, gk + col0);
+                    else acc.push32(d.obj, v, col0, d.dim);
                 }
             }
             tc_fence_before();
