@@ -562,20 +562,34 @@ struct ObjR {
         default: push4_t<kSchwefel12>(z0, z1, z2, z3, isq); break;
         }
     }
-    // 32 consecutive coordinates col0.. (those below dim), in order.
+    // 32 consecutive coordinates col0.. (those below dim), in order; a block
+    // wholly below dim (every block of a row but its last) without the test
+    // per coordinate.
     template <int OBJ>
     __device__ __forceinline__ void push32_t(const float (&v)[32], int col0, int dim) {
+        if (col0 + 32 <= dim) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-            if (col0 + j < dim) push_t<OBJ>(v[j], OBJ == kGriewank ? rsqrtf((float)(col0 + j + 1)) * kInv2Pi : 0.f);
+            for (int j = 0; j < 32; ++j)
+                push_t<OBJ>(v[j], OBJ == kGriewank ? rsqrtf((float)(col0 + j + 1)) * kInv2Pi : 0.f);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (col0 + j < dim)
+                    push_t<OBJ>(v[j], OBJ == kGriewank ? rsqrtf((float)(col0 + j + 1)) * kInv2Pi : 0.f);
+        }
     }
     // push32_t for Griewank with the factors of coordinates col0 .. col0 + 31
     // read from kj[0 ..] (a table holding rsqrtf(j + 1) * kInv2Pi, the values
     // push32_t computes, so the state is the same)
     __device__ __forceinline__ void push32_griewank(const float (&v)[32], int col0, int dim, const float* kj) {
+        if (col0 + 32 <= dim) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-            if (col0 + j < dim) push_t<kGriewank>(v[j], kj[j]);
+            for (int j = 0; j < 32; ++j) push_t<kGriewank>(v[j], kj[j]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (col0 + j < dim) push_t<kGriewank>(v[j], kj[j]);
+        }
     }
     __device__ __forceinline__ void push32(int obj, const float (&v)[32], int col0, int dim) {
         switch (obj) {
