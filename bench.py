@@ -524,7 +524,7 @@ def run_ours(args):
     sampler = ClockSampler(local)
     sampler.start()
     launches0 = M.metade_launch_count(b.ctx)
-    M.metade_profile(b.ctx, True)
+    M.metade_profile(b.ctx, PROFILE_STRIDE)
     M.metade_profile_read(b.ctx)
     evs, thetas = [], []
     for _ in range(args.steps):
@@ -543,6 +543,13 @@ def run_ours(args):
     M.metade_profile(b.ctx, False)
     if M.metade_sync(b.ctx) != 0:
         raise RuntimeError("device status after timing")
+    # the tensor-core kinds were sampled (one inner generation in PROFILE_STRIDE): their mean time per launch
+    # times the launches of the timed steps (one per kind and inner generation)
+    full = gens * args.steps
+    for k in TC_KINDS:
+        ms_k, n_k = prof[k]
+        if n_k:
+            prof[k] = (ms_k * full / n_k, full)
     total = sum(a.elapsed_time(c) for a, c in evs)
     total_max = max_over_ranks(total, world, dev)
     value = whole_job_rate(units, args.steps, world, total_max)
@@ -609,7 +616,13 @@ def run_ours(args):
                 "gpu_launches": launches,
                 "roofline": roof[0],
                 "roofline_by_kernel": roof[1],
-                "kernels": kernels, "near_ties_per_step": near_ties_per_step, "tie_fp64": tie64,
+                "kernels": kernels,
+                "kernel_timing": "CUDA events on the launching stream inside the timed steps: around the "
+                                 "tensor-core kernels of one inner generation in %d (mean per launch x the "
+                                 "launches of the steps), around every size-bucket launch; a sampled "
+                                 "generation also carries its events' gaps, so the tensor-core kinds sum to a "
+                                 "little more than the step" % PROFILE_STRIDE,
+                "near_ties_per_step": near_ties_per_step, "tie_fp64": tie64,
                 "final_error": fe,
                 "plain_fp32": plain,
                 "speedup_vs_plain": (value / plain["value"]) if plain else None,
@@ -621,6 +634,11 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# The headline's per-kernel CUDA events: around the tensor-core kernels of one inner generation in
+# PROFILE_STRIDE (events between kernels add to the step they measure); the size buckets' fused launches
+# on every call.
+PROFILE_STRIDE = 4
+TC_KINDS = ("tc_gemm", "tc_generation", "tc_prologue", "tc_trial", "tc_select", "tc_ties", "tc_sel")
 TIE_GENS = 20  # inner generations the literal tie rule is timed over (its FP64 ties cost seconds per step)
 # (kernel, tensor-core width) -> DRAM bytes per launch on the full workload, from an ncu capture of the
 # current kernel (read 84.4 MB: the population once and the draw records; write 81.4 MB: trial and operand

@@ -338,7 +338,11 @@ METADE_API metade_status metade_plan_info(const metade_ctx *ctx, char *buf, size
 
 /* Timing of the context's own kernels: with profiling enabled, calls made
  * outside stream capture record CUDA events on the context's stream around
- * each launch of the fused kernels and the tensor-core stage.  Reading waits
+ * each launch of the fused kernels and the tensor-core stage.  enable = n > 1
+ * samples the tensor-core generations: one in n (counted over the context's
+ * life) records its events, so the events perturb fewer kernel boundaries;
+ * the counts are then those of the sampled launches, and ms / count is still
+ * the mean launch time.  enable 1: every launch; 0: off.  Reading waits
  * for the stream and returns, per kind, the summed milliseconds and the number
  * of launches since the last read -- kinds: 0 fused small-D kernel, 1 fused
  * general kernel, 2 tensor-core rotation GEMM, 3 whole tensor-core generation,

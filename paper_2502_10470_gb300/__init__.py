@@ -273,7 +273,9 @@ PROFILE_KINDS = ["fused_small", "fused_general", "tc_gemm", "tc_generation", "fu
                  "mlp_generations", "tc_prologue", "tc_trial", "tc_select", "tc_ties", "tc_sel", "near_ties"]
 
 
-def metade_profile(ctx: int, enable: bool) -> None:
+def metade_profile(ctx: int, enable) -> None:
+    """enable: 0 off, 1 (or True) events around every launch, n > 1 around
+    the tensor-core kernels of one generation in n."""
     _check(_lib().metade_profile(ctx, int(enable)), "metade_profile")
 
 

@@ -102,6 +102,8 @@ struct metade_ctx {
     std::vector<GraphEntry> graphs;
     int64_t launches = 0;
     bool prof_on = false;
+    int prof_stride = 1;       // profiling: one tensor-core generation in prof_stride records its events
+    long long prof_gen = 0;    // tensor-core generations enqueued while profiling, for the sampling
     std::vector<ProfRec> prof;
     std::vector<cudaEvent_t> prof_events;  // every event the records refer to (destroyed on read)
     // large-D executors on the tensor cores (prec BF16 / BF16X3)
@@ -655,7 +657,8 @@ metade_status run_inner(metade_ctx* c, cudaStream_t st, float* pop, float* fit, 
         for (int g = 0; g < n_gens; ++g) {
             StepArgs t = step_args(c, pop, fit, theta, epoch, epoch_dev, gen0 + (uint32_t)g, 1, nullptr, nullptr);
             cudaEvent_t ev[6];
-            const bool pe = prof_tc(c, st, ev, c->tcp.fused != 0);
+            const bool sampled = !c->prof_on || c->prof_gen++ % c->prof_stride == 0;
+            const bool pe = sampled && prof_tc(c, st, ev, c->tcp.fused != 0);
             if (c->tcp.fused) {
                 CK(launch_tc_fused_generation(t, c->tcp, st, pe ? ev : nullptr));
                 *launches += 4;
@@ -1351,8 +1354,9 @@ metade_status metade_plan_info(const metade_ctx* c, char* buf, size_t len) {
 int64_t metade_launch_count(const metade_ctx* c) { return c ? c->launches : -1; }
 
 metade_status metade_profile(metade_ctx* c, int32_t enable) {
-    if (!c) return METADE_EINVAL;
+    if (!c || enable < 0) return METADE_EINVAL;
     c->prof_on = enable != 0;
+    c->prof_stride = enable > 1 ? enable : 1;
     return METADE_OK;
 }
 
