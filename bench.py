@@ -98,6 +98,19 @@ def max_over_ranks(ms: float, world: int, device) -> float:
     return float(t.item())
 
 
+def scale_sampled(prof, launches):
+    """Profile of a run whose tensor-core kinds were sampled (one inner
+    generation in PROFILE_STRIDE): each such kind's mean time per launch times
+    `launches` (one launch per kind and inner generation of the run), with the
+    count set to it; the other kinds as read."""
+    out = dict(prof)
+    for k in TC_KINDS:
+        ms_k, n_k = prof.get(k, (0.0, 0))
+        if n_k:
+            out[k] = (ms_k * launches / n_k, launches)
+    return out
+
+
 def whole_job_rate(units_per_step: float, steps: int, world: int, max_ms: float) -> float:
     """Units all ranks processed over the slowest rank's time (weak scaling:
     every rank runs the whole workload)."""
@@ -543,13 +556,7 @@ def run_ours(args):
     M.metade_profile(b.ctx, False)
     if M.metade_sync(b.ctx) != 0:
         raise RuntimeError("device status after timing")
-    # the tensor-core kinds were sampled (one inner generation in PROFILE_STRIDE): their mean time per launch
-    # times the launches of the timed steps (one per kind and inner generation)
-    full = gens * args.steps
-    for k in TC_KINDS:
-        ms_k, n_k = prof[k]
-        if n_k:
-            prof[k] = (ms_k * full / n_k, full)
+    prof = scale_sampled(prof, gens * args.steps)
     total = sum(a.elapsed_time(c) for a, c in evs)
     total_max = max_over_ranks(total, world, dev)
     value = whole_job_rate(units, args.steps, world, total_max)
